@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Pair-Poisson solves per second of the exact-exchange hot path on one GB300.
+
+One step = one exx_compute call over the water-64-scale workload (L = 23.5 bohr,
+120^3 grid, 256 orbitals in 64 clusters of 4, R_pair = 10 bohr, R_PE/R_ME =
+24/32 grid points, l_max = 6, relative residual 1e-8): pair list, gather,
+multipoles, shell potential, CG solves, E_xx reduction and D_xx scatter.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl exx|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+on its own GPU (the path has no exchange step on one node: replicas only) and
+rank 0 prints one JSON line with the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pair-Poisson solves/s at fixed E_xx error"
+UNIT = "pair solves/s"
+FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of a GB300 (profiling recipe table)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1911_10630_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_1911_10630_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(f"{kernel}|{workload}")
+    if not e or e.get("kernel_hash") != _kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _algorithmic(pairs, stats, n_pe, n_me, precision):
+    """Algorithmic DRAM bytes and FLOPs of one pair-kernel launch (per-pair
+    figures times the pairs; see the design notes for the derivation)."""
+    it = pairs["iters"].astype(np.float64)
+    npair = len(it)
+    s = 4 if precision == 1 else 8
+    cg_bytes = 6.0 * s * n_pe * it.sum()                    # d, r, p read + written once per iteration
+    refines = stats.get("refine_max", 1)
+    res_evals = npair * (1 + (2 if precision == 1 else 0))  # b, plus about two FP64 residuals per pair
+    res_bytes = 24.0 * n_pe * res_evals
+    two = (pairs["i"] != pairs["j"]).astype(np.float64)
+    gather = 16.0 * n_pe * npair
+    shell = 8.0 * (n_me - n_pe) * npair
+    scatter = float(np.sum((24.0 + 24.0 * two) * n_me))
+    flops = 38.0 * n_pe * it.sum()
+    return dict(bytes=cg_bytes + res_bytes + gather + shell + scatter, cg_bytes=cg_bytes, flops=flops,
+                refines=refines)
+
+
+def run_oracle_sample(w, phi, pairs_all, seconds=12.0, seed=0):
+    """Times the oracle on a bounded random sample of the workload's pairs."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    nthr = oracle.num_threads()
+    npair = len(pairs_all[0])
+    order = rng.permutation(npair)
+    done, t_used, k = 0, 0.0, 0
+    chunk = max(2 * nthr, 8)
+    while t_used < seconds and k < npair:
+        idx = np.sort(order[k:k + chunk])
+        sub = tuple(a[idx] for a in pairs_all)
+        t0 = time.perf_counter()
+        oracle.exx(w.cell, w.grid, phi, sub, w.r_pe, w.r_me, w.l_max, tol=w.tol, want_d=True)
+        t_used += time.perf_counter() - t0
+        done += len(idx)
+        k += chunk
+    return done / t_used, done, t_used, nthr
+
+
+def reference_arm(args, w):
+    """The oracle (FP64 C, OpenMP over pairs) on the host cores: each step a
+    bounded sample of the workload's pairs."""
+    import oracle
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    phi = w.orbitals()
+    pairs_all = oracle.pair_list(w.centers, w.cell, w.grid, w.r_pair)
+    nthr = oracle.num_threads()
+    per_step = max(2 * nthr, 8)
+    rng = np.random.default_rng(123)
+    times = []
+    for s in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(len(pairs_all[0]), per_step, replace=False))
+        sub = tuple(a[idx] for a in pairs_all)
+        t0 = time.perf_counter()
+        oracle.exx(w.cell, w.grid, phi, sub, w.r_pe, w.r_me, w.l_max, tol=w.tol, want_d=True)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = per_step * len(times) / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_orbitals": w.n, "grid": int(w.grid[0]), "r_pair_bohr": w.r_pair,
+                   "r_pe": w.r_pe, "r_me": w.r_me, "l_max": w.l_max, "tol": w.tol,
+                   "n_pair_total": int(len(pairs_all[0]))},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthr, "kind": "oracle",
+                         "sample": f"{per_step} random pairs of the workload per step (of {len(pairs_all[0])}), "
+                                   f"FP64 CG to the workload tol, D_xx scatter included"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="exx", choices=["exx", "reference"])
+    ap.add_argument("--precision", type=int, default=1, help="1: FP32 inner + FP64 refinement, 0: FP64 CG")
+    ap.add_argument("--plain-steps", type=int, default=1, help="timed steps of the plain FP64 CG comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    args = ap.parse_args()
+
+    from paper_1911_10630_gb300 import synth
+    w = synth.config1()
+    if args.impl == "reference":
+        return reference_arm(args, w)
+
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_1911_10630_gb300 import build as _build
+    _build.build(quiet=True)
+    from paper_1911_10630_gb300.exx import Exx
+
+    phi = w.orbitals()
+    centers = np.ascontiguousarray(w.centers)
+    dphi = torch.from_numpy(phi).to(dev)
+    dcen = torch.from_numpy(centers).to(dev)
+    dD = torch.empty_like(dphi)
+    stream = torch.cuda.current_stream(dev)
+    ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=args.precision,
+             threads=args.threads, ctas_per_sm=args.ctas_per_sm)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        ex.compute(dphi, dcen, dD, stream=stream)
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    solve_ms, exx_vals = [], []
+    with ClockSampler(dev.index) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            exx_vals.append(ex.compute(dphi, dcen, dD, stream=stream))
+            solve_ms.append(ex.stats()["solve_ms"])
+        ev1.record(stream)
+        barrier()
+    total_ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = ex.stats()
+    pairs = ex.pairs()
+    n_pair = st["n_pair"]
+    value = ws * n_pair * args.steps / (total_ms / 1e3)
+    n_pe, n_me = ex.ball_size()
+    alg = _algorithmic(pairs, st, n_pe, n_me, args.precision)
+    kern_ms = statistics.mean(solve_ms)
+    hbm_peak, peak_src = _peaks()
+    achieved = alg["bytes"] / (kern_ms / 1e3) / 1e9
+    workload_key = f"{w.name}|p{args.precision}"
+    roofline = {"kernel": "pair_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": peak_src,
+                "traffic": _traffic("pair_kernel", workload_key),
+                "algorithmic_bytes_per_launch": alg["bytes"], "kernel_ms": kern_ms}
+    if args.precision == 0:
+        fl = alg["flops"] / (kern_ms / 1e3) / 1e12
+        roofline.update({"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": fl / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64 rate"})
+
+    extra = {}
+    if rank == 0 and args.precision == 1 and args.plain_steps > 0:
+        ex0 = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=0)
+        ex0.compute(dphi, dcen, dD, stream=stream)
+        torch.cuda.synchronize(dev)
+        t = []
+        for _ in range(args.plain_steps):
+            ev0.record(stream)
+            e0 = ex0.compute(dphi, dcen, dD, stream=stream)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            t.append(ev0.elapsed_time(ev1))
+        st0 = ex0.stats()
+        extra["plain_fp64_cg"] = {"value": n_pair / (statistics.mean(t) / 1e3), "unit": UNIT,
+                                  "ms_per_step": statistics.mean(t), "E_xx": e0,
+                                  "dE_vs_fast_per_orbital": abs(e0 - exx_vals[-1]) / w.n,
+                                  "iters_p50": st0["iters_p50"], "iters_max": st0["iters_max"]}
+        extra["speedup_vs_plain_fp64_cg"] = value / ws / extra["plain_fp64_cg"]["value"]
+        ex0.close()
+
+    e2e = None
+    if not args.no_e2e:
+        hphi = torch.from_numpy(phi).pin_memory()
+        hD = torch.empty(phi.shape, dtype=torch.float64).pin_memory()
+        hc = torch.from_numpy(centers).pin_memory()
+        exh = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=args.precision)
+        exh.compute_host(hphi, hc, hD, stream=stream)  # warm-up (allocates the device copies)
+        barrier()
+        t0 = time.perf_counter()
+        nrep = max(1, min(args.steps, 3))
+        for _ in range(nrep):
+            exh.compute_host(hphi, hc, hD, stream=stream)
+        barrier()
+        dt = (time.perf_counter() - t0) / nrep
+        e2e = {"value": ws * n_pair / dt, "unit": UNIT, "h2d_bytes_per_step": int(phi.nbytes + centers.nbytes),
+               "d2h_bytes_per_step": int(phi.nbytes + 8), "ms_per_step": dt * 1e3}
+        exh.close()
+        del hphi, hD
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        pairs_all = (pairs["i"], pairs["j"], pairs["g"])
+        v, done, used, nthr = run_oracle_sample(w, phi, pairs_all)
+        cpu = {"value": v, "unit": UNIT, "cores": nthr, "kind": "oracle",
+               "sample": f"{done} random pairs of the workload ({used:.1f} s), FP64 CG to tol {w.tol}, "
+                         f"D_xx scatter included"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == 1 else "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_orbitals": w.n, "grid": int(w.grid[0]), "cell_bohr": float(w.cell[0]),
+                       "r_pair_bohr": w.r_pair, "r_pe": w.r_pe, "r_me": w.r_me, "l_max": w.l_max, "tol": w.tol,
+                       "n_pair": n_pair, "precision": "fp32 inner CG + fp64 refinement" if args.precision == 1
+                       else "fp64 CG", "l2": "inputs larger than L2 (orbitals 3.5 GB, D_xx 3.5 GB)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "solver": f"{st['solver_kind']}x{st['cluster_size']} ctas={st['grid_ctas']} "
+                                 f"threads={st['threads']}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 6 * args.steps,
+            "clocks": clk.summary(),
+            "E_xx": exx_vals[-1],
+            "cg": {"iters_p50": st["iters_p50"], "iters_p99": st["iters_p99"], "iters_max": st["iters_max"],
+                   "refine_max": st["refine_max"], "point_iters": st["point_iters"], "n_nonconv": st["n_nonconv"]},
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

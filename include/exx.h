@@ -1,0 +1,209 @@
+/*
+ * exx.h -- C ABI of the GB300 pair-Poisson exact-exchange library.
+ *
+ * The library evaluates the real-space exact exchange of localized orbitals
+ * (Ko et al., arXiv:1911.10630): for every pair of orbitals whose centres are
+ * closer than R_pair it forms rho_ij = phi_i phi_j on a ball of radius R_PE
+ * around the pair centre, sets Dirichlet values from a multipole expansion on
+ * the shell out to R_ME, solves the reduced Poisson system with the order-6,
+ * 19-point Laplacian by conjugate gradient, and returns
+ *     E_xx  = - sum over ordered pairs of int_PE rho_ij v_ij      (Eq. exx_omega)
+ *     D^i  += v_ij phi_j   on the ME ball of each pair            (Eqs. Dxx_mlwf,
+ *                                                                   Dxx_mlwf_omega)
+ * The input and output contract is the exx module's (Sec. III: the orbitals on
+ * the real-space grid in, E_xx and {D_xx^i} out).
+ *
+ * Conventions for every entry point:
+ *   - Hartree atomic units; the hybrid fraction a_x is NOT applied.
+ *   - Grids are orthorhombic, N0 x N1 x N2 points, numbered 0..N-1 along each
+ *     axis (Eq. l2g), point g at r = g * delta with delta_a = L_a / N_a.
+ *   - Orbital and force arrays are FP64, shape [n][N0][N1][N2], C order (the
+ *     last index fastest), one full grid per orbital.
+ *   - Radii R_PE and R_ME are in grid points; the balls are the integer sets
+ *     |o|^2 <= R_PE^2 and R_PE^2 < |o|^2 <= R_ME^2 (Algorithm 2).
+ *   - Every function returns an exx_status; none aborts, traps or exits.
+ *     After an error, exx_last_error() describes it.
+ *   - Pointers marked "device" must be CUDA device (or managed) memory of the
+ *     current device; "host" pointers are ordinary host memory (pinned memory
+ *     makes the host-buffer entry points faster).
+ *   - The caller owns every array it passes; the library owns its workspace.
+ *   - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef EXX_GB300_H
+#define EXX_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct exx_ctx exx_ctx;
+
+typedef enum {
+    EXX_OK = 0,
+    EXX_EINVAL = -1,   /* invalid argument (shape, radius, pointer, option)          */
+    EXX_ENOMEM = -2,   /* device or host allocation failed                           */
+    EXX_ECUDA = -3,    /* a CUDA call failed (no device, launch error, ...)           */
+    EXX_ENOCONV = -4,  /* some CG solves reached max_iter; all outputs still written */
+    EXX_ENOPAIR = -5   /* a query named a pair that is not in the current list       */
+} exx_status;
+
+/* Solver choices. exx_default_options() fills the defaults noted here. */
+typedef struct {
+    int precision;     /* 0: FP64 conjugate gradient (default).
+                          1: FP32 inner CG with FP64 residual refinement: the
+                             residual r = 4 pi rho + lap v is recomputed in FP64
+                             after each inner solve, and the stop test is FP64. */
+    int batched;       /* 0: pairs in list order. 1: largest pairs first from a
+                          device work queue, the whole call captured once and
+                          replayed as a CUDA graph (default 1).                  */
+    int warm_start;    /* 0: CG from zero (default). 1: previous call's v_ij for
+                          pairs kept from the previous call (same i, j, grid
+                          centre and radii); other pairs start from zero.        */
+    int radii_mode;    /* 0: fixed R_PE / R_ME for all pairs (default).
+                          1: per-pair radii from the orbital exponents passed to
+                             exx_compute (alphas), clamped to [12, R_PE]; R_PE and
+                             R_ME of exx_init are then the maxima.               */
+    int max_iter;      /* CG iteration cap per solve (default 20000).            */
+    int inner_max_iter;/* FP32 inner iterations per refinement step (default 4000) */
+    double inner_tol;  /* FP32 inner relative tolerance (default 1e-5).          */
+    int threads;       /* threads per CTA, 0 = library choice.                   */
+    int ctas_per_sm;   /* resident CTAs per SM, 0 = library choice.              */
+    int solver_kind;   /* 0 = library choice; 1 = one CTA per pair with state in
+                          global memory; 2 = one thread-block cluster per pair
+                          with the FP32 inner state in shared memory.            */
+    int cluster_size;  /* CTAs per cluster for solver_kind 2 (0 = library choice) */
+} exx_options;
+
+typedef struct {
+    int n_pair;            /* pairs in the last call                             */
+    int n_nonconv;         /* solves that hit max_iter                           */
+    int iters_max;         /* max CG iterations over pairs (inner, summed)        */
+    int iters_p50;         /* median CG iterations                               */
+    int iters_p99;         /* 99th percentile CG iterations                      */
+    long long iters_total; /* sum of CG iterations over pairs                     */
+    long long point_iters; /* sum over pairs of N_PE x CG iterations              */
+    int refine_max;        /* max FP64 refinement steps (precision 1)             */
+    double solve_ms;       /* device time of the pair kernel in the last call      */
+    double total_ms;       /* device time of the whole call (events on the stream) */
+    int n_pe, n_me;        /* ball sizes for the fixed radii                       */
+    int solver_kind;       /* solver that ran                                      */
+    int cluster_size;      /* CTAs per pair                                        */
+    int grid_ctas;         /* CTAs launched for the pair kernel                    */
+    int threads;           /* threads per CTA                                      */
+} exx_stats;
+
+/* Defaults described in exx_options. */
+exx_options exx_default_options(void);
+
+/*
+ * Creates a context for one grid and one set of method parameters.
+ *   cell[3]   orthorhombic cell lengths L_a (bohr), > 0
+ *   grid[3]   grid points N_a, >= 2 R_ME + 1 (a ball never overlaps its own
+ *             periodic image)
+ *   r_pair    pair cutoff in bohr, strict |C_i - C_j| < r_pair under the
+ *             minimum image (Sec. III.C Step II); INFINITY keeps all pairs
+ *   r_pe      PE ball radius in grid points, 1 <= r_pe
+ *   r_me      ME ball radius in grid points, r_me >= r_pe + 3 (the shell must
+ *             hold the stencil's reach, Sec. IV.A) and r_me <= 63
+ *   l_max     multipole order of Eqs. me/mepole, 0 <= l_max <= 6
+ *   tol       relative residual ||r||_2 <= tol ||b||_2 on the PE ball, where
+ *             b = 4 pi rho + boundary charge (Eq. pe_mat_red); 0 < tol < 1
+ *   opt       NULL for exx_default_options()
+ * Allocates the device tables on the current device. On error *out is NULL.
+ * Errors: EXX_EINVAL (checked before any CUDA call), EXX_ECUDA, EXX_ENOMEM.
+ */
+exx_status exx_init(exx_ctx **out, const double cell[3], const int grid[3], double r_pair, int r_pe,
+                    int r_me, int l_max, double tol, const exx_options *opt);
+
+/*
+ * One evaluation of E_xx and {D_xx^i}.
+ *   orbitals  device, [n][N0][N1][N2] FP64, read only
+ *   centers   device, [n][3] FP64 orbital centres in bohr (any real values;
+ *             they are used through the minimum image)
+ *   n         number of orbitals, 1 <= n <= 65535
+ *   alphas    device, [n] FP64 Gaussian-like exponents used only when
+ *             radii_mode = 1, else ignored (may be NULL)
+ *   e_xx      host, receives E_xx
+ *   d_xx      device, [n][N0][N1][N2] FP64, overwritten with D_xx (zeroed by
+ *             the library first); must not alias orbitals
+ *   stream    cudaStream_t, NULL = the legacy default stream
+ * Work is ordered on the stream; the call returns after E_xx is on the host,
+ * so d_xx is complete when it returns. The arrays must stay valid until then.
+ * Errors: EXX_EINVAL, EXX_ECUDA, EXX_ENOMEM, EXX_ENOCONV (outputs written).
+ */
+exx_status exx_compute(exx_ctx *ctx, const double *orbitals, const double *centers, int n,
+                       const double *alphas, double *e_xx, double *d_xx, void *stream);
+
+/*
+ * Same as exx_compute with HOST buffers: copies orbitals, centers (and alphas)
+ * to the device, runs exx_compute and copies D_xx back into d_xx_host.
+ *   orbitals_host [n][N0][N1][N2], centers_host [n][3], alphas_host [n] or NULL,
+ *   d_xx_host [n][N0][N1][N2] (written). Device buffers are held by the
+ *   context between calls and grown when n grows.
+ */
+exx_status exx_compute_host(exx_ctx *ctx, const double *orbitals_host, const double *centers_host,
+                            int n, const double *alphas_host, double *e_xx, double *d_xx_host,
+                            void *stream);
+
+/* Statistics of the last exx_compute / exx_compute_host call. */
+exx_status exx_get_stats(const exx_ctx *ctx, exx_stats *out);
+
+/*
+ * Pair list of the last call (Sec. III.C Step II), in list order (i-major, j
+ * ascending), with per-pair results:
+ *   pi, pj        orbital indices, i <= j
+ *   g             3 ints per pair: grid point nearest the pair centre, in [0, N)
+ *   radii         2 ints per pair: R_PE, R_ME used for the pair (may be NULL)
+ *   e_pair        sum over the PE ball of rho_ij v_ij dV (may be NULL)
+ *   iters         CG iterations of the pair (may be NULL)
+ * All host arrays of capacity cap pairs; *n_pair receives the count. Any
+ * output pointer may be NULL. EXX_EINVAL if cap is too small.
+ */
+exx_status exx_get_pairs(const exx_ctx *ctx, int *pi, int *pj, int *g, int *radii, double *e_pair,
+                         int *iters, int cap, int *n_pair);
+
+/*
+ * Intermediates of one pair of the last call, for step-level checks:
+ *   index     position in the pair list of the last call
+ *   rho       host [N_ME]: phi_i phi_j on the ME ball, PE points first (may be NULL)
+ *   v         host [N_ME]: the potential: CG solution on the PE ball, multipole
+ *             expansion (Eq. me) on the shell (may be NULL)
+ *   b         host [N_PE]: right-hand side 4 pi rho + boundary charge of
+ *             Eq. pe_mat_red written as A v = b (may be NULL)
+ * Ball points are in Algorithm 2 order (lexicographic (x, y, z) within the PE
+ * ball, then within the shell). Re-solves the pair on the device with the
+ * context's options. EXX_ENOPAIR if index is out of range.
+ */
+exx_status exx_debug_pair(exx_ctx *ctx, const double *orbitals, int index, double *rho, double *v,
+                          double *b, void *stream);
+
+/*
+ * Applies A = -lap_PE (the 19-point stencil of Eq. d2_1 restricted to the PE
+ * ball, zero outside it) to p on the PE ball of the context's R_PE.
+ *   p, ap     device, [N_PE] FP64 in Algorithm 2 order
+ */
+exx_status exx_apply_operator(exx_ctx *ctx, const double *p, double *ap, void *stream);
+
+/* Ball sizes for the context's fixed radii. */
+exx_status exx_ball_size(const exx_ctx *ctx, int *n_pe, int *n_me);
+
+/*
+ * Loads the learned warm-start model (not available in this build: returns
+ * EXX_EINVAL and leaves the context unchanged).
+ */
+exx_status exx_load_guess_model(exx_ctx *ctx, const void *weights, size_t bytes);
+
+/* Message of the last error on this context (or of the last failed exx_init
+ * when ctx is NULL); owned by the library, valid until the next call. */
+const char *exx_last_error(const exx_ctx *ctx);
+
+/* Frees the context and its device memory. NULL is ignored. */
+void exx_destroy(exx_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXX_GB300_H */

@@ -1,0 +1,656 @@
+// exx_api.cu -- the C ABI (include/exx.h): context, validation, workspace,
+// launch sequence and CUDA-graph replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/exx.h"
+#include "exx_geometry.h"
+#include "exx_internal.h"
+
+namespace exx {
+cudaError_t launch_pair_list(int n, const double* centers, const double L[3], const double delta[3], const int N[3],
+                             double r_pair, int r_pe, int r_me, int* counts, int* offsets, int* n_pair, int* queue,
+                             PairRec* pairs, cudaStream_t st);
+cudaError_t launch_zero(double* p, long long n, int num_sms, cudaStream_t st);
+cudaError_t launch_exx_reduce(const PairRec* pairs, const int* n_pair, const double* e_pair, double* out,
+                              cudaStream_t st);
+cudaError_t set_multipole_const(const MultipoleConst& mc);
+size_t pair_kernel_smem(int Rc, int r_pe_max);
+cudaError_t launch_pair_kernel(const SolveParams& P, int threads, bool mixed, int grid, size_t smem, cudaStream_t st);
+cudaError_t pair_kernel_occupancy(int threads, bool mixed, size_t smem, int* blocks_per_sm);
+cudaError_t launch_debug_readback(const SolveParams& P, const PairRec& pr, double* rho_me, double* v_me,
+                                  cudaStream_t st);
+cudaError_t launch_apply(const SolveParams& P, const double* p, double* ap, cudaStream_t st);
+}  // namespace exx
+
+using namespace exx;
+
+struct exx_ctx {
+    // parameters
+    double cell[3];
+    int grid[3];
+    double delta[3];
+    double dV;
+    double r_pair;
+    int r_pe, r_me, lmax;
+    double tol;
+    exx_options opt;
+    long long ngrid;
+
+    // device
+    int device = 0;
+    int num_sms = 0;
+
+    // geometry
+    HostBall hb;
+    void* geo_mem = nullptr;  // device tables
+    BallGeo* d_geos = nullptr;
+    BallGeo geo_host;
+
+    // workspace
+    char* ws = nullptr;
+    size_t slot_bytes = 0;
+    int n_slots = 0;
+    int threads = 512;
+    size_t smem = 0;
+    SolveParams P;
+
+    // pair buffers
+    int cap_n = 0;
+    long long cap_pairs = 0;
+    int* d_counts = nullptr;
+    int* d_offsets = nullptr;
+    PairRec* d_pairs = nullptr;
+    double* d_epair = nullptr;
+    int* d_iters = nullptr;
+    int* d_refines = nullptr;
+    int* d_scalars = nullptr;  // [0] n_pair, [1] queue, [2] nonconv
+    double* d_exx = nullptr;
+    double* h_exx = nullptr;   // pinned
+
+    // host-buffer path
+    double* d_orb = nullptr;
+    double* d_dxx = nullptr;
+    double* d_cent = nullptr;
+    double* d_alpha = nullptr;
+    size_t host_cap_bytes = 0;
+    int host_cap_n = 0;
+
+    // graph cache
+    cudaGraphExec_t gexec = nullptr;
+    const void* g_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int g_n = -1;
+    cudaStream_t g_stream = nullptr;
+
+    // timing
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool timed = false;
+
+    // last call
+    int last_n = 0;
+    const double* last_orb = nullptr;
+    exx_stats stats;
+    std::string err;
+};
+
+static thread_local std::string g_init_err;
+
+static exx_status fail(exx_ctx* c, exx_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_init_err = msg;
+    return s;
+}
+
+static exx_status cuda_fail(exx_ctx* c, cudaError_t e, const char* where) {
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
+    return fail(c, e == cudaErrorMemoryAllocation ? EXX_ENOMEM : EXX_ECUDA, buf);
+}
+
+#define CK(call, where)                                  \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+    } while (0)
+
+extern "C" exx_options exx_default_options(void) {
+    exx_options o;
+    std::memset(&o, 0, sizeof(o));
+    o.precision = 0;
+    o.batched = 1;
+    o.warm_start = 0;
+    o.radii_mode = 0;
+    o.max_iter = 20000;
+    o.inner_max_iter = 4000;
+    o.inner_tol = 1e-5;
+    o.threads = 0;
+    o.ctas_per_sm = 0;
+    o.solver_kind = 0;
+    o.cluster_size = 0;
+    return o;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static void free_pairs(exx_ctx* c) {
+    cudaFree(c->d_counts);
+    cudaFree(c->d_offsets);
+    cudaFree(c->d_pairs);
+    cudaFree(c->d_epair);
+    cudaFree(c->d_iters);
+    cudaFree(c->d_refines);
+    c->d_counts = c->d_offsets = nullptr;
+    c->d_pairs = nullptr;
+    c->d_epair = nullptr;
+    c->d_iters = c->d_refines = nullptr;
+    c->cap_n = 0;
+    c->cap_pairs = 0;
+}
+
+static void drop_graph(exx_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->g_n = -1;
+}
+
+extern "C" void exx_destroy(exx_ctx* c) {
+    if (!c) return;
+    drop_graph(c);
+    free_pairs(c);
+    cudaFree(c->d_scalars);
+    cudaFree(c->d_exx);
+    if (c->h_exx) cudaFreeHost(c->h_exx);
+    cudaFree(c->ws);
+    cudaFree(c->geo_mem);
+    cudaFree(c->d_orb);
+    cudaFree(c->d_dxx);
+    cudaFree(c->d_cent);
+    cudaFree(c->d_alpha);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int grid[3], double r_pair, int r_pe,
+                               int r_me, int l_max, double tol, const exx_options* opt) {
+    exx_ctx* c = nullptr;
+    if (!out) return fail(nullptr, EXX_EINVAL, "exx_init: out is NULL");
+    *out = nullptr;
+    if (!cell || !grid) return fail(nullptr, EXX_EINVAL, "exx_init: cell or grid is NULL");
+    for (int a = 0; a < 3; ++a) {
+        if (!(cell[a] > 0.0) || !std::isfinite(cell[a])) return fail(nullptr, EXX_EINVAL, "exx_init: cell lengths must be finite and > 0");
+        if (grid[a] < 1 || grid[a] > 4096) return fail(nullptr, EXX_EINVAL, "exx_init: grid sizes must be in [1, 4096]");
+    }
+    if (!(r_pair > 0.0)) return fail(nullptr, EXX_EINVAL, "exx_init: r_pair must be > 0 (INFINITY keeps all pairs)");
+    if (r_pe < 1) return fail(nullptr, EXX_EINVAL, "exx_init: r_pe must be >= 1");
+    if (r_me < r_pe + 3) return fail(nullptr, EXX_EINVAL, "exx_init: r_me must be >= r_pe + 3 (the shell holds the stencil reach)");
+    if (r_me > 63) return fail(nullptr, EXX_EINVAL, "exx_init: r_me must be <= 63");
+    for (int a = 0; a < 3; ++a)
+        if (2 * r_me + 1 > grid[a]) return fail(nullptr, EXX_EINVAL, "exx_init: 2 r_me + 1 must not exceed any grid size");
+    if (l_max < 0 || l_max > kLmaxMax) return fail(nullptr, EXX_EINVAL, "exx_init: l_max must be in [0, 6]");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(nullptr, EXX_EINVAL, "exx_init: tol must be in (0, 1)");
+    exx_options o = opt ? *opt : exx_default_options();
+    if (o.precision != 0 && o.precision != 1) return fail(nullptr, EXX_EINVAL, "exx_init: precision must be 0 or 1");
+    if (o.radii_mode != 0) return fail(nullptr, EXX_EINVAL, "exx_init: radii_mode 1 is not available in this build");
+    if (o.warm_start != 0) return fail(nullptr, EXX_EINVAL, "exx_init: warm_start 1 is not available in this build");
+    if (o.max_iter <= 0) o.max_iter = 20000;
+    if (o.inner_max_iter <= 0) o.inner_max_iter = 4000;
+    if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) o.inner_tol = 1e-5;
+    if (o.threads != 0 && o.threads != 256 && o.threads != 512 && o.threads != 1024)
+        return fail(nullptr, EXX_EINVAL, "exx_init: threads must be 0, 256, 512 or 1024");
+    if (o.solver_kind != 0 && o.solver_kind != 1) return fail(nullptr, EXX_EINVAL, "exx_init: solver_kind 2 is not available in this build");
+
+    c = new exx_ctx();
+    std::memset(&c->stats, 0, sizeof(c->stats));
+    c->opt = o;
+    for (int a = 0; a < 3; ++a) {
+        c->cell[a] = cell[a];
+        c->grid[a] = grid[a];
+        c->delta[a] = cell[a] / (double)grid[a];
+    }
+    c->dV = c->delta[0] * c->delta[1] * c->delta[2];
+    c->ngrid = (long long)grid[0] * grid[1] * grid[2];
+    c->r_pair = r_pair;
+    c->r_pe = r_pe;
+    c->r_me = r_me;
+    c->lmax = l_max;
+    c->tol = tol;
+
+    auto bail = [&](exx_status s) {
+        g_init_err = c->err;
+        exx_destroy(c);
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaGetDevice"));
+    e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaDeviceGetAttribute"));
+
+    // constants of the multipole expansion (identical for every context)
+    static MultipoleConst mc;
+    static bool mc_built = false;
+    if (!mc_built) {
+        build_multipole_const(mc);
+        mc_built = true;
+    }
+    e = set_multipole_const(mc);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpyToSymbol(multipoles)"));
+
+    // ball geometry (Algorithm 2), cube radius Rc = R_ME
+    const int Rc = r_me, S = 2 * Rc + 1;
+    build_ball(c->hb, r_pe, r_me, Rc);
+    const HostBall& B = c->hb;
+    size_t o_cube = 0;
+    size_t o_off = align256(o_cube + sizeof(int) * B.n_me);
+    size_t o_rpe = align256(o_off + sizeof(int) * B.n_me);
+    size_t o_rme = align256(o_rpe + sizeof(RowRec) * B.rows_pe.size());
+    size_t o_pl = align256(o_rme + sizeof(RowRec) * B.rows_me.size());
+    size_t o_geo = align256(o_pl + sizeof(int) * B.plane_pe.size());
+    size_t geo_bytes = align256(o_geo + sizeof(BallGeo));
+    e = cudaMalloc(&c->geo_mem, geo_bytes);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(geometry)"));
+    char* gm = (char*)c->geo_mem;
+    BallGeo G;
+    G.r_pe = r_pe;
+    G.r_me = r_me;
+    G.n_pe = B.n_pe;
+    G.n_me = B.n_me;
+    G.n_rows_pe = (int)B.rows_pe.size();
+    G.n_rows_me = (int)B.rows_me.size();
+    G.pt_cube = (const int*)(gm + o_cube);
+    G.pt_off = (const int*)(gm + o_off);
+    G.rows_pe = (const RowRec*)(gm + o_rpe);
+    G.rows_me = (const RowRec*)(gm + o_rme);
+    G.plane_pe = (const int*)(gm + o_pl);
+    c->geo_host = G;
+    c->d_geos = (BallGeo*)(gm + o_geo);
+    if ((e = cudaMemcpy(gm + o_cube, B.cube.data(), sizeof(int) * B.n_me, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(gm + o_off, B.off.data(), sizeof(int) * B.n_me, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(gm + o_rpe, B.rows_pe.data(), sizeof(RowRec) * B.rows_pe.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(gm + o_rme, B.rows_me.data(), sizeof(RowRec) * B.rows_me.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(gm + o_pl, B.plane_pe.data(), sizeof(int) * B.plane_pe.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(gm + o_geo, &G, sizeof(BallGeo), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(cuda_fail(c, e, "cudaMemcpy(geometry)"));
+
+    // workspace slots
+    const long long S3 = (long long)S * S * S;
+    SolveParams& P = c->P;
+    std::memset(&P, 0, sizeof(P));
+    size_t off = 0;
+    P.off_vcube = off; off = align256(off + sizeof(double) * S3);
+    P.off_pcube = off; off = align256(off + sizeof(double) * S3);
+    P.off_p32 = off; off = align256(off + sizeof(float) * S3);
+    P.off_rho = off; off = align256(off + sizeof(double) * B.n_pe);
+    P.off_r = off; off = align256(off + sizeof(double) * B.n_pe);
+    P.off_d = off; off = align256(off + sizeof(double) * B.n_pe);
+    P.off_ap = off; off = align256(off + sizeof(double) * B.n_pe);
+    P.off_r32 = off; off = align256(off + sizeof(float) * B.n_pe);
+    P.off_d32 = off; off = align256(off + sizeof(float) * B.n_pe);
+    P.off_ap32 = off; off = align256(off + sizeof(float) * B.n_pe);
+    P.off_rows = off; off = align256(off + sizeof(double) * 8 * B.rows_pe.size());
+    c->slot_bytes = off;
+
+    c->threads = o.threads ? o.threads : 512;
+    c->smem = pair_kernel_smem(Rc, r_pe);
+    int bps = 0;
+    e = pair_kernel_occupancy(c->threads, o.precision == 1, c->smem, &bps);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
+    if (bps < 1) return bail(fail(c, EXX_ECUDA, "pair kernel does not fit on an SM"));
+    int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, bps) : std::min(bps, 2);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    long long want = (long long)c->num_sms * per_sm;
+    long long fit = (long long)(0.25 * (double)free_b / (double)c->slot_bytes);
+    c->n_slots = (int)std::max(1LL, std::min(want, fit));
+    e = cudaMalloc(&c->ws, c->slot_bytes * (size_t)c->n_slots);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(workspace)"));
+    e = cudaMemset(c->ws, 0, c->slot_bytes * (size_t)c->n_slots);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemset(workspace)"));
+
+    e = cudaMalloc(&c->d_scalars, sizeof(int) * 8);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(scalars)"));
+    e = cudaMalloc(&c->d_exx, sizeof(double) * 2);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(exx)"));
+    e = cudaMallocHost(&c->h_exx, sizeof(double) * 2);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMallocHost"));
+    for (auto& ev : c->ev) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaEventCreate"));
+    }
+
+    // fixed kernel parameters
+    for (int a = 0; a < 3; ++a) {
+        P.N[a] = grid[a];
+        P.delta[a] = c->delta[a];
+    }
+    P.ngrid = c->ngrid;
+    P.dV = c->dV;
+    const double W[4] = {-49.0 / 18.0, 3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0};  // Eq. d2_1
+    double inv2[3];
+    for (int a = 0; a < 3; ++a) inv2[a] = 1.0 / (c->delta[a] * c->delta[a]);
+    P.st64.c0 = W[0] * (inv2[0] + inv2[1] + inv2[2]);
+    for (int q = 1; q <= 3; ++q) {
+        P.st64.cx[q - 1] = W[q] * inv2[0];
+        P.st64.cy[q - 1] = W[q] * inv2[1];
+        P.st64.cz[q - 1] = W[q] * inv2[2];
+    }
+    P.st32.c0 = (float)P.st64.c0;
+    for (int q = 0; q < 3; ++q) {
+        P.st32.cx[q] = (float)P.st64.cx[q];
+        P.st32.cy[q] = (float)P.st64.cy[q];
+        P.st32.cz[q] = (float)P.st64.cz[q];
+    }
+    P.geos = c->d_geos;
+    P.n_geo = 1;
+    P.S = S;
+    P.Rc = Rc;
+    P.S2 = (long long)S * S;
+    P.ws = c->ws;
+    P.slot_bytes = c->slot_bytes;
+    P.tol = tol;
+    P.max_iter = o.max_iter;
+    P.inner_max_iter = o.inner_max_iter;
+    P.inner_tol = o.inner_tol;
+    P.max_refine = 40;
+    P.lmax = l_max;
+    P.n_mono = (l_max + 1) * (l_max + 2) * (l_max + 3) / 6;
+    P.n_pair = c->d_scalars;
+    P.queue = c->d_scalars + 1;
+    P.nonconv = c->d_scalars + 2;
+
+    c->stats.n_pe = B.n_pe;
+    c->stats.n_me = B.n_me;
+    c->stats.solver_kind = 1;
+    c->stats.cluster_size = 1;
+    c->stats.grid_ctas = c->n_slots;
+    c->stats.threads = c->threads;
+    *out = c;
+    return EXX_OK;
+}
+
+static exx_status ensure_pairs(exx_ctx* c, int n) {
+    if (n <= c->cap_n) return EXX_OK;
+    drop_graph(c);
+    free_pairs(c);
+    const long long np = (long long)n * (n + 1) / 2;
+    CK(cudaMalloc(&c->d_counts, sizeof(int) * (size_t)n), "cudaMalloc(counts)");
+    CK(cudaMalloc(&c->d_offsets, sizeof(int) * (size_t)(n + 1)), "cudaMalloc(offsets)");
+    CK(cudaMalloc(&c->d_pairs, sizeof(PairRec) * (size_t)np), "cudaMalloc(pairs)");
+    CK(cudaMalloc(&c->d_epair, sizeof(double) * (size_t)np), "cudaMalloc(e_pair)");
+    CK(cudaMalloc(&c->d_iters, sizeof(int) * (size_t)np), "cudaMalloc(iters)");
+    CK(cudaMalloc(&c->d_refines, sizeof(int) * (size_t)np), "cudaMalloc(refines)");
+    c->cap_n = n;
+    c->cap_pairs = np;
+    return EXX_OK;
+}
+
+// The launch sequence of one call (captured into a graph when batched).
+static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* centers, int n, double* d_xx,
+                          cudaStream_t st) {
+    SolveParams P = c->P;
+    P.phi = orbitals;
+    P.dxx = d_xx;
+    P.pairs = c->d_pairs;
+    P.order = nullptr;
+    P.e_pair = c->d_epair;
+    P.iters = c->d_iters;
+    P.refines = c->d_refines;
+    P.dbg_b = nullptr;
+    CK(cudaEventRecord(c->ev[0], st), "cudaEventRecord");
+    CK(launch_zero(d_xx, (long long)n * c->ngrid, c->num_sms, st), "zero D_xx");
+    CK(cudaMemsetAsync(c->d_scalars + 2, 0, sizeof(int), st), "reset counters");
+    CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
+                        c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st),
+       "pair list");
+    CK(cudaEventRecord(c->ev[1], st), "cudaEventRecord");
+    CK(launch_pair_kernel(P, c->threads, c->opt.precision == 1, c->n_slots, c->smem, st), "pair kernel");
+    CK(cudaEventRecord(c->ev[2], st), "cudaEventRecord");
+    CK(launch_exx_reduce(c->d_pairs, c->d_scalars, c->d_epair, c->d_exx, st), "E_xx reduction");
+    CK(cudaMemcpyAsync(c->h_exx, c->d_exx, sizeof(double), cudaMemcpyDeviceToHost, st), "copy E_xx");
+    CK(cudaEventRecord(c->ev[3], st), "cudaEventRecord");
+    return EXX_OK;
+}
+
+extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const double* centers, int n,
+                                  const double* alphas, double* e_xx, double* d_xx, void* stream) {
+    (void)alphas;
+    if (!c) return fail(nullptr, EXX_EINVAL, "exx_compute: ctx is NULL");
+    if (!orbitals || !centers || !e_xx || !d_xx) return fail(c, EXX_EINVAL, "exx_compute: NULL array argument");
+    if (n < 1 || n > 65535) return fail(c, EXX_EINVAL, "exx_compute: n must be in [1, 65535]");
+    if ((const void*)orbitals == (const void*)d_xx) return fail(c, EXX_EINVAL, "exx_compute: d_xx aliases orbitals");
+    if (((reinterpret_cast<uintptr_t>(orbitals) | reinterpret_cast<uintptr_t>(centers) |
+          reinterpret_cast<uintptr_t>(d_xx) | reinterpret_cast<uintptr_t>(alphas)) & 7u) != 0)
+        return fail(c, EXX_EINVAL, "exx_compute: arrays must be 8-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    exx_status s = ensure_pairs(c, n);
+    if (s != EXX_OK) return s;
+    cudaError_t e;
+    if (c->opt.batched) {
+        const void* key[5] = {orbitals, centers, d_xx, (const void*)st, nullptr};
+        bool hit = c->gexec && c->g_n == n && std::equal(key, key + 5, c->g_key);
+        if (!hit) {
+            drop_graph(c);
+            cudaGraph_t g;
+            e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
+            s = enqueue(c, orbitals, centers, n, d_xx, st);
+            e = cudaStreamEndCapture(st, &g);
+            if (s != EXX_OK) {
+                if (e == cudaSuccess) cudaGraphDestroy(g);
+                return s;
+            }
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&c->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                c->gexec = nullptr;
+                return cuda_fail(c, e, "cudaGraphInstantiate");
+            }
+            std::copy(key, key + 5, c->g_key);
+            c->g_n = n;
+        }
+        e = cudaGraphLaunch(c->gexec, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+    } else {
+        s = enqueue(c, orbitals, centers, n, d_xx, st);
+        if (s != EXX_OK) return s;
+    }
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "exx_compute (stream synchronize)");
+    *e_xx = c->h_exx[0];
+    c->last_n = n;
+    c->last_orb = orbitals;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]);
+    c->stats.solve_ms = ms;
+    cudaEventElapsedTime(&ms, c->ev[0], c->ev[3]);
+    c->stats.total_ms = ms;
+    int nonconv = 0, npair = 0;
+    CK(cudaMemcpy(&npair, c->d_scalars, sizeof(int), cudaMemcpyDeviceToHost), "read n_pair");
+    CK(cudaMemcpy(&nonconv, c->d_scalars + 2, sizeof(int), cudaMemcpyDeviceToHost), "read nonconv");
+    c->stats.n_pair = npair;
+    c->stats.n_nonconv = nonconv;
+    c->stats.iters_max = -1;  // filled lazily by exx_get_stats
+    if (nonconv > 0) {
+        char buf[128];
+        std::snprintf(buf, sizeof(buf), "%d of %d pair solves reached the iteration cap", nonconv, npair);
+        return fail(c, EXX_ENOCONV, buf);
+    }
+    return EXX_OK;
+}
+
+extern "C" exx_status exx_compute_host(exx_ctx* c, const double* orbitals_host, const double* centers_host, int n,
+                                       const double* alphas_host, double* e_xx, double* d_xx_host, void* stream) {
+    if (!c) return fail(nullptr, EXX_EINVAL, "exx_compute_host: ctx is NULL");
+    if (!orbitals_host || !centers_host || !e_xx || !d_xx_host)
+        return fail(c, EXX_EINVAL, "exx_compute_host: NULL array argument");
+    if (n < 1 || n > 65535) return fail(c, EXX_EINVAL, "exx_compute_host: n must be in [1, 65535]");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * (size_t)n * (size_t)c->ngrid;
+    if (bytes > c->host_cap_bytes || n > c->host_cap_n) {
+        drop_graph(c);
+        cudaFree(c->d_orb);
+        cudaFree(c->d_dxx);
+        cudaFree(c->d_cent);
+        cudaFree(c->d_alpha);
+        c->d_orb = c->d_dxx = c->d_cent = c->d_alpha = nullptr;
+        c->host_cap_bytes = 0;
+        c->host_cap_n = 0;
+        CK(cudaMalloc(&c->d_orb, bytes), "cudaMalloc(orbitals copy)");
+        CK(cudaMalloc(&c->d_dxx, bytes), "cudaMalloc(d_xx copy)");
+        CK(cudaMalloc(&c->d_cent, sizeof(double) * 3 * (size_t)n), "cudaMalloc(centers copy)");
+        CK(cudaMalloc(&c->d_alpha, sizeof(double) * (size_t)n), "cudaMalloc(alphas copy)");
+        c->host_cap_bytes = bytes;
+        c->host_cap_n = n;
+    }
+    CK(cudaMemcpyAsync(c->d_orb, orbitals_host, bytes, cudaMemcpyHostToDevice, st), "copy orbitals");
+    CK(cudaMemcpyAsync(c->d_cent, centers_host, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, st),
+       "copy centers");
+    if (alphas_host)
+        CK(cudaMemcpyAsync(c->d_alpha, alphas_host, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, st),
+           "copy alphas");
+    exx_status s = exx_compute(c, c->d_orb, c->d_cent, n, alphas_host ? c->d_alpha : nullptr, e_xx, c->d_dxx, stream);
+    if (s != EXX_OK && s != EXX_ENOCONV) return s;
+    CK(cudaMemcpyAsync(d_xx_host, c->d_dxx, bytes, cudaMemcpyDeviceToHost, st), "copy d_xx");
+    CK(cudaStreamSynchronize(st), "exx_compute_host (stream synchronize)");
+    return s;
+}
+
+extern "C" exx_status exx_get_stats(const exx_ctx* cc, exx_stats* out) {
+    exx_ctx* c = const_cast<exx_ctx*>(cc);
+    if (!c || !out) return fail(c, EXX_EINVAL, "exx_get_stats: NULL argument");
+    if (c->stats.iters_max < 0 && c->stats.n_pair > 0) {
+        const int np = c->stats.n_pair;
+        std::vector<int> it(np), rf(np);
+        std::vector<PairRec> pr(np);
+        CK(cudaMemcpy(it.data(), c->d_iters, sizeof(int) * np, cudaMemcpyDeviceToHost), "read iters");
+        CK(cudaMemcpy(rf.data(), c->d_refines, sizeof(int) * np, cudaMemcpyDeviceToHost), "read refines");
+        CK(cudaMemcpy(pr.data(), c->d_pairs, sizeof(PairRec) * np, cudaMemcpyDeviceToHost), "read pairs");
+        long long tot = 0, pit = 0;
+        int rmax = 0;
+        for (int p = 0; p < np; ++p) {
+            tot += it[p];
+            pit += (long long)it[p] * c->hb.n_pe;
+            rmax = std::max(rmax, rf[p]);
+        }
+        std::vector<int> srt = it;
+        std::sort(srt.begin(), srt.end());
+        c->stats.iters_total = tot;
+        c->stats.point_iters = pit;
+        c->stats.iters_max = srt.back();
+        c->stats.iters_p50 = srt[(np - 1) / 2];
+        c->stats.iters_p99 = srt[std::min(np - 1, (int)std::ceil(0.99 * np) - 1)];
+        c->stats.refine_max = rmax;
+    }
+    *out = c->stats;
+    if (out->iters_max < 0) out->iters_max = 0;
+    return EXX_OK;
+}
+
+extern "C" exx_status exx_get_pairs(const exx_ctx* cc, int* pi, int* pj, int* g, int* radii, double* e_pair,
+                                    int* iters, int cap, int* n_pair) {
+    exx_ctx* c = const_cast<exx_ctx*>(cc);
+    if (!c) return fail(nullptr, EXX_EINVAL, "exx_get_pairs: ctx is NULL");
+    const int np = c->stats.n_pair;
+    if (n_pair) *n_pair = np;
+    if (np > cap && (pi || pj || g || radii || e_pair || iters))
+        return fail(c, EXX_EINVAL, "exx_get_pairs: cap smaller than the pair count");
+    if (np == 0) return EXX_OK;
+    std::vector<PairRec> pr(np);
+    CK(cudaMemcpy(pr.data(), c->d_pairs, sizeof(PairRec) * np, cudaMemcpyDeviceToHost), "read pairs");
+    for (int p = 0; p < np; ++p) {
+        if (pi) pi[p] = pr[p].i;
+        if (pj) pj[p] = pr[p].j;
+        if (g)
+            for (int a = 0; a < 3; ++a) g[3 * p + a] = pr[p].g[a];
+        if (radii) {
+            radii[2 * p] = pr[p].r_pe;
+            radii[2 * p + 1] = pr[p].r_me;
+        }
+    }
+    if (e_pair) CK(cudaMemcpy(e_pair, c->d_epair, sizeof(double) * np, cudaMemcpyDeviceToHost), "read e_pair");
+    if (iters) CK(cudaMemcpy(iters, c->d_iters, sizeof(int) * np, cudaMemcpyDeviceToHost), "read iters");
+    return EXX_OK;
+}
+
+extern "C" exx_status exx_debug_pair(exx_ctx* c, const double* orbitals, int index, double* rho, double* v, double* b,
+                                     void* stream) {
+    if (!c) return fail(nullptr, EXX_EINVAL, "exx_debug_pair: ctx is NULL");
+    if (!orbitals) return fail(c, EXX_EINVAL, "exx_debug_pair: orbitals is NULL");
+    if (index < 0 || index >= c->stats.n_pair) return fail(c, EXX_ENOPAIR, "exx_debug_pair: index out of range");
+    cudaStream_t st = (cudaStream_t)stream;
+    const HostBall& B = c->hb;
+    PairRec pr;
+    CK(cudaMemcpy(&pr, c->d_pairs + index, sizeof(PairRec), cudaMemcpyDeviceToHost), "read pair");
+    // a one-pair list in the spare tail of the scalars block
+    PairRec* d_one = nullptr;
+    double *d_rho = nullptr, *d_v = nullptr, *d_b = nullptr, *d_e = nullptr;
+    int* d_sc = nullptr;
+    CK(cudaMalloc(&d_one, sizeof(PairRec)), "cudaMalloc");
+    CK(cudaMalloc(&d_rho, sizeof(double) * B.n_me), "cudaMalloc");
+    CK(cudaMalloc(&d_v, sizeof(double) * B.n_me), "cudaMalloc");
+    CK(cudaMalloc(&d_b, sizeof(double) * B.n_pe), "cudaMalloc");
+    CK(cudaMalloc(&d_e, sizeof(double) * 2), "cudaMalloc");
+    CK(cudaMalloc(&d_sc, sizeof(int) * 8), "cudaMalloc");
+    int sc[8] = {1, 0, 0, 0, 0, 0, 0, 0};
+    CK(cudaMemcpy(d_one, &pr, sizeof(PairRec), cudaMemcpyHostToDevice), "copy pair");
+    CK(cudaMemcpy(d_sc, sc, sizeof(sc), cudaMemcpyHostToDevice), "copy scalars");
+    SolveParams P = c->P;
+    P.phi = orbitals;
+    P.dxx = nullptr;
+    P.pairs = d_one;
+    P.n_pair = d_sc;
+    P.queue = d_sc + 1;
+    P.nonconv = d_sc + 2;
+    P.order = nullptr;
+    P.e_pair = d_e;
+    P.iters = d_sc + 3;
+    P.refines = d_sc + 4;
+    P.dbg_b = d_b;
+    exx_status s = EXX_OK;
+    cudaError_t e = launch_pair_kernel(P, c->threads, c->opt.precision == 1, 1, c->smem, st);
+    if (e == cudaSuccess) e = launch_debug_readback(P, pr, d_rho, d_v, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && rho) e = cudaMemcpy(rho, d_rho, sizeof(double) * B.n_me, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v) e = cudaMemcpy(v, d_v, sizeof(double) * B.n_me, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && b) e = cudaMemcpy(b, d_b, sizeof(double) * B.n_pe, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) s = cuda_fail(c, e, "exx_debug_pair");
+    cudaFree(d_one);
+    cudaFree(d_rho);
+    cudaFree(d_v);
+    cudaFree(d_b);
+    cudaFree(d_e);
+    cudaFree(d_sc);
+    return s;
+}
+
+extern "C" exx_status exx_apply_operator(exx_ctx* c, const double* p, double* ap, void* stream) {
+    if (!c) return fail(nullptr, EXX_EINVAL, "exx_apply_operator: ctx is NULL");
+    if (!p || !ap) return fail(c, EXX_EINVAL, "exx_apply_operator: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(launch_apply(c->P, p, ap, st), "apply operator");
+    CK(cudaStreamSynchronize(st), "apply operator (synchronize)");
+    return EXX_OK;
+}
+
+extern "C" exx_status exx_ball_size(const exx_ctx* c, int* n_pe, int* n_me) {
+    if (!c) return fail(nullptr, EXX_EINVAL, "exx_ball_size: ctx is NULL");
+    if (n_pe) *n_pe = c->hb.n_pe;
+    if (n_me) *n_me = c->hb.n_me;
+    return EXX_OK;
+}
+
+extern "C" exx_status exx_load_guess_model(exx_ctx* c, const void* weights, size_t bytes) {
+    (void)weights;
+    (void)bytes;
+    return fail(c, EXX_EINVAL, "exx_load_guess_model: the learned warm start is not available in this build");
+}
+
+extern "C" const char* exx_last_error(const exx_ctx* c) { return c ? c->err.c_str() : g_init_err.c_str(); }

@@ -1,0 +1,147 @@
+// exx_geometry.cpp -- host-built tables: ball geometry (Algorithm 2) and the
+// Cartesian form of the multipole expansion (Eqs. me, mepole).
+//
+// Multipoles in Cartesian form. The expansion of Eq. me, summed over m with
+// the addition theorem of spherical harmonics, is the Legendre series
+//     v(r) = sum_l sum_q rho_q dV (r r_q)^l P_l(cos g) / r^(2l+1),
+// and (r r_q)^l P_l(cos g) = sum_k c_lk (r . r_q)^(l-2k) (r^2)^k (r_q^2)^k with
+// c_lk = (-1)^k (2l-2k)! / (2^l k! (l-k)! (l-2k)!). Expanding the powers with
+// multinomial coefficients gives, for each degree l, a symmetric matrix K_l
+// over the degree-l monomials with
+//     P_l(r) = sum_alpha T_alpha r^alpha,   T = K_l M,
+//     M_beta = sum_q rho_q dV r_q^beta      (Cartesian moments of degree l),
+// so the device never evaluates a spherical harmonic: it forms the 84
+// Cartesian moments of degree <= 6 and the polynomial P_l on the shell.
+#include "exx_geometry.h"
+
+#include <cmath>
+#include <cstring>
+
+namespace exx {
+
+static double fact(int n) {
+    double f = 1.0;
+    for (int k = 2; k <= n; ++k) f *= k;
+    return f;
+}
+
+static double multinom(int n, int a, int b, int c) { return fact(n) / (fact(a) * fact(b) * fact(c)); }
+
+void build_multipole_const(MultipoleConst& mc) {
+    std::memset(&mc, 0, sizeof(mc));
+    int m = 0;
+    int idx[kLmaxMax + 1][kLmaxMax + 1][kLmaxMax + 1];
+    for (int l = 0; l <= kLmaxMax; ++l) {
+        mc.mono_off[l] = m;
+        for (int a = l; a >= 0; --a)
+            for (int b = l - a; b >= 0; --b) {
+                const int c = l - a - b;
+                mc.mono[m][0] = (unsigned char)a;
+                mc.mono[m][1] = (unsigned char)b;
+                mc.mono[m][2] = (unsigned char)c;
+                idx[a][b][c] = m - mc.mono_off[l];
+                ++m;
+            }
+    }
+    mc.mono_off[kLmaxMax + 1] = m;
+    int koff = 0;
+    for (int l = 0; l <= kLmaxMax; ++l) {
+        const int nl = (l + 1) * (l + 2) / 2;
+        mc.k_off[l] = koff;
+        double* K = mc.K + koff;
+        for (int k = 0; 2 * k <= l; ++k) {
+            const double clk = ((k & 1) ? -1.0 : 1.0) * fact(2 * l - 2 * k) /
+                               (std::pow(2.0, l) * fact(k) * fact(l - k) * fact(l - 2 * k));
+            const int md = l - 2 * k;
+            for (int g0 = 0; g0 <= md; ++g0)
+                for (int g1 = 0; g0 + g1 <= md; ++g1) {
+                    const int g2 = md - g0 - g1;
+                    const double mg = multinom(md, g0, g1, g2);
+                    for (int d0 = 0; d0 <= k; ++d0)
+                        for (int d1 = 0; d0 + d1 <= k; ++d1) {
+                            const int d2 = k - d0 - d1;
+                            const double mdl = multinom(k, d0, d1, d2);
+                            for (int e0 = 0; e0 <= k; ++e0)
+                                for (int e1 = 0; e0 + e1 <= k; ++e1) {
+                                    const int e2 = k - e0 - e1;
+                                    const double me = multinom(k, e0, e1, e2);
+                                    const int ra = idx[g0 + 2 * d0][g1 + 2 * d1][g2 + 2 * d2];
+                                    const int cb = idx[g0 + 2 * e0][g1 + 2 * e1][g2 + 2 * e2];
+                                    K[ra * nl + cb] += clk * mg * mdl * me;
+                                }
+                        }
+                }
+        }
+        koff += nl * nl;
+    }
+    mc.k_off[kLmaxMax + 1] = koff;
+}
+
+static int isqrt_floor(long v) {
+    if (v < 0) return -1;
+    long r = (long)std::sqrt((double)v);
+    while (r * r > v) --r;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return (int)r;
+}
+
+static int pack_off(int x, int y, int z) { return (x + 128) | ((y + 128) << 8) | ((z + 128) << 16); }
+
+void build_ball(HostBall& B, int r_pe, int r_me, int Rc) {
+    const int S = 2 * Rc + 1;
+    const long rpe2 = (long)r_pe * r_pe, rme2 = (long)r_me * r_me;
+    B.r_pe = r_pe;
+    B.r_me = r_me;
+    B.cube.clear();
+    B.off.clear();
+    B.rows_pe.clear();
+    B.rows_me.clear();
+    B.plane_pe.assign(2 * r_pe + 2, 0);
+    auto cube = [&](int x, int y, int z) { return ((x + Rc) * S + (y + Rc)) * S + (z + Rc); };
+    // PE ball, lexicographic (Algorithm 2, first list)
+    for (int x = -r_pe; x <= r_pe; ++x) {
+        B.plane_pe[x + r_pe] = (int)B.rows_pe.size();
+        for (int y = -r_pe; y <= r_pe; ++y) {
+            const long s2 = (long)x * x + (long)y * y;
+            if (s2 > rpe2) continue;
+            const int zpe = isqrt_floor(rpe2 - s2);
+            RowRec R;
+            R.ox = (short)x;
+            R.oy = (short)y;
+            R.zpe = (short)zpe;
+            R.zme = (short)isqrt_floor(rme2 - s2);
+            R.pe_start = (int)B.cube.size();
+            R.sh_start = -1;
+            B.rows_pe.push_back(R);
+            for (int z = -zpe; z <= zpe; ++z) {
+                B.cube.push_back(cube(x, y, z));
+                B.off.push_back(pack_off(x, y, z));
+            }
+        }
+    }
+    B.plane_pe[2 * r_pe + 1] = (int)B.rows_pe.size();
+    B.n_pe = (int)B.cube.size();
+    // shell, lexicographic (Algorithm 2, second list); rows of the ME ball
+    int pe_row = 0;
+    for (int x = -r_me; x <= r_me; ++x)
+        for (int y = -r_me; y <= r_me; ++y) {
+            const long s2 = (long)x * x + (long)y * y;
+            if (s2 > rme2) continue;
+            RowRec R;
+            R.ox = (short)x;
+            R.oy = (short)y;
+            R.zme = (short)isqrt_floor(rme2 - s2);
+            R.zpe = (short)(s2 <= rpe2 ? isqrt_floor(rpe2 - s2) : -1);
+            R.pe_start = R.zpe >= 0 ? B.rows_pe[pe_row++].pe_start : -1;
+            R.sh_start = (int)B.cube.size();
+            B.rows_me.push_back(R);
+            for (int z = -R.zme; z <= R.zme; ++z) {
+                if (z >= -R.zpe && z <= R.zpe) continue;
+                B.cube.push_back(cube(x, y, z));
+                B.off.push_back(pack_off(x, y, z));
+            }
+        }
+    B.n_me = (int)B.cube.size();
+}
+
+}  // namespace exx

@@ -1,0 +1,117 @@
+// exx_internal.h -- types shared by the host orchestration and the kernels of
+// the pair-Poisson exact-exchange library (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace exx {
+
+// Multipole order limit and the Cartesian monomial count for l <= 6:
+// sum_{l=0..6} (l+1)(l+2)/2 = 84.
+constexpr int kLmaxMax = 6;
+constexpr int kNMono = 84;
+constexpr int kNU = 28;  // sum_{l<=6} (l+1): per-row polynomial coefficients U_{l,c}
+
+// One pair of the list (Sec. III.C Step II). 32 bytes.
+struct PairRec {
+    int i, j;       // orbitals, i <= j
+    int g[3];       // grid point nearest the pair centre, in [0, N)
+    int r_pe, r_me; // radii in grid points for this pair
+    int geo;        // index of the ball geometry used (radii table)
+};
+
+// One (x, y) row of a ball: z runs over [-zme, zme]; the PE part is
+// [-zpe, zpe] (zpe < 0 when the row has no PE points).
+struct RowRec {
+    short ox, oy;
+    short zpe, zme;
+    int pe_start;   // compact PE index of (ox, oy, -zpe), or -1
+    int sh_start;   // compact ME index of the first shell point of the row
+};
+
+// Device tables of one ball geometry (R_PE, R_ME); points in Algorithm 2
+// order: PE points lexicographic, then shell points lexicographic.
+struct BallGeo {
+    int r_pe, r_me;
+    int n_pe, n_me;
+    int n_rows_pe, n_rows_me;
+    const int* pt_cube;      // [n_me] index in the workspace cube
+    const int* pt_off;       // [n_me] packed offsets: (ox+128) | (oy+128)<<8 | (oz+128)<<16
+    const RowRec* rows_pe;   // [n_rows_pe]
+    const RowRec* rows_me;   // [n_rows_me]
+    const int* plane_pe;     // [2 r_pe + 2] first PE row of each x plane (last = n_rows_pe)
+};
+
+// 19-point Laplacian coefficients of Eq. d2_1 on an orthorhombic grid:
+// lap f(c) = c0 f(c) + sum_a sum_q ca[q-1] (f(c + q s_a) + f(c - q s_a)).
+template <typename T>
+struct Stencil {
+    T c0;
+    T cx[3], cy[3], cz[3];
+};
+
+constexpr int kMaxGeo = 64;
+
+// Everything the pair kernel needs, passed by value.
+struct SolveParams {
+    // inputs / outputs
+    const double* phi;
+    double* dxx;
+    long long ngrid;    // N0 N1 N2
+    int N[3];
+    double delta[3];
+    double dV;
+    Stencil<double> st64;
+    Stencil<float> st32;
+
+    // pairs
+    const PairRec* pairs;
+    const int* n_pair;  // device scalar
+    const int* order;   // processing order (NULL = list order)
+    int* queue;         // device work counter
+
+    // geometry
+    const BallGeo* geos;  // device array of geometries
+    int n_geo;
+    int S, Rc;            // cube side and cube radius of the workspace
+    long long S2;
+
+    // workspace: n_slots slots of slot_bytes each
+    char* ws;
+    size_t slot_bytes;
+    size_t off_vcube, off_pcube, off_rho, off_r, off_d, off_ap;  // FP64 parts
+    size_t off_p32, off_r32, off_d32, off_ap32;                  // FP32 parts
+    size_t off_rows;                                             // [n_rows_pe][8] row sums
+
+    // solver
+    double tol;
+    int max_iter;
+    int inner_max_iter;
+    double inner_tol;
+    int max_refine;
+    int lmax;
+    int n_mono;
+    int warm_start;       // 1: take x0 from the cache when valid
+    const double* x0_cache;   // [n_pair_cap][n_pe] previous solutions (fixed radii)
+    double* x_cache_out;      // write solutions here (may alias nothing)
+    const int* x0_valid;      // [n_pair] 1 when x0_cache row is this pair's previous solution
+
+    // outputs
+    double* e_pair;
+    int* iters;
+    int* refines;
+    int* nonconv;
+    // debug
+    double* dbg_b;        // if set, the RHS b of the processed pair (slot 0)
+};
+
+// Host-built constants of the Cartesian form of the multipole expansion.
+struct MultipoleConst {
+    double K[1596];        // block-diagonal K_l, l = 0..6, row-major per block
+    int k_off[8];          // offset of block l in K
+    int mono_off[8];       // first monomial of degree l
+    unsigned char mono[kNMono][3];  // (a, b, c) of each monomial
+};
+
+}  // namespace exx

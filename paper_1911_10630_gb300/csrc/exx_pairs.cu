@@ -1,0 +1,197 @@
+// exx_pairs.cu -- pair list (Sec. III.C Step II), D_xx zeroing, E_xx reduction.
+//
+// The pair list keeps i <= j with |minimg(C_j - C_i)| < R_pair (strict) and
+// stores for each pair the grid point nearest the pair centre
+// C_ij = C_i + minimg(C_j - C_i)/2 (the midpoint of Step III, snapped with NINT
+// and wrapped by MOD as in Eq. l2g). The list is built in parallel (count per
+// i, scan, ordered fill), so its order is i-major with j ascending. Doubles
+// decide integers here, so every operation is an explicitly rounded IEEE op.
+#include <cuda_runtime.h>
+
+#include "exx_kernels.cuh"
+
+namespace exx {
+
+__device__ __forceinline__ double minimg_d(double x, double L) {
+    double t = __dadd_rn(__ddiv_rn(x, L), 0.5);
+    return __dsub_rn(x, __dmul_rn(L, floor(t)));
+}
+
+struct PairGeom {
+    double L[3];
+    double delta[3];
+    int N[3];
+    double r2cut;
+    int r_pe, r_me;
+};
+
+__device__ __forceinline__ bool pair_within(const double* __restrict__ C, int i, int j, const PairGeom& G,
+                                            double d[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = minimg_d(__dsub_rn(C[3 * j + a], C[3 * i + a]), G.L[a]);
+    double d2 = __dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1]));
+    d2 = __dadd_rn(d2, __dmul_rn(d[2], d[2]));
+    return d2 < G.r2cut;
+}
+
+// counts[i] = number of j >= i paired with i. One block per i.
+__global__ void pairs_count_kernel(int n, const double* __restrict__ C, PairGeom G, int* __restrict__ counts) {
+    const int i = blockIdx.x;
+    int cnt = 0;
+    for (int j = i + threadIdx.x; j < n; j += blockDim.x) {
+        double d[3];
+        cnt += pair_within(C, i, j, G, d) ? 1 : 0;
+    }
+    __shared__ int s[32];
+    cnt = warp_sum_int(cnt);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int t = threadIdx.x < (blockDim.x >> 5) ? s[threadIdx.x] : 0;
+        t = warp_sum_int(t);
+        if (threadIdx.x == 0) counts[i] = t;
+    }
+}
+
+// Exclusive scan of counts into offsets[0..n]; offsets[n] = number of pairs.
+// One block of 1024 threads, each owning a contiguous segment.
+__global__ void pairs_scan_kernel(int n, const int* __restrict__ counts, int* __restrict__ offsets,
+                                  int* __restrict__ n_pair, int* __restrict__ queue) {
+    __shared__ int s[1024];
+    const int t = threadIdx.x;
+    const int seg = (n + 1023) / 1024;
+    const int b = t * seg, e = min(n, b + seg);
+    int sum = 0;
+    for (int k = b; k < e; ++k) sum += counts[k];
+    s[t] = sum;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over the 1024 segment sums
+    for (int o = 1; o < 1024; o <<= 1) {
+        int v = t >= o ? s[t - o] : 0;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    int run = s[t] - sum;
+    for (int k = b; k < e; ++k) {
+        offsets[k] = run;
+        run += counts[k];
+    }
+    if (t == 1023) {
+        offsets[n] = s[1023];
+        *n_pair = s[1023];
+        *queue = 0;
+    }
+}
+
+// Ordered fill: block i writes its pairs (i, j), j ascending, at offsets[i].
+__global__ void pairs_fill_kernel(int n, const double* __restrict__ C, PairGeom G, const int* __restrict__ offsets,
+                                  PairRec* __restrict__ pairs) {
+    const int i = blockIdx.x;
+    __shared__ int s_w[33];
+    int base = offsets[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j0 = i; j0 < n; j0 += blockDim.x) {
+        const int j = j0 + threadIdx.x;
+        double d[3] = {0.0, 0.0, 0.0};
+        bool keep = j < n && pair_within(C, i, j, G, d);
+        unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) s_w[w] = __popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int k = 0; k < nw; ++k) {
+                int c = s_w[k];
+                s_w[k] = run;
+                run += c;
+            }
+            s_w[32] = run;
+        }
+        __syncthreads();
+        if (keep) {
+            int pos = base + s_w[w] + __popc(m & ((1u << lane) - 1u));
+            PairRec r;
+            r.i = i;
+            r.j = j;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                double c = __dadd_rn(C[3 * i + a], __dmul_rn(0.5, d[a]));
+                long long g = llround(__ddiv_rn(c, G.delta[a]));
+                long long mm = g % G.N[a];
+                r.g[a] = (int)(mm < 0 ? mm + G.N[a] : mm);
+            }
+            r.r_pe = G.r_pe;
+            r.r_me = G.r_me;
+            r.geo = 0;
+            pairs[pos] = r;
+        }
+        base += s_w[32];
+        __syncthreads();
+    }
+}
+
+// D_xx = 0 (grid-stride fill; 16-byte stores when the pointer allows them).
+__global__ void zero_kernel(double* __restrict__ p, long long n, int vec) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (!vec) {
+        for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) p[k] = 0.0;
+        return;
+    }
+    long long n2 = n >> 1;
+    double2* p2 = reinterpret_cast<double2*>(p);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n2; k += stride)
+        p2[k] = make_double2(0.0, 0.0);
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) p[n - 1] = 0.0;
+}
+
+// E_xx = -(sum_i E_ii + 2 sum_{i<j} E_ij), in a fixed order (one block).
+__global__ void exx_reduce_kernel(const PairRec* __restrict__ pairs, const int* __restrict__ n_pair,
+                                  const double* __restrict__ e_pair, double* __restrict__ out) {
+    __shared__ double red[2][33];
+    int flip = 0;
+    const int np = *n_pair;
+    double s = 0.0;
+    for (int p = threadIdx.x; p < np; p += 1024) {
+        const PairRec r = pairs[p];
+        s += (r.i == r.j ? 1.0 : 2.0) * e_pair[p];
+    }
+    s = block_sum<1024>(s, red, flip);
+    if (threadIdx.x == 0) out[0] = -s;
+}
+
+}  // namespace exx
+
+// ---- host launchers (C++ linkage inside the library) ----
+namespace exx {
+
+cudaError_t launch_pair_list(int n, const double* centers, const double L[3], const double delta[3], const int N[3],
+                             double r_pair, int r_pe, int r_me, int* counts, int* offsets, int* n_pair, int* queue,
+                             PairRec* pairs, cudaStream_t st) {
+    PairGeom G;
+    for (int a = 0; a < 3; ++a) {
+        G.L[a] = L[a];
+        G.delta[a] = delta[a];
+        G.N[a] = N[a];
+    }
+    G.r2cut = r_pair * r_pair;
+    G.r_pe = r_pe;
+    G.r_me = r_me;
+    pairs_count_kernel<<<n, 256, 0, st>>>(n, centers, G, counts);
+    pairs_scan_kernel<<<1, 1024, 0, st>>>(n, counts, offsets, n_pair, queue);
+    pairs_fill_kernel<<<n, 256, 0, st>>>(n, centers, G, offsets, pairs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero(double* p, long long n, int num_sms, cudaStream_t st) {
+    const int vec = (reinterpret_cast<unsigned long long>(p) & 15ull) == 0 ? 1 : 0;
+    zero_kernel<<<num_sms * 8, 256, 0, st>>>(p, n, vec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exx_reduce(const PairRec* pairs, const int* n_pair, const double* e_pair, double* out,
+                              cudaStream_t st) {
+    exx_reduce_kernel<<<1, 1024, 0, st>>>(pairs, n_pair, e_pair, out);
+    return cudaGetLastError();
+}
+
+}  // namespace exx

@@ -1,0 +1,480 @@
+// exx_solve.cu -- the per-pair pipeline, one CTA per pair (Sec. III.C Steps III-V).
+//
+// A persistent grid pops pairs from a device work counter. For each pair the
+// CTA, using a workspace slot of its own:
+//   1. gathers rho_ij = phi_i phi_j on the PE ball through the wrapped indices
+//      of Eq. l2g (coalesced along z);
+//   2. forms the multipole moments of Eq. mepole in Cartesian form: row sums
+//      S_c = sum_z z^c rho, plane sums, then M_abc = sum rho x^a y^b z^c dV,
+//      and the coefficients T = K M of the degree-l polynomials P_l (K is the
+//      host-built Legendre-addition-theorem matrix);
+//   3. evaluates the far-field potential of Eq. me on the shell as
+//      v = sum_l P_l(r) / r^(2l+1), one thread per (x, y) row;
+//   4. builds the right-hand side of Eq. pe_mat_red as the residual
+//      b = 4 pi rho + lap v of the full 19-point stencil (Eq. d2_1) with v = 0
+//      on the PE ball and the multipole values on the shell;
+//   5. solves A d = b with A = -lap restricted to the PE ball by conjugate
+//      gradient, either in FP64 or as FP32 inner CG with FP64 refinement
+//      (r = 4 pi rho + lap v recomputed in FP64 after each inner solve);
+//   6. E_ij = sum_PE rho v dV (Eq. exx_omega) and the scatter
+//      D^i += v phi_j, D^j += v phi_i on the ME ball (Eqs. Dxx_mlwf_omega).
+// The potential lives in an FP64 cube of side 2 R_ME + 1 (shell values around
+// the PE ball); the CG direction lives in a zero-padded cube so the stencil
+// needs no bounds checks; the other CG vectors are compact over the PE ball.
+#include <cuda_runtime.h>
+
+#include "exx_kernels.cuh"
+
+namespace exx {
+
+__constant__ MultipoleConst c_mp;
+
+// --------------------------------------------------------------------------
+// Conjugate gradient on the PE ball (Step IV). On entry: r = rhs, p = rhs on
+// the PE ball (0 elsewhere in the cube), d = 0, rr = ||rhs||^2. Returns the
+// iteration count; rr_out receives the final recursive ||r||^2.
+// --------------------------------------------------------------------------
+template <typename T, int NT>
+__device__ int cg_ball(T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d, T* __restrict__ ap,
+                       const int* __restrict__ cube, int n_pe, int S, long long S2, const Stencil<T>& neg_st,
+                       double rr, double target2, int max_iter, double (*red)[33], int& flip, double& rr_out) {
+    int it = 0;
+    while (rr > target2 && it < max_iter) {
+        double pap = 0.0;
+        {
+            T acc = T(0);
+            for (int k = threadIdx.x; k < n_pe; k += NT) {
+                const int c = cube[k];
+                const T a = lap19<T>(pc, c, S, S2, neg_st);
+                ap[k] = a;
+                acc = fma(pc[c], a, acc);
+            }
+            pap = (double)acc;
+        }
+        pap = block_sum<NT>(pap, red, flip);
+        const double alpha = rr / pap;
+        const T al = (T)alpha;
+        double rrn;
+        {
+            T acc = T(0);
+            for (int k = threadIdx.x; k < n_pe; k += NT) {
+                const int c = cube[k];
+                d[k] = fma(al, pc[c], d[k]);
+                const T rk = fma(-al, ap[k], r[k]);
+                r[k] = rk;
+                acc = fma(rk, rk, acc);
+            }
+            rrn = (double)acc;
+        }
+        rrn = block_sum<NT>(rrn, red, flip);
+        ++it;
+        if (rrn <= target2 || !(rrn == rrn)) {
+            rr = rrn;
+            break;
+        }
+        const T be = (T)(rrn / rr);
+        rr = rrn;
+        for (int k = threadIdx.x; k < n_pe; k += NT) {
+            const int c = cube[k];
+            pc[c] = fma(be, pc[c], r[k]);
+        }
+        __syncthreads();
+    }
+    rr_out = rr;
+    return it;
+}
+
+// --------------------------------------------------------------------------
+// Multipole moments (Eq. mepole) in Cartesian form and the polynomial
+// coefficients T of P_l. Leaves T in s_T[84] (zero above lmax).
+// --------------------------------------------------------------------------
+template <int NT>
+__device__ void moments(const SolveParams& P, const BallGeo& G, const double* __restrict__ rho,
+                        double* __restrict__ rowS, const double* __restrict__ xp, const double* __restrict__ yp,
+                        const double* __restrict__ zp, double* __restrict__ sY, double* __restrict__ s_M,
+                        double* __restrict__ s_T, const int* __restrict__ plane_start) {
+    const int L = P.lmax;
+    const int Rc = P.Rc;
+    // row sums S_c(x, y) = sum_z z^c rho(x, y, z)
+    for (int row = threadIdx.x; row < G.n_rows_pe; row += NT) {
+        const RowRec R = G.rows_pe[row];
+        double s[kLmaxMax + 1];
+#pragma unroll
+        for (int c = 0; c <= kLmaxMax; ++c) s[c] = 0.0;
+        const double* rr = rho + R.pe_start;
+        for (int z = -R.zpe; z <= R.zpe; ++z) {
+            const double v = rr[z + R.zpe];
+            const double* zz = zp + (z + Rc) * 8;
+#pragma unroll
+            for (int c = 0; c <= kLmaxMax; ++c) s[c] = fma(v, zz[c], s[c]);
+        }
+#pragma unroll
+        for (int c = 0; c <= kLmaxMax; ++c) rowS[row * 8 + c] = s[c];
+    }
+    __syncthreads();
+    // plane sums Y_{bc}(x) = sum_y y^b S_c(x, y), b + c <= L
+    const int nplane = 2 * G.r_pe + 1;
+    const int nbc = (L + 1) * (L + 2) / 2;
+    for (int item = threadIdx.x; item < nplane * nbc; item += NT) {
+        const int pl = item / nbc, bc = item - pl * nbc;
+        int dgr = 0;
+        while ((dgr + 1) * (dgr + 2) / 2 <= bc) ++dgr;
+        const int c = bc - dgr * (dgr + 1) / 2, b = dgr - c;
+        double acc = 0.0;
+        for (int row = plane_start[pl]; row < plane_start[pl + 1]; ++row) {
+            const int oy = G.rows_pe[row].oy;
+            acc = fma(yp[(oy + Rc) * 8 + b], rowS[row * 8 + c], acc);
+        }
+        sY[pl * 28 + bc] = acc;
+    }
+    __syncthreads();
+    // M_abc = dV sum_x x^a Y_bc(x)
+    for (int m = threadIdx.x; m < kNMono; m += NT) {
+        const int a = c_mp.mono[m][0], b = c_mp.mono[m][1], c = c_mp.mono[m][2];
+        double acc = 0.0;
+        if (a + b + c <= L) {
+            const int dgr = b + c, bc = dgr * (dgr + 1) / 2 + c;
+            for (int pl = 0; pl < nplane; ++pl) acc = fma(xp[(pl - G.r_pe + Rc) * 8 + a], sY[pl * 28 + bc], acc);
+        }
+        s_M[m] = acc * P.dV;
+    }
+    __syncthreads();
+    // T_l = K_l M_l
+    for (int m = threadIdx.x; m < kNMono; m += NT) {
+        const int l = c_mp.mono[m][0] + c_mp.mono[m][1] + c_mp.mono[m][2];
+        double acc = 0.0;
+        if (l <= L) {
+            const int nl = (l + 1) * (l + 2) / 2, r0 = c_mp.mono_off[l];
+            const double* Kr = c_mp.K + c_mp.k_off[l] + (m - r0) * nl;
+            for (int t = 0; t < nl; ++t) acc = fma(Kr[t], s_M[r0 + t], acc);
+        }
+        s_T[m] = acc;
+    }
+    __syncthreads();
+}
+
+// --------------------------------------------------------------------------
+// Far-field potential on the shell (Eq. me): v = sum_l P_l(r) / r^(2l+1),
+// one thread per (x, y) row of the ME ball, written into the v cube.
+// --------------------------------------------------------------------------
+template <int NT>
+__device__ void shell_potential(const SolveParams& P, const BallGeo& G, double* __restrict__ vc,
+                                const double* __restrict__ xp, const double* __restrict__ yp,
+                                const double* __restrict__ s_T) {
+    const int Rc = P.Rc;
+    for (int row = threadIdx.x; row < G.n_rows_me; row += NT) {
+        const RowRec R = G.rows_me[row];
+        const double* xa = xp + (R.ox + Rc) * 8;
+        const double* yb = yp + (R.oy + Rc) * 8;
+        // U_{l,c} = sum_{a+b=l-c} T_abc x^a y^b
+        double U[kNU];
+#pragma unroll
+        for (int u = 0; u < kNU; ++u) U[u] = 0.0;
+        {
+            int m = 0;
+#pragma unroll
+            for (int l = 0; l <= kLmaxMax; ++l)
+#pragma unroll
+                for (int a = l; a >= 0; --a)
+#pragma unroll
+                    for (int b = l - a; b >= 0; --b) {
+                        const int c = l - a - b;
+                        U[l * (l + 1) / 2 + c] = fma(s_T[m], xa[a] * yb[b], U[l * (l + 1) / 2 + c]);
+                        ++m;
+                    }
+        }
+        const double x = R.ox * P.delta[0], y = R.oy * P.delta[1];
+        const double rxy2 = x * x + y * y;
+        const long long base = (long long)(R.ox + Rc) * P.S2 + (long long)(R.oy + Rc) * P.S + Rc;
+        const int zlo_hi = R.zpe >= 0 ? -R.zpe - 1 : R.zme;  // first segment ends here
+        for (int z = -R.zme; z <= R.zme; ++z) {
+            if (R.zpe >= 0 && z > zlo_hi && z <= R.zpe) continue;
+            const double zz = z * P.delta[2];
+            const double r2 = fma(zz, zz, rxy2);
+            const double ir = rsqrt(r2);
+            const double ir2 = ir * ir;
+            double acc = 0.0;
+#pragma unroll
+            for (int l = kLmaxMax; l >= 0; --l) {
+                const double* Ul = U + l * (l + 1) / 2;
+                double pl = Ul[l];
+#pragma unroll
+                for (int c = l - 1; c >= 0; --c) pl = fma(pl, zz, Ul[c]);
+                acc = fma(acc, ir2, pl);
+            }
+            vc[base + z] = acc * ir;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// The persistent pair kernel.
+// --------------------------------------------------------------------------
+template <int NT, bool MIXED>
+__global__ void __launch_bounds__(NT, 1) pair_kernel(const SolveParams P) {
+    extern __shared__ double smem[];
+    __shared__ double red[2][33];
+    __shared__ double s_M[kNMono], s_T[kNMono];
+    __shared__ int s_item;
+    int flip = 0;
+
+    const int Rc = P.Rc;
+    const int S = P.S;
+    const long long S2 = P.S2;
+    double* xp = smem;                      // [(2Rc+1)*8] x^a
+    double* yp = xp + (2 * Rc + 1) * 8;     // y^b
+    double* zp = yp + (2 * Rc + 1) * 8;     // z^c
+    double* sY = zp + (2 * Rc + 1) * 8;     // [(2 Rmax_pe + 1) * 28]
+
+    for (int t = threadIdx.x; t < (2 * Rc + 1) * 8; t += NT) {
+        const int o = t / 8 - Rc, e = t % 8;
+        double px = 1.0, py = 1.0, pz = 1.0;
+        const double x = o * P.delta[0], y = o * P.delta[1], z = o * P.delta[2];
+        for (int k = 0; k < e; ++k) {
+            px *= x;
+            py *= y;
+            pz *= z;
+        }
+        xp[t] = px;
+        yp[t] = py;
+        zp[t] = pz;
+    }
+    __syncthreads();
+
+    char* slot = P.ws + (size_t)blockIdx.x * P.slot_bytes;
+    double* vc = reinterpret_cast<double*>(slot + P.off_vcube);
+    double* pc = reinterpret_cast<double*>(slot + P.off_pcube);
+    double* rho = reinterpret_cast<double*>(slot + P.off_rho);
+    double* r = reinterpret_cast<double*>(slot + P.off_r);
+    double* d = reinterpret_cast<double*>(slot + P.off_d);
+    double* ap = reinterpret_cast<double*>(slot + P.off_ap);
+    float* p32 = reinterpret_cast<float*>(slot + P.off_p32);
+    float* r32 = reinterpret_cast<float*>(slot + P.off_r32);
+    float* d32 = reinterpret_cast<float*>(slot + P.off_d32);
+    float* ap32 = reinterpret_cast<float*>(slot + P.off_ap32);
+    double* rowS = reinterpret_cast<double*>(slot + P.off_rows);
+
+    Stencil<double> neg64;
+    Stencil<float> neg32;
+    neg64.c0 = -P.st64.c0;
+    neg32.c0 = -P.st32.c0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        neg64.cx[q] = -P.st64.cx[q];
+        neg64.cy[q] = -P.st64.cy[q];
+        neg64.cz[q] = -P.st64.cz[q];
+        neg32.cx[q] = -P.st32.cx[q];
+        neg32.cy[q] = -P.st32.cy[q];
+        neg32.cz[q] = -P.st32.cz[q];
+    }
+    const double four_pi = 12.566370614359172953850573533118;
+    const int np = *P.n_pair;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(P.queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= np) break;
+        const int pidx = P.order ? P.order[item] : item;
+        const PairRec pr = P.pairs[pidx];
+        const BallGeo G = P.geos[pr.geo];
+        const int* cube = G.pt_cube;
+        const int n_pe = G.n_pe;
+        const double* phi_i = P.phi + (long long)pr.i * P.ngrid;
+        const double* phi_j = P.phi + (long long)pr.j * P.ngrid;
+
+        // 1. gather rho on the PE ball; v = 0 there
+        for (int k = threadIdx.x; k < n_pe; k += NT) {
+            const long long g = grid_index(P.N, pr.g, G.pt_off[k]);
+            rho[k] = phi_i[g] * phi_j[g];
+            vc[cube[k]] = 0.0;
+        }
+        __syncthreads();
+
+        // 2. multipole moments and polynomial coefficients
+        moments<NT>(P, G, rho, rowS, xp, yp, zp, sY, s_M, s_T, G.plane_pe);
+
+        // 3. far-field potential on the shell
+        shell_potential<NT>(P, G, vc, xp, yp, s_T);
+        __syncthreads();
+
+        // 4./5. right-hand side and solve
+        int iters = 0, refines = 0;
+        bool conv = true;
+        if (!MIXED) {
+            double acc = 0.0;
+            for (int k = threadIdx.x; k < n_pe; k += NT) {
+                const int c = cube[k];
+                const double b = fma(four_pi, rho[k], lap19<double>(vc, c, S, S2, P.st64));
+                r[k] = b;
+                pc[c] = b;
+                d[k] = 0.0;
+                acc = fma(b, b, acc);
+                if (P.dbg_b) P.dbg_b[k] = b;
+            }
+            const double bb = block_sum<NT>(acc, red, flip);
+            double rr_fin;
+            const double target2 = P.tol * P.tol * bb;
+            iters = cg_ball<double, NT>(pc, r, d, ap, cube, n_pe, S, S2, neg64, bb, target2, P.max_iter, red, flip,
+                                        rr_fin);
+            conv = rr_fin <= target2;
+            for (int k = threadIdx.x; k < n_pe; k += NT) vc[cube[k]] += d[k];
+            refines = 1;
+        } else {
+            double bb = -1.0, rn_prev = 1e300;
+            for (;;) {
+                // FP64 residual r = 4 pi rho + lap v (v: current iterate on PE, shell values outside)
+                double acc = 0.0;
+                for (int k = threadIdx.x; k < n_pe; k += NT) {
+                    const int c = cube[k];
+                    const double rk = fma(four_pi, rho[k], lap19<double>(vc, c, S, S2, P.st64));
+                    r[k] = rk;
+                    acc = fma(rk, rk, acc);
+                    if (bb < 0.0 && P.dbg_b) P.dbg_b[k] = rk;
+                }
+                const double rn2 = block_sum<NT>(acc, red, flip);
+                if (bb < 0.0) bb = rn2;
+                if (rn2 <= P.tol * P.tol * bb) break;
+                const double rn = sqrt(rn2);
+                if (refines >= P.max_refine || iters >= P.max_iter || !(rn < rn_prev)) {
+                    conv = false;
+                    break;
+                }
+                rn_prev = rn;
+                const double inv = 1.0 / rn;
+                float acc32 = 0.0f;
+                for (int k = threadIdx.x; k < n_pe; k += NT) {
+                    const int c = cube[k];
+                    const float rk = (float)(r[k] * inv);
+                    r32[k] = rk;
+                    p32[c] = rk;
+                    d32[k] = 0.0f;
+                    acc32 = fmaf(rk, rk, acc32);
+                }
+                const double rr32 = block_sum<NT>((double)acc32, red, flip);
+                double eta = 0.3 * P.tol * sqrt(bb) / rn;
+                eta = eta > P.inner_tol ? eta : P.inner_tol;
+                double rr_fin;
+                const int budget = min(P.inner_max_iter, P.max_iter - iters);
+                iters += cg_ball<float, NT>(p32, r32, d32, ap32, cube, n_pe, S, S2, neg32, rr32, eta * eta * rr32,
+                                            budget, red, flip, rr_fin);
+                for (int k = threadIdx.x; k < n_pe; k += NT) vc[cube[k]] = fma(rn, (double)d32[k], vc[cube[k]]);
+                ++refines;
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+
+        // 6. E_ij over the PE ball and the D_xx scatter over the ME ball
+        double e = 0.0;
+        for (int k = threadIdx.x; k < n_pe; k += NT) e = fma(rho[k], vc[cube[k]], e);
+        e = block_sum<NT>(e, red, flip);
+        if (threadIdx.x == 0) {
+            P.e_pair[pidx] = e * P.dV;
+            P.iters[pidx] = iters;
+            if (P.refines) P.refines[pidx] = refines;
+            if (!conv) atomicAdd(P.nonconv, 1);
+        }
+        if (P.dxx) {
+            double* Di = P.dxx + (long long)pr.i * P.ngrid;
+            double* Dj = P.dxx + (long long)pr.j * P.ngrid;
+            const bool two = pr.i != pr.j;
+            for (int q = threadIdx.x; q < G.n_me; q += NT) {
+                const long long g = grid_index(P.N, pr.g, G.pt_off[q]);
+                const double v = vc[cube[q]];
+                atomicAdd(Di + g, v * phi_j[g]);
+                if (two) atomicAdd(Dj + g, v * phi_i[g]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Debug: rho on the whole ME ball and v read back from slot 0.
+__global__ void debug_pair_readback(const SolveParams P, PairRec pr, double* rho_me, double* v_me) {
+    const BallGeo G = P.geos[pr.geo];
+    const double* vc = reinterpret_cast<const double*>(P.ws + P.off_vcube);
+    const double* phi_i = P.phi + (long long)pr.i * P.ngrid;
+    const double* phi_j = P.phi + (long long)pr.j * P.ngrid;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < G.n_me; q += gridDim.x * blockDim.x) {
+        const long long g = grid_index(P.N, pr.g, G.pt_off[q]);
+        rho_me[q] = phi_i[g] * phi_j[g];
+        v_me[q] = vc[G.pt_cube[q]];
+    }
+}
+
+// A p on the PE ball: scatter p into the (zeroed) slot-0 cube, then apply.
+__global__ void apply_scatter(const SolveParams P, const double* p) {
+    const BallGeo G = P.geos[0];
+    double* pc = reinterpret_cast<double*>(P.ws + P.off_pcube);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G.n_pe; k += gridDim.x * blockDim.x)
+        pc[G.pt_cube[k]] = p[k];
+}
+
+__global__ void apply_stencil(const SolveParams P, double* ap) {
+    const BallGeo G = P.geos[0];
+    const double* pc = reinterpret_cast<const double*>(P.ws + P.off_pcube);
+    Stencil<double> neg;
+    neg.c0 = -P.st64.c0;
+    for (int q = 0; q < 3; ++q) {
+        neg.cx[q] = -P.st64.cx[q];
+        neg.cy[q] = -P.st64.cy[q];
+        neg.cz[q] = -P.st64.cz[q];
+    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G.n_pe; k += gridDim.x * blockDim.x)
+        ap[k] = lap19<double>(pc, G.pt_cube[k], P.S, P.S2, neg);
+}
+
+__global__ void apply_unscatter(const SolveParams P) {
+    const BallGeo G = P.geos[0];
+    double* pc = reinterpret_cast<double*>(P.ws + P.off_pcube);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G.n_pe; k += gridDim.x * blockDim.x)
+        pc[G.pt_cube[k]] = 0.0;
+}
+
+// ---- host side ----
+cudaError_t set_multipole_const(const MultipoleConst& mc) {
+    return cudaMemcpyToSymbol(c_mp, &mc, sizeof(MultipoleConst));
+}
+
+size_t pair_kernel_smem(int Rc, int r_pe_max) {
+    return sizeof(double) * ((size_t)3 * (2 * Rc + 1) * 8 + (size_t)(2 * r_pe_max + 1) * 28);
+}
+
+template <int NT, bool MIXED>
+static cudaError_t launch_t(const SolveParams& P, int grid, size_t smem, cudaStream_t st) {
+    pair_kernel<NT, MIXED><<<grid, NT, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_kernel(const SolveParams& P, int threads, bool mixed, int grid, size_t smem, cudaStream_t st) {
+    if (threads == 256) return mixed ? launch_t<256, true>(P, grid, smem, st) : launch_t<256, false>(P, grid, smem, st);
+    if (threads == 1024)
+        return mixed ? launch_t<1024, true>(P, grid, smem, st) : launch_t<1024, false>(P, grid, smem, st);
+    return mixed ? launch_t<512, true>(P, grid, smem, st) : launch_t<512, false>(P, grid, smem, st);
+}
+
+cudaError_t pair_kernel_occupancy(int threads, bool mixed, size_t smem, int* blocks_per_sm) {
+    const void* f;
+    if (threads == 256) f = mixed ? (const void*)pair_kernel<256, true> : (const void*)pair_kernel<256, false>;
+    else if (threads == 1024) f = mixed ? (const void*)pair_kernel<1024, true> : (const void*)pair_kernel<1024, false>;
+    else f = mixed ? (const void*)pair_kernel<512, true> : (const void*)pair_kernel<512, false>;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, smem);
+}
+
+cudaError_t launch_debug_readback(const SolveParams& P, const PairRec& pr, double* rho_me, double* v_me,
+                                  cudaStream_t st) {
+    debug_pair_readback<<<64, 256, 0, st>>>(P, pr, rho_me, v_me);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const SolveParams& P, const double* p, double* ap, cudaStream_t st) {
+    apply_scatter<<<64, 256, 0, st>>>(P, p);
+    apply_stencil<<<64, 256, 0, st>>>(P, ap);
+    apply_unscatter<<<64, 256, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace exx

@@ -1,0 +1,221 @@
+"""Thin ctypes binding of the C ABI in include/exx.h (same names, marshalling only).
+
+Every computation runs in the CUDA library ``libexx_gb300.so``; this module
+only converts arguments. Device arrays are torch CUDA tensors (their
+``data_ptr()`` is passed through); host arrays are numpy arrays. Loading fails
+loudly when the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libexx_gb300.so")
+
+EXX_OK, EXX_EINVAL, EXX_ENOMEM, EXX_ECUDA, EXX_ENOCONV, EXX_ENOPAIR = 0, -1, -2, -3, -4, -5
+_STATUS = {0: "EXX_OK", -1: "EXX_EINVAL", -2: "EXX_ENOMEM", -3: "EXX_ECUDA", -4: "EXX_ENOCONV",
+           -5: "EXX_ENOPAIR"}
+
+
+class ExxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class exx_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("batched", ctypes.c_int), ("warm_start", ctypes.c_int),
+                ("radii_mode", ctypes.c_int), ("max_iter", ctypes.c_int), ("inner_max_iter", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("solver_kind", ctypes.c_int), ("cluster_size", ctypes.c_int)]
+
+
+class exx_stats(ctypes.Structure):
+    _fields_ = [("n_pair", ctypes.c_int), ("n_nonconv", ctypes.c_int), ("iters_max", ctypes.c_int),
+                ("iters_p50", ctypes.c_int), ("iters_p99", ctypes.c_int), ("iters_total", ctypes.c_longlong),
+                ("point_iters", ctypes.c_longlong), ("refine_max", ctypes.c_int), ("solve_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double), ("n_pe", ctypes.c_int), ("n_me", ctypes.c_int),
+                ("solver_kind", ctypes.c_int), ("cluster_size", ctypes.c_int), ("grid_ctas", ctypes.c_int),
+                ("threads", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_d = ctypes.POINTER(ctypes.c_double)
+_i = ctypes.POINTER(ctypes.c_int)
+_ctx_p = ctypes.c_void_p
+
+# (name, restype, argtypes): every function declared in include/exx.h
+SIGNATURES = [
+    ("exx_default_options", exx_options, []),
+    ("exx_init", ctypes.c_int, [ctypes.POINTER(_ctx_p), _d, _i, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, ctypes.c_double, ctypes.POINTER(exx_options)]),
+    ("exx_compute", ctypes.c_int, [_ctx_p, _vp, _vp, ctypes.c_int, _vp, _d, _vp, _vp]),
+    ("exx_compute_host", ctypes.c_int, [_ctx_p, _vp, _vp, ctypes.c_int, _vp, _d, _vp, _vp]),
+    ("exx_get_stats", ctypes.c_int, [_ctx_p, ctypes.POINTER(exx_stats)]),
+    ("exx_get_pairs", ctypes.c_int, [_ctx_p, _i, _i, _i, _i, _d, _i, ctypes.c_int, _i]),
+    ("exx_debug_pair", ctypes.c_int, [_ctx_p, _vp, ctypes.c_int, _d, _d, _d, _vp]),
+    ("exx_apply_operator", ctypes.c_int, [_ctx_p, _vp, _vp, _vp]),
+    ("exx_ball_size", ctypes.c_int, [_ctx_p, _i, _i]),
+    ("exx_load_guess_model", ctypes.c_int, [_ctx_p, _vp, ctypes.c_size_t]),
+    ("exx_last_error", ctypes.c_char_p, [_ctx_p]),
+    ("exx_destroy", None, [_ctx_p]),
+]
+
+
+def load(path: Optional[str] = None):
+    """Loads libexx_gb300.so (raises OSError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise OSError(f"{p} is missing: build it with paper_1911_10630_gb300.build.build()")
+            L = ctypes.CDLL(p)
+            for name, res, args in SIGNATURES:
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def exx_default_options() -> exx_options:
+    return load().exx_default_options()
+
+
+def exx_last_error(ctx=None) -> str:
+    s = load().exx_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def _check(status: int, ctx=None):
+    if status != EXX_OK:
+        raise ExxError(status, exx_last_error(ctx))
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return int(t)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:  # pragma: no cover
+            return None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Exx:
+    """Owns one exx_ctx (exx_init ... exx_destroy)."""
+
+    def __init__(self, cell, grid, r_pair, r_pe, r_me, l_max=6, tol=1e-8, **opts):
+        L = load()
+        o = L.exx_default_options()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        self.options = o
+        cell = np.ascontiguousarray(cell, np.float64)
+        grid = np.ascontiguousarray(grid, np.int32)
+        self.cell, self.grid = cell, grid
+        self.r_pe, self.r_me = int(r_pe), int(r_me)
+        ctx = _ctx_p()
+        rp = float(r_pair) if math.isfinite(r_pair) else float("inf")
+        st = L.exx_init(ctypes.byref(ctx), cell.ctypes.data_as(_d), grid.ctypes.data_as(_i), rp, int(r_pe),
+                        int(r_me), int(l_max), float(tol), ctypes.byref(o))
+        _check(st, None)
+        self._ctx = ctx
+        self.last_status = EXX_OK
+
+    @property
+    def ctx(self):
+        return self._ctx
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            load().exx_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def compute(self, orbitals, centers, d_xx, alphas=None, stream=None, allow_noconv=False) -> float:
+        """exx_compute on device tensors; returns E_xx, fills d_xx."""
+        e = ctypes.c_double()
+        st = load().exx_compute(self._ctx, _ptr(orbitals), _ptr(centers), int(centers.shape[0]), _ptr(alphas),
+                                ctypes.byref(e), _ptr(d_xx), _stream_handle(stream))
+        self.last_status = st
+        if not (st == EXX_OK or (allow_noconv and st == EXX_ENOCONV)):
+            _check(st, self._ctx)
+        return e.value
+
+    def compute_host(self, orbitals, centers, d_xx, alphas=None, stream=None, allow_noconv=False) -> float:
+        """exx_compute_host on numpy arrays; returns E_xx, fills d_xx (numpy)."""
+        e = ctypes.c_double()
+        st = load().exx_compute_host(self._ctx, _ptr(orbitals), _ptr(centers), int(centers.shape[0]),
+                                     _ptr(alphas), ctypes.byref(e), _ptr(d_xx), _stream_handle(stream))
+        self.last_status = st
+        if not (st == EXX_OK or (allow_noconv and st == EXX_ENOCONV)):
+            _check(st, self._ctx)
+        return e.value
+
+    def stats(self) -> dict:
+        s = exx_stats()
+        _check(load().exx_get_stats(self._ctx, ctypes.byref(s)), self._ctx)
+        return s.as_dict()
+
+    def pairs(self):
+        n = ctypes.c_int()
+        _check(load().exx_get_pairs(self._ctx, None, None, None, None, None, None, 0, ctypes.byref(n)), self._ctx)
+        m = n.value
+        pi = np.empty(m, np.int32)
+        pj = np.empty(m, np.int32)
+        g = np.empty((m, 3), np.int32)
+        radii = np.empty((m, 2), np.int32)
+        e = np.empty(m)
+        it = np.empty(m, np.int32)
+        _check(load().exx_get_pairs(self._ctx, pi.ctypes.data_as(_i), pj.ctypes.data_as(_i), g.ctypes.data_as(_i),
+                                    radii.ctypes.data_as(_i), e.ctypes.data_as(_d), it.ctypes.data_as(_i), m,
+                                    ctypes.byref(n)), self._ctx)
+        return dict(i=pi, j=pj, g=g, radii=radii, e_pair=e, iters=it)
+
+    def ball_size(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(load().exx_ball_size(self._ctx, ctypes.byref(a), ctypes.byref(b)), self._ctx)
+        return a.value, b.value
+
+    def debug_pair(self, orbitals, index, stream=None):
+        n_pe, n_me = self.ball_size()
+        rho = np.empty(n_me)
+        v = np.empty(n_me)
+        b = np.empty(n_pe)
+        _check(load().exx_debug_pair(self._ctx, _ptr(orbitals), int(index), rho.ctypes.data_as(_d),
+                                     v.ctypes.data_as(_d), b.ctypes.data_as(_d), _stream_handle(stream)), self._ctx)
+        return dict(rho=rho, v=v, b=b)
+
+    def apply_operator(self, p, ap, stream=None):
+        _check(load().exx_apply_operator(self._ctx, _ptr(p), _ptr(ap), _stream_handle(stream)), self._ctx)

@@ -1,0 +1,113 @@
+"""The C-ABI library builds, loads and exports every symbol include/exx.h
+declares; argument validation happens on the host before any CUDA call."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "exx.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1911_10630_gb300 import build, exx
+    build.build(quiet=True)
+    return exx.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(exx_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("exx_init", "exx_compute", "exx_compute_host", "exx_get_stats", "exx_last_error",
+                     "exx_destroy", "exx_default_options"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1911_10630_gb300 import exx
+    names = declared_functions()
+    bound = {n for n, _, _ in exx.SIGNATURES}
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in bound, f"binding lacks {n}"
+
+
+def test_default_options(lib):
+    o = lib.exx_default_options()
+    assert o.precision == 0 and o.batched == 1 and o.max_iter == 20000
+    assert o.inner_max_iter == 4000 and abs(o.inner_tol - 1e-5) < 1e-20
+
+
+def _init(lib, cell=(9.0, 9.0, 9.0), grid=(48, 48, 48), r_pair=math.inf, r_pe=16, r_me=20, lmax=6, tol=1e-10,
+          opt=None):
+    from paper_1911_10630_gb300 import exx
+    ctx = ctypes.c_void_p()
+    c = np.asarray(cell, np.float64)
+    g = np.asarray(grid, np.int32)
+    st = lib.exx_init(ctypes.byref(ctx), c.ctypes.data_as(exx._d), g.ctypes.data_as(exx._i), r_pair, r_pe, r_me,
+                      lmax, tol, ctypes.byref(opt) if opt is not None else None)
+    return st, ctx
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(r_me=18), "r_pe + 3"),
+    (dict(grid=(48, 48, 40)), "2 r_me + 1"),
+    (dict(lmax=7), "l_max"),
+    (dict(tol=0.0), "tol"),
+    (dict(tol=1.5), "tol"),
+    (dict(r_pair=-1.0), "r_pair"),
+    (dict(cell=(9.0, -1.0, 9.0)), "cell"),
+    (dict(r_pe=0, r_me=3), "r_pe"),
+    (dict(r_pe=61, r_me=64, grid=(200, 200, 200)), "r_me"),
+])
+def test_init_rejects_invalid_arguments_before_cuda(lib, kw, frag):
+    st, ctx = _init(lib, **kw)
+    assert st == -1
+    assert not ctx.value
+    assert frag in lib.exx_last_error(None).decode()
+
+
+def test_init_rejects_bad_options(lib):
+    o = lib.exx_default_options()
+    o.precision = 3
+    st, ctx = _init(lib, opt=o)
+    assert st == -1 and "precision" in lib.exx_last_error(None).decode()
+    o = lib.exx_default_options()
+    o.threads = 300
+    st, ctx = _init(lib, opt=o)
+    assert st == -1 and "threads" in lib.exx_last_error(None).decode()
+
+
+def test_null_and_destroy_are_safe(lib):
+    from paper_1911_10630_gb300 import exx
+    e = ctypes.c_double()
+    assert lib.exx_compute(None, None, None, 1, None, ctypes.byref(e), None, None) == -1
+    lib.exx_destroy(None)
+    s = exx.exx_stats()
+    assert lib.exx_get_stats(None, ctypes.byref(s)) == -1
+
+
+def test_init_without_a_gpu_reports_cuda_error(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    st, ctx = _init(lib)
+    assert st == -3
+    assert lib.exx_last_error(None).decode()
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    import importlib
+    from paper_1911_10630_gb300 import exx
+    m = importlib.reload(exx)  # a fresh binding with no library loaded yet
+    with pytest.raises(OSError):
+        m.load(str(tmp_path / "missing.so"))
