@@ -21,13 +21,20 @@ cudaError_t launch_pair_list(int n, const double* centers, const double L[3], co
 cudaError_t launch_zero(double* p, long long n, int num_sms, cudaStream_t st);
 cudaError_t launch_exx_reduce(const PairRec* pairs, const int* n_pair, const double* e_pair, double* out,
                               cudaStream_t st);
-cudaError_t set_multipole_const(const MultipoleConst& mc);
+cudaError_t set_multipole_const_solve(const MultipoleConst& mc);
+cudaError_t set_multipole_const_cluster(const MultipoleConst& mc);
 size_t pair_kernel_smem(int Rc, int r_pe_max);
 cudaError_t launch_pair_kernel(const SolveParams& P, int threads, bool mixed, int grid, size_t smem, cudaStream_t st);
 cudaError_t pair_kernel_occupancy(int threads, bool mixed, size_t smem, int* blocks_per_sm);
 cudaError_t launch_debug_readback(const SolveParams& P, const PairRec& pr, double* rho_me, double* v_me,
                                   cudaStream_t st);
 cudaError_t launch_apply(const SolveParams& P, const double* p, double* ap, cudaStream_t st);
+size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant);
+int cluster_variant(int C, int max_pts, int threads);
+cudaError_t cluster_prepare(int variant, size_t smem, int* max_clusters);
+cudaError_t launch_cluster_kernel(int variant, const SolveParams& P, const ClusterLayout& CL, int n_clusters,
+                                  size_t smem, cudaStream_t st);
+int cluster_variant_threads(int variant);
 }  // namespace exx
 
 using namespace exx;
@@ -62,6 +69,13 @@ struct exx_ctx {
     size_t smem = 0;
     SolveParams P;
 
+    // cluster solver (precision 1): one thread-block cluster per pair
+    bool use_cluster = false;
+    int cl_variant = -1;
+    int n_clusters = 0;
+    ClusterLayout CL;
+    int* d_pt_slab = nullptr;
+
     // pair buffers
     int cap_n = 0;
     long long cap_pairs = 0;
@@ -88,6 +102,10 @@ struct exx_ctx {
     const void* g_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int g_n = -1;
     cudaStream_t g_stream = nullptr;
+
+    // internal stream (graph capture is not allowed on the legacy stream)
+    cudaStream_t work = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
     // timing
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -173,8 +191,12 @@ extern "C" void exx_destroy(exx_ctx* c) {
     cudaFree(c->d_dxx);
     cudaFree(c->d_cent);
     cudaFree(c->d_alpha);
+    cudaFree(c->d_pt_slab);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->work) cudaStreamDestroy(c->work);
     delete c;
 }
 
@@ -205,7 +227,11 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) o.inner_tol = 1e-5;
     if (o.threads != 0 && o.threads != 256 && o.threads != 512 && o.threads != 1024)
         return fail(nullptr, EXX_EINVAL, "exx_init: threads must be 0, 256, 512 or 1024");
-    if (o.solver_kind != 0 && o.solver_kind != 1) return fail(nullptr, EXX_EINVAL, "exx_init: solver_kind 2 is not available in this build");
+    if (o.solver_kind < 0 || o.solver_kind > 2) return fail(nullptr, EXX_EINVAL, "exx_init: solver_kind must be 0, 1 or 2");
+    if (o.solver_kind == 2 && o.precision != 1)
+        return fail(nullptr, EXX_EINVAL, "exx_init: solver_kind 2 (cluster) runs the FP32 inner solver: precision must be 1");
+    if (o.cluster_size != 0 && o.cluster_size != 2 && o.cluster_size != 4 && o.cluster_size != 8)
+        return fail(nullptr, EXX_EINVAL, "exx_init: cluster_size must be 0, 2, 4 or 8");
 
     c = new exx_ctx();
     std::memset(&c->stats, 0, sizeof(c->stats));
@@ -240,7 +266,8 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         build_multipole_const(mc);
         mc_built = true;
     }
-    e = set_multipole_const(mc);
+    e = set_multipole_const_solve(mc);
+    if (e == cudaSuccess) e = set_multipole_const_cluster(mc);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpyToSymbol(multipoles)"));
 
     // ball geometry (Algorithm 2), cube radius Rc = R_ME
@@ -297,18 +324,61 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     P.off_rows = off; off = align256(off + sizeof(double) * 8 * B.rows_pe.size());
     c->slot_bytes = off;
 
-    c->threads = o.threads ? o.threads : 512;
-    c->smem = pair_kernel_smem(Rc, r_pe);
+    // cluster solver: largest cluster size whose slab layout and registers fit
+    if (o.precision == 1 && o.solver_kind != 1) {
+        int max_optin = 0;
+        cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+        const int cands[3] = {8, 4, 2};
+        for (int ci = 0; ci < 3 && !c->use_cluster; ++ci) {
+            const int C = cands[ci];
+            if (o.cluster_size && o.cluster_size != C) continue;
+            ClusterLayout L;
+            std::vector<int> pt;
+            if (!build_cluster_layout(B, C, L, pt)) continue;
+            const int v = cluster_variant(C, L.max_pts, o.threads);
+            if (v < 0) continue;
+            const size_t sm = cluster_kernel_smem(Rc, L, v) + 2048;
+            if ((long)sm > (long)max_optin) continue;
+            int nclu = 0;
+            e = cluster_prepare(v, sm - 2048, &nclu);
+            if (e != cudaSuccess || nclu < 1) {
+                (void)cudaGetLastError();
+                continue;
+            }
+            e = cudaMalloc(&c->d_pt_slab, sizeof(int) * pt.size());
+            if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(slab table)"));
+            e = cudaMemcpy(c->d_pt_slab, pt.data(), sizeof(int) * pt.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpy(slab table)"));
+            L.pt_slab = c->d_pt_slab;
+            c->CL = L;
+            c->cl_variant = v;
+            c->n_clusters = nclu;
+            c->smem = sm - 2048;
+            c->threads = cluster_variant_threads(v);
+            c->use_cluster = true;
+        }
+        if (!c->use_cluster && o.solver_kind == 2)
+            return bail(fail(c, EXX_EINVAL, "exx_init: no cluster layout fits these radii"));
+    }
+
+    c->threads = c->use_cluster ? c->threads : (o.threads ? o.threads : 512);
+    if (!c->use_cluster) c->smem = pair_kernel_smem(Rc, r_pe);
     int bps = 0;
-    e = pair_kernel_occupancy(c->threads, o.precision == 1, c->smem, &bps);
-    if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
-    if (bps < 1) return bail(fail(c, EXX_ECUDA, "pair kernel does not fit on an SM"));
-    int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, bps) : std::min(bps, 2);
+    long long want;
+    if (c->use_cluster) {
+        want = c->n_clusters;
+    } else {
+        e = pair_kernel_occupancy(c->threads, o.precision == 1, c->smem, &bps);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
+        if (bps < 1) return bail(fail(c, EXX_ECUDA, "pair kernel does not fit on an SM"));
+        int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, bps) : std::min(bps, 2);
+        want = (long long)c->num_sms * per_sm;
+    }
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    long long want = (long long)c->num_sms * per_sm;
     long long fit = (long long)(0.25 * (double)free_b / (double)c->slot_bytes);
     c->n_slots = (int)std::max(1LL, std::min(want, fit));
+    if (c->use_cluster) c->n_clusters = c->n_slots;
     e = cudaMalloc(&c->ws, c->slot_bytes * (size_t)c->n_slots);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(workspace)"));
     e = cudaMemset(c->ws, 0, c->slot_bytes * (size_t)c->n_slots);
@@ -324,6 +394,10 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         e = cudaEventCreate(&ev);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaEventCreate"));
     }
+    if ((e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(c, e, "stream/event creation"));
 
     // fixed kernel parameters
     for (int a = 0; a < 3; ++a) {
@@ -367,9 +441,9 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
 
     c->stats.n_pe = B.n_pe;
     c->stats.n_me = B.n_me;
-    c->stats.solver_kind = 1;
-    c->stats.cluster_size = 1;
-    c->stats.grid_ctas = c->n_slots;
+    c->stats.solver_kind = c->use_cluster ? 2 : 1;
+    c->stats.cluster_size = c->use_cluster ? c->CL.C : 1;
+    c->stats.grid_ctas = c->use_cluster ? c->n_clusters * c->CL.C : c->n_slots;
     c->stats.threads = c->threads;
     *out = c;
     return EXX_OK;
@@ -393,7 +467,10 @@ static exx_status ensure_pairs(exx_ctx* c, int n) {
 
 // The launch sequence of one call (captured into a graph when batched).
 static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* centers, int n, double* d_xx,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool capturing) {
+    // inside a capture a plain event record only expresses a dependency; the
+    // external flag turns it into an event-record node that can be timed
+    const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     SolveParams P = c->P;
     P.phi = orbitals;
     P.dxx = d_xx;
@@ -403,18 +480,21 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
     P.iters = c->d_iters;
     P.refines = c->d_refines;
     P.dbg_b = nullptr;
-    CK(cudaEventRecord(c->ev[0], st), "cudaEventRecord");
+    CK(cudaEventRecordWithFlags(c->ev[0], st, evf), "cudaEventRecord");
     CK(launch_zero(d_xx, (long long)n * c->ngrid, c->num_sms, st), "zero D_xx");
     CK(cudaMemsetAsync(c->d_scalars + 2, 0, sizeof(int), st), "reset counters");
     CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
                         c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st),
        "pair list");
-    CK(cudaEventRecord(c->ev[1], st), "cudaEventRecord");
-    CK(launch_pair_kernel(P, c->threads, c->opt.precision == 1, c->n_slots, c->smem, st), "pair kernel");
-    CK(cudaEventRecord(c->ev[2], st), "cudaEventRecord");
+    CK(cudaEventRecordWithFlags(c->ev[1], st, evf), "cudaEventRecord");
+    if (c->use_cluster)
+        CK(launch_cluster_kernel(c->cl_variant, P, c->CL, c->n_clusters, c->smem, st), "cluster pair kernel");
+    else
+        CK(launch_pair_kernel(P, c->threads, c->opt.precision == 1, c->n_slots, c->smem, st), "pair kernel");
+    CK(cudaEventRecordWithFlags(c->ev[2], st, evf), "cudaEventRecord");
     CK(launch_exx_reduce(c->d_pairs, c->d_scalars, c->d_epair, c->d_exx, st), "E_xx reduction");
     CK(cudaMemcpyAsync(c->h_exx, c->d_exx, sizeof(double), cudaMemcpyDeviceToHost, st), "copy E_xx");
-    CK(cudaEventRecord(c->ev[3], st), "cudaEventRecord");
+    CK(cudaEventRecordWithFlags(c->ev[3], st, evf), "cudaEventRecord");
     return EXX_OK;
 }
 
@@ -428,19 +508,23 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
     if (((reinterpret_cast<uintptr_t>(orbitals) | reinterpret_cast<uintptr_t>(centers) |
           reinterpret_cast<uintptr_t>(d_xx) | reinterpret_cast<uintptr_t>(alphas)) & 7u) != 0)
         return fail(c, EXX_EINVAL, "exx_compute: arrays must be 8-byte aligned");
-    cudaStream_t st = (cudaStream_t)stream;
+    cudaStream_t user = (cudaStream_t)stream;
     exx_status s = ensure_pairs(c, n);
     if (s != EXX_OK) return s;
+    // all work runs on the context's stream, ordered after the caller's stream
+    cudaStream_t st = c->work;
+    CK(cudaEventRecord(c->ev_in, user), "cudaEventRecord(caller stream)");
+    CK(cudaStreamWaitEvent(st, c->ev_in, 0), "cudaStreamWaitEvent");
     cudaError_t e;
     if (c->opt.batched) {
-        const void* key[5] = {orbitals, centers, d_xx, (const void*)st, nullptr};
+        const void* key[5] = {orbitals, centers, d_xx, nullptr, nullptr};
         bool hit = c->gexec && c->g_n == n && std::equal(key, key + 5, c->g_key);
         if (!hit) {
             drop_graph(c);
             cudaGraph_t g;
             e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
-            s = enqueue(c, orbitals, centers, n, d_xx, st);
+            s = enqueue(c, orbitals, centers, n, d_xx, st, true);
             e = cudaStreamEndCapture(st, &g);
             if (s != EXX_OK) {
                 if (e == cudaSuccess) cudaGraphDestroy(g);
@@ -459,19 +543,20 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
         e = cudaGraphLaunch(c->gexec, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
     } else {
-        s = enqueue(c, orbitals, centers, n, d_xx, st);
+        s = enqueue(c, orbitals, centers, n, d_xx, st, false);
         if (s != EXX_OK) return s;
     }
+    CK(cudaEventRecord(c->ev_out, st), "cudaEventRecord(done)");
+    CK(cudaStreamWaitEvent(user, c->ev_out, 0), "cudaStreamWaitEvent(caller stream)");
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(c, e, "exx_compute (stream synchronize)");
     *e_xx = c->h_exx[0];
     c->last_n = n;
     c->last_orb = orbitals;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]);
-    c->stats.solve_ms = ms;
-    cudaEventElapsedTime(&ms, c->ev[0], c->ev[3]);
-    c->stats.total_ms = ms;
+    c->stats.solve_ms = cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess ? ms : -1.0;
+    c->stats.total_ms = cudaEventElapsedTime(&ms, c->ev[0], c->ev[3]) == cudaSuccess ? ms : -1.0;
+    (void)cudaGetLastError();  // a failed timing query must not leak into later status checks
     int nonconv = 0, npair = 0;
     CK(cudaMemcpy(&npair, c->d_scalars, sizeof(int), cudaMemcpyDeviceToHost), "read n_pair");
     CK(cudaMemcpy(&nonconv, c->d_scalars + 2, sizeof(int), cudaMemcpyDeviceToHost), "read nonconv");
@@ -585,6 +670,7 @@ extern "C" exx_status exx_debug_pair(exx_ctx* c, const double* orbitals, int ind
     if (!c) return fail(nullptr, EXX_EINVAL, "exx_debug_pair: ctx is NULL");
     if (!orbitals) return fail(c, EXX_EINVAL, "exx_debug_pair: orbitals is NULL");
     if (index < 0 || index >= c->stats.n_pair) return fail(c, EXX_ENOPAIR, "exx_debug_pair: index out of range");
+    (void)cudaGetLastError();
     cudaStream_t st = (cudaStream_t)stream;
     const HostBall& B = c->hb;
     PairRec pr;
@@ -615,7 +701,8 @@ extern "C" exx_status exx_debug_pair(exx_ctx* c, const double* orbitals, int ind
     P.refines = d_sc + 4;
     P.dbg_b = d_b;
     exx_status s = EXX_OK;
-    cudaError_t e = launch_pair_kernel(P, c->threads, c->opt.precision == 1, 1, c->smem, st);
+    cudaError_t e = c->use_cluster ? launch_cluster_kernel(c->cl_variant, P, c->CL, 1, c->smem, st)
+                                   : launch_pair_kernel(P, c->threads, c->opt.precision == 1, 1, c->smem, st);
     if (e == cudaSuccess) e = launch_debug_readback(P, pr, d_rho, d_v, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && rho) e = cudaMemcpy(rho, d_rho, sizeof(double) * B.n_me, cudaMemcpyDeviceToHost);
@@ -634,6 +721,7 @@ extern "C" exx_status exx_debug_pair(exx_ctx* c, const double* orbitals, int ind
 extern "C" exx_status exx_apply_operator(exx_ctx* c, const double* p, double* ap, void* stream) {
     if (!c) return fail(nullptr, EXX_EINVAL, "exx_apply_operator: ctx is NULL");
     if (!p || !ap) return fail(c, EXX_EINVAL, "exx_apply_operator: NULL argument");
+    (void)cudaGetLastError();
     cudaStream_t st = (cudaStream_t)stream;
     CK(launch_apply(c->P, p, ap, st), "apply operator");
     CK(cudaStreamSynchronize(st), "apply operator (synchronize)");

@@ -1,0 +1,341 @@
+// exx_cluster.cu -- one thread-block cluster per pair, FP32 inner CG state on chip.
+//
+// The C CTAs of a cluster share one pair. The PE ball is split into C slabs of
+// whole x planes (balanced by point count, at least 3 planes each so a stencil
+// leg reaches at most the adjacent CTA). Each CTA keeps the CG direction p of
+// its slab in shared memory as planes of a (2 R_PE + 7)^2 box (zero outside the
+// ball, so the stencil needs no bounds tests); the x legs that leave the slab
+// read the neighbouring CTA's slab through distributed shared memory. The
+// residual r, the correction d and A p of the CTA's points stay in registers
+// (a fixed point-to-thread map). Dot products are reduced per CTA, exchanged
+// through distributed shared memory and summed in rank order, so every CTA
+// holds the same value. Per inner iteration: three cluster barriers.
+//
+// The FP64 parts of the pair (gather, multipoles, shell potential, the FP64
+// residual 4 pi rho + lap v of each refinement step, E_ij, the D_xx scatter)
+// are spread over all threads of the cluster and keep their data in the
+// cluster's global workspace slot.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "exx_phases.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace exx {
+
+template <int NT, int C>
+__device__ __forceinline__ double cluster_sum(double v, double (*red)[33], int& flip, double (*part)[16], int& cflip,
+                                              cg::cluster_group& cl, int rank) {
+    v = block_sum<NT>(v, red, flip);
+    if (threadIdx.x < C) {
+        double* dst = cl.map_shared_rank(&part[cflip][0], (int)threadIdx.x);
+        dst[rank] = v;
+    }
+    cl.sync();
+    double s = 0.0;
+#pragma unroll
+    for (int r = 0; r < C; ++r) s += part[cflip][r];
+    cflip ^= 1;
+    return s;
+}
+
+// FP64 residual r = 4 pi rho + lap v on the CTA's points k0 + tid + j NT;
+// writes r64 (and the debug copy); returns the thread's sum of r^2.
+__device__ __noinline__ double cta_residual(const SolveParams& P, const int* __restrict__ cube,
+                                            const double* __restrict__ rho, const double* __restrict__ vc,
+                                            double* __restrict__ r64, int k0, int k1, int nt, bool dbg) {
+    double acc = 0.0;
+    for (int k = k0 + (int)threadIdx.x; k < k1; k += nt) {
+        const double rk = fma(kFourPi, rho[k], lap19<double>(vc, cube[k], P.S, P.S2, P.st64));
+        r64[k] = rk;
+        acc = fma(rk, rk, acc);
+        if (dbg) P.dbg_b[k] = rk;
+    }
+    return acc;
+}
+
+// v += scale * d on the CTA's points (d in shared memory, [j][NT] layout).
+__device__ __noinline__ void cta_update_v(const int* __restrict__ cube, double* __restrict__ vc,
+                                          const float* __restrict__ ds, double scale, int k0, int k1, int nt) {
+    int j = 0;
+    for (int k = k0 + (int)threadIdx.x; k < k1; k += nt, ++j) {
+        const int c = cube[k];
+        vc[c] = fma(scale, (double)ds[j * nt + threadIdx.x], vc[c]);
+    }
+}
+
+// sum of rho v over the CTA's points.
+__device__ __noinline__ double cta_energy(const int* __restrict__ cube, const double* __restrict__ rho,
+                                          const double* __restrict__ vc, int k0, int k1, int nt) {
+    double e = 0.0;
+    for (int k = k0 + (int)threadIdx.x; k < k1; k += nt) e = fma(rho[k], vc[cube[k]], e);
+    return e;
+}
+
+template <int NT, int C, int PTS>
+__global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P, const ClusterLayout CL) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    extern __shared__ double smem[];
+    __shared__ double red[2][33];
+    __shared__ double part[2][16];
+    __shared__ double s_M[kNMono], s_T[kNMono];
+    __shared__ int s_item;
+    int flip = 0, cflip = 0;
+
+    const int Rc = P.Rc;
+    double* xp = smem;
+    double* yp = xp + (2 * Rc + 1) * 8;
+    double* zp = yp + (2 * Rc + 1) * 8;
+    double* sY = zp + (2 * Rc + 1) * 8;
+    float* ps = reinterpret_cast<float*>(sY + CL.sy_doubles);
+    float* ds = ps + CL.cap_planes * CL.Sp2;  // [PTS][NT] CG correction of the CTA's points
+    const int Syz = CL.Syz;
+    const int Sp2 = CL.Sp2;
+
+    fill_power_tables(P, xp, yp, zp, threadIdx.x, NT);
+    for (int t = threadIdx.x; t < CL.cap_planes * Sp2; t += NT) ps[t] = 0.0f;
+
+    float* pm = rank > 0 ? cl.map_shared_rank(ps, rank - 1) : nullptr;
+    float* pp = rank < C - 1 ? cl.map_shared_rank(ps, rank + 1) : nullptr;
+    const int planes = CL.planes[rank];
+    const int planes_prev = rank > 0 ? CL.planes[rank - 1] : 0;
+    const int k0 = CL.k0[rank], k1 = CL.k1[rank];
+    int pk[PTS];
+#pragma unroll
+    for (int j = 0; j < PTS; ++j) {
+        const int k = k0 + (int)threadIdx.x + j * NT;
+        pk[j] = k < k1 ? CL.pt_slab[k] : -1;
+    }
+
+    const int cid = blockIdx.x / C;
+    char* slot = P.ws + (size_t)cid * P.slot_bytes;
+    double* vc = reinterpret_cast<double*>(slot + P.off_vcube);
+    double* rho = reinterpret_cast<double*>(slot + P.off_rho);
+    double* r64 = reinterpret_cast<double*>(slot + P.off_r);
+    double* rowS = reinterpret_cast<double*>(slot + P.off_rows);
+
+    const Stencil<float> st = P.st32;
+    const int gt = rank * NT + (int)threadIdx.x, gn = C * NT;
+    const int np = *P.n_pair;
+    cl.sync();
+
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) {
+            const int it = atomicAdd(P.queue, 1);
+            for (int r = 0; r < C; ++r) *cl.map_shared_rank(&s_item, r) = it;
+        }
+        cl.sync();
+        const int item = s_item;
+        if (item >= np) break;
+        const int pidx = P.order ? P.order[item] : item;
+        const PairRec pr = P.pairs[pidx];
+        const BallGeo G = P.geos[pr.geo];
+        const int* cube = G.pt_cube;
+
+        // gather, multipoles, shell potential (FP64, spread over the cluster)
+        gather_rho(P, G, pr, rho, vc, gt, gn);
+        cl.sync();
+        moment_rows(P, G, rho, rowS, zp, gt, gn);
+        cl.sync();
+        moment_finish<NT>(P, G, rowS, xp, yp, sY, s_M, s_T);
+        shell_potential(P, G, vc, xp, yp, s_T, gt, gn);
+        cl.sync();
+
+        // FP64 refinement around FP32 inner CG
+        double bb = -1.0, rn_prev = 1e300;
+        int iters = 0, refines = 0;
+        bool conv = true;
+        for (;;) {
+            const double acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, bb < 0.0 && P.dbg_b);
+            const double rn2 = cluster_sum<NT, C>(acc, red, flip, part, cflip, cl, rank);
+            if (bb < 0.0) bb = rn2;
+            if (rn2 <= P.tol * P.tol * bb) break;
+            const double rn = sqrt(rn2);
+            if (refines >= P.max_refine || iters >= P.max_iter || !(rn < rn_prev)) {
+                conv = false;
+                break;
+            }
+            rn_prev = rn;
+            const double inv = 1.0 / rn;
+            float r[PTS], ap[PTS];
+            float a32 = 0.0f;
+#pragma unroll
+            for (int j = 0; j < PTS; ++j) {
+                r[j] = 0.0f;
+                ap[j] = 0.0f;
+                ds[j * NT + threadIdx.x] = 0.0f;
+                if (pk[j] >= 0) {
+                    const int k = k0 + (int)threadIdx.x + j * NT;
+                    r[j] = (float)(r64[k] * inv);
+                    ps[pk[j] & 0xffffff] = r[j];
+                    a32 = fmaf(r[j], r[j], a32);
+                }
+            }
+            double rr = cluster_sum<NT, C>((double)a32, red, flip, part, cflip, cl, rank);
+            double eta = 0.3 * P.tol * sqrt(bb) / rn;
+            eta = eta > P.inner_tol ? eta : P.inner_tol;
+            const double target2 = eta * eta * rr;
+            const int budget = min(P.inner_max_iter, P.max_iter - iters);
+            int it = 0;
+            while (rr > target2 && it < budget) {
+                float pa = 0.0f;
+#pragma unroll
+                for (int j = 0; j < PTS; ++j) {
+                    if (pk[j] >= 0) {
+                        const int off = pk[j] & 0xffffff, xl = pk[j] >> 24;
+                        const float pc = ps[off];
+                        float a = st.c0 * pc;
+#pragma unroll
+                        for (int q = 1; q <= 3; ++q) {
+                            a = fmaf(st.cz[q - 1], ps[off + q] + ps[off - q], a);
+                            a = fmaf(st.cy[q - 1], ps[off + q * Syz] + ps[off - q * Syz], a);
+                            const float xpv = xl + q < planes ? ps[off + q * Sp2]
+                                                              : (pp ? pp[off + (q - planes) * Sp2] : 0.0f);
+                            const float xmv = xl - q >= 0 ? ps[off - q * Sp2]
+                                                          : (pm ? pm[off + (planes_prev - q) * Sp2] : 0.0f);
+                            a = fmaf(st.cx[q - 1], xpv + xmv, a);
+                        }
+                        ap[j] = -a;
+                        pa = fmaf(pc, -a, pa);
+                    }
+                }
+                const double pap = cluster_sum<NT, C>((double)pa, red, flip, part, cflip, cl, rank);
+                const float al = (float)(rr / pap);
+                float ra = 0.0f;
+#pragma unroll
+                for (int j = 0; j < PTS; ++j) {
+                    if (pk[j] >= 0) {
+                        float* dj = ds + j * NT + threadIdx.x;
+                        *dj = fmaf(al, ps[pk[j] & 0xffffff], *dj);
+                        r[j] = fmaf(-al, ap[j], r[j]);
+                        ra = fmaf(r[j], r[j], ra);
+                    }
+                }
+                const double rrn = cluster_sum<NT, C>((double)ra, red, flip, part, cflip, cl, rank);
+                ++it;
+                if (rrn <= target2 || !(rrn == rrn)) {
+                    rr = rrn;
+                    break;
+                }
+                const float be = (float)(rrn / rr);
+                rr = rrn;
+#pragma unroll
+                for (int j = 0; j < PTS; ++j)
+                    if (pk[j] >= 0) {
+                        const int off = pk[j] & 0xffffff;
+                        ps[off] = fmaf(be, ps[off], r[j]);
+                    }
+                cl.sync();
+            }
+            iters += it;
+            cta_update_v(cube, vc, ds, rn, k0, k1, NT);
+            ++refines;
+            cl.sync();
+        }
+
+        // E_ij and the scatter
+        double e = cta_energy(cube, rho, vc, k0, k1, NT);
+        e = cluster_sum<NT, C>(e, red, flip, part, cflip, cl, rank);
+        if (rank == 0 && threadIdx.x == 0) {
+            P.e_pair[pidx] = e * P.dV;
+            P.iters[pidx] = iters;
+            if (P.refines) P.refines[pidx] = refines;
+            if (!conv) atomicAdd(P.nonconv, 1);
+        }
+        scatter_dxx(P, G, pr, vc, gt, gn);
+        cl.sync();
+    }
+}
+
+// ---- host side ----
+cudaError_t set_multipole_const_cluster(const MultipoleConst& mc) {
+    return cudaMemcpyToSymbol(c_mp, &mc, sizeof(MultipoleConst));
+}
+
+size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant);
+
+template <int NT, int C, int PTS>
+static const void* kernel_ptr() {
+    return (const void*)cluster_pair_kernel<NT, C, PTS>;
+}
+
+// Supported (threads, cluster size, points per thread) instantiations.
+struct ClusterVariant {
+    int nt, c, pts;
+    const void* fn;
+    cudaError_t (*launch)(const SolveParams&, const ClusterLayout&, int, size_t, cudaStream_t);
+};
+
+template <int NT, int C, int PTS>
+static cudaError_t launch_cluster_t(const SolveParams& P, const ClusterLayout& CL, int n_clusters, size_t smem,
+                                    cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_clusters * C, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cluster_pair_kernel<NT, C, PTS>, P, CL);
+}
+
+static const ClusterVariant kVariants[] = {
+    {512, 2, 8, (const void*)cluster_pair_kernel<512, 2, 8>, launch_cluster_t<512, 2, 8>},
+    {512, 2, 18, (const void*)cluster_pair_kernel<512, 2, 18>, launch_cluster_t<512, 2, 18>},
+    {512, 4, 10, (const void*)cluster_pair_kernel<512, 4, 10>, launch_cluster_t<512, 4, 10>},
+    {512, 4, 18, (const void*)cluster_pair_kernel<512, 4, 18>, launch_cluster_t<512, 4, 18>},
+    {512, 8, 17, (const void*)cluster_pair_kernel<512, 8, 17>, launch_cluster_t<512, 8, 17>},
+    {1024, 8, 9, (const void*)cluster_pair_kernel<1024, 8, 9>, launch_cluster_t<1024, 8, 9>},
+};
+
+// Picks the instantiation for (C, max points per CTA, preferred threads).
+// Returns the index into kVariants or -1.
+int cluster_variant(int C, int max_pts, int threads) {
+    int best = -1;
+    for (int v = 0; v < (int)(sizeof(kVariants) / sizeof(kVariants[0])); ++v) {
+        const ClusterVariant& K = kVariants[v];
+        if (K.c != C || K.nt * K.pts < max_pts) continue;
+        if (threads && K.nt != threads) continue;
+        if (best < 0 || K.nt * K.pts < kVariants[best].nt * kVariants[best].pts) best = v;
+    }
+    return best;
+}
+
+cudaError_t cluster_prepare(int variant, size_t smem, int* max_clusters) {
+    const ClusterVariant& K = kVariants[variant];
+    cudaError_t e = cudaFuncSetAttribute(K.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(K.c, 1, 1);
+    cfg.blockDim = dim3(K.nt, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = K.c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(max_clusters, K.fn, &cfg);
+}
+
+cudaError_t launch_cluster_kernel(int variant, const SolveParams& P, const ClusterLayout& CL, int n_clusters,
+                                  size_t smem, cudaStream_t st) {
+    return kVariants[variant].launch(P, CL, n_clusters, smem, st);
+}
+
+int cluster_variant_threads(int variant) { return kVariants[variant].nt; }
+
+size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant) {
+    return sizeof(double) * ((size_t)3 * (2 * Rc + 1) * 8 + (size_t)CL.sy_doubles) +
+           sizeof(float) * ((size_t)CL.cap_planes * CL.Sp2 + (size_t)kVariants[variant].nt * kVariants[variant].pts);
+}
+
+}  // namespace exx

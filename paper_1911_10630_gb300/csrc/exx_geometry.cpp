@@ -14,6 +14,7 @@
 // Cartesian moments of degree <= 6 and the polynomial P_l on the shell.
 #include "exx_geometry.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -142,6 +143,60 @@ void build_ball(HostBall& B, int r_pe, int r_me, int Rc) {
             }
         }
     B.n_me = (int)B.cube.size();
+}
+
+bool build_cluster_layout(const HostBall& B, int C, ClusterLayout& L, std::vector<int>& pt_slab) {
+    const int R = B.r_pe, P = 2 * R + 1;
+    if (C < 1 || C > kMaxCluster || P < 3 * C) return false;
+    std::vector<long> n(P, 0), cum(P + 1, 0);
+    for (const RowRec& row : B.rows_pe) n[row.ox + R] += 2 * row.zpe + 1;
+    for (int i = 0; i < P; ++i) cum[i + 1] = cum[i] + n[i];
+    // f[r][i]: smallest max load of the first i planes in r slabs of >= 3 planes
+    const long INF = 1L << 60;
+    std::vector<std::vector<long>> f(C + 1, std::vector<long>(P + 1, INF));
+    std::vector<std::vector<int>> arg(C + 1, std::vector<int>(P + 1, -1));
+    f[0][0] = 0;
+    for (int r = 1; r <= C; ++r)
+        for (int i = 3 * r; i <= P; ++i)
+            for (int j = 3 * (r - 1); j <= i - 3; ++j) {
+                if (f[r - 1][j] >= INF) continue;
+                const long v = std::max(f[r - 1][j], cum[i] - cum[j]);
+                if (v < f[r][i]) {
+                    f[r][i] = v;
+                    arg[r][i] = j;
+                }
+            }
+    if (f[C][P] >= INF) return false;
+    std::vector<int> bounds(C + 1);
+    bounds[C] = P;
+    for (int r = C; r >= 1; --r) bounds[r - 1] = arg[r][bounds[r]];
+    std::memset(&L, 0, sizeof(L));
+    L.C = C;
+    L.Syz = 2 * R + 7;
+    L.Sp2 = L.Syz * L.Syz;
+    L.sy_doubles = ((2 * R + 1) * 28 + 1) & ~1;
+    int cap = 0, maxp = 0;
+    for (int r = 0; r < C; ++r) {
+        L.x0[r] = bounds[r] - R;
+        L.planes[r] = bounds[r + 1] - bounds[r];
+        L.k0[r] = (int)cum[bounds[r]];
+        L.k1[r] = (int)cum[bounds[r + 1]];
+        cap = std::max(cap, L.planes[r]);
+        maxp = std::max(maxp, L.k1[r] - L.k0[r]);
+    }
+    L.cap_planes = cap;
+    L.max_pts = maxp;
+    if ((long)cap * L.Sp2 >= (1L << 24)) return false;
+    pt_slab.assign(B.n_pe, 0);
+    int r = 0;
+    for (int k = 0; k < B.n_pe; ++k) {
+        while (k >= L.k1[r]) ++r;
+        const int packed = B.off[k];
+        const int ox = (packed & 0xff) - 128, oy = ((packed >> 8) & 0xff) - 128, oz = ((packed >> 16) & 0xff) - 128;
+        const int xl = ox - L.x0[r];
+        pt_slab[k] = (xl << 24) | (xl * L.Sp2 + (oy + R + 3) * L.Syz + (oz + R + 3));
+    }
+    return true;
 }
 
 }  // namespace exx

@@ -17,6 +17,11 @@ struct HostBall {
 };
 
 void build_multipole_const(MultipoleConst& mc);
+
+// Splits the PE ball of B into C slabs of whole x planes (each >= 3 planes),
+// minimising the largest point count. Fills L (without the device pointer) and
+// the per-point slab offsets. Returns false if no such split exists.
+bool build_cluster_layout(const HostBall& B, int C, ClusterLayout& L, std::vector<int>& pt_slab);
 void build_ball(HostBall& B, int r_pe, int r_me, int Rc);
 
 }  // namespace exx

@@ -106,6 +106,20 @@ struct SolveParams {
     double* dbg_b;        // if set, the RHS b of the processed pair (slot 0)
 };
 
+// Slab decomposition of the PE ball over the C CTAs of a cluster (FP32 inner
+// CG kept in shared memory): CTA r owns the whole x planes x0[r] .. x0[r] +
+// planes[r] - 1 and the compact PE points k0[r] .. k1[r] - 1.
+constexpr int kMaxCluster = 16;
+struct ClusterLayout {
+    int C;
+    int Syz, Sp2;        // slab box side 2 R_PE + 7 and its square
+    int cap_planes;      // max planes of a slab (shared memory per CTA)
+    int sy_doubles;      // doubles reserved for the plane sums before the slab
+    int max_pts;         // max points of a CTA
+    int x0[kMaxCluster], planes[kMaxCluster], k0[kMaxCluster], k1[kMaxCluster];
+    const int* pt_slab;  // [n_pe] slab offset | (plane within slab) << 24
+};
+
 // Host-built constants of the Cartesian form of the multipole expansion.
 struct MultipoleConst {
     double K[1596];        // block-diagonal K_l, l = 0..6, row-major per block

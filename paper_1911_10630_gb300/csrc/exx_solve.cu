@@ -23,11 +23,9 @@
 // needs no bounds checks; the other CG vectors are compact over the PE ball.
 #include <cuda_runtime.h>
 
-#include "exx_kernels.cuh"
+#include "exx_phases.cuh"
 
 namespace exx {
-
-__constant__ MultipoleConst c_mp;
 
 // --------------------------------------------------------------------------
 // Conjugate gradient on the PE ball (Step IV). On entry: r = rhs, p = rhs on
@@ -85,129 +83,6 @@ __device__ int cg_ball(T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d,
 }
 
 // --------------------------------------------------------------------------
-// Multipole moments (Eq. mepole) in Cartesian form and the polynomial
-// coefficients T of P_l. Leaves T in s_T[84] (zero above lmax).
-// --------------------------------------------------------------------------
-template <int NT>
-__device__ void moments(const SolveParams& P, const BallGeo& G, const double* __restrict__ rho,
-                        double* __restrict__ rowS, const double* __restrict__ xp, const double* __restrict__ yp,
-                        const double* __restrict__ zp, double* __restrict__ sY, double* __restrict__ s_M,
-                        double* __restrict__ s_T, const int* __restrict__ plane_start) {
-    const int L = P.lmax;
-    const int Rc = P.Rc;
-    // row sums S_c(x, y) = sum_z z^c rho(x, y, z)
-    for (int row = threadIdx.x; row < G.n_rows_pe; row += NT) {
-        const RowRec R = G.rows_pe[row];
-        double s[kLmaxMax + 1];
-#pragma unroll
-        for (int c = 0; c <= kLmaxMax; ++c) s[c] = 0.0;
-        const double* rr = rho + R.pe_start;
-        for (int z = -R.zpe; z <= R.zpe; ++z) {
-            const double v = rr[z + R.zpe];
-            const double* zz = zp + (z + Rc) * 8;
-#pragma unroll
-            for (int c = 0; c <= kLmaxMax; ++c) s[c] = fma(v, zz[c], s[c]);
-        }
-#pragma unroll
-        for (int c = 0; c <= kLmaxMax; ++c) rowS[row * 8 + c] = s[c];
-    }
-    __syncthreads();
-    // plane sums Y_{bc}(x) = sum_y y^b S_c(x, y), b + c <= L
-    const int nplane = 2 * G.r_pe + 1;
-    const int nbc = (L + 1) * (L + 2) / 2;
-    for (int item = threadIdx.x; item < nplane * nbc; item += NT) {
-        const int pl = item / nbc, bc = item - pl * nbc;
-        int dgr = 0;
-        while ((dgr + 1) * (dgr + 2) / 2 <= bc) ++dgr;
-        const int c = bc - dgr * (dgr + 1) / 2, b = dgr - c;
-        double acc = 0.0;
-        for (int row = plane_start[pl]; row < plane_start[pl + 1]; ++row) {
-            const int oy = G.rows_pe[row].oy;
-            acc = fma(yp[(oy + Rc) * 8 + b], rowS[row * 8 + c], acc);
-        }
-        sY[pl * 28 + bc] = acc;
-    }
-    __syncthreads();
-    // M_abc = dV sum_x x^a Y_bc(x)
-    for (int m = threadIdx.x; m < kNMono; m += NT) {
-        const int a = c_mp.mono[m][0], b = c_mp.mono[m][1], c = c_mp.mono[m][2];
-        double acc = 0.0;
-        if (a + b + c <= L) {
-            const int dgr = b + c, bc = dgr * (dgr + 1) / 2 + c;
-            for (int pl = 0; pl < nplane; ++pl) acc = fma(xp[(pl - G.r_pe + Rc) * 8 + a], sY[pl * 28 + bc], acc);
-        }
-        s_M[m] = acc * P.dV;
-    }
-    __syncthreads();
-    // T_l = K_l M_l
-    for (int m = threadIdx.x; m < kNMono; m += NT) {
-        const int l = c_mp.mono[m][0] + c_mp.mono[m][1] + c_mp.mono[m][2];
-        double acc = 0.0;
-        if (l <= L) {
-            const int nl = (l + 1) * (l + 2) / 2, r0 = c_mp.mono_off[l];
-            const double* Kr = c_mp.K + c_mp.k_off[l] + (m - r0) * nl;
-            for (int t = 0; t < nl; ++t) acc = fma(Kr[t], s_M[r0 + t], acc);
-        }
-        s_T[m] = acc;
-    }
-    __syncthreads();
-}
-
-// --------------------------------------------------------------------------
-// Far-field potential on the shell (Eq. me): v = sum_l P_l(r) / r^(2l+1),
-// one thread per (x, y) row of the ME ball, written into the v cube.
-// --------------------------------------------------------------------------
-template <int NT>
-__device__ void shell_potential(const SolveParams& P, const BallGeo& G, double* __restrict__ vc,
-                                const double* __restrict__ xp, const double* __restrict__ yp,
-                                const double* __restrict__ s_T) {
-    const int Rc = P.Rc;
-    for (int row = threadIdx.x; row < G.n_rows_me; row += NT) {
-        const RowRec R = G.rows_me[row];
-        const double* xa = xp + (R.ox + Rc) * 8;
-        const double* yb = yp + (R.oy + Rc) * 8;
-        // U_{l,c} = sum_{a+b=l-c} T_abc x^a y^b
-        double U[kNU];
-#pragma unroll
-        for (int u = 0; u < kNU; ++u) U[u] = 0.0;
-        {
-            int m = 0;
-#pragma unroll
-            for (int l = 0; l <= kLmaxMax; ++l)
-#pragma unroll
-                for (int a = l; a >= 0; --a)
-#pragma unroll
-                    for (int b = l - a; b >= 0; --b) {
-                        const int c = l - a - b;
-                        U[l * (l + 1) / 2 + c] = fma(s_T[m], xa[a] * yb[b], U[l * (l + 1) / 2 + c]);
-                        ++m;
-                    }
-        }
-        const double x = R.ox * P.delta[0], y = R.oy * P.delta[1];
-        const double rxy2 = x * x + y * y;
-        const long long base = (long long)(R.ox + Rc) * P.S2 + (long long)(R.oy + Rc) * P.S + Rc;
-        const int zlo_hi = R.zpe >= 0 ? -R.zpe - 1 : R.zme;  // first segment ends here
-        for (int z = -R.zme; z <= R.zme; ++z) {
-            if (R.zpe >= 0 && z > zlo_hi && z <= R.zpe) continue;
-            const double zz = z * P.delta[2];
-            const double r2 = fma(zz, zz, rxy2);
-            const double ir = rsqrt(r2);
-            const double ir2 = ir * ir;
-            double acc = 0.0;
-#pragma unroll
-            for (int l = kLmaxMax; l >= 0; --l) {
-                const double* Ul = U + l * (l + 1) / 2;
-                double pl = Ul[l];
-#pragma unroll
-                for (int c = l - 1; c >= 0; --c) pl = fma(pl, zz, Ul[c]);
-                acc = fma(acc, ir2, pl);
-            }
-            vc[base + z] = acc * ir;
-        }
-    }
-}
-
-// --------------------------------------------------------------------------
 // The persistent pair kernel.
 // --------------------------------------------------------------------------
 template <int NT, bool MIXED>
@@ -226,19 +101,7 @@ __global__ void __launch_bounds__(NT, 1) pair_kernel(const SolveParams P) {
     double* zp = yp + (2 * Rc + 1) * 8;     // z^c
     double* sY = zp + (2 * Rc + 1) * 8;     // [(2 Rmax_pe + 1) * 28]
 
-    for (int t = threadIdx.x; t < (2 * Rc + 1) * 8; t += NT) {
-        const int o = t / 8 - Rc, e = t % 8;
-        double px = 1.0, py = 1.0, pz = 1.0;
-        const double x = o * P.delta[0], y = o * P.delta[1], z = o * P.delta[2];
-        for (int k = 0; k < e; ++k) {
-            px *= x;
-            py *= y;
-            pz *= z;
-        }
-        xp[t] = px;
-        yp[t] = py;
-        zp[t] = pz;
-    }
+    fill_power_tables(P, xp, yp, zp, threadIdx.x, NT);
     __syncthreads();
 
     char* slot = P.ws + (size_t)blockIdx.x * P.slot_bytes;
@@ -254,20 +117,9 @@ __global__ void __launch_bounds__(NT, 1) pair_kernel(const SolveParams P) {
     float* ap32 = reinterpret_cast<float*>(slot + P.off_ap32);
     double* rowS = reinterpret_cast<double*>(slot + P.off_rows);
 
-    Stencil<double> neg64;
-    Stencil<float> neg32;
-    neg64.c0 = -P.st64.c0;
-    neg32.c0 = -P.st32.c0;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        neg64.cx[q] = -P.st64.cx[q];
-        neg64.cy[q] = -P.st64.cy[q];
-        neg64.cz[q] = -P.st64.cz[q];
-        neg32.cx[q] = -P.st32.cx[q];
-        neg32.cy[q] = -P.st32.cy[q];
-        neg32.cz[q] = -P.st32.cz[q];
-    }
-    const double four_pi = 12.566370614359172953850573533118;
+    const Stencil<double> neg64 = negated(P.st64);
+    const Stencil<float> neg32 = negated(P.st32);
+    const double four_pi = kFourPi;
     const int np = *P.n_pair;
 
     for (;;) {
@@ -280,22 +132,18 @@ __global__ void __launch_bounds__(NT, 1) pair_kernel(const SolveParams P) {
         const BallGeo G = P.geos[pr.geo];
         const int* cube = G.pt_cube;
         const int n_pe = G.n_pe;
-        const double* phi_i = P.phi + (long long)pr.i * P.ngrid;
-        const double* phi_j = P.phi + (long long)pr.j * P.ngrid;
 
         // 1. gather rho on the PE ball; v = 0 there
-        for (int k = threadIdx.x; k < n_pe; k += NT) {
-            const long long g = grid_index(P.N, pr.g, G.pt_off[k]);
-            rho[k] = phi_i[g] * phi_j[g];
-            vc[cube[k]] = 0.0;
-        }
+        gather_rho(P, G, pr, rho, vc, threadIdx.x, NT);
         __syncthreads();
 
         // 2. multipole moments and polynomial coefficients
-        moments<NT>(P, G, rho, rowS, xp, yp, zp, sY, s_M, s_T, G.plane_pe);
+        moment_rows(P, G, rho, rowS, zp, threadIdx.x, NT);
+        __syncthreads();
+        moment_finish<NT>(P, G, rowS, xp, yp, sY, s_M, s_T);
 
         // 3. far-field potential on the shell
-        shell_potential<NT>(P, G, vc, xp, yp, s_T);
+        shell_potential(P, G, vc, xp, yp, s_T, threadIdx.x, NT);
         __syncthreads();
 
         // 4./5. right-hand side and solve
@@ -375,17 +223,7 @@ __global__ void __launch_bounds__(NT, 1) pair_kernel(const SolveParams P) {
             if (P.refines) P.refines[pidx] = refines;
             if (!conv) atomicAdd(P.nonconv, 1);
         }
-        if (P.dxx) {
-            double* Di = P.dxx + (long long)pr.i * P.ngrid;
-            double* Dj = P.dxx + (long long)pr.j * P.ngrid;
-            const bool two = pr.i != pr.j;
-            for (int q = threadIdx.x; q < G.n_me; q += NT) {
-                const long long g = grid_index(P.N, pr.g, G.pt_off[q]);
-                const double v = vc[cube[q]];
-                atomicAdd(Di + g, v * phi_j[g]);
-                if (two) atomicAdd(Dj + g, v * phi_i[g]);
-            }
-        }
+        scatter_dxx(P, G, pr, vc, threadIdx.x, NT);
         __syncthreads();
     }
 }
@@ -414,13 +252,7 @@ __global__ void apply_scatter(const SolveParams P, const double* p) {
 __global__ void apply_stencil(const SolveParams P, double* ap) {
     const BallGeo G = P.geos[0];
     const double* pc = reinterpret_cast<const double*>(P.ws + P.off_pcube);
-    Stencil<double> neg;
-    neg.c0 = -P.st64.c0;
-    for (int q = 0; q < 3; ++q) {
-        neg.cx[q] = -P.st64.cx[q];
-        neg.cy[q] = -P.st64.cy[q];
-        neg.cz[q] = -P.st64.cz[q];
-    }
+    const Stencil<double> neg = negated(P.st64);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G.n_pe; k += gridDim.x * blockDim.x)
         ap[k] = lap19<double>(pc, G.pt_cube[k], P.S, P.S2, neg);
 }
@@ -433,7 +265,7 @@ __global__ void apply_unscatter(const SolveParams P) {
 }
 
 // ---- host side ----
-cudaError_t set_multipole_const(const MultipoleConst& mc) {
+cudaError_t set_multipole_const_solve(const MultipoleConst& mc) {
     return cudaMemcpyToSymbol(c_mp, &mc, sizeof(MultipoleConst));
 }
 

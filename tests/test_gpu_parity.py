@@ -39,10 +39,14 @@ def _pairs_equal(gpu_pairs, ref_pairs):
     np.testing.assert_array_equal(gpu_pairs["g"], g)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_cfg0_end_to_end(torch, cfg0, precision):
+@pytest.mark.parametrize("precision,solver_kind,cluster_size", [(0, 1, 0), (1, 1, 0), (1, 2, 8), (1, 2, 4),
+                                                               (1, 2, 2)])
+def test_cfg0_end_to_end(torch, cfg0, precision, solver_kind, cluster_size):
     w, phi, ref = cfg0
-    out = run_gpu(w, phi, torch=torch, precision=precision)
+    out = run_gpu(w, phi, torch=torch, precision=precision, solver_kind=solver_kind, cluster_size=cluster_size)
+    assert out["stats"]["solver_kind"] == solver_kind
+    if cluster_size:
+        assert out["stats"]["cluster_size"] == cluster_size
     _pairs_equal(out["pairs"], ref["pairs"])
     assert out["stats"]["n_pair"] == 36 and out["stats"]["n_nonconv"] == 0
     assert abs(out["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
@@ -57,9 +61,10 @@ def test_cfg0_end_to_end(torch, cfg0, precision):
         assert np.max(np.abs(out["pairs"]["iters"] - ref["rep_iters"])) <= 2
 
 
-def test_cfg0_pair_intermediates(torch, cfg0):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cfg0_pair_intermediates(torch, cfg0, precision):
     w, phi, ref = cfg0
-    out = run_gpu(w, phi, torch=torch, precision=0)
+    out = run_gpu(w, phi, torch=torch, precision=precision)
     pi, pj, g = ref["pairs"]
     for k in (0, 1, 9, 35):
         got = out["ex"].debug_pair(out["dphi"], k)
@@ -85,8 +90,8 @@ def test_operator_matches_oracle(torch):
     assert np.max(np.abs(dap.cpu().numpy() - ref)) <= 1e-13 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_small_anisotropic_ragged(torch, precision):
+@pytest.mark.parametrize("precision,solver_kind", [(0, 1), (1, 1), (1, 2)])
+def test_small_anisotropic_ragged(torch, precision, solver_kind):
     # non-cubic grid and cell, small balls, finite R_pair, pairs across faces
     w = synth.tiny(seed=3, n=6, npts=28, length=6.5, r_pe=5, r_me=9, r_pair=3.0, tol=1e-10)
     w.grid = np.array([28, 30, 26])
@@ -96,7 +101,8 @@ def test_small_anisotropic_ragged(torch, precision):
     w.centers[1] = [6.3, 3.2, 0.2]
     phi = w.orbitals()
     ref = oracle.exx_workload(w, tol=1e-13, orbitals=phi)
-    out = run_gpu(w, phi, torch=torch, precision=precision)
+    out = run_gpu(w, phi, torch=torch, precision=precision, solver_kind=solver_kind)
+    assert out["stats"]["solver_kind"] == solver_kind
     _pairs_equal(out["pairs"], ref["pairs"])
     assert abs(out["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
     assert d_maxrel(out["D"], ref["D"]) <= D_GATE_MAXREL
