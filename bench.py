@@ -214,10 +214,17 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--solver-kind", type=int, default=0, help="0 auto, 1 one CTA per pair, 2 cluster per pair")
+    ap.add_argument("--cluster-size", type=int, default=0)
+    ap.add_argument("--orbitals", type=int, default=0,
+                    help="keep only the first N orbitals of the workload (small cases for profiling)")
     args = ap.parse_args()
 
     from paper_1911_10630_gb300 import synth
     w = synth.config1()
+    if args.orbitals:
+        w.centers, w.alphas, w.pvecs = w.centers[:args.orbitals], w.alphas[:args.orbitals], w.pvecs[:args.orbitals]
+        w.name = w.name + "-first%d" % args.orbitals
     if args.impl == "reference":
         return reference_arm(args, w)
 
@@ -241,7 +248,8 @@ def main():
     dD = torch.empty_like(dphi)
     stream = torch.cuda.current_stream(dev)
     ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=args.precision,
-             threads=args.threads, ctas_per_sm=args.ctas_per_sm)
+             threads=args.threads, ctas_per_sm=args.ctas_per_sm, solver_kind=args.solver_kind,
+             cluster_size=args.cluster_size)
 
     def barrier():
         if ws > 1:

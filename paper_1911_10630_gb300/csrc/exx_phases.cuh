@@ -33,7 +33,7 @@ __device__ __forceinline__ void fill_power_tables(const SolveParams& P, double* 
 }
 
 // Step III: rho = phi_i phi_j on the PE ball (Eq. l2g indices); v = 0 there.
-__device__ __noinline__ void gather_rho(const SolveParams& P, const BallGeo& G, const PairRec& pr,
+static __device__ __noinline__ void gather_rho(const SolveParams& P, const BallGeo& G, const PairRec& pr,
                                            double* __restrict__ rho, double* __restrict__ vc, int tid, int nthr) {
     const double* phi_i = P.phi + (long long)pr.i * P.ngrid;
     const double* phi_j = P.phi + (long long)pr.j * P.ngrid;
@@ -45,7 +45,7 @@ __device__ __noinline__ void gather_rho(const SolveParams& P, const BallGeo& G, 
 }
 
 // Eq. mepole, stage 1: row sums S_c(x, y) = sum_z z^c rho(x, y, z), c <= 6.
-__device__ __noinline__ void moment_rows(const SolveParams& P, const BallGeo& G, const double* __restrict__ rho,
+static __device__ __noinline__ void moment_rows(const SolveParams& P, const BallGeo& G, const double* __restrict__ rho,
                                             double* __restrict__ rowS, const double* __restrict__ zp, int tid,
                                             int nthr) {
     const int Rc = P.Rc;
@@ -113,7 +113,7 @@ __device__ void moment_finish(const SolveParams& P, const BallGeo& G, const doub
 }
 
 // Eq. me on the shell: v = sum_l P_l(r) / r^(2l+1), one thread per ME row.
-__device__ __noinline__ void shell_potential(const SolveParams& P, const BallGeo& G, double* __restrict__ vc,
+static __device__ __noinline__ void shell_potential(const SolveParams& P, const BallGeo& G, double* __restrict__ vc,
                                                 const double* __restrict__ xp, const double* __restrict__ yp,
                                                 const double* __restrict__ s_T, int tid, int nthr) {
     const int Rc = P.Rc;
@@ -162,7 +162,7 @@ __device__ __noinline__ void shell_potential(const SolveParams& P, const BallGeo
 }
 
 // Step V scatter: D^i += v phi_j, D^j += v phi_i on the ME ball.
-__device__ __noinline__ void scatter_dxx(const SolveParams& P, const BallGeo& G, const PairRec& pr,
+static __device__ __noinline__ void scatter_dxx(const SolveParams& P, const BallGeo& G, const PairRec& pr,
                                             const double* __restrict__ vc, int tid, int nthr) {
     if (!P.dxx) return;
     const double* phi_i = P.phi + (long long)pr.i * P.ngrid;
