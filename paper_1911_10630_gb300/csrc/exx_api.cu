@@ -75,6 +75,8 @@ struct exx_ctx {
     int n_clusters = 0;
     ClusterLayout CL;
     int* d_pt_slab = nullptr;
+    int4* d_rank_info = nullptr;
+    double* d_pow = nullptr;
 
     // pair buffers
     int cap_n = 0;
@@ -119,6 +121,11 @@ struct exx_ctx {
 };
 
 static thread_local std::string g_init_err;
+
+namespace exx {
+// Error text for entry points without a context (read by exx_last_error(NULL)).
+void set_global_error(const std::string& msg) { g_init_err = msg; }
+}  // namespace exx
 
 static exx_status fail(exx_ctx* c, exx_status s, const std::string& msg) {
     if (c) c->err = msg;
@@ -192,6 +199,8 @@ extern "C" void exx_destroy(exx_ctx* c) {
     cudaFree(c->d_cent);
     cudaFree(c->d_alpha);
     cudaFree(c->d_pt_slab);
+    cudaFree(c->d_rank_info);
+    cudaFree(c->d_pow);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -322,7 +331,25 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     P.off_d32 = off; off = align256(off + sizeof(float) * B.n_pe);
     P.off_ap32 = off; off = align256(off + sizeof(float) * B.n_pe);
     P.off_rows = off; off = align256(off + sizeof(double) * 8 * B.rows_pe.size());
+    P.off_sy = off; off = align256(off + sizeof(double) * (size_t)kMaxCluster * (((2 * r_pe + 1) * 28 + 1) & ~1));
     c->slot_bytes = off;
+    // x^e, y^e, z^e (e < 8) for offsets -Rc..Rc, by repeated multiplication
+    {
+        std::vector<double> tab((size_t)3 * (2 * Rc + 1) * 8);
+        for (int a = 0; a < 3; ++a)
+            for (int o = -Rc; o <= Rc; ++o) {
+                const double x = o * c->delta[a];
+                double px = 1.0;
+                for (int e2 = 0; e2 < 8; ++e2) {
+                    tab[((size_t)a * (2 * Rc + 1) + (o + Rc)) * 8 + e2] = px;
+                    px *= x;
+                }
+            }
+        e = cudaMalloc(&c->d_pow, sizeof(double) * tab.size());
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_pow, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "power table"));
+        P.pow_tab = c->d_pow;
+    }
 
     // cluster solver: largest cluster size whose slab layout and registers fit
     if (o.precision == 1 && o.solver_kind != 1) {
@@ -350,6 +377,12 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             e = cudaMemcpy(c->d_pt_slab, pt.data(), sizeof(int) * pt.size(), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpy(slab table)"));
             L.pt_slab = c->d_pt_slab;
+            int4 ri[kMaxCluster];
+            for (int r = 0; r < C; ++r) ri[r] = make_int4(L.x0[r], L.planes[r], L.k0[r], L.k1[r]);
+            e = cudaMalloc(&c->d_rank_info, sizeof(int4) * C);
+            if (e == cudaSuccess) e = cudaMemcpy(c->d_rank_info, ri, sizeof(int4) * C, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return bail(cuda_fail(c, e, "slab rank table"));
+            L.rank_info = c->d_rank_info;
             c->CL = L;
             c->cl_variant = v;
             c->n_clusters = nclu;

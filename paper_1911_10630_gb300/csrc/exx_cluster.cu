@@ -24,16 +24,19 @@ namespace cg = cooperative_groups;
 
 namespace exx {
 
-template <int NT, int C>
-__device__ __forceinline__ double cluster_sum(double v, double (*red)[33], int& flip, double (*part)[16], int& cflip,
-                                              cg::cluster_group& cl, int rank) {
-    v = block_sum<NT>(v, red, flip);
+// Sum over the cluster: per-CTA block sum, then each CTA's partial is pushed
+// into every CTA's part[] through distributed shared memory and, after one
+// cluster barrier, summed in rank order (the same value in every CTA).
+template <int NT, int C, typename T>
+__device__ __forceinline__ T cluster_sum(T v, T (*red)[33], int& flip, T (*part)[16], int& cflip,
+                                         cg::cluster_group& cl, int rank) {
+    v = block_sum<NT, T>(v, red, flip);
     if (threadIdx.x < C) {
-        double* dst = cl.map_shared_rank(&part[cflip][0], (int)threadIdx.x);
+        T* dst = cl.map_shared_rank(&part[cflip][0], (int)threadIdx.x);
         dst[rank] = v;
     }
     cl.sync();
-    double s = 0.0;
+    T s = T(0);
 #pragma unroll
     for (int r = 0; r < C; ++r) s += part[cflip][r];
     cflip ^= 1;
@@ -80,33 +83,36 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
     extern __shared__ double smem[];
     __shared__ double red[2][33];
     __shared__ double part[2][16];
+    __shared__ float red32[2][33];
+    __shared__ float part32[2][16];
     __shared__ double s_M[kNMono], s_T[kNMono];
     __shared__ int s_item;
-    int flip = 0, cflip = 0;
+    int flip = 0, cflip = 0, flip32 = 0, cflip32 = 0;
 
     const int Rc = P.Rc;
-    double* xp = smem;
-    double* yp = xp + (2 * Rc + 1) * 8;
-    double* zp = yp + (2 * Rc + 1) * 8;
-    double* sY = zp + (2 * Rc + 1) * 8;
-    float* ps = reinterpret_cast<float*>(sY + CL.sy_doubles);
-    float* ds = ps + CL.cap_planes * CL.Sp2;  // [PTS][NT] CG correction of the CTA's points
+    // FP64 power tables (global, read-only) and this CTA's plane sums (global slot)
+    const double* xp = P.pow_tab;
+    const double* yp = xp + (2 * Rc + 1) * 8;
+    const double* zp = yp + (2 * Rc + 1) * 8;
+    // shared memory: the p slab, then the CG correction d and the point map, [PTS][NT] each
+    float* ps = reinterpret_cast<float*>(smem);
+    float* ds = ps + CL.cap_planes * CL.Sp2;
+    int* spk = reinterpret_cast<int*>(ds + PTS * NT);
     const int Syz = CL.Syz;
     const int Sp2 = CL.Sp2;
 
-    fill_power_tables(P, xp, yp, zp, threadIdx.x, NT);
     for (int t = threadIdx.x; t < CL.cap_planes * Sp2; t += NT) ps[t] = 0.0f;
 
     float* pm = rank > 0 ? cl.map_shared_rank(ps, rank - 1) : nullptr;
     float* pp = rank < C - 1 ? cl.map_shared_rank(ps, rank + 1) : nullptr;
-    const int planes = CL.planes[rank];
-    const int planes_prev = rank > 0 ? CL.planes[rank - 1] : 0;
-    const int k0 = CL.k0[rank], k1 = CL.k1[rank];
-    int pk[PTS];
+    const int4 me = CL.rank_info[rank];
+    const int planes = me.y;
+    const int planes_prev = rank > 0 ? CL.rank_info[rank - 1].y : 0;
+    const int k0 = me.z, k1 = me.w;
 #pragma unroll
     for (int j = 0; j < PTS; ++j) {
         const int k = k0 + (int)threadIdx.x + j * NT;
-        pk[j] = k < k1 ? CL.pt_slab[k] : -1;
+        spk[j * NT + threadIdx.x] = k < k1 ? CL.pt_slab[k] : -1;
     }
 
     const int cid = blockIdx.x / C;
@@ -115,6 +121,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
     double* rho = reinterpret_cast<double*>(slot + P.off_rho);
     double* r64 = reinterpret_cast<double*>(slot + P.off_r);
     double* rowS = reinterpret_cast<double*>(slot + P.off_rows);
+    double* sY = reinterpret_cast<double*>(slot + P.off_sy) + (size_t)rank * CL.sy_doubles;
 
     const Stencil<float> st = P.st32;
     const int gt = rank * NT + (int)threadIdx.x, gn = C * NT;
@@ -149,7 +156,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
         bool conv = true;
         for (;;) {
             const double acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, bb < 0.0 && P.dbg_b);
-            const double rn2 = cluster_sum<NT, C>(acc, red, flip, part, cflip, cl, rank);
+            const double rn2 = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
             if (bb < 0.0) bb = rn2;
             if (rn2 <= P.tol * P.tol * bb) break;
             const double rn = sqrt(rn2);
@@ -166,25 +173,27 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
                 r[j] = 0.0f;
                 ap[j] = 0.0f;
                 ds[j * NT + threadIdx.x] = 0.0f;
-                if (pk[j] >= 0) {
+                const int pkj = spk[j * NT + threadIdx.x];
+                if (pkj >= 0) {
                     const int k = k0 + (int)threadIdx.x + j * NT;
                     r[j] = (float)(r64[k] * inv);
-                    ps[pk[j] & 0xffffff] = r[j];
+                    ps[pkj & 0xffffff] = r[j];
                     a32 = fmaf(r[j], r[j], a32);
                 }
             }
-            double rr = cluster_sum<NT, C>((double)a32, red, flip, part, cflip, cl, rank);
+            float rr = cluster_sum<NT, C, float>(a32, red32, flip32, part32, cflip32, cl, rank);
             double eta = 0.3 * P.tol * sqrt(bb) / rn;
             eta = eta > P.inner_tol ? eta : P.inner_tol;
-            const double target2 = eta * eta * rr;
+            const float target2 = (float)(eta * eta) * rr;
             const int budget = min(P.inner_max_iter, P.max_iter - iters);
             int it = 0;
             while (rr > target2 && it < budget) {
                 float pa = 0.0f;
 #pragma unroll
                 for (int j = 0; j < PTS; ++j) {
-                    if (pk[j] >= 0) {
-                        const int off = pk[j] & 0xffffff, xl = pk[j] >> 24;
+                    const int pkj = spk[j * NT + threadIdx.x];
+                    if (pkj >= 0) {
+                        const int off = pkj & 0xffffff, xl = pkj >> 24;
                         const float pc = ps[off];
                         float a = st.c0 * pc;
 #pragma unroll
@@ -201,32 +210,35 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
                         pa = fmaf(pc, -a, pa);
                     }
                 }
-                const double pap = cluster_sum<NT, C>((double)pa, red, flip, part, cflip, cl, rank);
-                const float al = (float)(rr / pap);
+                const float pap = cluster_sum<NT, C, float>(pa, red32, flip32, part32, cflip32, cl, rank);
+                const float al = rr / pap;
                 float ra = 0.0f;
 #pragma unroll
                 for (int j = 0; j < PTS; ++j) {
-                    if (pk[j] >= 0) {
+                    const int pkj = spk[j * NT + threadIdx.x];
+                    if (pkj >= 0) {
                         float* dj = ds + j * NT + threadIdx.x;
-                        *dj = fmaf(al, ps[pk[j] & 0xffffff], *dj);
+                        *dj = fmaf(al, ps[pkj & 0xffffff], *dj);
                         r[j] = fmaf(-al, ap[j], r[j]);
                         ra = fmaf(r[j], r[j], ra);
                     }
                 }
-                const double rrn = cluster_sum<NT, C>((double)ra, red, flip, part, cflip, cl, rank);
+                const float rrn = cluster_sum<NT, C, float>(ra, red32, flip32, part32, cflip32, cl, rank);
                 ++it;
                 if (rrn <= target2 || !(rrn == rrn)) {
                     rr = rrn;
                     break;
                 }
-                const float be = (float)(rrn / rr);
+                const float be = rrn / rr;
                 rr = rrn;
 #pragma unroll
-                for (int j = 0; j < PTS; ++j)
-                    if (pk[j] >= 0) {
-                        const int off = pk[j] & 0xffffff;
+                for (int j = 0; j < PTS; ++j) {
+                    const int pkj = spk[j * NT + threadIdx.x];
+                    if (pkj >= 0) {
+                        const int off = pkj & 0xffffff;
                         ps[off] = fmaf(be, ps[off], r[j]);
                     }
+                }
                 cl.sync();
             }
             iters += it;
@@ -237,7 +249,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
 
         // E_ij and the scatter
         double e = cta_energy(cube, rho, vc, k0, k1, NT);
-        e = cluster_sum<NT, C>(e, red, flip, part, cflip, cl, rank);
+        e = cluster_sum<NT, C, double>(e, red, flip, part, cflip, cl, rank);
         if (rank == 0 && threadIdx.x == 0) {
             P.e_pair[pidx] = e * P.dV;
             P.iters[pidx] = iters;
@@ -334,8 +346,9 @@ cudaError_t launch_cluster_kernel(int variant, const SolveParams& P, const Clust
 int cluster_variant_threads(int variant) { return kVariants[variant].nt; }
 
 size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant) {
-    return sizeof(double) * ((size_t)3 * (2 * Rc + 1) * 8 + (size_t)CL.sy_doubles) +
-           sizeof(float) * ((size_t)CL.cap_planes * CL.Sp2 + (size_t)kVariants[variant].nt * kVariants[variant].pts);
+    (void)Rc;
+    const size_t per = (size_t)kVariants[variant].nt * kVariants[variant].pts;
+    return sizeof(float) * ((size_t)CL.cap_planes * CL.Sp2 + per) + sizeof(int) * per;
 }
 
 }  // namespace exx

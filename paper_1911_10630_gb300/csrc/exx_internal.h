@@ -83,6 +83,8 @@ struct SolveParams {
     size_t off_vcube, off_pcube, off_rho, off_r, off_d, off_ap;  // FP64 parts
     size_t off_p32, off_r32, off_d32, off_ap32;                  // FP32 parts
     size_t off_rows;                                             // [n_rows_pe][8] row sums
+    size_t off_sy;                                               // [C][(2 r_pe + 1) * 28] plane sums (cluster)
+    const double* pow_tab;  // [3][2 Rc + 1][8] x^e, y^e, z^e (cluster kernel; global, read-only)
 
     // solver
     double tol;
@@ -116,8 +118,9 @@ struct ClusterLayout {
     int cap_planes;      // max planes of a slab (shared memory per CTA)
     int sy_doubles;      // doubles reserved for the plane sums before the slab
     int max_pts;         // max points of a CTA
-    int x0[kMaxCluster], planes[kMaxCluster], k0[kMaxCluster], k1[kMaxCluster];
+    int x0[kMaxCluster], planes[kMaxCluster], k0[kMaxCluster], k1[kMaxCluster];  // host copy
     const int* pt_slab;  // [n_pe] slab offset | (plane within slab) << 24
+    const int4* rank_info;  // device [C]: x0, planes, k0, k1 (read by the kernel)
 };
 
 // Host-built constants of the Cartesian form of the multipole expansion.

@@ -11,6 +11,12 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __device__ __forceinline__ int warp_sum_int(int v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -19,16 +25,16 @@ __device__ __forceinline__ int warp_sum_int(int v) {
 
 // Deterministic block sum (fixed butterfly order). red is a [2][33] shared
 // buffer used alternately, so consecutive reductions need no trailing barrier.
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double (*red)[33], int& flip) {
+template <int NT, typename T>
+__device__ __forceinline__ T block_sum(T v, T (*red)[33], int& flip) {
     v = warp_sum(v);
-    double* buf = red[flip];
+    T* buf = red[flip];
     flip ^= 1;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) buf[w] = v;
     __syncthreads();
     if (w == 0) {
-        double t = lane < NT / 32 ? buf[lane] : 0.0;
+        T t = lane < NT / 32 ? buf[lane] : T(0);
         t = warp_sum(t);
         if (lane == 0) buf[32] = t;
     }

@@ -155,7 +155,7 @@ __global__ void exx_reduce_kernel(const PairRec* __restrict__ pairs, const int* 
         const PairRec r = pairs[p];
         s += (r.i == r.j ? 1.0 : 2.0) * e_pair[p];
     }
-    s = block_sum<1024>(s, red, flip);
+    s = block_sum<1024, double>(s, red, flip);
     if (threadIdx.x == 0) out[0] = -s;
 }
 

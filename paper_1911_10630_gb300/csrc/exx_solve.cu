@@ -35,42 +35,35 @@ namespace exx {
 template <typename T, int NT>
 __device__ int cg_ball(T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d, T* __restrict__ ap,
                        const int* __restrict__ cube, int n_pe, int S, long long S2, const Stencil<T>& neg_st,
-                       double rr, double target2, int max_iter, double (*red)[33], int& flip, double& rr_out) {
+                       T rr, T target2, int max_iter, T (*red)[33], int& flip, T& rr_out) {
+    // Dot products, alpha and beta stay in T: in the FP32 solve no FP64
+    // instruction runs per iteration (FP64 is 1/64 of the FP32 rate here).
     int it = 0;
     while (rr > target2 && it < max_iter) {
-        double pap = 0.0;
-        {
-            T acc = T(0);
-            for (int k = threadIdx.x; k < n_pe; k += NT) {
-                const int c = cube[k];
-                const T a = lap19<T>(pc, c, S, S2, neg_st);
-                ap[k] = a;
-                acc = fma(pc[c], a, acc);
-            }
-            pap = (double)acc;
+        T pap = T(0);
+        for (int k = threadIdx.x; k < n_pe; k += NT) {
+            const int c = cube[k];
+            const T a = lap19<T>(pc, c, S, S2, neg_st);
+            ap[k] = a;
+            pap = fma(pc[c], a, pap);
         }
-        pap = block_sum<NT>(pap, red, flip);
-        const double alpha = rr / pap;
-        const T al = (T)alpha;
-        double rrn;
-        {
-            T acc = T(0);
-            for (int k = threadIdx.x; k < n_pe; k += NT) {
-                const int c = cube[k];
-                d[k] = fma(al, pc[c], d[k]);
-                const T rk = fma(-al, ap[k], r[k]);
-                r[k] = rk;
-                acc = fma(rk, rk, acc);
-            }
-            rrn = (double)acc;
+        pap = block_sum<NT, T>(pap, red, flip);
+        const T al = rr / pap;
+        T rrn = T(0);
+        for (int k = threadIdx.x; k < n_pe; k += NT) {
+            const int c = cube[k];
+            d[k] = fma(al, pc[c], d[k]);
+            const T rk = fma(-al, ap[k], r[k]);
+            r[k] = rk;
+            rrn = fma(rk, rk, rrn);
         }
-        rrn = block_sum<NT>(rrn, red, flip);
+        rrn = block_sum<NT, T>(rrn, red, flip);
         ++it;
         if (rrn <= target2 || !(rrn == rrn)) {
             rr = rrn;
             break;
         }
-        const T be = (T)(rrn / rr);
+        const T be = rrn / rr;
         rr = rrn;
         for (int k = threadIdx.x; k < n_pe; k += NT) {
             const int c = cube[k];
@@ -89,9 +82,10 @@ template <int NT, bool MIXED>
 __global__ void __launch_bounds__(NT, 1) pair_kernel(const SolveParams P) {
     extern __shared__ double smem[];
     __shared__ double red[2][33];
+    __shared__ float red32[2][33];
     __shared__ double s_M[kNMono], s_T[kNMono];
     __shared__ int s_item;
-    int flip = 0;
+    int flip = 0, flip32 = 0;
 
     const int Rc = P.Rc;
     const int S = P.S;
@@ -160,7 +154,7 @@ __global__ void __launch_bounds__(NT, 1) pair_kernel(const SolveParams P) {
                 acc = fma(b, b, acc);
                 if (P.dbg_b) P.dbg_b[k] = b;
             }
-            const double bb = block_sum<NT>(acc, red, flip);
+            const double bb = block_sum<NT, double>(acc, red, flip);
             double rr_fin;
             const double target2 = P.tol * P.tol * bb;
             iters = cg_ball<double, NT>(pc, r, d, ap, cube, n_pe, S, S2, neg64, bb, target2, P.max_iter, red, flip,
@@ -180,7 +174,7 @@ __global__ void __launch_bounds__(NT, 1) pair_kernel(const SolveParams P) {
                     acc = fma(rk, rk, acc);
                     if (bb < 0.0 && P.dbg_b) P.dbg_b[k] = rk;
                 }
-                const double rn2 = block_sum<NT>(acc, red, flip);
+                const double rn2 = block_sum<NT, double>(acc, red, flip);
                 if (bb < 0.0) bb = rn2;
                 if (rn2 <= P.tol * P.tol * bb) break;
                 const double rn = sqrt(rn2);
@@ -199,13 +193,13 @@ __global__ void __launch_bounds__(NT, 1) pair_kernel(const SolveParams P) {
                     d32[k] = 0.0f;
                     acc32 = fmaf(rk, rk, acc32);
                 }
-                const double rr32 = block_sum<NT>((double)acc32, red, flip);
+                const float rr32 = block_sum<NT, float>(acc32, red32, flip32);
                 double eta = 0.3 * P.tol * sqrt(bb) / rn;
                 eta = eta > P.inner_tol ? eta : P.inner_tol;
-                double rr_fin;
+                float rr_fin;
                 const int budget = min(P.inner_max_iter, P.max_iter - iters);
-                iters += cg_ball<float, NT>(p32, r32, d32, ap32, cube, n_pe, S, S2, neg32, rr32, eta * eta * rr32,
-                                            budget, red, flip, rr_fin);
+                iters += cg_ball<float, NT>(p32, r32, d32, ap32, cube, n_pe, S, S2, neg32, rr32,
+                                            (float)(eta * eta) * rr32, budget, red32, flip32, rr_fin);
                 for (int k = threadIdx.x; k < n_pe; k += NT) vc[cube[k]] = fma(rn, (double)d32[k], vc[cube[k]]);
                 ++refines;
                 __syncthreads();
@@ -216,7 +210,7 @@ __global__ void __launch_bounds__(NT, 1) pair_kernel(const SolveParams P) {
         // 6. E_ij over the PE ball and the D_xx scatter over the ME ball
         double e = 0.0;
         for (int k = threadIdx.x; k < n_pe; k += NT) e = fma(rho[k], vc[cube[k]], e);
-        e = block_sum<NT>(e, red, flip);
+        e = block_sum<NT, double>(e, red, flip);
         if (threadIdx.x == 0) {
             P.e_pair[pidx] = e * P.dV;
             P.iters[pidx] = iters;
