@@ -195,6 +195,32 @@ exx_status exx_ball_size(const exx_ctx *ctx, int *n_pe, int *n_me);
  */
 exx_status exx_load_guess_model(exx_ctx *ctx, const void *weights, size_t bytes);
 
+/*
+ * Pair list without device allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, for example code
+ * running during CUDA-graph stream capture, or hosts confined to a fixed
+ * device-memory budget or their own pool. It computes the same pair list as
+ * exx_compute (Sec. III.C Step II rule, same rounding and order). Its scratch
+ * (per-orbital counts and prefix sums) lives in a static device array sized
+ * for 16384 orbitals; every GPU that loads the library holds that array
+ * (about 128 KiB) until the process exits.
+ *   centers   device, [n][3] FP64 orbital centres (bohr)
+ *   n         1 <= n <= 16384, else EXX_EINVAL
+ *   cell, grid, r_pair  as for exx_init
+ *   pairs     device, [cap][5] int: i, j (i <= j) and the grid point nearest
+ *             the pair centre (3 ints, in [0, N)), in list order
+ *   cap       capacity of pairs in records
+ *   n_pair    host, receives the number of pairs; if it exceeds cap only the
+ *             first cap records are written and EXX_EINVAL is returned
+ *   stream    cudaStream_t, NULL = legacy default stream; the call waits for it
+ * The first call on a device looks up the array's device address (once per
+ * device), so make that call before any stream capture. All calls share the
+ * one array: calls that overlap on the GPU race and must be serialised.
+ * Allocates nothing. Errors are read with exx_last_error(NULL).
+ */
+exx_status exx_pair_list_static(const double *centers, int n, const double cell[3], const int grid[3],
+                                double r_pair, int *pairs, int cap, int *n_pair, void *stream);
+
 /* Message of the last error on this context (or of the last failed exx_init
  * when ctx is NULL); owned by the library, valid until the next call. */
 const char *exx_last_error(const exx_ctx *ctx);

@@ -69,6 +69,8 @@ SIGNATURES = [
     ("exx_apply_operator", ctypes.c_int, [_ctx_p, _vp, _vp, _vp]),
     ("exx_ball_size", ctypes.c_int, [_ctx_p, _i, _i]),
     ("exx_load_guess_model", ctypes.c_int, [_ctx_p, _vp, ctypes.c_size_t]),
+    ("exx_pair_list_static", ctypes.c_int, [_vp, ctypes.c_int, _d, _i, ctypes.c_double, _vp, ctypes.c_int, _i,
+                                            _vp]),
     ("exx_last_error", ctypes.c_char_p, [_ctx_p]),
     ("exx_destroy", None, [_ctx_p]),
 ]
