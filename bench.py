@@ -216,6 +216,8 @@ def main():
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--solver-kind", type=int, default=0, help="0 auto, 1 one CTA per pair, 2 cluster per pair")
     ap.add_argument("--cluster-size", type=int, default=0)
+    ap.add_argument("--lane-map", type=int, default=0)
+    ap.add_argument("--update-drop", type=float, default=1e-3)
     ap.add_argument("--orbitals", type=int, default=0,
                     help="keep only the first N orbitals of the workload (small cases for profiling)")
     args = ap.parse_args()
@@ -249,7 +251,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
     ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=args.precision,
              threads=args.threads, ctas_per_sm=args.ctas_per_sm, solver_kind=args.solver_kind,
-             cluster_size=args.cluster_size)
+             cluster_size=args.cluster_size, lane_map=args.lane_map, update_drop=args.update_drop)
 
     def barrier():
         if ws > 1:
@@ -362,7 +364,9 @@ def main():
             "clocks": clk.summary(),
             "E_xx": exx_vals[-1],
             "cg": {"iters_p50": st["iters_p50"], "iters_p99": st["iters_p99"], "iters_max": st["iters_max"],
-                   "refine_max": st["refine_max"], "point_iters": st["point_iters"], "n_nonconv": st["n_nonconv"]},
+                   "refine_max": st["refine_max"], "point_iters": st["point_iters"], "n_nonconv": st["n_nonconv"],
+                   "phase_ms_per_cluster": {"setup": st["phase_ms"][0], "fp64_residuals": st["phase_ms"][1],
+                                            "fp32_cg": st["phase_ms"][2], "finish": st["phase_ms"][3]}},
         }
         line.update(extra)
         print(json.dumps(line), flush=True)

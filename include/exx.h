@@ -74,6 +74,12 @@ typedef struct {
                           global memory; 2 = one thread-block cluster per pair
                           with the FP32 inner state in shared memory.            */
     int cluster_size;  /* CTAs per cluster for solver_kind 2 (0 = library choice) */
+    double update_drop;/* cluster solver: the FP64 residual replaces the FP32 one
+                          each time the FP32 residual has dropped by this factor
+                          (reliable updates; default 1e-3).                      */
+    int lane_map;      /* cluster solver thread-to-point map: 0 = natural order
+                          (contiguous warps, default), 1 = bank-distinct lanes
+                          dealt plane by plane.                                  */
 } exx_options;
 
 typedef struct {
@@ -92,6 +98,10 @@ typedef struct {
     int cluster_size;      /* CTAs per pair                                        */
     int grid_ctas;         /* CTAs launched for the pair kernel                    */
     int threads;           /* threads per CTA                                      */
+    double phase_ms[4];    /* cluster solver: the pair-kernel time split by the
+                              clusters' cycle counts into setup (gather,
+                              multipoles, shell), FP64 residuals, FP32 CG
+                              iterations and finish (E_ij, scatter)               */
 } exx_stats;
 
 /* Defaults described in exx_options. */

@@ -35,6 +35,7 @@ cudaError_t cluster_prepare(int variant, size_t smem, int* max_clusters);
 cudaError_t launch_cluster_kernel(int variant, const SolveParams& P, const ClusterLayout& CL, int n_clusters,
                                   size_t smem, cudaStream_t st);
 int cluster_variant_threads(int variant);
+int cluster_variant_pts(int variant);
 }  // namespace exx
 
 using namespace exx;
@@ -76,7 +77,10 @@ struct exx_ctx {
     ClusterLayout CL;
     int* d_pt_slab = nullptr;
     int4* d_rank_info = nullptr;
+    int* d_slot = nullptr;  // slot_pk then slot_k
     double* d_pow = nullptr;
+    unsigned long long* d_phase = nullptr;  // [4] phase cycles of the cluster solver
+    int clock_khz = 0;
 
     // pair buffers
     int cap_n = 0;
@@ -159,6 +163,8 @@ extern "C" exx_options exx_default_options(void) {
     o.ctas_per_sm = 0;
     o.solver_kind = 0;
     o.cluster_size = 0;
+    o.update_drop = 1e-3;
+    o.lane_map = 0;
     return o;
 }
 
@@ -200,7 +206,9 @@ extern "C" void exx_destroy(exx_ctx* c) {
     cudaFree(c->d_alpha);
     cudaFree(c->d_pt_slab);
     cudaFree(c->d_rank_info);
+    cudaFree(c->d_slot);
     cudaFree(c->d_pow);
+    cudaFree(c->d_phase);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -234,6 +242,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (o.max_iter <= 0) o.max_iter = 20000;
     if (o.inner_max_iter <= 0) o.inner_max_iter = 4000;
     if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) o.inner_tol = 1e-5;
+    if (!(o.update_drop > 0.0 && o.update_drop < 1.0)) o.update_drop = 1e-3;
     if (o.threads != 0 && o.threads != 256 && o.threads != 512 && o.threads != 1024)
         return fail(nullptr, EXX_EINVAL, "exx_init: threads must be 0, 256, 512 or 1024");
     if (o.solver_kind < 0 || o.solver_kind > 2) return fail(nullptr, EXX_EINVAL, "exx_init: solver_kind must be 0, 1 or 2");
@@ -383,6 +392,16 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             if (e == cudaSuccess) e = cudaMemcpy(c->d_rank_info, ri, sizeof(int4) * C, cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return bail(cuda_fail(c, e, "slab rank table"));
             L.rank_info = c->d_rank_info;
+            std::vector<int> spk, sk;
+            if (build_slot_maps(L, pt, cluster_variant_threads(v), cluster_variant_pts(v), o.lane_map, spk, sk) < 0)
+                return bail(fail(c, EXX_ECUDA, "exx_init: slot map does not fit"));
+            e = cudaMalloc(&c->d_slot, sizeof(int) * (spk.size() + sk.size()));
+            if (e == cudaSuccess) e = cudaMemcpy(c->d_slot, spk.data(), sizeof(int) * spk.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(c->d_slot + spk.size(), sk.data(), sizeof(int) * sk.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return bail(cuda_fail(c, e, "slot maps"));
+            L.slot_pk = c->d_slot;
+            L.slot_k = c->d_slot + spk.size();
             c->CL = L;
             c->cl_variant = v;
             c->n_clusters = nclu;
@@ -417,6 +436,9 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     e = cudaMemset(c->ws, 0, c->slot_bytes * (size_t)c->n_slots);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemset(workspace)"));
 
+    cudaDeviceGetAttribute(&c->clock_khz, cudaDevAttrClockRate, c->device);
+    e = cudaMalloc(&c->d_phase, sizeof(unsigned long long) * 4);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(phase clocks)"));
     e = cudaMalloc(&c->d_scalars, sizeof(int) * 8);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(scalars)"));
     e = cudaMalloc(&c->d_exx, sizeof(double) * 2);
@@ -466,6 +488,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     P.inner_max_iter = o.inner_max_iter;
     P.inner_tol = o.inner_tol;
     P.max_refine = 40;
+    P.update_drop = o.update_drop;
     P.lmax = l_max;
     P.n_mono = (l_max + 1) * (l_max + 2) * (l_max + 3) / 6;
     P.n_pair = c->d_scalars;
@@ -513,9 +536,11 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
     P.iters = c->d_iters;
     P.refines = c->d_refines;
     P.dbg_b = nullptr;
+    P.phase_clk = c->use_cluster ? c->d_phase : nullptr;
     CK(cudaEventRecordWithFlags(c->ev[0], st, evf), "cudaEventRecord");
     CK(launch_zero(d_xx, (long long)n * c->ngrid, c->num_sms, st), "zero D_xx");
     CK(cudaMemsetAsync(c->d_scalars + 2, 0, sizeof(int), st), "reset counters");
+    CK(cudaMemsetAsync(c->d_phase, 0, sizeof(unsigned long long) * 4, st), "reset phase clocks");
     CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
                         c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st),
        "pair list");
@@ -666,6 +691,12 @@ extern "C" exx_status exx_get_stats(const exx_ctx* cc, exx_stats* out) {
         c->stats.iters_p50 = srt[(np - 1) / 2];
         c->stats.iters_p99 = srt[std::min(np - 1, (int)std::ceil(0.99 * np) - 1)];
         c->stats.refine_max = rmax;
+        unsigned long long ph[4] = {0, 0, 0, 0};
+        CK(cudaMemcpy(ph, c->d_phase, sizeof(ph), cudaMemcpyDeviceToHost), "read phase clocks");
+        // shares of the pair-kernel time (the clusters run side by side)
+        const double cyc = (double)ph[0] + (double)ph[1] + (double)ph[2] + (double)ph[3];
+        for (int k = 0; k < 4; ++k)
+            c->stats.phase_ms[k] = (c->use_cluster && cyc > 0.0) ? c->stats.solve_ms * (double)ph[k] / cyc : 0.0;
     }
     *out = c->stats;
     if (out->iters_max < 0) out->iters_max = 0;

@@ -58,11 +58,13 @@ __device__ __noinline__ double cta_residual(const SolveParams& P, const int* __r
     return acc;
 }
 
-// v += scale * d on the CTA's points (d in shared memory, [j][NT] layout).
+// v += scale * d on the CTA's points (d in shared memory, [j][NT] slots).
 __device__ __noinline__ void cta_update_v(const int* __restrict__ cube, double* __restrict__ vc,
-                                          const float* __restrict__ ds, double scale, int k0, int k1, int nt) {
-    int j = 0;
-    for (int k = k0 + (int)threadIdx.x; k < k1; k += nt, ++j) {
+                                          const float* __restrict__ ds, const int* __restrict__ slot_k, double scale,
+                                          int pts, int nt) {
+    for (int j = 0; j < pts; ++j) {
+        const int k = slot_k[j * nt + threadIdx.x];
+        if (k < 0) continue;
         const int c = cube[k];
         vc[c] = fma(scale, (double)ds[j * nt + threadIdx.x], vc[c]);
     }
@@ -109,11 +111,9 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
     const int planes = me.y;
     const int planes_prev = rank > 0 ? CL.rank_info[rank - 1].y : 0;
     const int k0 = me.z, k1 = me.w;
+    const int* slot_k = CL.slot_k + (size_t)rank * PTS * NT;
 #pragma unroll
-    for (int j = 0; j < PTS; ++j) {
-        const int k = k0 + (int)threadIdx.x + j * NT;
-        spk[j * NT + threadIdx.x] = k < k1 ? CL.pt_slab[k] : -1;
-    }
+    for (int j = 0; j < PTS; ++j) spk[j * NT + threadIdx.x] = CL.slot_pk[(size_t)rank * PTS * NT + j * NT + threadIdx.x];
 
     const int cid = blockIdx.x / C;
     char* slot = P.ws + (size_t)cid * P.slot_bytes;
@@ -141,6 +141,9 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
         const BallGeo G = P.geos[pr.geo];
         const int* cube = G.pt_cube;
 
+        const bool clk = P.phase_clk && rank == 0 && threadIdx.x == 0;
+        long long t0 = clk ? clock64() : 0, tr = 0;
+
         // gather, multipoles, shell potential (FP64, spread over the cluster)
         gather_rho(P, G, pr, rho, vc, gt, gn);
         cl.sync();
@@ -149,45 +152,48 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
         moment_finish<NT>(P, G, rowS, xp, yp, sY, s_M, s_T);
         shell_potential(P, G, vc, xp, yp, s_T, gt, gn);
         cl.sync();
+        const long long t1 = clk ? clock64() : 0;
 
-        // FP64 refinement around FP32 inner CG
-        double bb = -1.0, rn_prev = 1e300;
-        int iters = 0, refines = 0;
+        // CG in FP32 with reliable updates: the FP32 recursive residual is
+        // replaced by the FP64 residual 4 pi rho + lap v whenever it has
+        // dropped by update_drop (or looks converged); the search direction is
+        // kept, rescaled to the new residual norm, so the Krylov progress
+        // survives each replacement. The stop test is the FP64 residual.
+        double acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, P.dbg_b != nullptr);
+        const double bb = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
+        const double target2 = P.tol * P.tol * bb;
+        if (clk) tr += clock64() - t1;
+        int iters = 0, refines = 1;
         bool conv = true;
-        for (;;) {
-            const double acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, bb < 0.0 && P.dbg_b);
-            const double rn2 = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
-            if (bb < 0.0) bb = rn2;
-            if (rn2 <= P.tol * P.tol * bb) break;
-            const double rn = sqrt(rn2);
-            if (refines >= P.max_refine || iters >= P.max_iter || !(rn < rn_prev)) {
-                conv = false;
-                break;
-            }
-            rn_prev = rn;
-            const double inv = 1.0 / rn;
+        if (bb > target2 && bb == bb) {
+            double scale = sqrt(bb);
             float r[PTS], ap[PTS];
             float a32 = 0.0f;
+            {
+                const double inv = 1.0 / scale;
 #pragma unroll
-            for (int j = 0; j < PTS; ++j) {
-                r[j] = 0.0f;
-                ap[j] = 0.0f;
-                ds[j * NT + threadIdx.x] = 0.0f;
-                const int pkj = spk[j * NT + threadIdx.x];
-                if (pkj >= 0) {
-                    const int k = k0 + (int)threadIdx.x + j * NT;
-                    r[j] = (float)(r64[k] * inv);
-                    ps[pkj & 0xffffff] = r[j];
-                    a32 = fmaf(r[j], r[j], a32);
+                for (int j = 0; j < PTS; ++j) {
+                    r[j] = 0.0f;
+                    ap[j] = 0.0f;
+                    ds[j * NT + threadIdx.x] = 0.0f;
+                    const int pkj = spk[j * NT + threadIdx.x];
+                    if (pkj >= 0) {
+                        const int k = slot_k[j * NT + threadIdx.x];
+                        r[j] = (float)(r64[k] * inv);
+                        ps[pkj & 0xffffff] = r[j];
+                        a32 = fmaf(r[j], r[j], a32);
+                    }
                 }
             }
             float rr = cluster_sum<NT, C, float>(a32, red32, flip32, part32, cflip32, cl, rank);
-            double eta = 0.3 * P.tol * sqrt(bb) / rn;
-            eta = eta > P.inner_tol ? eta : P.inner_tol;
-            const float target2 = (float)(eta * eta) * rr;
-            const int budget = min(P.inner_max_iter, P.max_iter - iters);
-            int it = 0;
-            while (rr > target2 && it < budget) {
+            float maxrr = rr;
+            const float drop2 = (float)(P.update_drop * P.update_drop);
+            float conv_thr = (float)(0.25 * target2 / (scale * scale));
+            for (;;) {
+                if (iters >= P.max_iter) {
+                    conv = false;
+                    break;
+                }
                 float pa = 0.0f;
 #pragma unroll
                 for (int j = 0; j < PTS; ++j) {
@@ -224,10 +230,43 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
                     }
                 }
                 const float rrn = cluster_sum<NT, C, float>(ra, red32, flip32, part32, cflip32, cl, rank);
-                ++it;
-                if (rrn <= target2 || !(rrn == rrn)) {
-                    rr = rrn;
-                    break;
+                ++iters;
+                // recursive residual dropped enough, or (in absolute terms) below tol ||b|| / 2
+                const bool update = rrn <= drop2 * maxrr || rrn <= conv_thr || !(rrn == rrn);
+                if (update) {
+                    const long long tu = clk ? clock64() : 0;
+                    cta_update_v(cube, vc, ds, slot_k, scale, PTS, NT);  // v += scale d
+                    cl.sync();
+                    acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, false);
+                    const double rn2 = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
+                    ++refines;
+                    if (clk) tr += clock64() - tu;
+                    if (rn2 <= target2) break;
+                    if (refines > P.max_refine || !(rn2 < scale * scale)) {
+                        conv = false;
+                        break;
+                    }
+                    const double ns = sqrt(rn2);
+                    const float carry = (float)(ns / scale) / rr;  // beta of the new residual, in the new units
+                    const double inv = 1.0 / ns;
+                    a32 = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < PTS; ++j) {
+                        const int pkj = spk[j * NT + threadIdx.x];
+                        if (pkj >= 0) {
+                            const int k = slot_k[j * NT + threadIdx.x];
+                            r[j] = (float)(r64[k] * inv);
+                            ds[j * NT + threadIdx.x] = 0.0f;
+                            const int off = pkj & 0xffffff;
+                            ps[off] = fmaf(carry, ps[off], r[j]);
+                            a32 = fmaf(r[j], r[j], a32);
+                        }
+                    }
+                    rr = cluster_sum<NT, C, float>(a32, red32, flip32, part32, cflip32, cl, rank);
+                    maxrr = rr;
+                    scale = ns;
+                    conv_thr = (float)(0.25 * target2 / (scale * scale));
+                    continue;
                 }
                 const float be = rrn / rr;
                 rr = rrn;
@@ -241,11 +280,8 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
                 }
                 cl.sync();
             }
-            iters += it;
-            cta_update_v(cube, vc, ds, rn, k0, k1, NT);
-            ++refines;
-            cl.sync();
         }
+        const long long t2 = clk ? clock64() : 0;
 
         // E_ij and the scatter
         double e = cta_energy(cube, rho, vc, k0, k1, NT);
@@ -258,6 +294,13 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
         }
         scatter_dxx(P, G, pr, vc, gt, gn);
         cl.sync();
+        if (clk) {
+            const long long t3 = clock64();
+            atomicAdd(P.phase_clk + 0, (unsigned long long)(t1 - t0));
+            atomicAdd(P.phase_clk + 1, (unsigned long long)tr);
+            atomicAdd(P.phase_clk + 2, (unsigned long long)(t2 - t1 - tr));
+            atomicAdd(P.phase_clk + 3, (unsigned long long)(t3 - t2));
+        }
     }
 }
 
@@ -315,7 +358,11 @@ int cluster_variant(int C, int max_pts, int threads) {
         const ClusterVariant& K = kVariants[v];
         if (K.c != C || K.nt * K.pts < max_pts) continue;
         if (threads && K.nt != threads) continue;
-        if (best < 0 || K.nt * K.pts < kVariants[best].nt * kVariants[best].pts) best = v;
+        // prefer more threads (more warps to hide shared-memory and barrier
+        // latency), then the smallest per-thread point capacity
+        if (best < 0 || K.nt > kVariants[best].nt ||
+            (K.nt == kVariants[best].nt && K.pts < kVariants[best].pts))
+            best = v;
     }
     return best;
 }
@@ -344,6 +391,7 @@ cudaError_t launch_cluster_kernel(int variant, const SolveParams& P, const Clust
 }
 
 int cluster_variant_threads(int variant) { return kVariants[variant].nt; }
+int cluster_variant_pts(int variant) { return kVariants[variant].pts; }
 
 size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant) {
     (void)Rc;

@@ -199,4 +199,82 @@ bool build_cluster_layout(const HostBall& B, int C, ClusterLayout& L, std::vecto
     return true;
 }
 
+int build_slot_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int NT, int PTS, int bank_aware,
+                    std::vector<int>& slot_pk, std::vector<int>& slot_k) {
+    const int per = NT * PTS, warps_per_j = NT / 32, n_ws = PTS * warps_per_j;
+    slot_pk.assign((size_t)L.C * per, -1);
+    slot_k.assign((size_t)L.C * per, -1);
+    if (!bank_aware) {
+        for (int r = 0; r < L.C; ++r) {
+            if (L.k1[r] - L.k0[r] > per) return -1;
+            for (int k = L.k0[r]; k < L.k1[r]; ++k) {
+                const int s = k - L.k0[r];
+                slot_pk[(size_t)r * per + s] = pt_slab[k];
+                slot_k[(size_t)r * per + s] = k;
+            }
+        }
+        return 0;
+    }
+    int conflicted = 0;
+    for (int r = 0; r < L.C; ++r) {
+        int ws = 0;  // next warp slot: j = ws / warps_per_j, warp = ws % warps_per_j
+        auto place = [&](int slot_ws, int lane, int k) {
+            const int j = slot_ws / warps_per_j, t = (slot_ws % warps_per_j) * 32 + lane;
+            slot_pk[(size_t)r * per + (size_t)j * NT + t] = pt_slab[k];
+            slot_k[(size_t)r * per + (size_t)j * NT + t] = k;
+        };
+        // 1) plane by plane: whole warps of one plane, one point per bank, so the
+        //    lanes of a warp agree on which x legs leave the slab
+        std::vector<int> pool;
+        int k = L.k0[r];
+        while (k < L.k1[r]) {
+            const int xl = pt_slab[k] >> 24;
+            std::vector<std::vector<int>> bucket(32);
+            while (k < L.k1[r] && (pt_slab[k] >> 24) == xl) {
+                bucket[(pt_slab[k] & 0xffffff) & 31].push_back(k);
+                ++k;
+            }
+            std::vector<size_t> head(32, 0);
+            for (;;) {
+                bool full = true;
+                for (int b = 0; b < 32; ++b) full = full && head[b] < bucket[b].size();
+                if (!full || ws >= n_ws) break;
+                for (int b = 0; b < 32; ++b) place(ws, b, bucket[b][head[b]++]);
+                ++ws;
+            }
+            for (int b = 0; b < 32; ++b)
+                for (size_t h = head[b]; h < bucket[b].size(); ++h) pool.push_back(bucket[b][h]);
+        }
+        // 2) the per-plane remainders: distinct banks within a warp where possible
+        std::vector<std::vector<int>> bucket(32);
+        for (int q : pool) bucket[(pt_slab[q] & 0xffffff) & 31].push_back(q);
+        std::vector<size_t> head(32, 0);
+        size_t left = pool.size();
+        while (left > 0 && ws < n_ws) {
+            int lane = 0;
+            for (int b = 0; b < 32 && left > 0; ++b)
+                if (head[b] < bucket[b].size()) {
+                    place(ws, lane++, bucket[b][head[b]++]);
+                    --left;
+                }
+            ++ws;
+        }
+        // 3) anything still left shares banks in free slots
+        for (int s2 = 0; s2 < n_ws && left > 0; ++s2)
+            for (int lane = 0; lane < 32 && left > 0; ++lane) {
+                const int j = s2 / warps_per_j, t = (s2 % warps_per_j) * 32 + lane;
+                if (slot_k[(size_t)r * per + (size_t)j * NT + t] >= 0) continue;
+                for (int b = 0; b < 32; ++b)
+                    if (head[b] < bucket[b].size()) {
+                        place(s2, lane, bucket[b][head[b]++]);
+                        --left;
+                        ++conflicted;
+                        break;
+                    }
+            }
+        if (left > 0) return -1;
+    }
+    return conflicted;
+}
+
 }  // namespace exx

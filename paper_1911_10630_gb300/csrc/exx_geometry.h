@@ -24,4 +24,17 @@ void build_multipole_const(MultipoleConst& mc);
 bool build_cluster_layout(const HostBall& B, int C, ClusterLayout& L, std::vector<int>& pt_slab);
 void build_ball(HostBall& B, int r_pe, int r_me, int Rc);
 
+// Thread-slot maps of the cluster solver for NT threads x PTS points per CTA:
+// slot (j, t) of CTA r holds one point of the CTA's slab. Points are dealt so
+// that the 32 lanes of every warp read 32 different shared-memory banks
+// (distinct slab offsets mod 32); every stencil leg shifts all lanes by the
+// same amount, so the whole stencil is conflict-free. slot_pk gets the packed
+// slab offset (or -1), slot_k the compact PE index (or -1), [C][PTS][NT].
+// Returns the number of warps in which two lanes share a bank.
+// bank_aware = 0 keeps the natural order (slot (j, t) = point k0 + t + j NT),
+// whose warps read contiguous addresses (coalesced remote loads, at most a
+// two-row bank conflict).
+int build_slot_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int NT, int PTS, int bank_aware,
+                    std::vector<int>& slot_pk, std::vector<int>& slot_k);
+
 }  // namespace exx

@@ -92,6 +92,8 @@ struct SolveParams {
     int inner_max_iter;
     double inner_tol;
     int max_refine;
+    double update_drop;       // reliable-update trigger of the cluster solver
+    unsigned long long* phase_clk;  // [4] cycles: setup, FP64 residuals, FP32 CG, finish (cluster solver)
     int lmax;
     int n_mono;
     int warm_start;       // 1: take x0 from the cache when valid
@@ -121,6 +123,8 @@ struct ClusterLayout {
     int x0[kMaxCluster], planes[kMaxCluster], k0[kMaxCluster], k1[kMaxCluster];  // host copy
     const int* pt_slab;  // [n_pe] slab offset | (plane within slab) << 24
     const int4* rank_info;  // device [C]: x0, planes, k0, k1 (read by the kernel)
+    const int* slot_pk;     // device [C][PTS][NT]: packed slab offset of each thread slot, or -1
+    const int* slot_k;      // device [C][PTS][NT]: compact PE index of each thread slot, or -1
 };
 
 // Host-built constants of the Cartesian form of the multipole expansion.
