@@ -48,12 +48,16 @@ __device__ __forceinline__ T cluster_sum(T v, T (*red)[33], int& flip, T (*part)
 __device__ __noinline__ double cta_residual(const SolveParams& P, const int* __restrict__ cube,
                                             const double* __restrict__ rho, const double* __restrict__ vc,
                                             double* __restrict__ r64, int k0, int k1, int nt, bool dbg) {
+    const Stencil<double> st = P.st64;  // into registers (see gather_rho)
+    const int S = P.S;
+    const long long S2 = P.S2;
+    double* __restrict__ db = P.dbg_b;
     double acc = 0.0;
     for (int k = k0 + (int)threadIdx.x; k < k1; k += nt) {
-        const double rk = fma(kFourPi, rho[k], lap19<double>(vc, cube[k], P.S, P.S2, P.st64));
+        const double rk = fma(kFourPi, rho[k], lap19<double>(vc, cube[k], S, S2, st));
         r64[k] = rk;
         acc = fma(rk, rk, acc);
-        if (dbg) P.dbg_b[k] = rk;
+        if (dbg) db[k] = rk;
     }
     return acc;
 }
@@ -98,8 +102,10 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
     const double* zp = yp + (2 * Rc + 1) * 8;
     // shared memory: the p slab, then the CG correction d and the point map, [PTS][NT] each
     float* ps = reinterpret_cast<float*>(smem);
-    float* ds = ps + CL.cap_planes * CL.Sp2;
+    float* ds = ps + ((CL.cap_planes * CL.Sp2 + 3) & ~3);  // 16-byte aligned
     int* spk = reinterpret_cast<int*>(ds + PTS * NT);
+    // the shell phase's per-warp coefficient buffers reuse ds (idle outside the CG)
+    double* ub = reinterpret_cast<double*>(ds) + (threadIdx.x >> 5) * (kNU + kNU / 2);
     const int Syz = CL.Syz;
     const int Sp2 = CL.Sp2;
 
@@ -150,7 +156,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
         moment_rows(P, G, rho, rowS, zp, gt, gn);
         cl.sync();
         moment_finish<NT>(P, G, rowS, xp, yp, sY, s_M, s_T);
-        shell_potential(P, G, vc, xp, yp, s_T, gt, gn);
+        shell_potential(P, G, vc, xp, yp, s_T, ub, gt >> 5, gn >> 5);
         cl.sync();
         const long long t1 = clk ? clock64() : 0;
 
@@ -396,7 +402,7 @@ int cluster_variant_pts(int variant) { return kVariants[variant].pts; }
 size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant) {
     (void)Rc;
     const size_t per = (size_t)kVariants[variant].nt * kVariants[variant].pts;
-    return sizeof(float) * ((size_t)CL.cap_planes * CL.Sp2 + per) + sizeof(int) * per;
+    return sizeof(float) * ((((size_t)CL.cap_planes * CL.Sp2 + 3) & ~(size_t)3) + per) + sizeof(int) * per;
 }
 
 }  // namespace exx

@@ -45,6 +45,19 @@ void build_multipole_const(MultipoleConst& mc) {
             }
     }
     mc.mono_off[kLmaxMax + 1] = m;
+    for (int l = 0; l <= kLmaxMax; ++l)
+        for (int c = 0; c <= l; ++c) {
+            const int u = l * (l + 1) / 2 + c;
+            int n = 0;
+            for (int a = l - c; a >= 0; --a) {
+                const int b = l - c - a;
+                mc.uterm[u][n][0] = (unsigned char)(mc.mono_off[l] + idx[a][b][c]);
+                mc.uterm[u][n][1] = (unsigned char)a;
+                mc.uterm[u][n][2] = (unsigned char)b;
+                ++n;
+            }
+            mc.uterm_n[u] = (unsigned char)n;
+        }
     int koff = 0;
     for (int l = 0; l <= kLmaxMax; ++l) {
         const int nl = (l + 1) * (l + 2) / 2;
@@ -112,7 +125,7 @@ void build_ball(HostBall& B, int r_pe, int r_me, int Rc) {
             R.zpe = (short)zpe;
             R.zme = (short)isqrt_floor(rme2 - s2);
             R.pe_start = (int)B.cube.size();
-            R.sh_start = -1;
+            R.zn = -1;
             B.rows_pe.push_back(R);
             for (int z = -zpe; z <= zpe; ++z) {
                 B.cube.push_back(cube(x, y, z));
@@ -134,7 +147,18 @@ void build_ball(HostBall& B, int r_pe, int r_me, int Rc) {
             R.zme = (short)isqrt_floor(rme2 - s2);
             R.zpe = (short)(s2 <= rpe2 ? isqrt_floor(rpe2 - s2) : -1);
             R.pe_start = R.zpe >= 0 ? B.rows_pe[pe_row++].pe_start : -1;
-            R.sh_start = (int)B.cube.size();
+            // boundary layer: shell points (x, y, z) with a PE point within three
+            // steps along an axis: |z| <= zpe + 3 of the row itself, or |z| <= zpe
+            // of a row (x +- q, y) or (x, y +- q), q <= 3
+            int zn = R.zpe >= 0 ? R.zpe + 3 : -1;
+            for (int q = 1; q <= 3; ++q) {
+                const int nb[4][2] = {{x + q, y}, {x - q, y}, {x, y + q}, {x, y - q}};
+                for (int t = 0; t < 4; ++t) {
+                    const long n2 = (long)nb[t][0] * nb[t][0] + (long)nb[t][1] * nb[t][1];
+                    if (n2 <= rpe2) zn = std::max(zn, isqrt_floor(rpe2 - n2));
+                }
+            }
+            R.zn = zn;
             B.rows_me.push_back(R);
             for (int z = -R.zme; z <= R.zme; ++z) {
                 if (z >= -R.zpe && z <= R.zpe) continue;

@@ -27,7 +27,7 @@ struct RowRec {
     short ox, oy;
     short zpe, zme;
     int pe_start;   // compact PE index of (ox, oy, -zpe), or -1
-    int sh_start;   // compact ME index of the first shell point of the row
+    int zn;         // shell points with |z| <= zn are read by stencil legs of PE points (-1: none)
 };
 
 // Device tables of one ball geometry (R_PE, R_ME); points in Algorithm 2
@@ -133,6 +133,10 @@ struct MultipoleConst {
     int k_off[8];          // offset of block l in K
     int mono_off[8];       // first monomial of degree l
     unsigned char mono[kNMono][3];  // (a, b, c) of each monomial
+    // U_{l,c} = sum over a + b = l - c of T_abc x^a y^b: for u = l(l+1)/2 + c,
+    // the terms (monomial m, a, b) and their count
+    unsigned char uterm[kNU][kLmaxMax + 1][3];
+    unsigned char uterm_n[kNU];
 };
 
 }  // namespace exx

@@ -33,36 +33,39 @@ __device__ __forceinline__ void fill_power_tables(const SolveParams& P, double* 
 }
 
 // Step III: rho = phi_i phi_j on the PE ball (Eq. l2g indices); v = 0 there.
+// Parameters are copied into registers first: P and G live in local memory,
+// and stores through generic pointers would otherwise force their reload.
 static __device__ __noinline__ void gather_rho(const SolveParams& P, const BallGeo& G, const PairRec& pr,
-                                           double* __restrict__ rho, double* __restrict__ vc, int tid, int nthr) {
-    const double* phi_i = P.phi + (long long)pr.i * P.ngrid;
-    const double* phi_j = P.phi + (long long)pr.j * P.ngrid;
-    for (int k = tid; k < G.n_pe; k += nthr) {
-        const long long g = grid_index(P.N, pr.g, G.pt_off[k]);
-        rho[k] = phi_i[g] * phi_j[g];
-        vc[G.pt_cube[k]] = 0.0;
+                                               double* __restrict__ rho, double* __restrict__ vc, int tid, int nthr) {
+    const double* __restrict__ phi_i = P.phi + (long long)pr.i * P.ngrid;
+    const double* __restrict__ phi_j = P.phi + (long long)pr.j * P.ngrid;
+    const int N[3] = {P.N[0], P.N[1], P.N[2]};
+    const int g[3] = {pr.g[0], pr.g[1], pr.g[2]};
+    const int n_pe = G.n_pe;
+    const int* __restrict__ off = G.pt_off;
+    const int* __restrict__ cube = G.pt_cube;
+    for (int k = tid; k < n_pe; k += nthr) {
+        const long long gi = grid_index(N, g, off[k]);
+        rho[k] = phi_i[gi] * phi_j[gi];
+        vc[cube[k]] = 0.0;
     }
 }
 
-// Eq. mepole, stage 1: row sums S_c(x, y) = sum_z z^c rho(x, y, z), c <= 6.
-static __device__ __noinline__ void moment_rows(const SolveParams& P, const BallGeo& G, const double* __restrict__ rho,
-                                            double* __restrict__ rowS, const double* __restrict__ zp, int tid,
-                                            int nthr) {
+// Eq. mepole, stage 1: row sums S_c(x, y) = sum_z z^c rho(x, y, z), c <= 6,
+// one thread per (row, c).
+static __device__ __noinline__ void moment_rows(const SolveParams& P, const BallGeo& G,
+                                                const double* __restrict__ rho, double* __restrict__ rowS,
+                                                const double* __restrict__ zp, int tid, int nthr) {
     const int Rc = P.Rc;
-    for (int row = tid; row < G.n_rows_pe; row += nthr) {
-        const RowRec R = G.rows_pe[row];
-        double s[kLmaxMax + 1];
-#pragma unroll
-        for (int c = 0; c <= kLmaxMax; ++c) s[c] = 0.0;
-        const double* rr = rho + R.pe_start;
-        for (int z = -R.zpe; z <= R.zpe; ++z) {
-            const double v = rr[z + R.zpe];
-            const double* zz = zp + (z + Rc) * 8;
-#pragma unroll
-            for (int c = 0; c <= kLmaxMax; ++c) s[c] = fma(v, zz[c], s[c]);
-        }
-#pragma unroll
-        for (int c = 0; c <= kLmaxMax; ++c) rowS[row * 8 + c] = s[c];
+    const int items = G.n_rows_pe * (kLmaxMax + 1);
+    const RowRec* __restrict__ rows = G.rows_pe;
+    for (int it = tid; it < items; it += nthr) {
+        const int row = it / (kLmaxMax + 1), c = it - row * (kLmaxMax + 1);
+        const RowRec R = rows[row];
+        const double* rr = rho + R.pe_start + R.zpe;
+        double s = 0.0;
+        for (int z = -R.zpe; z <= R.zpe; ++z) s = fma(rr[z], zp[(z + Rc) * 8 + c], s);
+        rowS[row * 8 + c] = s;
     }
 }
 
@@ -112,69 +115,106 @@ __device__ void moment_finish(const SolveParams& P, const BallGeo& G, const doub
     __syncthreads();
 }
 
-// Eq. me on the shell: v = sum_l P_l(r) / r^(2l+1), one thread per ME row.
+// Eq. me on the shell: v = sum_l P_l(r) / r^(2l+1), one warp per ME row.
+// The lanes form the row's coefficients U_{l,c} = sum T_abc x^a y^b of
+// P_l(z) together (ub: 2 x 28 values per warp in shared memory, FP64 and FP32
+// copies), then evaluate the row's shell points. Points within zn of the row
+// centre (the boundary layer that the stencil legs of the PE ball read) are
+// evaluated in FP64; the rest of the shell only feeds the D_xx scatter and is
+// evaluated in FP32.
 static __device__ __noinline__ void shell_potential(const SolveParams& P, const BallGeo& G, double* __restrict__ vc,
-                                                const double* __restrict__ xp, const double* __restrict__ yp,
-                                                const double* __restrict__ s_T, int tid, int nthr) {
+                                                    const double* __restrict__ xp, const double* __restrict__ yp,
+                                                    const double* __restrict__ s_T, double* ub, int wid, int nw) {
+    const int lane = threadIdx.x & 31;
     const int Rc = P.Rc;
-    for (int row = tid; row < G.n_rows_me; row += nthr) {
-        const RowRec R = G.rows_me[row];
-        const double* xa = xp + (R.ox + Rc) * 8;
-        const double* yb = yp + (R.oy + Rc) * 8;
-        double U[kNU];  // U_{l,c} = sum_{a+b=l-c} T_abc x^a y^b
-#pragma unroll
-        for (int u = 0; u < kNU; ++u) U[u] = 0.0;
-        {
-            int m = 0;
-#pragma unroll
-            for (int l = 0; l <= kLmaxMax; ++l)
-#pragma unroll
-                for (int a = l; a >= 0; --a)
-#pragma unroll
-                    for (int b = l - a; b >= 0; --b) {
-                        const int c = l - a - b;
-                        U[l * (l + 1) / 2 + c] = fma(s_T[m], xa[a] * yb[b], U[l * (l + 1) / 2 + c]);
-                        ++m;
-                    }
+    const double dx = P.delta[0], dy = P.delta[1], dz = P.delta[2];
+    const float dzf = (float)dz;
+    const long long S2 = P.S2;
+    const long long S = P.S;
+    const int nrows = G.n_rows_me;
+    const RowRec* __restrict__ rows = G.rows_me;
+    float* ub32 = reinterpret_cast<float*>(ub + kNU);
+    for (int row = wid; row < nrows; row += nw) {
+        const RowRec R = rows[row];
+        if (lane < kNU) {
+            const double* xa = xp + (R.ox + Rc) * 8;
+            const double* yb = yp + (R.oy + Rc) * 8;
+            double u = 0.0;
+            for (int t = 0; t < c_mp.uterm_n[lane]; ++t)
+                u = fma(s_T[c_mp.uterm[lane][t][0]], xa[c_mp.uterm[lane][t][1]] * yb[c_mp.uterm[lane][t][2]], u);
+            ub[lane] = u;
+            ub32[lane] = (float)u;
         }
-        const double x = R.ox * P.delta[0], y = R.oy * P.delta[1];
+        __syncwarp();
+        const double x = R.ox * dx, y = R.oy * dy;
         const double rxy2 = x * x + y * y;
-        const long long base = (long long)(R.ox + Rc) * P.S2 + (long long)(R.oy + Rc) * P.S + Rc;
-        const int zlo_hi = R.zpe >= 0 ? -R.zpe - 1 : R.zme;
-        for (int z = -R.zme; z <= R.zme; ++z) {
-            if (R.zpe >= 0 && z > zlo_hi && z <= R.zpe) continue;
-            const double zz = z * P.delta[2];
-            const double r2 = fma(zz, zz, rxy2);
-            const double ir = rsqrt(r2);
-            const double ir2 = ir * ir;
-            double acc = 0.0;
+        const float rxy2f = (float)rxy2;
+        const long long base = (long long)(R.ox + Rc) * S2 + (long long)(R.oy + Rc) * S + Rc;
+        // shell points of the row: z in [-zme, -zpe-1] and [zpe+1, zme] (or all when zpe < 0)
+        const int zin = R.zpe >= 0 ? R.zpe + 1 : 0;      // first |z| on the shell
+        const int nseg = R.zme - zin + 1;                 // points per half (z >= 0 side counts z = 0 once)
+        const int npts = R.zpe >= 0 ? 2 * nseg : 2 * R.zme + 1;
+        for (int t = lane; t < npts; t += 32) {
+            int z;
+            if (R.zpe >= 0) z = t < nseg ? -(zin + t) : zin + (t - nseg);
+            else z = t - R.zme;
+            const int az = z < 0 ? -z : z;
+            if (az <= R.zn) {
+                const double zz = z * dz;
+                const double r2 = fma(zz, zz, rxy2);
+                const double ir = rsqrt(r2);
+                const double ir2 = ir * ir;
+                double acc = 0.0;
 #pragma unroll
-            for (int l = kLmaxMax; l >= 0; --l) {
-                const double* Ul = U + l * (l + 1) / 2;
-                double pl = Ul[l];
+                for (int l = kLmaxMax; l >= 0; --l) {
+                    const double* Ul = ub + l * (l + 1) / 2;
+                    double pl = Ul[l];
 #pragma unroll
-                for (int c = l - 1; c >= 0; --c) pl = fma(pl, zz, Ul[c]);
-                acc = fma(acc, ir2, pl);
+                    for (int c = l - 1; c >= 0; --c) pl = fma(pl, zz, Ul[c]);
+                    acc = fma(acc, ir2, pl);
+                }
+                vc[base + z] = acc * ir;
+            } else {
+                const float zz = (float)z * dzf;
+                const float r2 = fmaf(zz, zz, rxy2f);
+                const float ir = rsqrtf(r2);
+                const float ir2 = ir * ir;
+                float acc = 0.0f;
+#pragma unroll
+                for (int l = kLmaxMax; l >= 0; --l) {
+                    const float* Ul = ub32 + l * (l + 1) / 2;
+                    float pl = Ul[l];
+#pragma unroll
+                    for (int c = l - 1; c >= 0; --c) pl = fmaf(pl, zz, Ul[c]);
+                    acc = fmaf(acc, ir2, pl);
+                }
+                vc[base + z] = (double)(acc * ir);
             }
-            vc[base + z] = acc * ir;
         }
+        __syncwarp();
     }
 }
 
 // Step V scatter: D^i += v phi_j, D^j += v phi_i on the ME ball.
 static __device__ __noinline__ void scatter_dxx(const SolveParams& P, const BallGeo& G, const PairRec& pr,
-                                            const double* __restrict__ vc, int tid, int nthr) {
+                                                const double* __restrict__ vc, int tid, int nthr) {
     if (!P.dxx) return;
-    const double* phi_i = P.phi + (long long)pr.i * P.ngrid;
-    const double* phi_j = P.phi + (long long)pr.j * P.ngrid;
-    double* Di = P.dxx + (long long)pr.i * P.ngrid;
-    double* Dj = P.dxx + (long long)pr.j * P.ngrid;
+    const long long ng = P.ngrid;
+    const double* __restrict__ phi_i = P.phi + (long long)pr.i * ng;
+    const double* __restrict__ phi_j = P.phi + (long long)pr.j * ng;
+    double* Di = P.dxx + (long long)pr.i * ng;
+    double* Dj = P.dxx + (long long)pr.j * ng;
     const bool two = pr.i != pr.j;
-    for (int q = tid; q < G.n_me; q += nthr) {
-        const long long g = grid_index(P.N, pr.g, G.pt_off[q]);
-        const double v = vc[G.pt_cube[q]];
-        atomicAdd(Di + g, v * phi_j[g]);
-        if (two) atomicAdd(Dj + g, v * phi_i[g]);
+    const int N[3] = {P.N[0], P.N[1], P.N[2]};
+    const int g[3] = {pr.g[0], pr.g[1], pr.g[2]};
+    const int n_me = G.n_me;
+    const int* __restrict__ off = G.pt_off;
+    const int* __restrict__ cube = G.pt_cube;
+    for (int q = tid; q < n_me; q += nthr) {
+        const long long gi = grid_index(N, g, off[q]);
+        const double v = vc[cube[q]];
+        atomicAdd(Di + gi, v * phi_j[gi]);
+        if (two) atomicAdd(Dj + gi, v * phi_i[gi]);
     }
 }
 

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(NT, 1) pair_kernel(const SolveParams P) {
     __shared__ float red32[2][33];
     __shared__ double s_M[kNMono], s_T[kNMono];
     __shared__ int s_item;
+    __shared__ double s_ub[NT / 32][kNU + kNU / 2];
     int flip = 0, flip32 = 0;
 
     const int Rc = P.Rc;
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(NT, 1) pair_kernel(const SolveParams P) {
         moment_finish<NT>(P, G, rowS, xp, yp, sY, s_M, s_T);
 
         // 3. far-field potential on the shell
-        shell_potential(P, G, vc, xp, yp, s_T, threadIdx.x, NT);
+        shell_potential(P, G, vc, xp, yp, s_T, s_ub[threadIdx.x >> 5], threadIdx.x >> 5, NT / 32);
         __syncthreads();
 
         // 4./5. right-hand side and solve

@@ -72,9 +72,29 @@ def test_cfg0_pair_intermediates(torch, cfg0, precision):
         npe = orc["n_pe"]
         np.testing.assert_array_equal(got["rho"][:npe], orc["rho"][:npe])  # one IEEE product per point
         sh_scale = np.max(np.abs(orc["v"][npe:]))
-        assert np.max(np.abs(got["v"][npe:] - orc["v"][npe:])) <= 1e-12 * sh_scale  # Eq. me on the shell
+        layer = _boundary_layer(orc["off"], npe)
+        dv = np.abs(got["v"][npe:] - orc["v"][npe:])
+        # Eq. me on the shell: FP64 where the stencil legs of the PE ball read it,
+        # FP32 on the rest (only the D_xx scatter reads it)
+        assert np.max(dv[layer]) <= 1e-12 * sh_scale
+        assert np.max(dv) <= 1e-6 * sh_scale
         assert np.max(np.abs(got["b"] - orc["b"])) <= 1e-11 * np.max(np.abs(orc["b"]))
         assert np.max(np.abs(got["v"][:npe] - orc["v"][:npe])) <= 1e-8 * np.max(np.abs(orc["v"][:npe]))
+
+
+def _boundary_layer(off, npe):
+    """Shell points within three axial steps of a PE point."""
+    pe = {tuple(o) for o in off[:npe]}
+    out = np.zeros(len(off) - npe, bool)
+    for t, o in enumerate(off[npe:]):
+        for a in range(3):
+            for q in (1, 2, 3):
+                for sg in (-1, 1):
+                    u = list(o)
+                    u[a] += sg * q
+                    if tuple(u) in pe:
+                        out[t] = True
+    return out
 
 
 def test_operator_matches_oracle(torch):
