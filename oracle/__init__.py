@@ -65,6 +65,16 @@ def lib():
             L.oracle_pair_solve.argtypes = [_d, _i, _d, ctypes.c_int, ctypes.c_int, _i, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_int, _d, _d, _d, _d, _d, _i]
+            L.oracle_pair_radius.restype = ctypes.c_int
+            L.oracle_pair_radius.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int, ctypes.c_int, _i]
+            L.oracle_pair_list_radii.restype = ctypes.c_int
+            L.oracle_pair_list_radii.argtypes = [ctypes.c_int, _d, _d, _i, ctypes.c_double, _d, ctypes.c_double,
+                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, _i, _i, _i, _i, _i]
+            L.oracle_exx_pairs_radii.restype = ctypes.c_double
+            L.oracle_exx_pairs_radii.argtypes = [_d, _i, _d, ctypes.c_int, ctypes.c_int, _i, _i, _i, _i, _i,
+                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_int, _d, _i, _d, _i, ctypes.c_int]
             L.oracle_exx_pairs.restype = ctypes.c_double
             L.oracle_exx_pairs.argtypes = [_d, _i, _d, ctypes.c_int, ctypes.c_int, _i, _i, _i, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -107,6 +117,36 @@ def pair_list(centers, cell, grid, r_pair):
     if cnt < 0:
         raise RuntimeError("pair list overflow")
     return pi[:cnt].copy(), pj[:cnt].copy(), g[:cnt].copy()
+
+
+LN_INV_EPS = math.log(1e14)  # ln(1/eps) of the per-pair radius rule, eps = 1e-14
+
+
+def pair_radius(ai, aj, d2, delta, r_min=12, r_max=32):
+    """Per-pair (R_PE, R_ME) of the spread-dependent subdomain rule."""
+    rme = ctypes.c_int()
+    r = lib().oracle_pair_radius(float(ai), float(aj), float(d2), float(delta), LN_INV_EPS, int(r_min), int(r_max),
+                                 ctypes.byref(rme))
+    return r, rme.value
+
+
+def pair_list_radii(centers, cell, grid, r_pair, alphas, r_min=12, r_max=32):
+    """Pair list plus per-pair radii: (i, j, g, r_pe, r_me)."""
+    centers = _f64(centers).reshape(-1, 3)
+    n = centers.shape[0]
+    cap = n * (n + 1) // 2
+    pi = np.empty(cap, np.int32)
+    pj = np.empty(cap, np.int32)
+    g = np.empty((cap, 3), np.int32)
+    rpe = np.empty(cap, np.int32)
+    rme = np.empty(cap, np.int32)
+    r = float(r_pair) if math.isfinite(r_pair) else 1e300
+    cnt = lib().oracle_pair_list_radii(n, _dp(centers), _dp(_f64(cell)), _ip(_i32(grid)), r, _dp(_f64(alphas)),
+                                       LN_INV_EPS, int(r_min), int(r_max), cap, _ip(pi), _ip(pj), _ip(g),
+                                       _ip(rpe), _ip(rme))
+    if cnt < 0:
+        raise RuntimeError("pair list overflow")
+    return tuple(a[:cnt].copy() for a in (pi, pj, g, rpe, rme))
 
 
 def proto_subdomain(r_pe, r_me):
@@ -182,26 +222,32 @@ def pair_solve(cell, grid, orbitals, i, j, gij, r_pe, r_me, lmax=6, tol=1e-13, t
 
 def exx(cell, grid, orbitals, pairs, r_pe, r_me, lmax=6, tol=1e-13, tol_report=None, maxit=100000,
         want_d=True, dmask=None, solve_all=True):
-    """Step V over a pair list (i, j, g). Returns dict(E_xx, E_pair, iters, rep_iters, D)."""
+    """Step V over a pair list (i, j, g) or (i, j, g, r_pe, r_me) with per-pair
+    radii. Returns dict(E_xx, E_pair, iters, rep_iters, D)."""
     orbitals = _f64(orbitals)
-    pi, pj, g = (_i32(a) for a in pairs)
+    pi, pj, g = (_i32(a) for a in pairs[:3])
+    rpe = _i32(pairs[3]) if len(pairs) > 3 else None
+    rme = _i32(pairs[4]) if len(pairs) > 4 else None
     npair = len(pi)
     n_orb = orbitals.shape[0]
     e_pair = np.empty(npair)
     iters = np.empty((npair, 2), np.int32)
     D = np.empty_like(orbitals) if want_d else None
     mask = None if dmask is None else _i32(dmask)
-    exx_v = lib().oracle_exx_pairs(_dp(_f64(cell)), _ip(_i32(grid)), _dp(orbitals), n_orb, npair,
-                                   _ip(pi), _ip(pj), _ip(g), r_pe, r_me, lmax, tol,
-                                   tol if tol_report is None else tol_report, maxit, _dp(e_pair),
-                                   _ip(iters), _dp(D), _ip(mask), 1 if solve_all else 0)
+    exx_v = lib().oracle_exx_pairs_radii(_dp(_f64(cell)), _ip(_i32(grid)), _dp(orbitals), n_orb, npair,
+                                         _ip(pi), _ip(pj), _ip(g), _ip(rpe), _ip(rme), r_pe, r_me, lmax, tol,
+                                         tol if tol_report is None else tol_report, maxit, _dp(e_pair),
+                                         _ip(iters), _dp(D), _ip(mask), 1 if solve_all else 0)
     return dict(E_xx=exx_v, E_pair=e_pair, iters=iters[:, 0].copy(), rep_iters=iters[:, 1].copy(), D=D)
 
 
 def exx_workload(w, tol=1e-13, tol_report=None, want_d=True, orbitals=None):
-    """Full pipeline for a synth.Workload with fixed radii."""
+    """Full pipeline for a synth.Workload (per-pair radii when w.radii_mode == 1)."""
     phi = w.orbitals() if orbitals is None else orbitals
-    pairs = pair_list(w.centers, w.cell, w.grid, w.r_pair)
+    if getattr(w, "radii_mode", 0) == 1:
+        pairs = pair_list_radii(w.centers, w.cell, w.grid, w.r_pair, w.alphas, 12, w.r_pe)
+    else:
+        pairs = pair_list(w.centers, w.cell, w.grid, w.r_pair)
     out = exx(w.cell, w.grid, phi, pairs, w.r_pe, w.r_me, w.l_max, tol=tol,
               tol_report=w.tol if tol_report is None else tol_report, want_d=want_d)
     out["pairs"] = pairs

@@ -30,7 +30,11 @@
  *   oracle_exx_pairs        Step V over a pair list: E_xx = -sum over ordered
  *                           pairs (self x1, i<j x2) and the force scatter
  *                           D^i += v_ij phi_j, D^j += v_ij phi_i on the ME ball
- *                           (Eqs. Dxx_mlwf, Dxx_mlwf_omega).
+ *                           (Eqs. Dxx_mlwf, Dxx_mlwf_omega); the _radii form
+ *                           takes per-pair radii.
+ *   oracle_pair_radius,     Per-pair radii from the orbitals' Gaussian
+ *   oracle_pair_list_radii     envelopes (spread-dependent subdomains, the
+ *                           outlook of Sec. IV.A; reading listed below).
  *   oracle_laplacian_box,   The same 19-point stencil on a plain box (interior
  *   oracle_laplacian_periodic  points) and on a periodic box, for the pins.
  *   oracle_cg_periodic,     The same CG on a periodic box and on a given ball
@@ -42,7 +46,10 @@
  *   - Q_lm is summed over the PE ball only;
  *   - MOD is the non-negative periodic remainder;
  *   - CG stops when ||r||_2 <= tol * ||b||_2, b including the boundary charge;
- *   - D^i = sum_j v_ij phi_j literally (no a_x, no factor 2 or 4).
+ *   - D^i = sum_j v_ij phi_j literally (no a_x, no factor 2 or 4);
+ *   - per-pair radii: the eps-support of the Gaussian product envelope seen
+ *     from the pair centre, eps = 1e-14, clamped to [r_min, r_max], and
+ *     R_ME = R_PE + max(3, ceil(R_PE/3)).
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (see build.py).
  * Floating-point contraction is off so that the pair list (where doubles
@@ -117,6 +124,52 @@ int oracle_pair_list(int n, const double *centers, const double *cell, const int
         }
     }
     return count;
+}
+
+/*
+ * Per-pair radii for spread-dependent subdomains (the "beta-version" outlook of
+ * Sec. IV.A, with Omega = {|phi| > eps}, Sec. II.C). For Gaussian envelopes the
+ * product decays as exp(-mu d^2) exp(-(a_i + a_j) s^2) about the weighted centre
+ * cbar = C_i + a_j/(a_i + a_j) d, mu = a_i a_j/(a_i + a_j). Its eps-support radius is
+ * s_eps = sqrt(max(0, (ln(1/eps) - mu |d|^2)/(a_i + a_j))), seen from the pair
+ * centre C_ij = C_i + d/2 at distance |a_j/(a_i + a_j) - 1/2| |d| from cbar:
+ *   R_PE = clamp(ceil((s_eps + |cbar - C_ij|)/delta), r_min, r_max),
+ *   R_ME = R_PE + max(3, ceil(R_PE/3)).
+ * ln_inv_eps is ln(1/eps); delta the largest grid spacing.
+ */
+int oracle_pair_radius(double ai, double aj, double d2, double delta, double ln_inv_eps, int r_min, int r_max,
+                       int *r_me) {
+    double beta = ai + aj;
+    double mu = ai * aj / beta;
+    double t = (ln_inv_eps - mu * d2) / beta;
+    double s = t > 0.0 ? sqrt(t) : 0.0;
+    double w = fabs(aj / beta - 0.5) * sqrt(d2);
+    double rf = ceil((s + w) / delta);
+    int r = rf < (double)r_min ? r_min : (rf > (double)r_max ? r_max : (int)rf);
+    if (r_me) *r_me = r + ((r + 2) / 3 > 3 ? (r + 2) / 3 : 3);
+    return r;
+}
+
+/* Pair list as oracle_pair_list plus the per-pair radii of oracle_pair_radius. */
+int oracle_pair_list_radii(int n, const double *centers, const double *cell, const int *grid, double r_pair,
+                           const double *alphas, double ln_inv_eps, int r_min, int r_max, int cap, int *pi,
+                           int *pj, int *gij, int *rpe, int *rme) {
+    int cnt = oracle_pair_list(n, centers, cell, grid, r_pair, cap, pi, pj, gij);
+    if (cnt < 0) return cnt;
+    double delta = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double da = cell[a] / (double)grid[a];
+        if (da > delta) delta = da;
+    }
+    for (int p = 0; p < cnt; ++p) {
+        int i = pi[p], j = pj[p];
+        double d[3];
+        for (int a = 0; a < 3; ++a) d[a] = minimg(centers[3 * j + a] - centers[3 * i + a], cell[a]);
+        double d2 = d[0] * d[0] + d[1] * d[1];
+        d2 = d2 + d[2] * d[2];
+        rpe[p] = oracle_pair_radius(alphas[i], alphas[j], d2, delta, ln_inv_eps, r_min, r_max, rme + p);
+    }
+    return cnt;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -551,20 +604,35 @@ double oracle_pair_solve(const double *cell, const int *grid, const double *orbi
  * solve_all != 0 (otherwise their E_pair is NaN and they are skipped).
  * Returns E_xx = -(sum_i E_ii + 2 sum_{i<j} E_ij) over the solved pairs.
  */
-double oracle_exx_pairs(const double *cell, const int *grid, const double *orbitals, int n_orb,
-                        int npair, const int *pi, const int *pj, const int *gij, int r_pe, int r_me,
-                        int lmax, double tol, double tol_report, int maxit, double *E_pair,
-                        int *iters, double *D, const int *dmask, int solve_all) {
+/*
+ * As oracle_exx_pairs, with per-pair radii rpe[p], rme[p] when they are given
+ * (NULL: r_pe, r_me for every pair). Balls are built once per distinct radius.
+ */
+double oracle_exx_pairs_radii(const double *cell, const int *grid, const double *orbitals, int n_orb,
+                              int npair, const int *pi, const int *pj, const int *gij, const int *rpe,
+                              const int *rme, int r_pe, int r_me, int lmax, double tol, double tol_report,
+                              int maxit, double *E_pair, int *iters, double *D, const int *dmask,
+                              int solve_all) {
     geom_t G;
     geom_make(&G, cell, grid, lmax, tol, tol_report, maxit);
-    ball_t B;
-    if (ball_make(&B, r_pe, r_me, G.delta)) return NAN;
+    /* one ball per distinct (R_PE, R_ME); radii stay below 64 grid points */
+    ball_t *balls = calloc(64 * 64, sizeof(ball_t));
+    int max_nme = 0;
+    for (int p = -1; p < npair; ++p) {
+        int a = p < 0 ? r_pe : rpe ? rpe[p] : r_pe, b = p < 0 ? r_me : rme ? rme[p] : r_me;
+        if (a < 0 || a >= 64 || b < 0 || b >= 64) { free(balls); return NAN; }
+        ball_t *Bp = &balls[a * 64 + b];
+        if (!Bp->off) {
+            if (ball_make(Bp, a, b, G.delta)) { free(balls); return NAN; }
+        }
+        if (Bp->n_me > max_nme) max_nme = Bp->n_me;
+    }
     long ng = (long)grid[0] * grid[1] * grid[2];
     if (D) memset(D, 0, sizeof(double) * (size_t)n_orb * ng);
 
     int chunk = 4 * oracle_num_threads();
     if (chunk < 1) chunk = 1;
-    double *vbuf = D ? malloc(sizeof(double) * (size_t)chunk * B.n_me) : NULL;
+    double *vbuf = D ? malloc(sizeof(double) * (size_t)chunk * max_nme) : NULL;
     for (int p0 = 0; p0 < npair; p0 += chunk) {
         int p1 = p0 + chunk < npair ? p0 + chunk : npair;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -572,8 +640,9 @@ double oracle_exx_pairs(const double *cell, const int *grid, const double *orbit
             int i = pi[p], j = pj[p];
             int want = solve_all || !dmask || dmask[i] || dmask[j];
             if (!want) { E_pair[p] = NAN; if (iters) { iters[2 * p] = -1; iters[2 * p + 1] = -1; } continue; }
-            double *v = vbuf ? vbuf + (size_t)(p - p0) * B.n_me : NULL;
-            E_pair[p] = pair_solve(&G, &B, orbitals + (long)i * ng, orbitals + (long)j * ng, gij + 3 * p,
+            const ball_t *Bp = &balls[(rpe ? rpe[p] : r_pe) * 64 + (rme ? rme[p] : r_me)];
+            double *v = vbuf ? vbuf + (size_t)(p - p0) * max_nme : NULL;
+            E_pair[p] = pair_solve(&G, Bp, orbitals + (long)i * ng, orbitals + (long)j * ng, gij + 3 * p,
                                    NULL, NULL, v, NULL, iters ? iters + 2 * p : NULL, NULL);
         }
         if (!D) continue;
@@ -581,19 +650,22 @@ double oracle_exx_pairs(const double *cell, const int *grid, const double *orbit
         for (int p = p0; p < p1; ++p) {
             if (isnan(E_pair[p])) continue;
             int i = pi[p], j = pj[p];
-            const double *v = vbuf + (size_t)(p - p0) * B.n_me;
+            const ball_t *Bp = &balls[(rpe ? rpe[p] : r_pe) * 64 + (rme ? rme[p] : r_me)];
+            const double *v = vbuf + (size_t)(p - p0) * max_nme;
             const double *phi_i = orbitals + (long)i * ng, *phi_j = orbitals + (long)j * ng;
             double *Di = D + (long)i * ng, *Dj = D + (long)j * ng;
             int mi = !dmask || dmask[i], mj = !dmask || dmask[j];
-            for (int q = 0; q < B.n_me; ++q) {
-                long gq = ball_global(&G, &B, gij + 3 * p, q);
+            for (int q = 0; q < Bp->n_me; ++q) {
+                long gq = ball_global(&G, Bp, gij + 3 * p, q);
                 if (mi) Di[gq] += v[q] * phi_j[gq];
                 if (i != j && mj) Dj[gq] += v[q] * phi_i[gq];
             }
         }
     }
     free(vbuf);
-    ball_free(&B);
+    for (int t = 0; t < 64 * 64; ++t)
+        if (balls[t].off) ball_free(&balls[t]);
+    free(balls);
 
     double e = 0.0;
     for (int p = 0; p < npair; ++p) {
@@ -601,4 +673,12 @@ double oracle_exx_pairs(const double *cell, const int *grid, const double *orbit
         e += (pi[p] == pj[p] ? 1.0 : 2.0) * E_pair[p];
     }
     return -e;
+}
+
+double oracle_exx_pairs(const double *cell, const int *grid, const double *orbitals, int n_orb,
+                        int npair, const int *pi, const int *pj, const int *gij, int r_pe, int r_me,
+                        int lmax, double tol, double tol_report, int maxit, double *E_pair,
+                        int *iters, double *D, const int *dmask, int solve_all) {
+    return oracle_exx_pairs_radii(cell, grid, orbitals, n_orb, npair, pi, pj, gij, NULL, NULL, r_pe, r_me, lmax,
+                                  tol, tol_report, maxit, E_pair, iters, D, dmask, solve_all);
 }

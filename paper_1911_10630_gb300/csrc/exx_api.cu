@@ -17,7 +17,10 @@
 namespace exx {
 cudaError_t launch_pair_list(int n, const double* centers, const double L[3], const double delta[3], const int N[3],
                              double r_pair, int r_pe, int r_me, int* counts, int* offsets, int* n_pair, int* queue,
-                             PairRec* pairs, cudaStream_t st);
+                             PairRec* pairs, cudaStream_t st, const double* alphas, double ln_inv_eps,
+                             double delta_max, int r_min);
+cudaError_t launch_radii_sort(const PairRec* pairs, const int* n_pair, int* hist, int n_geo, int* order, int num_sms,
+                              cudaStream_t st);
 cudaError_t launch_zero(double* p, long long n, int num_sms, cudaStream_t st);
 cudaError_t launch_exx_reduce(const PairRec* pairs, const int* n_pair, const double* e_pair, double* out,
                               cudaStream_t st);
@@ -56,8 +59,11 @@ struct exx_ctx {
     int device = 0;
     int num_sms = 0;
 
-    // geometry
-    HostBall hb;
+    // geometry: one ball per radius (fixed radii: one; per-pair radii: r_min .. r_pe)
+    HostBall hb;                  // the largest ball (sizes the workspace)
+    std::vector<HostBall> balls;  // balls[geo], R_PE = r_min + geo
+    int r_min = 0, n_geo = 1;
+    double ln_inv_eps = 0.0, delta_max = 0.0;
     void* geo_mem = nullptr;  // device tables
     BallGeo* d_geos = nullptr;
     BallGeo geo_host;
@@ -91,6 +97,8 @@ struct exx_ctx {
     double* d_epair = nullptr;
     int* d_iters = nullptr;
     int* d_refines = nullptr;
+    int* d_order = nullptr;  // largest-first processing order (per-pair radii)
+    int* d_hist = nullptr;
     int* d_scalars = nullptr;  // [0] n_pair, [1] queue, [2] nonconv
     double* d_exx = nullptr;
     double* h_exx = nullptr;   // pinned
@@ -177,6 +185,8 @@ static void free_pairs(exx_ctx* c) {
     cudaFree(c->d_epair);
     cudaFree(c->d_iters);
     cudaFree(c->d_refines);
+    cudaFree(c->d_order);
+    c->d_order = nullptr;
     c->d_counts = c->d_offsets = nullptr;
     c->d_pairs = nullptr;
     c->d_epair = nullptr;
@@ -196,6 +206,7 @@ extern "C" void exx_destroy(exx_ctx* c) {
     drop_graph(c);
     free_pairs(c);
     cudaFree(c->d_scalars);
+    cudaFree(c->d_hist);
     cudaFree(c->d_exx);
     if (c->h_exx) cudaFreeHost(c->h_exx);
     cudaFree(c->ws);
@@ -237,7 +248,14 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (!(tol > 0.0 && tol < 1.0)) return fail(nullptr, EXX_EINVAL, "exx_init: tol must be in (0, 1)");
     exx_options o = opt ? *opt : exx_default_options();
     if (o.precision != 0 && o.precision != 1) return fail(nullptr, EXX_EINVAL, "exx_init: precision must be 0 or 1");
-    if (o.radii_mode != 0) return fail(nullptr, EXX_EINVAL, "exx_init: radii_mode 1 is not available in this build");
+    if (o.radii_mode != 0 && o.radii_mode != 1) return fail(nullptr, EXX_EINVAL, "exx_init: radii_mode must be 0 or 1");
+    if (o.radii_mode == 1) {
+        const int rme_rule = r_pe + std::max(3, (r_pe + 2) / 3);
+        if (r_me < rme_rule)
+            return fail(nullptr, EXX_EINVAL,
+                        "exx_init: with radii_mode 1, r_me must be >= r_pe + max(3, ceil(r_pe/3)) (the largest pair's R_ME)");
+        if (o.solver_kind == 2) return fail(nullptr, EXX_EINVAL, "exx_init: radii_mode 1 runs on solver_kind 1");
+    }
     if (o.warm_start != 0) return fail(nullptr, EXX_EINVAL, "exx_init: warm_start 1 is not available in this build");
     if (o.max_iter <= 0) o.max_iter = 20000;
     if (o.inner_max_iter <= 0) o.inner_max_iter = 4000;
@@ -288,41 +306,68 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (e == cudaSuccess) e = set_multipole_const_cluster(mc);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpyToSymbol(multipoles)"));
 
-    // ball geometry (Algorithm 2), cube radius Rc = R_ME
+    // ball geometries (Algorithm 2), cube radius Rc = R_ME (the largest)
     const int Rc = r_me, S = 2 * Rc + 1;
-    build_ball(c->hb, r_pe, r_me, Rc);
+    if (o.radii_mode == 1) {
+        c->r_min = std::min(12, r_pe);
+        c->n_geo = r_pe - c->r_min + 1;
+    } else {
+        c->r_min = r_pe;
+        c->n_geo = 1;
+    }
+    c->ln_inv_eps = std::log(1e14);
+    c->delta_max = std::max(c->delta[0], std::max(c->delta[1], c->delta[2]));
+    c->balls.resize(c->n_geo);
+    for (int g = 0; g < c->n_geo; ++g) {
+        const int R = c->r_min + g;
+        const int Rm = o.radii_mode == 1 ? R + std::max(3, (R + 2) / 3) : r_me;
+        build_ball(c->balls[g], R, Rm, Rc);
+    }
+    c->hb = c->balls.back();
     const HostBall& B = c->hb;
-    size_t o_cube = 0;
-    size_t o_off = align256(o_cube + sizeof(int) * B.n_me);
-    size_t o_rpe = align256(o_off + sizeof(int) * B.n_me);
-    size_t o_rme = align256(o_rpe + sizeof(RowRec) * B.rows_pe.size());
-    size_t o_pl = align256(o_rme + sizeof(RowRec) * B.rows_me.size());
-    size_t o_geo = align256(o_pl + sizeof(int) * B.plane_pe.size());
-    size_t geo_bytes = align256(o_geo + sizeof(BallGeo));
-    e = cudaMalloc(&c->geo_mem, geo_bytes);
-    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(geometry)"));
-    char* gm = (char*)c->geo_mem;
-    BallGeo G;
-    G.r_pe = r_pe;
-    G.r_me = r_me;
-    G.n_pe = B.n_pe;
-    G.n_me = B.n_me;
-    G.n_rows_pe = (int)B.rows_pe.size();
-    G.n_rows_me = (int)B.rows_me.size();
-    G.pt_cube = (const int*)(gm + o_cube);
-    G.pt_off = (const int*)(gm + o_off);
-    G.rows_pe = (const RowRec*)(gm + o_rpe);
-    G.rows_me = (const RowRec*)(gm + o_rme);
-    G.plane_pe = (const int*)(gm + o_pl);
-    c->geo_host = G;
-    c->d_geos = (BallGeo*)(gm + o_geo);
-    if ((e = cudaMemcpy(gm + o_cube, B.cube.data(), sizeof(int) * B.n_me, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(gm + o_off, B.off.data(), sizeof(int) * B.n_me, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(gm + o_rpe, B.rows_pe.data(), sizeof(RowRec) * B.rows_pe.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(gm + o_rme, B.rows_me.data(), sizeof(RowRec) * B.rows_me.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(gm + o_pl, B.plane_pe.data(), sizeof(int) * B.plane_pe.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(gm + o_geo, &G, sizeof(BallGeo), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return bail(cuda_fail(c, e, "cudaMemcpy(geometry)"));
+    {
+        std::vector<size_t> o_cube(c->n_geo), o_off(c->n_geo), o_rpe(c->n_geo), o_rme(c->n_geo), o_pl(c->n_geo);
+        size_t at = 0;
+        for (int g = 0; g < c->n_geo; ++g) {
+            const HostBall& Bg = c->balls[g];
+            o_cube[g] = at; at = align256(at + sizeof(int) * Bg.n_me);
+            o_off[g] = at; at = align256(at + sizeof(int) * Bg.n_me);
+            o_rpe[g] = at; at = align256(at + sizeof(RowRec) * Bg.rows_pe.size());
+            o_rme[g] = at; at = align256(at + sizeof(RowRec) * Bg.rows_me.size());
+            o_pl[g] = at; at = align256(at + sizeof(int) * Bg.plane_pe.size());
+        }
+        const size_t o_geo = at;
+        const size_t geo_bytes = align256(o_geo + sizeof(BallGeo) * c->n_geo);
+        e = cudaMalloc(&c->geo_mem, geo_bytes);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(geometry)"));
+        char* gm = (char*)c->geo_mem;
+        std::vector<BallGeo> gv(c->n_geo);
+        for (int g = 0; g < c->n_geo; ++g) {
+            const HostBall& Bg = c->balls[g];
+            BallGeo& G = gv[g];
+            G.r_pe = Bg.r_pe;
+            G.r_me = Bg.r_me;
+            G.n_pe = Bg.n_pe;
+            G.n_me = Bg.n_me;
+            G.n_rows_pe = (int)Bg.rows_pe.size();
+            G.n_rows_me = (int)Bg.rows_me.size();
+            G.pt_cube = (const int*)(gm + o_cube[g]);
+            G.pt_off = (const int*)(gm + o_off[g]);
+            G.rows_pe = (const RowRec*)(gm + o_rpe[g]);
+            G.rows_me = (const RowRec*)(gm + o_rme[g]);
+            G.plane_pe = (const int*)(gm + o_pl[g]);
+            if ((e = cudaMemcpy(gm + o_cube[g], Bg.cube.data(), sizeof(int) * Bg.n_me, cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(gm + o_off[g], Bg.off.data(), sizeof(int) * Bg.n_me, cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(gm + o_rpe[g], Bg.rows_pe.data(), sizeof(RowRec) * Bg.rows_pe.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(gm + o_rme[g], Bg.rows_me.data(), sizeof(RowRec) * Bg.rows_me.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(gm + o_pl[g], Bg.plane_pe.data(), sizeof(int) * Bg.plane_pe.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+                return bail(cuda_fail(c, e, "cudaMemcpy(geometry)"));
+        }
+        c->geo_host = gv.back();
+        c->d_geos = (BallGeo*)(gm + o_geo);
+        e = cudaMemcpy(gm + o_geo, gv.data(), sizeof(BallGeo) * c->n_geo, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpy(geometry records)"));
+    }
 
     // workspace slots
     const long long S3 = (long long)S * S * S;
@@ -361,7 +406,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     }
 
     // cluster solver: largest cluster size whose slab layout and registers fit
-    if (o.precision == 1 && o.solver_kind != 1) {
+    if (o.precision == 1 && o.solver_kind != 1 && c->n_geo == 1) {
         int max_optin = 0;
         cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
         const int cands[3] = {8, 4, 2};
@@ -439,6 +484,8 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     cudaDeviceGetAttribute(&c->clock_khz, cudaDevAttrClockRate, c->device);
     e = cudaMalloc(&c->d_phase, sizeof(unsigned long long) * 4);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(phase clocks)"));
+    e = cudaMalloc(&c->d_hist, sizeof(int) * 2 * (size_t)c->n_geo);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(radius histogram)"));
     e = cudaMalloc(&c->d_scalars, sizeof(int) * 8);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(scalars)"));
     e = cudaMalloc(&c->d_exx, sizeof(double) * 2);
@@ -477,7 +524,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         P.st32.cz[q] = (float)P.st64.cz[q];
     }
     P.geos = c->d_geos;
-    P.n_geo = 1;
+    P.n_geo = c->n_geo;
     P.S = S;
     P.Rc = Rc;
     P.S2 = (long long)S * S;
@@ -516,14 +563,15 @@ static exx_status ensure_pairs(exx_ctx* c, int n) {
     CK(cudaMalloc(&c->d_epair, sizeof(double) * (size_t)np), "cudaMalloc(e_pair)");
     CK(cudaMalloc(&c->d_iters, sizeof(int) * (size_t)np), "cudaMalloc(iters)");
     CK(cudaMalloc(&c->d_refines, sizeof(int) * (size_t)np), "cudaMalloc(refines)");
+    if (c->n_geo > 1) CK(cudaMalloc(&c->d_order, sizeof(int) * (size_t)np), "cudaMalloc(order)");
     c->cap_n = n;
     c->cap_pairs = np;
     return EXX_OK;
 }
 
 // The launch sequence of one call (captured into a graph when batched).
-static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* centers, int n, double* d_xx,
-                          cudaStream_t st, bool capturing) {
+static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* centers, const double* alphas, int n,
+                          double* d_xx, cudaStream_t st, bool capturing) {
     // inside a capture a plain event record only expresses a dependency; the
     // external flag turns it into an event-record node that can be timed
     const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -531,7 +579,7 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
     P.phi = orbitals;
     P.dxx = d_xx;
     P.pairs = c->d_pairs;
-    P.order = nullptr;
+    P.order = c->n_geo > 1 ? c->d_order : nullptr;
     P.e_pair = c->d_epair;
     P.iters = c->d_iters;
     P.refines = c->d_refines;
@@ -542,8 +590,12 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
     CK(cudaMemsetAsync(c->d_scalars + 2, 0, sizeof(int), st), "reset counters");
     CK(cudaMemsetAsync(c->d_phase, 0, sizeof(unsigned long long) * 4, st), "reset phase clocks");
     CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
-                        c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st),
+                        c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st,
+                        c->n_geo > 1 ? alphas : nullptr, c->ln_inv_eps, c->delta_max, c->r_min),
        "pair list");
+    if (c->n_geo > 1)
+        CK(launch_radii_sort(c->d_pairs, c->d_scalars, c->d_hist, c->n_geo, c->d_order, c->num_sms, st),
+           "largest-first order");
     CK(cudaEventRecordWithFlags(c->ev[1], st, evf), "cudaEventRecord");
     if (c->use_cluster)
         CK(launch_cluster_kernel(c->cl_variant, P, c->CL, c->n_clusters, c->smem, st), "cluster pair kernel");
@@ -558,11 +610,11 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
 
 extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const double* centers, int n,
                                   const double* alphas, double* e_xx, double* d_xx, void* stream) {
-    (void)alphas;
     if (!c) return fail(nullptr, EXX_EINVAL, "exx_compute: ctx is NULL");
     if (!orbitals || !centers || !e_xx || !d_xx) return fail(c, EXX_EINVAL, "exx_compute: NULL array argument");
     if (n < 1 || n > 65535) return fail(c, EXX_EINVAL, "exx_compute: n must be in [1, 65535]");
     if ((const void*)orbitals == (const void*)d_xx) return fail(c, EXX_EINVAL, "exx_compute: d_xx aliases orbitals");
+    if (c->n_geo > 1 && !alphas) return fail(c, EXX_EINVAL, "exx_compute: radii_mode 1 needs the orbital exponents (alphas)");
     if (((reinterpret_cast<uintptr_t>(orbitals) | reinterpret_cast<uintptr_t>(centers) |
           reinterpret_cast<uintptr_t>(d_xx) | reinterpret_cast<uintptr_t>(alphas)) & 7u) != 0)
         return fail(c, EXX_EINVAL, "exx_compute: arrays must be 8-byte aligned");
@@ -575,14 +627,14 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
     CK(cudaStreamWaitEvent(st, c->ev_in, 0), "cudaStreamWaitEvent");
     cudaError_t e;
     if (c->opt.batched) {
-        const void* key[5] = {orbitals, centers, d_xx, nullptr, nullptr};
+        const void* key[5] = {orbitals, centers, d_xx, alphas, nullptr};
         bool hit = c->gexec && c->g_n == n && std::equal(key, key + 5, c->g_key);
         if (!hit) {
             drop_graph(c);
             cudaGraph_t g;
             e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
-            s = enqueue(c, orbitals, centers, n, d_xx, st, true);
+            s = enqueue(c, orbitals, centers, alphas, n, d_xx, st, true);
             e = cudaStreamEndCapture(st, &g);
             if (s != EXX_OK) {
                 if (e == cudaSuccess) cudaGraphDestroy(g);
@@ -601,7 +653,7 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
         e = cudaGraphLaunch(c->gexec, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
     } else {
-        s = enqueue(c, orbitals, centers, n, d_xx, st, false);
+        s = enqueue(c, orbitals, centers, alphas, n, d_xx, st, false);
         if (s != EXX_OK) return s;
     }
     CK(cudaEventRecord(c->ev_out, st), "cudaEventRecord(done)");
@@ -680,7 +732,8 @@ extern "C" exx_status exx_get_stats(const exx_ctx* cc, exx_stats* out) {
         int rmax = 0;
         for (int p = 0; p < np; ++p) {
             tot += it[p];
-            pit += (long long)it[p] * c->hb.n_pe;
+            const int g = std::min(std::max(pr[p].geo, 0), c->n_geo - 1);
+            pit += (long long)it[p] * c->balls[g].n_pe;
             rmax = std::max(rmax, rf[p]);
         }
         std::vector<int> srt = it;

@@ -207,17 +207,23 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
                     if (pkj >= 0) {
                         const int off = pkj & 0xffffff, xl = pkj >> 24;
                         const float pc = ps[off];
-                        float a = st.c0 * pc;
+                        // leg pair sums first, then a shallow tree of products:
+                        // independent chains instead of one 10-deep FMA chain
+                        float sz[3], sy[3], sx[3];
 #pragma unroll
                         for (int q = 1; q <= 3; ++q) {
-                            a = fmaf(st.cz[q - 1], ps[off + q] + ps[off - q], a);
-                            a = fmaf(st.cy[q - 1], ps[off + q * Syz] + ps[off - q * Syz], a);
+                            sz[q - 1] = ps[off + q] + ps[off - q];
+                            sy[q - 1] = ps[off + q * Syz] + ps[off - q * Syz];
                             const float xpv = xl + q < planes ? ps[off + q * Sp2]
                                                               : (pp ? pp[off + (q - planes) * Sp2] : 0.0f);
                             const float xmv = xl - q >= 0 ? ps[off - q * Sp2]
                                                           : (pm ? pm[off + (planes_prev - q) * Sp2] : 0.0f);
-                            a = fmaf(st.cx[q - 1], xpv + xmv, a);
+                            sx[q - 1] = xpv + xmv;
                         }
+                        const float az = fmaf(st.cz[0], sz[0], fmaf(st.cz[1], sz[1], st.cz[2] * sz[2]));
+                        const float ay = fmaf(st.cy[0], sy[0], fmaf(st.cy[1], sy[1], st.cy[2] * sy[2]));
+                        const float ax = fmaf(st.cx[0], sx[0], fmaf(st.cx[1], sx[1], st.cx[2] * sx[2]));
+                        const float a = fmaf(st.c0, pc, (az + ay) + ax);
                         ap[j] = -a;
                         pa = fmaf(pc, -a, pa);
                     }

@@ -23,7 +23,27 @@ struct PairGeom {
     int N[3];
     double r2cut;
     int r_pe, r_me;
+    // per-pair radii (alphas != NULL): rule of the spread-dependent subdomains
+    const double* alphas;
+    double ln_inv_eps, delta_max;
+    int r_min;
 };
+
+// R_PE = clamp(ceil((s_eps + |cbar - C_ij|)/delta), r_min, r_max) with
+// s_eps = sqrt(max(0, (ln(1/eps) - mu d^2)/(a_i + a_j))), mu = a_i a_j/(a_i + a_j),
+// |cbar - C_ij| = |a_j/(a_i + a_j) - 1/2| |d|; R_ME = R_PE + max(3, ceil(R_PE/3)).
+// Every operation is explicitly rounded: doubles decide the integer radius.
+__device__ __forceinline__ int pair_radius_d(double ai, double aj, double d2, const PairGeom& G, int* r_me) {
+    const double beta = __dadd_rn(ai, aj);
+    const double mu = __ddiv_rn(__dmul_rn(ai, aj), beta);
+    const double t = __ddiv_rn(__dsub_rn(G.ln_inv_eps, __dmul_rn(mu, d2)), beta);
+    const double s = t > 0.0 ? __dsqrt_rn(t) : 0.0;
+    const double w = __dmul_rn(fabs(__dsub_rn(__ddiv_rn(aj, beta), 0.5)), __dsqrt_rn(d2));
+    const double rf = ceil(__ddiv_rn(__dadd_rn(s, w), G.delta_max));
+    const int r = rf < (double)G.r_min ? G.r_min : (rf > (double)G.r_pe ? G.r_pe : (int)rf);
+    *r_me = r + ((r + 2) / 3 > 3 ? (r + 2) / 3 : 3);
+    return r;
+}
 
 __device__ __forceinline__ bool pair_within(const double* __restrict__ C, int i, int j, const PairGeom& G,
                                             double d[3]) {
@@ -120,14 +140,49 @@ __global__ void pairs_fill_kernel(int n, const double* __restrict__ C, PairGeom 
                 long long mm = g % G.N[a];
                 r.g[a] = (int)(mm < 0 ? mm + G.N[a] : mm);
             }
-            r.r_pe = G.r_pe;
-            r.r_me = G.r_me;
-            r.geo = 0;
+            if (G.alphas) {
+                double d2 = __dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1]));
+                d2 = __dadd_rn(d2, __dmul_rn(d[2], d[2]));
+                int rme;
+                r.r_pe = pair_radius_d(G.alphas[i], G.alphas[j], d2, G, &rme);
+                r.r_me = rme;
+                r.geo = r.r_pe - G.r_min;
+            } else {
+                r.r_pe = G.r_pe;
+                r.r_me = G.r_me;
+                r.geo = 0;
+            }
             pairs[pos] = r;
         }
         base += s_w[32];
         __syncthreads();
     }
+}
+
+// Largest pairs first: counting sort of the pair indices by geometry
+// (descending radius). hist[0..n_geo) counts, hist[n_geo..2 n_geo) cursors.
+__global__ void radii_count_kernel(const PairRec* __restrict__ pairs, const int* __restrict__ n_pair,
+                                   int* __restrict__ hist, int n_geo) {
+    const int np = *n_pair;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x)
+        atomicAdd(hist + pairs[p].geo, 1);
+}
+
+__global__ void radii_scan_kernel(int* __restrict__ hist, int n_geo) {
+    if (threadIdx.x != 0) return;
+    int run = 0;
+    for (int g = n_geo - 1; g >= 0; --g) {
+        const int c = hist[g];
+        hist[n_geo + g] = run;
+        run += c;
+    }
+}
+
+__global__ void radii_scatter_kernel(const PairRec* __restrict__ pairs, const int* __restrict__ n_pair,
+                                     int* __restrict__ hist, int n_geo, int* __restrict__ order) {
+    const int np = *n_pair;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x)
+        order[atomicAdd(hist + n_geo + pairs[p].geo, 1)] = p;
 }
 
 // D_xx = 0 (grid-stride fill; 16-byte stores when the pointer allows them).
@@ -166,7 +221,8 @@ namespace exx {
 
 cudaError_t launch_pair_list(int n, const double* centers, const double L[3], const double delta[3], const int N[3],
                              double r_pair, int r_pe, int r_me, int* counts, int* offsets, int* n_pair, int* queue,
-                             PairRec* pairs, cudaStream_t st) {
+                             PairRec* pairs, cudaStream_t st, const double* alphas, double ln_inv_eps,
+                             double delta_max, int r_min) {
     PairGeom G;
     for (int a = 0; a < 3; ++a) {
         G.L[a] = L[a];
@@ -176,9 +232,23 @@ cudaError_t launch_pair_list(int n, const double* centers, const double L[3], co
     G.r2cut = r_pair * r_pair;
     G.r_pe = r_pe;
     G.r_me = r_me;
+    G.alphas = alphas;
+    G.ln_inv_eps = ln_inv_eps;
+    G.delta_max = delta_max;
+    G.r_min = r_min;
     pairs_count_kernel<<<n, 256, 0, st>>>(n, centers, G, counts);
     pairs_scan_kernel<<<1, 1024, 0, st>>>(n, counts, offsets, n_pair, queue);
     pairs_fill_kernel<<<n, 256, 0, st>>>(n, centers, G, offsets, pairs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_radii_sort(const PairRec* pairs, const int* n_pair, int* hist, int n_geo, int* order, int num_sms,
+                              cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * 2 * n_geo, st);
+    if (e != cudaSuccess) return e;
+    radii_count_kernel<<<num_sms * 2, 256, 0, st>>>(pairs, n_pair, hist, n_geo);
+    radii_scan_kernel<<<1, 32, 0, st>>>(hist, n_geo);
+    radii_scatter_kernel<<<num_sms * 2, 256, 0, st>>>(pairs, n_pair, hist, n_geo, order);
     return cudaGetLastError();
 }
 

@@ -219,6 +219,14 @@ __global__ void __launch_bounds__(NT, 1) pair_kernel(const SolveParams P) {
             if (!conv) atomicAdd(P.nonconv, 1);
         }
         scatter_dxx(P, G, pr, vc, threadIdx.x, NT);
+        if (P.n_geo > 1) {
+            // the next pair may have another ball: the direction cube must be
+            // zero outside it, so clear the points this pair wrote
+            for (int k = threadIdx.x; k < n_pe; k += NT) {
+                if (MIXED) p32[cube[k]] = 0.0f;
+                else pc[cube[k]] = 0.0;
+            }
+        }
         __syncthreads();
     }
 }
@@ -238,14 +246,14 @@ __global__ void debug_pair_readback(const SolveParams P, PairRec pr, double* rho
 
 // A p on the PE ball: scatter p into the (zeroed) slot-0 cube, then apply.
 __global__ void apply_scatter(const SolveParams P, const double* p) {
-    const BallGeo G = P.geos[0];
+    const BallGeo G = P.geos[P.n_geo - 1];
     double* pc = reinterpret_cast<double*>(P.ws + P.off_pcube);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G.n_pe; k += gridDim.x * blockDim.x)
         pc[G.pt_cube[k]] = p[k];
 }
 
 __global__ void apply_stencil(const SolveParams P, double* ap) {
-    const BallGeo G = P.geos[0];
+    const BallGeo G = P.geos[P.n_geo - 1];
     const double* pc = reinterpret_cast<const double*>(P.ws + P.off_pcube);
     const Stencil<double> neg = negated(P.st64);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G.n_pe; k += gridDim.x * blockDim.x)
@@ -253,7 +261,7 @@ __global__ void apply_stencil(const SolveParams P, double* ap) {
 }
 
 __global__ void apply_unscatter(const SolveParams P) {
-    const BallGeo G = P.geos[0];
+    const BallGeo G = P.geos[P.n_geo - 1];
     double* pc = reinterpret_cast<double*>(P.ws + P.off_pcube);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G.n_pe; k += gridDim.x * blockDim.x)
         pc[G.pt_cube[k]] = 0.0;

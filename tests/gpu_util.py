@@ -25,8 +25,12 @@ def run_gpu(w, phi=None, torch=None, allow_noconv=False, **opts):
     dphi = torch.from_numpy(phi).cuda()
     dcen = torch.from_numpy(np.ascontiguousarray(w.centers)).cuda()
     dD = torch.empty_like(dphi)
+    dal = None
+    if getattr(w, "radii_mode", 0) == 1:
+        opts.setdefault("radii_mode", 1)
+        dal = torch.from_numpy(np.ascontiguousarray(w.alphas, dtype=np.float64)).cuda()
     ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, opts.pop("tol", w.tol), **opts)
-    e = ex.compute(dphi, dcen, dD, allow_noconv=allow_noconv)
+    e = ex.compute(dphi, dcen, dD, alphas=dal, allow_noconv=allow_noconv)
     torch.cuda.synchronize()
     out = dict(E_xx=e, D=dD.cpu().numpy(), pairs=ex.pairs(), stats=ex.stats(), ex=ex, dphi=dphi,
                status=ex.last_status)

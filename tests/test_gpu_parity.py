@@ -212,3 +212,61 @@ def test_water64_full_size_sampled(torch, precision):
     # E_xx is the multiplicity-weighted sum of the pair energies
     m = np.where(out["pairs"]["i"] == out["pairs"]["j"], 1.0, 2.0)
     assert abs(out["E_xx"] + np.sum(m * out["pairs"]["e_pair"])) <= 1e-12 * abs(out["E_xx"])
+
+
+# --------------------------------------------------------------------------
+# Per-pair radii, largest pairs first (batched uneven workloads)
+# --------------------------------------------------------------------------
+
+def _pairs_radii_equal(gpu_pairs, ref_pairs):
+    pi, pj, g, rpe, rme = ref_pairs
+    np.testing.assert_array_equal(gpu_pairs["i"], pi)
+    np.testing.assert_array_equal(gpu_pairs["j"], pj)
+    np.testing.assert_array_equal(gpu_pairs["g"], g)
+    np.testing.assert_array_equal(gpu_pairs["radii"][:, 0], rpe)
+    np.testing.assert_array_equal(gpu_pairs["radii"][:, 1], rme)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_per_pair_radii_small(torch, precision):
+    w = synth.tiny(seed=8, n=6, npts=48, length=9.6, r_pe=16, r_me=22, alpha=(0.5, 2.0), tol=1e-10, min_sep=1.2)
+    w.radii_mode = 1
+    phi = w.orbitals()
+    ref = oracle.exx_workload(w, tol=1e-13, orbitals=phi)
+    assert len(set(ref["pairs"][3])) >= 3  # several radii in play
+    out = run_gpu(w, phi, torch=torch, precision=precision)
+    _pairs_radii_equal(out["pairs"], ref["pairs"])
+    assert out["stats"]["n_nonconv"] == 0
+    assert abs(out["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
+    assert d_maxrel(out["D"], ref["D"]) <= D_GATE_MAXREL
+    np.testing.assert_allclose(out["pairs"]["e_pair"], ref["E_pair"], rtol=1e-7, atol=1e-12)
+
+
+def test_batched_uneven_full_size_sampled(torch):
+    """The batched-uneven workload (150^3, 512 orbitals in 128 clusters,
+    alpha ~ U(0.5, 2), per-pair radii 12..32, largest pairs first), checked
+    on sampled pairs and one sampled orbital."""
+    w = synth.config2()
+    phi = w.orbitals()
+    out = run_gpu(w, phi, torch=torch, precision=1)
+    ref_pairs = oracle.pair_list_radii(w.centers, w.cell, w.grid, w.r_pair, w.alphas, 12, w.r_pe)
+    _pairs_radii_equal(out["pairs"], ref_pairs)
+    assert out["stats"]["n_nonconv"] == 0
+    rpe = ref_pairs[3]
+    assert rpe.min() <= 14 and rpe.max() >= 28
+    rng = np.random.default_rng(3)
+    npair = len(rpe)
+    sample = np.unique(np.concatenate([rng.choice(npair, 12, replace=False), [int(np.argmax(rpe)),
+                                                                              int(np.argmin(rpe))]]))
+    sub = tuple(a[sample] for a in ref_pairs)
+    orc = oracle.exx(w.cell, w.grid, phi, sub, w.r_pe, w.r_me, w.l_max, tol=1e-13, want_d=False)
+    np.testing.assert_allclose(out["pairs"]["e_pair"][sample], orc["E_pair"], rtol=0,
+                               atol=E_GATE_PER_ORBITAL / 4)
+    orb = int(ref_pairs[0][sample[0]])
+    mask = np.zeros(w.n, np.int32)
+    mask[orb] = 1
+    touch = np.nonzero(mask[ref_pairs[0]] | mask[ref_pairs[1]])[0]
+    sub2 = tuple(a[touch] for a in ref_pairs)
+    orc2 = oracle.exx(w.cell, w.grid, phi, sub2, w.r_pe, w.r_me, w.l_max, tol=1e-13, want_d=True, dmask=mask)
+    den = np.max(np.abs(orc2["D"][orb]))
+    assert np.max(np.abs(out["D"][orb] - orc2["D"][orb])) <= D_GATE_MAXREL * den

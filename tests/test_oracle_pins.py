@@ -510,3 +510,64 @@ def test_bruteforce_dense_restatement(oracle_mod):
     out = oracle_mod.exx_workload(w, tol=1e-14, orbitals=phi)
     assert abs(out["E_xx"] - ref_e) <= 1e-11 * abs(ref_e)
     assert np.max(np.abs(out["D"] - ref_d)) <= 1e-10 * np.max(np.abs(ref_d))
+
+
+# --------------------------------------------------------------------------
+# Per-pair radii (spread-dependent subdomains)
+# --------------------------------------------------------------------------
+
+def test_pair_radius_rule_bounds_the_envelope(oracle_mod):
+    # brute force: beyond R_PE grid steps from the pair centre the product of the
+    # two Gaussian envelopes is below eps = 1e-14 (unless R_PE was clamped)
+    rng = np.random.default_rng(12)
+    delta = 0.197
+    for _ in range(40):
+        ai, aj = rng.uniform(0.5, 2.0, 2)
+        d = rng.normal(size=3) * rng.uniform(0.0, 3.0)
+        r, rme = oracle_mod.pair_radius(ai, aj, d @ d, delta, 12, 32)
+        ci, cj = np.zeros(3), d
+        cij = 0.5 * d
+        dirs = rng.normal(size=(400, 3))
+        dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+        pts = cij + dirs * (r * delta * (1.0 + 1e-9))
+        env = np.exp(-ai * np.sum((pts - ci) ** 2, 1) - aj * np.sum((pts - cj) ** 2, 1))
+        if 12 < r < 32:
+            assert env.max() <= 1e-14 * (1 + 1e-9)
+            # and one step less would not bound it everywhere (the radius is tight)
+            pts_in = cij + dirs * ((r - 1) * delta)
+            env_in = np.exp(-ai * np.sum((pts_in - ci) ** 2, 1) - aj * np.sum((pts_in - cj) ** 2, 1))
+            cbar = aj / (ai + aj) * d
+            toward = cij + (cbar - cij) / max(np.linalg.norm(cbar - cij), 1e-300) * ((r - 1) * delta)
+            worst = np.exp(-ai * np.sum((toward - ci) ** 2) - aj * np.sum((toward - cj) ** 2))
+            assert max(env_in.max(), worst) > 1e-14 * 0.999 or np.linalg.norm(cbar - cij) < 1e-12
+        assert 12 <= r <= 32 and rme == r + max(3, -(-r // 3))
+        assert (r, rme) == oracle_mod.pair_radius(aj, ai, d @ d, delta, 12, 32)  # symmetric in i, j
+
+
+def test_pair_radius_self_pair_closed_form(oracle_mod):
+    # d = 0: s_eps = sqrt(ln(1e14) / (2 alpha)), R = ceil(s_eps / delta)
+    for alpha in (0.5, 0.8, 1.0, 1.5, 2.0):
+        r, _ = oracle_mod.pair_radius(alpha, alpha, 0.0, 0.19733, 12, 32)
+        want = min(32, max(12, math.ceil(math.sqrt(math.log(1e14) / (2 * alpha)) / 0.19733)))
+        assert r == want
+    assert oracle_mod.pair_radius(0.5, 0.5, 0.0, 0.19733, 12, 32)[0] == 29
+
+
+def test_exx_with_per_pair_radii_matches_fixed_when_radii_agree(oracle_mod):
+    # the per-pair form with every pair at the same radii equals the fixed form
+    w = synth.tiny(seed=6, n=3, npts=24, length=6.0, r_pe=6, r_me=9)
+    phi = w.orbitals()
+    pi, pj, g = oracle_mod.pair_list(w.centers, w.cell, w.grid, w.r_pair)
+    a = oracle_mod.exx(w.cell, w.grid, phi, (pi, pj, g), 6, 9, tol=1e-13)
+    rp = np.full(len(pi), 6, np.int32)
+    rm = np.full(len(pi), 9, np.int32)
+    b = oracle_mod.exx(w.cell, w.grid, phi, (pi, pj, g, rp, rm), 6, 9, tol=1e-13)
+    assert a["E_xx"] == b["E_xx"]
+    np.testing.assert_array_equal(a["D"], b["D"])
+    # and mixed radii change the per-pair subdomains
+    rp2 = np.where(pi == pj, 7, 5).astype(np.int32)
+    rm2 = rp2 + 3
+    c = oracle_mod.exx(w.cell, w.grid, phi, (pi, pj, g, rp2, rm2), 7, 10, tol=1e-13)
+    for k in range(len(pi)):
+        e = oracle_mod.pair_solve(w.cell, w.grid, phi, pi[k], pj[k], g[k], int(rp2[k]), int(rm2[k]), tol=1e-13)["E"]
+        assert abs(e - c["E_pair"][k]) <= 1e-14 * max(abs(e), 1e-300)
