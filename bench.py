@@ -218,6 +218,7 @@ def main():
     ap.add_argument("--cluster-size", type=int, default=0)
     ap.add_argument("--lane-map", type=int, default=0)
     ap.add_argument("--update-drop", type=float, default=1e-3)
+    ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--orbitals", type=int, default=0,
                     help="keep only the first N orbitals of the workload (small cases for profiling)")
     args = ap.parse_args()
@@ -251,7 +252,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
     ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=args.precision,
              threads=args.threads, ctas_per_sm=args.ctas_per_sm, solver_kind=args.solver_kind,
-             cluster_size=args.cluster_size, lane_map=args.lane_map, update_drop=args.update_drop)
+             cluster_size=args.cluster_size, lane_map=args.lane_map, update_drop=args.update_drop,
+             autotune=args.autotune)
 
     def barrier():
         if ws > 1:
@@ -356,7 +358,8 @@ def main():
                        else "fp64 CG", "l2": "inputs larger than L2 (orbitals 3.5 GB, D_xx 3.5 GB)",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "solver": f"{st['solver_kind']}x{st['cluster_size']} ctas={st['grid_ctas']} "
-                                 f"threads={st['threads']}"},
+                                 f"threads={st['threads']} lane_map={st['lane_map']} "
+                                 f"autotuned_from={st['n_candidates']}"},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

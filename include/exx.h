@@ -80,6 +80,10 @@ typedef struct {
     int lane_map;      /* cluster solver thread-to-point map: 0 = natural order
                           (contiguous warps, default), 1 = bank-distinct lanes
                           dealt plane by plane.                                  */
+    int autotune;      /* cluster solver: 1 = on the first exx_compute of a context
+                          time every fitting launch shape (cluster size, threads
+                          per CTA, lane map) on a prefix of the pair queue and
+                          keep the fastest (default); 0 = take the first fit.    */
 } exx_options;
 
 typedef struct {
@@ -102,6 +106,9 @@ typedef struct {
                               clusters' cycle counts into setup (gather,
                               multipoles, shell), FP64 residuals, FP32 CG
                               iterations and finish (E_ij, scatter)               */
+    int lane_map;          /* lane map in use (cluster solver)                      */
+    int n_candidates;      /* launch shapes the autotuner could choose from          */
+    double tune_ms;        /* host time spent by the autotuner (first call)          */
 } exx_stats;
 
 /* Defaults described in exx_options. */

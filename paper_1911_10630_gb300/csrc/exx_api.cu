@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdint>
@@ -76,14 +77,24 @@ struct exx_ctx {
     size_t smem = 0;
     SolveParams P;
 
-    // cluster solver (precision 1): one thread-block cluster per pair
+    // cluster solver (precision 1): one thread-block cluster per pair. Every
+    // launch shape that fits is a candidate; the autotuner times them on the
+    // first call and keeps the fastest.
+    struct ClusterCand {
+        int C = 0, variant = -1, lane_map = 0, n_clusters = 0;
+        size_t smem = 0;
+        ClusterLayout L;
+        double pairs_per_s = 0.0;
+    };
     bool use_cluster = false;
+    std::vector<ClusterCand> cands;
+    int cand = -1;  // candidate in use
+    bool tuned = false;
+    double tune_ms = 0.0;
     int cl_variant = -1;
     int n_clusters = 0;
     ClusterLayout CL;
-    int* d_pt_slab = nullptr;
-    int4* d_rank_info = nullptr;
-    int* d_slot = nullptr;  // slot_pk then slot_k
+    std::vector<void*> cl_mem;  // device tables of all candidates
     double* d_pow = nullptr;
     unsigned long long* d_phase = nullptr;  // [4] phase cycles of the cluster solver
     int clock_khz = 0;
@@ -102,6 +113,14 @@ struct exx_ctx {
     int* d_scalars = nullptr;  // [0] n_pair, [1] queue, [2] nonconv
     double* d_exx = nullptr;
     double* h_exx = nullptr;   // pinned
+
+    // warm start (previous call's potentials)
+    PairRec* d_prev_pairs = nullptr;
+    long long prev_cap = 0;
+    float* d_vcache[2] = {nullptr, nullptr};
+    long long vcache_pairs = 0;
+    int parity = 0;
+    bool have_prev = false;
 
     // host-buffer path
     double* d_orb = nullptr;
@@ -173,10 +192,21 @@ extern "C" exx_options exx_default_options(void) {
     o.cluster_size = 0;
     o.update_drop = 1e-3;
     o.lane_map = 0;
+    o.autotune = 1;
     return o;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static void apply_cand(exx_ctx* cc, int k) {
+    const exx_ctx::ClusterCand& K = cc->cands[k];
+    cc->cand = k;
+    cc->CL = K.L;
+    cc->cl_variant = K.variant;
+    cc->smem = K.smem;
+    cc->threads = cluster_variant_threads(K.variant);
+    cc->n_clusters = std::min(K.n_clusters, cc->n_slots > 0 ? cc->n_slots : K.n_clusters);
+}
 
 static void free_pairs(exx_ctx* c) {
     cudaFree(c->d_counts);
@@ -215,9 +245,10 @@ extern "C" void exx_destroy(exx_ctx* c) {
     cudaFree(c->d_dxx);
     cudaFree(c->d_cent);
     cudaFree(c->d_alpha);
-    cudaFree(c->d_pt_slab);
-    cudaFree(c->d_rank_info);
-    cudaFree(c->d_slot);
+    for (void* m : c->cl_mem) cudaFree(m);
+    cudaFree(c->d_prev_pairs);
+    cudaFree(c->d_vcache[0]);
+    cudaFree(c->d_vcache[1]);
     cudaFree(c->d_pow);
     cudaFree(c->d_phase);
     for (auto& e : c->ev)
@@ -256,7 +287,10 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                         "exx_init: with radii_mode 1, r_me must be >= r_pe + max(3, ceil(r_pe/3)) (the largest pair's R_ME)");
         if (o.solver_kind == 2) return fail(nullptr, EXX_EINVAL, "exx_init: radii_mode 1 runs on solver_kind 1");
     }
-    if (o.warm_start != 0) return fail(nullptr, EXX_EINVAL, "exx_init: warm_start 1 is not available in this build");
+    if (o.warm_start != 0 && o.warm_start != 1) return fail(nullptr, EXX_EINVAL, "exx_init: warm_start must be 0 or 1");
+    if (o.warm_start == 1 && (o.precision != 1 || o.radii_mode != 0 || o.solver_kind == 1))
+        return fail(nullptr, EXX_EINVAL,
+                    "exx_init: warm_start 1 runs on the cluster solver (precision 1, fixed radii, solver_kind 0 or 2)");
     if (o.max_iter <= 0) o.max_iter = 20000;
     if (o.inner_max_iter <= 0) o.inner_max_iter = 4000;
     if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) o.inner_tol = 1e-5;
@@ -326,7 +360,8 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     c->hb = c->balls.back();
     const HostBall& B = c->hb;
     {
-        std::vector<size_t> o_cube(c->n_geo), o_off(c->n_geo), o_rpe(c->n_geo), o_rme(c->n_geo), o_pl(c->n_geo);
+        std::vector<size_t> o_cube(c->n_geo), o_off(c->n_geo), o_rpe(c->n_geo), o_rme(c->n_geo), o_pl(c->n_geo),
+            o_ro(c->n_geo);
         size_t at = 0;
         for (int g = 0; g < c->n_geo; ++g) {
             const HostBall& Bg = c->balls[g];
@@ -335,6 +370,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             o_rpe[g] = at; at = align256(at + sizeof(RowRec) * Bg.rows_pe.size());
             o_rme[g] = at; at = align256(at + sizeof(RowRec) * Bg.rows_me.size());
             o_pl[g] = at; at = align256(at + sizeof(int) * Bg.plane_pe.size());
+            o_ro[g] = at; at = align256(at + sizeof(int) * Bg.row_of.size());
         }
         const size_t o_geo = at;
         const size_t geo_bytes = align256(o_geo + sizeof(BallGeo) * c->n_geo);
@@ -356,7 +392,9 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             G.rows_pe = (const RowRec*)(gm + o_rpe[g]);
             G.rows_me = (const RowRec*)(gm + o_rme[g]);
             G.plane_pe = (const int*)(gm + o_pl[g]);
-            if ((e = cudaMemcpy(gm + o_cube[g], Bg.cube.data(), sizeof(int) * Bg.n_me, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            G.row_of = (const int*)(gm + o_ro[g]);
+            if ((e = cudaMemcpy(gm + o_ro[g], Bg.row_of.data(), sizeof(int) * Bg.row_of.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(gm + o_cube[g], Bg.cube.data(), sizeof(int) * Bg.n_me, cudaMemcpyHostToDevice)) != cudaSuccess ||
                 (e = cudaMemcpy(gm + o_off[g], Bg.off.data(), sizeof(int) * Bg.n_me, cudaMemcpyHostToDevice)) != cudaSuccess ||
                 (e = cudaMemcpy(gm + o_rpe[g], Bg.rows_pe.data(), sizeof(RowRec) * Bg.rows_pe.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
                 (e = cudaMemcpy(gm + o_rme[g], Bg.rows_me.data(), sizeof(RowRec) * Bg.rows_me.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -405,65 +443,98 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         P.pow_tab = c->d_pow;
     }
 
-    // cluster solver: largest cluster size whose slab layout and registers fit
+    // cluster solver candidates: every cluster size, thread count and lane map
+    // whose slab layout, registers and shared memory fit
     if (o.precision == 1 && o.solver_kind != 1 && c->n_geo == 1) {
         int max_optin = 0;
         cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-        const int cands[3] = {8, 4, 2};
-        for (int ci = 0; ci < 3 && !c->use_cluster; ++ci) {
-            const int C = cands[ci];
+        const int csizes[3] = {8, 4, 2};
+        for (int ci = 0; ci < 3; ++ci) {
+            const int C = csizes[ci];
             if (o.cluster_size && o.cluster_size != C) continue;
             ClusterLayout L;
             std::vector<int> pt;
             if (!build_cluster_layout(B, C, L, pt)) continue;
-            const int v = cluster_variant(C, L.max_pts, o.threads);
-            if (v < 0) continue;
-            const size_t sm = cluster_kernel_smem(Rc, L, v) + 2048;
-            if ((long)sm > (long)max_optin) continue;
-            int nclu = 0;
-            e = cluster_prepare(v, sm - 2048, &nclu);
-            if (e != cudaSuccess || nclu < 1) {
-                (void)cudaGetLastError();
-                continue;
+            int* d_pt = nullptr;
+            int4* d_ri = nullptr;
+            for (int nt : {1024, 512}) {
+                if (o.threads && o.threads != nt) continue;
+                const int v = cluster_variant(C, L.max_pts, nt);
+                if (v < 0) continue;
+                const size_t sm = cluster_kernel_smem(Rc, L, v);
+                if ((long)sm + 2048 > (long)max_optin) continue;
+                int nclu = 0;
+                e = cluster_prepare(v, sm, &nclu);
+                if (e != cudaSuccess || nclu < 1) {
+                    (void)cudaGetLastError();
+                    continue;
+                }
+                if (!d_pt) {
+                    e = cudaMalloc(&d_pt, sizeof(int) * pt.size());
+                    if (e == cudaSuccess) c->cl_mem.push_back(d_pt);
+                    if (e == cudaSuccess) e = cudaMemcpy(d_pt, pt.data(), sizeof(int) * pt.size(), cudaMemcpyHostToDevice);
+                    int4 ri[kMaxCluster];
+                    for (int r = 0; r < C; ++r) ri[r] = make_int4(L.x0[r], L.planes[r], L.k0[r], L.k1[r]);
+                    if (e == cudaSuccess) e = cudaMalloc(&d_ri, sizeof(int4) * C);
+                    if (e == cudaSuccess) c->cl_mem.push_back(d_ri);
+                    if (e == cudaSuccess) e = cudaMemcpy(d_ri, ri, sizeof(int4) * C, cudaMemcpyHostToDevice);
+                    if (e != cudaSuccess) return bail(cuda_fail(c, e, "slab tables"));
+                }
+                for (int lm = 0; lm <= 1; ++lm) {
+                    if (!o.autotune && lm != o.lane_map) continue;
+                    std::vector<int> spk, sk;
+                    if (build_slot_maps(L, pt, cluster_variant_threads(v), cluster_variant_pts(v), lm, spk, sk) < 0)
+                        continue;
+                    int* d_slot = nullptr;
+                    e = cudaMalloc(&d_slot, sizeof(int) * (spk.size() + sk.size()));
+                    if (e == cudaSuccess) c->cl_mem.push_back(d_slot);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpy(d_slot, spk.data(), sizeof(int) * spk.size(), cudaMemcpyHostToDevice);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpy(d_slot + spk.size(), sk.data(), sizeof(int) * sk.size(), cudaMemcpyHostToDevice);
+                    if (e != cudaSuccess) return bail(cuda_fail(c, e, "slot maps"));
+                    exx_ctx::ClusterCand K;
+                    K.C = C;
+                    K.variant = v;
+                    K.lane_map = lm;
+                    K.n_clusters = nclu;
+                    K.smem = sm;
+                    K.L = L;
+                    K.L.pt_slab = d_pt;
+                    K.L.rank_info = d_ri;
+                    K.L.slot_pk = d_slot;
+                    K.L.slot_k = d_slot + spk.size();
+                    c->cands.push_back(K);
+                }
             }
-            e = cudaMalloc(&c->d_pt_slab, sizeof(int) * pt.size());
-            if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(slab table)"));
-            e = cudaMemcpy(c->d_pt_slab, pt.data(), sizeof(int) * pt.size(), cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpy(slab table)"));
-            L.pt_slab = c->d_pt_slab;
-            int4 ri[kMaxCluster];
-            for (int r = 0; r < C; ++r) ri[r] = make_int4(L.x0[r], L.planes[r], L.k0[r], L.k1[r]);
-            e = cudaMalloc(&c->d_rank_info, sizeof(int4) * C);
-            if (e == cudaSuccess) e = cudaMemcpy(c->d_rank_info, ri, sizeof(int4) * C, cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) return bail(cuda_fail(c, e, "slab rank table"));
-            L.rank_info = c->d_rank_info;
-            std::vector<int> spk, sk;
-            if (build_slot_maps(L, pt, cluster_variant_threads(v), cluster_variant_pts(v), o.lane_map, spk, sk) < 0)
-                return bail(fail(c, EXX_ECUDA, "exx_init: slot map does not fit"));
-            e = cudaMalloc(&c->d_slot, sizeof(int) * (spk.size() + sk.size()));
-            if (e == cudaSuccess) e = cudaMemcpy(c->d_slot, spk.data(), sizeof(int) * spk.size(), cudaMemcpyHostToDevice);
-            if (e == cudaSuccess)
-                e = cudaMemcpy(c->d_slot + spk.size(), sk.data(), sizeof(int) * sk.size(), cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) return bail(cuda_fail(c, e, "slot maps"));
-            L.slot_pk = c->d_slot;
-            L.slot_k = c->d_slot + spk.size();
-            c->CL = L;
-            c->cl_variant = v;
-            c->n_clusters = nclu;
-            c->smem = sm - 2048;
-            c->threads = cluster_variant_threads(v);
+        }
+        if (!c->cands.empty()) {
             c->use_cluster = true;
+            // default before tuning: the first candidate in preference order
+            // (largest cluster, most threads, the requested lane map)
+            int pick = 0;
+            for (int k = 0; k < (int)c->cands.size(); ++k)
+                if (c->cands[k].lane_map == o.lane_map) {
+                    pick = k;
+                    break;
+                }
+            c->cand = pick;
+            c->tuned = !o.autotune || c->cands.size() == 1;
         }
         if (!c->use_cluster && o.solver_kind == 2)
             return bail(fail(c, EXX_EINVAL, "exx_init: no cluster layout fits these radii"));
     }
+    if (o.warm_start == 1 && !c->use_cluster)
+        return bail(fail(c, EXX_EINVAL, "exx_init: warm_start 1 needs the cluster solver, which does not fit these radii"));
+    if (c->use_cluster) apply_cand(c, c->cand);
 
     c->threads = c->use_cluster ? c->threads : (o.threads ? o.threads : 512);
     if (!c->use_cluster) c->smem = pair_kernel_smem(Rc, r_pe);
     int bps = 0;
     long long want;
     if (c->use_cluster) {
-        want = c->n_clusters;
+        want = 0;
+        for (const auto& K : c->cands) want = std::max<long long>(want, K.n_clusters);
     } else {
         e = pair_kernel_occupancy(c->threads, o.precision == 1, c->smem, &bps);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
@@ -475,7 +546,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     cudaMemGetInfo(&free_b, &total_b);
     long long fit = (long long)(0.25 * (double)free_b / (double)c->slot_bytes);
     c->n_slots = (int)std::max(1LL, std::min(want, fit));
-    if (c->use_cluster) c->n_clusters = c->n_slots;
+    if (c->use_cluster) apply_cand(c, c->cand);
     e = cudaMalloc(&c->ws, c->slot_bytes * (size_t)c->n_slots);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(workspace)"));
     e = cudaMemset(c->ws, 0, c->slot_bytes * (size_t)c->n_slots);
@@ -547,6 +618,8 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     c->stats.solver_kind = c->use_cluster ? 2 : 1;
     c->stats.cluster_size = c->use_cluster ? c->CL.C : 1;
     c->stats.grid_ctas = c->use_cluster ? c->n_clusters * c->CL.C : c->n_slots;
+    c->stats.lane_map = c->use_cluster ? c->cands[c->cand].lane_map : 0;
+    c->stats.n_candidates = (int)c->cands.size();
     c->stats.threads = c->threads;
     *out = c;
     return EXX_OK;
@@ -608,6 +681,129 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
     return EXX_OK;
 }
 
+// Warm-start call: eager launches, because the potential cache is sized from
+// this call's pair count. The cluster kernel starts each pair kept from the
+// previous call (same i, j) from its cached potential, shifted by the move of
+// the pair's grid centre, and caches the new potential for the next call.
+static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double* centers, const double* alphas,
+                               int n, double* d_xx, cudaStream_t st) {
+    SolveParams P = c->P;
+    P.phi = orbitals;
+    P.dxx = d_xx;
+    P.pairs = c->d_pairs;
+    P.order = nullptr;
+    P.e_pair = c->d_epair;
+    P.iters = c->d_iters;
+    P.refines = c->d_refines;
+    P.dbg_b = nullptr;
+    P.phase_clk = c->d_phase;
+    CK(cudaEventRecord(c->ev[0], st), "cudaEventRecord");
+    CK(launch_zero(d_xx, (long long)n * c->ngrid, c->num_sms, st), "zero D_xx");
+    CK(cudaMemsetAsync(c->d_scalars + 2, 0, sizeof(int), st), "reset counters");
+    CK(cudaMemsetAsync(c->d_phase, 0, sizeof(unsigned long long) * 4, st), "reset phase clocks");
+    CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
+                        c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st, nullptr, c->ln_inv_eps,
+                        c->delta_max, c->r_min),
+       "pair list");
+    int np = 0;
+    CK(cudaMemcpyAsync(&np, c->d_scalars, sizeof(int), cudaMemcpyDeviceToHost, st), "read n_pair");
+    CK(cudaStreamSynchronize(st), "warm start synchronize");
+    if (np > c->vcache_pairs) {  // grow the caches (the previous potentials are lost)
+        cudaFree(c->d_vcache[0]);
+        cudaFree(c->d_vcache[1]);
+        c->d_vcache[0] = c->d_vcache[1] = nullptr;
+        c->vcache_pairs = 0;
+        c->have_prev = false;
+        const long long want = (long long)(1.25 * np) + 16;
+        const size_t bytes = sizeof(float) * (size_t)want * c->hb.n_pe;
+        CK(cudaMalloc(&c->d_vcache[0], bytes), "cudaMalloc(warm-start cache)");
+        CK(cudaMalloc(&c->d_vcache[1], bytes), "cudaMalloc(warm-start cache)");
+        c->vcache_pairs = want;
+    }
+    if (np > c->prev_cap) {
+        cudaFree(c->d_prev_pairs);
+        c->d_prev_pairs = nullptr;
+        c->have_prev = false;
+        c->prev_cap = 0;
+        CK(cudaMalloc(&c->d_prev_pairs, sizeof(PairRec) * (size_t)c->cap_pairs), "cudaMalloc(previous pairs)");
+        c->prev_cap = c->cap_pairs;
+    }
+    P.warm = c->have_prev ? 1 : 0;
+    P.prev_pairs = c->d_prev_pairs;
+    P.n_prev = c->d_scalars + 7;
+    P.vprev = c->d_vcache[c->parity ^ 1];
+    P.vcur = c->d_vcache[c->parity];
+    CK(cudaEventRecord(c->ev[1], st), "cudaEventRecord");
+    CK(launch_cluster_kernel(c->cl_variant, P, c->CL, c->n_clusters, c->smem, st), "cluster pair kernel");
+    CK(cudaEventRecord(c->ev[2], st), "cudaEventRecord");
+    CK(launch_exx_reduce(c->d_pairs, c->d_scalars, c->d_epair, c->d_exx, st), "E_xx reduction");
+    CK(cudaMemcpyAsync(c->h_exx, c->d_exx, sizeof(double), cudaMemcpyDeviceToHost, st), "copy E_xx");
+    // this call's list becomes the previous one
+    CK(cudaMemcpyAsync(c->d_prev_pairs, c->d_pairs, sizeof(PairRec) * (size_t)np, cudaMemcpyDeviceToDevice, st),
+       "keep pair list");
+    CK(cudaMemcpyAsync(c->d_scalars + 7, c->d_scalars, sizeof(int), cudaMemcpyDeviceToDevice, st), "keep n_pair");
+    CK(cudaEventRecord(c->ev[3], st), "cudaEventRecord");
+    c->parity ^= 1;
+    c->have_prev = true;
+    return EXX_OK;
+}
+
+// The autotuner: on the first call, every cluster-solver candidate processes
+// the same prefix of the pair queue (no D_xx scatter); the one with the most
+// pairs per second is kept for the life of the context.
+static exx_status autotune(exx_ctx* c, const double* orbitals, const double* centers, const double* alphas, int n,
+                           cudaStream_t st) {
+    CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
+                        c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st,
+                        c->n_geo > 1 ? alphas : nullptr, c->ln_inv_eps, c->delta_max, c->r_min),
+       "pair list (autotune)");
+    int np = 0;
+    CK(cudaMemcpyAsync(&np, c->d_scalars, sizeof(int), cudaMemcpyDeviceToHost, st), "read n_pair");
+    CK(cudaStreamSynchronize(st), "autotune synchronize");
+    int widest = 1;
+    for (const auto& K : c->cands) widest = std::max(widest, std::min(K.n_clusters, c->n_slots));
+    const int K = std::max(1, std::min(np, 4 * widest));
+    CK(cudaMemcpy(c->d_scalars + 4, &K, sizeof(int), cudaMemcpyHostToDevice), "tuning count");
+    SolveParams P = c->P;
+    P.phi = orbitals;
+    P.dxx = nullptr;
+    P.pairs = c->d_pairs;
+    P.order = nullptr;
+    P.e_pair = c->d_epair;
+    P.iters = c->d_iters;
+    P.refines = c->d_refines;
+    P.dbg_b = nullptr;
+    P.phase_clk = nullptr;
+    P.n_pair = c->d_scalars + 4;
+    P.queue = c->d_scalars + 5;
+    P.nonconv = c->d_scalars + 6;
+    int best = c->cand;
+    double best_rate = -1.0;
+    auto t_start = std::chrono::steady_clock::now();
+    for (int k = 0; k < (int)c->cands.size(); ++k) {
+        apply_cand(c, k);
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {  // the first launch also loads the kernel
+            CK(cudaMemsetAsync(c->d_scalars + 5, 0, sizeof(int), st), "tuning queue");
+            CK(cudaEventRecord(c->ev[1], st), "cudaEventRecord");
+            CK(launch_cluster_kernel(c->cl_variant, P, c->CL, c->n_clusters, c->smem, st), "autotune launch");
+            CK(cudaEventRecord(c->ev[2], st), "cudaEventRecord");
+            CK(cudaStreamSynchronize(st), "autotune synchronize");
+            CK(cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]), "autotune timing");
+        }
+        c->cands[k].pairs_per_s = K / (ms * 1e-3);
+        if (c->cands[k].pairs_per_s > best_rate) {
+            best_rate = c->cands[k].pairs_per_s;
+            best = k;
+        }
+    }
+    apply_cand(c, best);
+    c->tuned = true;
+    c->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    drop_graph(c);
+    return EXX_OK;
+}
+
 extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const double* centers, int n,
                                   const double* alphas, double* e_xx, double* d_xx, void* stream) {
     if (!c) return fail(nullptr, EXX_EINVAL, "exx_compute: ctx is NULL");
@@ -625,8 +821,15 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
     cudaStream_t st = c->work;
     CK(cudaEventRecord(c->ev_in, user), "cudaEventRecord(caller stream)");
     CK(cudaStreamWaitEvent(st, c->ev_in, 0), "cudaStreamWaitEvent");
+    if (c->use_cluster && !c->tuned) {
+        s = autotune(c, orbitals, centers, alphas, n, st);
+        if (s != EXX_OK) return s;
+    }
     cudaError_t e;
-    if (c->opt.batched) {
+    if (c->opt.warm_start) {
+        s = compute_warm(c, orbitals, centers, alphas, n, d_xx, st);
+        if (s != EXX_OK) return s;
+    } else if (c->opt.batched) {
         const void* key[5] = {orbitals, centers, d_xx, alphas, nullptr};
         bool hit = c->gexec && c->g_n == n && std::equal(key, key + 5, c->g_key);
         if (!hit) {
@@ -750,6 +953,14 @@ extern "C" exx_status exx_get_stats(const exx_ctx* cc, exx_stats* out) {
         const double cyc = (double)ph[0] + (double)ph[1] + (double)ph[2] + (double)ph[3];
         for (int k = 0; k < 4; ++k)
             c->stats.phase_ms[k] = (c->use_cluster && cyc > 0.0) ? c->stats.solve_ms * (double)ph[k] / cyc : 0.0;
+    }
+    if (c->use_cluster) {
+        c->stats.solver_kind = 2;
+        c->stats.cluster_size = c->CL.C;
+        c->stats.grid_ctas = c->n_clusters * c->CL.C;
+        c->stats.threads = c->threads;
+        c->stats.lane_map = c->cands[c->cand].lane_map;
+        c->stats.tune_ms = c->tune_ms;
     }
     *out = c->stats;
     if (out->iters_max < 0) out->iters_max = 0;

@@ -34,7 +34,7 @@ class exx_options(ctypes.Structure):
                 ("radii_mode", ctypes.c_int), ("max_iter", ctypes.c_int), ("inner_max_iter", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("solver_kind", ctypes.c_int), ("cluster_size", ctypes.c_int), ("update_drop", ctypes.c_double),
-                ("lane_map", ctypes.c_int)]
+                ("lane_map", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class exx_stats(ctypes.Structure):
@@ -43,7 +43,8 @@ class exx_stats(ctypes.Structure):
                 ("point_iters", ctypes.c_longlong), ("refine_max", ctypes.c_int), ("solve_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("n_pe", ctypes.c_int), ("n_me", ctypes.c_int),
                 ("solver_kind", ctypes.c_int), ("cluster_size", ctypes.c_int), ("grid_ctas", ctypes.c_int),
-                ("threads", ctypes.c_int), ("phase_ms", ctypes.c_double * 4)]
+                ("threads", ctypes.c_int), ("phase_ms", ctypes.c_double * 4), ("lane_map", ctypes.c_int),
+                ("n_candidates", ctypes.c_int), ("tune_ms", ctypes.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
