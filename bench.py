@@ -35,13 +35,17 @@ UNIT = "pair solves/s"
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of a GB300 (profiling recipe table)
 
 
+SMEM_BYTES_PER_CLK_SM = 128  # shared-memory bandwidth of one SM (32 banks x 4 B per clock)
+
+
 def _peaks():
+    """HBM GB/s and the maximum SM clock (MHz) with their source."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return float(d.get("hbm_gbs", 6800.0)), "measured"
-    return 6800.0, "fallback"
+        return float(d.get("hbm_gbs", 6800.0)), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
 
 
 def _kernel_hash():
@@ -125,22 +129,21 @@ def _dist():
 
 
 def _algorithmic(pairs, stats, n_pe, n_me, precision):
-    """Algorithmic DRAM bytes and FLOPs of one pair-kernel launch (per-pair
-    figures times the pairs; see the design notes for the derivation)."""
+    """Algorithmic bytes and FLOPs of one pair-kernel launch: per-unit figures
+    times the units the launch processed (the design notes derive each).
+
+    smem: the CG keeps every vector on chip; each point-iteration reads the
+      19 stencil operands of p and stores p once (80 B in FP32).
+    hbm: per pair, the gather of phi_i, phi_j on the ME ball (16 B per point),
+      the D_xx read-modify-write of one or two orbitals on the ME ball
+      (16 or 32 B per point) and one more read of phi_i, phi_j for the scatter.
+    flops: 38 per point-iteration (19-point stencil and the CG updates)."""
     it = pairs["iters"].astype(np.float64)
-    npair = len(it)
-    s = 4 if precision == 1 else 8
-    cg_bytes = 6.0 * s * n_pe * it.sum()                    # d, r, p read + written once per iteration
-    refines = stats.get("refine_max", 1)
-    res_evals = npair * (1 + (2 if precision == 1 else 0))  # b, plus about two FP64 residuals per pair
-    res_bytes = 24.0 * n_pe * res_evals
+    point_iters = float(stats.get("point_iters") or n_pe * it.sum())
     two = (pairs["i"] != pairs["j"]).astype(np.float64)
-    gather = 16.0 * n_pe * npair
-    shell = 8.0 * (n_me - n_pe) * npair
-    scatter = float(np.sum((24.0 + 24.0 * two) * n_me))
-    flops = 38.0 * n_pe * it.sum()
-    return dict(bytes=cg_bytes + res_bytes + gather + shell + scatter, cg_bytes=cg_bytes, flops=flops,
-                refines=refines)
+    hbm = float(np.sum((16.0 + 16.0 + 16.0 * (1.0 + two)) * n_me))
+    s = 4 if precision == 1 else 8
+    return dict(smem=20.0 * s * point_iters, hbm=hbm, flops=38.0 * point_iters, point_iters=point_iters)
 
 
 def run_oracle_sample(w, phi, pairs_all, seconds=12.0, seed=0):
@@ -286,17 +289,28 @@ def main():
     n_pe, n_me = ex.ball_size()
     alg = _algorithmic(pairs, st, n_pe, n_me, args.precision)
     kern_ms = statistics.mean(solve_ms)
-    hbm_peak, peak_src = _peaks()
-    achieved = alg["bytes"] / (kern_ms / 1e3) / 1e9
+    hbm_peak, sm_mhz_max, peak_src = _peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     workload_key = f"{w.name}|p{args.precision}"
-    roofline = {"kernel": "pair_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "peak_source": peak_src,
-                "traffic": _traffic("pair_kernel", workload_key),
-                "algorithmic_bytes_per_launch": alg["bytes"], "kernel_ms": kern_ms}
-    if args.precision == 0:
+    if args.precision == 1:
+        kname = "cluster_pair_kernel" if st["solver_kind"] == 2 else "pair_kernel"
+        smem_peak = n_sm * SMEM_BYTES_PER_CLK_SM * sm_mhz_max * 1e6 / 1e9
+        achieved = alg["smem"] / (kern_ms / 1e3) / 1e9
+        roofline = {"kernel": kname, "bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
+                    "frac": achieved / smem_peak,
+                    "peak_source": f"{n_sm} SMs x {SMEM_BYTES_PER_CLK_SM} B/clk x {sm_mhz_max:.0f} MHz "
+                                   f"(max SM clock, {peak_src})",
+                    "algorithmic_bytes_per_launch": alg["smem"], "bytes_per_point_iteration": 80,
+                    "traffic": _traffic(kname, workload_key),
+                    "hbm": {"algorithmic_bytes_per_launch": alg["hbm"],
+                            "achieved": alg["hbm"] / (kern_ms / 1e3) / 1e9, "peak": hbm_peak,
+                            "peak_source": peak_src},
+                    "kernel_ms": kern_ms}
+    else:
         fl = alg["flops"] / (kern_ms / 1e3) / 1e12
-        roofline.update({"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": fl / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64 rate"})
+        roofline = {"kernel": "pair_kernel", "bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": fl / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64 rate",
+                    "traffic": _traffic("pair_kernel", workload_key), "kernel_ms": kern_ms}
 
     extra = {}
     if rank == 0 and args.precision == 1 and args.plain_steps > 0:

@@ -82,6 +82,51 @@ __device__ __noinline__ double cta_energy(const int* __restrict__ cube, const do
     return e;
 }
 
+// The previous call's list position of pair (i, j), or -1 (lists are i-major, j ascending).
+__device__ __forceinline__ int find_prev_pair(const PairRec* __restrict__ prev, int n, int i, int j) {
+    int lo = 0, hi = n - 1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const PairRec q = prev[mid];
+        if (q.i == i && q.j == j) return mid;
+        if (q.i < i || (q.i == i && q.j < j)) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+// Warm start: v on the CTA's PE points from the previous call's potential of
+// the same pair. Its grid centre moved by dlt, so the point at offset o now
+// held the old offset o + dlt; where that leaves the PE ball the old value at
+// o itself is taken.
+__device__ __noinline__ void cta_warm_insert(const BallGeo& G, const int* __restrict__ cube, double* __restrict__ vc,
+                                             const float* __restrict__ vold, int dx, int dy, int dz, int k0, int k1,
+                                             int nt) {
+    const int R = G.r_pe, W = 2 * G.r_pe + 1;
+    const int* __restrict__ off = G.pt_off;
+    const int* __restrict__ row_of = G.row_of;
+    const RowRec* __restrict__ rows = G.rows_pe;
+    for (int k = k0 + (int)threadIdx.x; k < k1; k += nt) {
+        const int o = off[k];
+        const int x = off_x(o) + dx, y = off_y(o) + dy, z = off_z(o) + dz;
+        int src = k;
+        if (x >= -R && x <= R && y >= -R && y <= R) {
+            const int rr = row_of[(x + R) * W + (y + R)];
+            if (rr >= 0) {
+                const RowRec Rw = rows[rr];
+                if (z >= -Rw.zpe && z <= Rw.zpe) src = Rw.pe_start + z + Rw.zpe;
+            }
+        }
+        vc[cube[k]] = (double)vold[src];
+    }
+}
+
+// Stores v on the CTA's PE points (FP32) for the next call's warm start.
+__device__ __noinline__ void cta_warm_store(const int* __restrict__ cube, const double* __restrict__ vc,
+                                            float* __restrict__ vdst, int k0, int k1, int nt) {
+    for (int k = k0 + (int)threadIdx.x; k < k1; k += nt) vdst[k] = (float)vc[cube[k]];
+}
+
 template <int NT, int C, int PTS>
 __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P, const ClusterLayout CL) {
     cg::cluster_group cl = cg::this_cluster();
@@ -171,8 +216,32 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
         if (clk) tr += clock64() - t1;
         int iters = 0, refines = 1;
         bool conv = true;
-        if (bb > target2 && bb == bb) {
-            double scale = sqrt(bb);
+        double rn_start = bb;
+        if (P.warm && bb > target2 && bb == bb) {
+            const int prev = find_prev_pair(P.prev_pairs, *P.n_prev, pr.i, pr.j);
+            if (prev >= 0) {
+                const PairRec po = P.prev_pairs[prev];
+                int dlt[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    int d = pr.g[a] - po.g[a];
+                    if (d > P.N[a] / 2) d -= P.N[a];
+                    if (d < -(P.N[a] - 1) / 2) d += P.N[a];
+                    dlt[a] = d;
+                }
+                if (abs(dlt[0]) <= 3 && abs(dlt[1]) <= 3 && abs(dlt[2]) <= 3) {
+                    const long long tu = clk ? clock64() : 0;
+                    cta_warm_insert(G, cube, vc, P.vprev + (size_t)prev * G.n_pe, dlt[0], dlt[1], dlt[2], k0, k1, NT);
+                    cl.sync();
+                    acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, false);
+                    rn_start = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
+                    ++refines;
+                    if (clk) tr += clock64() - tu;
+                }
+            }
+        }
+        if (rn_start > target2 && rn_start == rn_start) {
+            double scale = sqrt(rn_start);
             float r[PTS], ap[PTS];
             float a32 = 0.0f;
             {
@@ -295,7 +364,8 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
         }
         const long long t2 = clk ? clock64() : 0;
 
-        // E_ij and the scatter
+        // E_ij, the warm-start cache and the scatter
+        if (P.vcur) cta_warm_store(cube, vc, P.vcur + (size_t)pidx * G.n_pe, k0, k1, NT);
         double e = cta_energy(cube, rho, vc, k0, k1, NT);
         e = cluster_sum<NT, C, double>(e, red, flip, part, cflip, cl, rank);
         if (rank == 0 && threadIdx.x == 0) {

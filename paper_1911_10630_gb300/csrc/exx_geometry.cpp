@@ -110,6 +110,7 @@ void build_ball(HostBall& B, int r_pe, int r_me, int Rc) {
     B.off.clear();
     B.rows_pe.clear();
     B.rows_me.clear();
+    B.row_of.clear();
     B.plane_pe.assign(2 * r_pe + 2, 0);
     auto cube = [&](int x, int y, int z) { return ((x + Rc) * S + (y + Rc)) * S + (z + Rc); };
     // PE ball, lexicographic (Algorithm 2, first list)
@@ -135,6 +136,9 @@ void build_ball(HostBall& B, int r_pe, int r_me, int Rc) {
     }
     B.plane_pe[2 * r_pe + 1] = (int)B.rows_pe.size();
     B.n_pe = (int)B.cube.size();
+    B.row_of.assign((size_t)(2 * r_pe + 1) * (2 * r_pe + 1), -1);
+    for (int rr = 0; rr < (int)B.rows_pe.size(); ++rr)
+        B.row_of[(size_t)(B.rows_pe[rr].ox + r_pe) * (2 * r_pe + 1) + (B.rows_pe[rr].oy + r_pe)] = rr;
     // shell, lexicographic (Algorithm 2, second list); rows of the ME ball
     int pe_row = 0;
     for (int x = -r_me; x <= r_me; ++x)

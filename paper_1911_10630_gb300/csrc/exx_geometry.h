@@ -14,6 +14,7 @@ struct HostBall {
     std::vector<RowRec> rows_pe;    // PE rows, lexicographic
     std::vector<RowRec> rows_me;    // ME rows, lexicographic
     std::vector<int> plane_pe;      // [2 r_pe + 2]
+    std::vector<int> row_of;        // [(2 r_pe + 1)^2] PE row of (ox, oy) or -1
 };
 
 void build_multipole_const(MultipoleConst& mc);

@@ -41,6 +41,7 @@ struct BallGeo {
     const RowRec* rows_pe;   // [n_rows_pe]
     const RowRec* rows_me;   // [n_rows_me]
     const int* plane_pe;     // [2 r_pe + 2] first PE row of each x plane (last = n_rows_pe)
+    const int* row_of;       // [(2 r_pe + 1)^2] PE row index of (ox, oy), -1 outside
 };
 
 // 19-point Laplacian coefficients of Eq. d2_1 on an orthorhombic grid:
@@ -100,6 +101,13 @@ struct SolveParams {
     const double* x0_cache;   // [n_pair_cap][n_pe] previous solutions (fixed radii)
     double* x_cache_out;      // write solutions here (may alias nothing)
     const int* x0_valid;      // [n_pair] 1 when x0_cache row is this pair's previous solution
+
+    // warm start from the previous call (cluster solver, fixed radii)
+    int warm;                     // 1: look the pair up in prev_pairs and start from its cached v
+    const PairRec* prev_pairs;    // previous call's pair list (i-major, j ascending)
+    const int* n_prev;            // its length (device)
+    const float* vprev;           // [n_prev][n_pe] previous PE potentials
+    float* vcur;                  // [n_pair][n_pe] this call's PE potentials (written)
 
     // outputs
     double* e_pair;

@@ -270,3 +270,38 @@ def test_batched_uneven_full_size_sampled(torch):
     orc2 = oracle.exx(w.cell, w.grid, phi, sub2, w.r_pe, w.r_me, w.l_max, tol=1e-13, want_d=True, dmask=mask)
     den = np.max(np.abs(orc2["D"][orb]))
     assert np.max(np.abs(out["D"][orb] - orc2["D"][orb])) <= D_GATE_MAXREL * den
+
+
+# --------------------------------------------------------------------------
+# Warm start from the previous call (MD-like sequences)
+# --------------------------------------------------------------------------
+
+def test_warm_start_from_previous_step(torch):
+    """Two consecutive calls on drifted inputs (centres + N(0, 0.02^2) bohr,
+    alpha x (1 + 0.01 xi)): the second starts each kept pair from the first
+    call's potential (shifted where its grid centre moved), meets the same
+    accuracy gates and needs fewer CG iterations than a cold start."""
+    import copy
+    from paper_1911_10630_gb300.exx import Exx
+    w0 = synth.config0()
+    rng = np.random.default_rng(21)
+    w1 = copy.deepcopy(w0)
+    w1.centers = np.mod(w0.centers + rng.normal(0.0, 0.02, size=w0.centers.shape), w0.cell)
+    w1.alphas = w0.alphas * (1.0 + 0.01 * rng.normal(size=w0.n))
+    phi0, phi1 = w0.orbitals(), w1.orbitals()
+    ex = Exx(w0.cell, w0.grid, w0.r_pair, w0.r_pe, w0.r_me, 6, w0.tol, precision=1, warm_start=1)
+    dD = torch.empty(phi0.shape, dtype=torch.float64, device="cuda")
+    for w, phi in ((w0, phi0), (w1, phi1)):
+        e = ex.compute(torch.from_numpy(phi).cuda(), torch.from_numpy(np.ascontiguousarray(w.centers)).cuda(), dD)
+    warm_iters = ex.stats()["iters_total"]
+    D = dD.cpu().numpy()
+    ref = oracle.exx_workload(w1, tol=1e-13, orbitals=phi1)
+    assert abs(e - ref["E_xx"]) / w1.n <= E_GATE_PER_ORBITAL
+    assert d_maxrel(D, ref["D"]) <= D_GATE_MAXREL
+    cold = run_gpu(w1, phi1, torch=torch, precision=1)
+    assert warm_iters < 0.97 * cold["stats"]["iters_total"], (warm_iters, cold["stats"]["iters_total"])
+    i0, j0, g0 = oracle.pair_list(w0.centers, w0.cell, w0.grid, w0.r_pair)
+    i1, j1, g1 = oracle.pair_list(w1.centers, w1.cell, w1.grid, w1.r_pair)
+    before = {(a, b): g for a, b, g in zip(i0.tolist(), j0.tolist(), g0.tolist())}
+    moved = [k for k, g in zip(zip(i1.tolist(), j1.tolist()), g1.tolist()) if k in before and before[k] != g]
+    assert moved  # some kept pairs' grid centres moved: the shifted start was exercised
