@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libexx_gb300.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["exx_api.cu", "exx_pairs.cu", "exx_solve.cu", "exx_cluster.cu", "exx_static.cu", "exx_geometry.cpp"]
+SOURCES = ["exx_api.cu", "exx_pairs.cu", "exx_solve.cu", "exx_cluster.cu", "exx_static.cu", "exx_unet.cu",
+           "exx_geometry.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,7 +40,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "exx.h"), __file__]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", f) for f in
+                                                          os.listdir(os.path.join(ROOT, "include"))] + [__file__]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 

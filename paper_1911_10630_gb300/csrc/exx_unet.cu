@@ -1,0 +1,959 @@
+// exx_unet.cu -- the learned CG warm start: a 3D U-Net that maps the pair
+// density rho_ij on a cube around the pair centre to a guess of v_ij.
+//
+// The paper starts each CG from a guess and names better guesses as the way to
+// fewer iterations (Sec. III.C Step IV and the conclusions); the network is
+// this library's own addition. Four levels (widths 16/32/64/128), two 3x3x3
+// convolutions per level with ReLU, 2x2x2 average pooling down, nearest
+// up-sampling and concatenation with the skip tensor up, a 1x1x1 head.
+// Activations and weights are BF16 in channels-last layout, accumulation FP32.
+//
+// The 3x3x3 convolutions (all but the 2-channel input layer) are implicit GEMMs
+// on the tcgen05 tensor cores: one CTA computes a 16 (H) x 8 (W) x DT (D)
+// output tile for all output channels, the input halo tile and the weights of
+// one 16-channel chunk are staged in shared memory as 8-row core matrices, and
+// each of the 27 taps is one MMA (M = 128 voxels, N = cout, K = 16) whose A
+// operand is the same staged tile seen through a shifted descriptor. The
+// accumulators live in tensor memory and are read back with tcgen05.ld for
+// the bias / ReLU / mask epilogue.
+#include "exx_unet.cuh"
+#include "exx_unet_tc.cuh"
+
+#include <cmath>
+#include <cstring>
+
+namespace exx {
+namespace unet {
+
+namespace {
+
+constexpr int kTH = 16, kTW = 8, kHH = kTH + 2, kWW = kTW + 2;
+constexpr int kWaitLimit = 1 << 22;
+
+__device__ __forceinline__ float bf2f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ __nv_bfloat16 f2bf(float v) { return __float2bfloat16_rn(v); }
+
+struct ConvArgs {
+    const __nv_bfloat16* x;
+    const __nv_bfloat16* wp;
+    const float* bias;
+    const __nv_bfloat16* mask;
+    __nv_bfloat16* y;
+    int B, D, H, W, cin, cout;
+    int epi, DT, ncols, nbuf;
+    int tiles_d, tiles_h, tiles_w;
+    uint32_t itile, wtile, stage;
+    int* err;
+};
+
+__global__ void __launch_bounds__(128) conv3_tc_kernel(const ConvArgs a) {
+    extern __shared__ unsigned char smem_dyn[];
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t s_tmem;
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int t = blockIdx.x;
+    const int tw = t % a.tiles_w;
+    t /= a.tiles_w;
+    const int th = t % a.tiles_h;
+    t /= a.tiles_h;
+    const int td = t % a.tiles_d;
+    const int b = t / a.tiles_d;
+    const int DT = a.DT;
+    const int d0 = td * DT, h0 = th * kTH, w0 = tw * kTW;
+
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        tc::mbar_init_fence();
+    }
+    if (warp == 0) tc::tmem_alloc(&s_tmem, (uint32_t)a.ncols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = s_tmem;
+
+    const int nch = a.cin / 16;
+    const uint32_t idesc = tc::idesc_bf16_f32(128, a.cout);
+    const int nvox = (DT + 2) * kHH * kWW;
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+        const int s = a.nbuf == 2 ? (c & 1) : 0;
+        unsigned char* st = base + (size_t)s * a.stage;
+        if (c >= a.nbuf) {  // the MMAs of chunk c - nbuf read this buffer
+            const int prev = c - a.nbuf;
+            if (!tc::mbar_wait(&mbar[s], (uint32_t)((prev / a.nbuf) & 1), kWaitLimit)) ok = false;
+        }
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        // input halo tile: two channel octets, [DT+2][18][10] voxels x 16 B each
+        for (int u = tid; u < 2 * nvox; u += 128) {
+            const int o = u >= nvox ? 1 : 0;
+            const int vx = u - o * nvox;
+            const int wx = vx % kWW, r2 = vx / kWW, hy = r2 % kHH, dz = r2 / kHH;
+            const int d = d0 - 1 + dz, h = h0 - 1 + hy, w = w0 - 1 + wx;
+            const bool in = d >= 0 && d < a.D && h >= 0 && h < a.H && w >= 0 && w < a.W;
+            const __nv_bfloat16* src =
+                in ? a.x + ((((size_t)b * a.D + d) * a.H + h) * a.W + w) * a.cin + c * 16 + o * 8 : a.x;
+            tc::cp_async16(st + (size_t)o * a.itile + (size_t)vx * 16, src, in ? 16u : 0u);
+        }
+        // weights of chunk c: [27][cout/8][2][8][8] BF16, contiguous
+        const unsigned char* wsrc = reinterpret_cast<const unsigned char*>(a.wp) + (size_t)c * a.wtile;
+        unsigned char* wdst = st + 2 * (size_t)a.itile;
+        for (uint32_t u = tid; u < a.wtile / 16; u += 128) tc::cp_async16(wdst + u * 16, wsrc + u * 16, 16u);
+        tc::cp_async_wait_all();
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t sa = tc::smem_addr(st), sw = tc::smem_addr(wdst);
+            for (int tt = 0; tt < DT; ++tt) {
+#pragma unroll 1
+                for (int tap = 0; tap < 27; ++tap) {
+                    const int dd = tap / 9, dh = (tap / 3) % 3, dw = tap % 3;
+                    const uint32_t aoff = (uint32_t)((((tt + dd) * kHH + dh) * kWW + dw) * 16);
+                    const uint64_t ad = tc::sdesc(sa + aoff, a.itile, kWW * 16);
+                    const uint64_t bd = tc::sdesc(sw + (uint32_t)(tap * a.cout * 32), 128, 256);
+                    tc::mma_bf16(tbase + (uint32_t)(tt * a.cout), ad, bd, idesc, (c > 0 || tap > 0) ? 1u : 0u);
+                }
+            }
+            tc::commit(&mbar[s]);
+        }
+    }
+    if (ok) {
+        const int last = nch - 1, s = a.nbuf == 2 ? (last & 1) : 0;
+        if (!tc::mbar_wait(&mbar[s], (uint32_t)((last / a.nbuf) & 1), kWaitLimit)) ok = false;
+    }
+    ok = __syncthreads_and(ok);
+    tc::fence_after_sync();
+    if (ok) {
+        const int m = warp * 32 + lane;  // accumulator row = TMEM lane
+        const int h = h0 + (m >> 3), w = w0 + (m & 7);
+        for (int tt = 0; tt < DT; ++tt) {
+            const int d = d0 + tt;
+            const bool live = d < a.D && h < a.H && w < a.W;
+            const size_t vox = (((size_t)b * a.D + d) * a.H + h) * a.W + w;
+            for (int c0 = 0; c0 < a.cout; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(tt * a.cout + c0), v);
+                if (!live) continue;
+                if (a.bias) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) v[k] += a.bias[c0 + k];
+                }
+                if (a.epi == 1) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) v[k] = fmaxf(v[k], 0.0f);
+                } else if (a.epi == 2) {
+                    const uint4* mp = reinterpret_cast<const uint4*>(a.mask + vox * a.cout + c0);
+                    uint4 mm[2] = {mp[0], mp[1]};
+                    const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(mm);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) v[k] = bf2f(mb[k]) > 0.0f ? v[k] : 0.0f;
+                }
+                uint4 o[2];
+                __nv_bfloat16* ob = reinterpret_cast<__nv_bfloat16*>(o);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) ob[k] = f2bf(v[k]);
+                uint4* yp = reinterpret_cast<uint4*>(a.y + vox * a.cout + c0);
+                yp[0] = o[0];
+                yp[1] = o[1];
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(a.err, 1);
+        // let MMAs still in flight finish before the tensor memory goes back
+        tc::mbar_wait(&mbar[0], 0, 1024);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tbase, (uint32_t)a.ncols);
+}
+
+// ---- packing ---------------------------------------------------------------
+
+// Packed operand: [K/16][27][N/8][2][8 n][8 k], k = 16 chunk + 8 half + e.
+// Forward: K = cin, N = cout, value W[tap][k][n]. Data gradient (flip): the
+// convolution maps cout -> cin channels, K = cout, N = cin, value
+// W[26 - tap][n][k].
+__global__ void pack_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wp, int cin, int cout,
+                            int flip) {
+    const int K = flip ? cout : cin, N = flip ? cin : cout;
+    const long long total = 27LL * K * N;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long r = idx;
+        const int e = (int)(r % 8);
+        r /= 8;
+        const int nl = (int)(r % 8);
+        r /= 8;
+        const int half = (int)(r % 2);
+        r /= 2;
+        const int ng = (int)(r % (N / 8));
+        r /= (N / 8);
+        const int tap = (int)(r % 27);
+        const int chunk = (int)(r / 27);
+        const int k = chunk * 16 + half * 8 + e, n = ng * 8 + nl;
+        const float v = flip ? w[((size_t)(26 - tap) * cin + n) * cout + k] : w[((size_t)tap * cin + k) * cout + n];
+        wp[idx] = f2bf(v);
+    }
+}
+
+// ---- CUDA-core layers ------------------------------------------------------
+
+// Input layer: 2 FP32 channels -> 16, ReLU. One thread per output voxel.
+__global__ void conv_first_kernel(const float* __restrict__ in, const float* __restrict__ w,
+                                  const float* __restrict__ bias, __nv_bfloat16* __restrict__ y, int B, int S) {
+    __shared__ float ws[27 * 2 * 16 + 16];
+    for (int i = threadIdx.x; i < 27 * 32; i += blockDim.x) ws[i] = w[i];
+    if (threadIdx.x < 16) ws[27 * 32 + threadIdx.x] = bias[threadIdx.x];
+    __syncthreads();
+    const long long nv = (long long)B * S * S * S;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(v % S), yy = (int)((v / S) % S), z = (int)((v / ((long long)S * S)) % S);
+        const long long bb = v / ((long long)S * S * S);
+        float acc[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = ws[27 * 32 + c];
+        for (int tap = 0; tap < 27; ++tap) {
+            const int zz = z + tap / 9 - 1, y2 = yy + (tap / 3) % 3 - 1, x2 = x + tap % 3 - 1;
+            if (zz < 0 || zz >= S || y2 < 0 || y2 >= S || x2 < 0 || x2 >= S) continue;
+            const float2 iv = reinterpret_cast<const float2*>(in)[((bb * S + zz) * S + y2) * S + x2];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] = fmaf(iv.x, ws[tap * 32 + c], fmaf(iv.y, ws[tap * 32 + 16 + c], acc[c]));
+        }
+        uint4 o[2];
+        __nv_bfloat16* ob = reinterpret_cast<__nv_bfloat16*>(o);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) ob[c] = f2bf(fmaxf(acc[c], 0.0f));
+        uint4* yp = reinterpret_cast<uint4*>(y + v * 16);
+        yp[0] = o[0];
+        yp[1] = o[1];
+    }
+}
+
+// 1x1x1 head: out = b + sum_c y0[c] w[c] (FP32).
+__global__ void head_kernel(const __nv_bfloat16* __restrict__ y0, const float* __restrict__ hw, float* __restrict__ out,
+                            long long nv) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
+         v += (long long)gridDim.x * blockDim.x) {
+        const uint4* p = reinterpret_cast<const uint4*>(y0 + v * 16);
+        uint4 q[2] = {p[0], p[1]};
+        const __nv_bfloat16* qb = reinterpret_cast<const __nv_bfloat16*>(q);
+        float acc = hw[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc = fmaf(bf2f(qb[c]), hw[c], acc);
+        out[v] = acc;
+    }
+}
+
+// Loss L = sum_v m_v (out_v - t_v)^2 / (B S^3), m_v = input mask channel; the
+// head's gradients, and the gradient at y0 masked by ReLU (y0 > 0).
+__global__ void head_backward_kernel(const float* __restrict__ in, const float* __restrict__ target,
+                                     const float* __restrict__ out, const __nv_bfloat16* __restrict__ y0,
+                                     const float* __restrict__ hw, float* __restrict__ ghw,
+                                     __nv_bfloat16* __restrict__ g_y0, float* __restrict__ loss, long long nv,
+                                     float inv_n) {
+    __shared__ float red[17][8];
+    float lsum = 0.0f, gw[17];
+#pragma unroll
+    for (int c = 0; c < 17; ++c) gw[c] = 0.0f;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
+         v += (long long)gridDim.x * blockDim.x) {
+        const float m = in[2 * v + 1] > 0.5f ? 1.0f : 0.0f;
+        const float diff = out[v] - target[v];
+        lsum += m * diff * diff;
+        const float g = 2.0f * m * diff * inv_n;
+        const uint4* p = reinterpret_cast<const uint4*>(y0 + v * 16);
+        uint4 q[2] = {p[0], p[1]};
+        const __nv_bfloat16* qb = reinterpret_cast<const __nv_bfloat16*>(q);
+        uint4 o[2];
+        __nv_bfloat16* ob = reinterpret_cast<__nv_bfloat16*>(o);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const float yv = bf2f(qb[c]);
+            gw[c] = fmaf(g, yv, gw[c]);
+            ob[c] = f2bf(yv > 0.0f ? g * hw[c] : 0.0f);
+        }
+        gw[16] += g;
+        uint4* gp = reinterpret_cast<uint4*>(g_y0 + v * 16);
+        gp[0] = o[0];
+        gp[1] = o[1];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 17; ++c) {
+        float s = gw[c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[c][wid] = s;
+    }
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    __shared__ float lred[8];
+    if (lane == 0) lred[wid] = lsum;
+    __syncthreads();
+    if (threadIdx.x < 17) {
+        float s = 0.0f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[threadIdx.x][k];
+        atomicAdd(&ghw[threadIdx.x], s);
+    }
+    if (threadIdx.x == 32) {
+        float s = 0.0f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += lred[k];
+        atomicAdd(loss, s * inv_n);
+    }
+}
+
+// 2x2x2 average pooling, channels last; one thread per (coarse voxel, 8 channels).
+__global__ void pool_kernel(const __nv_bfloat16* __restrict__ x, __nv_bfloat16* __restrict__ y, int B, int S, int C) {
+    const int s = S / 2, g8 = C / 8;
+    const long long total = (long long)B * s * s * s * g8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(i % g8);
+        long long p = i / g8;
+        const int px = (int)(p % s), py = (int)((p / s) % s), pz = (int)((p / ((long long)s * s)) % s);
+        const long long bb = p / ((long long)s * s * s);
+        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = 0; k < 8; ++k) {
+            const long long v = ((bb * S + 2 * pz + (k >> 2)) * S + 2 * py + ((k >> 1) & 1)) * S + 2 * px + (k & 1);
+            const uint4 q = *reinterpret_cast<const uint4*>(x + v * C + g * 8);
+            const __nv_bfloat16* qb = reinterpret_cast<const __nv_bfloat16*>(&q);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] += bf2f(qb[c]);
+        }
+        uint4 o;
+        __nv_bfloat16* ob = reinterpret_cast<__nv_bfloat16*>(&o);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) ob[c] = f2bf(0.125f * acc[c]);
+        *reinterpret_cast<uint4*>(y + p * C + g * 8) = o;
+    }
+}
+
+// cat[v] = (low[parent(v)], skip[v]); fine side S, low has Cl channels, skip Cs.
+__global__ void upcat_kernel(const __nv_bfloat16* __restrict__ low, const __nv_bfloat16* __restrict__ skip,
+                             __nv_bfloat16* __restrict__ cat, int B, int S, int Cl, int Cs) {
+    const int C = Cl + Cs, g8 = C / 8, s = S / 2;
+    const long long total = (long long)B * S * S * S * g8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(i % g8);
+        const long long v = i / g8;
+        const int x = (int)(v % S), y = (int)((v / S) % S), z = (int)((v / ((long long)S * S)) % S);
+        const long long bb = v / ((long long)S * S * S);
+        uint4 q;
+        if (g * 8 < Cl) {
+            const long long p = ((bb * s + z / 2) * s + y / 2) * s + x / 2;
+            q = *reinterpret_cast<const uint4*>(low + p * Cl + g * 8);
+        } else {
+            q = *reinterpret_cast<const uint4*>(skip + v * Cs + g * 8 - Cl);
+        }
+        *reinterpret_cast<uint4*>(cat + v * C + g * 8) = q;
+    }
+}
+
+// Gradient at the up-sampled input: dlow[p] = sum over the 8 children of
+// dcat[child][0:Cl], masked by ReLU (low > 0).
+__global__ void upcat_back_low_kernel(const __nv_bfloat16* __restrict__ dcat, const __nv_bfloat16* __restrict__ low,
+                                      __nv_bfloat16* __restrict__ dlow, int B, int S, int Cl, int Cs) {
+    const int C = Cl + Cs, s = S / 2, g8 = Cl / 8;
+    const long long total = (long long)B * s * s * s * g8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(i % g8);
+        const long long p = i / g8;
+        const int px = (int)(p % s), py = (int)((p / s) % s), pz = (int)((p / ((long long)s * s)) % s);
+        const long long bb = p / ((long long)s * s * s);
+        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = 0; k < 8; ++k) {
+            const long long v = ((bb * S + 2 * pz + (k >> 2)) * S + 2 * py + ((k >> 1) & 1)) * S + 2 * px + (k & 1);
+            const uint4 q = *reinterpret_cast<const uint4*>(dcat + v * C + g * 8);
+            const __nv_bfloat16* qb = reinterpret_cast<const __nv_bfloat16*>(&q);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] += bf2f(qb[c]);
+        }
+        const uint4 lq = *reinterpret_cast<const uint4*>(low + p * Cl + g * 8);
+        const __nv_bfloat16* lb = reinterpret_cast<const __nv_bfloat16*>(&lq);
+        uint4 o;
+        __nv_bfloat16* ob = reinterpret_cast<__nv_bfloat16*>(&o);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) ob[c] = f2bf(bf2f(lb[c]) > 0.0f ? acc[c] : 0.0f);
+        *reinterpret_cast<uint4*>(dlow + p * Cl + g * 8) = o;
+    }
+}
+
+// Gradient at a skip tensor: from the pooling (dpool[parent] / 8) and from the
+// concatenation (dcat[v][Cl:]), masked by ReLU (skip > 0).
+__global__ void skip_back_kernel(const __nv_bfloat16* __restrict__ dpool, const __nv_bfloat16* __restrict__ dcat,
+                                 const __nv_bfloat16* __restrict__ skip, __nv_bfloat16* __restrict__ dskip, int B,
+                                 int S, int Cl, int Cs) {
+    const int C = Cl + Cs, s = S / 2, g8 = Cs / 8;
+    const long long total = (long long)B * S * S * S * g8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(i % g8);
+        const long long v = i / g8;
+        const int x = (int)(v % S), y = (int)((v / S) % S), z = (int)((v / ((long long)S * S)) % S);
+        const long long bb = v / ((long long)S * S * S);
+        const long long p = ((bb * s + z / 2) * s + y / 2) * s + x / 2;
+        const uint4 a = *reinterpret_cast<const uint4*>(dpool + p * Cs + g * 8);
+        const uint4 c = *reinterpret_cast<const uint4*>(dcat + v * C + Cl + g * 8);
+        const uint4 k = *reinterpret_cast<const uint4*>(skip + v * Cs + g * 8);
+        const __nv_bfloat16 *ab = reinterpret_cast<const __nv_bfloat16*>(&a),
+                            *cb = reinterpret_cast<const __nv_bfloat16*>(&c),
+                            *kb = reinterpret_cast<const __nv_bfloat16*>(&k);
+        uint4 o;
+        __nv_bfloat16* ob = reinterpret_cast<__nv_bfloat16*>(&o);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) ob[e] = f2bf(bf2f(kb[e]) > 0.0f ? 0.125f * bf2f(ab[e]) + bf2f(cb[e]) : 0.0f);
+        *reinterpret_cast<uint4*>(dskip + v * Cs + g * 8) = o;
+    }
+}
+
+// Weight gradient of a 3x3x3 layer: dW[tap][ci][co] += sum over samples and
+// voxels of x[v + tap - 1][ci] g[v][co]; the centre-tap blocks of the first ci
+// block also accumulate the bias gradient. Block = 16 x 16 (ci, co); grid.x =
+// tap, grid.y = ci block, grid.z = co block x voxel split.
+constexpr int kDwTile = 64;
+__global__ void __launch_bounds__(256) dw_kernel(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ g,
+                                                 float* __restrict__ dw, float* __restrict__ db, int B, int S, int cin,
+                                                 int cout, int nsplit) {
+    __shared__ float xs[kDwTile][17];
+    __shared__ float gs[kDwTile][17];
+    const int tap = blockIdx.x, cib = blockIdx.y;
+    const int cob = blockIdx.z % (cout / 16), split = blockIdx.z / (cout / 16);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const long long nv = (long long)B * S * S * S;
+    const long long per = ((nv + nsplit - 1) / nsplit + kDwTile - 1) / kDwTile * kDwTile;
+    const long long v0 = split * per, v1 = v0 + per < nv ? v0 + per : nv;
+    float acc = 0.0f, bacc = 0.0f;
+    const bool do_bias = (tap == 13 && cib == 0);
+    for (long long vt = v0; vt < v1; vt += kDwTile) {
+        {   // 64 voxels x 16 channels of x (shifted) and g: each thread loads 4 channels of one voxel
+            const int vl = threadIdx.x >> 2, cq = (threadIdx.x & 3) * 4;
+            const long long v = vt + vl;
+            float xv[4] = {0, 0, 0, 0}, gv[4] = {0, 0, 0, 0};
+            if (v < v1) {
+                const int xx = (int)(v % S), yy = (int)((v / S) % S), zz = (int)((v / ((long long)S * S)) % S);
+                const long long bb = v / ((long long)S * S * S);
+                const int z2 = zz + dz, y2 = yy + dy, x2 = xx + dx;
+                if (z2 >= 0 && z2 < S && y2 >= 0 && y2 < S && x2 >= 0 && x2 < S) {
+                    const long long u = ((bb * S + z2) * S + y2) * S + x2;
+                    const uint2 q = *reinterpret_cast<const uint2*>(x + u * cin + cib * 16 + cq);
+                    const __nv_bfloat16* qb = reinterpret_cast<const __nv_bfloat16*>(&q);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) xv[e] = bf2f(qb[e]);
+                }
+                const uint2 r = *reinterpret_cast<const uint2*>(g + v * cout + cob * 16 + cq);
+                const __nv_bfloat16* rb = reinterpret_cast<const __nv_bfloat16*>(&r);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) gv[e] = bf2f(rb[e]);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                xs[vl][cq + e] = xv[e];
+                gs[vl][cq + e] = gv[e];
+            }
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < kDwTile; ++k) {
+            acc = fmaf(xs[k][ty], gs[k][tx], acc);
+            if (do_bias && ty == 0) bacc += gs[k][tx];
+        }
+        __syncthreads();
+    }
+    atomicAdd(&dw[((size_t)tap * cin + cib * 16 + ty) * cout + cob * 16 + tx], acc);
+    if (do_bias && ty == 0) atomicAdd(&db[cob * 16 + tx], bacc);
+}
+
+// Weight gradient of the 2-channel FP32 input layer: 27 x 2 x 16 weights and
+// 16 biases; one thread per weight, voxels split over blocks.
+__global__ void dw_first_kernel(const float* __restrict__ in, const __nv_bfloat16* __restrict__ g,
+                                float* __restrict__ dw, float* __restrict__ db, int B, int S, int nsplit) {
+    const int t = threadIdx.x;  // 0 .. 27*32+16-1
+    if (t >= 27 * 32 + 16) return;
+    const long long nv = (long long)B * S * S * S;
+    const long long per = (nv + nsplit - 1) / nsplit;
+    const long long v0 = blockIdx.x * per, v1 = v0 + per < nv ? v0 + per : nv;
+    float acc = 0.0f;
+    if (t < 27 * 32) {
+        const int tap = t / 32, ci = (t / 16) % 2, co = t % 16;
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        for (long long v = v0; v < v1; ++v) {
+            const int xx = (int)(v % S), yy = (int)((v / S) % S), zz = (int)((v / ((long long)S * S)) % S);
+            const long long bb = v / ((long long)S * S * S);
+            const int z2 = zz + dz, y2 = yy + dy, x2 = xx + dx;
+            if (z2 < 0 || z2 >= S || y2 < 0 || y2 >= S || x2 < 0 || x2 >= S) continue;
+            const long long u = ((bb * S + z2) * S + y2) * S + x2;
+            acc = fmaf(in[2 * u + ci], bf2f(g[v * 16 + co]), acc);
+        }
+        atomicAdd(&dw[t], acc);
+    } else {
+        const int co = t - 27 * 32;
+        for (long long v = v0; v < v1; ++v) acc += bf2f(g[v * 16 + co]);
+        atomicAdd(&db[co], acc);
+    }
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+__global__ void zero_f32_kernel(float* p, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = 0.0f;
+}
+
+int grid_for(long long n, int n_sm) {
+    long long g = (n + 255) / 256;
+    const long long cap = 16LL * n_sm;
+    return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+#define UCK(x)                            \
+    do {                                  \
+        cudaError_t e_ = (x);             \
+        if (e_ != cudaSuccess) return e_; \
+    } while (0)
+
+}  // namespace
+
+size_t param_offset(int layer) {
+    size_t off = 0;
+    for (int l = 0; l < layer; ++l)
+        off += (l == kHead ? (size_t)kCin[l] : (size_t)27 * kCin[l]) * kCout[l] + kCout[l];
+    return off;
+}
+size_t param_count() { return param_offset(kLayers); }
+
+cudaError_t pack_weights(const float* w, __nv_bfloat16* wp, int cin, int cout, int flip, cudaStream_t st) {
+    const long long total = 27LL * cin * cout;
+    pack_kernel<<<(int)((total + 255) / 256), 256, 0, st>>>(w, wp, cin, cout, flip);
+    return cudaGetLastError();
+}
+
+cudaError_t conv3_tc(const __nv_bfloat16* x, const __nv_bfloat16* wp, const float* bias, const __nv_bfloat16* mask,
+                     __nv_bfloat16* y, int B, int D, int H, int W, int cin, int cout, int epi, int* err, int n_sm,
+                     cudaStream_t st) {
+    (void)n_sm;
+    if (cin % 16 || cout % 16 || cout < 16 || cout > 256 || B < 1) return cudaErrorInvalidValue;
+    ConvArgs a;
+    a.x = x;
+    a.wp = wp;
+    a.bias = bias;
+    a.mask = mask;
+    a.y = y;
+    a.B = B;
+    a.D = D;
+    a.H = H;
+    a.W = W;
+    a.cin = cin;
+    a.cout = cout;
+    a.epi = epi;
+    int DT = 4;
+    while (DT > 1 && DT * cout > 512) --DT;
+    if (DT > D) DT = D;
+    a.DT = DT;
+    int nc = 32;
+    while (nc < DT * cout) nc *= 2;
+    a.ncols = nc;
+    a.itile = (uint32_t)(DT + 2) * kHH * kWW * 16;
+    a.wtile = 27u * (uint32_t)cout * 32u;
+    a.stage = 2 * a.itile + a.wtile;
+    a.nbuf = (2 * a.stage + 128 <= 200 * 1024 && cin > 16) ? 2 : 1;
+    a.tiles_w = (W + kTW - 1) / kTW;
+    a.tiles_h = (H + kTH - 1) / kTH;
+    a.tiles_d = (D + DT - 1) / DT;
+    a.err = err;
+    size_t smem = (size_t)a.nbuf * a.stage + 128;
+    // keep (CTAs per SM) x (TMEM columns) within the 512 columns of an SM
+    const size_t sm_bytes = 228 * 1024, per_cta_reserve = 1024 + 64;
+    const int max_ctas = 512 / nc;
+    if ((sm_bytes / (smem + per_cta_reserve)) > (size_t)max_ctas) smem = sm_bytes / max_ctas - per_cta_reserve + 1;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    UCK(cudaFuncSetAttribute(conv3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long nblk = (long long)a.tiles_w * a.tiles_h * a.tiles_d * B;
+    if (nblk > 0x7fffffffLL) return cudaErrorInvalidValue;
+    conv3_tc_kernel<<<(unsigned)nblk, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---- network driver --------------------------------------------------------
+
+cudaError_t create(Net& n, int S, int Bmax) {
+    n.S = S;
+    n.Bmax = Bmax;
+    int dev = 0;
+    UCK(cudaGetDevice(&dev));
+    UCK(cudaDeviceGetAttribute(&n.n_sm, cudaDevAttrMultiProcessorCount, dev));
+    n.nparam = param_count();
+    auto alloc = [&](void** p, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) n.bufs.push_back(*p);
+        return e;
+    };
+    UCK(alloc((void**)&n.params, n.nparam * 4));
+    UCK(alloc((void**)&n.grads, n.nparam * 4));
+    UCK(alloc((void**)&n.adam_m, n.nparam * 4));
+    UCK(alloc((void**)&n.adam_v, n.nparam * 4));
+    UCK(cudaMemset(n.adam_m, 0, n.nparam * 4));
+    UCK(cudaMemset(n.adam_v, 0, n.nparam * 4));
+    UCK(cudaMemset(n.params, 0, n.nparam * 4));
+    for (int l = 1; l < kHead; ++l) {
+        const size_t e = (size_t)27 * kCin[l] * kCout[l] * sizeof(__nv_bfloat16);
+        UCK(alloc((void**)&n.wfwd[l], e));
+        UCK(alloc((void**)&n.wbwd[l], e));
+    }
+    const size_t v0 = (size_t)Bmax * S * S * S, v1 = v0 / 8, v2 = v1 / 8, v3 = v2 / 8;
+    auto act = [&](__nv_bfloat16** p, size_t vox, int C) { return alloc((void**)p, vox * C * 2); };
+    UCK(act(&n.x0a, v0, 16));
+    UCK(act(&n.x0, v0, 16));
+    UCK(act(&n.p0, v1, 16));
+    UCK(act(&n.x1a, v1, 32));
+    UCK(act(&n.x1, v1, 32));
+    UCK(act(&n.p1, v2, 32));
+    UCK(act(&n.x2a, v2, 64));
+    UCK(act(&n.x2, v2, 64));
+    UCK(act(&n.p2, v3, 64));
+    UCK(act(&n.x3a, v3, 128));
+    UCK(act(&n.x3, v3, 128));
+    UCK(act(&n.c2, v2, 192));
+    UCK(act(&n.y2a, v2, 64));
+    UCK(act(&n.y2, v2, 64));
+    UCK(act(&n.c1, v1, 96));
+    UCK(act(&n.y1a, v1, 32));
+    UCK(act(&n.y1, v1, 32));
+    UCK(act(&n.c0, v0, 48));
+    UCK(act(&n.y0a, v0, 16));
+    UCK(act(&n.y0, v0, 16));
+    UCK(act(&n.g_y0, v0, 16));
+    UCK(act(&n.g_y0a, v0, 16));
+    UCK(act(&n.g_c0, v0, 48));
+    UCK(act(&n.g_y1, v1, 32));
+    UCK(act(&n.g_y1a, v1, 32));
+    UCK(act(&n.g_c1, v1, 96));
+    UCK(act(&n.g_y2, v2, 64));
+    UCK(act(&n.g_y2a, v2, 64));
+    UCK(act(&n.g_c2, v2, 192));
+    UCK(act(&n.g_x3, v3, 128));
+    UCK(act(&n.g_x3a, v3, 128));
+    UCK(act(&n.g_p2, v3, 64));
+    UCK(act(&n.g_x2, v2, 64));
+    UCK(act(&n.g_x2a, v2, 64));
+    UCK(act(&n.g_p1, v2, 32));
+    UCK(act(&n.g_x1, v1, 32));
+    UCK(act(&n.g_x1a, v1, 32));
+    UCK(act(&n.g_p0, v1, 16));
+    UCK(act(&n.g_x0, v0, 16));
+    UCK(act(&n.g_x0a, v0, 16));
+    UCK(alloc((void**)&n.out, v0 * 4));
+    UCK(alloc((void**)&n.d_loss, 4));
+    UCK(alloc((void**)&n.d_err, 4));
+    UCK(cudaMemset(n.d_err, 0, 4));
+    return cudaSuccess;
+}
+
+void destroy(Net& n) {
+    for (void* p : n.bufs) cudaFree(p);
+    n.bufs.clear();
+}
+
+cudaError_t pack(Net& n, cudaStream_t st) {
+    for (int l = 1; l < kHead; ++l) {
+        const float* w = n.params + param_offset(l);
+        UCK(pack_weights(w, n.wfwd[l], kCin[l], kCout[l], 0, st));
+        UCK(pack_weights(w, n.wbwd[l], kCin[l], kCout[l], 1, st));
+    }
+    n.packed = true;
+    return cudaSuccess;
+}
+
+static const float* bias_of(const Net& n, int l) { return n.params + param_offset(l) + (size_t)27 * kCin[l] * kCout[l]; }
+
+cudaError_t forward(Net& n, const float* in, int B, cudaStream_t st) {
+    if (B < 1 || B > n.Bmax) return cudaErrorInvalidValue;
+    if (!n.packed) UCK(pack(n, st));
+    const int S = n.S, S1 = S / 2, S2 = S / 4, S3 = S / 8;
+    const long long v0 = (long long)B * S * S * S, v1 = v0 / 8, v2 = v1 / 8, v3 = v2 / 8;
+    auto conv = [&](const __nv_bfloat16* x, __nv_bfloat16* y, int l, int s) {
+        return conv3_tc(x, n.wfwd[l], bias_of(n, l), nullptr, y, B, s, s, s, kCin[l], kCout[l], 1, n.d_err, n.n_sm,
+                        st);
+    };
+    conv_first_kernel<<<grid_for(v0, n.n_sm), 256, 0, st>>>(in, n.params, bias_of(n, 0), n.x0a, B, S);
+    UCK(cudaGetLastError());
+    UCK(conv(n.x0a, n.x0, 1, S));
+    pool_kernel<<<grid_for(v1 * 2, n.n_sm), 256, 0, st>>>(n.x0, n.p0, B, S, 16);
+    UCK(conv(n.p0, n.x1a, 2, S1));
+    UCK(conv(n.x1a, n.x1, 3, S1));
+    pool_kernel<<<grid_for(v2 * 4, n.n_sm), 256, 0, st>>>(n.x1, n.p1, B, S1, 32);
+    UCK(conv(n.p1, n.x2a, 4, S2));
+    UCK(conv(n.x2a, n.x2, 5, S2));
+    pool_kernel<<<grid_for(v3 * 8, n.n_sm), 256, 0, st>>>(n.x2, n.p2, B, S2, 64);
+    UCK(conv(n.p2, n.x3a, 6, S3));
+    UCK(conv(n.x3a, n.x3, 7, S3));
+    upcat_kernel<<<grid_for(v2 * 24, n.n_sm), 256, 0, st>>>(n.x3, n.x2, n.c2, B, S2, 128, 64);
+    UCK(conv(n.c2, n.y2a, 8, S2));
+    UCK(conv(n.y2a, n.y2, 9, S2));
+    upcat_kernel<<<grid_for(v1 * 12, n.n_sm), 256, 0, st>>>(n.y2, n.x1, n.c1, B, S1, 64, 32);
+    UCK(conv(n.c1, n.y1a, 10, S1));
+    UCK(conv(n.y1a, n.y1, 11, S1));
+    upcat_kernel<<<grid_for(v0 * 6, n.n_sm), 256, 0, st>>>(n.y1, n.x0, n.c0, B, S, 32, 16);
+    UCK(conv(n.c0, n.y0a, 12, S));
+    UCK(conv(n.y0a, n.y0, 13, S));
+    head_kernel<<<grid_for(v0, n.n_sm), 256, 0, st>>>(n.y0, n.params + param_offset(kHead), n.out, v0);
+    return cudaGetLastError();
+}
+
+cudaError_t backward(Net& n, const float* in, const float* target, int B, cudaStream_t st) {
+    const int S = n.S, S1 = S / 2, S2 = S / 4, S3 = S / 8;
+    const long long v0 = (long long)B * S * S * S, v1 = v0 / 8, v2 = v1 / 8, v3 = v2 / 8;
+    zero_f32_kernel<<<grid_for((long long)n.nparam, n.n_sm), 256, 0, st>>>(n.grads, (long long)n.nparam);
+    UCK(cudaMemsetAsync(n.d_loss, 0, 4, st));
+    head_backward_kernel<<<grid_for(v0, n.n_sm), 256, 0, st>>>(in, target, n.out, n.y0, n.params + param_offset(kHead),
+                                                              n.grads + param_offset(kHead), n.g_y0, n.d_loss, v0,
+                                                              1.0f / (float)v0);
+    UCK(cudaGetLastError());
+    // data gradient through layer l: from g (cout channels) to cin channels,
+    // masked by ReLU of the layer's input when that input is a ReLU output
+    auto dconv = [&](const __nv_bfloat16* g, const __nv_bfloat16* xmask, __nv_bfloat16* dx, int l, int s) {
+        return conv3_tc(g, n.wbwd[l], nullptr, xmask, dx, B, s, s, s, kCout[l], kCin[l], xmask ? 2 : 0, n.d_err,
+                        n.n_sm, st);
+    };
+    auto dweight = [&](const __nv_bfloat16* x, const __nv_bfloat16* g, int l, int s) {
+        const long long nv = (long long)B * s * s * s;
+        int nsplit = (int)((nv + 8191) / 8192);
+        const int blocks = 27 * (kCin[l] / 16) * (kCout[l] / 16);
+        while (nsplit > 1 && (long long)blocks * nsplit > 64LL * n.n_sm) --nsplit;
+        dim3 grid(27, kCin[l] / 16, (kCout[l] / 16) * nsplit);
+        float* gw = n.grads + param_offset(l);
+        dw_kernel<<<grid, 256, 0, st>>>(x, g, gw, gw + (size_t)27 * kCin[l] * kCout[l], B, s, kCin[l], kCout[l], nsplit);
+        return cudaGetLastError();
+    };
+    // level 0, up path
+    UCK(dweight(n.y0a, n.g_y0, 13, S));
+    UCK(dconv(n.g_y0, n.y0a, n.g_y0a, 13, S));
+    UCK(dweight(n.c0, n.g_y0a, 12, S));
+    UCK(dconv(n.g_y0a, nullptr, n.g_c0, 12, S));
+    upcat_back_low_kernel<<<grid_for(v1 * 4, n.n_sm), 256, 0, st>>>(n.g_c0, n.y1, n.g_y1, B, S, 32, 16);
+    // level 1, up path
+    UCK(dweight(n.y1a, n.g_y1, 11, S1));
+    UCK(dconv(n.g_y1, n.y1a, n.g_y1a, 11, S1));
+    UCK(dweight(n.c1, n.g_y1a, 10, S1));
+    UCK(dconv(n.g_y1a, nullptr, n.g_c1, 10, S1));
+    upcat_back_low_kernel<<<grid_for(v2 * 8, n.n_sm), 256, 0, st>>>(n.g_c1, n.y2, n.g_y2, B, S1, 64, 32);
+    // level 2, up path
+    UCK(dweight(n.y2a, n.g_y2, 9, S2));
+    UCK(dconv(n.g_y2, n.y2a, n.g_y2a, 9, S2));
+    UCK(dweight(n.c2, n.g_y2a, 8, S2));
+    UCK(dconv(n.g_y2a, nullptr, n.g_c2, 8, S2));
+    upcat_back_low_kernel<<<grid_for(v3 * 16, n.n_sm), 256, 0, st>>>(n.g_c2, n.x3, n.g_x3, B, S2, 128, 64);
+    // bottleneck
+    UCK(dweight(n.x3a, n.g_x3, 7, S3));
+    UCK(dconv(n.g_x3, n.x3a, n.g_x3a, 7, S3));
+    UCK(dweight(n.p2, n.g_x3a, 6, S3));
+    UCK(dconv(n.g_x3a, nullptr, n.g_p2, 6, S3));
+    // level 2, down path
+    skip_back_kernel<<<grid_for(v2 * 8, n.n_sm), 256, 0, st>>>(n.g_p2, n.g_c2, n.x2, n.g_x2, B, S2, 128, 64);
+    UCK(dweight(n.x2a, n.g_x2, 5, S2));
+    UCK(dconv(n.g_x2, n.x2a, n.g_x2a, 5, S2));
+    UCK(dweight(n.p1, n.g_x2a, 4, S2));
+    UCK(dconv(n.g_x2a, nullptr, n.g_p1, 4, S2));
+    // level 1, down path
+    skip_back_kernel<<<grid_for(v1 * 4, n.n_sm), 256, 0, st>>>(n.g_p1, n.g_c1, n.x1, n.g_x1, B, S1, 64, 32);
+    UCK(dweight(n.x1a, n.g_x1, 3, S1));
+    UCK(dconv(n.g_x1, n.x1a, n.g_x1a, 3, S1));
+    UCK(dweight(n.p0, n.g_x1a, 2, S1));
+    UCK(dconv(n.g_x1a, nullptr, n.g_p0, 2, S1));
+    // level 0, down path
+    skip_back_kernel<<<grid_for(v0 * 2, n.n_sm), 256, 0, st>>>(n.g_p0, n.g_c0, n.x0, n.g_x0, B, S, 32, 16);
+    UCK(dweight(n.x0a, n.g_x0, 1, S));
+    UCK(dconv(n.g_x0, n.x0a, n.g_x0a, 1, S));
+    {
+        const int nsplit = 4 * n.n_sm;
+        float* gw = n.grads + param_offset(0);
+        dw_first_kernel<<<nsplit, 27 * 32 + 16, 0, st>>>(in, n.g_x0a, gw, gw + 27 * 32, B, S, nsplit);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t adam_step(Net& n, float lr, cudaStream_t st) {
+    n.adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f / (1.0f - std::pow(b1, (float)n.adam_t));
+    const float c2 = 1.0f / (1.0f - std::pow(b2, (float)n.adam_t));
+    adam_kernel<<<grid_for((long long)n.nparam, n.n_sm), 256, 0, st>>>(n.params, n.grads, n.adam_m, n.adam_v,
+                                                                      (long long)n.nparam, lr, b1, b2, 1e-8f, c1, c2);
+    UCK(cudaGetLastError());
+    return pack(n, st);
+}
+
+cudaError_t check_error(Net& n, cudaStream_t st) {
+    int h = 0;
+    UCK(cudaMemcpyAsync(&h, n.d_err, 4, cudaMemcpyDeviceToHost, st));
+    UCK(cudaStreamSynchronize(st));
+    return h ? cudaErrorLaunchTimeout : cudaSuccess;
+}
+
+}  // namespace unet
+}  // namespace exx
+
+// ---- C ABI -----------------------------------------------------------------
+
+#include "exx_guess.h"
+#include <string>
+
+namespace exx {
+void set_global_error(const std::string& msg);  // defined in exx_api.cu
+}
+
+struct exx_guess {
+    exx::unet::Net net;
+};
+
+namespace {
+
+exx_status gfail(exx_status s, const std::string& m) {
+    exx::set_global_error(m);
+    return s;
+}
+
+exx_status gcuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return EXX_OK;
+    (void)cudaGetLastError();
+    if (e == cudaErrorLaunchTimeout)
+        return gfail(EXX_ECUDA, std::string(what) + ": a tensor-core wait timed out");
+    return gfail(e == cudaErrorMemoryAllocation ? EXX_ENOMEM : EXX_ECUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" size_t exx_guess_param_count(void) { return exx::unet::param_count(); }
+
+extern "C" exx_status exx_guess_create(exx_guess** out, int S, int batch_max) {
+    if (!out) return gfail(EXX_EINVAL, "exx_guess_create: out is NULL");
+    *out = nullptr;
+    if (S < 16 || S > 64 || S % 8) return gfail(EXX_EINVAL, "exx_guess_create: S must be a multiple of 8 in [16, 64]");
+    if (batch_max < 1 || batch_max > 1024) return gfail(EXX_EINVAL, "exx_guess_create: batch_max must be in [1, 1024]");
+    exx_guess* g = new exx_guess();
+    cudaError_t e = exx::unet::create(g->net, S, batch_max);
+    if (e != cudaSuccess) {
+        exx::unet::destroy(g->net);
+        delete g;
+        return gcuda(e, "exx_guess_create");
+    }
+    *out = g;
+    return EXX_OK;
+}
+
+extern "C" exx_status exx_guess_set_params(exx_guess* g, const float* params, size_t n) {
+    if (!g || !params) return gfail(EXX_EINVAL, "exx_guess_set_params: NULL argument");
+    if (n != g->net.nparam) return gfail(EXX_EINVAL, "exx_guess_set_params: wrong parameter count");
+    exx_status s = gcuda(cudaMemcpy(g->net.params, params, n * 4, cudaMemcpyHostToDevice), "exx_guess_set_params");
+    if (s != EXX_OK) return s;
+    g->net.packed = false;
+    return gcuda(exx::unet::pack(g->net, nullptr), "exx_guess_set_params");
+}
+
+extern "C" exx_status exx_guess_get_params(exx_guess* g, float* params, size_t n) {
+    if (!g || !params) return gfail(EXX_EINVAL, "exx_guess_get_params: NULL argument");
+    if (n != g->net.nparam) return gfail(EXX_EINVAL, "exx_guess_get_params: wrong parameter count");
+    return gcuda(cudaMemcpy(params, g->net.params, n * 4, cudaMemcpyDeviceToHost), "exx_guess_get_params");
+}
+
+extern "C" exx_status exx_guess_forward(exx_guess* g, const float* input, float* output, int batch, void* stream) {
+    if (!g || !input || !output) return gfail(EXX_EINVAL, "exx_guess_forward: NULL argument");
+    if (batch < 1 || batch > g->net.Bmax) return gfail(EXX_EINVAL, "exx_guess_forward: batch out of range");
+    cudaStream_t st = (cudaStream_t)stream;
+    exx_status s = gcuda(exx::unet::forward(g->net, input, batch, st), "exx_guess_forward");
+    if (s != EXX_OK) return s;
+    const size_t bytes = (size_t)batch * g->net.S * g->net.S * g->net.S * 4;
+    s = gcuda(cudaMemcpyAsync(output, g->net.out, bytes, cudaMemcpyDeviceToDevice, st), "exx_guess_forward");
+    if (s != EXX_OK) return s;
+    return gcuda(exx::unet::check_error(g->net, st), "exx_guess_forward");
+}
+
+extern "C" exx_status exx_guess_gradient(exx_guess* g, const float* input, const float* target, int batch, float* loss,
+                                         float* grad, void* stream) {
+    if (!g || !input || !target) return gfail(EXX_EINVAL, "exx_guess_gradient: NULL argument");
+    if (batch < 1 || batch > g->net.Bmax) return gfail(EXX_EINVAL, "exx_guess_gradient: batch out of range");
+    cudaStream_t st = (cudaStream_t)stream;
+    exx_status s = gcuda(exx::unet::forward(g->net, input, batch, st), "exx_guess_gradient");
+    if (s == EXX_OK) s = gcuda(exx::unet::backward(g->net, input, target, batch, st), "exx_guess_gradient");
+    if (s == EXX_OK) s = gcuda(exx::unet::check_error(g->net, st), "exx_guess_gradient");
+    if (s == EXX_OK && loss)
+        s = gcuda(cudaMemcpy(loss, g->net.d_loss, 4, cudaMemcpyDeviceToHost), "exx_guess_gradient");
+    if (s == EXX_OK && grad)
+        s = gcuda(cudaMemcpy(grad, g->net.grads, g->net.nparam * 4, cudaMemcpyDeviceToHost), "exx_guess_gradient");
+    return s;
+}
+
+extern "C" exx_status exx_guess_train_step(exx_guess* g, const float* input, const float* target, int batch, float lr,
+                                           float* loss, void* stream) {
+    if (!g || !input || !target) return gfail(EXX_EINVAL, "exx_guess_train_step: NULL argument");
+    if (batch < 1 || batch > g->net.Bmax) return gfail(EXX_EINVAL, "exx_guess_train_step: batch out of range");
+    if (!(lr > 0.0f)) return gfail(EXX_EINVAL, "exx_guess_train_step: lr must be positive");
+    cudaStream_t st = (cudaStream_t)stream;
+    exx_status s = gcuda(exx::unet::forward(g->net, input, batch, st), "exx_guess_train_step");
+    if (s == EXX_OK) s = gcuda(exx::unet::backward(g->net, input, target, batch, st), "exx_guess_train_step");
+    if (s == EXX_OK) s = gcuda(exx::unet::adam_step(g->net, lr, st), "exx_guess_train_step");
+    if (s == EXX_OK && loss)
+        s = gcuda(cudaMemcpyAsync(loss, g->net.d_loss, 4, cudaMemcpyDeviceToHost, st), "exx_guess_train_step");
+    if (s == EXX_OK) s = gcuda(exx::unet::check_error(g->net, st), "exx_guess_train_step");
+    return s;
+}
+
+extern "C" void exx_guess_destroy(exx_guess* g) {
+    if (!g) return;
+    exx::unet::destroy(g->net);
+    delete g;
+}
+
+extern "C" exx_status exx_unet_conv3d(const void* x, const float* w, const float* bias, const void* mask, void* y,
+                                      int batch, int D, int H, int W, int cin, int cout, int mode, void* stream) {
+    if (!x || !w || !y) return gfail(EXX_EINVAL, "exx_unet_conv3d: NULL argument");
+    if (cin % 16 || cout % 16 || cin < 16 || cout < 16 || cin > 256 || cout > 256)
+        return gfail(EXX_EINVAL, "exx_unet_conv3d: channels must be multiples of 16 in [16, 256]");
+    if (batch < 1 || D < 1 || H < 1 || W < 1 || mode < 0 || mode > 2)
+        return gfail(EXX_EINVAL, "exx_unet_conv3d: bad size or mode");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    __nv_bfloat16* wp = nullptr;
+    int* err = nullptr;
+    exx_status s = gcuda(cudaMalloc(&wp, (size_t)27 * cin * cout * 2), "exx_unet_conv3d");
+    if (s == EXX_OK) s = gcuda(cudaMalloc(&err, 4), "exx_unet_conv3d");
+    if (s == EXX_OK) s = gcuda(cudaMemsetAsync(err, 0, 4, st), "exx_unet_conv3d");
+    const int flip = mode == 2 ? 1 : 0;
+    if (s == EXX_OK) s = gcuda(exx::unet::pack_weights(w, wp, cin, cout, flip, st), "exx_unet_conv3d");
+    if (s == EXX_OK) {
+        const int ci = flip ? cout : cin, co = flip ? cin : cout;
+        const int epi = mode == 1 ? 1 : (mode == 2 && mask ? 2 : 0);
+        s = gcuda(exx::unet::conv3_tc((const __nv_bfloat16*)x, wp, flip ? nullptr : bias,
+                                      (const __nv_bfloat16*)mask, (__nv_bfloat16*)y, batch, D, H, W, ci, co, epi, err,
+                                      nsm, st),
+                  "exx_unet_conv3d");
+    }
+    int h = 0;
+    if (s == EXX_OK) s = gcuda(cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st), "exx_unet_conv3d");
+    if (s == EXX_OK) s = gcuda(cudaStreamSynchronize(st), "exx_unet_conv3d");
+    if (s == EXX_OK && h) s = gfail(EXX_ECUDA, "exx_unet_conv3d: a tensor-core wait timed out");
+    cudaFree(wp);
+    cudaFree(err);
+    return s;
+}

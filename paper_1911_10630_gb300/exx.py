@@ -58,6 +58,7 @@ _lib = None
 _vp = ctypes.c_void_p
 _d = ctypes.POINTER(ctypes.c_double)
 _i = ctypes.POINTER(ctypes.c_int)
+_f = ctypes.POINTER(ctypes.c_float)
 _ctx_p = ctypes.c_void_p
 
 # (name, restype, argtypes): every function declared in include/exx.h
@@ -77,6 +78,17 @@ SIGNATURES = [
                                             _vp]),
     ("exx_last_error", ctypes.c_char_p, [_ctx_p]),
     ("exx_destroy", None, [_ctx_p]),
+    # include/exx_guess.h
+    ("exx_guess_param_count", ctypes.c_size_t, []),
+    ("exx_guess_create", ctypes.c_int, [ctypes.POINTER(_ctx_p), ctypes.c_int, ctypes.c_int]),
+    ("exx_guess_set_params", ctypes.c_int, [_ctx_p, _f, ctypes.c_size_t]),
+    ("exx_guess_get_params", ctypes.c_int, [_ctx_p, _f, ctypes.c_size_t]),
+    ("exx_guess_forward", ctypes.c_int, [_ctx_p, _vp, _vp, ctypes.c_int, _vp]),
+    ("exx_guess_gradient", ctypes.c_int, [_ctx_p, _vp, _vp, ctypes.c_int, _f, _f, _vp]),
+    ("exx_guess_train_step", ctypes.c_int, [_ctx_p, _vp, _vp, ctypes.c_int, ctypes.c_float, _f, _vp]),
+    ("exx_guess_destroy", None, [_ctx_p]),
+    ("exx_unet_conv3d", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
 ]
 
 
@@ -225,3 +237,58 @@ class Exx:
 
     def apply_operator(self, p, ap, stream=None):
         _check(load().exx_apply_operator(self._ctx, _ptr(p), _ptr(ap), _stream_handle(stream)), self._ctx)
+
+
+class GuessNet:
+    """Owns one exx_guess (the learned warm start's U-Net; include/exx_guess.h)."""
+
+    def __init__(self, S: int, batch_max: int):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.exx_guess_create(ctypes.byref(h), int(S), int(batch_max)))
+        self._h = h
+        self.S = int(S)
+        self.batch_max = int(batch_max)
+        self.n_params = int(L.exx_guess_param_count())
+
+    def set_params(self, params: np.ndarray):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(load().exx_guess_set_params(self._h, p.ctypes.data_as(_f), p.size))
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.n_params, np.float32)
+        _check(load().exx_guess_get_params(self._h, p.ctypes.data_as(_f), p.size))
+        return p
+
+    def forward(self, inp, out, batch: int, stream=None):
+        _check(load().exx_guess_forward(self._h, _ptr(inp), _ptr(out), int(batch), _stream_handle(stream)))
+
+    def gradient(self, inp, target, batch: int, want_grad: bool = True, stream=None):
+        loss = ctypes.c_float()
+        g = np.empty(self.n_params, np.float32) if want_grad else None
+        _check(load().exx_guess_gradient(self._h, _ptr(inp), _ptr(target), int(batch), ctypes.byref(loss),
+                                         g.ctypes.data_as(_f) if g is not None else None, _stream_handle(stream)))
+        return float(loss.value), g
+
+    def train_step(self, inp, target, batch: int, lr: float, stream=None) -> float:
+        loss = ctypes.c_float()
+        _check(load().exx_guess_train_step(self._h, _ptr(inp), _ptr(target), int(batch), float(lr),
+                                           ctypes.byref(loss), _stream_handle(stream)))
+        return float(loss.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().exx_guess_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover
+            pass
+
+
+def unet_conv3d(x, w, bias, mask, y, batch, D, H, W, cin, cout, mode, stream=None):
+    """One tensor-core 3x3x3 convolution (exx_unet_conv3d); device tensors."""
+    _check(load().exx_unet_conv3d(_ptr(x), _ptr(w), _ptr(bias), _ptr(mask), _ptr(y), int(batch), int(D), int(H),
+                                  int(W), int(cin), int(cout), int(mode), _stream_handle(stream)))

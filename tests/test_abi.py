@@ -10,6 +10,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "exx.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
 
 
 @pytest.fixture(scope="module")
@@ -20,7 +22,7 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "\n".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(exx_[a-z_0-9]+)\s*\(", text)))
 
@@ -111,3 +113,17 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
     m = importlib.reload(exx)  # a fresh binding with no library loaded yet
     with pytest.raises(OSError):
         m.load(str(tmp_path / "missing.so"))
+
+
+def test_guess_param_count_matches_the_oracle_network(lib):
+    from oracle import unet
+    assert lib.exx_guess_param_count() == unet.param_count()
+
+
+def test_guess_create_rejects_bad_sizes(lib):
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.exx_guess_create(ctypes.byref(h), 12, 4) == -1
+    assert "multiple of 8" in lib.exx_last_error(None).decode()
+    assert lib.exx_guess_create(ctypes.byref(h), 16, 0) == -1
+    assert not h.value
