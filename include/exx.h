@@ -59,8 +59,13 @@ typedef struct {
                           device work queue, the whole call captured once and
                           replayed as a CUDA graph (default 1).                  */
     int warm_start;    /* 0: CG from zero (default). 1: previous call's v_ij for
-                          pairs kept from the previous call (same i, j, grid
-                          centre and radii); other pairs start from zero.        */
+                          pairs kept from the previous call (same i and j), moved
+                          with the pair's grid centre; other pairs start from
+                          zero. 2: the learned guess of the model loaded with
+                          exx_load_guess_model (include/exx_guess.h). 1 and 2
+                          need precision 1, fixed radii and the cluster solver;
+                          the stop rule is unchanged, so a start only changes
+                          the iteration count.                                  */
     int radii_mode;    /* 0: fixed R_PE / R_ME for all pairs (default).
                           1: per-pair radii from the orbital exponents passed to
                              exx_compute (alphas), clamped to [12, R_PE]; R_PE and
@@ -109,6 +114,7 @@ typedef struct {
     int lane_map;          /* lane map in use (cluster solver)                      */
     int n_candidates;      /* launch shapes the autotuner could choose from          */
     double tune_ms;        /* host time spent by the autotuner (first call)          */
+    double guess_ms;       /* device time of the learned guesses (warm_start 2)      */
 } exx_stats;
 
 /* Defaults described in exx_options. */
@@ -207,8 +213,12 @@ exx_status exx_apply_operator(exx_ctx *ctx, const double *p, double *ap, void *s
 exx_status exx_ball_size(const exx_ctx *ctx, int *n_pe, int *n_me);
 
 /*
- * Loads the learned warm-start model (not available in this build: returns
- * EXX_EINVAL and leaves the context unchanged).
+ * Loads the learned warm-start model used by warm_start = 2: a blob of four
+ * int32 {0x47585845, 1, S, count} followed by count FP32 parameters of the
+ * U-Net described in include/exx_guess.h (S = side of the network's input
+ * cube). weights: host. Allocates the network and its batch buffers (about
+ * 4 GB). EXX_EINVAL if the header or the size does not match; a later load
+ * replaces the model.
  */
 exx_status exx_load_guess_model(exx_ctx *ctx, const void *weights, size_t bytes);
 

@@ -86,6 +86,20 @@ exx_status exx_guess_train_step(exx_guess *g, const float *input, const float *t
 void exx_guess_destroy(exx_guess *g);
 
 /*
+ * Training samples from a solved call: after exx_compute on ctx with
+ * warm_start = 1 (which keeps every pair's converged v on its PE ball), writes
+ * for the first min(count, cap) pairs of that call's list the network input
+ * and target on a cube of side S (even, 8..128) as laid out above.
+ *   orbitals  device, the same array the call used (EXX_EINVAL otherwise)
+ *   input     device [cap][S^3][2]; target device [cap][S^3]
+ *   count     host, receives the call's pair count
+ * Synchronises the context's work and the given stream. Errors are reported
+ * through exx_last_error(ctx).
+ */
+exx_status exx_export_samples(exx_ctx *ctx, const double *orbitals, int S, float *input, float *target, int cap,
+                              int *count, void *stream);
+
+/*
  * One 3x3x3 convolution (zero padding) on the tensor-core path, for tests.
  *   x     device BF16 [batch][D][H][W][cin], channels last
  *   w     device FP32 [27][cin][cout] (tap order as above)

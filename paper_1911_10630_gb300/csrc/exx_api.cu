@@ -14,6 +14,7 @@
 #include "../../include/exx.h"
 #include "exx_geometry.h"
 #include "exx_internal.h"
+#include "exx_unet.cuh"
 
 namespace exx {
 cudaError_t launch_pair_list(int n, const double* centers, const double L[3], const double delta[3], const int N[3],
@@ -121,6 +122,15 @@ struct exx_ctx {
     long long vcache_pairs = 0;
     int parity = 0;
     bool have_prev = false;
+
+    // learned warm start (warm_start 2): the U-Net and its per-pair guesses
+    exx::unet::Net* gnet = nullptr;
+    float* d_guess = nullptr;   // [guess_cap][n_pe] FP32 guesses, list order
+    long long guess_cap = 0;
+    float* d_gin = nullptr;     // [Bmax][S^3][2] network input
+    float* d_gscale = nullptr;  // [Bmax] per-pair density scale
+    cudaEvent_t ev_g[2] = {nullptr, nullptr};
+    double guess_ms = 0.0;
 
     // host-buffer path
     double* d_orb = nullptr;
@@ -251,6 +261,15 @@ extern "C" void exx_destroy(exx_ctx* c) {
     cudaFree(c->d_vcache[1]);
     cudaFree(c->d_pow);
     cudaFree(c->d_phase);
+    if (c->gnet) {
+        exx::unet::destroy(*c->gnet);
+        delete c->gnet;
+    }
+    cudaFree(c->d_guess);
+    cudaFree(c->d_gin);
+    cudaFree(c->d_gscale);
+    for (auto& e : c->ev_g)
+        if (e) cudaEventDestroy(e);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -287,10 +306,10 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                         "exx_init: with radii_mode 1, r_me must be >= r_pe + max(3, ceil(r_pe/3)) (the largest pair's R_ME)");
         if (o.solver_kind == 2) return fail(nullptr, EXX_EINVAL, "exx_init: radii_mode 1 runs on solver_kind 1");
     }
-    if (o.warm_start != 0 && o.warm_start != 1) return fail(nullptr, EXX_EINVAL, "exx_init: warm_start must be 0 or 1");
-    if (o.warm_start == 1 && (o.precision != 1 || o.radii_mode != 0 || o.solver_kind == 1))
+    if (o.warm_start < 0 || o.warm_start > 2) return fail(nullptr, EXX_EINVAL, "exx_init: warm_start must be 0, 1 or 2");
+    if (o.warm_start != 0 && (o.precision != 1 || o.radii_mode != 0 || o.solver_kind == 1))
         return fail(nullptr, EXX_EINVAL,
-                    "exx_init: warm_start 1 runs on the cluster solver (precision 1, fixed radii, solver_kind 0 or 2)");
+                    "exx_init: warm_start 1 and 2 run on the cluster solver (precision 1, fixed radii, solver_kind 0 or 2)");
     if (o.max_iter <= 0) o.max_iter = 20000;
     if (o.inner_max_iter <= 0) o.inner_max_iter = 4000;
     if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) o.inner_tol = 1e-5;
@@ -524,8 +543,8 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         if (!c->use_cluster && o.solver_kind == 2)
             return bail(fail(c, EXX_EINVAL, "exx_init: no cluster layout fits these radii"));
     }
-    if (o.warm_start == 1 && !c->use_cluster)
-        return bail(fail(c, EXX_EINVAL, "exx_init: warm_start 1 needs the cluster solver, which does not fit these radii"));
+    if (o.warm_start != 0 && !c->use_cluster)
+        return bail(fail(c, EXX_EINVAL, "exx_init: warm_start 1 and 2 need the cluster solver, which does not fit these radii"));
     if (c->use_cluster) apply_cand(c, c->cand);
 
     c->threads = c->use_cluster ? c->threads : (o.threads ? o.threads : 512);
@@ -733,6 +752,33 @@ static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double*
     P.n_prev = c->d_scalars + 7;
     P.vprev = c->d_vcache[c->parity ^ 1];
     P.vcur = c->d_vcache[c->parity];
+    if (c->opt.warm_start == 2) {
+        // learned guesses: the network runs on batches of pairs, its output
+        // is scattered to each pair's PE points and the CG starts from it
+        exx::unet::Net& net = *c->gnet;
+        if (np > c->guess_cap) {
+            cudaFree(c->d_guess);
+            c->d_guess = nullptr;
+            c->guess_cap = 0;
+            const long long want = (long long)(1.25 * np) + 16;
+            CK(cudaMalloc(&c->d_guess, sizeof(float) * (size_t)want * c->hb.n_pe), "cudaMalloc(learned guesses)");
+            c->guess_cap = want;
+        }
+        const double d2 = std::cbrt(c->delta[0] * c->delta[0] * c->delta[1] * c->delta[1] * c->delta[2] * c->delta[2]);
+        CK(cudaEventRecord(c->ev_g[0], st), "cudaEventRecord");
+        for (int k0 = 0; k0 < np; k0 += net.Bmax) {
+            const int nk = std::min(net.Bmax, np - k0);
+            CK(exx::unet::sample_prep(orbitals, c->grid, c->d_pairs, k0, nk, net.S, c->geo_host, c->d_gin,
+                                      c->d_gscale, nullptr, nullptr, d2, st),
+               "guess input");
+            CK(exx::unet::forward(net, c->d_gin, nk, st), "guess network");
+            CK(exx::unet::guess_scatter(net.out, c->d_gscale, k0, nk, net.S, c->geo_host, d2, c->d_guess, st),
+               "guess scatter");
+        }
+        CK(cudaEventRecord(c->ev_g[1], st), "cudaEventRecord");
+        P.warm = 2;
+        P.vprev = c->d_guess;
+    }
     CK(cudaEventRecord(c->ev[1], st), "cudaEventRecord");
     CK(launch_cluster_kernel(c->cl_variant, P, c->CL, c->n_clusters, c->smem, st), "cluster pair kernel");
     CK(cudaEventRecord(c->ev[2], st), "cudaEventRecord");
@@ -745,6 +791,14 @@ static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double*
     CK(cudaEventRecord(c->ev[3], st), "cudaEventRecord");
     c->parity ^= 1;
     c->have_prev = true;
+    if (c->opt.warm_start == 2) {
+        int h = 0;
+        CK(cudaMemcpyAsync(&h, c->gnet->d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "guess status");
+        CK(cudaStreamSynchronize(st), "guess status");
+        if (h) return fail(c, EXX_ECUDA, "exx_compute: a tensor-core wait of the guess network timed out");
+        float ms = 0.f;
+        c->guess_ms = cudaEventElapsedTime(&ms, c->ev_g[0], c->ev_g[1]) == cudaSuccess ? ms : -1.0;
+    }
     return EXX_OK;
 }
 
@@ -821,6 +875,8 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
     cudaStream_t st = c->work;
     CK(cudaEventRecord(c->ev_in, user), "cudaEventRecord(caller stream)");
     CK(cudaStreamWaitEvent(st, c->ev_in, 0), "cudaStreamWaitEvent");
+    if (c->opt.warm_start == 2 && !c->gnet)
+        return fail(c, EXX_EINVAL, "exx_compute: warm_start 2 needs a model (exx_load_guess_model)");
     if (c->use_cluster && !c->tuned) {
         s = autotune(c, orbitals, centers, alphas, n, st);
         if (s != EXX_OK) return s;
@@ -961,6 +1017,7 @@ extern "C" exx_status exx_get_stats(const exx_ctx* cc, exx_stats* out) {
         c->stats.threads = c->threads;
         c->stats.lane_map = c->cands[c->cand].lane_map;
         c->stats.tune_ms = c->tune_ms;
+        c->stats.guess_ms = c->opt.warm_start == 2 ? c->guess_ms : 0.0;
     }
     *out = c->stats;
     if (out->iters_max < 0) out->iters_max = 0;
@@ -1064,9 +1121,74 @@ extern "C" exx_status exx_ball_size(const exx_ctx* c, int* n_pe, int* n_me) {
 }
 
 extern "C" exx_status exx_load_guess_model(exx_ctx* c, const void* weights, size_t bytes) {
-    (void)weights;
-    (void)bytes;
-    return fail(c, EXX_EINVAL, "exx_load_guess_model: the learned warm start is not available in this build");
+    if (!c) return fail(nullptr, EXX_EINVAL, "exx_load_guess_model: ctx is NULL");
+    if (!weights || bytes < 16) return fail(c, EXX_EINVAL, "exx_load_guess_model: blob too short");
+    int32_t hdr[4];
+    std::memcpy(hdr, weights, sizeof(hdr));
+    const size_t np = exx::unet::param_count();
+    if (hdr[0] != 0x47585845 || hdr[1] != 1) return fail(c, EXX_EINVAL, "exx_load_guess_model: bad magic or version");
+    if (hdr[2] < 16 || hdr[2] > 64 || hdr[2] % 8) return fail(c, EXX_EINVAL, "exx_load_guess_model: bad cube side");
+    if ((size_t)hdr[3] != np || bytes != 16 + np * sizeof(float))
+        return fail(c, EXX_EINVAL, "exx_load_guess_model: parameter count does not match the network");
+    (void)cudaGetLastError();
+    if (c->gnet) {
+        exx::unet::destroy(*c->gnet);
+        delete c->gnet;
+        c->gnet = nullptr;
+    }
+    cudaFree(c->d_gin);
+    cudaFree(c->d_gscale);
+    c->d_gin = nullptr;
+    c->d_gscale = nullptr;
+    const int S = hdr[2];
+    // batch: about 4 GB of activations
+    const long long per = (long long)S * S * S * 1200;
+    const int bmax = (int)std::max(1LL, std::min(256LL, (4LL << 30) / per));
+    c->gnet = new exx::unet::Net();
+    cudaError_t e = exx::unet::create(*c->gnet, S, bmax);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_gin, sizeof(float) * 2 * (size_t)bmax * S * S * S);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_gscale, sizeof(float) * (size_t)bmax);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->gnet->params, static_cast<const char*>(weights) + 16, np * sizeof(float),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = exx::unet::pack(*c->gnet, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    for (auto& ev : c->ev_g)
+        if (e == cudaSuccess && !ev) e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) {
+        exx::unet::destroy(*c->gnet);
+        delete c->gnet;
+        c->gnet = nullptr;
+        return cuda_fail(c, e, "exx_load_guess_model");
+    }
+    return EXX_OK;
+}
+
+extern "C" exx_status exx_export_samples(exx_ctx* c, const double* orbitals, int S, float* input, float* target,
+                                         int cap, int* count, void* stream) {
+    if (!c) return fail(nullptr, EXX_EINVAL, "exx_export_samples: ctx is NULL");
+    if (!orbitals || !input || !target || !count) return fail(c, EXX_EINVAL, "exx_export_samples: NULL argument");
+    if (S < 8 || S > 128 || S % 2) return fail(c, EXX_EINVAL, "exx_export_samples: S must be even in [8, 128]");
+    if (c->opt.warm_start != 1 || !c->have_prev)
+        return fail(c, EXX_EINVAL, "exx_export_samples: needs a completed exx_compute call with warm_start 1");
+    if (orbitals != c->last_orb) return fail(c, EXX_EINVAL, "exx_export_samples: orbitals differ from the last call's");
+    (void)cudaGetLastError();
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(c->work), "exx_export_samples");
+    int np = 0;
+    CK(cudaMemcpy(&np, c->d_scalars + 7, sizeof(int), cudaMemcpyDeviceToHost), "exx_export_samples");
+    *count = np;
+    const int nk = std::min(np, std::max(cap, 0));
+    if (nk <= 0) return EXX_OK;
+    float* d_scale = nullptr;
+    CK(cudaMalloc(&d_scale, sizeof(float) * (size_t)nk), "exx_export_samples");
+    const double d2 = std::cbrt(c->delta[0] * c->delta[0] * c->delta[1] * c->delta[1] * c->delta[2] * c->delta[2]);
+    cudaError_t e = exx::unet::sample_prep(orbitals, c->grid, c->d_prev_pairs, 0, nk, S, c->geo_host, input, d_scale,
+                                           target, c->d_vcache[c->parity ^ 1], d2, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_scale);
+    if (e != cudaSuccess) return cuda_fail(c, e, "exx_export_samples");
+    return EXX_OK;
 }
 
 extern "C" const char* exx_last_error(const exx_ctx* c) { return c ? c->err.c_str() : g_init_err.c_str(); }

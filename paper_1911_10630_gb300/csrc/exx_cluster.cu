@@ -218,16 +218,20 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
         bool conv = true;
         double rn_start = bb;
         if (P.warm && bb > target2 && bb == bb) {
-            const int prev = find_prev_pair(P.prev_pairs, *P.n_prev, pr.i, pr.j);
+            // warm 1: the same pair in the previous call's list; warm 2: this
+            // pair's learned guess (same list position, no shift)
+            const int prev = P.warm == 2 ? pidx : find_prev_pair(P.prev_pairs, *P.n_prev, pr.i, pr.j);
             if (prev >= 0) {
-                const PairRec po = P.prev_pairs[prev];
-                int dlt[3];
+                int dlt[3] = {0, 0, 0};
+                if (P.warm == 1) {
+                    const PairRec po = P.prev_pairs[prev];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    int d = pr.g[a] - po.g[a];
-                    if (d > P.N[a] / 2) d -= P.N[a];
-                    if (d < -(P.N[a] - 1) / 2) d += P.N[a];
-                    dlt[a] = d;
+                    for (int a = 0; a < 3; ++a) {
+                        int d = pr.g[a] - po.g[a];
+                        if (d > P.N[a] / 2) d -= P.N[a];
+                        if (d < -(P.N[a] - 1) / 2) d += P.N[a];
+                        dlt[a] = d;
+                    }
                 }
                 if (abs(dlt[0]) <= 3 && abs(dlt[1]) <= 3 && abs(dlt[2]) <= 3) {
                     const long long tu = clk ? clock64() : 0;

@@ -811,6 +811,105 @@ cudaError_t check_error(Net& n, cudaStream_t st) {
 }  // namespace unet
 }  // namespace exx
 
+namespace exx {
+namespace unet {
+
+// ---- pair samples ------------------------------------------------------------
+
+namespace {
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+__global__ void __launch_bounds__(256) sample_prep_kernel(const double* __restrict__ phi, int N0, int N1, int N2,
+                                                          const PairRec* __restrict__ pairs, int k0, int S,
+                                                          const BallGeo G, float* __restrict__ input,
+                                                          float* __restrict__ scale, float* __restrict__ target,
+                                                          const float* __restrict__ vcache, double d2) {
+    __shared__ double red[8];
+    const int k = k0 + blockIdx.x;
+    const PairRec pr = pairs[k];
+    const long long ng = (long long)N0 * N1 * N2;
+    const double* pi = phi + (long long)pr.i * ng;
+    const double* pj = phi + (long long)pr.j * ng;
+    const int R = G.r_pe, h = S / 2, S3 = S * S * S;
+    double mx = 0.0;
+    for (int v = threadIdx.x; v < S3; v += blockDim.x) {
+        const int ox = v / (S * S) - h, oy = (v / S) % S - h, oz = v % S - h;
+        if (ox * ox + oy * oy + oz * oz > R * R) continue;
+        const long long g = ((long long)wrapi(pr.g[0] + ox, N0) * N1 + wrapi(pr.g[1] + oy, N1)) * N2 +
+                            wrapi(pr.g[2] + oz, N2);
+        mx = fmax(mx, fabs(pi[g] * pj[g]));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    double s = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, red[w]);
+    if (!(s > 0.0)) s = 1.0;
+    const double inv = 1.0 / s, tinv = 1.0 / (s * d2);
+    float* in = input + (size_t)blockIdx.x * S3 * 2;
+    float* tg = target ? target + (size_t)blockIdx.x * S3 : nullptr;
+    const float* vc = vcache ? vcache + (size_t)k * G.n_pe : nullptr;
+    const int W = 2 * R + 1;
+    for (int v = threadIdx.x; v < S3; v += blockDim.x) {
+        const int ox = v / (S * S) - h, oy = (v / S) % S - h, oz = v % S - h;
+        float r = 0.0f, m = 0.0f, t = 0.0f;
+        if (ox * ox + oy * oy + oz * oz <= R * R) {
+            const long long g = ((long long)wrapi(pr.g[0] + ox, N0) * N1 + wrapi(pr.g[1] + oy, N1)) * N2 +
+                                wrapi(pr.g[2] + oz, N2);
+            r = (float)(pi[g] * pj[g] * inv);
+            m = 1.0f;
+            if (tg && vc) {
+                const RowRec Rw = G.rows_pe[G.row_of[(ox + R) * W + (oy + R)]];
+                t = (float)(vc[Rw.pe_start + oz + Rw.zpe] * tinv);
+            }
+        }
+        in[2 * v] = r;
+        in[2 * v + 1] = m;
+        if (tg) tg[v] = t;
+    }
+    if (threadIdx.x == 0) scale[blockIdx.x] = (float)s;
+}
+
+__global__ void __launch_bounds__(256) guess_scatter_kernel(const float* __restrict__ out,
+                                                            const float* __restrict__ scale, int k0, int S,
+                                                            const BallGeo G, double d2, float* __restrict__ vguess) {
+    const int b = blockIdx.x, h = S / 2, S3 = S * S * S;
+    const float f = (float)(scale[b] * d2);
+    const float* o = out + (size_t)b * S3;
+    float* vg = vguess + (size_t)(k0 + b) * G.n_pe;
+    for (int p = threadIdx.x; p < G.n_pe; p += blockDim.x) {
+        const int pk = G.pt_off[p];
+        const int ox = (pk & 255) - 128 + h, oy = ((pk >> 8) & 255) - 128 + h, oz = ((pk >> 16) & 255) - 128 + h;
+        float v = 0.0f;
+        if (ox >= 0 && ox < S && oy >= 0 && oy < S && oz >= 0 && oz < S) v = o[(ox * S + oy) * S + oz] * f;
+        vg[p] = v;
+    }
+}
+
+}  // namespace
+
+cudaError_t sample_prep(const double* phi, const int N[3], const PairRec* pairs, int k0, int nk, int S,
+                        const BallGeo& G, float* input, float* scale, float* target, const float* vcache, double d2,
+                        cudaStream_t st) {
+    if (nk <= 0) return cudaSuccess;
+    sample_prep_kernel<<<nk, 256, 0, st>>>(phi, N[0], N[1], N[2], pairs, k0, S, G, input, scale, target, vcache, d2);
+    return cudaGetLastError();
+}
+
+cudaError_t guess_scatter(const float* out, const float* scale, int k0, int nk, int S, const BallGeo& G, double d2,
+                          float* vguess, cudaStream_t st) {
+    if (nk <= 0) return cudaSuccess;
+    guess_scatter_kernel<<<nk, 256, 0, st>>>(out, scale, k0, S, G, d2, vguess);
+    return cudaGetLastError();
+}
+
+}  // namespace unet
+}  // namespace exx
+
 // ---- C ABI -----------------------------------------------------------------
 
 #include "exx_guess.h"

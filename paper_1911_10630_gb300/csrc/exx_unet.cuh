@@ -9,6 +9,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "exx_internal.h"
+
 namespace exx {
 namespace unet {
 
@@ -67,6 +69,20 @@ cudaError_t conv3_tc(const __nv_bfloat16* x, const __nv_bfloat16* wp, const floa
 // weights of the data gradient (a convolution from cout to cin channels with
 // the taps mirrored).
 cudaError_t pack_weights(const float* w, __nv_bfloat16* wp, int cin, int cout, int flip, cudaStream_t st);
+
+// Network inputs of pairs k0 .. k0 + nk - 1 of the list: cube of side S
+// centred on g_ij (offset o = index - S/2), channel 0 = rho / s on the PE
+// ball, channel 1 = ball mask, s = max |rho| on the ball (scale[k - k0]).
+// With vcache (the pairs' PE-ball potentials, FP32, list order), target
+// receives v / (s d2) on the ball and 0 elsewhere. input [nk][S^3][2],
+// target [nk][S^3].
+cudaError_t sample_prep(const double* phi, const int N[3], const PairRec* pairs, int k0, int nk, int S,
+                        const BallGeo& G, float* input, float* scale, float* target, const float* vcache, double d2,
+                        cudaStream_t st);
+// vguess[k][p] = out[k - k0][cube(o_p)] * scale[k - k0] * d2 on the PE points
+// p of pairs k0 .. k0 + nk - 1 (0 where o_p falls outside the cube).
+cudaError_t guess_scatter(const float* out, const float* scale, int k0, int nk, int S, const BallGeo& G, double d2,
+                          float* vguess, cudaStream_t st);
 
 }  // namespace unet
 }  // namespace exx

@@ -44,7 +44,8 @@ class exx_stats(ctypes.Structure):
                 ("total_ms", ctypes.c_double), ("n_pe", ctypes.c_int), ("n_me", ctypes.c_int),
                 ("solver_kind", ctypes.c_int), ("cluster_size", ctypes.c_int), ("grid_ctas", ctypes.c_int),
                 ("threads", ctypes.c_int), ("phase_ms", ctypes.c_double * 4), ("lane_map", ctypes.c_int),
-                ("n_candidates", ctypes.c_int), ("tune_ms", ctypes.c_double)]
+                ("n_candidates", ctypes.c_int), ("tune_ms", ctypes.c_double),
+                ("guess_ms", ctypes.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -87,6 +88,7 @@ SIGNATURES = [
     ("exx_guess_gradient", ctypes.c_int, [_ctx_p, _vp, _vp, ctypes.c_int, _f, _f, _vp]),
     ("exx_guess_train_step", ctypes.c_int, [_ctx_p, _vp, _vp, ctypes.c_int, ctypes.c_float, _f, _vp]),
     ("exx_guess_destroy", None, [_ctx_p]),
+    ("exx_export_samples", ctypes.c_int, [_ctx_p, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _i, _vp]),
     ("exx_unet_conv3d", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
 ]
@@ -201,6 +203,18 @@ class Exx:
             _check(st, self._ctx)
         return e.value
 
+    def load_guess_model(self, blob: bytes):
+        """exx_load_guess_model: the learned warm start used by warm_start = 2."""
+        b = ctypes.create_string_buffer(bytes(blob), len(blob))
+        _check(load().exx_load_guess_model(self._ctx, b, len(blob)), self._ctx)
+
+    def export_samples(self, orbitals, S: int, inp, target, cap: int, stream=None) -> int:
+        """exx_export_samples after a warm_start = 1 call; returns the call's pair count."""
+        n = ctypes.c_int()
+        _check(load().exx_export_samples(self._ctx, _ptr(orbitals), int(S), _ptr(inp), _ptr(target), int(cap),
+                                         ctypes.byref(n), _stream_handle(stream)), self._ctx)
+        return n.value
+
     def stats(self) -> dict:
         s = exx_stats()
         _check(load().exx_get_stats(self._ctx, ctypes.byref(s)), self._ctx)
@@ -292,3 +306,12 @@ def unet_conv3d(x, w, bias, mask, y, batch, D, H, W, cin, cout, mode, stream=Non
     """One tensor-core 3x3x3 convolution (exx_unet_conv3d); device tensors."""
     _check(load().exx_unet_conv3d(_ptr(x), _ptr(w), _ptr(bias), _ptr(mask), _ptr(y), int(batch), int(D), int(H),
                                   int(W), int(cin), int(cout), int(mode), _stream_handle(stream)))
+
+
+GUESS_MAGIC = 0x47585845
+
+
+def guess_model_blob(S: int, params: np.ndarray) -> bytes:
+    """Model blob of exx_load_guess_model: {magic, 1, S, count} then the FP32 parameters."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    return np.array([GUESS_MAGIC, 1, int(S), p.size], dtype=np.int32).tobytes() + p.tobytes()

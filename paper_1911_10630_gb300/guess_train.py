@@ -1,0 +1,119 @@
+"""Training of the learned CG warm start (include/exx_guess.h).
+
+Samples come from the solver itself: each seeded workload of the tiny form
+(8 Gaussian orbitals in a 9-bohr cell on 48^3 points, R_PE = 16, R_ME = 20,
+every pair, CG to 1e-10) is solved with warm_start = 1, and
+exx_export_samples turns every pair's converged v_ij and its density into
+one (input, target) cube of side 32. The network then trains with Adam on the
+GPU through exx_guess_train_step; every step runs in the library's kernels.
+
+    python -m paper_1911_10630_gb300.guess_train --out guess_r16.bin
+
+The model blob is what exx_load_guess_model (warm_start = 2) expects.
+"""
+from __future__ import annotations
+
+import argparse
+import math
+import time
+
+import numpy as np
+
+from . import synth
+from .exx import Exx, GuessNet, guess_model_blob
+
+CUBE = 32  # network input side for R_PE = 16 (the ball's +16 poles fall outside)
+
+
+def init_params(n_params: int, seed: int) -> np.ndarray:
+    """He-uniform weights (bound sqrt(6 / fan_in)), zero biases, layer table of exx_guess.h."""
+    cin = (2, 16, 16, 32, 32, 64, 64, 128, 192, 64, 96, 32, 48, 16, 16)
+    cout = (16, 16, 32, 32, 64, 64, 128, 128, 64, 64, 32, 32, 16, 16, 1)
+    rng = np.random.default_rng(seed)
+    parts = []
+    for l, (a, b) in enumerate(zip(cin, cout)):
+        fan = a if l == len(cin) - 1 else 27 * a
+        parts.append(rng.uniform(-math.sqrt(6.0 / fan), math.sqrt(6.0 / fan), fan * b))
+        parts.append(np.zeros(b))
+    p = np.concatenate(parts).astype(np.float32)
+    if p.size != n_params:
+        raise RuntimeError("layer table does not match the library's network")
+    return p
+
+
+def solve_and_export(seeds, S: int = CUBE, torch=None):
+    """Solves each seeded tiny workload and returns the samples of all its
+    pairs as device tensors (input [n][S^3][2], target [n][S^3])."""
+    import torch as _t
+    torch = torch or _t
+    ins, tgts = [], []
+    ex = None
+    for seed in seeds:
+        w = synth.config0(seed)
+        if ex is None:
+            ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=1, warm_start=1)
+        phi = torch.from_numpy(w.orbitals()).cuda()
+        cen = torch.from_numpy(np.ascontiguousarray(w.centers)).cuda()
+        D = torch.empty_like(phi)
+        ex.compute(phi, cen, D)
+        cap = w.n * (w.n + 1) // 2
+        inp = torch.empty((cap, S, S, S, 2), dtype=torch.float32, device="cuda")
+        tgt = torch.empty((cap, S, S, S), dtype=torch.float32, device="cuda")
+        n = ex.export_samples(phi, S, inp, tgt, cap)
+        ins.append(inp[:n])
+        tgts.append(tgt[:n])
+    ex.close()
+    return torch.cat(ins), torch.cat(tgts)
+
+
+def train(inp, tgt, S: int = CUBE, epochs: int = 20, batch: int = 32, lr: float = 2e-3, seed: int = 0,
+          time_limit: float = 1e30, log=None):
+    """Adam on the samples (cosine-decayed learning rate); returns the net and the per-epoch mean loss."""
+    import torch
+    n = inp.shape[0]
+    net = GuessNet(S, batch)
+    net.set_params(init_params(net.n_params, seed))
+    rng = np.random.default_rng(seed + 1)
+    steps_per_epoch = max(1, n // batch)
+    total = epochs * steps_per_epoch
+    hist = []
+    t0 = time.time()
+    k = 0
+    for ep in range(epochs):
+        perm = torch.from_numpy(rng.permutation(n)).cuda()
+        acc = 0.0
+        for s in range(steps_per_epoch):
+            idx = perm[s * batch:(s + 1) * batch]
+            bi = inp.index_select(0, idx).contiguous()
+            bt = tgt.index_select(0, idx).contiguous()
+            a = lr * 0.5 * (1.0 + math.cos(math.pi * k / total))
+            acc += net.train_step(bi, bt, batch, max(a, 1e-3 * lr))
+            k += 1
+        hist.append(acc / steps_per_epoch)
+        if log:
+            log(f"epoch {ep} loss {hist[-1]:.4e} ({time.time() - t0:.1f} s)")
+        if time.time() - t0 > time_limit:
+            break
+    return net, hist
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--train-seeds", type=int, default=140)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    args = ap.parse_args()
+    import torch
+    t0 = time.time()
+    inp, tgt = solve_and_export(range(1000, 1000 + args.train_seeds), torch=torch)
+    print(f"{inp.shape[0]} samples in {time.time() - t0:.1f} s", flush=True)
+    net, hist = train(inp, tgt, epochs=args.epochs, batch=args.batch, lr=args.lr, log=print)
+    with open(args.out, "wb") as f:
+        f.write(guess_model_blob(CUBE, net.get_params()))
+    print("loss", hist[0], "->", hist[-1])
+
+
+if __name__ == "__main__":
+    main()
