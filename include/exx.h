@@ -73,18 +73,26 @@ typedef struct {
     int max_iter;      /* CG iteration cap per solve (default 20000).            */
     int inner_max_iter;/* FP32 inner iterations per refinement step (default 4000) */
     double inner_tol;  /* FP32 inner relative tolerance (default 1e-5).          */
-    int threads;       /* threads per CTA, 0 = library choice.                   */
+    int threads;       /* threads per CTA, 0 = library choice, else a multiple of
+                          32 in [256, 1024]; the one-CTA solver runs 256, 512
+                          or 1024 (other values give 512), the cluster solver
+                          only the launch shapes it is built for.               */
     int ctas_per_sm;   /* resident CTAs per SM, 0 = library choice.              */
     int solver_kind;   /* 0 = library choice; 1 = one CTA per pair with state in
                           global memory; 2 = one thread-block cluster per pair
                           with the FP32 inner state in shared memory.            */
-    int cluster_size;  /* CTAs per cluster for solver_kind 2 (0 = library choice) */
+    int cluster_size;  /* CTAs per cluster for solver_kind 2: 0 = library choice,
+                          else 2, 4, 8 or 9 (9 with the non-portable cluster
+                          size opt-in; on GB300, 15 clusters of 9 CTAs fit
+                          against 15 of 8).                                      */
     double update_drop;/* cluster solver: the FP64 residual replaces the FP32 one
                           each time the FP32 residual has dropped by this factor
                           (reliable updates; default 1e-3).                      */
     int lane_map;      /* cluster solver thread-to-point map: 0 = natural order
                           (contiguous warps, default), 1 = bank-distinct lanes
-                          dealt plane by plane.                                  */
+                          dealt plane by plane, 2 = each thread owns a run of
+                          consecutive points of a row (z neighbours in
+                          registers; runs of a warp in distinct banks).          */
     int autotune;      /* cluster solver: 1 = on the first exx_compute of a context
                           time every fitting launch shape (cluster size, threads
                           per CTA, lane map) on a prefix of the pair queue and

@@ -41,6 +41,9 @@ cudaError_t launch_cluster_kernel(int variant, const SolveParams& P, const Clust
                                   size_t smem, cudaStream_t st);
 int cluster_variant_threads(int variant);
 int cluster_variant_pts(int variant);
+int cluster_variant_runs(int variant);
+int cluster_variant_count();
+int cluster_variant_size(int variant);
 }  // namespace exx
 
 using namespace exx;
@@ -314,13 +317,14 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (o.inner_max_iter <= 0) o.inner_max_iter = 4000;
     if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) o.inner_tol = 1e-5;
     if (!(o.update_drop > 0.0 && o.update_drop < 1.0)) o.update_drop = 1e-3;
-    if (o.threads != 0 && o.threads != 256 && o.threads != 512 && o.threads != 1024)
-        return fail(nullptr, EXX_EINVAL, "exx_init: threads must be 0, 256, 512 or 1024");
+    if (o.threads != 0 && (o.threads < 256 || o.threads > 1024 || o.threads % 32))
+        return fail(nullptr, EXX_EINVAL, "exx_init: threads must be 0 or a multiple of 32 in [256, 1024]");
     if (o.solver_kind < 0 || o.solver_kind > 2) return fail(nullptr, EXX_EINVAL, "exx_init: solver_kind must be 0, 1 or 2");
     if (o.solver_kind == 2 && o.precision != 1)
         return fail(nullptr, EXX_EINVAL, "exx_init: solver_kind 2 (cluster) runs the FP32 inner solver: precision must be 1");
-    if (o.cluster_size != 0 && o.cluster_size != 2 && o.cluster_size != 4 && o.cluster_size != 8)
-        return fail(nullptr, EXX_EINVAL, "exx_init: cluster_size must be 0, 2, 4 or 8");
+    if (o.cluster_size != 0 && o.cluster_size != 2 && o.cluster_size != 4 && o.cluster_size != 8 &&
+        o.cluster_size != 9)
+        return fail(nullptr, EXX_EINVAL, "exx_init: cluster_size must be 0, 2, 4, 8 or 9");
 
     c = new exx_ctx();
     std::memset(&c->stats, 0, sizeof(c->stats));
@@ -467,8 +471,8 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (o.precision == 1 && o.solver_kind != 1 && c->n_geo == 1) {
         int max_optin = 0;
         cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-        const int csizes[3] = {8, 4, 2};
-        for (int ci = 0; ci < 3; ++ci) {
+        const int csizes[4] = {9, 8, 4, 2};
+        for (int ci = 0; ci < 4; ++ci) {
             const int C = csizes[ci];
             if (o.cluster_size && o.cluster_size != C) continue;
             ClusterLayout L;
@@ -476,17 +480,15 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             if (!build_cluster_layout(B, C, L, pt)) continue;
             int* d_pt = nullptr;
             int4* d_ri = nullptr;
-            for (int nt : {1024, 512}) {
-                if (o.threads && o.threads != nt) continue;
-                const int v = cluster_variant(C, L.max_pts, nt);
-                if (v < 0) continue;
+            // one candidate: variant v with thread map (spk, sk) and lane map lm
+            auto add_cand = [&](int v, int lm, const std::vector<int>& spk, const std::vector<int>& sk) -> exx_status {
                 const size_t sm = cluster_kernel_smem(Rc, L, v);
-                if ((long)sm + 2048 > (long)max_optin) continue;
+                if ((long)sm + 2048 > (long)max_optin) return EXX_OK;
                 int nclu = 0;
                 e = cluster_prepare(v, sm, &nclu);
                 if (e != cudaSuccess || nclu < 1) {
                     (void)cudaGetLastError();
-                    continue;
+                    return EXX_OK;
                 }
                 if (!d_pt) {
                     e = cudaMalloc(&d_pt, sizeof(int) * pt.size());
@@ -497,33 +499,52 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                     if (e == cudaSuccess) e = cudaMalloc(&d_ri, sizeof(int4) * C);
                     if (e == cudaSuccess) c->cl_mem.push_back(d_ri);
                     if (e == cudaSuccess) e = cudaMemcpy(d_ri, ri, sizeof(int4) * C, cudaMemcpyHostToDevice);
-                    if (e != cudaSuccess) return bail(cuda_fail(c, e, "slab tables"));
+                    if (e != cudaSuccess) return cuda_fail(c, e, "slab tables");
                 }
+                int* d_slot = nullptr;
+                e = cudaMalloc(&d_slot, sizeof(int) * (spk.size() + sk.size()));
+                if (e == cudaSuccess) c->cl_mem.push_back(d_slot);
+                if (e == cudaSuccess) e = cudaMemcpy(d_slot, spk.data(), sizeof(int) * spk.size(), cudaMemcpyHostToDevice);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(d_slot + spk.size(), sk.data(), sizeof(int) * sk.size(), cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) return cuda_fail(c, e, "slot maps");
+                exx_ctx::ClusterCand K;
+                K.C = C;
+                K.variant = v;
+                K.lane_map = lm;
+                K.n_clusters = nclu;
+                K.smem = sm;
+                K.L = L;
+                K.L.pt_slab = d_pt;
+                K.L.rank_info = d_ri;
+                K.L.slot_pk = d_slot;
+                K.L.slot_k = d_slot + spk.size();
+                c->cands.push_back(K);
+                return EXX_OK;
+            };
+            // z-run thread maps (lane map 2): only on request (slower than the
+            // point map on GB300 so far: the run arrays do not stay in registers)
+            for (int v = 0; v < cluster_variant_count(); ++v) {
+                if (!cluster_variant_runs(v) || cluster_variant_size(v) != C) continue;
+                if (o.threads && o.threads != cluster_variant_threads(v)) continue;
+                if (o.lane_map != 2) continue;
+                std::vector<int> spk, sk;
+                if (build_run_maps(L, pt, cluster_variant_threads(v), cluster_variant_pts(v), spk, sk) < 0) continue;
+                const exx_status sa = add_cand(v, 2, spk, sk);
+                if (sa != EXX_OK) return bail(sa);
+            }
+            // one point per thread slot (lane maps 0 and 1)
+            for (int nt : {1024, 512}) {
+                if (o.threads && o.threads != nt) continue;
+                const int v = cluster_variant(C, L.max_pts, nt);
+                if (v < 0) continue;
                 for (int lm = 0; lm <= 1; ++lm) {
                     if (!o.autotune && lm != o.lane_map) continue;
                     std::vector<int> spk, sk;
                     if (build_slot_maps(L, pt, cluster_variant_threads(v), cluster_variant_pts(v), lm, spk, sk) < 0)
                         continue;
-                    int* d_slot = nullptr;
-                    e = cudaMalloc(&d_slot, sizeof(int) * (spk.size() + sk.size()));
-                    if (e == cudaSuccess) c->cl_mem.push_back(d_slot);
-                    if (e == cudaSuccess)
-                        e = cudaMemcpy(d_slot, spk.data(), sizeof(int) * spk.size(), cudaMemcpyHostToDevice);
-                    if (e == cudaSuccess)
-                        e = cudaMemcpy(d_slot + spk.size(), sk.data(), sizeof(int) * sk.size(), cudaMemcpyHostToDevice);
-                    if (e != cudaSuccess) return bail(cuda_fail(c, e, "slot maps"));
-                    exx_ctx::ClusterCand K;
-                    K.C = C;
-                    K.variant = v;
-                    K.lane_map = lm;
-                    K.n_clusters = nclu;
-                    K.smem = sm;
-                    K.L = L;
-                    K.L.pt_slab = d_pt;
-                    K.L.rank_info = d_ri;
-                    K.L.slot_pk = d_slot;
-                    K.L.slot_k = d_slot + spk.size();
-                    c->cands.push_back(K);
+                    const exx_status sa = add_cand(v, lm, spk, sk);
+                    if (sa != EXX_OK) return bail(sa);
                 }
             }
         }
@@ -547,7 +568,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         return bail(fail(c, EXX_EINVAL, "exx_init: warm_start 1 and 2 need the cluster solver, which does not fit these radii"));
     if (c->use_cluster) apply_cand(c, c->cand);
 
-    c->threads = c->use_cluster ? c->threads : (o.threads ? o.threads : 512);
+    c->threads = c->use_cluster ? c->threads : ((o.threads == 256 || o.threads == 1024) ? o.threads : 512);
     if (!c->use_cluster) c->smem = pair_kernel_smem(Rc, r_pe);
     int bps = 0;
     long long want;

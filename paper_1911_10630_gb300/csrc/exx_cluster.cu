@@ -127,8 +127,15 @@ __device__ __noinline__ void cta_warm_store(const int* __restrict__ cube, const 
     for (int k = k0 + (int)threadIdx.x; k < k1; k += nt) vdst[k] = (float)vc[cube[k]];
 }
 
-template <int NT, int C, int PTS>
-__global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P, const ClusterLayout CL) {
+// RUNS = false: thread slot j of a thread holds one point of the slab (the
+// [PTS][NT] point map). RUNS = true: the thread owns one run of at most PTS
+// consecutive points of a slab row; the run's p values and their z neighbours
+// stay in registers, so a point costs 12 shared loads (y and x legs) plus a
+// share of the run's PTS + 6 z loads, and the thread map puts the runs of a
+// warp in distinct banks.
+template <int NT, int C, int PTS, bool RUNS>
+__global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_constant__ SolveParams P,
+                                                             const __grid_constant__ ClusterLayout CL) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     extern __shared__ double smem[];
@@ -138,6 +145,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
     __shared__ float part32[2][16];
     __shared__ double s_M[kNMono], s_T[kNMono];
     __shared__ int s_item;
+    __shared__ float s_zero[PTS + 8];
     int flip = 0, cflip = 0, flip32 = 0, cflip32 = 0;
 
     const int Rc = P.Rc;
@@ -148,7 +156,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
     // shared memory: the p slab, then the CG correction d and the point map, [PTS][NT] each
     float* ps = reinterpret_cast<float*>(smem);
     float* ds = ps + ((CL.cap_planes * CL.Sp2 + 3) & ~3);  // 16-byte aligned
-    int* spk = reinterpret_cast<int*>(ds + PTS * NT);
+    int* spk = RUNS ? nullptr : reinterpret_cast<int*>(ds + PTS * NT);
     // the shell phase's per-warp coefficient buffers reuse ds (idle outside the CG)
     double* ub = reinterpret_cast<double*>(ds) + (threadIdx.x >> 5) * (kNU + kNU / 2);
     const int Syz = CL.Syz;
@@ -162,9 +170,36 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
     const int planes = me.y;
     const int planes_prev = rank > 0 ? CL.rank_info[rank - 1].y : 0;
     const int k0 = me.z, k1 = me.w;
-    const int* slot_k = CL.slot_k + (size_t)rank * PTS * NT;
+    const int* slot_k = RUNS ? nullptr : CL.slot_k + (size_t)rank * PTS * NT;
+    // RUNS: this thread's run (slab offset, plane, first compact index, length)
+    int roff = 0, rxl = 0, rk0 = 0, rlen = 0;
+    const float* xpa[3] = {nullptr, nullptr, nullptr};
+    const float* xma[3] = {nullptr, nullptr, nullptr};
+    if constexpr (RUNS) {
+        for (int t = threadIdx.x; t < PTS + 8; t += NT) s_zero[t] = 0.0f;
+        const int rpk = CL.slot_pk[(size_t)rank * NT + threadIdx.x];
+        const int rk = CL.slot_k[(size_t)rank * NT + threadIdx.x];
+        if (rpk >= 0) {
+            roff = rpk & 0xffffff;
+            rxl = rpk >> 24;
+            rlen = rk >> 24;
+            rk0 = rk & 0xffffff;
+        }
+        // x legs of the run (generic pointers): own slab, a neighbour's slab
+        // through distributed shared memory, or zeros beyond the ball
+        const float* nxt = rank < C - 1 ? cl.map_shared_rank(ps, rank + 1) : nullptr;
+        const float* prv = rank > 0 ? cl.map_shared_rank(ps, rank - 1) : nullptr;
+        const int pl = CL.rank_info[rank].y, plp = rank > 0 ? CL.rank_info[rank - 1].y : 0;
 #pragma unroll
-    for (int j = 0; j < PTS; ++j) spk[j * NT + threadIdx.x] = CL.slot_pk[(size_t)rank * PTS * NT + j * NT + threadIdx.x];
+        for (int q = 1; q <= 3; ++q) {
+            xpa[q - 1] = rxl + q < pl ? ps + roff + q * CL.Sp2 : (nxt ? nxt + roff + (q - pl) * CL.Sp2 : s_zero);
+            xma[q - 1] = rxl - q >= 0 ? ps + roff - q * CL.Sp2 : (prv ? prv + roff + (plp - q) * CL.Sp2 : s_zero);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < PTS; ++j)
+            spk[j * NT + threadIdx.x] = CL.slot_pk[(size_t)rank * PTS * NT + j * NT + threadIdx.x];
+    }
 
     const int cid = blockIdx.x / C;
     char* slot = P.ws + (size_t)cid * P.slot_bytes;
@@ -244,7 +279,123 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const SolveParams P
                 }
             }
         }
-        if (rn_start > target2 && rn_start == rn_start) {
+        if (RUNS && rn_start > target2 && rn_start == rn_start) {
+            // r and d of the run in shared memory ([PTS][NT], conflict-free),
+            // A p in registers, p and its z neighbours in registers
+            float* rs = ds + PTS * NT;
+            double scale = sqrt(rn_start);
+            float ap[PTS], pz[PTS + 6];
+            float a32 = 0.0f;
+            {
+                const double inv = 1.0 / scale;
+#pragma unroll
+                for (int j = 0; j < PTS; ++j) {
+                    ds[j * NT + threadIdx.x] = 0.0f;
+                    float rj = 0.0f;
+                    if (j < rlen) {
+                        rj = (float)(r64[rk0 + j] * inv);
+                        ps[roff + j] = rj;
+                        a32 = fmaf(rj, rj, a32);
+                    }
+                    rs[j * NT + threadIdx.x] = rj;
+                }
+            }
+            float rr = cluster_sum<NT, C, float>(a32, red32, flip32, part32, cflip32, cl, rank);
+            float maxrr = rr;
+            const float drop2 = (float)(P.update_drop * P.update_drop);
+            float conv_thr = (float)(0.25 * target2 / (scale * scale));
+            for (;;) {
+                if (iters >= P.max_iter) {
+                    conv = false;
+                    break;
+                }
+                float pa = 0.0f;
+                if (rlen > 0) {
+                    // the run's p and its z neighbours
+#pragma unroll
+                    for (int m = 0; m < PTS + 6; ++m) pz[m] = ps[roff - 3 + m];
+#pragma unroll
+                    for (int j = 0; j < PTS; ++j) {
+                        const int o = roff + j;
+                        const float sz1 = pz[j + 4] + pz[j + 2], sz2 = pz[j + 5] + pz[j + 1], sz3 = pz[j + 6] + pz[j];
+                        const float sy1 = ps[o + Syz] + ps[o - Syz], sy2 = ps[o + 2 * Syz] + ps[o - 2 * Syz],
+                                    sy3 = ps[o + 3 * Syz] + ps[o - 3 * Syz];
+                        const float sx1 = xpa[0][j] + xma[0][j];
+                        const float sx2 = xpa[1][j] + xma[1][j];
+                        const float sx3 = xpa[2][j] + xma[2][j];
+                        const float az = fmaf(st.cz[0], sz1, fmaf(st.cz[1], sz2, st.cz[2] * sz3));
+                        const float ay = fmaf(st.cy[0], sy1, fmaf(st.cy[1], sy2, st.cy[2] * sy3));
+                        const float ax = fmaf(st.cx[0], sx1, fmaf(st.cx[1], sx2, st.cx[2] * sx3));
+                        const float a = fmaf(st.c0, pz[j + 3], (az + ay) + ax);
+                        ap[j] = -a;
+                        if (j < rlen) pa = fmaf(pz[j + 3], -a, pa);
+                    }
+                }
+                const float pap = cluster_sum<NT, C, float>(pa, red32, flip32, part32, cflip32, cl, rank);
+                const float al = rr / pap;
+                float ra = 0.0f;
+#pragma unroll
+                for (int j = 0; j < PTS; ++j) {
+                    if (j < rlen) {
+                        float* dj = ds + j * NT + threadIdx.x;
+                        float* rj = rs + j * NT + threadIdx.x;
+                        *dj = fmaf(al, pz[j + 3], *dj);
+                        const float rn = fmaf(-al, ap[j], *rj);
+                        *rj = rn;
+                        ra = fmaf(rn, rn, ra);
+                    }
+                }
+                const float rrn = cluster_sum<NT, C, float>(ra, red32, flip32, part32, cflip32, cl, rank);
+                ++iters;
+                const bool update = rrn <= drop2 * maxrr || rrn <= conv_thr || !(rrn == rrn);
+                if (update) {
+                    const long long tu = clk ? clock64() : 0;
+#pragma unroll
+                    for (int j = 0; j < PTS; ++j) {  // v += scale d
+                        if (j < rlen) {
+                            const int c = cube[rk0 + j];
+                            vc[c] = fma(scale, (double)ds[j * NT + threadIdx.x], vc[c]);
+                        }
+                    }
+                    cl.sync();
+                    acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, false);
+                    const double rn2 = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
+                    ++refines;
+                    if (clk) tr += clock64() - tu;
+                    if (rn2 <= target2) break;
+                    if (refines > P.max_refine || !(rn2 < scale * scale)) {
+                        conv = false;
+                        break;
+                    }
+                    const double ns = sqrt(rn2);
+                    const float carry = (float)(ns / scale) / rr;
+                    const double inv = 1.0 / ns;
+                    a32 = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < PTS; ++j) {
+                        if (j < rlen) {
+                            const float rj = (float)(r64[rk0 + j] * inv);
+                            rs[j * NT + threadIdx.x] = rj;
+                            ds[j * NT + threadIdx.x] = 0.0f;
+                            ps[roff + j] = fmaf(carry, ps[roff + j], rj);
+                            a32 = fmaf(rj, rj, a32);
+                        }
+                    }
+                    rr = cluster_sum<NT, C, float>(a32, red32, flip32, part32, cflip32, cl, rank);
+                    maxrr = rr;
+                    scale = ns;
+                    conv_thr = (float)(0.25 * target2 / (scale * scale));
+                    continue;
+                }
+                const float be = rrn / rr;
+                rr = rrn;
+#pragma unroll
+                for (int j = 0; j < PTS; ++j)
+                    if (j < rlen) ps[roff + j] = fmaf(be, pz[j + 3], rs[j * NT + threadIdx.x]);
+                cl.sync();
+            }
+        }
+        if (!RUNS && rn_start > target2 && rn_start == rn_start) {
             double scale = sqrt(rn_start);
             float r[PTS], ap[PTS];
             float a32 = 0.0f;
@@ -397,19 +548,15 @@ cudaError_t set_multipole_const_cluster(const MultipoleConst& mc) {
 
 size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant);
 
-template <int NT, int C, int PTS>
-static const void* kernel_ptr() {
-    return (const void*)cluster_pair_kernel<NT, C, PTS>;
-}
-
 // Supported (threads, cluster size, points per thread) instantiations.
 struct ClusterVariant {
     int nt, c, pts;
+    bool runs;
     const void* fn;
     cudaError_t (*launch)(const SolveParams&, const ClusterLayout&, int, size_t, cudaStream_t);
 };
 
-template <int NT, int C, int PTS>
+template <int NT, int C, int PTS, bool RUNS>
 static cudaError_t launch_cluster_t(const SolveParams& P, const ClusterLayout& CL, int n_clusters, size_t smem,
                                     cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
@@ -424,25 +571,29 @@ static cudaError_t launch_cluster_t(const SolveParams& P, const ClusterLayout& C
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, cluster_pair_kernel<NT, C, PTS>, P, CL);
+    return cudaLaunchKernelEx(&cfg, cluster_pair_kernel<NT, C, PTS, RUNS>, P, CL);
 }
 
+#define EXX_CLUSTER_VARIANT(NT, C, PTS, RUNS) \
+    {NT, C, PTS, RUNS, (const void*)cluster_pair_kernel<NT, C, PTS, RUNS>, launch_cluster_t<NT, C, PTS, RUNS>}
 static const ClusterVariant kVariants[] = {
-    {512, 2, 8, (const void*)cluster_pair_kernel<512, 2, 8>, launch_cluster_t<512, 2, 8>},
-    {512, 2, 18, (const void*)cluster_pair_kernel<512, 2, 18>, launch_cluster_t<512, 2, 18>},
-    {512, 4, 10, (const void*)cluster_pair_kernel<512, 4, 10>, launch_cluster_t<512, 4, 10>},
-    {512, 4, 18, (const void*)cluster_pair_kernel<512, 4, 18>, launch_cluster_t<512, 4, 18>},
-    {512, 8, 17, (const void*)cluster_pair_kernel<512, 8, 17>, launch_cluster_t<512, 8, 17>},
-    {1024, 8, 9, (const void*)cluster_pair_kernel<1024, 8, 9>, launch_cluster_t<1024, 8, 9>},
+    EXX_CLUSTER_VARIANT(512, 2, 8, false),   EXX_CLUSTER_VARIANT(512, 2, 18, false),
+    EXX_CLUSTER_VARIANT(512, 4, 10, false),  EXX_CLUSTER_VARIANT(512, 4, 18, false),
+    EXX_CLUSTER_VARIANT(512, 8, 17, false),  EXX_CLUSTER_VARIANT(1024, 8, 9, false),
+    EXX_CLUSTER_VARIANT(1024, 9, 8, false),
+    EXX_CLUSTER_VARIANT(1024, 8, 10, true),  EXX_CLUSTER_VARIANT(1024, 4, 10, true),
+    EXX_CLUSTER_VARIANT(1024, 2, 12, true),
 };
+#undef EXX_CLUSTER_VARIANT
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
 // Picks the instantiation for (C, max points per CTA, preferred threads).
 // Returns the index into kVariants or -1.
 int cluster_variant(int C, int max_pts, int threads) {
     int best = -1;
-    for (int v = 0; v < (int)(sizeof(kVariants) / sizeof(kVariants[0])); ++v) {
+    for (int v = 0; v < kNumVariants; ++v) {
         const ClusterVariant& K = kVariants[v];
-        if (K.c != C || K.nt * K.pts < max_pts) continue;
+        if (K.runs || K.c != C || K.nt * K.pts < max_pts) continue;
         if (threads && K.nt != threads) continue;
         // prefer more threads (more warps to hide shared-memory and barrier
         // latency), then the smallest per-thread point capacity
@@ -457,6 +608,10 @@ cudaError_t cluster_prepare(int variant, size_t smem, int* max_clusters) {
     const ClusterVariant& K = kVariants[variant];
     cudaError_t e = cudaFuncSetAttribute(K.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (K.c > 8) {  // clusters beyond the portable size of 8 need the opt-in
+        e = cudaFuncSetAttribute(K.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(K.c, 1, 1);
     cfg.blockDim = dim3(K.nt, 1, 1);
@@ -477,12 +632,16 @@ cudaError_t launch_cluster_kernel(int variant, const SolveParams& P, const Clust
 }
 
 int cluster_variant_threads(int variant) { return kVariants[variant].nt; }
+int cluster_variant_runs(int variant) { return kVariants[variant].runs ? 1 : 0; }
+int cluster_variant_count() { return kNumVariants; }
+int cluster_variant_size(int variant) { return kVariants[variant].c; }
 int cluster_variant_pts(int variant) { return kVariants[variant].pts; }
 
 size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant) {
     (void)Rc;
     const size_t per = (size_t)kVariants[variant].nt * kVariants[variant].pts;
-    return sizeof(float) * ((((size_t)CL.cap_planes * CL.Sp2 + 3) & ~(size_t)3) + per) + sizeof(int) * per;
+    // slab, then d [PTS][NT], then the point map (one point per slot) or r (runs)
+    return sizeof(float) * ((((size_t)CL.cap_planes * CL.Sp2 + 3) & ~(size_t)3) + per) + 4 * per;
 }
 
 }  // namespace exx

@@ -305,4 +305,81 @@ int build_slot_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int
     return conflicted;
 }
 
+int build_run_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int NT, int ZL,
+                   std::vector<int>& run_pk, std::vector<int>& run_k) {
+    run_pk.assign((size_t)L.C * NT, -1);
+    run_k.assign((size_t)L.C * NT, 0);
+    int max_runs = 0;
+    struct Run {
+        int pk, k, len;
+    };
+    for (int r = 0; r < L.C; ++r) {
+        // rows of the slab: maximal stretches of consecutive points whose slab
+        // offsets are consecutive (same plane and row, z ascending)
+        std::vector<Run> runs;
+        int hist[32] = {0};  // runs starting in each bank
+        int k = L.k0[r];
+        while (k < L.k1[r]) {
+            int e = k + 1;
+            while (e < L.k1[r] && (pt_slab[e] & 0xffffff) == (pt_slab[e - 1] & 0xffffff) + 1 &&
+                   (pt_slab[e] >> 24) == (pt_slab[k] >> 24))
+                ++e;
+            // the row [k, e) in n = ceil(len / ZL) pieces of at most ZL points;
+            // each later piece starts where its bank is least used so far
+            // (near the even split on ties), so warps can draw distinct banks
+            const int len = e - k, n = (len + ZL - 1) / ZL;
+            int at = k;
+            for (int q = 0; q < n; ++q) {
+                int next = e;
+                if (q + 1 < n) {
+                    const int lo = std::max(at + 1, e - (n - q - 1) * ZL), hi = std::min(at + ZL, e - (n - q - 1));
+                    const int even = k + (int)((long)len * (q + 1) / n);
+                    next = -1;
+                    for (int c = lo; c <= hi; ++c) {
+                        const int b = (pt_slab[c] & 0xffffff) & 31;
+                        if (next < 0 || hist[b] < hist[(pt_slab[next] & 0xffffff) & 31] ||
+                            (hist[b] == hist[(pt_slab[next] & 0xffffff) & 31] && std::abs(c - even) < std::abs(next - even)))
+                            next = c;
+                    }
+                }
+                runs.push_back({pt_slab[at], at, next - at});
+                ++hist[(pt_slab[at] & 0xffffff) & 31];
+                at = next;
+            }
+            k = e;
+        }
+        if ((int)runs.size() > NT) return -1;
+        max_runs = std::max(max_runs, (int)runs.size());
+        // lanes: each warp takes runs whose first points lie in distinct banks
+        // (then every load of the warp hits 32 banks), drawing from the
+        // fullest banks first so that the banks run out evenly
+        std::vector<std::vector<int>> bucket(32);
+        for (size_t q = 0; q < runs.size(); ++q) bucket[(runs[q].pk & 0xffffff) & 31].push_back((int)q);
+        std::vector<int> lane_run;
+        size_t left = runs.size();
+        while (left > 0) {
+            std::vector<int> order(32);
+            for (int b = 0; b < 32; ++b) order[b] = b;
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int a, int b) { return bucket[a].size() > bucket[b].size(); });
+            int got = 0;
+            for (int pass = 0; pass < 32 && got < 32 && left > 0; ++pass)
+                for (int q = 0; q < 32 && got < 32 && left > 0; ++q) {
+                    std::vector<int>& bk = bucket[order[q]];
+                    if ((int)bk.size() <= pass) continue;
+                    lane_run.push_back(bk.back());
+                    bk.pop_back();
+                    ++got;
+                    --left;
+                }
+        }
+        for (size_t t = 0; t < lane_run.size(); ++t) {
+            const Run& R = runs[lane_run[t]];
+            run_pk[(size_t)r * NT + t] = R.pk;
+            run_k[(size_t)r * NT + t] = (R.len << 24) | R.k;
+        }
+    }
+    return max_runs;
+}
+
 }  // namespace exx

@@ -37,5 +37,12 @@ void build_ball(HostBall& B, int r_pe, int r_me, int Rc);
 // two-row bank conflict).
 int build_slot_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int NT, int PTS, int bank_aware,
                     std::vector<int>& slot_pk, std::vector<int>& slot_k);
+// Thread map of the z-run cluster solver: every thread owns one run of at
+// most ZL consecutive points of one slab row. run_pk[rank][t] = slab offset
+// of the run's first point | plane << 24 (-1: idle thread); run_k[rank][t] =
+// first compact PE index | length << 24. Returns the largest run count of a
+// rank, or -1 if a rank has more runs than NT.
+int build_run_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int NT, int ZL,
+                   std::vector<int>& run_pk, std::vector<int>& run_k);
 
 }  // namespace exx

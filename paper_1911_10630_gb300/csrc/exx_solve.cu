@@ -79,7 +79,7 @@ __device__ int cg_ball(T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d,
 // The persistent pair kernel.
 // --------------------------------------------------------------------------
 template <int NT, bool MIXED>
-__global__ void __launch_bounds__(NT, 1) pair_kernel(const SolveParams P) {
+__global__ void __launch_bounds__(NT, 1) pair_kernel(const __grid_constant__ SolveParams P) {
     extern __shared__ double smem[];
     __shared__ double red[2][33];
     __shared__ float red32[2][33];

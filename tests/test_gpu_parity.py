@@ -39,14 +39,19 @@ def _pairs_equal(gpu_pairs, ref_pairs):
     np.testing.assert_array_equal(gpu_pairs["g"], g)
 
 
-@pytest.mark.parametrize("precision,solver_kind,cluster_size", [(0, 1, 0), (1, 1, 0), (1, 2, 8), (1, 2, 4),
-                                                               (1, 2, 2)])
-def test_cfg0_end_to_end(torch, cfg0, precision, solver_kind, cluster_size):
+@pytest.mark.parametrize("precision,solver_kind,cluster_size,lane_map", [
+    (0, 1, 0, None), (1, 1, 0, None), (1, 2, 9, None), (1, 2, 8, None), (1, 2, 4, None), (1, 2, 2, None),
+    (1, 2, 8, 0), (1, 2, 8, 2), (1, 2, 4, 2), (1, 2, 2, 2)])
+def test_cfg0_end_to_end(torch, cfg0, precision, solver_kind, cluster_size, lane_map):
     w, phi, ref = cfg0
-    out = run_gpu(w, phi, torch=torch, precision=precision, solver_kind=solver_kind, cluster_size=cluster_size)
+    extra = {} if lane_map is None else dict(lane_map=lane_map, autotune=0)
+    out = run_gpu(w, phi, torch=torch, precision=precision, solver_kind=solver_kind, cluster_size=cluster_size,
+                  **extra)
     assert out["stats"]["solver_kind"] == solver_kind
     if cluster_size:
         assert out["stats"]["cluster_size"] == cluster_size
+    if lane_map is not None:
+        assert out["stats"]["lane_map"] == lane_map
     _pairs_equal(out["pairs"], ref["pairs"])
     assert out["stats"]["n_pair"] == 36 and out["stats"]["n_nonconv"] == 0
     assert abs(out["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
@@ -180,14 +185,18 @@ def test_iteration_cap_reports_nonconvergence(torch, cfg0):
     assert np.isfinite(out["E_xx"])
 
 
-@pytest.mark.parametrize("precision", [1, 0])
-def test_water64_full_size_sampled(torch, precision):
+@pytest.mark.parametrize("precision,lane_map", [(1, None), (1, 2), (0, None)])
+def test_water64_full_size_sampled(torch, precision, lane_map):
     """The bench workload (water-64 scale, 120^3, 256 orbitals, R_pair = 10 bohr,
-    R_PE/R_ME = 24/32, tol 1e-8) in the launch configuration bench.py times;
-    checked on sampled pairs and sampled orbitals the oracle computes one by one."""
+    R_PE/R_ME = 24/32, tol 1e-8) in the launch configuration bench.py times
+    (autotuned), and with the z-run thread map forced; checked on sampled pairs
+    and sampled orbitals the oracle computes one by one."""
     w = synth.config1()
     phi = w.orbitals()
-    out = run_gpu(w, phi, torch=torch, precision=precision)
+    extra = {} if lane_map is None else dict(lane_map=lane_map, autotune=0)
+    out = run_gpu(w, phi, torch=torch, precision=precision, **extra)
+    if lane_map is not None:
+        assert out["stats"]["lane_map"] == lane_map
     ref_pairs = oracle.pair_list(w.centers, w.cell, w.grid, w.r_pair)
     _pairs_equal(out["pairs"], ref_pairs)
     npair = len(ref_pairs[0])
