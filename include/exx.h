@@ -92,7 +92,9 @@ typedef struct {
                           (contiguous warps, default), 1 = bank-distinct lanes
                           dealt plane by plane, 2 = each thread owns a run of
                           consecutive points of a row (z neighbours in
-                          registers; runs of a warp in distinct banks).          */
+                          registers, runs of a warp in distinct banks, halo
+                          planes filled by the neighbours; isotropic grids
+                          with R_PE 16 or 24; only when requested).             */
     int autotune;      /* cluster solver: 1 = on the first exx_compute of a context
                           time every fitting launch shape (cluster size, threads
                           per CTA, lane map) on a prefix of the pair queue and

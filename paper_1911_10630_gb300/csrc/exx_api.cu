@@ -42,6 +42,7 @@ cudaError_t launch_cluster_kernel(int variant, const SolveParams& P, const Clust
 int cluster_variant_threads(int variant);
 int cluster_variant_pts(int variant);
 int cluster_variant_runs(int variant);
+int cluster_variant_syz(int variant);
 int cluster_variant_count();
 int cluster_variant_size(int variant);
 }  // namespace exx
@@ -522,10 +523,15 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                 c->cands.push_back(K);
                 return EXX_OK;
             };
-            // z-run thread maps (lane map 2): only on request (slower than the
-            // point map on GB300 so far: the run arrays do not stay in registers)
+            const bool isotropic = c->delta[0] == c->delta[1] && c->delta[1] == c->delta[2];
+            // z-run thread maps with halo planes (lane map 2): only on request;
+            // on GB300 the point map is faster (the halo copies add a remote
+            // store for nearly every point of a thin slab, and the cluster
+            // barrier waits for them)
             for (int v = 0; v < cluster_variant_count(); ++v) {
                 if (!cluster_variant_runs(v) || cluster_variant_size(v) != C) continue;
+                if (cluster_variant_syz(v) && cluster_variant_syz(v) != L.Syz) continue;
+                if (!isotropic) continue;  // the run kernel's stencil has one spacing
                 if (o.threads && o.threads != cluster_variant_threads(v)) continue;
                 if (o.lane_map != 2) continue;
                 std::vector<int> spk, sk;

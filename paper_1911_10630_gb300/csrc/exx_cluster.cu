@@ -127,13 +127,141 @@ __device__ __noinline__ void cta_warm_store(const int* __restrict__ cube, const 
     for (int k = k0 + (int)threadIdx.x; k < k1; k += nt) vdst[k] = (float)vc[cube[k]];
 }
 
+// The z-run CG of one pair (RUNS = true), in segments between FP64 residual
+// replacements, each in its own register allocation: a segment (re)starts
+// from r = r64 / scale (p = r, or p = carry p + r after a replacement), runs
+// FP32 CG iterations until the recursive residual has dropped by update_drop
+// (or looks converged), adds scale d to v and returns; the caller then forms
+// the FP64 residual. The arrays and scalars a segment does not touch in its
+// inner loop come from a per-CTA block in shared memory, the reduction
+// buffers are file-scope shared arrays and the stencil is the isotropic one
+// (4 coefficients), so the run's registers fit the 64 a thread has at 1024
+// threads per CTA.
+struct RunSeg {
+    int iters, maxed;  // maxed: stopped at max_iter
+    float rr;          // r.r (in the segment's units) before the last iteration
+    int flip32, cflip32;
+};
+
+struct RunCgCtx {
+    const int* cube;
+    double* vc;
+    const double* r64;
+    int max_iter;
+    double target2;
+    float drop2;
+};
+
+__shared__ float g_rc_red32[2][33];
+__shared__ float g_rc_part32[2][16];
+__shared__ RunCgCtx g_rc;
+
+template <int NT, int C, int PTS, int SYZ>
+__device__ __noinline__ RunSeg run_segment(float* pcr, float* dst, float* hm, float* hp, int rk0, int rlen,
+                                           double scale, float carry, float c0, float c1, float c2, float c3,
+                                           int iters, int flip32, int cflip32) {
+    constexpr int Syz = SYZ, Sp2 = SYZ * SYZ;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    // p of the run: own slab plus the neighbours' halo copies
+    auto put_p = [&](int j, float v) {
+        pcr[j] = v;
+        if (hm) hm[j] = v;
+        if (hp) hp[j] = v;
+    };
+    float r[PTS], ap[PTS], pz[PTS + 6];
+    float a32 = 0.0f;
+    {
+        const double inv = 1.0 / scale;
+        const double* r64 = g_rc.r64;
+#pragma unroll
+        for (int j = 0; j < PTS; ++j) {
+            r[j] = 0.0f;
+            ap[j] = 0.0f;
+            dst[j * NT] = 0.0f;
+            if (j < rlen) {
+                r[j] = (float)(r64[rk0 + j] * inv);
+                put_p(j, carry < 0.0f ? r[j] : fmaf(carry, pcr[j], r[j]));
+                a32 = fmaf(r[j], r[j], a32);
+            }
+        }
+    }
+    float rr = cluster_sum<NT, C, float>(a32, g_rc_red32, flip32, g_rc_part32, cflip32, cl, rank);
+    const float lim = g_rc.drop2 * rr;
+    const float conv_thr = (float)(0.25 * g_rc.target2 / (scale * scale));
+    RunSeg out;
+    for (;;) {
+        if (iters >= g_rc.max_iter) {
+            out.maxed = 1;
+            break;
+        }
+        float pa = 0.0f;
+        if (rlen > 0) {
+#pragma unroll
+            for (int m = 0; m < PTS + 6; ++m) pz[m] = pcr[m - 3];
+#pragma unroll
+            for (int j = 0; j < PTS; ++j) {
+                const float s1 = (pz[j + 4] + pz[j + 2]) + (pcr[j + Syz] + pcr[j - Syz]) + (pcr[j + Sp2] + pcr[j - Sp2]);
+                const float s2 = (pz[j + 5] + pz[j + 1]) + (pcr[j + 2 * Syz] + pcr[j - 2 * Syz]) +
+                                 (pcr[j + 2 * Sp2] + pcr[j - 2 * Sp2]);
+                const float s3 = (pz[j + 6] + pz[j]) + (pcr[j + 3 * Syz] + pcr[j - 3 * Syz]) +
+                                 (pcr[j + 3 * Sp2] + pcr[j - 3 * Sp2]);
+                const float a = fmaf(c0, pz[j + 3], fmaf(c1, s1, fmaf(c2, s2, c3 * s3)));
+                ap[j] = -a;
+                if (j < rlen) pa = fmaf(pz[j + 3], -a, pa);
+            }
+        }
+        const float pap = cluster_sum<NT, C, float>(pa, g_rc_red32, flip32, g_rc_part32, cflip32, cl, rank);
+        const float al = rr / pap;
+        float ra = 0.0f;
+#pragma unroll
+        for (int j = 0; j < PTS; ++j) {
+            if (j < rlen) {
+                dst[j * NT] = fmaf(al, pz[j + 3], dst[j * NT]);
+                r[j] = fmaf(-al, ap[j], r[j]);
+                ra = fmaf(r[j], r[j], ra);
+            }
+        }
+        const float rrn = cluster_sum<NT, C, float>(ra, g_rc_red32, flip32, g_rc_part32, cflip32, cl, rank);
+        ++iters;
+        if (rrn <= lim || rrn <= conv_thr || !(rrn == rrn)) {
+            out.maxed = 0;
+            break;
+        }
+        const float be = rrn / rr;
+        rr = rrn;
+#pragma unroll
+        for (int j = 0; j < PTS; ++j)
+            if (j < rlen) put_p(j, fmaf(be, pz[j + 3], r[j]));
+        cl.sync();
+    }
+    // v += scale d
+    const int* cube = g_rc.cube;
+    double* vc = g_rc.vc;
+#pragma unroll
+    for (int j = 0; j < PTS; ++j) {
+        if (j < rlen) {
+            const int c = cube[rk0 + j];
+            vc[c] = fma(scale, (double)dst[j * NT], vc[c]);
+        }
+    }
+    out.iters = iters;
+    out.rr = rr;
+    out.flip32 = flip32;
+    out.cflip32 = cflip32;
+    return out;
+}
+
 // RUNS = false: thread slot j of a thread holds one point of the slab (the
-// [PTS][NT] point map). RUNS = true: the thread owns one run of at most PTS
-// consecutive points of a slab row; the run's p values and their z neighbours
-// stay in registers, so a point costs 12 shared loads (y and x legs) plus a
-// share of the run's PTS + 6 z loads, and the thread map puts the runs of a
-// warp in distinct banks.
-template <int NT, int C, int PTS, bool RUNS>
+// [PTS][NT] point map); x legs that leave the slab read the neighbour's slab.
+// RUNS = true: the thread owns one run of at most PTS consecutive points of a
+// slab row, and the slab carries 3 halo planes on each side that the
+// neighbours fill with remote stores whenever they write p; the stencil then
+// reads only the CTA's own shared memory at fixed offsets, the run's p values
+// and z neighbours stay in registers (a point costs 12 shared loads plus a
+// share of the run's PTS + 6), and the thread map puts the runs of a warp in
+// distinct banks.
+template <int NT, int C, int PTS, bool RUNS, int SYZ>
 __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_constant__ SolveParams P,
                                                              const __grid_constant__ ClusterLayout CL) {
     cg::cluster_group cl = cg::this_cluster();
@@ -145,7 +273,6 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
     __shared__ float part32[2][16];
     __shared__ double s_M[kNMono], s_T[kNMono];
     __shared__ int s_item;
-    __shared__ float s_zero[PTS + 8];
     int flip = 0, cflip = 0, flip32 = 0, cflip32 = 0;
 
     const int Rc = P.Rc;
@@ -155,14 +282,15 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
     const double* zp = yp + (2 * Rc + 1) * 8;
     // shared memory: the p slab, then the CG correction d and the point map, [PTS][NT] each
     float* ps = reinterpret_cast<float*>(smem);
-    float* ds = ps + ((CL.cap_planes * CL.Sp2 + 3) & ~3);  // 16-byte aligned
+    const int slab_floats = (CL.cap_planes + (RUNS ? 6 : 0)) * CL.Sp2;
+    float* ds = ps + ((slab_floats + 3) & ~3);  // 16-byte aligned
     int* spk = RUNS ? nullptr : reinterpret_cast<int*>(ds + PTS * NT);
     // the shell phase's per-warp coefficient buffers reuse ds (idle outside the CG)
     double* ub = reinterpret_cast<double*>(ds) + (threadIdx.x >> 5) * (kNU + kNU / 2);
     const int Syz = CL.Syz;
     const int Sp2 = CL.Sp2;
 
-    for (int t = threadIdx.x; t < CL.cap_planes * Sp2; t += NT) ps[t] = 0.0f;
+    for (int t = threadIdx.x; t < slab_floats; t += NT) ps[t] = 0.0f;
 
     float* pm = rank > 0 ? cl.map_shared_rank(ps, rank - 1) : nullptr;
     float* pp = rank < C - 1 ? cl.map_shared_rank(ps, rank + 1) : nullptr;
@@ -172,11 +300,12 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
     const int k0 = me.z, k1 = me.w;
     const int* slot_k = RUNS ? nullptr : CL.slot_k + (size_t)rank * PTS * NT;
     // RUNS: this thread's run (slab offset, plane, first compact index, length)
+    // and where its p values go in the neighbours' halo planes
     int roff = 0, rxl = 0, rk0 = 0, rlen = 0;
-    const float* xpa[3] = {nullptr, nullptr, nullptr};
-    const float* xma[3] = {nullptr, nullptr, nullptr};
+    float* pc = ps;                               // plane 0 of the CTA's slab
+    float *hm = nullptr, *hp = nullptr;
     if constexpr (RUNS) {
-        for (int t = threadIdx.x; t < PTS + 8; t += NT) s_zero[t] = 0.0f;
+        pc = ps + 3 * Sp2;
         const int rpk = CL.slot_pk[(size_t)rank * NT + threadIdx.x];
         const int rk = CL.slot_k[(size_t)rank * NT + threadIdx.x];
         if (rpk >= 0) {
@@ -185,16 +314,12 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
             rlen = rk >> 24;
             rk0 = rk & 0xffffff;
         }
-        // x legs of the run (generic pointers): own slab, a neighbour's slab
-        // through distributed shared memory, or zeros beyond the ball
-        const float* nxt = rank < C - 1 ? cl.map_shared_rank(ps, rank + 1) : nullptr;
-        const float* prv = rank > 0 ? cl.map_shared_rank(ps, rank - 1) : nullptr;
         const int pl = CL.rank_info[rank].y, plp = rank > 0 ? CL.rank_info[rank - 1].y : 0;
-#pragma unroll
-        for (int q = 1; q <= 3; ++q) {
-            xpa[q - 1] = rxl + q < pl ? ps + roff + q * CL.Sp2 : (nxt ? nxt + roff + (q - pl) * CL.Sp2 : s_zero);
-            xma[q - 1] = rxl - q >= 0 ? ps + roff - q * CL.Sp2 : (prv ? prv + roff + (plp - q) * CL.Sp2 : s_zero);
-        }
+        const int rest = roff - rxl * Sp2;  // row and column within the plane
+        if (rlen > 0 && rank > 0 && rxl < 3)
+            hm = cl.map_shared_rank(ps, rank - 1) + (3 + plp + rxl) * Sp2 + rest;
+        if (rlen > 0 && rank < C - 1 && rxl >= pl - 3)
+            hp = cl.map_shared_rank(ps, rank + 1) + (3 + rxl - pl) * Sp2 + rest;
     } else {
 #pragma unroll
         for (int j = 0; j < PTS; ++j)
@@ -280,119 +405,43 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
             }
         }
         if (RUNS && rn_start > target2 && rn_start == rn_start) {
-            // r and d of the run in shared memory ([PTS][NT], conflict-free),
-            // A p in registers, p and its z neighbours in registers
-            float* rs = ds + PTS * NT;
-            double scale = sqrt(rn_start);
-            float ap[PTS], pz[PTS + 6];
-            float a32 = 0.0f;
-            {
-                const double inv = 1.0 / scale;
-#pragma unroll
-                for (int j = 0; j < PTS; ++j) {
-                    ds[j * NT + threadIdx.x] = 0.0f;
-                    float rj = 0.0f;
-                    if (j < rlen) {
-                        rj = (float)(r64[rk0 + j] * inv);
-                        ps[roff + j] = rj;
-                        a32 = fmaf(rj, rj, a32);
-                    }
-                    rs[j * NT + threadIdx.x] = rj;
-                }
+            if (threadIdx.x == 0) {
+                g_rc.cube = cube;
+                g_rc.vc = vc;
+                g_rc.r64 = r64;
+                g_rc.max_iter = P.max_iter;
+                g_rc.target2 = target2;
+                g_rc.drop2 = (float)(P.update_drop * P.update_drop);
             }
-            float rr = cluster_sum<NT, C, float>(a32, red32, flip32, part32, cflip32, cl, rank);
-            float maxrr = rr;
-            const float drop2 = (float)(P.update_drop * P.update_drop);
-            float conv_thr = (float)(0.25 * target2 / (scale * scale));
+            __syncthreads();
+            double scale = sqrt(rn_start);
+            float carry = -1.0f;
+            int f32 = 0, cf32 = 0;
             for (;;) {
-                if (iters >= P.max_iter) {
+                const RunSeg sg = run_segment<NT, C, PTS, SYZ>(pc + roff, ds + threadIdx.x, hm, hp, rk0, rlen, scale,
+                                                               carry, P.st32.c0, P.st32.cz[0], P.st32.cz[1],
+                                                               P.st32.cz[2], iters, f32, cf32);
+                iters = sg.iters;
+                f32 = sg.flip32;
+                cf32 = sg.cflip32;
+                if (sg.maxed) {
                     conv = false;
                     break;
                 }
-                float pa = 0.0f;
-                if (rlen > 0) {
-                    // the run's p and its z neighbours
-#pragma unroll
-                    for (int m = 0; m < PTS + 6; ++m) pz[m] = ps[roff - 3 + m];
-#pragma unroll
-                    for (int j = 0; j < PTS; ++j) {
-                        const int o = roff + j;
-                        const float sz1 = pz[j + 4] + pz[j + 2], sz2 = pz[j + 5] + pz[j + 1], sz3 = pz[j + 6] + pz[j];
-                        const float sy1 = ps[o + Syz] + ps[o - Syz], sy2 = ps[o + 2 * Syz] + ps[o - 2 * Syz],
-                                    sy3 = ps[o + 3 * Syz] + ps[o - 3 * Syz];
-                        const float sx1 = xpa[0][j] + xma[0][j];
-                        const float sx2 = xpa[1][j] + xma[1][j];
-                        const float sx3 = xpa[2][j] + xma[2][j];
-                        const float az = fmaf(st.cz[0], sz1, fmaf(st.cz[1], sz2, st.cz[2] * sz3));
-                        const float ay = fmaf(st.cy[0], sy1, fmaf(st.cy[1], sy2, st.cy[2] * sy3));
-                        const float ax = fmaf(st.cx[0], sx1, fmaf(st.cx[1], sx2, st.cx[2] * sx3));
-                        const float a = fmaf(st.c0, pz[j + 3], (az + ay) + ax);
-                        ap[j] = -a;
-                        if (j < rlen) pa = fmaf(pz[j + 3], -a, pa);
-                    }
-                }
-                const float pap = cluster_sum<NT, C, float>(pa, red32, flip32, part32, cflip32, cl, rank);
-                const float al = rr / pap;
-                float ra = 0.0f;
-#pragma unroll
-                for (int j = 0; j < PTS; ++j) {
-                    if (j < rlen) {
-                        float* dj = ds + j * NT + threadIdx.x;
-                        float* rj = rs + j * NT + threadIdx.x;
-                        *dj = fmaf(al, pz[j + 3], *dj);
-                        const float rn = fmaf(-al, ap[j], *rj);
-                        *rj = rn;
-                        ra = fmaf(rn, rn, ra);
-                    }
-                }
-                const float rrn = cluster_sum<NT, C, float>(ra, red32, flip32, part32, cflip32, cl, rank);
-                ++iters;
-                const bool update = rrn <= drop2 * maxrr || rrn <= conv_thr || !(rrn == rrn);
-                if (update) {
-                    const long long tu = clk ? clock64() : 0;
-#pragma unroll
-                    for (int j = 0; j < PTS; ++j) {  // v += scale d
-                        if (j < rlen) {
-                            const int c = cube[rk0 + j];
-                            vc[c] = fma(scale, (double)ds[j * NT + threadIdx.x], vc[c]);
-                        }
-                    }
-                    cl.sync();
-                    acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, false);
-                    const double rn2 = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
-                    ++refines;
-                    if (clk) tr += clock64() - tu;
-                    if (rn2 <= target2) break;
-                    if (refines > P.max_refine || !(rn2 < scale * scale)) {
-                        conv = false;
-                        break;
-                    }
-                    const double ns = sqrt(rn2);
-                    const float carry = (float)(ns / scale) / rr;
-                    const double inv = 1.0 / ns;
-                    a32 = 0.0f;
-#pragma unroll
-                    for (int j = 0; j < PTS; ++j) {
-                        if (j < rlen) {
-                            const float rj = (float)(r64[rk0 + j] * inv);
-                            rs[j * NT + threadIdx.x] = rj;
-                            ds[j * NT + threadIdx.x] = 0.0f;
-                            ps[roff + j] = fmaf(carry, ps[roff + j], rj);
-                            a32 = fmaf(rj, rj, a32);
-                        }
-                    }
-                    rr = cluster_sum<NT, C, float>(a32, red32, flip32, part32, cflip32, cl, rank);
-                    maxrr = rr;
-                    scale = ns;
-                    conv_thr = (float)(0.25 * target2 / (scale * scale));
-                    continue;
-                }
-                const float be = rrn / rr;
-                rr = rrn;
-#pragma unroll
-                for (int j = 0; j < PTS; ++j)
-                    if (j < rlen) ps[roff + j] = fmaf(be, pz[j + 3], rs[j * NT + threadIdx.x]);
+                const long long tu = clk ? clock64() : 0;
                 cl.sync();
+                acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, false);
+                const double rn2 = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
+                ++refines;
+                if (clk) tr += clock64() - tu;
+                if (rn2 <= target2) break;
+                if (refines > P.max_refine || !(rn2 < scale * scale)) {
+                    conv = false;
+                    break;
+                }
+                const double ns = sqrt(rn2);
+                carry = (float)(ns / scale) / sg.rr;
+                scale = ns;
             }
         }
         if (!RUNS && rn_start > target2 && rn_start == rn_start) {
@@ -552,11 +601,12 @@ size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant);
 struct ClusterVariant {
     int nt, c, pts;
     bool runs;
+    int syz;  // runs: slab row pitch the variant is specialised for (0 = any)
     const void* fn;
     cudaError_t (*launch)(const SolveParams&, const ClusterLayout&, int, size_t, cudaStream_t);
 };
 
-template <int NT, int C, int PTS, bool RUNS>
+template <int NT, int C, int PTS, bool RUNS, int SYZ>
 static cudaError_t launch_cluster_t(const SolveParams& P, const ClusterLayout& CL, int n_clusters, size_t smem,
                                     cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
@@ -571,18 +621,19 @@ static cudaError_t launch_cluster_t(const SolveParams& P, const ClusterLayout& C
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, cluster_pair_kernel<NT, C, PTS, RUNS>, P, CL);
+    return cudaLaunchKernelEx(&cfg, cluster_pair_kernel<NT, C, PTS, RUNS, SYZ>, P, CL);
 }
 
-#define EXX_CLUSTER_VARIANT(NT, C, PTS, RUNS) \
-    {NT, C, PTS, RUNS, (const void*)cluster_pair_kernel<NT, C, PTS, RUNS>, launch_cluster_t<NT, C, PTS, RUNS>}
+#define EXX_CLUSTER_VARIANT(NT, C, PTS, RUNS, SYZ)                                                  \
+    {NT, C, PTS, RUNS, SYZ, (const void*)cluster_pair_kernel<NT, C, PTS, RUNS, SYZ>,                 \
+     launch_cluster_t<NT, C, PTS, RUNS, SYZ>}
 static const ClusterVariant kVariants[] = {
-    EXX_CLUSTER_VARIANT(512, 2, 8, false),   EXX_CLUSTER_VARIANT(512, 2, 18, false),
-    EXX_CLUSTER_VARIANT(512, 4, 10, false),  EXX_CLUSTER_VARIANT(512, 4, 18, false),
-    EXX_CLUSTER_VARIANT(512, 8, 17, false),  EXX_CLUSTER_VARIANT(1024, 8, 9, false),
-    EXX_CLUSTER_VARIANT(1024, 9, 8, false),
-    EXX_CLUSTER_VARIANT(1024, 8, 10, true),  EXX_CLUSTER_VARIANT(1024, 4, 10, true),
-    EXX_CLUSTER_VARIANT(1024, 2, 12, true),
+    EXX_CLUSTER_VARIANT(512, 2, 8, false, 0),   EXX_CLUSTER_VARIANT(512, 2, 18, false, 0),
+    EXX_CLUSTER_VARIANT(512, 4, 10, false, 0),  EXX_CLUSTER_VARIANT(512, 4, 18, false, 0),
+    EXX_CLUSTER_VARIANT(512, 8, 17, false, 0),  EXX_CLUSTER_VARIANT(1024, 8, 9, false, 0),
+    EXX_CLUSTER_VARIANT(1024, 9, 8, false, 0),
+    // z runs with halo planes, specialised for R_PE = 24 (pitch 55) and 16 (39)
+    EXX_CLUSTER_VARIANT(1024, 9, 8, true, 55),  EXX_CLUSTER_VARIANT(1024, 4, 8, true, 39),
 };
 #undef EXX_CLUSTER_VARIANT
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
@@ -633,6 +684,7 @@ cudaError_t launch_cluster_kernel(int variant, const SolveParams& P, const Clust
 
 int cluster_variant_threads(int variant) { return kVariants[variant].nt; }
 int cluster_variant_runs(int variant) { return kVariants[variant].runs ? 1 : 0; }
+int cluster_variant_syz(int variant) { return kVariants[variant].syz; }
 int cluster_variant_count() { return kNumVariants; }
 int cluster_variant_size(int variant) { return kVariants[variant].c; }
 int cluster_variant_pts(int variant) { return kVariants[variant].pts; }
@@ -640,8 +692,10 @@ int cluster_variant_pts(int variant) { return kVariants[variant].pts; }
 size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant) {
     (void)Rc;
     const size_t per = (size_t)kVariants[variant].nt * kVariants[variant].pts;
-    // slab, then d [PTS][NT], then the point map (one point per slot) or r (runs)
-    return sizeof(float) * ((((size_t)CL.cap_planes * CL.Sp2 + 3) & ~(size_t)3) + per) + 4 * per;
+    const bool runs = kVariants[variant].runs;
+    // slab (runs: with 3 halo planes per side), d [PTS][NT], the point map (point slots)
+    const size_t slab = (size_t)(CL.cap_planes + (runs ? 6 : 0)) * CL.Sp2;
+    return sizeof(float) * (((slab + 3) & ~(size_t)3) + per) + (runs ? 0 : sizeof(int) * per);
 }
 
 }  // namespace exx
