@@ -9,6 +9,10 @@ GPU through exx_guess_train_step; every step runs in the library's kernels.
 
     python -m paper_1911_10630_gb300.guess_train --out guess_r16.bin
 
+With --workload water64 the samples come from water-64-form workloads
+(R_PE = 24, cube side 48; a subset of each workload's pairs), for the solver
+at the radii of the water-64 and MD-like workloads.
+
 The model blob is what exx_load_guess_model (warm_start = 2) expects.
 """
 from __future__ import annotations
@@ -22,7 +26,8 @@ import numpy as np
 from . import synth
 from .exx import Exx, GuessNet, guess_model_blob
 
-CUBE = 32  # network input side for R_PE = 16 (the ball's +16 poles fall outside)
+CUBE = 32      # network input side for R_PE = 16 (the ball's +16 poles fall outside)
+CUBE_R24 = 48  # and for R_PE = 24
 
 
 def init_params(n_params: int, seed: int) -> np.ndarray:
@@ -41,27 +46,35 @@ def init_params(n_params: int, seed: int) -> np.ndarray:
     return p
 
 
-def solve_and_export(seeds, S: int = CUBE, torch=None):
-    """Solves each seeded tiny workload and returns the samples of all its
-    pairs as device tensors (input [n][S^3][2], target [n][S^3])."""
+def solve_and_export(seeds, S: int = CUBE, torch=None, workload=None, per_workload: int = 0):
+    """Solves each seeded workload (default: the tiny form, synth.config0) and
+    returns the samples of its pairs as device tensors (input [n][S^3][2],
+    target [n][S^3]); per_workload > 0 keeps that many pairs, spread evenly
+    over the list, of each workload."""
     import torch as _t
     torch = torch or _t
+    make = workload or synth.config0
     ins, tgts = [], []
     ex = None
     for seed in seeds:
-        w = synth.config0(seed)
+        w = make(seed)
         if ex is None:
             ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=1, warm_start=1)
-        phi = torch.from_numpy(w.orbitals()).cuda()
+        phi = synth.orbitals_torch(w)
         cen = torch.from_numpy(np.ascontiguousarray(w.centers)).cuda()
         D = torch.empty_like(phi)
         ex.compute(phi, cen, D)
-        cap = w.n * (w.n + 1) // 2
+        del D
+        cap = ex.stats()["n_pair"]
         inp = torch.empty((cap, S, S, S, 2), dtype=torch.float32, device="cuda")
         tgt = torch.empty((cap, S, S, S), dtype=torch.float32, device="cuda")
         n = ex.export_samples(phi, S, inp, tgt, cap)
-        ins.append(inp[:n])
-        tgts.append(tgt[:n])
+        keep = torch.arange(n, device="cuda")
+        if per_workload and per_workload < n:
+            keep = torch.linspace(0, n - 1, per_workload, device="cuda").round().long()
+        ins.append(inp.index_select(0, keep))
+        tgts.append(tgt.index_select(0, keep))
+        del inp, tgt, phi
     ex.close()
     return torch.cat(ins), torch.cat(tgts)
 
@@ -104,14 +117,22 @@ def main():
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--workload", default="tiny", choices=["tiny", "water64"])
+    ap.add_argument("--per-workload", type=int, default=400, help="water64: pairs kept per workload")
     args = ap.parse_args()
     import torch
     t0 = time.time()
-    inp, tgt = solve_and_export(range(1000, 1000 + args.train_seeds), torch=torch)
+    if args.workload == "tiny":
+        S = CUBE
+        inp, tgt = solve_and_export(range(1000, 1000 + args.train_seeds), torch=torch)
+    else:
+        S = CUBE_R24
+        inp, tgt = solve_and_export(range(1000, 1000 + args.train_seeds), S=S, torch=torch, workload=synth.config1,
+                                    per_workload=args.per_workload)
     print(f"{inp.shape[0]} samples in {time.time() - t0:.1f} s", flush=True)
-    net, hist = train(inp, tgt, epochs=args.epochs, batch=args.batch, lr=args.lr, log=print)
+    net, hist = train(inp, tgt, S=S, epochs=args.epochs, batch=args.batch, lr=args.lr, log=print)
     with open(args.out, "wb") as f:
-        f.write(guess_model_blob(CUBE, net.get_params()))
+        f.write(guess_model_blob(S, net.get_params()))
     print("loss", hist[0], "->", hist[-1])
 
 

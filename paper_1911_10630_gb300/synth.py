@@ -37,6 +37,7 @@ __all__ = [
     "config1",
     "config2",
     "config4",
+    "orbitals_torch",
     "tiny",
     "CONFIGS",
 ]
@@ -111,6 +112,42 @@ def orbitals(cell, grid, centers, alphas, pvecs, dtype=np.float64) -> np.ndarray
     for i in range(n):
         orbital(cell, grid, centers[i], float(alphas[i]), pvecs[i], out=phi[i])
     return phi if dtype == np.float64 else phi.astype(dtype)
+
+
+def orbitals_torch(w: "Workload", device="cuda", chunk: int = 16, out=None):
+    """The workload's orbitals evaluated on a torch device, same formula and
+    normalisation as :func:`orbital` (float64, [n][N0][N1][N2]); for inputs too
+    large to build in host memory. Values agree with the NumPy path to
+    rounding; tests that compare against the oracle copy the device arrays
+    back rather than rebuilding them."""
+    import torch
+    cell = np.asarray(w.cell, dtype=np.float64)
+    grid = [int(g) for g in w.grid]
+    n = w.n
+    if out is None:
+        out = torch.empty((n, grid[0], grid[1], grid[2]), dtype=torch.float64, device=device)
+    axes = [torch.arange(grid[a], dtype=torch.float64, device=device) * (cell[a] / grid[a]) for a in range(3)]
+    dv = float(np.prod(cell / np.asarray(grid)))
+    cen = torch.as_tensor(np.asarray(w.centers, dtype=np.float64), device=device)
+    alp = torch.as_tensor(np.asarray(w.alphas, dtype=np.float64), device=device)
+    pv = torch.as_tensor(np.asarray(w.pvecs, dtype=np.float64), device=device)
+    for i0 in range(0, n, chunk):
+        i1 = min(n, i0 + chunk)
+        d = []
+        e = []
+        for a in range(3):
+            x = axes[a][None, :] - cen[i0:i1, a:a + 1]
+            x = x - cell[a] * torch.floor(x / cell[a] + 0.5)
+            d.append(x)
+            e.append(torch.exp(-alp[i0:i1, None] * x * x))
+        exy = e[0][:, :, None] * e[1][:, None, :]
+        lin = 1.0 + pv[i0:i1, 0, None, None] * d[0][:, :, None] + pv[i0:i1, 1, None, None] * d[1][:, None, :]
+        blk = out[i0:i1]
+        blk.copy_((exy * lin)[:, :, :, None] * e[2][:, None, None, :])
+        blk.add_((exy * pv[i0:i1, 2, None, None])[:, :, :, None] * (e[2] * d[2])[:, None, None, :])
+        norm = torch.sqrt(torch.einsum("bxyz,bxyz->b", blk, blk) * dv)
+        blk.div_(norm[:, None, None, None])
+    return out
 
 
 def _minimg_dist(a: np.ndarray, b: np.ndarray, cell: np.ndarray) -> np.ndarray:
