@@ -19,6 +19,7 @@
 #include "exx_unet.cuh"
 #include "exx_unet_tc.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -564,9 +565,17 @@ cudaError_t conv3_tc(const __nv_bfloat16* x, const __nv_bfloat16* wp, const floa
     a.cin = cin;
     a.cout = cout;
     a.epi = epi;
+    // Output depth per CTA: 4 D slices (fewer when the accumulators need more
+    // than 512 TMEM columns). Deeper tiles reuse the staged halo tile more but
+    // leave one CTA per SM whose 128 threads stage too slowly to keep the
+    // tensor cores fed (measured slower on GB300); double-buffered chunks when
+    // the input has more than one chunk and two stages fit.
     int DT = 4;
     while (DT > 1 && DT * cout > 512) --DT;
     if (DT > D) DT = D;
+    const size_t stage_b = (size_t)2 * (DT + 2) * kHH * kWW * 16 + (size_t)27 * cout * 32;
+    const int nbuf = (2 * stage_b + 128 <= 200 * 1024 && cin > 16) ? 2 : 1;
+    if (DT < 1) return cudaErrorInvalidValue;
     a.DT = DT;
     int nc = 32;
     while (nc < DT * cout) nc *= 2;
@@ -574,7 +583,7 @@ cudaError_t conv3_tc(const __nv_bfloat16* x, const __nv_bfloat16* wp, const floa
     a.itile = (uint32_t)(DT + 2) * kHH * kWW * 16;
     a.wtile = 27u * (uint32_t)cout * 32u;
     a.stage = 2 * a.itile + a.wtile;
-    a.nbuf = (2 * a.stage + 128 <= 200 * 1024 && cin > 16) ? 2 : 1;
+    a.nbuf = nbuf;
     a.tiles_w = (W + kTW - 1) / kTW;
     a.tiles_h = (H + kTH - 1) / kTH;
     a.tiles_d = (D + DT - 1) / DT;
