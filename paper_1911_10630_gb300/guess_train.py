@@ -110,17 +110,51 @@ def train(inp, tgt, S: int = CUBE, epochs: int = 20, batch: int = 32, lr: float 
     return net, hist
 
 
+def conv_macs(S: int) -> int:
+    """Multiply-adds of one forward pass at cube side S (3x3x3 layers)."""
+    cin = (2, 16, 16, 32, 32, 64, 64, 128, 192, 64, 96, 32, 48, 16)
+    cout = (16, 16, 32, 32, 64, 64, 128, 128, 64, 64, 32, 32, 16, 16)
+    lvl = (0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0)
+    return sum(27 * a * b * (S >> l) ** 3 for a, b, l in zip(cin, cout, lvl))
+
+
+def time_forward(S: int, B: int, reps: int = 5) -> dict:
+    """CUDA-event time of the network's forward pass on B random samples."""
+    import torch
+    net = GuessNet(S, B)
+    net.set_params(init_params(net.n_params, 0))
+    inp = torch.rand((B, S, S, S, 2), device="cuda", dtype=torch.float32)
+    out = torch.empty((B, S, S, S), device="cuda", dtype=torch.float32)
+    net.forward(inp, out, B)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        net.forward(inp, out, B)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    net.close()
+    return {"S": S, "batch": B, "ms": ms, "us_per_sample": 1e3 * ms / B,
+            "tflops": 2.0 * conv_macs(S) * B / (ms / 1e3) / 1e12}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--out", required=True)
+    ap.add_argument("--out", default=None)
     ap.add_argument("--train-seeds", type=int, default=140)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--workload", default="tiny", choices=["tiny", "water64"])
     ap.add_argument("--per-workload", type=int, default=400, help="water64: pairs kept per workload")
+    ap.add_argument("--time-forward", type=int, nargs=2, metavar=("S", "B"), default=None,
+                    help="only time the forward pass on B random samples of side S (He-initialised weights)")
     args = ap.parse_args()
     import torch
+    if args.time_forward:
+        print(time_forward(*args.time_forward))
+        return
     t0 = time.time()
     if args.workload == "tiny":
         S = CUBE
@@ -131,6 +165,8 @@ def main():
                                     per_workload=args.per_workload)
     print(f"{inp.shape[0]} samples in {time.time() - t0:.1f} s", flush=True)
     net, hist = train(inp, tgt, S=S, epochs=args.epochs, batch=args.batch, lr=args.lr, log=print)
+    if not args.out:
+        raise SystemExit("--out is required for training")
     with open(args.out, "wb") as f:
         f.write(guess_model_blob(S, net.get_params()))
     print("loss", hist[0], "->", hist[-1])
