@@ -35,7 +35,7 @@ cudaError_t launch_debug_readback(const SolveParams& P, const PairRec& pr, doubl
                                   cudaStream_t st);
 cudaError_t launch_apply(const SolveParams& P, const double* p, double* ap, cudaStream_t st);
 size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant);
-int cluster_variant(int C, int max_pts, int threads);
+int cluster_variant(int C, int max_pts, int threads, int syz, bool iso);
 cudaError_t cluster_prepare(int variant, size_t smem, int* max_clusters);
 cudaError_t launch_cluster_kernel(int variant, const SolveParams& P, const ClusterLayout& CL, int n_clusters,
                                   size_t smem, cudaStream_t st);
@@ -542,7 +542,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             // one point per thread slot (lane maps 0 and 1)
             for (int nt : {1024, 512}) {
                 if (o.threads && o.threads != nt) continue;
-                const int v = cluster_variant(C, L.max_pts, nt);
+                const int v = cluster_variant(C, L.max_pts, nt, L.Syz, isotropic);
                 if (v < 0) continue;
                 for (int lm = 0; lm <= 1; ++lm) {
                     if (!o.autotune && lm != o.lane_map) continue;

@@ -252,6 +252,128 @@ __device__ __noinline__ RunSeg run_segment(float* pcr, float* dst, float* hm, fl
     return out;
 }
 
+// The point-map CG of one pair in segments, like run_segment: each thread
+// slot j holds one point (slab offset | plane << 24 in spk, compact index in
+// slot_k); x legs leaving the slab read the neighbour's slab (pm, pp). SYZ > 0
+// makes the box pitches compile-time constants and ISO selects the isotropic
+// stencil (4 coefficients), both to keep the loop within 64 registers.
+struct StencilArgs {
+    float c0, cx[3], cy[3], cz[3];
+};
+
+template <int NT, int C, int PTS, int SYZ, bool ISO>
+__device__ __noinline__ RunSeg pts_segment(float* ps, const float* pm, const float* pp, float* dst, const int* spt,
+                                           const int* skt, int planes, int planes_prev, int syz_rt, double scale,
+                                           float carry, StencilArgs sa, int iters, int flip32, int cflip32) {
+    const int Syz = SYZ > 0 ? SYZ : syz_rt;
+    const int Sp2 = Syz * Syz;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    float r[PTS], ap[PTS];
+    float a32 = 0.0f;
+    {
+        const double inv = 1.0 / scale;
+        const double* r64 = g_rc.r64;
+#pragma unroll
+        for (int j = 0; j < PTS; ++j) {
+            r[j] = 0.0f;
+            ap[j] = 0.0f;
+            dst[j * NT] = 0.0f;
+            const int pkj = spt[j * NT];
+            if (pkj >= 0) {
+                const int off = pkj & 0xffffff;
+                r[j] = (float)(r64[skt[j * NT]] * inv);
+                ps[off] = carry < 0.0f ? r[j] : fmaf(carry, ps[off], r[j]);
+                a32 = fmaf(r[j], r[j], a32);
+            }
+        }
+    }
+    float rr = cluster_sum<NT, C, float>(a32, g_rc_red32, flip32, g_rc_part32, cflip32, cl, rank);
+    const float lim = g_rc.drop2 * rr;
+    const float conv_thr = (float)(0.25 * g_rc.target2 / (scale * scale));
+    RunSeg out;
+    for (;;) {
+        if (iters >= g_rc.max_iter) {
+            out.maxed = 1;
+            break;
+        }
+        float pa = 0.0f;
+#pragma unroll
+        for (int j = 0; j < PTS; ++j) {
+            const int pkj = spt[j * NT];
+            if (pkj >= 0) {
+                const int off = pkj & 0xffffff, xl = pkj >> 24;
+                const float pc = ps[off];
+                float sz[3], sy[3], sx[3];
+#pragma unroll
+                for (int q = 1; q <= 3; ++q) {
+                    sz[q - 1] = ps[off + q] + ps[off - q];
+                    sy[q - 1] = ps[off + q * Syz] + ps[off - q * Syz];
+                    const float xpv = xl + q < planes ? ps[off + q * Sp2] : (pp ? pp[off + (q - planes) * Sp2] : 0.0f);
+                    const float xmv = xl - q >= 0 ? ps[off - q * Sp2] : (pm ? pm[off + (planes_prev - q) * Sp2] : 0.0f);
+                    sx[q - 1] = xpv + xmv;
+                }
+                float a;
+                if constexpr (ISO) {
+                    a = fmaf(sa.c0, pc, fmaf(sa.cz[0], (sz[0] + sy[0]) + sx[0],
+                                             fmaf(sa.cz[1], (sz[1] + sy[1]) + sx[1], sa.cz[2] * ((sz[2] + sy[2]) + sx[2]))));
+                } else {
+                    const float az = fmaf(sa.cz[0], sz[0], fmaf(sa.cz[1], sz[1], sa.cz[2] * sz[2]));
+                    const float ay = fmaf(sa.cy[0], sy[0], fmaf(sa.cy[1], sy[1], sa.cy[2] * sy[2]));
+                    const float ax = fmaf(sa.cx[0], sx[0], fmaf(sa.cx[1], sx[1], sa.cx[2] * sx[2]));
+                    a = fmaf(sa.c0, pc, (az + ay) + ax);
+                }
+                ap[j] = -a;
+                pa = fmaf(pc, -a, pa);
+            }
+        }
+        const float pap = cluster_sum<NT, C, float>(pa, g_rc_red32, flip32, g_rc_part32, cflip32, cl, rank);
+        const float al = rr / pap;
+        float ra = 0.0f;
+#pragma unroll
+        for (int j = 0; j < PTS; ++j) {
+            const int pkj = spt[j * NT];
+            if (pkj >= 0) {
+                dst[j * NT] = fmaf(al, ps[pkj & 0xffffff], dst[j * NT]);
+                r[j] = fmaf(-al, ap[j], r[j]);
+                ra = fmaf(r[j], r[j], ra);
+            }
+        }
+        const float rrn = cluster_sum<NT, C, float>(ra, g_rc_red32, flip32, g_rc_part32, cflip32, cl, rank);
+        ++iters;
+        if (rrn <= lim || rrn <= conv_thr || !(rrn == rrn)) {
+            out.maxed = 0;
+            break;
+        }
+        const float be = rrn / rr;
+        rr = rrn;
+#pragma unroll
+        for (int j = 0; j < PTS; ++j) {
+            const int pkj = spt[j * NT];
+            if (pkj >= 0) {
+                const int off = pkj & 0xffffff;
+                ps[off] = fmaf(be, ps[off], r[j]);
+            }
+        }
+        cl.sync();
+    }
+    // v += scale d
+    const int* cube = g_rc.cube;
+    double* vc = g_rc.vc;
+#pragma unroll
+    for (int j = 0; j < PTS; ++j) {
+        if (spt[j * NT] >= 0) {
+            const int c = cube[skt[j * NT]];
+            vc[c] = fma(scale, (double)dst[j * NT], vc[c]);
+        }
+    }
+    out.iters = iters;
+    out.rr = rr;
+    out.flip32 = flip32;
+    out.cflip32 = cflip32;
+    return out;
+}
+
 // RUNS = false: thread slot j of a thread holds one point of the slab (the
 // [PTS][NT] point map); x legs that leave the slab read the neighbour's slab.
 // RUNS = true: the thread owns one run of at most PTS consecutive points of a
@@ -261,7 +383,7 @@ __device__ __noinline__ RunSeg run_segment(float* pcr, float* dst, float* hm, fl
 // and z neighbours stay in registers (a point costs 12 shared loads plus a
 // share of the run's PTS + 6), and the thread map puts the runs of a warp in
 // distinct banks.
-template <int NT, int C, int PTS, bool RUNS, int SYZ>
+template <int NT, int C, int PTS, bool RUNS, int SYZ, bool ISO>
 __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_constant__ SolveParams P,
                                                              const __grid_constant__ ClusterLayout CL) {
     cg::cluster_group cl = cg::this_cluster();
@@ -269,11 +391,9 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
     extern __shared__ double smem[];
     __shared__ double red[2][33];
     __shared__ double part[2][16];
-    __shared__ float red32[2][33];
-    __shared__ float part32[2][16];
     __shared__ double s_M[kNMono], s_T[kNMono];
     __shared__ int s_item;
-    int flip = 0, cflip = 0, flip32 = 0, cflip32 = 0;
+    int flip = 0, cflip = 0;
 
     const int Rc = P.Rc;
     // FP64 power tables (global, read-only) and this CTA's plane sums (global slot)
@@ -334,7 +454,6 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
     double* rowS = reinterpret_cast<double*>(slot + P.off_rows);
     double* sY = reinterpret_cast<double*>(slot + P.off_sy) + (size_t)rank * CL.sy_doubles;
 
-    const Stencil<float> st = P.st32;
     const int gt = rank * NT + (int)threadIdx.x, gn = C * NT;
     const int np = *P.n_pair;
     cl.sync();
@@ -404,7 +523,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
                 }
             }
         }
-        if (RUNS && rn_start > target2 && rn_start == rn_start) {
+        if (rn_start > target2 && rn_start == rn_start) {
             if (threadIdx.x == 0) {
                 g_rc.cube = cube;
                 g_rc.vc = vc;
@@ -417,10 +536,23 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
             double scale = sqrt(rn_start);
             float carry = -1.0f;
             int f32 = 0, cf32 = 0;
+            StencilArgs sa;
+            sa.c0 = P.st32.c0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                sa.cx[q] = P.st32.cx[q];
+                sa.cy[q] = P.st32.cy[q];
+                sa.cz[q] = P.st32.cz[q];
+            }
             for (;;) {
-                const RunSeg sg = run_segment<NT, C, PTS, SYZ>(pc + roff, ds + threadIdx.x, hm, hp, rk0, rlen, scale,
-                                                               carry, P.st32.c0, P.st32.cz[0], P.st32.cz[1],
-                                                               P.st32.cz[2], iters, f32, cf32);
+                RunSeg sg;
+                if constexpr (RUNS)
+                    sg = run_segment<NT, C, PTS, SYZ>(pc + roff, ds + threadIdx.x, hm, hp, rk0, rlen, scale, carry,
+                                                      sa.c0, sa.cz[0], sa.cz[1], sa.cz[2], iters, f32, cf32);
+                else
+                    sg = pts_segment<NT, C, PTS, SYZ, ISO>(ps, pm, pp, ds + threadIdx.x, spk + threadIdx.x,
+                                                           slot_k + threadIdx.x, planes, planes_prev, Syz, scale,
+                                                           carry, sa, iters, f32, cf32);
                 iters = sg.iters;
                 f32 = sg.flip32;
                 cf32 = sg.cflip32;
@@ -442,128 +574,6 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
                 const double ns = sqrt(rn2);
                 carry = (float)(ns / scale) / sg.rr;
                 scale = ns;
-            }
-        }
-        if (!RUNS && rn_start > target2 && rn_start == rn_start) {
-            double scale = sqrt(rn_start);
-            float r[PTS], ap[PTS];
-            float a32 = 0.0f;
-            {
-                const double inv = 1.0 / scale;
-#pragma unroll
-                for (int j = 0; j < PTS; ++j) {
-                    r[j] = 0.0f;
-                    ap[j] = 0.0f;
-                    ds[j * NT + threadIdx.x] = 0.0f;
-                    const int pkj = spk[j * NT + threadIdx.x];
-                    if (pkj >= 0) {
-                        const int k = slot_k[j * NT + threadIdx.x];
-                        r[j] = (float)(r64[k] * inv);
-                        ps[pkj & 0xffffff] = r[j];
-                        a32 = fmaf(r[j], r[j], a32);
-                    }
-                }
-            }
-            float rr = cluster_sum<NT, C, float>(a32, red32, flip32, part32, cflip32, cl, rank);
-            float maxrr = rr;
-            const float drop2 = (float)(P.update_drop * P.update_drop);
-            float conv_thr = (float)(0.25 * target2 / (scale * scale));
-            for (;;) {
-                if (iters >= P.max_iter) {
-                    conv = false;
-                    break;
-                }
-                float pa = 0.0f;
-#pragma unroll
-                for (int j = 0; j < PTS; ++j) {
-                    const int pkj = spk[j * NT + threadIdx.x];
-                    if (pkj >= 0) {
-                        const int off = pkj & 0xffffff, xl = pkj >> 24;
-                        const float pc = ps[off];
-                        // leg pair sums first, then a shallow tree of products:
-                        // independent chains instead of one 10-deep FMA chain
-                        float sz[3], sy[3], sx[3];
-#pragma unroll
-                        for (int q = 1; q <= 3; ++q) {
-                            sz[q - 1] = ps[off + q] + ps[off - q];
-                            sy[q - 1] = ps[off + q * Syz] + ps[off - q * Syz];
-                            const float xpv = xl + q < planes ? ps[off + q * Sp2]
-                                                              : (pp ? pp[off + (q - planes) * Sp2] : 0.0f);
-                            const float xmv = xl - q >= 0 ? ps[off - q * Sp2]
-                                                          : (pm ? pm[off + (planes_prev - q) * Sp2] : 0.0f);
-                            sx[q - 1] = xpv + xmv;
-                        }
-                        const float az = fmaf(st.cz[0], sz[0], fmaf(st.cz[1], sz[1], st.cz[2] * sz[2]));
-                        const float ay = fmaf(st.cy[0], sy[0], fmaf(st.cy[1], sy[1], st.cy[2] * sy[2]));
-                        const float ax = fmaf(st.cx[0], sx[0], fmaf(st.cx[1], sx[1], st.cx[2] * sx[2]));
-                        const float a = fmaf(st.c0, pc, (az + ay) + ax);
-                        ap[j] = -a;
-                        pa = fmaf(pc, -a, pa);
-                    }
-                }
-                const float pap = cluster_sum<NT, C, float>(pa, red32, flip32, part32, cflip32, cl, rank);
-                const float al = rr / pap;
-                float ra = 0.0f;
-#pragma unroll
-                for (int j = 0; j < PTS; ++j) {
-                    const int pkj = spk[j * NT + threadIdx.x];
-                    if (pkj >= 0) {
-                        float* dj = ds + j * NT + threadIdx.x;
-                        *dj = fmaf(al, ps[pkj & 0xffffff], *dj);
-                        r[j] = fmaf(-al, ap[j], r[j]);
-                        ra = fmaf(r[j], r[j], ra);
-                    }
-                }
-                const float rrn = cluster_sum<NT, C, float>(ra, red32, flip32, part32, cflip32, cl, rank);
-                ++iters;
-                // recursive residual dropped enough, or (in absolute terms) below tol ||b|| / 2
-                const bool update = rrn <= drop2 * maxrr || rrn <= conv_thr || !(rrn == rrn);
-                if (update) {
-                    const long long tu = clk ? clock64() : 0;
-                    cta_update_v(cube, vc, ds, slot_k, scale, PTS, NT);  // v += scale d
-                    cl.sync();
-                    acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, false);
-                    const double rn2 = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
-                    ++refines;
-                    if (clk) tr += clock64() - tu;
-                    if (rn2 <= target2) break;
-                    if (refines > P.max_refine || !(rn2 < scale * scale)) {
-                        conv = false;
-                        break;
-                    }
-                    const double ns = sqrt(rn2);
-                    const float carry = (float)(ns / scale) / rr;  // beta of the new residual, in the new units
-                    const double inv = 1.0 / ns;
-                    a32 = 0.0f;
-#pragma unroll
-                    for (int j = 0; j < PTS; ++j) {
-                        const int pkj = spk[j * NT + threadIdx.x];
-                        if (pkj >= 0) {
-                            const int k = slot_k[j * NT + threadIdx.x];
-                            r[j] = (float)(r64[k] * inv);
-                            ds[j * NT + threadIdx.x] = 0.0f;
-                            const int off = pkj & 0xffffff;
-                            ps[off] = fmaf(carry, ps[off], r[j]);
-                            a32 = fmaf(r[j], r[j], a32);
-                        }
-                    }
-                    rr = cluster_sum<NT, C, float>(a32, red32, flip32, part32, cflip32, cl, rank);
-                    maxrr = rr;
-                    scale = ns;
-                    conv_thr = (float)(0.25 * target2 / (scale * scale));
-                    continue;
-                }
-                const float be = rrn / rr;
-                rr = rrn;
-#pragma unroll
-                for (int j = 0; j < PTS; ++j) {
-                    const int pkj = spk[j * NT + threadIdx.x];
-                    if (pkj >= 0) {
-                        const int off = pkj & 0xffffff;
-                        ps[off] = fmaf(be, ps[off], r[j]);
-                    }
-                }
-                cl.sync();
             }
         }
         const long long t2 = clk ? clock64() : 0;
@@ -601,12 +611,13 @@ size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant);
 struct ClusterVariant {
     int nt, c, pts;
     bool runs;
-    int syz;  // runs: slab row pitch the variant is specialised for (0 = any)
+    int syz;   // slab row pitch the variant is specialised for (0 = any)
+    bool iso;  // isotropic stencil only
     const void* fn;
     cudaError_t (*launch)(const SolveParams&, const ClusterLayout&, int, size_t, cudaStream_t);
 };
 
-template <int NT, int C, int PTS, bool RUNS, int SYZ>
+template <int NT, int C, int PTS, bool RUNS, int SYZ, bool ISO>
 static cudaError_t launch_cluster_t(const SolveParams& P, const ClusterLayout& CL, int n_clusters, size_t smem,
                                     cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
@@ -621,36 +632,48 @@ static cudaError_t launch_cluster_t(const SolveParams& P, const ClusterLayout& C
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, cluster_pair_kernel<NT, C, PTS, RUNS, SYZ>, P, CL);
+    return cudaLaunchKernelEx(&cfg, cluster_pair_kernel<NT, C, PTS, RUNS, SYZ, ISO>, P, CL);
 }
 
-#define EXX_CLUSTER_VARIANT(NT, C, PTS, RUNS, SYZ)                                                  \
-    {NT, C, PTS, RUNS, SYZ, (const void*)cluster_pair_kernel<NT, C, PTS, RUNS, SYZ>,                 \
-     launch_cluster_t<NT, C, PTS, RUNS, SYZ>}
+#define EXX_CLUSTER_VARIANT(NT, C, PTS, RUNS, SYZ, ISO)                                             \
+    {NT, C, PTS, RUNS, SYZ, ISO, (const void*)cluster_pair_kernel<NT, C, PTS, RUNS, SYZ, ISO>,       \
+     launch_cluster_t<NT, C, PTS, RUNS, SYZ, ISO>}
 static const ClusterVariant kVariants[] = {
-    EXX_CLUSTER_VARIANT(512, 2, 8, false, 0),   EXX_CLUSTER_VARIANT(512, 2, 18, false, 0),
-    EXX_CLUSTER_VARIANT(512, 4, 10, false, 0),  EXX_CLUSTER_VARIANT(512, 4, 18, false, 0),
-    EXX_CLUSTER_VARIANT(512, 8, 17, false, 0),  EXX_CLUSTER_VARIANT(1024, 8, 9, false, 0),
-    EXX_CLUSTER_VARIANT(1024, 9, 8, false, 0),
+    // point map, any radius and spacing
+    EXX_CLUSTER_VARIANT(512, 2, 8, false, 0, false),   EXX_CLUSTER_VARIANT(512, 2, 18, false, 0, false),
+    EXX_CLUSTER_VARIANT(512, 4, 10, false, 0, false),  EXX_CLUSTER_VARIANT(512, 4, 18, false, 0, false),
+    EXX_CLUSTER_VARIANT(512, 8, 17, false, 0, false),  EXX_CLUSTER_VARIANT(1024, 8, 9, false, 0, false),
+    EXX_CLUSTER_VARIANT(1024, 9, 8, false, 0, false),
+    // point map specialised for R_PE = 24 (pitch 55) on isotropic grids
+    EXX_CLUSTER_VARIANT(1024, 9, 8, false, 55, true),  EXX_CLUSTER_VARIANT(1024, 8, 9, false, 55, true),
     // z runs with halo planes, specialised for R_PE = 24 (pitch 55) and 16 (39)
-    EXX_CLUSTER_VARIANT(1024, 9, 8, true, 55),  EXX_CLUSTER_VARIANT(1024, 4, 8, true, 39),
+    EXX_CLUSTER_VARIANT(1024, 9, 8, true, 55, true),   EXX_CLUSTER_VARIANT(1024, 4, 8, true, 39, true),
 };
 #undef EXX_CLUSTER_VARIANT
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
-// Picks the instantiation for (C, max points per CTA, preferred threads).
-// Returns the index into kVariants or -1.
-int cluster_variant(int C, int max_pts, int threads) {
+// Picks the point-map instantiation for (C, max points per CTA, threads):
+// the one specialised for this slab pitch and an isotropic stencil when there
+// is one, else the generic one with the most threads and the fewest points
+// per thread. Returns the index into kVariants or -1.
+int cluster_variant(int C, int max_pts, int threads, int syz, bool iso) {
     int best = -1;
     for (int v = 0; v < kNumVariants; ++v) {
         const ClusterVariant& K = kVariants[v];
         if (K.runs || K.c != C || K.nt * K.pts < max_pts) continue;
         if (threads && K.nt != threads) continue;
-        // prefer more threads (more warps to hide shared-memory and barrier
-        // latency), then the smallest per-thread point capacity
-        if (best < 0 || K.nt > kVariants[best].nt ||
-            (K.nt == kVariants[best].nt && K.pts < kVariants[best].pts))
+        if (K.syz && (K.syz != syz || !iso)) continue;
+        if (best < 0) {
             best = v;
+            continue;
+        }
+        const ClusterVariant& B = kVariants[best];
+        const bool spec = K.syz != 0, bspec = B.syz != 0;
+        if (spec != bspec) {
+            if (spec) best = v;
+            continue;
+        }
+        if (K.nt > B.nt || (K.nt == B.nt && K.pts < B.pts)) best = v;
     }
     return best;
 }
