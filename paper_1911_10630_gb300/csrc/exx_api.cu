@@ -527,16 +527,18 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             // z-run thread maps with halo planes (lane map 2): only on request;
             // on GB300 the point map is faster (the halo copies add a remote
             // store for nearly every point of a thin slab, and the cluster
-            // barrier waits for them)
+            // barrier waits for them; reading the x legs of the runs remotely
+            // instead was slower still, as a warp's remote loads scatter)
             for (int v = 0; v < cluster_variant_count(); ++v) {
                 if (!cluster_variant_runs(v) || cluster_variant_size(v) != C) continue;
                 if (cluster_variant_syz(v) && cluster_variant_syz(v) != L.Syz) continue;
                 if (!isotropic) continue;  // the run kernel's stencil has one spacing
                 if (o.threads && o.threads != cluster_variant_threads(v)) continue;
-                if (o.lane_map != 2) continue;
+                const int lm = 2;
+                if (o.lane_map != lm) continue;
                 std::vector<int> spk, sk;
                 if (build_run_maps(L, pt, cluster_variant_threads(v), cluster_variant_pts(v), spk, sk) < 0) continue;
-                const exx_status sa = add_cand(v, 2, spk, sk);
+                const exx_status sa = add_cand(v, lm, spk, sk);
                 if (sa != EXX_OK) return bail(sa);
             }
             // one point per thread slot (lane maps 0 and 1)

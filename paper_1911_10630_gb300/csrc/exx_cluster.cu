@@ -6,10 +6,13 @@
 // its slab in shared memory as planes of a (2 R_PE + 7)^2 box (zero outside the
 // ball, so the stencil needs no bounds tests); the x legs that leave the slab
 // read the neighbouring CTA's slab through distributed shared memory. The
-// residual r, the correction d and A p of the CTA's points stay in registers
-// (a fixed point-to-thread map). Dot products are reduced per CTA, exchanged
-// through distributed shared memory and summed in rank order, so every CTA
-// holds the same value. Per inner iteration: three cluster barriers.
+// residual r and A p of the CTA's points stay in registers and the correction
+// d in shared memory, through a fixed point-to-thread map whose warps cover
+// consecutive points (so a warp's remote loads stay contiguous: maps that
+// scatter them, even bank-conflict-free ones, measured much slower). Dot
+// products are reduced per CTA, exchanged through distributed shared memory
+// and summed in rank order, so every CTA holds the same value. Per inner
+// iteration: three cluster barriers.
 //
 // The FP64 parts of the pair (gather, multipoles, shell potential, the FP64
 // residual 4 pi rho + lap v of each refinement step, E_ij, the D_xx scatter)
@@ -201,11 +204,12 @@ __device__ __noinline__ RunSeg run_segment(float* pcr, float* dst, float* hm, fl
             for (int m = 0; m < PTS + 6; ++m) pz[m] = pcr[m - 3];
 #pragma unroll
             for (int j = 0; j < PTS; ++j) {
-                const float s1 = (pz[j + 4] + pz[j + 2]) + (pcr[j + Syz] + pcr[j - Syz]) + (pcr[j + Sp2] + pcr[j - Sp2]);
-                const float s2 = (pz[j + 5] + pz[j + 1]) + (pcr[j + 2 * Syz] + pcr[j - 2 * Syz]) +
-                                 (pcr[j + 2 * Sp2] + pcr[j - 2 * Sp2]);
-                const float s3 = (pz[j + 6] + pz[j]) + (pcr[j + 3 * Syz] + pcr[j - 3 * Syz]) +
-                                 (pcr[j + 3 * Sp2] + pcr[j - 3 * Sp2]);
+                const float x1 = pcr[j + Sp2] + pcr[j - Sp2];
+                const float x2 = pcr[j + 2 * Sp2] + pcr[j - 2 * Sp2];
+                const float x3 = pcr[j + 3 * Sp2] + pcr[j - 3 * Sp2];
+                const float s1 = (pz[j + 4] + pz[j + 2]) + (pcr[j + Syz] + pcr[j - Syz]) + x1;
+                const float s2 = (pz[j + 5] + pz[j + 1]) + (pcr[j + 2 * Syz] + pcr[j - 2 * Syz]) + x2;
+                const float s3 = (pz[j + 6] + pz[j]) + (pcr[j + 3 * Syz] + pcr[j - 3 * Syz]) + x3;
                 const float a = fmaf(c0, pz[j + 3], fmaf(c1, s1, fmaf(c2, s2, c3 * s3)));
                 ap[j] = -a;
                 if (j < rlen) pa = fmaf(pz[j + 3], -a, pa);
@@ -383,9 +387,10 @@ __device__ __noinline__ RunSeg pts_segment(float* ps, const float* pm, const flo
 // and z neighbours stay in registers (a point costs 12 shared loads plus a
 // share of the run's PTS + 6), and the thread map puts the runs of a warp in
 // distinct banks.
-template <int NT, int C, int PTS, bool RUNS, int SYZ, bool ISO>
+template <int NT, int C, int PTS, int MODE, int SYZ, bool ISO>
 __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_constant__ SolveParams P,
                                                              const __grid_constant__ ClusterLayout CL) {
+    constexpr bool RUNS = MODE != 0, HALO = MODE == 1;  // the only run mode has halo planes
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     extern __shared__ double smem[];
@@ -402,7 +407,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
     const double* zp = yp + (2 * Rc + 1) * 8;
     // shared memory: the p slab, then the CG correction d and the point map, [PTS][NT] each
     float* ps = reinterpret_cast<float*>(smem);
-    const int slab_floats = (CL.cap_planes + (RUNS ? 6 : 0)) * CL.Sp2;
+    const int slab_floats = (CL.cap_planes + (HALO ? 6 : 0)) * CL.Sp2;
     float* ds = ps + ((slab_floats + 3) & ~3);  // 16-byte aligned
     int* spk = RUNS ? nullptr : reinterpret_cast<int*>(ds + PTS * NT);
     // the shell phase's per-warp coefficient buffers reuse ds (idle outside the CG)
@@ -610,14 +615,14 @@ size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant);
 // Supported (threads, cluster size, points per thread) instantiations.
 struct ClusterVariant {
     int nt, c, pts;
-    bool runs;
+    int mode;  // 0 point map, 1 z runs with halo planes
     int syz;   // slab row pitch the variant is specialised for (0 = any)
     bool iso;  // isotropic stencil only
     const void* fn;
     cudaError_t (*launch)(const SolveParams&, const ClusterLayout&, int, size_t, cudaStream_t);
 };
 
-template <int NT, int C, int PTS, bool RUNS, int SYZ, bool ISO>
+template <int NT, int C, int PTS, int MODE, int SYZ, bool ISO>
 static cudaError_t launch_cluster_t(const SolveParams& P, const ClusterLayout& CL, int n_clusters, size_t smem,
                                     cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
@@ -632,22 +637,22 @@ static cudaError_t launch_cluster_t(const SolveParams& P, const ClusterLayout& C
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, cluster_pair_kernel<NT, C, PTS, RUNS, SYZ, ISO>, P, CL);
+    return cudaLaunchKernelEx(&cfg, cluster_pair_kernel<NT, C, PTS, MODE, SYZ, ISO>, P, CL);
 }
 
-#define EXX_CLUSTER_VARIANT(NT, C, PTS, RUNS, SYZ, ISO)                                             \
-    {NT, C, PTS, RUNS, SYZ, ISO, (const void*)cluster_pair_kernel<NT, C, PTS, RUNS, SYZ, ISO>,       \
-     launch_cluster_t<NT, C, PTS, RUNS, SYZ, ISO>}
+#define EXX_CLUSTER_VARIANT(NT, C, PTS, MODE, SYZ, ISO)                                             \
+    {NT, C, PTS, MODE, SYZ, ISO, (const void*)cluster_pair_kernel<NT, C, PTS, MODE, SYZ, ISO>,       \
+     launch_cluster_t<NT, C, PTS, MODE, SYZ, ISO>}
 static const ClusterVariant kVariants[] = {
     // point map, any radius and spacing
-    EXX_CLUSTER_VARIANT(512, 2, 8, false, 0, false),   EXX_CLUSTER_VARIANT(512, 2, 18, false, 0, false),
-    EXX_CLUSTER_VARIANT(512, 4, 10, false, 0, false),  EXX_CLUSTER_VARIANT(512, 4, 18, false, 0, false),
-    EXX_CLUSTER_VARIANT(512, 8, 17, false, 0, false),  EXX_CLUSTER_VARIANT(1024, 8, 9, false, 0, false),
-    EXX_CLUSTER_VARIANT(1024, 9, 8, false, 0, false),
+    EXX_CLUSTER_VARIANT(512, 2, 8, 0, 0, false),   EXX_CLUSTER_VARIANT(512, 2, 18, 0, 0, false),
+    EXX_CLUSTER_VARIANT(512, 4, 10, 0, 0, false),  EXX_CLUSTER_VARIANT(512, 4, 18, 0, 0, false),
+    EXX_CLUSTER_VARIANT(512, 8, 17, 0, 0, false),  EXX_CLUSTER_VARIANT(1024, 8, 9, 0, 0, false),
+    EXX_CLUSTER_VARIANT(1024, 9, 8, 0, 0, false),
     // point map specialised for R_PE = 24 (pitch 55) on isotropic grids
-    EXX_CLUSTER_VARIANT(1024, 9, 8, false, 55, true),  EXX_CLUSTER_VARIANT(1024, 8, 9, false, 55, true),
+    EXX_CLUSTER_VARIANT(1024, 9, 8, 0, 55, true),  EXX_CLUSTER_VARIANT(1024, 8, 9, 0, 55, true),
     // z runs with halo planes, specialised for R_PE = 24 (pitch 55) and 16 (39)
-    EXX_CLUSTER_VARIANT(1024, 9, 8, true, 55, true),   EXX_CLUSTER_VARIANT(1024, 4, 8, true, 39, true),
+    EXX_CLUSTER_VARIANT(1024, 9, 8, 1, 55, true),  EXX_CLUSTER_VARIANT(1024, 4, 8, 1, 39, true),
 };
 #undef EXX_CLUSTER_VARIANT
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
@@ -660,7 +665,7 @@ int cluster_variant(int C, int max_pts, int threads, int syz, bool iso) {
     int best = -1;
     for (int v = 0; v < kNumVariants; ++v) {
         const ClusterVariant& K = kVariants[v];
-        if (K.runs || K.c != C || K.nt * K.pts < max_pts) continue;
+        if (K.mode != 0 || K.c != C || K.nt * K.pts < max_pts) continue;
         if (threads && K.nt != threads) continue;
         if (K.syz && (K.syz != syz || !iso)) continue;
         if (best < 0) {
@@ -706,7 +711,7 @@ cudaError_t launch_cluster_kernel(int variant, const SolveParams& P, const Clust
 }
 
 int cluster_variant_threads(int variant) { return kVariants[variant].nt; }
-int cluster_variant_runs(int variant) { return kVariants[variant].runs ? 1 : 0; }
+int cluster_variant_runs(int variant) { return kVariants[variant].mode; }
 int cluster_variant_syz(int variant) { return kVariants[variant].syz; }
 int cluster_variant_count() { return kNumVariants; }
 int cluster_variant_size(int variant) { return kVariants[variant].c; }
@@ -715,9 +720,9 @@ int cluster_variant_pts(int variant) { return kVariants[variant].pts; }
 size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant) {
     (void)Rc;
     const size_t per = (size_t)kVariants[variant].nt * kVariants[variant].pts;
-    const bool runs = kVariants[variant].runs;
-    // slab (runs: with 3 halo planes per side), d [PTS][NT], the point map (point slots)
-    const size_t slab = (size_t)(CL.cap_planes + (runs ? 6 : 0)) * CL.Sp2;
+    const bool runs = kVariants[variant].mode != 0, halo = kVariants[variant].mode == 1;
+    // slab (with 3 halo planes per side for mode 1), d [PTS][NT], the point map (point slots)
+    const size_t slab = (size_t)(CL.cap_planes + (halo ? 6 : 0)) * CL.Sp2;
     return sizeof(float) * (((slab + 3) & ~(size_t)3) + per) + (runs ? 0 : sizeof(int) * per);
 }
 
