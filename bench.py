@@ -220,7 +220,7 @@ def main():
     ap.add_argument("--solver-kind", type=int, default=0, help="0 auto, 1 one CTA per pair, 2 cluster per pair")
     ap.add_argument("--cluster-size", type=int, default=0)
     ap.add_argument("--lane-map", type=int, default=0)
-    ap.add_argument("--update-drop", type=float, default=1e-3)
+    ap.add_argument("--update-drop", type=float, default=1e-4)
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--orbitals", type=int, default=0,
                     help="keep only the first N orbitals of the workload (small cases for profiling)")

@@ -204,7 +204,7 @@ extern "C" exx_options exx_default_options(void) {
     o.ctas_per_sm = 0;
     o.solver_kind = 0;
     o.cluster_size = 0;
-    o.update_drop = 1e-3;
+    o.update_drop = 1e-4;
     o.lane_map = 0;
     o.autotune = 1;
     return o;
@@ -317,7 +317,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (o.max_iter <= 0) o.max_iter = 20000;
     if (o.inner_max_iter <= 0) o.inner_max_iter = 4000;
     if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) o.inner_tol = 1e-5;
-    if (!(o.update_drop > 0.0 && o.update_drop < 1.0)) o.update_drop = 1e-3;
+    if (!(o.update_drop > 0.0 && o.update_drop < 1.0)) o.update_drop = 1e-4;
     if (o.threads != 0 && (o.threads < 256 || o.threads > 1024 || o.threads % 32))
         return fail(nullptr, EXX_EINVAL, "exx_init: threads must be 0 or a multiple of 32 in [256, 1024]");
     if (o.solver_kind < 0 || o.solver_kind > 2) return fail(nullptr, EXX_EINVAL, "exx_init: solver_kind must be 0, 1 or 2");
