@@ -130,7 +130,7 @@ __device__ __noinline__ void cta_warm_store(const int* __restrict__ cube, const 
     for (int k = k0 + (int)threadIdx.x; k < k1; k += nt) vdst[k] = (float)vc[cube[k]];
 }
 
-// The z-run CG of one pair (RUNS = true), in segments between FP64 residual
+// The z-run CG of one pair (MODE 1), in segments between FP64 residual
 // replacements, each in its own register allocation: a segment (re)starts
 // from r = r64 / scale (p = r, or p = carry p + r after a replacement), runs
 // FP32 CG iterations until the recursive residual has dropped by update_drop
@@ -378,9 +378,9 @@ __device__ __noinline__ RunSeg pts_segment(float* ps, const float* pm, const flo
     return out;
 }
 
-// RUNS = false: thread slot j of a thread holds one point of the slab (the
+// MODE 0: thread slot j of a thread holds one point of the slab (the
 // [PTS][NT] point map); x legs that leave the slab read the neighbour's slab.
-// RUNS = true: the thread owns one run of at most PTS consecutive points of a
+// MODE 1: the thread owns one run of at most PTS consecutive points of a
 // slab row, and the slab carries 3 halo planes on each side that the
 // neighbours fill with remote stores whenever they write p; the stencil then
 // reads only the CTA's own shared memory at fixed offsets, the run's p values
