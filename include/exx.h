@@ -69,7 +69,12 @@ typedef struct {
     int radii_mode;    /* 0: fixed R_PE / R_ME for all pairs (default).
                           1: per-pair radii from the orbital exponents passed to
                              exx_compute (alphas), clamped to [12, R_PE]; R_PE and
-                             R_ME of exx_init are then the maxima.               */
+                             R_ME of exx_init are then the maxima.
+                          2: separate radii for self and non-self pairs (the
+                             paper's self / non-self proto-subdomains, Sec. IV):
+                             self pairs use R_PE / R_ME of exx_init, non-self
+                             pairs r_pe_nonself / r_me_nonself below.
+                          1 and 2 run on the one-CTA solver (solver_kind 1).   */
     int max_iter;      /* CG iteration cap per solve (default 20000).            */
     int inner_max_iter;/* FP32 inner iterations per refinement step (default 4000) */
     double inner_tol;  /* FP32 inner relative tolerance (default 1e-5).          */
@@ -101,6 +106,9 @@ typedef struct {
                           time every fitting launch shape (cluster size, threads
                           per CTA, lane map) on a prefix of the pair queue and
                           keep the fastest (default); 0 = take the first fit.    */
+    int r_pe_nonself;  /* radii_mode 2: R_PE of non-self pairs, 1..R_PE        */
+    int r_me_nonself;  /* radii_mode 2: R_ME of non-self pairs,
+                          r_pe_nonself + 3 .. R_ME                              */
 } exx_options;
 
 typedef struct {

@@ -20,7 +20,7 @@ namespace exx {
 cudaError_t launch_pair_list(int n, const double* centers, const double L[3], const double delta[3], const int N[3],
                              double r_pair, int r_pe, int r_me, int* counts, int* offsets, int* n_pair, int* queue,
                              PairRec* pairs, cudaStream_t st, const double* alphas, double ln_inv_eps,
-                             double delta_max, int r_min);
+                             double delta_max, int r_min, int ns_pe = 0, int ns_me = 0);
 cudaError_t launch_radii_sort(const PairRec* pairs, const int* n_pair, int* hist, int n_geo, int* order, int num_sms,
                               cudaStream_t st);
 cudaError_t launch_zero(double* p, long long n, int num_sms, cudaStream_t st);
@@ -69,6 +69,7 @@ struct exx_ctx {
     HostBall hb;                  // the largest ball (sizes the workspace)
     std::vector<HostBall> balls;  // balls[geo], R_PE = r_min + geo
     int r_min = 0, n_geo = 1;
+    int ns_pe = 0, ns_me = 0;     // radii_mode 2: non-self radii (geometry 0; self pairs use geometry 1)
     double ln_inv_eps = 0.0, delta_max = 0.0;
     void* geo_mem = nullptr;  // device tables
     BallGeo* d_geos = nullptr;
@@ -197,6 +198,8 @@ extern "C" exx_options exx_default_options(void) {
     o.batched = 1;
     o.warm_start = 0;
     o.radii_mode = 0;
+    o.r_pe_nonself = 0;
+    o.r_me_nonself = 0;
     o.max_iter = 20000;
     o.inner_max_iter = 4000;
     o.inner_tol = 1e-5;
@@ -302,7 +305,14 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (!(tol > 0.0 && tol < 1.0)) return fail(nullptr, EXX_EINVAL, "exx_init: tol must be in (0, 1)");
     exx_options o = opt ? *opt : exx_default_options();
     if (o.precision != 0 && o.precision != 1) return fail(nullptr, EXX_EINVAL, "exx_init: precision must be 0 or 1");
-    if (o.radii_mode != 0 && o.radii_mode != 1) return fail(nullptr, EXX_EINVAL, "exx_init: radii_mode must be 0 or 1");
+    if (o.radii_mode < 0 || o.radii_mode > 2) return fail(nullptr, EXX_EINVAL, "exx_init: radii_mode must be 0, 1 or 2");
+    if (o.radii_mode == 2) {
+        if (o.r_pe_nonself < 1 || o.r_pe_nonself > r_pe || o.r_me_nonself > r_me ||
+            o.r_me_nonself < o.r_pe_nonself + 3)
+            return fail(nullptr, EXX_EINVAL,
+                        "exx_init: radii_mode 2 needs 1 <= r_pe_nonself <= r_pe, r_pe_nonself + 3 <= r_me_nonself <= r_me");
+        if (o.solver_kind == 2) return fail(nullptr, EXX_EINVAL, "exx_init: radii_mode 2 runs on solver_kind 1");
+    }
     if (o.radii_mode == 1) {
         const int rme_rule = r_pe + std::max(3, (r_pe + 2) / 3);
         if (r_me < rme_rule)
@@ -369,6 +379,11 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (o.radii_mode == 1) {
         c->r_min = std::min(12, r_pe);
         c->n_geo = r_pe - c->r_min + 1;
+    } else if (o.radii_mode == 2) {
+        c->r_min = o.r_pe_nonself;
+        c->n_geo = 2;
+        c->ns_pe = o.r_pe_nonself;
+        c->ns_me = o.r_me_nonself;
     } else {
         c->r_min = r_pe;
         c->n_geo = 1;
@@ -377,8 +392,12 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     c->delta_max = std::max(c->delta[0], std::max(c->delta[1], c->delta[2]));
     c->balls.resize(c->n_geo);
     for (int g = 0; g < c->n_geo; ++g) {
-        const int R = c->r_min + g;
-        const int Rm = o.radii_mode == 1 ? R + std::max(3, (R + 2) / 3) : r_me;
+        int R = c->r_min + g;
+        int Rm = o.radii_mode == 1 ? R + std::max(3, (R + 2) / 3) : r_me;
+        if (o.radii_mode == 2) {  // geometry 0: non-self pairs, 1: self pairs
+            R = g == 0 ? o.r_pe_nonself : r_pe;
+            Rm = g == 0 ? o.r_me_nonself : r_me;
+        }
         build_ball(c->balls[g], R, Rm, Rc);
     }
     c->hb = c->balls.back();
@@ -712,7 +731,8 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
     CK(cudaMemsetAsync(c->d_phase, 0, sizeof(unsigned long long) * 4, st), "reset phase clocks");
     CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
                         c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st,
-                        c->n_geo > 1 ? alphas : nullptr, c->ln_inv_eps, c->delta_max, c->r_min),
+                        c->opt.radii_mode == 1 ? alphas : nullptr, c->ln_inv_eps, c->delta_max, c->r_min, c->ns_pe,
+                        c->ns_me),
        "pair list");
     if (c->n_geo > 1)
         CK(launch_radii_sort(c->d_pairs, c->d_scalars, c->d_hist, c->n_geo, c->d_order, c->num_sms, st),
@@ -838,7 +858,8 @@ static exx_status autotune(exx_ctx* c, const double* orbitals, const double* cen
                            cudaStream_t st) {
     CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
                         c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st,
-                        c->n_geo > 1 ? alphas : nullptr, c->ln_inv_eps, c->delta_max, c->r_min),
+                        c->opt.radii_mode == 1 ? alphas : nullptr, c->ln_inv_eps, c->delta_max, c->r_min, c->ns_pe,
+                        c->ns_me),
        "pair list (autotune)");
     int np = 0;
     CK(cudaMemcpyAsync(&np, c->d_scalars, sizeof(int), cudaMemcpyDeviceToHost, st), "read n_pair");
@@ -893,7 +914,8 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
     if (!orbitals || !centers || !e_xx || !d_xx) return fail(c, EXX_EINVAL, "exx_compute: NULL array argument");
     if (n < 1 || n > 65535) return fail(c, EXX_EINVAL, "exx_compute: n must be in [1, 65535]");
     if ((const void*)orbitals == (const void*)d_xx) return fail(c, EXX_EINVAL, "exx_compute: d_xx aliases orbitals");
-    if (c->n_geo > 1 && !alphas) return fail(c, EXX_EINVAL, "exx_compute: radii_mode 1 needs the orbital exponents (alphas)");
+    if (c->opt.radii_mode == 1 && !alphas)
+        return fail(c, EXX_EINVAL, "exx_compute: radii_mode 1 needs the orbital exponents (alphas)");
     if (((reinterpret_cast<uintptr_t>(orbitals) | reinterpret_cast<uintptr_t>(centers) |
           reinterpret_cast<uintptr_t>(d_xx) | reinterpret_cast<uintptr_t>(alphas)) & 7u) != 0)
         return fail(c, EXX_EINVAL, "exx_compute: arrays must be 8-byte aligned");

@@ -27,6 +27,9 @@ struct PairGeom {
     const double* alphas;
     double ln_inv_eps, delta_max;
     int r_min;
+    // separate radii for non-self pairs (ns_pe > 0): self pairs keep r_pe,
+    // r_me (geometry 1), non-self pairs take ns_pe, ns_me (geometry 0)
+    int ns_pe, ns_me;
 };
 
 // R_PE = clamp(ceil((s_eps + |cbar - C_ij|)/delta), r_min, r_max) with
@@ -147,6 +150,11 @@ __global__ void pairs_fill_kernel(int n, const double* __restrict__ C, PairGeom 
                 r.r_pe = pair_radius_d(G.alphas[i], G.alphas[j], d2, G, &rme);
                 r.r_me = rme;
                 r.geo = r.r_pe - G.r_min;
+            } else if (G.ns_pe > 0) {
+                const bool self = i == j;
+                r.r_pe = self ? G.r_pe : G.ns_pe;
+                r.r_me = self ? G.r_me : G.ns_me;
+                r.geo = self ? 1 : 0;
             } else {
                 r.r_pe = G.r_pe;
                 r.r_me = G.r_me;
@@ -222,7 +230,7 @@ namespace exx {
 cudaError_t launch_pair_list(int n, const double* centers, const double L[3], const double delta[3], const int N[3],
                              double r_pair, int r_pe, int r_me, int* counts, int* offsets, int* n_pair, int* queue,
                              PairRec* pairs, cudaStream_t st, const double* alphas, double ln_inv_eps,
-                             double delta_max, int r_min) {
+                             double delta_max, int r_min, int ns_pe, int ns_me) {
     PairGeom G;
     for (int a = 0; a < 3; ++a) {
         G.L[a] = L[a];
@@ -236,6 +244,8 @@ cudaError_t launch_pair_list(int n, const double* centers, const double L[3], co
     G.ln_inv_eps = ln_inv_eps;
     G.delta_max = delta_max;
     G.r_min = r_min;
+    G.ns_pe = ns_pe;
+    G.ns_me = ns_me;
     pairs_count_kernel<<<n, 256, 0, st>>>(n, centers, G, counts);
     pairs_scan_kernel<<<1, 1024, 0, st>>>(n, counts, offsets, n_pair, queue);
     pairs_fill_kernel<<<n, 256, 0, st>>>(n, centers, G, offsets, pairs);

@@ -139,6 +139,44 @@ def time_forward(S: int, B: int, reps: int = 5) -> dict:
             "tflops": 2.0 * conv_macs(S) * B / (ms / 1e3) / 1e12}
 
 
+def evaluate(model_blob: bytes, seeds, tol: float = 1e-8, log=None) -> dict:
+    """CG iterations to tol from zero and from the learned guess on every pair
+    of the seeded tiny-form workloads (each solved twice, warm_start 0 and 2)."""
+    import torch
+    it0 = it2 = pairs = 0
+    de = 0.0
+    guess_ms = solve0 = solve2 = 0.0
+    ex0 = ex2 = None
+    for seed in seeds:
+        w = synth.config0(seed)
+        if ex0 is None:
+            ex0 = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, tol, precision=1, warm_start=0)
+            ex2 = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, tol, precision=1, warm_start=2)
+            ex2.load_guess_model(model_blob)
+        phi = torch.from_numpy(w.orbitals()).cuda()
+        cen = torch.from_numpy(np.ascontiguousarray(w.centers)).cuda()
+        D = torch.empty_like(phi)
+        e0 = ex0.compute(phi, cen, D)
+        s0 = ex0.stats()
+        e2 = ex2.compute(phi, cen, D)
+        s2 = ex2.stats()
+        it0 += s0["iters_total"]
+        it2 += s2["iters_total"]
+        pairs += s0["n_pair"]
+        de = max(de, abs(e2 - e0) / w.n)
+        guess_ms += s2["guess_ms"]
+        solve0 += s0["solve_ms"]
+        solve2 += s2["solve_ms"]
+    ex0.close()
+    ex2.close()
+    out = {"pairs": pairs, "tol": tol, "iters_per_pair_zero": it0 / pairs, "iters_per_pair_learned": it2 / pairs,
+           "iteration_ratio": it2 / it0, "max_dE_per_orbital": de, "guess_us_per_pair": 1e3 * guess_ms / pairs,
+           "solve_ms_zero": solve0, "solve_ms_learned": solve2}
+    if log:
+        log(str(out))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=None)
@@ -148,6 +186,8 @@ def main():
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--workload", default="tiny", choices=["tiny", "water64"])
     ap.add_argument("--per-workload", type=int, default=400, help="water64: pairs kept per workload")
+    ap.add_argument("--eval-seeds", type=int, default=0, help="held-out tiny-form workloads to evaluate on")
+    ap.add_argument("--eval-tol", type=float, default=1e-8)
     ap.add_argument("--time-forward", type=int, nargs=2, metavar=("S", "B"), default=None,
                     help="only time the forward pass on B random samples of side S (He-initialised weights)")
     args = ap.parse_args()
@@ -165,11 +205,16 @@ def main():
                                     per_workload=args.per_workload)
     print(f"{inp.shape[0]} samples in {time.time() - t0:.1f} s", flush=True)
     net, hist = train(inp, tgt, S=S, epochs=args.epochs, batch=args.batch, lr=args.lr, log=print)
-    if not args.out:
-        raise SystemExit("--out is required for training")
-    with open(args.out, "wb") as f:
-        f.write(guess_model_blob(S, net.get_params()))
-    print("loss", hist[0], "->", hist[-1])
+    blob = guess_model_blob(S, net.get_params())
+    if args.out:
+        with open(args.out, "wb") as f:
+            f.write(blob)
+    print("loss", hist[0], "->", hist[-1], flush=True)
+    if args.eval_seeds and args.workload == "tiny":
+        del inp, tgt
+        net.close()
+        torch.cuda.empty_cache()
+        evaluate(blob, range(5000, 5000 + args.eval_seeds), tol=args.eval_tol, log=print)
 
 
 if __name__ == "__main__":

@@ -87,6 +87,19 @@ def test_init_rejects_bad_options(lib):
     o.threads = 300
     st, ctx = _init(lib, opt=o)
     assert st == -1 and "threads" in lib.exx_last_error(None).decode()
+    # separate self / non-self radii: the non-self ball must fit inside the self one
+    for pe, me in ((0, 16), (17, 20), (12, 14), (12, 21)):
+        o = lib.exx_default_options()
+        o.radii_mode = 2
+        o.r_pe_nonself, o.r_me_nonself = pe, me
+        st, ctx = _init(lib, opt=o)
+        assert st == -1 and "r_pe_nonself" in lib.exx_last_error(None).decode(), (pe, me)
+    o = lib.exx_default_options()
+    o.radii_mode = 2
+    o.r_pe_nonself, o.r_me_nonself = 12, 16
+    o.solver_kind = 2
+    st, ctx = _init(lib, opt=o)
+    assert st == -1 and "solver_kind 1" in lib.exx_last_error(None).decode()
 
 
 def test_null_and_destroy_are_safe(lib):

@@ -251,6 +251,30 @@ def test_per_pair_radii_small(torch, precision):
     np.testing.assert_allclose(out["pairs"]["e_pair"], ref["E_pair"], rtol=1e-7, atol=1e-12)
 
 
+@pytest.mark.parametrize("precision", [1, 0])
+def test_self_and_nonself_radii(torch, precision):
+    """Separate self / non-self proto-subdomains (radii_mode 2): self pairs on
+    R_PE/R_ME = 16/20, non-self pairs on 12/16, against the oracle with the
+    same per-pair radii."""
+    w = synth.config0()
+    phi = w.orbitals()
+    pi, pj, g = oracle.pair_list(w.centers, w.cell, w.grid, w.r_pair)
+    self_ = pi == pj
+    rpe = np.where(self_, 16, 12).astype(np.int32)
+    rme = np.where(self_, 20, 16).astype(np.int32)
+    ref = oracle.exx(w.cell, w.grid, phi, (pi, pj, g, rpe, rme), 16, 20, w.l_max, tol=1e-13, want_d=True)
+    out = run_gpu(w, phi, torch=torch, precision=precision, radii_mode=2, r_pe_nonself=12, r_me_nonself=16)
+    _pairs_radii_equal(out["pairs"], (pi, pj, g, rpe, rme))
+    assert out["stats"]["n_nonconv"] == 0 and out["stats"]["solver_kind"] == 1
+    assert abs(out["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
+    assert d_maxrel(out["D"], ref["D"]) <= D_GATE_MAXREL
+    np.testing.assert_allclose(out["pairs"]["e_pair"], ref["E_pair"], rtol=1e-7, atol=1e-12)
+    # the GPU used the non-self radii: it is far closer to the per-pair-radii
+    # oracle than to the fixed-radii one
+    fixed = oracle.exx(w.cell, w.grid, phi, (pi, pj, g), 16, 20, w.l_max, tol=1e-13, want_d=False)
+    assert abs(out["E_xx"] - fixed["E_xx"]) > 10 * abs(out["E_xx"] - ref["E_xx"])
+
+
 def test_batched_uneven_full_size_sampled(torch):
     """The batched-uneven workload (150^3, 512 orbitals in 128 clusters,
     alpha ~ U(0.5, 2), per-pair radii 12..32, largest pairs first), checked
