@@ -27,16 +27,27 @@ namespace cg = cooperative_groups;
 
 namespace exx {
 
-// Sum over the cluster: per-CTA block sum, then each CTA's partial is pushed
-// into every CTA's part[] through distributed shared memory and, after one
-// cluster barrier, summed in rank order (the same value in every CTA).
+// Sum over the cluster: warp sums into shared memory, one CTA barrier, warp 0
+// forms the CTA total and its first C lanes push it into every CTA's part[]
+// through distributed shared memory; after one cluster barrier each CTA sums
+// part[] in rank order (the same value in every CTA, the same summation order
+// as a block sum followed by the exchange).
 template <int NT, int C, typename T>
 __device__ __forceinline__ T cluster_sum(T v, T (*red)[33], int& flip, T (*part)[16], int& cflip,
                                          cg::cluster_group& cl, int rank) {
-    v = block_sum<NT, T>(v, red, flip);
-    if (threadIdx.x < C) {
-        T* dst = cl.map_shared_rank(&part[cflip][0], (int)threadIdx.x);
-        dst[rank] = v;
+    v = warp_sum(v);
+    T* buf = red[flip];
+    flip ^= 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) buf[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        T t = lane < NT / 32 ? buf[lane] : T(0);
+        t = warp_sum(t);
+        if (lane < C) {
+            T* dst = cl.map_shared_rank(&part[cflip][0], lane);
+            dst[rank] = t;
+        }
     }
     cl.sync();
     T s = T(0);
