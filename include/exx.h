@@ -101,7 +101,10 @@ typedef struct {
                           consecutive points of a row (z neighbours in
                           registers, runs of a warp in distinct banks, halo
                           planes filled by the neighbours; isotropic grids
-                          with R_PE 16 or 24; only when requested).             */
+                          with R_PE 16 or 24; only when requested), 3 = each
+                          thread slot holds a quad of 4 consecutive points of
+                          a row (rows padded to 16 bytes, every stencil leg one
+                          16-byte load; tried by the autotuner).               */
     int autotune;      /* cluster solver: 1 = on the first exx_compute of a context
                           time every fitting launch shape (cluster size, threads
                           per CTA, lane map) on a prefix of the pair queue and

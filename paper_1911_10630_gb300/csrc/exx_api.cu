@@ -41,7 +41,8 @@ cudaError_t launch_cluster_kernel(int variant, const SolveParams& P, const Clust
                                   size_t smem, cudaStream_t st);
 int cluster_variant_threads(int variant);
 int cluster_variant_pts(int variant);
-int cluster_variant_runs(int variant);
+int cluster_variant_mode(int variant);
+int cluster_variant_iso(int variant);
 int cluster_variant_syz(int variant);
 int cluster_variant_count();
 int cluster_variant_size(int variant);
@@ -501,8 +502,9 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             int* d_pt = nullptr;
             int4* d_ri = nullptr;
             // one candidate: variant v with thread map (spk, sk) and lane map lm
-            auto add_cand = [&](int v, int lm, const std::vector<int>& spk, const std::vector<int>& sk) -> exx_status {
-                const size_t sm = cluster_kernel_smem(Rc, L, v);
+            auto add_cand = [&](int v, int lm, const std::vector<int>& spk, const std::vector<int>& sk,
+                                const ClusterLayout& LL) -> exx_status {
+                const size_t sm = cluster_kernel_smem(Rc, LL, v);
                 if ((long)sm + 2048 > (long)max_optin) return EXX_OK;
                 int nclu = 0;
                 e = cluster_prepare(v, sm, &nclu);
@@ -534,7 +536,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                 K.lane_map = lm;
                 K.n_clusters = nclu;
                 K.smem = sm;
-                K.L = L;
+                K.L = LL;
                 K.L.pt_slab = d_pt;
                 K.L.rank_info = d_ri;
                 K.L.slot_pk = d_slot;
@@ -549,7 +551,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             // barrier waits for them; reading the x legs of the runs remotely
             // instead was slower still, as a warp's remote loads scatter)
             for (int v = 0; v < cluster_variant_count(); ++v) {
-                if (!cluster_variant_runs(v) || cluster_variant_size(v) != C) continue;
+                if (cluster_variant_mode(v) != 1 || cluster_variant_size(v) != C) continue;
                 if (cluster_variant_syz(v) && cluster_variant_syz(v) != L.Syz) continue;
                 if (!isotropic) continue;  // the run kernel's stencil has one spacing
                 if (o.threads && o.threads != cluster_variant_threads(v)) continue;
@@ -557,8 +559,31 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                 if (o.lane_map != lm) continue;
                 std::vector<int> spk, sk;
                 if (build_run_maps(L, pt, cluster_variant_threads(v), cluster_variant_pts(v), spk, sk) < 0) continue;
-                const exx_status sa = add_cand(v, lm, spk, sk);
+                const exx_status sa = add_cand(v, lm, spk, sk, L);
                 if (sa != EXX_OK) return bail(sa);
+            }
+            // quads of 4 consecutive z positions per thread slot (lane map 3),
+            // on a layout whose rows are padded to 16 bytes
+            if (o.autotune || o.lane_map == 3) {
+                ClusterLayout Lq;
+                std::vector<int> ptq;
+                if (build_cluster_layout(B, C, Lq, ptq, true)) {
+                    // per thread count the first fit (the table lists specialised before generic)
+                    std::vector<int> have;  // thread counts with a candidate
+                    for (int v = 0; v < cluster_variant_count(); ++v) {
+                        if (cluster_variant_mode(v) != 2 || cluster_variant_size(v) != C) continue;
+                        if (cluster_variant_syz(v) && (cluster_variant_syz(v) != 2 * r_pe + 7 || !isotropic)) continue;
+                        if (cluster_variant_iso(v) && !isotropic) continue;
+                        const int nt = cluster_variant_threads(v);
+                        if (o.threads && o.threads != nt) continue;
+                        if (std::find(have.begin(), have.end(), nt) != have.end()) continue;
+                        std::vector<int> spk, sk;
+                        if (build_quad_maps(Lq, ptq, nt, cluster_variant_pts(v), spk, sk) < 0) continue;
+                        const exx_status sa = add_cand(v, 3, spk, sk, Lq);
+                        if (sa != EXX_OK) return bail(sa);
+                        have.push_back(nt);
+                    }
+                }
             }
             // one point per thread slot (lane maps 0 and 1)
             for (int nt : {1024, 512}) {
@@ -570,7 +595,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                     std::vector<int> spk, sk;
                     if (build_slot_maps(L, pt, cluster_variant_threads(v), cluster_variant_pts(v), lm, spk, sk) < 0)
                         continue;
-                    const exx_status sa = add_cand(v, lm, spk, sk);
+                    const exx_status sa = add_cand(v, lm, spk, sk, L);
                     if (sa != EXX_OK) return bail(sa);
                 }
             }

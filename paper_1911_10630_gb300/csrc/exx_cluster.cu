@@ -389,6 +389,180 @@ __device__ __noinline__ RunSeg pts_segment(float* ps, const float* pm, const flo
     return out;
 }
 
+// The quad-map CG of one pair in segments (MODE 2), like pts_segment: thread
+// slot j holds a 16-byte aligned quad of 4 consecutive z positions of a slab
+// row (spt: slab offset | valid mask << 20 | plane << 24; skt: compact index
+// of element 0), and a warp covers consecutive quads. Every stencil leg is one
+// 16-byte load: the quad itself and the quads before and after it (the z legs),
+// and the quads one to three rows or planes away (the y and x legs; x legs
+// past the slab come from the neighbour's slab). Elements outside the ball
+// keep r = 0 (their A p is masked) and therefore p = 0. SY > 0 is the box side
+// 2 R_PE + 7 the pitches are specialised for (row pitch rounded up to 4).
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+template <int NT, int C, int Q, int SY, bool ISO>
+__device__ __noinline__ RunSeg quad_segment(float* ps, const float* pm, const float* pp, float4* dst, const int* spt,
+                                            const int* skt, int planes, int planes_prev, int syz_rt, int sp2_rt,
+                                            double scale, float carry, StencilArgs sa, int iters, int flip32,
+                                            int cflip32) {
+    constexpr int PZ = (SY + 3) & ~3;
+    const int Syz = SY > 0 ? PZ : syz_rt;
+    const int Sp2 = SY > 0 ? SY * PZ : sp2_rt;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    float4 r[Q], ap[Q];
+    float a32 = 0.0f;
+    {
+        const double inv = 1.0 / scale;
+        const double* r64 = g_rc.r64;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const int pk = spt[j * NT];
+            const int off = pk & 0xfffff, m = (pk >> 20) & 15;
+            const int k = skt[j * NT];
+            float4 rv;
+            rv.x = (m & 1) ? (float)(r64[k] * inv) : 0.0f;
+            rv.y = (m & 2) ? (float)(r64[k + 1] * inv) : 0.0f;
+            rv.z = (m & 4) ? (float)(r64[k + 2] * inv) : 0.0f;
+            rv.w = (m & 8) ? (float)(r64[k + 3] * inv) : 0.0f;
+            r[j] = rv;
+            ap[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            dst[j * NT] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float4 pv = rv;
+            if (carry >= 0.0f) {
+                const float4 po = ld4(ps + off);
+                pv.x = fmaf(carry, po.x, rv.x);
+                pv.y = fmaf(carry, po.y, rv.y);
+                pv.z = fmaf(carry, po.z, rv.z);
+                pv.w = fmaf(carry, po.w, rv.w);
+            }
+            st4(ps + off, pv);
+            a32 = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, fmaf(rv.w, rv.w, a32))));
+        }
+    }
+    float rr = cluster_sum<NT, C, float>(a32, g_rc_red32, flip32, g_rc_part32, cflip32, cl, rank);
+    const float lim = g_rc.drop2 * rr;
+    const float conv_thr = (float)(0.25 * g_rc.target2 / (scale * scale));
+    const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    RunSeg out;
+    float al = 0.0f;
+    for (;;) {
+        if (iters >= g_rc.max_iter) {
+            out.maxed = 1;
+            break;
+        }
+        float pa = 0.0f;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const int pk = spt[j * NT];
+            const int off = pk & 0xfffff, m = (pk >> 20) & 15, xl = (int)((unsigned)pk >> 24);
+            const float* b = ps + off;
+            const float4 c = ld4(b), zl = ld4(b - 4), zh = ld4(b + 4);
+            // z window: w[i + 3] is element i, i = -3 .. 6
+            const float w[10] = {zl.y, zl.z, zl.w, c.x, c.y, c.z, c.w, zh.x, zh.y, zh.z};
+            const float cz1 = sa.cz[0], cz2 = sa.cz[1], cz3 = sa.cz[2];
+            float a[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                a[i] = fmaf(cz1, w[i + 4] + w[i + 2],
+                            fmaf(cz2, w[i + 5] + w[i + 1], fmaf(cz3, w[i + 6] + w[i], sa.c0 * w[i + 3])));
+#pragma unroll
+            for (int q = 1; q <= 3; ++q) {
+                const float cyq = ISO ? sa.cz[q - 1] : sa.cy[q - 1];
+                const float4 ym = ld4(b - q * Syz), yp = ld4(b + q * Syz);
+                a[0] = fmaf(cyq, ym.x + yp.x, a[0]);
+                a[1] = fmaf(cyq, ym.y + yp.y, a[1]);
+                a[2] = fmaf(cyq, ym.z + yp.z, a[2]);
+                a[3] = fmaf(cyq, ym.w + yp.w, a[3]);
+            }
+#pragma unroll
+            for (int q = 1; q <= 3; ++q) {
+                const float cxq = ISO ? sa.cz[q - 1] : sa.cx[q - 1];
+                const float4 xp = xl + q < planes ? ld4(b + q * Sp2)
+                                                  : (pp ? ld4(pp + off + (q - planes) * Sp2) : zero4);
+                const float4 xm = xl - q >= 0 ? ld4(b - q * Sp2)
+                                              : (pm ? ld4(pm + off + (planes_prev - q) * Sp2) : zero4);
+                a[0] = fmaf(cxq, xm.x + xp.x, a[0]);
+                a[1] = fmaf(cxq, xm.y + xp.y, a[1]);
+                a[2] = fmaf(cxq, xm.z + xp.z, a[2]);
+                a[3] = fmaf(cxq, xm.w + xp.w, a[3]);
+            }
+            // A p = -lap p on the ball's elements, 0 elsewhere
+            float4 av;
+            av.x = (m & 1) ? -a[0] : 0.0f;
+            av.y = (m & 2) ? -a[1] : 0.0f;
+            av.z = (m & 4) ? -a[2] : 0.0f;
+            av.w = (m & 8) ? -a[3] : 0.0f;
+            ap[j] = av;
+            pa = fmaf(c.x, av.x, fmaf(c.y, av.y, fmaf(c.z, av.z, fmaf(c.w, av.w, pa))));
+        }
+        const float pap = cluster_sum<NT, C, float>(pa, g_rc_red32, flip32, g_rc_part32, cflip32, cl, rank);
+        al = rr / pap;
+        float ra = 0.0f;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            r[j].x = fmaf(-al, ap[j].x, r[j].x);
+            r[j].y = fmaf(-al, ap[j].y, r[j].y);
+            r[j].z = fmaf(-al, ap[j].z, r[j].z);
+            r[j].w = fmaf(-al, ap[j].w, r[j].w);
+            ra = fmaf(r[j].x, r[j].x, fmaf(r[j].y, r[j].y, fmaf(r[j].z, r[j].z, fmaf(r[j].w, r[j].w, ra))));
+        }
+        const float rrn = cluster_sum<NT, C, float>(ra, g_rc_red32, flip32, g_rc_part32, cflip32, cl, rank);
+        ++iters;
+        if (rrn <= lim || rrn <= conv_thr || !(rrn == rrn)) {
+            out.maxed = 0;
+            break;
+        }
+        const float be = rrn / rr;
+        rr = rrn;
+        // d += alpha p and p = r + beta p in one pass over the quads
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            float* b = ps + (spt[j * NT] & 0xfffff);
+            const float4 po = ld4(b);
+            float4 d = dst[j * NT];
+            d.x = fmaf(al, po.x, d.x);
+            d.y = fmaf(al, po.y, d.y);
+            d.z = fmaf(al, po.z, d.z);
+            d.w = fmaf(al, po.w, d.w);
+            dst[j * NT] = d;
+            st4(b, make_float4(fmaf(be, po.x, r[j].x), fmaf(be, po.y, r[j].y), fmaf(be, po.z, r[j].z),
+                               fmaf(be, po.w, r[j].w)));
+        }
+        al = 0.0f;
+        cl.sync();
+    }
+    // the last iteration's d += alpha p (p is unchanged since its stencil), then v += scale d
+    const int* cube = g_rc.cube;
+    double* vc = g_rc.vc;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int pk = spt[j * NT];
+        const int m = (pk >> 20) & 15;
+        const float4 po = ld4(ps + (pk & 0xfffff));
+        float4 d = dst[j * NT];
+        d.x = fmaf(al, po.x, d.x);
+        d.y = fmaf(al, po.y, d.y);
+        d.z = fmaf(al, po.z, d.z);
+        d.w = fmaf(al, po.w, d.w);
+        const int k = skt[j * NT];
+        const float dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (m & (1 << i)) {
+                const int cc = cube[k + i];
+                vc[cc] = fma(scale, (double)dv[i], vc[cc]);
+            }
+        }
+    }
+    out.iters = iters;
+    out.rr = rr;
+    out.flip32 = flip32;
+    out.cflip32 = cflip32;
+    return out;
+}
+
 // MODE 0: thread slot j of a thread holds one point of the slab (the
 // [PTS][NT] point map); x legs that leave the slab read the neighbour's slab.
 // MODE 1: the thread owns one run of at most PTS consecutive points of a
@@ -398,13 +572,16 @@ __device__ __noinline__ RunSeg pts_segment(float* ps, const float* pm, const flo
 // and z neighbours stay in registers (a point costs 12 shared loads plus a
 // share of the run's PTS + 6), and the thread map puts the runs of a warp in
 // distinct banks.
+// MODE 2: thread slot j holds a quad of 4 consecutive z positions (PTS quads
+// per thread, rows padded to a multiple of 4 points), so every stencil leg
+// is one 16-byte load for 4 points (quad_segment).
 template <int NT, int C, int PTS, int MODE, int SYZ, bool ISO>
 __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_constant__ SolveParams P,
                                                              const __grid_constant__ ClusterLayout CL) {
-    constexpr bool RUNS = MODE != 0, HALO = MODE == 1;  // the only run mode has halo planes
+    constexpr bool RUNS = MODE == 1, HALO = MODE == 1, QUADS = MODE == 2;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) double smem[];
     __shared__ double red[2][33];
     __shared__ double part[2][16];
     __shared__ double s_M[kNMono], s_T[kNMono];
@@ -420,7 +597,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
     float* ps = reinterpret_cast<float*>(smem);
     const int slab_floats = (CL.cap_planes + (HALO ? 6 : 0)) * CL.Sp2;
     float* ds = ps + ((slab_floats + 3) & ~3);  // 16-byte aligned
-    int* spk = RUNS ? nullptr : reinterpret_cast<int*>(ds + PTS * NT);
+    int* spk = RUNS ? nullptr : reinterpret_cast<int*>(ds + (QUADS ? 4 : 1) * PTS * NT);
     // the shell phase's per-warp coefficient buffers reuse ds (idle outside the CG)
     double* ub = reinterpret_cast<double*>(ds) + (threadIdx.x >> 5) * (kNU + kNU / 2);
     const int Syz = CL.Syz;
@@ -565,6 +742,10 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
                 if constexpr (RUNS)
                     sg = run_segment<NT, C, PTS, SYZ>(pc + roff, ds + threadIdx.x, hm, hp, rk0, rlen, scale, carry,
                                                       sa.c0, sa.cz[0], sa.cz[1], sa.cz[2], iters, f32, cf32);
+                else if constexpr (QUADS)
+                    sg = quad_segment<NT, C, PTS, SYZ, ISO>(ps, pm, pp, reinterpret_cast<float4*>(ds) + threadIdx.x,
+                                                            spk + threadIdx.x, slot_k + threadIdx.x, planes,
+                                                            planes_prev, Syz, Sp2, scale, carry, sa, iters, f32, cf32);
                 else
                     sg = pts_segment<NT, C, PTS, SYZ, ISO>(ps, pm, pp, ds + threadIdx.x, spk + threadIdx.x,
                                                            slot_k + threadIdx.x, planes, planes_prev, Syz, scale,
@@ -626,8 +807,9 @@ size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant);
 // Supported (threads, cluster size, points per thread) instantiations.
 struct ClusterVariant {
     int nt, c, pts;
-    int mode;  // 0 point map, 1 z runs with halo planes
-    int syz;   // slab row pitch the variant is specialised for (0 = any)
+    int mode;  // 0 point map, 1 z runs with halo planes, 2 quad map
+    int syz;   // modes 0, 1: slab row pitch the variant is specialised for;
+               // mode 2: box side 2 R_PE + 7 (0 = any)
     bool iso;  // isotropic stencil only
     const void* fn;
     cudaError_t (*launch)(const SolveParams&, const ClusterLayout&, int, size_t, cudaStream_t);
@@ -664,6 +846,11 @@ static const ClusterVariant kVariants[] = {
     EXX_CLUSTER_VARIANT(1024, 9, 8, 0, 55, true),  EXX_CLUSTER_VARIANT(1024, 8, 9, 0, 55, true),
     // z runs with halo planes, specialised for R_PE = 24 (pitch 55) and 16 (39)
     EXX_CLUSTER_VARIANT(1024, 9, 8, 1, 55, true),  EXX_CLUSTER_VARIANT(1024, 4, 8, 1, 39, true),
+    // quad map (PTS = quads per thread): R_PE = 24 on isotropic grids, and any radius
+    EXX_CLUSTER_VARIANT(1024, 9, 2, 2, 55, true),  EXX_CLUSTER_VARIANT(512, 9, 4, 2, 55, true),
+    EXX_CLUSTER_VARIANT(1024, 8, 3, 2, 55, true),
+    EXX_CLUSTER_VARIANT(1024, 9, 2, 2, 0, false),  EXX_CLUSTER_VARIANT(1024, 4, 2, 2, 0, false),
+    EXX_CLUSTER_VARIANT(512, 2, 4, 2, 0, false),
 };
 #undef EXX_CLUSTER_VARIANT
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
@@ -722,7 +909,8 @@ cudaError_t launch_cluster_kernel(int variant, const SolveParams& P, const Clust
 }
 
 int cluster_variant_threads(int variant) { return kVariants[variant].nt; }
-int cluster_variant_runs(int variant) { return kVariants[variant].mode; }
+int cluster_variant_mode(int variant) { return kVariants[variant].mode; }
+int cluster_variant_iso(int variant) { return kVariants[variant].iso ? 1 : 0; }
 int cluster_variant_syz(int variant) { return kVariants[variant].syz; }
 int cluster_variant_count() { return kNumVariants; }
 int cluster_variant_size(int variant) { return kVariants[variant].c; }
@@ -731,10 +919,12 @@ int cluster_variant_pts(int variant) { return kVariants[variant].pts; }
 size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant) {
     (void)Rc;
     const size_t per = (size_t)kVariants[variant].nt * kVariants[variant].pts;
-    const bool runs = kVariants[variant].mode != 0, halo = kVariants[variant].mode == 1;
-    // slab (with 3 halo planes per side for mode 1), d [PTS][NT], the point map (point slots)
+    const int mode = kVariants[variant].mode;
+    const bool runs = mode == 1, halo = mode == 1;
+    // slab (with 3 halo planes per side for mode 1), d ([PTS][NT] points, or
+    // quads for mode 2), the slot map (point or quad slots)
     const size_t slab = (size_t)(CL.cap_planes + (halo ? 6 : 0)) * CL.Sp2;
-    return sizeof(float) * (((slab + 3) & ~(size_t)3) + per) + (runs ? 0 : sizeof(int) * per);
+    return sizeof(float) * (((slab + 3) & ~(size_t)3) + (mode == 2 ? 4 : 1) * per) + (runs ? 0 : sizeof(int) * per);
 }
 
 }  // namespace exx

@@ -173,7 +173,7 @@ void build_ball(HostBall& B, int r_pe, int r_me, int Rc) {
     B.n_me = (int)B.cube.size();
 }
 
-bool build_cluster_layout(const HostBall& B, int C, ClusterLayout& L, std::vector<int>& pt_slab) {
+bool build_cluster_layout(const HostBall& B, int C, ClusterLayout& L, std::vector<int>& pt_slab, bool pitch4) {
     const int R = B.r_pe, P = 2 * R + 1;
     if (C < 1 || C > kMaxCluster || P < 3 * C) return false;
     std::vector<long> n(P, 0), cum(P + 1, 0);
@@ -200,8 +200,8 @@ bool build_cluster_layout(const HostBall& B, int C, ClusterLayout& L, std::vecto
     for (int r = C; r >= 1; --r) bounds[r - 1] = arg[r][bounds[r]];
     std::memset(&L, 0, sizeof(L));
     L.C = C;
-    L.Syz = 2 * R + 7;
-    L.Sp2 = L.Syz * L.Syz;
+    L.Syz = pitch4 ? (2 * R + 7 + 3) & ~3 : 2 * R + 7;  // row pitch (z)
+    L.Sp2 = (2 * R + 7) * L.Syz;                         // plane pitch
     L.sy_doubles = ((2 * R + 1) * 28 + 1) & ~1;
     int cap = 0, maxp = 0;
     for (int r = 0; r < C; ++r) {
@@ -380,6 +380,44 @@ int build_run_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int 
         }
     }
     return max_runs;
+}
+
+
+int build_quad_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int NT, int Q, std::vector<int>& quad_pk,
+                    std::vector<int>& quad_k) {
+    const int per = NT * Q;
+    // idle slots: the quad at row 3, z 0..3 of plane 0 (outside the ball in
+    // every plane, so it stays zero), with no valid element
+    const int idle = 3 * L.Syz;
+    quad_pk.assign((size_t)L.C * per, idle);
+    quad_k.assign((size_t)L.C * per, 0);
+    if ((L.Syz & 3) || (long)L.cap_planes * L.Sp2 >= (1L << 20)) return -1;
+    int max_quads = 0;
+    for (int r = 0; r < L.C; ++r) {
+        int s = 0;
+        int k = L.k0[r];
+        while (k < L.k1[r]) {
+            // one row of the slab: consecutive offsets within one plane
+            int e = k + 1;
+            while (e < L.k1[r] && (pt_slab[e] & 0xffffff) == (pt_slab[e - 1] & 0xffffff) + 1 &&
+                   (pt_slab[e] >> 24) == (pt_slab[k] >> 24))
+                ++e;
+            const int off0 = pt_slab[k] & 0xffffff, xl = pt_slab[k] >> 24;
+            const int z0 = off0 % L.Syz, z1 = z0 + (e - k) - 1;  // z positions of the row's ends in the box
+            for (int qz = z0 & ~3; qz <= z1; qz += 4) {
+                if (s >= per) return -1;
+                int mask = 0;
+                for (int i = 0; i < 4; ++i)
+                    if (qz + i >= z0 && qz + i <= z1) mask |= 1 << i;
+                quad_pk[(size_t)r * per + s] = (off0 - z0 + qz) | (mask << 20) | (xl << 24);
+                quad_k[(size_t)r * per + s] = k + (qz - z0);
+                ++s;
+            }
+            k = e;
+        }
+        max_quads = std::max(max_quads, s);
+    }
+    return max_quads;
 }
 
 }  // namespace exx

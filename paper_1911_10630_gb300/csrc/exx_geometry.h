@@ -21,8 +21,10 @@ void build_multipole_const(MultipoleConst& mc);
 
 // Splits the PE ball of B into C slabs of whole x planes (each >= 3 planes),
 // minimising the largest point count. Fills L (without the device pointer) and
-// the per-point slab offsets. Returns false if no such split exists.
-bool build_cluster_layout(const HostBall& B, int C, ClusterLayout& L, std::vector<int>& pt_slab);
+// the per-point slab offsets. The slab box has 2 R_PE + 7 rows of 2 R_PE + 7
+// points per plane; pitch4 pads the row pitch to a multiple of 4 (16-byte rows
+// for the quad map). Returns false if no such split exists.
+bool build_cluster_layout(const HostBall& B, int C, ClusterLayout& L, std::vector<int>& pt_slab, bool pitch4 = false);
 void build_ball(HostBall& B, int r_pe, int r_me, int Rc);
 
 // Thread-slot maps of the cluster solver for NT threads x PTS points per CTA:
@@ -44,5 +46,16 @@ int build_slot_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int
 // rank, or -1 if a rank has more runs than NT.
 int build_run_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int NT, int ZL,
                    std::vector<int>& run_pk, std::vector<int>& run_k);
+// Thread map of the quad cluster solver (a layout built with pitch4): every
+// row of a slab is cut into 16-byte aligned quads of 4 consecutive z
+// positions, and quad s of CTA r goes to slot (j, t) = (s / NT, s % NT), so a
+// warp covers consecutive quads. quad_pk[r][j][t] = slab offset of the quad
+// | valid-element mask << 20 | plane << 24; quad_k = compact PE index of the
+// quad's element 0 (element i is k + i when mask bit i is set). Idle slots
+// point at a quad that lies outside the ball in every plane, with mask 0.
+// Returns the largest quad count of a rank, or -1 if a rank has more than
+// Q x NT quads or the slab offsets do not fit 20 bits.
+int build_quad_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int NT, int Q, std::vector<int>& quad_pk,
+                    std::vector<int>& quad_k);
 
 }  // namespace exx
