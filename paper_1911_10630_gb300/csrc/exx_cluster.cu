@@ -164,11 +164,78 @@ struct RunCgCtx {
     int max_iter;
     double target2;
     float drop2;
+    int* fault;  // incremented when a cluster-reduction wait gives up
 };
 
 __shared__ float g_rc_red32[2][33];
 __shared__ float g_rc_part32[2][16];
 __shared__ RunCgCtx g_rc;
+// one mbarrier per buffer of g_rc_mpart (cluster_sum_mb)
+__shared__ __align__(8) unsigned long long g_rc_mbar[2];
+__shared__ float g_rc_mpart[2][16];
+__shared__ int g_rc_late;  // set once a wait has given up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+// Sum over the cluster without a cluster barrier: the CTA total goes to every
+// CTA's g_rc_mpart[b][rank] by st.async, which counts its bytes on that CTA's
+// mbarrier b; each CTA announces the C x 4 bytes it expects and waits for the
+// phase to complete. Buffer b = n & 1 and its phase parity (n >> 1) & 1 follow
+// from the running count n of these sums. A CTA refills buffer b (sum n + 2)
+// only after every CTA has sent sum n + 1, which each does after all of its
+// threads have read sum n, so the two buffers suffice. A wait that gives up
+// (it never should) bumps *g_rc.fault and takes what has arrived.
+template <int NT, int C>
+__device__ __forceinline__ float cluster_sum_mb(float v, int& flip, int& n, int rank) {
+    v = warp_sum(v);
+    float* buf = g_rc_red32[flip];
+    flip ^= 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) buf[w] = v;
+    __syncthreads();
+    const int b = n & 1;
+    const uint32_t parity = (uint32_t)(n >> 1) & 1u;
+    ++n;
+    const uint32_t mb = smem_u32(&g_rc_mbar[b]);
+    if (w == 0) {
+        float t = lane < NT / 32 ? buf[lane] : 0.0f;
+        t = warp_sum(t);
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(C * 4) : "memory");
+        if (lane < C) {
+            const uint32_t dst = cluster_addr(smem_u32(&g_rc_mpart[b][rank]), lane);
+            const uint32_t rmb = cluster_addr(mb, lane);
+            asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(dst),
+                         "f"(t), "r"(rmb)
+                         : "memory");
+        }
+    }
+    uint32_t done = 0;
+    const int limit = g_rc_late ? 1 : (1 << 16);
+    for (int it = 0; it < limit && !done; ++it)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mb), "r"(parity)
+            : "memory");
+    if (!done) {
+        g_rc_late = 1;  // later waits of this CTA give up at once
+        if (threadIdx.x == 0) atomicAdd(g_rc.fault, 1);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int r = 0; r < C; ++r) s += g_rc_mpart[b][r];
+    return s;
+}
 
 template <int NT, int C, int PTS, int SYZ>
 __device__ __noinline__ RunSeg run_segment(float* pcr, float* dst, float* hm, float* hp, int rk0, int rlen,
@@ -441,7 +508,7 @@ __device__ __noinline__ RunSeg quad_segment(float* ps, const float* pm, const fl
             a32 = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, fmaf(rv.w, rv.w, a32))));
         }
     }
-    float rr = cluster_sum<NT, C, float>(a32, g_rc_red32, flip32, g_rc_part32, cflip32, cl, rank);
+    float rr = cluster_sum_mb<NT, C>(a32, flip32, cflip32, rank);
     const float lim = g_rc.drop2 * rr;
     const float conv_thr = (float)(0.25 * g_rc.target2 / (scale * scale));
     const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -497,7 +564,7 @@ __device__ __noinline__ RunSeg quad_segment(float* ps, const float* pm, const fl
             ap[j] = av;
             pa = fmaf(c.x, av.x, fmaf(c.y, av.y, fmaf(c.z, av.z, fmaf(c.w, av.w, pa))));
         }
-        const float pap = cluster_sum<NT, C, float>(pa, g_rc_red32, flip32, g_rc_part32, cflip32, cl, rank);
+        const float pap = cluster_sum_mb<NT, C>(pa, flip32, cflip32, rank);
         al = rr / pap;
         float ra = 0.0f;
 #pragma unroll
@@ -508,7 +575,7 @@ __device__ __noinline__ RunSeg quad_segment(float* ps, const float* pm, const fl
             r[j].w = fmaf(-al, ap[j].w, r[j].w);
             ra = fmaf(r[j].x, r[j].x, fmaf(r[j].y, r[j].y, fmaf(r[j].z, r[j].z, fmaf(r[j].w, r[j].w, ra))));
         }
-        const float rrn = cluster_sum<NT, C, float>(ra, g_rc_red32, flip32, g_rc_part32, cflip32, cl, rank);
+        const float rrn = cluster_sum_mb<NT, C>(ra, flip32, cflip32, rank);
         ++iters;
         if (rrn <= lim || rrn <= conv_thr || !(rrn == rrn)) {
             out.maxed = 0;
@@ -587,6 +654,9 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
     __shared__ double s_M[kNMono], s_T[kNMono];
     __shared__ int s_item;
     int flip = 0, cflip = 0;
+    // FP32 reduction state, kept for the whole launch: the quad segments' mbarrier
+    // phases advance with every sum (cluster_sum_mb), across segments and pairs
+    int f32 = 0, cf32 = 0;
 
     const int Rc = P.Rc;
     // FP64 power tables (global, read-only) and this CTA's plane sums (global slot)
@@ -649,6 +719,13 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
 
     const int gt = rank * NT + (int)threadIdx.x, gn = C * NT;
     const int np = *P.n_pair;
+    if (QUADS && threadIdx.x == 0) {
+        // the quad segments' reduction barriers (count 1: this CTA's own arrive)
+        for (int b = 0; b < 2; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&g_rc_mbar[b])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        g_rc_late = 0;
+    }
     cl.sync();
 
     for (;;) {
@@ -724,11 +801,11 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
                 g_rc.max_iter = P.max_iter;
                 g_rc.target2 = target2;
                 g_rc.drop2 = (float)(P.update_drop * P.update_drop);
+                g_rc.fault = P.nonconv;
             }
             __syncthreads();
             double scale = sqrt(rn_start);
             float carry = -1.0f;
-            int f32 = 0, cf32 = 0;
             StencilArgs sa;
             sa.c0 = P.st32.c0;
 #pragma unroll
