@@ -104,7 +104,11 @@ typedef struct {
                           with R_PE 16 or 24; only when requested), 3 = each
                           thread slot holds a quad of 4 consecutive points of
                           a row (rows padded to 16 bytes, every stencil leg one
-                          16-byte load; tried by the autotuner).               */
+                          16-byte load; x legs past the slab read from the
+                          neighbour), 4 = quads with 3 halo planes per side
+                          that the neighbours fill by asynchronous remote
+                          stores (all stencil loads local); 3 and 4 are tried
+                          by the autotuner.                                    */
     int autotune;      /* cluster solver: 1 = on the first exx_compute of a context
                           time every fitting launch shape (cluster size, threads
                           per CTA, lane map) on a prefix of the pair queue and

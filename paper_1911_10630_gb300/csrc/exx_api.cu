@@ -503,7 +503,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             int4* d_ri = nullptr;
             // one candidate: variant v with thread map (spk, sk) and lane map lm
             auto add_cand = [&](int v, int lm, const std::vector<int>& spk, const std::vector<int>& sk,
-                                const ClusterLayout& LL) -> exx_status {
+                                const ClusterLayout& LL, const std::vector<int>* hb = nullptr) -> exx_status {
                 const size_t sm = cluster_kernel_smem(Rc, LL, v);
                 if ((long)sm + 2048 > (long)max_optin) return EXX_OK;
                 int nclu = 0;
@@ -524,11 +524,15 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                     if (e != cudaSuccess) return cuda_fail(c, e, "slab tables");
                 }
                 int* d_slot = nullptr;
-                e = cudaMalloc(&d_slot, sizeof(int) * (spk.size() + sk.size()));
+                const size_t nhb = hb ? hb->size() : 0;
+                e = cudaMalloc(&d_slot, sizeof(int) * (spk.size() + sk.size() + nhb));
                 if (e == cudaSuccess) c->cl_mem.push_back(d_slot);
                 if (e == cudaSuccess) e = cudaMemcpy(d_slot, spk.data(), sizeof(int) * spk.size(), cudaMemcpyHostToDevice);
                 if (e == cudaSuccess)
                     e = cudaMemcpy(d_slot + spk.size(), sk.data(), sizeof(int) * sk.size(), cudaMemcpyHostToDevice);
+                if (e == cudaSuccess && nhb)
+                    e = cudaMemcpy(d_slot + spk.size() + sk.size(), hb->data(), sizeof(int) * nhb,
+                                   cudaMemcpyHostToDevice);
                 if (e != cudaSuccess) return cuda_fail(c, e, "slot maps");
                 exx_ctx::ClusterCand K;
                 K.C = C;
@@ -541,6 +545,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                 K.L.rank_info = d_ri;
                 K.L.slot_pk = d_slot;
                 K.L.slot_k = d_slot + spk.size();
+                K.L.halo_bytes = nhb ? d_slot + spk.size() + sk.size() : nullptr;
                 c->cands.push_back(K);
                 return EXX_OK;
             };
@@ -562,26 +567,31 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                 const exx_status sa = add_cand(v, lm, spk, sk, L);
                 if (sa != EXX_OK) return bail(sa);
             }
-            // quads of 4 consecutive z positions per thread slot (lane map 3),
-            // on a layout whose rows are padded to 16 bytes
-            if (o.autotune || o.lane_map == 3) {
+            // quads of 4 consecutive z positions per thread slot, on a layout
+            // whose rows are padded to 16 bytes: x legs read from the
+            // neighbours (lane map 3) or from halo planes (lane map 4)
+            if (o.autotune || o.lane_map == 3 || o.lane_map == 4) {
                 ClusterLayout Lq;
                 std::vector<int> ptq;
                 if (build_cluster_layout(B, C, Lq, ptq, true)) {
                     // per thread count the first fit (the table lists specialised before generic)
-                    std::vector<int> have;  // thread counts with a candidate
+                    std::vector<int> have;  // (mode, thread count) pairs with a candidate
                     for (int v = 0; v < cluster_variant_count(); ++v) {
-                        if (cluster_variant_mode(v) != 2 || cluster_variant_size(v) != C) continue;
+                        const int mode = cluster_variant_mode(v);
+                        if ((mode != 2 && mode != 3) || cluster_variant_size(v) != C) continue;
                         if (cluster_variant_syz(v) && (cluster_variant_syz(v) != 2 * r_pe + 7 || !isotropic)) continue;
                         if (cluster_variant_iso(v) && !isotropic) continue;
                         const int nt = cluster_variant_threads(v);
                         if (o.threads && o.threads != nt) continue;
-                        if (std::find(have.begin(), have.end(), nt) != have.end()) continue;
-                        std::vector<int> spk, sk;
+                        const int lm = mode == 2 ? 3 : 4;
+                        if (!o.autotune && o.lane_map != lm) continue;
+                        if (std::find(have.begin(), have.end(), mode * 4096 + nt) != have.end()) continue;
+                        std::vector<int> spk, sk, hb;
                         if (build_quad_maps(Lq, ptq, nt, cluster_variant_pts(v), spk, sk) < 0) continue;
-                        const exx_status sa = add_cand(v, 3, spk, sk, Lq);
+                        if (mode == 3) quad_halo_bytes(Lq, spk, nt * cluster_variant_pts(v), hb);
+                        const exx_status sa = add_cand(v, lm, spk, sk, Lq, mode == 3 ? &hb : nullptr);
                         if (sa != EXX_OK) return bail(sa);
-                        have.push_back(nt);
+                        have.push_back(mode * 4096 + nt);
                     }
                 }
             }

@@ -155,6 +155,7 @@ struct RunSeg {
     int iters, maxed;  // maxed: stopped at max_iter
     float rr;          // r.r (in the segment's units) before the last iteration
     int flip32, cflip32;
+    int hphase;        // halo mbarrier phases so far (quad_halo_segment)
 };
 
 struct RunCgCtx {
@@ -630,6 +631,218 @@ __device__ __noinline__ RunSeg quad_segment(float* ps, const float* pm, const fl
     return out;
 }
 
+// The quad-map CG with halo planes (MODE 3). The slab array holds 3 halo planes
+// on each side of the CTA's planes (pc = plane 0), so every stencil leg is a
+// local 16-byte load at a fixed offset. Whenever a CTA writes p, each quad of
+// its first or last 3 planes also goes by st.async to the neighbour's halo,
+// counted in bytes on the neighbour's halo mbarrier (g_halo_mbar). Every
+// thread arrives on its own CTA's halo mbarrier after its p writes (thread 0
+// also announces the bytes the neighbours send per phase), so one completed
+// phase means the CTA's p and both halos are current: no cluster barrier. The
+// correction d stays in registers. A neighbour refills a halo only after the
+// r.r sum of the iteration, to which this CTA contributed after its stencil,
+// so one mbarrier suffices; its phase count hph runs for the whole launch.
+__shared__ __align__(8) unsigned long long g_halo_mbar;
+
+// Bounded wait for the given phase parity of a CTA-local mbarrier; a wait that
+// gives up marks the CTA late (later waits give up at once) and bumps the fault count.
+__device__ __forceinline__ void halo_wait(uint32_t mb, uint32_t parity) {
+    uint32_t done = 0;
+    const int limit = g_rc_late ? 1 : (1 << 16);
+    for (int it = 0; it < limit && !done; ++it)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mb), "r"(parity)
+            : "memory");
+    if (!done) {
+        g_rc_late = 1;
+        if (threadIdx.x == 0) atomicAdd(g_rc.fault, 1);
+    }
+}
+
+__device__ __forceinline__ void push4(uint32_t dst, float4 v, uint32_t mbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(dst),
+                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(mbar)
+                 : "memory");
+}
+
+// This thread's arrival on the CTA's halo mbarrier (thread 0 also announces
+// the neighbours' bytes of the phase).
+__device__ __forceinline__ void halo_arrive(uint32_t mb, int halo_bytes) {
+    if (threadIdx.x == 0)
+        asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(halo_bytes)
+                     : "memory");
+    else
+        asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
+}
+
+template <int NT, int C, int Q, int SY, bool ISO>
+__device__ __noinline__ RunSeg quad_halo_segment(float* pc, const int* spt, const int* skt, int planes, uint32_t nbl,
+                                                 uint32_t nbr, uint32_t mbl, uint32_t mbr, int halo_bytes,
+                                                 int syz_rt, int sp2_rt, double scale, float carry, StencilArgs sa,
+                                                 int iters, int flip32, int cflip32, int hph) {
+    constexpr int PZ = (SY + 3) & ~3;
+    const int Syz = SY > 0 ? PZ : syz_rt;
+    const int Sp2 = SY > 0 ? SY * PZ : sp2_rt;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const uint32_t hmb = smem_u32(&g_halo_mbar);
+    float4 r[Q], ap[Q], d[Q];
+    // p of quad j written: locally, and to the neighbours' halos for the first / last 3 planes
+    auto put_p = [&](int pk, float4 v) {
+        const int off = pk & 0xfffff, xl = (int)((unsigned)pk >> 24);
+        st4(pc + off, v);
+        if ((pk >> 20) & 15) {
+            if (rank > 0 && xl < 3) push4(nbl + 4u * (uint32_t)off, v, mbl);
+            if (rank < C - 1 && xl >= planes - 3) push4(nbr + 4u * (uint32_t)off, v, mbr);
+        }
+    };
+    float a32 = 0.0f;
+    {
+        const double inv = 1.0 / scale;
+        const double* r64 = g_rc.r64;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const int pk = spt[j * NT];
+            const int off = pk & 0xfffff, m = (pk >> 20) & 15;
+            const int k = skt[j * NT];
+            float4 rv;
+            rv.x = (m & 1) ? (float)(r64[k] * inv) : 0.0f;
+            rv.y = (m & 2) ? (float)(r64[k + 1] * inv) : 0.0f;
+            rv.z = (m & 4) ? (float)(r64[k + 2] * inv) : 0.0f;
+            rv.w = (m & 8) ? (float)(r64[k + 3] * inv) : 0.0f;
+            r[j] = rv;
+            d[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float4 pv = rv;
+            if (carry >= 0.0f) {
+                const float4 po = ld4(pc + off);
+                pv.x = fmaf(carry, po.x, rv.x);
+                pv.y = fmaf(carry, po.y, rv.y);
+                pv.z = fmaf(carry, po.z, rv.z);
+                pv.w = fmaf(carry, po.w, rv.w);
+            }
+            put_p(pk, pv);
+            a32 = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, fmaf(rv.w, rv.w, a32))));
+        }
+    }
+    halo_arrive(hmb, halo_bytes);
+    float rr = cluster_sum_mb<NT, C>(a32, flip32, cflip32, rank);
+    const float lim = g_rc.drop2 * rr;
+    const float conv_thr = (float)(0.25 * g_rc.target2 / (scale * scale));
+    halo_wait(hmb, (uint32_t)hph & 1u);
+    ++hph;
+    RunSeg out;
+    float al = 0.0f;
+    for (;;) {
+        if (iters >= g_rc.max_iter) {
+            out.maxed = 1;
+            break;
+        }
+        float pa = 0.0f;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const int pk = spt[j * NT];
+            const int m = (pk >> 20) & 15;
+            const float* b = pc + (pk & 0xfffff);
+            const float4 c = ld4(b), zl = ld4(b - 4), zh = ld4(b + 4);
+            const float w[10] = {zl.y, zl.z, zl.w, c.x, c.y, c.z, c.w, zh.x, zh.y, zh.z};
+            float a[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                a[i] = fmaf(sa.cz[0], w[i + 4] + w[i + 2],
+                            fmaf(sa.cz[1], w[i + 5] + w[i + 1], fmaf(sa.cz[2], w[i + 6] + w[i], sa.c0 * w[i + 3])));
+#pragma unroll
+            for (int q = 1; q <= 3; ++q) {
+                const float cyq = ISO ? sa.cz[q - 1] : sa.cy[q - 1];
+                const float4 ym = ld4(b - q * Syz), yp = ld4(b + q * Syz);
+                a[0] = fmaf(cyq, ym.x + yp.x, a[0]);
+                a[1] = fmaf(cyq, ym.y + yp.y, a[1]);
+                a[2] = fmaf(cyq, ym.z + yp.z, a[2]);
+                a[3] = fmaf(cyq, ym.w + yp.w, a[3]);
+            }
+#pragma unroll
+            for (int q = 1; q <= 3; ++q) {
+                const float cxq = ISO ? sa.cz[q - 1] : sa.cx[q - 1];
+                const float4 xm = ld4(b - q * Sp2), xp = ld4(b + q * Sp2);
+                a[0] = fmaf(cxq, xm.x + xp.x, a[0]);
+                a[1] = fmaf(cxq, xm.y + xp.y, a[1]);
+                a[2] = fmaf(cxq, xm.z + xp.z, a[2]);
+                a[3] = fmaf(cxq, xm.w + xp.w, a[3]);
+            }
+            float4 av;
+            av.x = (m & 1) ? -a[0] : 0.0f;
+            av.y = (m & 2) ? -a[1] : 0.0f;
+            av.z = (m & 4) ? -a[2] : 0.0f;
+            av.w = (m & 8) ? -a[3] : 0.0f;
+            ap[j] = av;
+            pa = fmaf(c.x, av.x, fmaf(c.y, av.y, fmaf(c.z, av.z, fmaf(c.w, av.w, pa))));
+        }
+        const float pap = cluster_sum_mb<NT, C>(pa, flip32, cflip32, rank);
+        al = rr / pap;
+        float ra = 0.0f;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            r[j].x = fmaf(-al, ap[j].x, r[j].x);
+            r[j].y = fmaf(-al, ap[j].y, r[j].y);
+            r[j].z = fmaf(-al, ap[j].z, r[j].z);
+            r[j].w = fmaf(-al, ap[j].w, r[j].w);
+            ra = fmaf(r[j].x, r[j].x, fmaf(r[j].y, r[j].y, fmaf(r[j].z, r[j].z, fmaf(r[j].w, r[j].w, ra))));
+        }
+        const float rrn = cluster_sum_mb<NT, C>(ra, flip32, cflip32, rank);
+        ++iters;
+        if (rrn <= lim || rrn <= conv_thr || !(rrn == rrn)) {
+            out.maxed = 0;
+            break;
+        }
+        const float be = rrn / rr;
+        rr = rrn;
+        // d += alpha p and p = r + beta p, then publish p
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const int pk = spt[j * NT];
+            const float4 po = ld4(pc + (pk & 0xfffff));
+            d[j].x = fmaf(al, po.x, d[j].x);
+            d[j].y = fmaf(al, po.y, d[j].y);
+            d[j].z = fmaf(al, po.z, d[j].z);
+            d[j].w = fmaf(al, po.w, d[j].w);
+            put_p(pk, make_float4(fmaf(be, po.x, r[j].x), fmaf(be, po.y, r[j].y), fmaf(be, po.z, r[j].z),
+                                  fmaf(be, po.w, r[j].w)));
+        }
+        al = 0.0f;
+        halo_arrive(hmb, halo_bytes);
+        halo_wait(hmb, (uint32_t)hph & 1u);
+        ++hph;
+    }
+    // the last iteration's d += alpha p (p is unchanged since its stencil), then v += scale d
+    const int* cube = g_rc.cube;
+    double* vc = g_rc.vc;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int pk = spt[j * NT];
+        const int m = (pk >> 20) & 15;
+        const float4 po = ld4(pc + (pk & 0xfffff));
+        const float dv[4] = {fmaf(al, po.x, d[j].x), fmaf(al, po.y, d[j].y), fmaf(al, po.z, d[j].z),
+                             fmaf(al, po.w, d[j].w)};
+        const int k = skt[j * NT];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (m & (1 << i)) {
+                const int cc = cube[k + i];
+                vc[cc] = fma(scale, (double)dv[i], vc[cc]);
+            }
+        }
+    }
+    out.iters = iters;
+    out.rr = rr;
+    out.flip32 = flip32;
+    out.cflip32 = cflip32;
+    out.hphase = hph;
+    return out;
+}
+
 // MODE 0: thread slot j of a thread holds one point of the slab (the
 // [PTS][NT] point map); x legs that leave the slab read the neighbour's slab.
 // MODE 1: the thread owns one run of at most PTS consecutive points of a
@@ -645,7 +858,8 @@ __device__ __noinline__ RunSeg quad_segment(float* ps, const float* pm, const fl
 template <int NT, int C, int PTS, int MODE, int SYZ, bool ISO>
 __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_constant__ SolveParams P,
                                                              const __grid_constant__ ClusterLayout CL) {
-    constexpr bool RUNS = MODE == 1, HALO = MODE == 1, QUADS = MODE == 2;
+    constexpr bool RUNS = MODE == 1, HALO = MODE == 1 || MODE == 3, QUADS = MODE == 2 || MODE == 3;
+    constexpr bool QHALO = MODE == 3;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     extern __shared__ __align__(16) double smem[];
@@ -656,7 +870,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
     int flip = 0, cflip = 0;
     // FP32 reduction state, kept for the whole launch: the quad segments' mbarrier
     // phases advance with every sum (cluster_sum_mb), across segments and pairs
-    int f32 = 0, cf32 = 0;
+    int f32 = 0, cf32 = 0, hph = 0;
 
     const int Rc = P.Rc;
     // FP64 power tables (global, read-only) and this CTA's plane sums (global slot)
@@ -667,7 +881,9 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
     float* ps = reinterpret_cast<float*>(smem);
     const int slab_floats = (CL.cap_planes + (HALO ? 6 : 0)) * CL.Sp2;
     float* ds = ps + ((slab_floats + 3) & ~3);  // 16-byte aligned
-    int* spk = RUNS ? nullptr : reinterpret_cast<int*>(ds + (QUADS ? 4 : 1) * PTS * NT);
+    // MODE 3 keeps d in registers: ds only holds the shell phase's buffers
+    constexpr int ds_floats = QHALO ? (((NT / 32) * (kNU + kNU / 2) * 2 + 3) & ~3) : (QUADS ? 4 : 1) * PTS * NT;
+    int* spk = RUNS ? nullptr : reinterpret_cast<int*>(ds + ds_floats);
     // the shell phase's per-warp coefficient buffers reuse ds (idle outside the CG)
     double* ub = reinterpret_cast<double*>(ds) + (threadIdx.x >> 5) * (kNU + kNU / 2);
     const int Syz = CL.Syz;
@@ -704,9 +920,27 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
         if (rlen > 0 && rank < C - 1 && rxl >= pl - 3)
             hp = cl.map_shared_rank(ps, rank + 1) + (3 + rxl - pl) * Sp2 + rest;
     } else {
+        if constexpr (QHALO) pc = ps + 3 * Sp2;
 #pragma unroll
         for (int j = 0; j < PTS; ++j)
             spk[j * NT + threadIdx.x] = CL.slot_pk[(size_t)rank * PTS * NT + j * NT + threadIdx.x];
+    }
+    // MODE 3: where this CTA's boundary quads go in the neighbours' halos
+    // (shared::cluster addresses of the image of pc), their halo mbarriers,
+    // and the bytes the neighbours send this CTA per phase
+    uint32_t nbl = 0, nbr = 0, mbl = 0, mbr = 0;
+    int hbytes = 0;
+    if constexpr (QHALO) {
+        const uint32_t base = smem_u32(ps), hm0 = smem_u32(&g_halo_mbar);
+        if (rank > 0) {
+            nbl = cluster_addr(base, rank - 1) + 4u * (uint32_t)((3 + planes_prev) * Sp2);
+            mbl = cluster_addr(hm0, rank - 1);
+        }
+        if (rank < C - 1) {
+            nbr = cluster_addr(base, rank + 1) + 4u * (uint32_t)((3 - planes) * Sp2);
+            mbr = cluster_addr(hm0, rank + 1);
+        }
+        hbytes = CL.halo_bytes[rank];
     }
 
     const int cid = blockIdx.x / C;
@@ -723,6 +957,8 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
         // the quad segments' reduction barriers (count 1: this CTA's own arrive)
         for (int b = 0; b < 2; ++b)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&g_rc_mbar[b])) : "memory");
+        if (QHALO)  // every thread of the CTA arrives once per phase
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&g_halo_mbar)), "r"(NT) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         g_rc_late = 0;
     }
@@ -819,6 +1055,10 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
                 if constexpr (RUNS)
                     sg = run_segment<NT, C, PTS, SYZ>(pc + roff, ds + threadIdx.x, hm, hp, rk0, rlen, scale, carry,
                                                       sa.c0, sa.cz[0], sa.cz[1], sa.cz[2], iters, f32, cf32);
+                else if constexpr (QHALO)
+                    sg = quad_halo_segment<NT, C, PTS, SYZ, ISO>(pc, spk + threadIdx.x, slot_k + threadIdx.x, planes,
+                                                                 nbl, nbr, mbl, mbr, hbytes, Syz, Sp2, scale, carry,
+                                                                 sa, iters, f32, cf32, hph);
                 else if constexpr (QUADS)
                     sg = quad_segment<NT, C, PTS, SYZ, ISO>(ps, pm, pp, reinterpret_cast<float4*>(ds) + threadIdx.x,
                                                             spk + threadIdx.x, slot_k + threadIdx.x, planes,
@@ -830,6 +1070,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
                 iters = sg.iters;
                 f32 = sg.flip32;
                 cf32 = sg.cflip32;
+                if constexpr (QHALO) hph = sg.hphase;
                 if (sg.maxed) {
                     conv = false;
                     break;
@@ -884,7 +1125,7 @@ size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant);
 // Supported (threads, cluster size, points per thread) instantiations.
 struct ClusterVariant {
     int nt, c, pts;
-    int mode;  // 0 point map, 1 z runs with halo planes, 2 quad map
+    int mode;  // 0 point map, 1 z runs with halo planes, 2 quad map, 3 quad map with halo planes
     int syz;   // modes 0, 1: slab row pitch the variant is specialised for;
                // mode 2: box side 2 R_PE + 7 (0 = any)
     bool iso;  // isotropic stencil only
@@ -928,6 +1169,9 @@ static const ClusterVariant kVariants[] = {
     EXX_CLUSTER_VARIANT(1024, 8, 3, 2, 55, true),
     EXX_CLUSTER_VARIANT(1024, 9, 2, 2, 0, false),  EXX_CLUSTER_VARIANT(1024, 4, 2, 2, 0, false),
     EXX_CLUSTER_VARIANT(512, 2, 4, 2, 0, false),
+    // quad map with halo planes: R_PE = 24 on isotropic grids, and any radius
+    EXX_CLUSTER_VARIANT(512, 9, 4, 3, 55, true),   EXX_CLUSTER_VARIANT(512, 9, 4, 3, 0, false),
+    EXX_CLUSTER_VARIANT(512, 2, 4, 3, 0, false),
 };
 #undef EXX_CLUSTER_VARIANT
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
@@ -996,12 +1240,15 @@ int cluster_variant_pts(int variant) { return kVariants[variant].pts; }
 size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant) {
     (void)Rc;
     const size_t per = (size_t)kVariants[variant].nt * kVariants[variant].pts;
-    const int mode = kVariants[variant].mode;
-    const bool runs = mode == 1, halo = mode == 1;
-    // slab (with 3 halo planes per side for mode 1), d ([PTS][NT] points, or
-    // quads for mode 2), the slot map (point or quad slots)
+    const int mode = kVariants[variant].mode, nt = kVariants[variant].nt;
+    const bool runs = mode == 1, halo = mode == 1 || mode == 3;
+    // slab (with 3 halo planes per side for modes 1 and 3), d ([PTS][NT]
+    // points, or quads for mode 2; mode 3 only the shell buffers), the slot
+    // map (point or quad slots); as laid out by cluster_pair_kernel
     const size_t slab = (size_t)(CL.cap_planes + (halo ? 6 : 0)) * CL.Sp2;
-    return sizeof(float) * (((slab + 3) & ~(size_t)3) + (mode == 2 ? 4 : 1) * per) + (runs ? 0 : sizeof(int) * per);
+    const size_t dsf = mode == 3 ? (((size_t)(nt / 32) * (kNU + kNU / 2) * 2 + 3) & ~(size_t)3)
+                                 : (mode == 2 ? 4 : 1) * per;
+    return sizeof(float) * (((slab + 3) & ~(size_t)3) + dsf) + (runs ? 0 : sizeof(int) * per);
 }
 
 }  // namespace exx

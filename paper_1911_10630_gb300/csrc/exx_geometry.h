@@ -57,5 +57,9 @@ int build_run_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int 
 // Q x NT quads or the slab offsets do not fit 20 bits.
 int build_quad_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int NT, int Q, std::vector<int>& quad_pk,
                     std::vector<int>& quad_k);
+// Halo traffic of the quad map with halo planes: bytes[r] = 16 x the quads
+// with valid elements that rank r's neighbours push into its halos per phase
+// (rank r - 1's last 3 planes, rank r + 1's first 3). per = slots per rank.
+void quad_halo_bytes(const ClusterLayout& L, const std::vector<int>& quad_pk, int per, std::vector<int>& bytes);
 
 }  // namespace exx
