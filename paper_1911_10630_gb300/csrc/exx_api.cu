@@ -405,7 +405,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     const HostBall& B = c->hb;
     {
         std::vector<size_t> o_cube(c->n_geo), o_off(c->n_geo), o_rpe(c->n_geo), o_rme(c->n_geo), o_pl(c->n_geo),
-            o_ro(c->n_geo);
+            o_ro(c->n_geo), o_sn(c->n_geo), o_sf(c->n_geo);
         size_t at = 0;
         for (int g = 0; g < c->n_geo; ++g) {
             const HostBall& Bg = c->balls[g];
@@ -415,6 +415,8 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             o_rme[g] = at; at = align256(at + sizeof(RowRec) * Bg.rows_me.size());
             o_pl[g] = at; at = align256(at + sizeof(int) * Bg.plane_pe.size());
             o_ro[g] = at; at = align256(at + sizeof(int) * Bg.row_of.size());
+            o_sn[g] = at; at = align256(at + sizeof(int) * Bg.sh_near.size());
+            o_sf[g] = at; at = align256(at + sizeof(int) * Bg.sh_far.size());
         }
         const size_t o_geo = at;
         const size_t geo_bytes = align256(o_geo + sizeof(BallGeo) * c->n_geo);
@@ -437,12 +439,18 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             G.rows_me = (const RowRec*)(gm + o_rme[g]);
             G.plane_pe = (const int*)(gm + o_pl[g]);
             G.row_of = (const int*)(gm + o_ro[g]);
+            G.sh_near = (const int*)(gm + o_sn[g]);
+            G.sh_far = (const int*)(gm + o_sf[g]);
+            G.n_near = (int)Bg.sh_near.size();
+            G.n_far = (int)Bg.sh_far.size();
             if ((e = cudaMemcpy(gm + o_ro[g], Bg.row_of.data(), sizeof(int) * Bg.row_of.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
                 (e = cudaMemcpy(gm + o_cube[g], Bg.cube.data(), sizeof(int) * Bg.n_me, cudaMemcpyHostToDevice)) != cudaSuccess ||
                 (e = cudaMemcpy(gm + o_off[g], Bg.off.data(), sizeof(int) * Bg.n_me, cudaMemcpyHostToDevice)) != cudaSuccess ||
                 (e = cudaMemcpy(gm + o_rpe[g], Bg.rows_pe.data(), sizeof(RowRec) * Bg.rows_pe.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
                 (e = cudaMemcpy(gm + o_rme[g], Bg.rows_me.data(), sizeof(RowRec) * Bg.rows_me.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-                (e = cudaMemcpy(gm + o_pl[g], Bg.plane_pe.data(), sizeof(int) * Bg.plane_pe.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+                (e = cudaMemcpy(gm + o_pl[g], Bg.plane_pe.data(), sizeof(int) * Bg.plane_pe.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(gm + o_sn[g], Bg.sh_near.data(), sizeof(int) * Bg.sh_near.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(gm + o_sf[g], Bg.sh_far.data(), sizeof(int) * Bg.sh_far.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
                 return bail(cuda_fail(c, e, "cudaMemcpy(geometry)"));
         }
         c->geo_host = gv.back();
@@ -468,6 +476,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     P.off_ap32 = off; off = align256(off + sizeof(float) * B.n_pe);
     P.off_rows = off; off = align256(off + sizeof(double) * 8 * B.rows_pe.size());
     P.off_sy = off; off = align256(off + sizeof(double) * (size_t)kMaxCluster * (((2 * r_pe + 1) * 28 + 1) & ~1));
+    P.off_ush = off; off = align256(off + (sizeof(double) + sizeof(float)) * kNU * B.rows_me.size());
     c->slot_bytes = off;
     // x^e, y^e, z^e (e < 8) for offsets -Rc..Rc, by repeated multiplication
     {

@@ -881,11 +881,9 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
     float* ps = reinterpret_cast<float*>(smem);
     const int slab_floats = (CL.cap_planes + (HALO ? 6 : 0)) * CL.Sp2;
     float* ds = ps + ((slab_floats + 3) & ~3);  // 16-byte aligned
-    // MODE 3 keeps d in registers: ds only holds the shell phase's buffers
-    constexpr int ds_floats = QHALO ? (((NT / 32) * (kNU + kNU / 2) * 2 + 3) & ~3) : (QUADS ? 4 : 1) * PTS * NT;
+    // MODE 3 keeps d in registers (no ds)
+    constexpr int ds_floats = QHALO ? 0 : (QUADS ? 4 : 1) * PTS * NT;
     int* spk = RUNS ? nullptr : reinterpret_cast<int*>(ds + ds_floats);
-    // the shell phase's per-warp coefficient buffers reuse ds (idle outside the CG)
-    double* ub = reinterpret_cast<double*>(ds) + (threadIdx.x >> 5) * (kNU + kNU / 2);
     const int Syz = CL.Syz;
     const int Sp2 = CL.Sp2;
 
@@ -950,6 +948,9 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
     double* r64 = reinterpret_cast<double*>(slot + P.off_r);
     double* rowS = reinterpret_cast<double*>(slot + P.off_rows);
     double* sY = reinterpret_cast<double*>(slot + P.off_sy) + (size_t)rank * CL.sy_doubles;
+    // the shell's row coefficients U_{l,c}: FP64, then the FP32 copy (shell_rows)
+    double* U64 = reinterpret_cast<double*>(slot + P.off_ush);
+    float* U32 = reinterpret_cast<float*>(U64 + (size_t)kNU * P.geos[P.n_geo - 1].n_rows_me);
 
     const int gt = rank * NT + (int)threadIdx.x, gn = C * NT;
     const int np = *P.n_pair;
@@ -986,7 +987,10 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
         moment_rows(P, G, rho, rowS, zp, gt, gn);
         cl.sync();
         moment_finish<NT>(P, G, rowS, xp, yp, sY, s_M, s_T);
-        shell_potential(P, G, vc, xp, yp, s_T, ub, gt >> 5, gn >> 5);
+        shell_rows(P, G, xp, yp, s_T, U64, U32, gt, gn);
+        cl.sync();
+        shell_points<true>(P, G, vc, U64, U32, G.sh_near, G.n_near, gt, gn);
+        shell_points<false>(P, G, vc, U64, U32, G.sh_far, G.n_far, gt, gn);
         cl.sync();
         const long long t1 = clk ? clock64() : 0;
 
@@ -1240,14 +1244,13 @@ int cluster_variant_pts(int variant) { return kVariants[variant].pts; }
 size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant) {
     (void)Rc;
     const size_t per = (size_t)kVariants[variant].nt * kVariants[variant].pts;
-    const int mode = kVariants[variant].mode, nt = kVariants[variant].nt;
+    const int mode = kVariants[variant].mode;
     const bool runs = mode == 1, halo = mode == 1 || mode == 3;
     // slab (with 3 halo planes per side for modes 1 and 3), d ([PTS][NT]
-    // points, or quads for mode 2; mode 3 only the shell buffers), the slot
+    // points, or quads for mode 2; none for mode 3), the slot
     // map (point or quad slots); as laid out by cluster_pair_kernel
     const size_t slab = (size_t)(CL.cap_planes + (halo ? 6 : 0)) * CL.Sp2;
-    const size_t dsf = mode == 3 ? (((size_t)(nt / 32) * (kNU + kNU / 2) * 2 + 3) & ~(size_t)3)
-                                 : (mode == 2 ? 4 : 1) * per;
+    const size_t dsf = mode == 3 ? 0 : (mode == 2 ? 4 : 1) * per;
     return sizeof(float) * (((slab + 3) & ~(size_t)3) + dsf) + (runs ? 0 : sizeof(int) * per);
 }
 

@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 namespace exx {
@@ -111,6 +112,8 @@ void build_ball(HostBall& B, int r_pe, int r_me, int Rc) {
     B.rows_pe.clear();
     B.rows_me.clear();
     B.row_of.clear();
+    B.sh_near.clear();
+    B.sh_far.clear();
     B.plane_pe.assign(2 * r_pe + 2, 0);
     auto cube = [&](int x, int y, int z) { return ((x + Rc) * S + (y + Rc)) * S + (z + Rc); };
     // PE ball, lexicographic (Algorithm 2, first list)
@@ -163,11 +166,13 @@ void build_ball(HostBall& B, int r_pe, int r_me, int Rc) {
                 }
             }
             R.zn = zn;
+            const int row = (int)B.rows_me.size();
             B.rows_me.push_back(R);
             for (int z = -R.zme; z <= R.zme; ++z) {
                 if (z >= -R.zpe && z <= R.zpe) continue;
                 B.cube.push_back(cube(x, y, z));
                 B.off.push_back(pack_off(x, y, z));
+                (std::abs(z) <= zn ? B.sh_near : B.sh_far).push_back((row << 8) | (z + 128));
             }
         }
     B.n_me = (int)B.cube.size();

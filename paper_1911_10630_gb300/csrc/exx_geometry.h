@@ -15,6 +15,8 @@ struct HostBall {
     std::vector<RowRec> rows_me;    // ME rows, lexicographic
     std::vector<int> plane_pe;      // [2 r_pe + 2]
     std::vector<int> row_of;        // [(2 r_pe + 1)^2] PE row of (ox, oy) or -1
+    std::vector<int> sh_near;       // shell points with |z| <= zn of their ME row: row << 8 | (z + 128)
+    std::vector<int> sh_far;        // the other shell points, same packing
 };
 
 void build_multipole_const(MultipoleConst& mc);

@@ -42,6 +42,11 @@ struct BallGeo {
     const RowRec* rows_me;   // [n_rows_me]
     const int* plane_pe;     // [2 r_pe + 2] first PE row of each x plane (last = n_rows_pe)
     const int* row_of;       // [(2 r_pe + 1)^2] PE row index of (ox, oy), -1 outside
+    // shell points split by the precision of their boundary value (|z| <= zn
+    // of the row: FP64, read by the stencil; else FP32), ME row << 8 | (z + 128)
+    const int* sh_near;
+    const int* sh_far;
+    int n_near, n_far;
 };
 
 // 19-point Laplacian coefficients of Eq. d2_1 on an orthorhombic grid:
@@ -85,6 +90,7 @@ struct SolveParams {
     size_t off_p32, off_r32, off_d32, off_ap32;                  // FP32 parts
     size_t off_rows;                                             // [n_rows_pe][8] row sums
     size_t off_sy;                                               // [C][(2 r_pe + 1) * 28] plane sums (cluster)
+    size_t off_ush;                                              // [28][n_rows_me] FP64 then FP32 row coefficients U_{l,c} (cluster)
     const double* pow_tab;  // [3][2 Rc + 1][8] x^e, y^e, z^e (cluster kernel; global, read-only)
 
     // solver

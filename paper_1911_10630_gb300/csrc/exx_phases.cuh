@@ -195,6 +195,83 @@ static __device__ __noinline__ void shell_potential(const SolveParams& P, const 
     }
 }
 
+// Eq. me on the shell, in two dense stages for the cluster kernel (the
+// per-row form above leaves most lanes of its FP64 instructions idle, and
+// GB300 issues FP64 at 1/64 of the FP32 rate). Stage 1: the coefficients
+// U_{l,c}(x, y) of every ME row, one item per (u, row), u-major so that the
+// lanes of a warp share u and its terms; FP64 into U64[u][row] with an FP32
+// copy in U32[u][row].
+static __device__ __noinline__ void shell_rows(const SolveParams& P, const BallGeo& G, const double* __restrict__ xp,
+                                               const double* __restrict__ yp, const double* __restrict__ s_T,
+                                               double* __restrict__ U64, float* __restrict__ U32, int tid, int nthr) {
+    const int Rc = P.Rc;
+    const int nr = G.n_rows_me;
+    const RowRec* __restrict__ rows = G.rows_me;
+    for (int it = tid; it < kNU * nr; it += nthr) {
+        const int u = it / nr, row = it - u * nr;
+        const RowRec R = rows[row];
+        const double* xa = xp + (R.ox + Rc) * 8;
+        const double* yb = yp + (R.oy + Rc) * 8;
+        double acc = 0.0;
+        for (int t = 0; t < c_mp.uterm_n[u]; ++t)
+            acc = fma(s_T[c_mp.uterm[u][t][0]], xa[c_mp.uterm[u][t][1]] * yb[c_mp.uterm[u][t][2]], acc);
+        U64[it] = acc;
+        U32[it] = (float)acc;
+    }
+}
+
+// Stage 2: v = sum_l P_l(z) / r^(2l+1) at the listed shell points (ME row << 8
+// | (z + 128)), one point per thread: FP64 for the boundary layer the stencil
+// reads (sh_near), FP32 with the FP32 copy of U for the rest (sh_far).
+template <bool F64>
+static __device__ __noinline__ void shell_points(const SolveParams& P, const BallGeo& G, double* __restrict__ vc,
+                                                 const double* __restrict__ U64, const float* __restrict__ U32,
+                                                 const int* __restrict__ list, int n, int tid, int nthr) {
+    const int Rc = P.Rc;
+    const int nr = G.n_rows_me;
+    const double dx = P.delta[0], dy = P.delta[1], dz = P.delta[2];
+    const long long S2 = P.S2, S = P.S;
+    const RowRec* __restrict__ rows = G.rows_me;
+    for (int q = tid; q < n; q += nthr) {
+        const int pk = list[q];
+        const int row = pk >> 8, z = (pk & 255) - 128;
+        const RowRec R = rows[row];
+        const long long base = (long long)(R.ox + Rc) * S2 + (long long)(R.oy + Rc) * S + Rc;
+        const double x = R.ox * dx, y = R.oy * dy;
+        if constexpr (F64) {
+            const double zz = z * dz;
+            const double r2 = fma(zz, zz, x * x + y * y);
+            const double ir = rsqrt(r2);
+            const double ir2 = ir * ir;
+            double acc = 0.0;
+#pragma unroll
+            for (int l = kLmaxMax; l >= 0; --l) {
+                const double* Ul = U64 + (size_t)(l * (l + 1) / 2) * nr + row;
+                double pl = Ul[(size_t)l * nr];
+#pragma unroll
+                for (int c = l - 1; c >= 0; --c) pl = fma(pl, zz, Ul[(size_t)c * nr]);
+                acc = fma(acc, ir2, pl);
+            }
+            vc[base + z] = acc * ir;
+        } else {
+            const float zz = (float)z * (float)dz;
+            const float r2 = fmaf(zz, zz, (float)(x * x + y * y));
+            const float ir = rsqrtf(r2);
+            const float ir2 = ir * ir;
+            float acc = 0.0f;
+#pragma unroll
+            for (int l = kLmaxMax; l >= 0; --l) {
+                const float* Ul = U32 + (size_t)(l * (l + 1) / 2) * nr + row;
+                float pl = Ul[(size_t)l * nr];
+#pragma unroll
+                for (int c = l - 1; c >= 0; --c) pl = fmaf(pl, zz, Ul[(size_t)c * nr]);
+                acc = fmaf(acc, ir2, pl);
+            }
+            vc[base + z] = (double)(acc * ir);
+        }
+    }
+}
+
 // Step V scatter: D^i += v phi_j, D^j += v phi_i on the ME ball.
 static __device__ __noinline__ void scatter_dxx(const SolveParams& P, const BallGeo& G, const PairRec& pr,
                                                 const double* __restrict__ vc, int tid, int nthr) {
