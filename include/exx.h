@@ -107,8 +107,10 @@ typedef struct {
                           16-byte load; x legs past the slab read from the
                           neighbour), 4 = quads with 3 halo planes per side
                           that the neighbours fill by asynchronous remote
-                          stores (all stencil loads local); 3 and 4 are tried
-                          by the autotuner.                                    */
+                          stores (all stencil loads local), 5 = as 4 with the
+                          quads dealt so that the 8 lanes of each phase of a
+                          16-byte shared-memory access hit distinct banks;
+                          3, 4 and 5 are tried by the autotuner.               */
     int autotune;      /* cluster solver: 1 = on the first exx_compute of a context
                           time every fitting launch shape (cluster size, threads
                           per CTA, lane map) on a prefix of the pair queue and

@@ -579,7 +579,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             // quads of 4 consecutive z positions per thread slot, on a layout
             // whose rows are padded to 16 bytes: x legs read from the
             // neighbours (lane map 3) or from halo planes (lane map 4)
-            if (o.autotune || o.lane_map == 3 || o.lane_map == 4) {
+            if (o.autotune || (o.lane_map >= 3 && o.lane_map <= 5)) {
                 ClusterLayout Lq;
                 std::vector<int> ptq;
                 if (build_cluster_layout(B, C, Lq, ptq, true)) {
@@ -592,14 +592,17 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                         if (cluster_variant_iso(v) && !isotropic) continue;
                         const int nt = cluster_variant_threads(v);
                         if (o.threads && o.threads != nt) continue;
-                        const int lm = mode == 2 ? 3 : 4;
-                        if (!o.autotune && o.lane_map != lm) continue;
                         if (std::find(have.begin(), have.end(), mode * 4096 + nt) != have.end()) continue;
-                        std::vector<int> spk, sk, hb;
-                        if (build_quad_maps(Lq, ptq, nt, cluster_variant_pts(v), spk, sk) < 0) continue;
-                        if (mode == 3) quad_halo_bytes(Lq, spk, nt * cluster_variant_pts(v), hb);
-                        const exx_status sa = add_cand(v, lm, spk, sk, Lq, mode == 3 ? &hb : nullptr);
-                        if (sa != EXX_OK) return bail(sa);
+                        // lane map 3: mode 2; 4: mode 3; 5: mode 3 with bank-aware dealing
+                        for (int ba = 0; ba <= (mode == 3 ? 1 : 0); ++ba) {
+                            const int lm = mode == 2 ? 3 : 4 + ba;
+                            if (!o.autotune && o.lane_map != lm) continue;
+                            std::vector<int> spk, sk, hb;
+                            if (build_quad_maps(Lq, ptq, nt, cluster_variant_pts(v), spk, sk, ba) < 0) continue;
+                            if (mode == 3) quad_halo_bytes(Lq, spk, nt * cluster_variant_pts(v), hb);
+                            const exx_status sa = add_cand(v, lm, spk, sk, Lq, mode == 3 ? &hb : nullptr);
+                            if (sa != EXX_OK) return bail(sa);
+                        }
                         have.push_back(mode * 4096 + nt);
                     }
                 }

@@ -389,17 +389,26 @@ int build_run_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int 
 
 
 int build_quad_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int NT, int Q, std::vector<int>& quad_pk,
-                    std::vector<int>& quad_k) {
+                    std::vector<int>& quad_k, int bank_aware) {
     const int per = NT * Q;
     // idle slots: the quad at row 3, z 0..3 of plane 0 (outside the ball in
     // every plane, so it stays zero), with no valid element
     const int idle = 3 * L.Syz;
     quad_pk.assign((size_t)L.C * per, idle);
     quad_k.assign((size_t)L.C * per, 0);
-    if ((L.Syz & 3) || (long)L.cap_planes * L.Sp2 >= (1L << 20)) return -1;
+    if ((L.Syz & 3) || (long)L.cap_planes * L.Sp2 >= (1L << 20) || (bank_aware && (per & 7))) return -1;
+    // bank-aware idle quads: one per bank group (offset / 4) mod 8 from rows
+    // 0..2 of plane 0, which lie outside the ball in every plane
+    int idle_of[8];
+    for (int c = 0; c < 8; ++c) idle_of[c] = -1;
+    for (int row = 0; row < 3; ++row)
+        for (int q = 0; 4 * q + 3 < L.Syz; ++q) {
+            const int off = row * L.Syz + 4 * q;
+            if (idle_of[(off >> 2) & 7] < 0) idle_of[(off >> 2) & 7] = off;
+        }
     int max_quads = 0;
     for (int r = 0; r < L.C; ++r) {
-        int s = 0;
+        std::vector<int> qpk, qk;  // the rank's quads, row by row
         int k = L.k0[r];
         while (k < L.k1[r]) {
             // one row of the slab: consecutive offsets within one plane
@@ -410,17 +419,42 @@ int build_quad_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int
             const int off0 = pt_slab[k] & 0xffffff, xl = pt_slab[k] >> 24;
             const int z0 = off0 % L.Syz, z1 = z0 + (e - k) - 1;  // z positions of the row's ends in the box
             for (int qz = z0 & ~3; qz <= z1; qz += 4) {
-                if (s >= per) return -1;
                 int mask = 0;
                 for (int i = 0; i < 4; ++i)
                     if (qz + i >= z0 && qz + i <= z1) mask |= 1 << i;
-                quad_pk[(size_t)r * per + s] = (off0 - z0 + qz) | (mask << 20) | (xl << 24);
-                quad_k[(size_t)r * per + s] = k + (qz - z0);
-                ++s;
+                qpk.push_back((off0 - z0 + qz) | (mask << 20) | (xl << 24));
+                qk.push_back(k + (qz - z0));
             }
             k = e;
         }
-        max_quads = std::max(max_quads, s);
+        const int nq = (int)qpk.size();
+        int* dpk = quad_pk.data() + (size_t)r * per;
+        int* dk = quad_k.data() + (size_t)r * per;
+        if (!bank_aware) {
+            if (nq > per) return -1;
+            for (int s = 0; s < nq; ++s) {
+                dpk[s] = qpk[s];
+                dk[s] = qk[s];
+            }
+        } else {
+            // every 8 consecutive slots (the lanes of one phase of a 16-byte
+            // shared-memory access) take quads of 8 distinct bank groups, so
+            // every stencil leg, shifted alike for all lanes, is conflict-free
+            for (int c = 0; c < 8; ++c)
+                if (idle_of[c] < 0) return -1;
+            std::vector<std::vector<int>> bucket(8);
+            for (int q = 0; q < nq; ++q) bucket[((qpk[q] & 0xfffff) >> 2) & 7].push_back(q);
+            size_t groups = 0;
+            for (int c = 0; c < 8; ++c) groups = std::max(groups, bucket[c].size());
+            if ((long)groups * 8 > per) return -1;
+            for (int s = 0; s < per; ++s) dpk[s] = idle_of[s & 7];
+            for (int c = 0; c < 8; ++c)
+                for (size_t g = 0; g < bucket[c].size(); ++g) {
+                    dpk[8 * g + c] = qpk[bucket[c][g]];
+                    dk[8 * g + c] = qk[bucket[c][g]];
+                }
+        }
+        max_quads = std::max(max_quads, nq);
     }
     return max_quads;
 }

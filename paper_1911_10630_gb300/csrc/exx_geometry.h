@@ -55,10 +55,14 @@ int build_run_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int 
 // | valid-element mask << 20 | plane << 24; quad_k = compact PE index of the
 // quad's element 0 (element i is k + i when mask bit i is set). Idle slots
 // point at a quad that lies outside the ball in every plane, with mask 0.
-// Returns the largest quad count of a rank, or -1 if a rank has more than
-// Q x NT quads or the slab offsets do not fit 20 bits.
+// bank_aware (only for the layout with halo planes, whose idle quads sit in
+// rows 0..2 of plane 0) deals the quads so that every 8 consecutive slots hold
+// quads of 8 distinct bank groups ((offset / 4) mod 8), which makes every
+// 16-byte stencil load conflict-free. Returns the largest quad count of a
+// rank, or -1 if the quads do not fit Q x NT slots or the slab offsets do not
+// fit 20 bits.
 int build_quad_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int NT, int Q, std::vector<int>& quad_pk,
-                    std::vector<int>& quad_k);
+                    std::vector<int>& quad_k, int bank_aware = 0);
 // Halo traffic of the quad map with halo planes: bytes[r] = 16 x the quads
 // with valid elements that rank r's neighbours push into its halos per phase
 // (rank r - 1's last 3 planes, rank r + 1's first 3). per = slots per rank.

@@ -41,7 +41,7 @@ def _pairs_equal(gpu_pairs, ref_pairs):
 
 @pytest.mark.parametrize("precision,solver_kind,cluster_size,lane_map", [
     (0, 1, 0, None), (1, 1, 0, None), (1, 2, 9, None), (1, 2, 8, None), (1, 2, 4, None), (1, 2, 2, None),
-    (1, 2, 8, 0), (1, 2, 4, 2), (1, 2, 9, 3), (1, 2, 4, 3), (1, 2, 9, 4)])
+    (1, 2, 8, 0), (1, 2, 4, 2), (1, 2, 9, 3), (1, 2, 4, 3), (1, 2, 9, 4), (1, 2, 9, 5)])
 def test_cfg0_end_to_end(torch, cfg0, precision, solver_kind, cluster_size, lane_map):
     w, phi, ref = cfg0
     extra = {} if lane_map is None else dict(lane_map=lane_map, autotune=0)
@@ -115,7 +115,7 @@ def test_operator_matches_oracle(torch):
     assert np.max(np.abs(dap.cpu().numpy() - ref)) <= 1e-13 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("precision,solver_kind,lane_map", [(0, 1, None), (1, 1, None), (1, 2, None), (1, 2, 3), (1, 2, 4)])
+@pytest.mark.parametrize("precision,solver_kind,lane_map", [(0, 1, None), (1, 1, None), (1, 2, None), (1, 2, 3), (1, 2, 4), (1, 2, 5)])
 def test_small_anisotropic_ragged(torch, precision, solver_kind, lane_map):
     # non-cubic grid and cell, small balls, finite R_pair, pairs across faces
     w = synth.tiny(seed=3, n=6, npts=28, length=6.5, r_pe=5, r_me=9, r_pair=3.0, tol=1e-10)
@@ -188,7 +188,7 @@ def test_iteration_cap_reports_nonconvergence(torch, cfg0):
     assert np.isfinite(out["E_xx"])
 
 
-@pytest.mark.parametrize("precision,lane_map", [(1, None), (1, 2), (1, 3), (1, 4), (0, None)])
+@pytest.mark.parametrize("precision,lane_map", [(1, None), (1, 2), (1, 3), (1, 4), (1, 5), (0, None)])
 def test_water64_full_size_sampled(torch, precision, lane_map):
     """The bench workload (water-64 scale, 120^3, 256 orbitals, R_pair = 10 bohr,
     R_PE/R_ME = 24/32, tol 1e-8) in the launch configuration bench.py times
