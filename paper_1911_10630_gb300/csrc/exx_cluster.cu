@@ -238,6 +238,70 @@ __device__ __forceinline__ float cluster_sum_mb(float v, int& flip, int& n, int 
     return s;
 }
 
+// Four sums at once, as cluster_sum_mb (same mbarriers and phase count, one
+// 16-byte st.async per CTA pair).
+__shared__ __align__(16) float4 g_rc_red4[2][32];
+__shared__ __align__(16) float4 g_rc_mpart4[2][16];
+
+__device__ __forceinline__ float4 warp_sum4(float4 v) {
+    v.x = warp_sum(v.x);
+    v.y = warp_sum(v.y);
+    v.z = warp_sum(v.z);
+    v.w = warp_sum(v.w);
+    return v;
+}
+
+template <int NT, int C>
+__device__ __forceinline__ float4 cluster_sum4_mb(float4 v, int& flip, int& n, int rank) {
+    v = warp_sum4(v);
+    float4* buf = g_rc_red4[flip];
+    flip ^= 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) buf[w] = v;
+    __syncthreads();
+    const int b = n & 1;
+    const uint32_t parity = (uint32_t)(n >> 1) & 1u;
+    ++n;
+    const uint32_t mb = smem_u32(&g_rc_mbar[b]);
+    if (w == 0) {
+        float4 t = lane < NT / 32 ? buf[lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        t = warp_sum4(t);
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(C * 16) : "memory");
+        if (lane < C) {
+            const uint32_t dst = cluster_addr(smem_u32(&g_rc_mpart4[b][rank]), lane);
+            const uint32_t rmb = cluster_addr(mb, lane);
+            asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(dst),
+                         "f"(t.x), "f"(t.y), "f"(t.z), "f"(t.w), "r"(rmb)
+                         : "memory");
+        }
+    }
+    uint32_t done = 0;
+    const int limit = g_rc_late ? 1 : (1 << 16);
+    for (int it = 0; it < limit && !done; ++it)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mb), "r"(parity)
+            : "memory");
+    if (!done) {
+        g_rc_late = 1;
+        if (threadIdx.x == 0) atomicAdd(g_rc.fault, 1);
+    }
+    float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+        const float4 q = g_rc_mpart4[b][r];
+        s.x += q.x;
+        s.y += q.y;
+        s.z += q.z;
+        s.w += q.w;
+    }
+    return s;
+}
+
 template <int NT, int C, int PTS, int SYZ>
 __device__ __noinline__ RunSeg run_segment(float* pcr, float* dst, float* hm, float* hp, int rk0, int rlen,
                                            double scale, float carry, float c0, float c1, float c2, float c3,
@@ -729,7 +793,7 @@ __device__ __noinline__ RunSeg quad_halo_segment(float* pc, const int* spt, cons
         }
     }
     halo_arrive(hmb, halo_bytes);
-    float rr = cluster_sum_mb<NT, C>(a32, flip32, cflip32, rank);
+    float rr = cluster_sum4_mb<NT, C>(make_float4(a32, 0.0f, 0.0f, 0.0f), flip32, cflip32, rank).x;
     const float lim = g_rc.drop2 * rr;
     const float conv_thr = (float)(0.25 * g_rc.target2 / (scale * scale));
     halo_wait(hmb, (uint32_t)hph & 1u);
@@ -741,7 +805,12 @@ __device__ __noinline__ RunSeg quad_halo_segment(float* pc, const int* spt, cons
             out.maxed = 1;
             break;
         }
-        float pa = 0.0f;
+        // p.Ap, r.Ap, Ap.Ap and r.r in one cluster sum: alpha = r.r / p.Ap and
+        // r.r after the update = r.r - 2 alpha r.Ap + alpha^2 Ap.Ap, all four from
+        // this iteration's vectors. (Carrying the predicted r.r into the next
+        // iteration instead of summing it afresh lets its rounding errors add up
+        // while r.r falls, and the solve diverges.)
+        float pa = 0.0f, ra = 0.0f, aa = 0.0f, rq = 0.0f;
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
             const int pk = spt[j * NT];
@@ -779,27 +848,21 @@ __device__ __noinline__ RunSeg quad_halo_segment(float* pc, const int* spt, cons
             av.w = (m & 8) ? -a[3] : 0.0f;
             ap[j] = av;
             pa = fmaf(c.x, av.x, fmaf(c.y, av.y, fmaf(c.z, av.z, fmaf(c.w, av.w, pa))));
+            ra = fmaf(r[j].x, av.x, fmaf(r[j].y, av.y, fmaf(r[j].z, av.z, fmaf(r[j].w, av.w, ra))));
+            aa = fmaf(av.x, av.x, fmaf(av.y, av.y, fmaf(av.z, av.z, fmaf(av.w, av.w, aa))));
+            rq = fmaf(r[j].x, r[j].x, fmaf(r[j].y, r[j].y, fmaf(r[j].z, r[j].z, fmaf(r[j].w, r[j].w, rq))));
         }
-        const float pap = cluster_sum_mb<NT, C>(pa, flip32, cflip32, rank);
-        al = rr / pap;
-        float ra = 0.0f;
-#pragma unroll
-        for (int j = 0; j < Q; ++j) {
-            r[j].x = fmaf(-al, ap[j].x, r[j].x);
-            r[j].y = fmaf(-al, ap[j].y, r[j].y);
-            r[j].z = fmaf(-al, ap[j].z, r[j].z);
-            r[j].w = fmaf(-al, ap[j].w, r[j].w);
-            ra = fmaf(r[j].x, r[j].x, fmaf(r[j].y, r[j].y, fmaf(r[j].z, r[j].z, fmaf(r[j].w, r[j].w, ra))));
-        }
-        const float rrn = cluster_sum_mb<NT, C>(ra, flip32, cflip32, rank);
+        const float4 sums = cluster_sum4_mb<NT, C>(make_float4(pa, ra, aa, rq), flip32, cflip32, rank);
+        rr = sums.w;
+        al = rr / sums.x;
+        const float rrn = fmaf(al, fmaf(al, sums.z, -2.0f * sums.y), rr);
         ++iters;
         if (rrn <= lim || rrn <= conv_thr || !(rrn == rrn)) {
             out.maxed = 0;
             break;
         }
         const float be = rrn / rr;
-        rr = rrn;
-        // d += alpha p and p = r + beta p, then publish p
+        // d += alpha p, r -= alpha Ap and p = r + beta p, then publish p
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
             const int pk = spt[j * NT];
@@ -808,6 +871,10 @@ __device__ __noinline__ RunSeg quad_halo_segment(float* pc, const int* spt, cons
             d[j].y = fmaf(al, po.y, d[j].y);
             d[j].z = fmaf(al, po.z, d[j].z);
             d[j].w = fmaf(al, po.w, d[j].w);
+            r[j].x = fmaf(-al, ap[j].x, r[j].x);
+            r[j].y = fmaf(-al, ap[j].y, r[j].y);
+            r[j].z = fmaf(-al, ap[j].z, r[j].z);
+            r[j].w = fmaf(-al, ap[j].w, r[j].w);
             put_p(pk, make_float4(fmaf(be, po.x, r[j].x), fmaf(be, po.y, r[j].y), fmaf(be, po.z, r[j].z),
                                   fmaf(be, po.w, r[j].w)));
         }
