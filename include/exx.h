@@ -277,6 +277,32 @@ exx_status exx_load_guess_model(exx_ctx *ctx, const void *weights, size_t bytes)
 exx_status exx_pair_list_static(const double *centers, int n, const double cell[3], const int grid[3],
                                 double r_pair, int *pairs, int cap, int *n_pair, void *stream);
 
+/*
+ * The cluster solver's quad thread map (lane maps 4 and 5), built on the host
+ * exactly as exx_init builds it, for tests of the layout; no device work. The
+ * paper has no counterpart (the map is how this library lays the PE ball of
+ * Sec. III.C Step IV out over a thread-block cluster).
+ *   r_pe          PE radius in grid points (1..64)
+ *   cluster_size  CTAs sharing a pair (2..16); slabs of >= 3 whole x planes
+ *   threads       threads per CTA (a multiple of 32, <= 1024)
+ *   quads         quad slots per thread (1..16)
+ *   bank_aware    0: quads in row order; 1: dealt so that every 8
+ *                 consecutive slots hold 8 distinct bank groups
+ *   quad_pk       host [cluster_size][quads][threads] ints: slab offset of
+ *                 the quad (floats from the CTA's plane 0, a multiple of 4)
+ *                 | valid-element mask << 20 | plane << 24
+ *   quad_k        host, same shape: compact PE index of the quad's element 0
+ *                 (Algorithm 2 order; element i is k + i when mask bit i is set)
+ *   cap           entries each of quad_pk and quad_k can hold
+ *   info          host int[4 + 4 * cluster_size]: largest quad count of a CTA,
+ *                 row pitch, plane pitch (floats), largest slab (planes), then per
+ *                 CTA: first plane offset x0, planes, first and end compact index
+ * Returns EXX_EINVAL on bad arguments or when the map does not fit; the
+ * message is read with exx_last_error(NULL).
+ */
+exx_status exx_quad_map(int r_pe, int cluster_size, int threads, int quads, int bank_aware, int *quad_pk,
+                        int *quad_k, size_t cap, int *info);
+
 /* Message of the last error on this context (or of the last failed exx_init
  * when ctx is NULL); owned by the library, valid until the next call. */
 const char *exx_last_error(const exx_ctx *ctx);

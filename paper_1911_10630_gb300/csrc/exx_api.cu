@@ -1211,6 +1211,36 @@ extern "C" exx_status exx_apply_operator(exx_ctx* c, const double* p, double* ap
     return EXX_OK;
 }
 
+extern "C" exx_status exx_quad_map(int r_pe, int cluster_size, int threads, int quads, int bank_aware,
+                                   int* quad_pk, int* quad_k, size_t cap, int* info) {
+    if (r_pe < 1 || r_pe > 64 || cluster_size < 2 || cluster_size > kMaxCluster || threads < 32 || threads > 1024 ||
+        threads % 32 || quads < 1 || quads > 16 || !quad_pk || !quad_k || !info)
+        return fail(nullptr, EXX_EINVAL, "exx_quad_map: bad arguments");
+    const size_t per = (size_t)threads * quads;
+    if (cap < per * cluster_size) return fail(nullptr, EXX_EINVAL, "exx_quad_map: cap too small");
+    HostBall B;
+    build_ball(B, r_pe, r_pe + 3, r_pe + 3);
+    ClusterLayout L;
+    std::vector<int> pt, pk, kk;
+    if (!build_cluster_layout(B, cluster_size, L, pt, true))
+        return fail(nullptr, EXX_EINVAL, "exx_quad_map: no slab layout for these radii and cluster size");
+    const int mq = build_quad_maps(L, pt, threads, quads, pk, kk, bank_aware ? 1 : 0);
+    if (mq < 0) return fail(nullptr, EXX_EINVAL, "exx_quad_map: the quads do not fit the slots");
+    std::memcpy(quad_pk, pk.data(), sizeof(int) * pk.size());
+    std::memcpy(quad_k, kk.data(), sizeof(int) * kk.size());
+    info[0] = mq;
+    info[1] = L.Syz;
+    info[2] = L.Sp2;
+    info[3] = L.cap_planes;
+    for (int r = 0; r < cluster_size; ++r) {
+        info[4 + 4 * r] = L.x0[r];
+        info[5 + 4 * r] = L.planes[r];
+        info[6 + 4 * r] = L.k0[r];
+        info[7 + 4 * r] = L.k1[r];
+    }
+    return EXX_OK;
+}
+
 extern "C" exx_status exx_ball_size(const exx_ctx* c, int* n_pe, int* n_me) {
     if (!c) return fail(nullptr, EXX_EINVAL, "exx_ball_size: ctx is NULL");
     if (n_pe) *n_pe = c->hb.n_pe;

@@ -75,6 +75,8 @@ SIGNATURES = [
     ("exx_debug_pair", ctypes.c_int, [_ctx_p, _vp, ctypes.c_int, _d, _d, _d, _vp]),
     ("exx_apply_operator", ctypes.c_int, [_ctx_p, _vp, _vp, _vp]),
     ("exx_ball_size", ctypes.c_int, [_ctx_p, _i, _i]),
+    ("exx_quad_map", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("exx_load_guess_model", ctypes.c_int, [_ctx_p, _vp, ctypes.c_size_t]),
     ("exx_pair_list_static", ctypes.c_int, [_vp, ctypes.c_int, _d, _i, ctypes.c_double, _vp, ctypes.c_int, _i,
                                             _vp]),
@@ -310,6 +312,20 @@ def unet_conv3d(x, w, bias, mask, y, batch, D, H, W, cin, cout, mode, stream=Non
 
 
 GUESS_MAGIC = 0x47585845
+
+
+def quad_map(r_pe: int, cluster_size: int, threads: int, quads: int, bank_aware: int = 0):
+    """exx_quad_map: the cluster solver's quad thread map built on the host.
+    Returns (quad_pk, quad_k) as int32 arrays [cluster_size][quads][threads]
+    and the info vector (see include/exx.h)."""
+    n = cluster_size * quads * threads
+    pk = np.zeros(n, np.int32)
+    kk = np.zeros(n, np.int32)
+    info = np.zeros(4 + 4 * cluster_size, np.int32)
+    _check(load().exx_quad_map(int(r_pe), int(cluster_size), int(threads), int(quads), int(bank_aware),
+                               pk.ctypes.data, kk.ctypes.data, n, info.ctypes.data))
+    shape = (cluster_size, quads, threads)
+    return pk.reshape(shape), kk.reshape(shape), info
 
 
 def guess_model_blob(S: int, params: np.ndarray) -> bytes:
