@@ -510,6 +510,9 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             if (!build_cluster_layout(B, C, L, pt)) continue;
             int* d_pt = nullptr;
             int4* d_ri = nullptr;
+            int* d_res = nullptr;  // residual order and rim counts of this partition
+            std::vector<int> res_list, res_nrim;
+            build_residual_order(B, L, res_list, res_nrim);
             // one candidate: variant v with thread map (spk, sk) and lane map lm
             auto add_cand = [&](int v, int lm, const std::vector<int>& spk, const std::vector<int>& sk,
                                 const ClusterLayout& LL, const std::vector<int>* hb = nullptr) -> exx_status {
@@ -530,6 +533,13 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                     if (e == cudaSuccess) e = cudaMalloc(&d_ri, sizeof(int4) * C);
                     if (e == cudaSuccess) c->cl_mem.push_back(d_ri);
                     if (e == cudaSuccess) e = cudaMemcpy(d_ri, ri, sizeof(int4) * C, cudaMemcpyHostToDevice);
+                    if (e == cudaSuccess) e = cudaMalloc(&d_res, sizeof(int) * (res_list.size() + res_nrim.size()));
+                    if (e == cudaSuccess) c->cl_mem.push_back(d_res);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpy(d_res, res_list.data(), sizeof(int) * res_list.size(), cudaMemcpyHostToDevice);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpy(d_res + res_list.size(), res_nrim.data(), sizeof(int) * res_nrim.size(),
+                                       cudaMemcpyHostToDevice);
                     if (e != cudaSuccess) return cuda_fail(c, e, "slab tables");
                 }
                 int* d_slot = nullptr;
@@ -555,6 +565,8 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                 K.L.slot_pk = d_slot;
                 K.L.slot_k = d_slot + spk.size();
                 K.L.halo_bytes = nhb ? d_slot + spk.size() + sk.size() : nullptr;
+                K.L.res_list = d_res;
+                K.L.res_nrim = d_res + res_list.size();
                 c->cands.push_back(K);
                 return EXX_OK;
             };

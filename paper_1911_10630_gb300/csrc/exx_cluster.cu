@@ -76,6 +76,77 @@ __device__ __noinline__ double cta_residual(const SolveParams& P, const int* __r
     return acc;
 }
 
+// The first FP64 residual of a pair, while v is zero on the PE ball: the
+// CTA's rim points (list[0 .. nrim)) take the full stencil, the interior ones
+// r = 4 pi rho (lap v = 0 there exactly), each group in dense warps.
+__device__ __noinline__ double cta_residual0(const SolveParams& P, const int* __restrict__ cube,
+                                             const double* __restrict__ rho, const double* __restrict__ vc,
+                                             double* __restrict__ r64, const int* __restrict__ list, int n, int nrim,
+                                             int nt, bool dbg) {
+    const Stencil<double> st = P.st64;
+    const int S = P.S;
+    const long long S2 = P.S2;
+    double* __restrict__ db = P.dbg_b;
+    double acc = 0.0;
+    for (int t = (int)threadIdx.x; t < n; t += nt) {
+        const int k = list[t];
+        const double rk = t < nrim ? fma(kFourPi, rho[k], lap19<double>(vc, cube[k], S, S2, st)) : kFourPi * rho[k];
+        r64[k] = rk;
+        acc = fma(rk, rk, acc);
+        if (dbg) db[k] = rk;
+    }
+    return acc;
+}
+
+// Eq. mepole, stages 2-4 on the cluster: each CTA forms the plane sums of its
+// own slab's planes [pl0, pl0 + npl) into the cluster's shared array sYc
+// [(2 R_PE + 1)][28] (global workspace); after a cluster barrier every CTA
+// forms the moments M (times dV) and T = K M from all planes, as moment_finish.
+template <int NT>
+__device__ void moment_finish_cluster(const SolveParams& P, const BallGeo& G, const double* __restrict__ rowS,
+                                      const double* __restrict__ xp, const double* __restrict__ yp,
+                                      double* __restrict__ sYc, int pl0, int npl, double* __restrict__ s_M,
+                                      double* __restrict__ s_T, cg::cluster_group& cl) {
+    const int L = P.lmax;
+    const int Rc = P.Rc;
+    const int nplane = 2 * G.r_pe + 1;
+    const int nbc = (L + 1) * (L + 2) / 2;
+    for (int item = threadIdx.x; item < npl * nbc; item += NT) {
+        const int pl = pl0 + item / nbc, bc = item % nbc;
+        int dgr = 0;
+        while ((dgr + 1) * (dgr + 2) / 2 <= bc) ++dgr;
+        const int c = bc - dgr * (dgr + 1) / 2, b = dgr - c;
+        double acc = 0.0;
+        for (int row = G.plane_pe[pl]; row < G.plane_pe[pl + 1]; ++row) {
+            const int oy = G.rows_pe[row].oy;
+            acc = fma(yp[(oy + Rc) * 8 + b], rowS[row * 8 + c], acc);
+        }
+        sYc[pl * 28 + bc] = acc;
+    }
+    cl.sync();
+    for (int m = threadIdx.x; m < kNMono; m += NT) {
+        const int a = c_mp.mono[m][0], b = c_mp.mono[m][1], c = c_mp.mono[m][2];
+        double acc = 0.0;
+        if (a + b + c <= L) {
+            const int dgr = b + c, bc = dgr * (dgr + 1) / 2 + c;
+            for (int pl = 0; pl < nplane; ++pl) acc = fma(xp[(pl - G.r_pe + Rc) * 8 + a], sYc[pl * 28 + bc], acc);
+        }
+        s_M[m] = acc * P.dV;
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < kNMono; m += NT) {
+        const int l = c_mp.mono[m][0] + c_mp.mono[m][1] + c_mp.mono[m][2];
+        double acc = 0.0;
+        if (l <= L) {
+            const int nl = (l + 1) * (l + 2) / 2, r0 = c_mp.mono_off[l];
+            const double* Kr = c_mp.K + c_mp.k_off[l] + (m - r0) * nl;
+            for (int t = 0; t < nl; ++t) acc = fma(Kr[t], s_M[r0 + t], acc);
+        }
+        s_T[m] = acc;
+    }
+    __syncthreads();
+}
+
 // v += scale * d on the CTA's points (d in shared memory, [j][NT] slots).
 __device__ __noinline__ void cta_update_v(const int* __restrict__ cube, double* __restrict__ vc,
                                           const float* __restrict__ ds, const int* __restrict__ slot_k, double scale,
@@ -1014,7 +1085,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
     double* rho = reinterpret_cast<double*>(slot + P.off_rho);
     double* r64 = reinterpret_cast<double*>(slot + P.off_r);
     double* rowS = reinterpret_cast<double*>(slot + P.off_rows);
-    double* sY = reinterpret_cast<double*>(slot + P.off_sy) + (size_t)rank * CL.sy_doubles;
+    double* sYc = reinterpret_cast<double*>(slot + P.off_sy);  // plane sums of the whole ball (cluster-shared)
     // the shell's row coefficients U_{l,c}: FP64, then the FP32 copy (shell_rows)
     double* U64 = reinterpret_cast<double*>(slot + P.off_ush);
     float* U32 = reinterpret_cast<float*>(U64 + (size_t)kNU * P.geos[P.n_geo - 1].n_rows_me);
@@ -1053,7 +1124,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
         cl.sync();
         moment_rows(P, G, rho, rowS, zp, gt, gn);
         cl.sync();
-        moment_finish<NT>(P, G, rowS, xp, yp, sY, s_M, s_T);
+        moment_finish_cluster<NT>(P, G, rowS, xp, yp, sYc, me.x + G.r_pe, planes, s_M, s_T, cl);
         shell_rows(P, G, xp, yp, s_T, U64, U32, gt, gn);
         cl.sync();
         shell_points<true>(P, G, vc, U64, U32, G.sh_near, G.n_near, gt, gn);
@@ -1066,7 +1137,8 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
         // dropped by update_drop (or looks converged); the search direction is
         // kept, rescaled to the new residual norm, so the Krylov progress
         // survives each replacement. The stop test is the FP64 residual.
-        double acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, P.dbg_b != nullptr);
+        double acc = cta_residual0(P, cube, rho, vc, r64, CL.res_list + k0, k1 - k0, CL.res_nrim[rank], NT,
+                                   P.dbg_b != nullptr);
         const double bb = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
         const double target2 = P.tol * P.tol * bb;
         if (clk) tr += clock64() - t1;

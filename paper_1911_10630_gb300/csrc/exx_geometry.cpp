@@ -474,4 +474,23 @@ void quad_halo_bytes(const ClusterLayout& L, const std::vector<int>& quad_pk, in
     for (int r = 0; r < L.C; ++r) bytes[r] = 16 * ((r > 0 ? last3[r - 1] : 0) + (r + 1 < L.C ? first3[r + 1] : 0));
 }
 
+
+void build_residual_order(const HostBall& B, const ClusterLayout& L, std::vector<int>& list, std::vector<int>& nrim) {
+    const long in2 = (long)(B.r_pe - 3) * (B.r_pe - 3);
+    list.assign(B.n_pe, 0);
+    nrim.assign(L.C, 0);
+    for (int r = 0; r < L.C; ++r) {
+        int at = L.k0[r];
+        for (int pass = 0; pass < 2; ++pass)
+            for (int k = L.k0[r]; k < L.k1[r]; ++k) {
+                const int p = B.off[k];
+                const long x = (p & 0xff) - 128, y = ((p >> 8) & 0xff) - 128, z = ((p >> 16) & 0xff) - 128;
+                const bool rim = B.r_pe < 3 || x * x + y * y + z * z > in2;
+                if (rim != (pass == 0)) continue;
+                list[at++] = k;
+                if (rim) ++nrim[r];
+            }
+    }
+}
+
 }  // namespace exx

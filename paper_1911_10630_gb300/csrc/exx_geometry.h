@@ -67,5 +67,10 @@ int build_quad_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int
 // with valid elements that rank r's neighbours push into its halos per phase
 // (rank r - 1's last 3 planes, rank r + 1's first 3). per = slots per rank.
 void quad_halo_bytes(const ClusterLayout& L, const std::vector<int>& quad_pk, int per, std::vector<int>& bytes);
+// Order of the first FP64 residual of a pair, when v is still zero on the PE
+// ball: per rank, its points whose stencil reaches the shell (|o| > R_PE - 3,
+// the rim) first, then the interior ones, where lap v = 0 and r = 4 pi rho.
+// list[k0 .. k1) holds rank r's compact indices, nrim[r] its rim count.
+void build_residual_order(const HostBall& B, const ClusterLayout& L, std::vector<int>& list, std::vector<int>& nrim);
 
 }  // namespace exx
