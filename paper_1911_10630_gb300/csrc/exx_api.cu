@@ -477,6 +477,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     P.off_rows = off; off = align256(off + sizeof(double) * 8 * B.rows_pe.size());
     P.off_sy = off; off = align256(off + sizeof(double) * (size_t)kMaxCluster * (((2 * r_pe + 1) * 28 + 1) & ~1));
     P.off_ush = off; off = align256(off + (sizeof(double) + sizeof(float)) * kNU * B.rows_me.size());
+    P.off_vfix = off; off = align256(off + sizeof(long long) * S3);
     c->slot_bytes = off;
     // x^e, y^e, z^e (e < 8) for offsets -Rc..Rc, by repeated multiplication
     {
@@ -708,6 +709,9 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     const double W[4] = {-49.0 / 18.0, 3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0};  // Eq. d2_1
     double inv2[3];
     for (int a = 0; a < 3; ++a) inv2[a] = 1.0 / (c->delta[a] * c->delta[a]);
+    // isotropic grids: 180 delta^2 x the weights are the integers -490, 270, -27, 2
+    P.fixres = (c->delta[0] == c->delta[1] && c->delta[1] == c->delta[2]) ? 1 : 0;
+    P.fix_inv = inv2[0] / 180.0;
     P.st64.c0 = W[0] * (inv2[0] + inv2[1] + inv2[2]);
     for (int q = 1; q <= 3; ++q) {
         P.st64.cx[q - 1] = W[q] * inv2[0];

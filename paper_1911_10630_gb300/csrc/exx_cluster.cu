@@ -57,18 +57,74 @@ __device__ __forceinline__ T cluster_sum(T v, T (*red)[33], int& flip, T (*part)
     return s;
 }
 
+// Max over the cluster (same pattern and buffers as cluster_sum).
+template <int NT, int C>
+__device__ __forceinline__ double cluster_max(double v, double (*red)[33], int& flip, double (*part)[16], int& cflip,
+                                              cg::cluster_group& cl, int rank) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    double* buf = red[flip];
+    flip ^= 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) buf[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double t = lane < NT / 32 ? buf[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+        if (lane < C) {
+            double* dst = cl.map_shared_rank(&part[cflip][0], lane);
+            dst[rank] = t;
+        }
+    }
+    cl.sync();
+    double m = 0.0;
+#pragma unroll
+    for (int r = 0; r < C; ++r) m = fmax(m, part[cflip][r]);
+    cflip ^= 1;
+    return m;
+}
+
+// Fixed-point residuals (isotropic grids). 180 delta^2 times the weights of
+// Eq. d2_1 (n = 3) are the integers -490, 270, -27, 2 per axis, so with v held
+// as the integers round(v 2^E) the Laplacian is an exact integer sum, and the
+// FP64 residual costs one conversion and two FP64 operations per point instead
+// of twenty (GB300 issues FP64 at 1/64 of the FP32 rate). E is chosen per pair
+// from a bound on |v| so that |v| 2^E < 2^50, which keeps every stencil sum
+// below 2^62; a value outside the bound marks the pair, which then takes the
+// FP64 stencil. The integer stencil rounds v to 2^-E of the bound, far below
+// the rounding of the FP64 sums it replaces.
+__device__ __forceinline__ long long to_fix(double v, double s2E, int& ovf) {
+    const double x = v * s2E;
+    if (!(fabs(x) <= 1125899906842624.0)) {  // 2^50
+        ovf = 1;
+        return 0;
+    }
+    return __double2ll_rn(x);
+}
+
+__device__ __forceinline__ long long lap_fix(const long long* __restrict__ f, long long c, int S, long long S2) {
+    const long long s1 = (f[c + 1] + f[c - 1]) + (f[c + S] + f[c - S]) + (f[c + S2] + f[c - S2]);
+    const long long s2 = (f[c + 2] + f[c - 2]) + (f[c + 2 * S] + f[c - 2 * S]) + (f[c + 2 * S2] + f[c - 2 * S2]);
+    const long long s3 = (f[c + 3] + f[c - 3]) + (f[c + 3 * S] + f[c - 3 * S]) + (f[c + 3 * S2] + f[c - 3 * S2]);
+    return 270 * s1 - 27 * s2 + 2 * s3 - 1470 * f[c];
+}
+
 // FP64 residual r = 4 pi rho + lap v on the CTA's points k0 + tid + j NT;
 // writes r64 (and the debug copy); returns the thread's sum of r^2.
+// With vf set, lap v comes from the fixed-point copy (lap_fix times finv).
 __device__ __noinline__ double cta_residual(const SolveParams& P, const int* __restrict__ cube,
                                             const double* __restrict__ rho, const double* __restrict__ vc,
-                                            double* __restrict__ r64, int k0, int k1, int nt, bool dbg) {
+                                            double* __restrict__ r64, int k0, int k1, int nt, bool dbg,
+                                            const long long* __restrict__ vf = nullptr, double finv = 0.0) {
     const Stencil<double> st = P.st64;  // into registers (see gather_rho)
     const int S = P.S;
     const long long S2 = P.S2;
     double* __restrict__ db = P.dbg_b;
     double acc = 0.0;
     for (int k = k0 + (int)threadIdx.x; k < k1; k += nt) {
-        const double rk = fma(kFourPi, rho[k], lap19<double>(vc, cube[k], S, S2, st));
+        const double lap = vf ? (double)lap_fix(vf, cube[k], S, S2) * finv : lap19<double>(vc, cube[k], S, S2, st);
+        const double rk = fma(kFourPi, rho[k], lap);
         r64[k] = rk;
         acc = fma(rk, rk, acc);
         if (dbg) db[k] = rk;
@@ -82,7 +138,8 @@ __device__ __noinline__ double cta_residual(const SolveParams& P, const int* __r
 __device__ __noinline__ double cta_residual0(const SolveParams& P, const int* __restrict__ cube,
                                              const double* __restrict__ rho, const double* __restrict__ vc,
                                              double* __restrict__ r64, const int* __restrict__ list, int n, int nrim,
-                                             int nt, bool dbg) {
+                                             int nt, bool dbg, const long long* __restrict__ vf = nullptr,
+                                             double finv = 0.0) {
     const Stencil<double> st = P.st64;
     const int S = P.S;
     const long long S2 = P.S2;
@@ -90,7 +147,14 @@ __device__ __noinline__ double cta_residual0(const SolveParams& P, const int* __
     double acc = 0.0;
     for (int t = (int)threadIdx.x; t < n; t += nt) {
         const int k = list[t];
-        const double rk = t < nrim ? fma(kFourPi, rho[k], lap19<double>(vc, cube[k], S, S2, st)) : kFourPi * rho[k];
+        double rk;
+        if (t < nrim) {
+            const double lap =
+                vf ? (double)lap_fix(vf, cube[k], S, S2) * finv : lap19<double>(vc, cube[k], S, S2, st);
+            rk = fma(kFourPi, rho[k], lap);
+        } else {
+            rk = kFourPi * rho[k];
+        }
         r64[k] = rk;
         acc = fma(rk, rk, acc);
         if (dbg) db[k] = rk;
@@ -237,6 +301,9 @@ struct RunCgCtx {
     double target2;
     float drop2;
     int* fault;  // incremented when a cluster-reduction wait gives up
+    long long* vfix;  // fixed-point copy of v (when fix)
+    double s2E;       // its scale 2^E
+    int fix;          // keep vfix current at the end of each segment
 };
 
 __shared__ float g_rc_red32[2][33];
@@ -246,6 +313,7 @@ __shared__ RunCgCtx g_rc;
 __shared__ __align__(8) unsigned long long g_rc_mbar[2];
 __shared__ float g_rc_mpart[2][16];
 __shared__ int g_rc_late;  // set once a wait has given up
+__shared__ int g_fix_ovf;  // a fixed-point conversion of this CTA left the bound (this pair)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -969,7 +1037,13 @@ __device__ __noinline__ RunSeg quad_halo_segment(float* pc, const int* spt, cons
         for (int i = 0; i < 4; ++i) {
             if (m & (1 << i)) {
                 const int cc = cube[k + i];
-                vc[cc] = fma(scale, (double)dv[i], vc[cc]);
+                const double nv = fma(scale, (double)dv[i], vc[cc]);
+                vc[cc] = nv;
+                if (g_rc.fix) {
+                    int o = 0;
+                    g_rc.vfix[cc] = to_fix(nv, g_rc.s2E, o);
+                    if (o) g_fix_ovf = 1;
+                }
             }
         }
     }
@@ -1086,6 +1160,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
     double* r64 = reinterpret_cast<double*>(slot + P.off_r);
     double* rowS = reinterpret_cast<double*>(slot + P.off_rows);
     double* sYc = reinterpret_cast<double*>(slot + P.off_sy);  // plane sums of the whole ball (cluster-shared)
+    long long* vfix = reinterpret_cast<long long*>(slot + P.off_vfix);  // fixed-point v (mode 3)
     // the shell's row coefficients U_{l,c}: FP64, then the FP32 copy (shell_rows)
     double* U64 = reinterpret_cast<double*>(slot + P.off_ush);
     float* U32 = reinterpret_cast<float*>(U64 + (size_t)kNU * P.geos[P.n_geo - 1].n_rows_me);
@@ -1127,8 +1202,39 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
         moment_finish_cluster<NT>(P, G, rowS, xp, yp, sYc, me.x + G.r_pe, planes, s_M, s_T, cl);
         shell_rows(P, G, xp, yp, s_T, U64, U32, gt, gn);
         cl.sync();
-        shell_points<true>(P, G, vc, U64, U32, G.sh_near, G.n_near, gt, gn);
+        const double vnear = shell_points<true>(P, G, vc, U64, U32, G.sh_near, G.n_near, gt, gn);
         shell_points<false>(P, G, vc, U64, U32, G.sh_far, G.n_far, gt, gn);
+        // fixed-point copy of v for the FP64 residuals (mode 3, isotropic grids):
+        // |v| <= max |v| on the shell layer + (2 pi / 3) max |rho| (R_PE delta)^2
+        // (the ball's maximum-principle bound), taken twice over
+        bool fix = QHALO && P.fixres;
+        double s2E = 0.0, finvE = 0.0;
+        if (fix) {
+            double rm = 0.0;
+            for (int k = gt; k < G.n_pe; k += gn) rm = fmax(rm, fabs(rho[k]));
+            const double a2 = (double)G.r_pe * G.r_pe * P.delta[0] * P.delta[0];
+            const double vb = 2.0 * cluster_max<NT, C>(fmax(vnear, (kFourPi / 3.0) * rm * a2), red, flip, part,
+                                                      cflip, cl, rank);
+            int e = 0;
+            (void)frexp(vb, &e);  // vb < 2^e
+            if (!(vb < 1e300)) fix = false;
+            s2E = ldexp(1.0, 50 - e);
+            finvE = ldexp(P.fix_inv, e - 50);
+            if (threadIdx.x == 0) g_fix_ovf = 0;
+            __syncthreads();
+            if (fix) {
+                int o = 0;
+                for (int k = k0 + (int)threadIdx.x; k < k1; k += NT) vfix[cube[k]] = 0;
+                const long long S2 = P.S2, S = P.S;
+                for (int q = gt; q < G.n_near; q += gn) {
+                    const int pk = G.sh_near[q];
+                    const RowRec R = G.rows_me[pk >> 8];
+                    const long long c = (long long)(R.ox + Rc) * S2 + (long long)(R.oy + Rc) * S + Rc + (pk & 255) - 128;
+                    vfix[c] = to_fix(vc[c], s2E, o);
+                }
+                if (o) g_fix_ovf = 1;
+            }
+        }
         cl.sync();
         const long long t1 = clk ? clock64() : 0;
 
@@ -1138,8 +1244,15 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
         // kept, rescaled to the new residual norm, so the Krylov progress
         // survives each replacement. The stop test is the FP64 residual.
         double acc = cta_residual0(P, cube, rho, vc, r64, CL.res_list + k0, k1 - k0, CL.res_nrim[rank], NT,
-                                   P.dbg_b != nullptr);
-        const double bb = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
+                                   P.dbg_b != nullptr, fix ? vfix : nullptr, finvE);
+        if (fix && g_fix_ovf) acc = __longlong_as_double(0x7ff8000000000000LL);  // NaN: the cluster falls back
+        double bb = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
+        if (fix && !(bb == bb)) {
+            fix = false;
+            acc = cta_residual0(P, cube, rho, vc, r64, CL.res_list + k0, k1 - k0, CL.res_nrim[rank], NT,
+                                P.dbg_b != nullptr);
+            bb = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
+        }
         const double target2 = P.tol * P.tol * bb;
         if (clk) tr += clock64() - t1;
         int iters = 0, refines = 1;
@@ -1162,6 +1275,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
                     }
                 }
                 if (abs(dlt[0]) <= 3 && abs(dlt[1]) <= 3 && abs(dlt[2]) <= 3) {
+                    fix = false;  // the warm values are not in the fixed-point copy
                     const long long tu = clk ? clock64() : 0;
                     cta_warm_insert(G, cube, vc, P.vprev + (size_t)prev * G.n_pe, dlt[0], dlt[1], dlt[2], k0, k1, NT);
                     cl.sync();
@@ -1181,6 +1295,9 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
                 g_rc.target2 = target2;
                 g_rc.drop2 = (float)(P.update_drop * P.update_drop);
                 g_rc.fault = P.nonconv;
+                g_rc.vfix = vfix;
+                g_rc.s2E = s2E;
+                g_rc.fix = fix ? 1 : 0;
             }
             __syncthreads();
             double scale = sqrt(rn_start);
@@ -1220,8 +1337,15 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
                 }
                 const long long tu = clk ? clock64() : 0;
                 cl.sync();
-                acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, false);
-                const double rn2 = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
+                acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, false, fix ? vfix : nullptr, finvE);
+                if (fix && g_fix_ovf) acc = __longlong_as_double(0x7ff8000000000000LL);
+                double rn2 = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
+                if (fix && !(rn2 == rn2)) {  // a conversion left the bound (or the solve broke down): FP64 stencil
+                    fix = false;
+                    if (threadIdx.x == 0) g_rc.fix = 0;
+                    acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, false);
+                    rn2 = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
+                }
                 ++refines;
                 if (clk) tr += clock64() - tu;
                 if (rn2 <= target2) break;

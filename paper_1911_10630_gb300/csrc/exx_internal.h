@@ -91,6 +91,9 @@ struct SolveParams {
     size_t off_rows;                                             // [n_rows_pe][8] row sums
     size_t off_sy;                                               // [C][(2 r_pe + 1) * 28] plane sums (cluster)
     size_t off_ush;                                              // [28][n_rows_me] FP64 then FP32 row coefficients U_{l,c} (cluster)
+    size_t off_vfix;                                             // [S^3] int64 fixed-point copy of v (cluster, fixres)
+    int fixres;               // cluster kernel: FP64 residuals from an exact integer stencil on a fixed-point v
+    double fix_inv;           // 1 / (180 delta^2): the integer stencil's weights are 180 delta^2 x Eq. d2_1's
     const double* pow_tab;  // [3][2 Rc + 1][8] x^e, y^e, z^e (cluster kernel; global, read-only)
 
     // solver

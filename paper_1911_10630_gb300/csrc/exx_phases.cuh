@@ -224,7 +224,7 @@ static __device__ __noinline__ void shell_rows(const SolveParams& P, const BallG
 // | (z + 128)), one point per thread: FP64 for the boundary layer the stencil
 // reads (sh_near), FP32 with the FP32 copy of U for the rest (sh_far).
 template <bool F64>
-static __device__ __noinline__ void shell_points(const SolveParams& P, const BallGeo& G, double* __restrict__ vc,
+static __device__ __noinline__ double shell_points(const SolveParams& P, const BallGeo& G, double* __restrict__ vc,
                                                  const double* __restrict__ U64, const float* __restrict__ U32,
                                                  const int* __restrict__ list, int n, int tid, int nthr) {
     const int Rc = P.Rc;
@@ -232,6 +232,7 @@ static __device__ __noinline__ void shell_points(const SolveParams& P, const Bal
     const double dx = P.delta[0], dy = P.delta[1], dz = P.delta[2];
     const long long S2 = P.S2, S = P.S;
     const RowRec* __restrict__ rows = G.rows_me;
+    double vmax = 0.0;  // largest |v| written (FP64 points)
     for (int q = tid; q < n; q += nthr) {
         const int pk = list[q];
         const int row = pk >> 8, z = (pk & 255) - 128;
@@ -253,6 +254,7 @@ static __device__ __noinline__ void shell_points(const SolveParams& P, const Bal
                 acc = fma(acc, ir2, pl);
             }
             vc[base + z] = acc * ir;
+            vmax = fmax(vmax, fabs(acc * ir));
         } else {
             const float zz = (float)z * (float)dz;
             const float r2 = fmaf(zz, zz, (float)(x * x + y * y));
@@ -270,6 +272,7 @@ static __device__ __noinline__ void shell_points(const SolveParams& P, const Bal
             vc[base + z] = (double)(acc * ir);
         }
     }
+    return vmax;
 }
 
 // Step V scatter: D^i += v phi_j, D^j += v phi_i on the ME ball.
