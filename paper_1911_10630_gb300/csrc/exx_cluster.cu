@@ -838,13 +838,15 @@ __device__ __noinline__ RunSeg quad_segment(float* ps, const float* pm, const fl
 // on each side of the CTA's planes (pc = plane 0), so every stencil leg is a
 // local 16-byte load at a fixed offset. Whenever a CTA writes p, each quad of
 // its first or last 3 planes also goes by st.async to the neighbour's halo,
-// counted in bytes on the neighbour's halo mbarrier (g_halo_mbar). Every
-// thread arrives on its own CTA's halo mbarrier after its p writes (thread 0
-// also announces the bytes the neighbours send per phase), so one completed
-// phase means the CTA's p and both halos are current: no cluster barrier. The
-// correction d stays in registers. A neighbour refills a halo only after the
-// r.r sum of the iteration, to which this CTA contributed after its stencil,
-// so one mbarrier suffices; its phase count hph runs for the whole launch.
+// counted in bytes on the neighbour's halo mbarrier (g_halo_mbar); thread 0
+// opens each phase, announcing the bytes the neighbours send in it. An
+// iteration first applies the centre, z and y legs, which read only the CTA's
+// own planes (complete after a CTA barrier), then waits for the phase and
+// applies the x legs, so the exchange overlaps the first pass: no cluster
+// barrier. The correction d stays in registers. A neighbour refills a halo
+// only after the cluster sum of the iteration, to which this CTA contributed
+// after its x legs, so one mbarrier suffices; its phase count hph runs for
+// the whole launch, and every phase opened is waited for.
 __shared__ __align__(8) unsigned long long g_halo_mbar;
 
 // Bounded wait for the given phase parity of a CTA-local mbarrier; a wait that
@@ -872,14 +874,12 @@ __device__ __forceinline__ void push4(uint32_t dst, float4 v, uint32_t mbar) {
                  : "memory");
 }
 
-// This thread's arrival on the CTA's halo mbarrier (thread 0 also announces
-// the neighbours' bytes of the phase).
+// Thread 0 opens the next phase of the CTA's halo mbarrier, announcing the
+// bytes the neighbours send in it (the mbarrier counts this one arrival).
 __device__ __forceinline__ void halo_arrive(uint32_t mb, int halo_bytes) {
     if (threadIdx.x == 0)
         asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(halo_bytes)
                      : "memory");
-    else
-        asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
 }
 
 template <int NT, int C, int Q, int SY, bool ISO>
@@ -935,12 +935,12 @@ __device__ __noinline__ RunSeg quad_halo_segment(float* pc, const int* spt, cons
     float rr = cluster_sum4_mb<NT, C>(make_float4(a32, 0.0f, 0.0f, 0.0f), flip32, cflip32, rank).x;
     const float lim = g_rc.drop2 * rr;
     const float conv_thr = (float)(0.25 * g_rc.target2 / (scale * scale));
-    halo_wait(hmb, (uint32_t)hph & 1u);
-    ++hph;
     RunSeg out;
     float al = 0.0f;
     for (;;) {
         if (iters >= g_rc.max_iter) {
+            halo_wait(hmb, (uint32_t)hph & 1u);  // complete the pending phase
+            ++hph;
             out.maxed = 1;
             break;
         }
@@ -950,11 +950,11 @@ __device__ __noinline__ RunSeg quad_halo_segment(float* pc, const int* spt, cons
         // iteration instead of summing it afresh lets its rounding errors add up
         // while r.r falls, and the solve diverges.)
         float pa = 0.0f, ra = 0.0f, aa = 0.0f, rq = 0.0f;
+        // pass 1, while the neighbours' planes are still on their way: the
+        // centre, z and y legs, which read only this CTA's planes
 #pragma unroll
         for (int j = 0; j < Q; ++j) {
-            const int pk = spt[j * NT];
-            const int m = (pk >> 20) & 15;
-            const float* b = pc + (pk & 0xfffff);
+            const float* b = pc + (spt[j * NT] & 0xfffff);
             const float4 c = ld4(b), zl = ld4(b - 4), zh = ld4(b + 4);
             const float w[10] = {zl.y, zl.z, zl.w, c.x, c.y, c.z, c.w, zh.x, zh.y, zh.z};
             float a[4];
@@ -971,6 +971,18 @@ __device__ __noinline__ RunSeg quad_halo_segment(float* pc, const int* spt, cons
                 a[2] = fmaf(cyq, ym.z + yp.z, a[2]);
                 a[3] = fmaf(cyq, ym.w + yp.w, a[3]);
             }
+            ap[j] = make_float4(a[0], a[1], a[2], a[3]);
+        }
+        halo_wait(hmb, (uint32_t)hph & 1u);  // the halos hold the neighbours' p
+        ++hph;
+        // pass 2: the x legs, the mask and the dot products
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const int pk = spt[j * NT];
+            const int m = (pk >> 20) & 15;
+            const float* b = pc + (pk & 0xfffff);
+            const float4 c = ld4(b);
+            float a[4] = {ap[j].x, ap[j].y, ap[j].z, ap[j].w};
 #pragma unroll
             for (int q = 1; q <= 3; ++q) {
                 const float cxq = ISO ? sa.cz[q - 1] : sa.cx[q - 1];
@@ -1019,8 +1031,7 @@ __device__ __noinline__ RunSeg quad_halo_segment(float* pc, const int* spt, cons
         }
         al = 0.0f;
         halo_arrive(hmb, halo_bytes);
-        halo_wait(hmb, (uint32_t)hph & 1u);
-        ++hph;
+        __syncthreads();  // this CTA's p is complete (pass 1 of the next iteration reads it)
     }
     // the last iteration's d += alpha p (p is unchanged since its stencil), then v += scale d
     const int* cube = g_rc.cube;
@@ -1171,8 +1182,8 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
         // the quad segments' reduction barriers (count 1: this CTA's own arrive)
         for (int b = 0; b < 2; ++b)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&g_rc_mbar[b])) : "memory");
-        if (QHALO)  // every thread of the CTA arrives once per phase
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&g_halo_mbar)), "r"(NT) : "memory");
+        if (QHALO)  // thread 0 arrives once per phase; the neighbours' bytes complete it
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&g_halo_mbar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         g_rc_late = 0;
     }
