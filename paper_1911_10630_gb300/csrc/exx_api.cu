@@ -516,7 +516,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             build_residual_order(B, L, res_list, res_nrim);
             // one candidate: variant v with thread map (spk, sk) and lane map lm
             auto add_cand = [&](int v, int lm, const std::vector<int>& spk, const std::vector<int>& sk,
-                                const ClusterLayout& LL, const std::vector<int>* hb = nullptr) -> exx_status {
+                                const ClusterLayout& LL) -> exx_status {
                 const size_t sm = cluster_kernel_smem(Rc, LL, v);
                 if ((long)sm + 2048 > (long)max_optin) return EXX_OK;
                 int nclu = 0;
@@ -544,15 +544,11 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                     if (e != cudaSuccess) return cuda_fail(c, e, "slab tables");
                 }
                 int* d_slot = nullptr;
-                const size_t nhb = hb ? hb->size() : 0;
-                e = cudaMalloc(&d_slot, sizeof(int) * (spk.size() + sk.size() + nhb));
+                e = cudaMalloc(&d_slot, sizeof(int) * (spk.size() + sk.size()));
                 if (e == cudaSuccess) c->cl_mem.push_back(d_slot);
                 if (e == cudaSuccess) e = cudaMemcpy(d_slot, spk.data(), sizeof(int) * spk.size(), cudaMemcpyHostToDevice);
                 if (e == cudaSuccess)
                     e = cudaMemcpy(d_slot + spk.size(), sk.data(), sizeof(int) * sk.size(), cudaMemcpyHostToDevice);
-                if (e == cudaSuccess && nhb)
-                    e = cudaMemcpy(d_slot + spk.size() + sk.size(), hb->data(), sizeof(int) * nhb,
-                                   cudaMemcpyHostToDevice);
                 if (e != cudaSuccess) return cuda_fail(c, e, "slot maps");
                 exx_ctx::ClusterCand K;
                 K.C = C;
@@ -565,7 +561,6 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                 K.L.rank_info = d_ri;
                 K.L.slot_pk = d_slot;
                 K.L.slot_k = d_slot + spk.size();
-                K.L.halo_bytes = nhb ? d_slot + spk.size() + sk.size() : nullptr;
                 K.L.res_list = d_res;
                 K.L.res_nrim = d_res + res_list.size();
                 c->cands.push_back(K);
@@ -610,10 +605,9 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                         for (int ba = 0; ba <= (mode == 3 ? 1 : 0); ++ba) {
                             const int lm = mode == 2 ? 3 : 4 + ba;
                             if (!o.autotune && o.lane_map != lm) continue;
-                            std::vector<int> spk, sk, hb;
+                            std::vector<int> spk, sk;
                             if (build_quad_maps(Lq, ptq, nt, cluster_variant_pts(v), spk, sk, ba) < 0) continue;
-                            if (mode == 3) quad_halo_bytes(Lq, spk, nt * cluster_variant_pts(v), hb);
-                            const exx_status sa = add_cand(v, lm, spk, sk, Lq, mode == 3 ? &hb : nullptr);
+                            const exx_status sa = add_cand(v, lm, spk, sk, Lq);
                             if (sa != EXX_OK) return bail(sa);
                         }
                         have.push_back(mode * 4096 + nt);

@@ -836,10 +836,11 @@ __device__ __noinline__ RunSeg quad_segment(float* ps, const float* pm, const fl
 
 // The quad-map CG with halo planes (MODE 3). The slab array holds 3 halo planes
 // on each side of the CTA's planes (pc = plane 0), so every stencil leg is a
-// local 16-byte load at a fixed offset. Whenever a CTA writes p, each quad of
-// its first or last 3 planes also goes by st.async to the neighbour's halo,
-// counted in bytes on the neighbour's halo mbarrier (g_halo_mbar); thread 0
-// opens each phase, announcing the bytes the neighbours send in it. An
+// local 16-byte load at a fixed offset. Whenever a CTA has written p, one
+// thread copies its first and last 3 planes into the neighbours' halos with
+// two bulk copies (cp.async.bulk, shared::cta -> shared::cluster), counted in
+// bytes on the neighbours' halo mbarriers (g_halo_mbar), and opens the next
+// phase of its own, announcing the bytes the neighbours send in it. An
 // iteration first applies the centre, z and y legs, which read only the CTA's
 // own planes (complete after a CTA barrier), then waits for the phase and
 // applies the x legs, so the exchange overlaps the first pass: no cluster
@@ -868,23 +869,9 @@ __device__ __forceinline__ void halo_wait(uint32_t mb, uint32_t parity) {
     }
 }
 
-__device__ __forceinline__ void push4(uint32_t dst, float4 v, uint32_t mbar) {
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(dst),
-                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(mbar)
-                 : "memory");
-}
-
-// Thread 0 opens the next phase of the CTA's halo mbarrier, announcing the
-// bytes the neighbours send in it (the mbarrier counts this one arrival).
-__device__ __forceinline__ void halo_arrive(uint32_t mb, int halo_bytes) {
-    if (threadIdx.x == 0)
-        asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(halo_bytes)
-                     : "memory");
-}
-
 template <int NT, int C, int Q, int SY, bool ISO>
 __device__ __noinline__ RunSeg quad_halo_segment(float* pc, const int* spt, const int* skt, int planes, uint32_t nbl,
-                                                 uint32_t nbr, uint32_t mbl, uint32_t mbr, int halo_bytes,
+                                                 uint32_t nbr, uint32_t mbl, uint32_t mbr,
                                                  int syz_rt, int sp2_rt, double scale, float carry, StencilArgs sa,
                                                  int iters, int flip32, int cflip32, int hph) {
     constexpr int PZ = (SY + 3) & ~3;
@@ -894,13 +881,27 @@ __device__ __noinline__ RunSeg quad_halo_segment(float* pc, const int* spt, cons
     const int rank = (int)cl.block_rank();
     const uint32_t hmb = smem_u32(&g_halo_mbar);
     float4 r[Q], ap[Q], d[Q];
-    // p of quad j written: locally, and to the neighbours' halos for the first / last 3 planes
-    auto put_p = [&](int pk, float4 v) {
-        const int off = pk & 0xfffff, xl = (int)((unsigned)pk >> 24);
-        st4(pc + off, v);
-        if ((pk >> 20) & 15) {
-            if (rank > 0 && xl < 3) push4(nbl + 4u * (uint32_t)off, v, mbl);
-            if (rank < C - 1 && xl >= planes - 3) push4(nbr + 4u * (uint32_t)off, v, mbr);
+    auto put_p = [&](int pk, float4 v) { st4(pc + (pk & 0xfffff), v); };
+    // After a CTA barrier (this CTA's p complete), thread 0 copies the first
+    // and last 3 planes into the neighbours' halos by bulk copies that count
+    // their bytes on the neighbours' halo mbarriers, and opens the next phase
+    // of its own, announcing the bytes the neighbours send.
+    const uint32_t plane3 = 12u * (uint32_t)Sp2;  // bytes of 3 planes
+    const uint32_t in_bytes = (rank > 0 ? plane3 : 0u) + (rank < C - 1 ? plane3 : 0u);
+    auto publish = [&]() {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // p writes -> the bulk copies' reads
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (rank > 0)
+                asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             ::"r"(nbl), "r"(smem_u32(pc)), "r"(plane3), "r"(mbl) : "memory");
+            if (rank < C - 1) {
+                const uint32_t o = 4u * (uint32_t)((planes - 3) * Sp2);
+                asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             ::"r"(nbr + o), "r"(smem_u32(pc) + o), "r"(plane3), "r"(mbr) : "memory");
+            }
+            asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(hmb), "r"(in_bytes)
+                         : "memory");
         }
     };
     float a32 = 0.0f;
@@ -931,7 +932,7 @@ __device__ __noinline__ RunSeg quad_halo_segment(float* pc, const int* spt, cons
             a32 = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, fmaf(rv.w, rv.w, a32))));
         }
     }
-    halo_arrive(hmb, halo_bytes);
+    publish();
     float rr = cluster_sum4_mb<NT, C>(make_float4(a32, 0.0f, 0.0f, 0.0f), flip32, cflip32, rank).x;
     const float lim = g_rc.drop2 * rr;
     const float conv_thr = (float)(0.25 * g_rc.target2 / (scale * scale));
@@ -1030,8 +1031,7 @@ __device__ __noinline__ RunSeg quad_halo_segment(float* pc, const int* spt, cons
                                   fmaf(be, po.w, r[j].w)));
         }
         al = 0.0f;
-        halo_arrive(hmb, halo_bytes);
-        __syncthreads();  // this CTA's p is complete (pass 1 of the next iteration reads it)
+        publish();  // also makes this CTA's p complete for pass 1 of the next iteration
     }
     // the last iteration's d += alpha p (p is unchanged since its stencil), then v += scale d
     const int* cube = g_rc.cube;
@@ -1146,11 +1146,9 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
         for (int j = 0; j < PTS; ++j)
             spk[j * NT + threadIdx.x] = CL.slot_pk[(size_t)rank * PTS * NT + j * NT + threadIdx.x];
     }
-    // MODE 3: where this CTA's boundary quads go in the neighbours' halos
-    // (shared::cluster addresses of the image of pc), their halo mbarriers,
-    // and the bytes the neighbours send this CTA per phase
+    // MODE 3: where this CTA's first and last planes go in the neighbours'
+    // halos (shared::cluster addresses of the image of pc) and their halo mbarriers
     uint32_t nbl = 0, nbr = 0, mbl = 0, mbr = 0;
-    int hbytes = 0;
     if constexpr (QHALO) {
         const uint32_t base = smem_u32(ps), hm0 = smem_u32(&g_halo_mbar);
         if (rank > 0) {
@@ -1161,7 +1159,6 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
             nbr = cluster_addr(base, rank + 1) + 4u * (uint32_t)((3 - planes) * Sp2);
             mbr = cluster_addr(hm0, rank + 1);
         }
-        hbytes = CL.halo_bytes[rank];
     }
 
     const int cid = blockIdx.x / C;
@@ -1328,7 +1325,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
                                                       sa.c0, sa.cz[0], sa.cz[1], sa.cz[2], iters, f32, cf32);
                 else if constexpr (QHALO)
                     sg = quad_halo_segment<NT, C, PTS, SYZ, ISO>(pc, spk + threadIdx.x, slot_k + threadIdx.x, planes,
-                                                                 nbl, nbr, mbl, mbr, hbytes, Syz, Sp2, scale, carry,
+                                                                 nbl, nbr, mbl, mbr, Syz, Sp2, scale, carry,
                                                                  sa, iters, f32, cf32, hph);
                 else if constexpr (QUADS)
                     sg = quad_segment<NT, C, PTS, SYZ, ISO>(ps, pm, pp, reinterpret_cast<float4*>(ds) + threadIdx.x,

@@ -460,21 +460,6 @@ int build_quad_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int
 }
 
 
-void quad_halo_bytes(const ClusterLayout& L, const std::vector<int>& quad_pk, int per, std::vector<int>& bytes) {
-    std::vector<int> first3(L.C, 0), last3(L.C, 0);  // quads with valid elements in a rank's first / last 3 planes
-    for (int r = 0; r < L.C; ++r)
-        for (int s = 0; s < per; ++s) {
-            const int pk = quad_pk[(size_t)r * per + s];
-            if (!((pk >> 20) & 15)) continue;
-            const int xl = (int)((unsigned)pk >> 24);
-            if (xl < 3) ++first3[r];
-            if (xl >= L.planes[r] - 3) ++last3[r];
-        }
-    bytes.assign(L.C, 0);
-    for (int r = 0; r < L.C; ++r) bytes[r] = 16 * ((r > 0 ? last3[r - 1] : 0) + (r + 1 < L.C ? first3[r + 1] : 0));
-}
-
-
 void build_residual_order(const HostBall& B, const ClusterLayout& L, std::vector<int>& list, std::vector<int>& nrim) {
     const long in2 = (long)(B.r_pe - 3) * (B.r_pe - 3);
     list.assign(B.n_pe, 0);

@@ -63,10 +63,6 @@ int build_run_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int 
 // fit 20 bits.
 int build_quad_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int NT, int Q, std::vector<int>& quad_pk,
                     std::vector<int>& quad_k, int bank_aware = 0);
-// Halo traffic of the quad map with halo planes: bytes[r] = 16 x the quads
-// with valid elements that rank r's neighbours push into its halos per phase
-// (rank r - 1's last 3 planes, rank r + 1's first 3). per = slots per rank.
-void quad_halo_bytes(const ClusterLayout& L, const std::vector<int>& quad_pk, int per, std::vector<int>& bytes);
 // Order of the first FP64 residual of a pair, when v is still zero on the PE
 // ball: per rank, its points whose stencil reaches the shell (|o| > R_PE - 3,
 // the rim) first, then the interior ones, where lap v = 0 and r = 4 pi rho.

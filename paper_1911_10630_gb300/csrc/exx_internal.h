@@ -142,7 +142,6 @@ struct ClusterLayout {
     const int4* rank_info;  // device [C]: x0, planes, k0, k1 (read by the kernel)
     const int* slot_pk;     // device [C][PTS][NT]: packed slab offset of each thread slot, or -1
     const int* slot_k;      // device [C][PTS][NT]: compact PE index of each thread slot, or -1
-    const int* halo_bytes;  // device [C]: bytes the neighbours push into a CTA's halos per phase (mode 3)
     const int* res_list;    // device [n_pe]: per rank, rim points then interior points (first residual)
     const int* res_nrim;    // device [C]: rim points of each rank
 };
