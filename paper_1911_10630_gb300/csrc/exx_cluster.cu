@@ -1283,12 +1283,22 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
                     }
                 }
                 if (abs(dlt[0]) <= 3 && abs(dlt[1]) <= 3 && abs(dlt[2]) <= 3) {
-                    fix = false;  // the warm values are not in the fixed-point copy
                     const long long tu = clk ? clock64() : 0;
                     cta_warm_insert(G, cube, vc, P.vprev + (size_t)prev * G.n_pe, dlt[0], dlt[1], dlt[2], k0, k1, NT);
+                    if (fix) {  // the warm values into the fixed-point copy
+                        int o = 0;
+                        for (int k = k0 + (int)threadIdx.x; k < k1; k += NT) vfix[cube[k]] = to_fix(vc[cube[k]], s2E, o);
+                        if (o) g_fix_ovf = 1;
+                    }
                     cl.sync();
-                    acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, false);
+                    acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, false, fix ? vfix : nullptr, finvE);
+                    if (fix && g_fix_ovf) acc = __longlong_as_double(0x7ff8000000000000LL);
                     rn_start = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
+                    if (fix && !(rn_start == rn_start)) {
+                        fix = false;
+                        acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, false);
+                        rn_start = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
+                    }
                     ++refines;
                     if (clk) tr += clock64() - tu;
                 }
