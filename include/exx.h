@@ -114,7 +114,9 @@ typedef struct {
     int autotune;      /* cluster solver: 1 = on the first exx_compute of a context
                           time every fitting launch shape (cluster size, threads
                           per CTA, lane map) on a prefix of the pair queue and
-                          keep the fastest (default); 0 = take the first fit.    */
+                          keep the fastest (default); later contexts of the
+                          process with the same grid, radii and options reuse
+                          that choice; 0 = take the first fit.                  */
     int r_pe_nonself;  /* radii_mode 2: R_PE of non-self pairs, 1..R_PE        */
     int r_me_nonself;  /* radii_mode 2: R_ME of non-self pairs,
                           r_pe_nonself + 3 .. R_ME                              */

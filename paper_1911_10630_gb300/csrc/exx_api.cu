@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -908,11 +909,56 @@ static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double*
     return EXX_OK;
 }
 
+// Choices of the autotuner, kept for the process: contexts with the same grid,
+// radii and solver options build the same candidate list and reuse the
+// first context's choice (consistent launch shapes, no repeated tuning).
+struct TuneKey {
+    double cell[3], delta[3], r_pair, update_drop;
+    int grid[3], r_pe, r_me, precision, cluster_size, threads, lane_map, radii_mode, n_cands;
+    bool operator==(const TuneKey& o) const { return std::memcmp(this, &o, sizeof(TuneKey)) == 0; }
+};
+static std::mutex g_tune_mu;
+static std::vector<std::pair<TuneKey, int>> g_tune_cache;
+
+static TuneKey tune_key(const exx_ctx* c) {
+    TuneKey k;
+    std::memset(&k, 0, sizeof(k));
+    for (int a = 0; a < 3; ++a) {
+        k.cell[a] = c->cell[a];
+        k.delta[a] = c->delta[a];
+        k.grid[a] = c->grid[a];
+    }
+    k.r_pair = c->r_pair;
+    k.update_drop = c->opt.update_drop;
+    k.r_pe = c->r_pe;
+    k.r_me = c->r_me;
+    k.precision = c->opt.precision;
+    k.cluster_size = c->opt.cluster_size;
+    k.threads = c->opt.threads;
+    k.lane_map = c->opt.lane_map;
+    k.radii_mode = c->opt.radii_mode;
+    k.n_cands = (int)c->cands.size();
+    return k;
+}
+
 // The autotuner: on the first call, every cluster-solver candidate processes
 // the same prefix of the pair queue (no D_xx scatter); the one with the most
-// pairs per second is kept for the life of the context.
+// pairs per second is kept for the life of the context (and for later
+// contexts with the same key).
 static exx_status autotune(exx_ctx* c, const double* orbitals, const double* centers, const double* alphas, int n,
                            cudaStream_t st) {
+    const TuneKey key = tune_key(c);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (const auto& e : g_tune_cache)
+            if (e.first == key && e.second >= 0 && e.second < (int)c->cands.size()) {
+                apply_cand(c, e.second);
+                c->tuned = true;
+                c->tune_ms = 0.0;
+                drop_graph(c);
+                return EXX_OK;
+            }
+    }
     CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
                         c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st,
                         c->opt.radii_mode == 1 ? alphas : nullptr, c->ln_inv_eps, c->delta_max, c->r_min, c->ns_pe,
@@ -923,7 +969,7 @@ static exx_status autotune(exx_ctx* c, const double* orbitals, const double* cen
     CK(cudaStreamSynchronize(st), "autotune synchronize");
     int widest = 1;
     for (const auto& K : c->cands) widest = std::max(widest, std::min(K.n_clusters, c->n_slots));
-    const int K = std::max(1, std::min(np, 4 * widest));
+    const int K = std::max(1, std::min(np, 8 * widest));  // 8 pairs per cluster: tail and noise small
     CK(cudaMemcpy(c->d_scalars + 4, &K, sizeof(int), cudaMemcpyHostToDevice), "tuning count");
     SolveParams P = c->P;
     P.phi = orbitals;
@@ -961,6 +1007,10 @@ static exx_status autotune(exx_ctx* c, const double* orbitals, const double* cen
     apply_cand(c, best);
     c->tuned = true;
     c->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache.push_back({key, best});
+    }
     drop_graph(c);
     return EXX_OK;
 }
