@@ -3,16 +3,20 @@
 // The C CTAs of a cluster share one pair. The PE ball is split into C slabs of
 // whole x planes (balanced by point count, at least 3 planes each so a stencil
 // leg reaches at most the adjacent CTA). Each CTA keeps the CG direction p of
-// its slab in shared memory as planes of a (2 R_PE + 7)^2 box (zero outside the
-// ball, so the stencil needs no bounds tests); the x legs that leave the slab
-// read the neighbouring CTA's slab through distributed shared memory. The
-// residual r and A p of the CTA's points stay in registers and the correction
-// d in shared memory, through a fixed point-to-thread map whose warps cover
-// consecutive points (so a warp's remote loads stay contiguous: maps that
-// scatter them, even bank-conflict-free ones, measured much slower). Dot
-// products are reduced per CTA, exchanged through distributed shared memory
-// and summed in rank order, so every CTA holds the same value. Per inner
-// iteration: three cluster barriers.
+// its slab in shared memory as planes of a box of 2 R_PE + 7 rows (zero outside
+// the ball, so the stencil needs no bounds tests). The thread maps (MODE):
+//   0  one point per thread slot; x legs that leave the slab read the
+//      neighbour's slab through distributed shared memory; three cluster
+//      barriers per iteration (pts_segment)
+//   1  z runs, halo planes filled by plain remote stores (run_segment)
+//   2  quads of 4 consecutive z positions per slot, every leg one 16-byte
+//      load, x legs read remotely, mbarrier cluster sums (quad_segment)
+//   3  quads with 3 halo planes per side filled by bulk copies counted on an
+//      mbarrier, one cluster sum per iteration, no cluster barrier in the CG,
+//      fixed-point FP64 residuals (quad_halo_segment; the fastest on GB300)
+// In every map r and A p stay in registers; dot products are summed per CTA,
+// exchanged through distributed shared memory and added in rank order, so
+// every CTA holds the same value.
 //
 // The FP64 parts of the pair (gather, multipoles, shell potential, the FP64
 // residual 4 pi rho + lap v of each refinement step, E_ij, the D_xx scatter)
