@@ -120,6 +120,13 @@ typedef struct {
     int r_pe_nonself;  /* radii_mode 2: R_PE of non-self pairs, 1..R_PE        */
     int r_me_nonself;  /* radii_mode 2: R_ME of non-self pairs,
                           r_pe_nonself + 3 .. R_ME                              */
+    int fixed_residual;/* cluster solver with lane map 4 or 5 on an isotropic
+                          grid: 0 = the FP64 residuals of the refinement come
+                          from an exact integer stencil on a fixed-point copy
+                          of v (default), 1 = from the FP64 stencil, 2 = test
+                          mode: the fixed-point bound is made too small, so
+                          every pair takes the overflow fallback to the FP64
+                          stencil.                                              */
 } exx_options;
 
 typedef struct {

@@ -202,6 +202,7 @@ extern "C" exx_options exx_default_options(void) {
     o.radii_mode = 0;
     o.r_pe_nonself = 0;
     o.r_me_nonself = 0;
+    o.fixed_residual = 0;
     o.max_iter = 20000;
     o.inner_max_iter = 4000;
     o.inner_tol = 1e-5;
@@ -338,6 +339,8 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (o.cluster_size != 0 && o.cluster_size != 2 && o.cluster_size != 4 && o.cluster_size != 8 &&
         o.cluster_size != 9)
         return fail(nullptr, EXX_EINVAL, "exx_init: cluster_size must be 0, 2, 4, 8 or 9");
+    if (o.fixed_residual < 0 || o.fixed_residual > 2)
+        return fail(nullptr, EXX_EINVAL, "exx_init: fixed_residual must be 0, 1 or 2");
 
     c = new exx_ctx();
     std::memset(&c->stats, 0, sizeof(c->stats));
@@ -705,7 +708,9 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     double inv2[3];
     for (int a = 0; a < 3; ++a) inv2[a] = 1.0 / (c->delta[a] * c->delta[a]);
     // isotropic grids: 180 delta^2 x the weights are the integers -490, 270, -27, 2
-    P.fixres = (c->delta[0] == c->delta[1] && c->delta[1] == c->delta[2]) ? 1 : 0;
+    P.fixres = (c->delta[0] == c->delta[1] && c->delta[1] == c->delta[2] && c->opt.fixed_residual != 1)
+                   ? (c->opt.fixed_residual == 2 ? 2 : 1)
+                   : 0;
     P.fix_inv = inv2[0] / 180.0;
     P.st64.c0 = W[0] * (inv2[0] + inv2[1] + inv2[2]);
     for (int q = 1; q <= 3; ++q) {

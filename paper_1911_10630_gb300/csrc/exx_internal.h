@@ -93,6 +93,7 @@ struct SolveParams {
     size_t off_ush;                                              // [28][n_rows_me] FP64 then FP32 row coefficients U_{l,c} (cluster)
     size_t off_vfix;                                             // [S^3] int64 fixed-point copy of v (cluster, fixres)
     int fixres;               // cluster kernel: FP64 residuals from an exact integer stencil on a fixed-point v
+                              // (1; 2: bound made too small, every pair falls back, for tests)
     double fix_inv;           // 1 / (180 delta^2): the integer stencil's weights are 180 delta^2 x Eq. d2_1's
     const double* pow_tab;  // [3][2 Rc + 1][8] x^e, y^e, z^e (cluster kernel; global, read-only)
 

@@ -100,6 +100,11 @@ def test_init_rejects_bad_options(lib):
     o.solver_kind = 2
     st, ctx = _init(lib, opt=o)
     assert st == -1 and "solver_kind 1" in lib.exx_last_error(None).decode()
+    o = lib.exx_default_options()
+    assert o.fixed_residual == 0
+    o.fixed_residual = 3
+    st, ctx = _init(lib, opt=o)
+    assert st == -1 and "fixed_residual" in lib.exx_last_error(None).decode()
 
 
 def test_null_and_destroy_are_safe(lib):

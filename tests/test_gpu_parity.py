@@ -66,6 +66,20 @@ def test_cfg0_end_to_end(torch, cfg0, precision, solver_kind, cluster_size, lane
         assert np.max(np.abs(out["pairs"]["iters"] - ref["rep_iters"])) <= 2
 
 
+@pytest.mark.parametrize("fixed_residual", [1, 2])
+def test_cfg0_residual_paths(torch, cfg0, fixed_residual):
+    """The quad map with halo planes with the FP64 stencil for the refinement
+    residuals (1) and with the fixed-point copy forced past its bound on every
+    pair (2), which must fall back to the FP64 stencil: both meet the gates."""
+    w, phi, ref = cfg0
+    out = run_gpu(w, phi, torch=torch, precision=1, solver_kind=2, cluster_size=9, lane_map=5, autotune=0,
+                  fixed_residual=fixed_residual)
+    assert out["stats"]["lane_map"] == 5 and out["stats"]["n_nonconv"] == 0
+    assert abs(out["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
+    assert d_maxrel(out["D"], ref["D"]) <= D_GATE_MAXREL
+    np.testing.assert_allclose(out["pairs"]["e_pair"], ref["E_pair"], rtol=1e-8, atol=1e-12)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_cfg0_pair_intermediates(torch, cfg0, precision):
     w, phi, ref = cfg0
