@@ -215,18 +215,6 @@ __device__ void moment_finish_cluster(const SolveParams& P, const BallGeo& G, co
     __syncthreads();
 }
 
-// v += scale * d on the CTA's points (d in shared memory, [j][NT] slots).
-__device__ __noinline__ void cta_update_v(const int* __restrict__ cube, double* __restrict__ vc,
-                                          const float* __restrict__ ds, const int* __restrict__ slot_k, double scale,
-                                          int pts, int nt) {
-    for (int j = 0; j < pts; ++j) {
-        const int k = slot_k[j * nt + threadIdx.x];
-        if (k < 0) continue;
-        const int c = cube[k];
-        vc[c] = fma(scale, (double)ds[j * nt + threadIdx.x], vc[c]);
-    }
-}
-
 // sum of rho v over the CTA's points.
 __device__ __noinline__ double cta_energy(const int* __restrict__ cube, const double* __restrict__ rho,
                                           const double* __restrict__ vc, int k0, int k1, int nt) {
