@@ -127,6 +127,12 @@ typedef struct {
                           mode: the fixed-point bound is made too small, so
                           every pair takes the overflow fallback to the FP64
                           stencil.                                              */
+    int deterministic; /* 0 = D_xx accumulated by FP64 atomic adds (the order of
+                          the adds, hence the last bits, varies; default);
+                          1 = accumulated as 64-bit fixed-point integers
+                          (resolution 2^-40, |D_xx| < 2^22) by integer atomic
+                          adds, whose sum does not depend on their order, then
+                          converted to FP64 in place: bitwise reproducible.     */
 } exx_options;
 
 typedef struct {

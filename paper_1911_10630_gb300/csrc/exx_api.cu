@@ -25,6 +25,7 @@ cudaError_t launch_pair_list(int n, const double* centers, const double L[3], co
 cudaError_t launch_radii_sort(const PairRec* pairs, const int* n_pair, int* hist, int n_geo, int* order, int num_sms,
                               cudaStream_t st);
 cudaError_t launch_zero(double* p, long long n, int num_sms, cudaStream_t st);
+cudaError_t launch_dfix_convert(double* p, long long n, double inv, int num_sms, cudaStream_t st);
 cudaError_t launch_exx_reduce(const PairRec* pairs, const int* n_pair, const double* e_pair, double* out,
                               cudaStream_t st);
 cudaError_t set_multipole_const_solve(const MultipoleConst& mc);
@@ -203,6 +204,7 @@ extern "C" exx_options exx_default_options(void) {
     o.r_pe_nonself = 0;
     o.r_me_nonself = 0;
     o.fixed_residual = 0;
+    o.deterministic = 0;
     o.max_iter = 20000;
     o.inner_max_iter = 4000;
     o.inner_tol = 1e-5;
@@ -341,6 +343,8 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         return fail(nullptr, EXX_EINVAL, "exx_init: cluster_size must be 0, 2, 4, 8 or 9");
     if (o.fixed_residual < 0 || o.fixed_residual > 2)
         return fail(nullptr, EXX_EINVAL, "exx_init: fixed_residual must be 0, 1 or 2");
+    if (o.deterministic < 0 || o.deterministic > 1)
+        return fail(nullptr, EXX_EINVAL, "exx_init: deterministic must be 0 or 1");
 
     c = new exx_ctx();
     std::memset(&c->stats, 0, sizeof(c->stats));
@@ -712,6 +716,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                    ? (c->opt.fixed_residual == 2 ? 2 : 1)
                    : 0;
     P.fix_inv = inv2[0] / 180.0;
+    P.dfix = c->opt.deterministic ? 1099511627776.0 : 0.0;  // 2^40
     P.st64.c0 = W[0] * (inv2[0] + inv2[1] + inv2[2]);
     for (int q = 1; q <= 3; ++q) {
         P.st64.cx[q - 1] = W[q] * inv2[0];
@@ -805,6 +810,8 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
         CK(launch_cluster_kernel(c->cl_variant, P, c->CL, c->n_clusters, c->smem, st), "cluster pair kernel");
     else
         CK(launch_pair_kernel(P, c->threads, c->opt.precision == 1, c->n_slots, c->smem, st), "pair kernel");
+    if (P.dfix != 0.0)
+        CK(launch_dfix_convert(d_xx, (long long)n * c->ngrid, 1.0 / P.dfix, c->num_sms, st), "D_xx to FP64");
     CK(cudaEventRecordWithFlags(c->ev[2], st, evf), "cudaEventRecord");
     CK(launch_exx_reduce(c->d_pairs, c->d_scalars, c->d_epair, c->d_exx, st), "E_xx reduction");
     CK(cudaMemcpyAsync(c->h_exx, c->d_exx, sizeof(double), cudaMemcpyDeviceToHost, st), "copy E_xx");
@@ -893,6 +900,8 @@ static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double*
     }
     CK(cudaEventRecord(c->ev[1], st), "cudaEventRecord");
     CK(launch_cluster_kernel(c->cl_variant, P, c->CL, c->n_clusters, c->smem, st), "cluster pair kernel");
+    if (P.dfix != 0.0)
+        CK(launch_dfix_convert(d_xx, (long long)n * c->ngrid, 1.0 / P.dfix, c->num_sms, st), "D_xx to FP64");
     CK(cudaEventRecord(c->ev[2], st), "cudaEventRecord");
     CK(launch_exx_reduce(c->d_pairs, c->d_scalars, c->d_epair, c->d_exx, st), "E_xx reduction");
     CK(cudaMemcpyAsync(c->h_exx, c->d_exx, sizeof(double), cudaMemcpyDeviceToHost, st), "copy E_xx");

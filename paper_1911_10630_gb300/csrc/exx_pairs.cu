@@ -207,6 +207,15 @@ __global__ void zero_kernel(double* __restrict__ p, long long n, int vec) {
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) p[n - 1] = 0.0;
 }
 
+// D_xx accumulated as fixed-point integers (deterministic mode): each word
+// holds a 64-bit integer sum; convert it to FP64 in place.
+__global__ void dfix_convert_kernel(double* __restrict__ p, long long n, double inv) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long* q = reinterpret_cast<long long*>(p);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride)
+        p[k] = (double)q[k] * inv;
+}
+
 // E_xx = -(sum_i E_ii + 2 sum_{i<j} E_ij), in a fixed order (one block).
 __global__ void exx_reduce_kernel(const PairRec* __restrict__ pairs, const int* __restrict__ n_pair,
                                   const double* __restrict__ e_pair, double* __restrict__ out) {
@@ -265,6 +274,11 @@ cudaError_t launch_radii_sort(const PairRec* pairs, const int* n_pair, int* hist
 cudaError_t launch_zero(double* p, long long n, int num_sms, cudaStream_t st) {
     const int vec = (reinterpret_cast<unsigned long long>(p) & 15ull) == 0 ? 1 : 0;
     zero_kernel<<<num_sms * 8, 256, 0, st>>>(p, n, vec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dfix_convert(double* p, long long n, double inv, int num_sms, cudaStream_t st) {
+    dfix_convert_kernel<<<num_sms * 8, 256, 0, st>>>(p, n, inv);
     return cudaGetLastError();
 }
 

@@ -290,11 +290,20 @@ static __device__ __noinline__ void scatter_dxx(const SolveParams& P, const Ball
     const int n_me = G.n_me;
     const int* __restrict__ off = G.pt_off;
     const int* __restrict__ cube = G.pt_cube;
+    const double dfix = P.dfix;
     for (int q = tid; q < n_me; q += nthr) {
         const long long gi = grid_index(N, g, off[q]);
         const double v = vc[cube[q]];
-        atomicAdd(Di + gi, v * phi_j[gi]);
-        if (two) atomicAdd(Dj + gi, v * phi_i[gi]);
+        if (dfix != 0.0) {  // integer adds: the sum is the same in any order
+            atomicAdd(reinterpret_cast<unsigned long long*>(Di + gi),
+                      (unsigned long long)__double2ll_rn(v * phi_j[gi] * dfix));
+            if (two)
+                atomicAdd(reinterpret_cast<unsigned long long*>(Dj + gi),
+                          (unsigned long long)__double2ll_rn(v * phi_i[gi] * dfix));
+        } else {
+            atomicAdd(Di + gi, v * phi_j[gi]);
+            if (two) atomicAdd(Dj + gi, v * phi_i[gi]);
+        }
     }
 }
 

@@ -105,6 +105,11 @@ def test_init_rejects_bad_options(lib):
     o.fixed_residual = 3
     st, ctx = _init(lib, opt=o)
     assert st == -1 and "fixed_residual" in lib.exx_last_error(None).decode()
+    o = lib.exx_default_options()
+    assert o.deterministic == 0
+    o.deterministic = 2
+    st, ctx = _init(lib, opt=o)
+    assert st == -1 and "deterministic" in lib.exx_last_error(None).decode()
 
 
 def test_null_and_destroy_are_safe(lib):

@@ -66,6 +66,28 @@ def test_cfg0_end_to_end(torch, cfg0, precision, solver_kind, cluster_size, lane
         assert np.max(np.abs(out["pairs"]["iters"] - ref["rep_iters"])) <= 2
 
 
+@pytest.mark.parametrize("solver_kind", [1, 2])
+def test_cfg0_deterministic_d_xx(torch, cfg0, solver_kind):
+    """deterministic = 1: D_xx from fixed-point integer atomics meets the gates
+    and repeats bit for bit (the FP64-atomic default need not)."""
+    w, phi, ref = cfg0
+    from paper_1911_10630_gb300.exx import Exx
+    dphi = torch.from_numpy(phi).cuda()
+    dcen = torch.from_numpy(np.ascontiguousarray(w.centers)).cuda()
+    ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=1, solver_kind=solver_kind,
+             deterministic=1)
+    outs = []
+    for _ in range(2):
+        D = torch.empty_like(dphi)
+        e = ex.compute(dphi, dcen, D)
+        outs.append((e, D.cpu().numpy()))
+    ex.close()
+    (e0, D0), (e1, D1) = outs
+    assert e0 == e1 and np.array_equal(D0, D1)
+    assert abs(e0 - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
+    assert d_maxrel(D0, ref["D"]) <= D_GATE_MAXREL
+
+
 @pytest.mark.parametrize("fixed_residual", [1, 2])
 def test_cfg0_residual_paths(torch, cfg0, fixed_residual):
     """The quad map with halo planes with the FP64 stencil for the refinement
