@@ -62,8 +62,13 @@ typedef struct {
                           pairs kept from the previous call (same i and j), moved
                           with the pair's grid centre; other pairs start from
                           zero. 2: the learned guess of the model loaded with
-                          exx_load_guess_model (include/exx_guess.h). 1 and 2
-                          need precision 1, fixed radii and the cluster solver;
+                          exx_load_guess_model (include/exx_guess.h). 3:
+                          polynomial extrapolation over the calls that hold the
+                          pair (Step IV: guesses from earlier MD steps): v1,
+                          2 v1 - v2 or 3 v1 - 3 v2 + v3 from the last one, two
+                          or three calls, each moved with the pair's grid
+                          centre. 1, 2 and 3 need precision 1, fixed radii and
+                          the cluster solver;
                           the stop rule is unchanged, so a start only changes
                           the iteration count.                                  */
     int radii_mode;    /* 0: fixed R_PE / R_ME for all pairs (default).

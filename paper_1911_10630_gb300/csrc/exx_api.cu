@@ -127,6 +127,11 @@ struct exx_ctx {
     PairRec* d_prev_pairs = nullptr;
     long long prev_cap = 0;
     float* d_vcache[2] = {nullptr, nullptr};
+    // warm 3: the potentials and pair lists of the two calls before the previous one
+    float* hv[2] = {nullptr, nullptr};
+    PairRec* hp[2] = {nullptr, nullptr};
+    int hk = 0;  // valid history levels beyond the previous call (0..2)
+    long long hv_pairs = 0, hp_cap = 0;  // capacities of the history buffers
     long long vcache_pairs = 0;
     int parity = 0;
     bool have_prev = false;
@@ -271,6 +276,10 @@ extern "C" void exx_destroy(exx_ctx* c) {
     cudaFree(c->d_prev_pairs);
     cudaFree(c->d_vcache[0]);
     cudaFree(c->d_vcache[1]);
+    cudaFree(c->hv[0]);
+    cudaFree(c->hv[1]);
+    cudaFree(c->hp[0]);
+    cudaFree(c->hp[1]);
     cudaFree(c->d_pow);
     cudaFree(c->d_phase);
     if (c->gnet) {
@@ -325,7 +334,8 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                         "exx_init: with radii_mode 1, r_me must be >= r_pe + max(3, ceil(r_pe/3)) (the largest pair's R_ME)");
         if (o.solver_kind == 2) return fail(nullptr, EXX_EINVAL, "exx_init: radii_mode 1 runs on solver_kind 1");
     }
-    if (o.warm_start < 0 || o.warm_start > 2) return fail(nullptr, EXX_EINVAL, "exx_init: warm_start must be 0, 1 or 2");
+    if (o.warm_start < 0 || o.warm_start > 3)
+        return fail(nullptr, EXX_EINVAL, "exx_init: warm_start must be 0, 1, 2 or 3");
     if (o.warm_start != 0 && (o.precision != 1 || o.radii_mode != 0 || o.solver_kind == 1))
         return fail(nullptr, EXX_EINVAL,
                     "exx_init: warm_start 1 and 2 run on the cluster solver (precision 1, fixed radii, solver_kind 0 or 2)");
@@ -686,7 +696,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(phase clocks)"));
     e = cudaMalloc(&c->d_hist, sizeof(int) * 2 * (size_t)c->n_geo);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(radius histogram)"));
-    e = cudaMalloc(&c->d_scalars, sizeof(int) * 8);
+    e = cudaMalloc(&c->d_scalars, sizeof(int) * 16);  // [8], [9]: pair counts of the extrapolation history
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(scalars)"));
     e = cudaMalloc(&c->d_exx, sizeof(double) * 2);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(exx)"));
@@ -866,8 +876,37 @@ static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double*
         CK(cudaMalloc(&c->d_prev_pairs, sizeof(PairRec) * (size_t)c->cap_pairs), "cudaMalloc(previous pairs)");
         c->prev_cap = c->cap_pairs;
     }
-    P.warm = c->have_prev ? 1 : 0;
+    if (c->opt.warm_start == 3) {  // history for the extrapolation, sized like the previous call's cache
+        const size_t vbytes = sizeof(float) * (size_t)c->vcache_pairs * c->hb.n_pe;
+        for (int h = 0; h < 2; ++h) {
+            if (!c->hv[h] || c->hv_pairs < c->vcache_pairs) {
+                cudaFree(c->hv[h]);
+                c->hv[h] = nullptr;
+                CK(cudaMalloc(&c->hv[h], vbytes), "cudaMalloc(extrapolation history)");
+                c->hk = 0;
+            }
+            if (!c->hp[h] || c->hp_cap < c->prev_cap) {
+                cudaFree(c->hp[h]);
+                c->hp[h] = nullptr;
+                CK(cudaMalloc(&c->hp[h], sizeof(PairRec) * (size_t)c->prev_cap), "cudaMalloc(extrapolation history)");
+                c->hk = 0;
+            }
+        }
+        c->hv_pairs = c->vcache_pairs;
+        c->hp_cap = c->prev_cap;
+        if (!c->have_prev) c->hk = 0;
+    }
+    P.warm = c->have_prev ? (c->opt.warm_start == 3 ? 3 : 1) : 0;
     P.prev_pairs = c->d_prev_pairs;
+    P.xk = c->have_prev ? 1 + c->hk : 0;
+    P.xv[0] = c->d_vcache[c->parity ^ 1];
+    P.xp[0] = c->d_prev_pairs;
+    P.xn[0] = c->d_scalars + 7;
+    for (int h = 0; h < 2; ++h) {
+        P.xv[h + 1] = c->hv[h];
+        P.xp[h + 1] = c->hp[h];
+        P.xn[h + 1] = c->d_scalars + 8 + h;
+    }
     P.n_prev = c->d_scalars + 7;
     P.vprev = c->d_vcache[c->parity ^ 1];
     P.vcur = c->d_vcache[c->parity];
@@ -905,6 +944,23 @@ static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double*
     CK(cudaEventRecord(c->ev[2], st), "cudaEventRecord");
     CK(launch_exx_reduce(c->d_pairs, c->d_scalars, c->d_epair, c->d_exx, st), "E_xx reduction");
     CK(cudaMemcpyAsync(c->h_exx, c->d_exx, sizeof(double), cudaMemcpyDeviceToHost, st), "copy E_xx");
+    if (c->opt.warm_start == 3 && c->have_prev) {
+        // the previous call moves one level back in the history (pointer
+        // swaps; the oldest buffers are recycled for this call's successors)
+        CK(cudaMemcpyAsync(c->d_scalars + 9, c->d_scalars + 8, sizeof(int), cudaMemcpyDeviceToDevice, st),
+           "history counts");
+        CK(cudaMemcpyAsync(c->d_scalars + 8, c->d_scalars + 7, sizeof(int), cudaMemcpyDeviceToDevice, st),
+           "history counts");
+        float* tv = c->hv[1];
+        c->hv[1] = c->hv[0];
+        c->hv[0] = c->d_vcache[c->parity ^ 1];
+        c->d_vcache[c->parity ^ 1] = tv;
+        PairRec* tp = c->hp[1];
+        c->hp[1] = c->hp[0];
+        c->hp[0] = c->d_prev_pairs;
+        c->d_prev_pairs = tp;
+        c->hk = std::min(c->hk + 1, 2);
+    }
     // this call's list becomes the previous one
     CK(cudaMemcpyAsync(c->d_prev_pairs, c->d_pairs, sizeof(PairRec) * (size_t)np, cudaMemcpyDeviceToDevice, st),
        "keep pair list");

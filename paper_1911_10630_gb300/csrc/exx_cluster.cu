@@ -262,6 +262,34 @@ __device__ __noinline__ void cta_warm_insert(const BallGeo& G, const int* __rest
     }
 }
 
+// Polynomial extrapolation from the last m calls (warm 3): v(o) = sum_s
+// coef[s] v_s(o + dlt_s), each v_s read as in cta_warm_insert.
+__device__ __noinline__ void cta_warm_extrapolate(const BallGeo& G, const int* __restrict__ cube,
+                                                  double* __restrict__ vc, int m, const float* const* vold,
+                                                  const int (*dlt)[3], const double* coef, int k0, int k1, int nt) {
+    const int R = G.r_pe, W = 2 * G.r_pe + 1;
+    const int* __restrict__ off = G.pt_off;
+    const int* __restrict__ row_of = G.row_of;
+    const RowRec* __restrict__ rows = G.rows_pe;
+    for (int k = k0 + (int)threadIdx.x; k < k1; k += nt) {
+        const int o = off[k];
+        double acc = 0.0;
+        for (int s = 0; s < m; ++s) {
+            const int x = off_x(o) + dlt[s][0], y = off_y(o) + dlt[s][1], z = off_z(o) + dlt[s][2];
+            int src = k;
+            if (x >= -R && x <= R && y >= -R && y <= R) {
+                const int rr = row_of[(x + R) * W + (y + R)];
+                if (rr >= 0) {
+                    const RowRec Rw = rows[rr];
+                    if (z >= -Rw.zpe && z <= Rw.zpe) src = Rw.pe_start + z + Rw.zpe;
+                }
+            }
+            acc = fma(coef[s], (double)vold[s][src], acc);
+        }
+        vc[cube[k]] = acc;
+    }
+}
+
 // Stores v on the CTA's PE points (FP32) for the next call's warm start.
 __device__ __noinline__ void cta_warm_store(const int* __restrict__ cube, const double* __restrict__ vc,
                                             float* __restrict__ vdst, int k0, int k1, int nt) {
@@ -1260,9 +1288,34 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
         bool conv = true;
         double rn_start = bb;
         if (P.warm && bb > target2 && bb == bb) {
+            // warm 3: extrapolate from the last calls that all hold the pair
+            // (order = their number, up to 3: v1; 2 v1 - v2; 3 v1 - 3 v2 + v3)
+            int xm = 0;
+            int xdl[3][3];
+            const float* xsrc[3];
+            if (P.warm == 3) {
+                for (int h = 0; h < P.xk; ++h) {
+                    const int q = find_prev_pair(P.xp[h], *P.xn[h], pr.i, pr.j);
+                    if (q < 0) break;
+                    const PairRec po = P.xp[h][q];
+                    bool ok = true;
+                    for (int a = 0; a < 3; ++a) {
+                        int d = pr.g[a] - po.g[a];
+                        if (d > P.N[a] / 2) d -= P.N[a];
+                        if (d < -(P.N[a] - 1) / 2) d += P.N[a];
+                        xdl[h][a] = d;
+                        ok = ok && abs(d) <= 3;
+                    }
+                    if (!ok) break;
+                    xsrc[h] = P.xv[h] + (size_t)q * G.n_pe;
+                    xm = h + 1;
+                }
+            }
             // warm 1: the same pair in the previous call's list; warm 2: this
             // pair's learned guess (same list position, no shift)
-            const int prev = P.warm == 2 ? pidx : find_prev_pair(P.prev_pairs, *P.n_prev, pr.i, pr.j);
+            const int prev = P.warm == 3 ? (xm > 0 ? 0 : -1)
+                             : P.warm == 2 ? pidx
+                                           : find_prev_pair(P.prev_pairs, *P.n_prev, pr.i, pr.j);
             if (prev >= 0) {
                 int dlt[3] = {0, 0, 0};
                 if (P.warm == 1) {
@@ -1277,7 +1330,14 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
                 }
                 if (abs(dlt[0]) <= 3 && abs(dlt[1]) <= 3 && abs(dlt[2]) <= 3) {
                     const long long tu = clk ? clock64() : 0;
-                    cta_warm_insert(G, cube, vc, P.vprev + (size_t)prev * G.n_pe, dlt[0], dlt[1], dlt[2], k0, k1, NT);
+                    if (P.warm == 3) {
+                        const double c1[3] = {1.0, 0.0, 0.0}, c2[3] = {2.0, -1.0, 0.0}, c3[3] = {3.0, -3.0, 1.0};
+                        cta_warm_extrapolate(G, cube, vc, xm, xsrc, xdl, xm == 1 ? c1 : (xm == 2 ? c2 : c3), k0, k1,
+                                             NT);
+                    } else {
+                        cta_warm_insert(G, cube, vc, P.vprev + (size_t)prev * G.n_pe, dlt[0], dlt[1], dlt[2], k0, k1,
+                                        NT);
+                    }
                     if (fix) {  // the warm values into the fixed-point copy
                         int o = 0;
                         for (int k = k0 + (int)threadIdx.x; k < k1; k += NT) vfix[cube[k]] = to_fix(vc[cube[k]], s2E, o);

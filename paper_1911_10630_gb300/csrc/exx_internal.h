@@ -119,6 +119,12 @@ struct SolveParams {
     const int* n_prev;            // its length (device)
     const float* vprev;           // [n_prev][n_pe] previous PE potentials
     float* vcur;                  // [n_pair][n_pe] this call's PE potentials (written)
+    // polynomial extrapolation (warm 3): the potentials, pair lists and pair
+    // counts of the last xk calls, newest first (xv[0] = vprev)
+    const float* xv[3];
+    const PairRec* xp[3];
+    const int* xn[3];
+    int xk;
 
     // outputs
     double* e_pair;

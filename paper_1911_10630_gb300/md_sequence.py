@@ -7,7 +7,8 @@ drifts of the centres (N(0, 0.02^2) bohr per component) and 1 % perturbations
 of the exponents; the orbitals are rebuilt on the device between steps
 (untimed). The solver runs the batched mixed-precision path with one of the
 warm starts of exx_options.warm_start: 0 (zero), 1 (the previous step's
-potential of each pair kept from the previous step) or 2 (a learned guess).
+potential of each pair kept from the previous step), 2 (a learned guess) or 3
+(polynomial extrapolation from the last two or three steps).
 
     python -m paper_1911_10630_gb300.md_sequence --steps 20 --warm 1
 """
@@ -58,7 +59,7 @@ def run(steps: int = 20, warm: int = 0, model_blob: bytes = None, seed: int = 0,
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warm", type=int, default=1, choices=[0, 1, 2])
+    ap.add_argument("--warm", type=int, default=1, choices=[0, 1, 2, 3])
     ap.add_argument("--model", default=None, help="model blob for --warm 2")
     args = ap.parse_args()
     blob = open(args.model, "rb").read() if args.model else None

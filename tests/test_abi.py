@@ -106,6 +106,10 @@ def test_init_rejects_bad_options(lib):
     st, ctx = _init(lib, opt=o)
     assert st == -1 and "fixed_residual" in lib.exx_last_error(None).decode()
     o = lib.exx_default_options()
+    o.warm_start = 4
+    st, ctx = _init(lib, opt=o)
+    assert st == -1 and "warm_start" in lib.exx_last_error(None).decode()
+    o = lib.exx_default_options()
     assert o.deterministic == 0
     o.deterministic = 2
     st, ctx = _init(lib, opt=o)
