@@ -6,8 +6,8 @@
  * it does not use a network. This library adds one: a 3D U-Net that maps the
  * pair density rho_ij on a cube of S^3 grid points centred on the pair's grid
  * point g_ij to a guess of v_ij on the same cube. The solver's
- * warm_start = 2 option (exx.h) runs it before the CG, which stays the judge
- * of the result (the stop rule is relative to ||b||, so a poor guess costs
+ * warm_start = 2 option (exx.h) runs it before the CG, which still decides
+ * the result (the stop rule is relative to ||b||, so a poor guess costs
  * iterations, never accuracy).
  *
  * Network: 4 levels of widths 16/32/64/128, two 3x3x3 convolutions with ReLU
