@@ -127,6 +127,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over the ranks of the default process group (any backend)."""
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws: int, units_per_rank: int, steps: int, max_ms: float) -> float:
+    """Whole-job units per second: every rank processed units_per_rank per step
+    (replicas), timed by the slowest rank."""
+    return ws * units_per_rank * steps / (max_ms / 1e3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -285,13 +299,11 @@ def main():
         barrier()
     total_ms = ev0.elapsed_time(ev1)
     if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, dev)
     st = ex.stats()
     pairs = ex.pairs()
     n_pair = st["n_pair"]
-    value = ws * n_pair * args.steps / (total_ms / 1e3)
+    value = job_rate(ws, n_pair, args.steps, total_ms)
     n_pe, n_me = ex.ball_size()
     alg = _algorithmic(pairs, st, n_pe, n_me, args.precision)
     kern_ms = statistics.mean(solve_ms)
