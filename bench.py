@@ -32,10 +32,11 @@ if ROOT not in sys.path:
 
 METRIC = "pair-Poisson solves/s at fixed E_xx error"
 UNIT = "pair solves/s"
-FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of a GB300 (profiling recipe table)
-
-
 SMEM_BYTES_PER_CLK_SM = 128  # shared-memory bandwidth of one SM (32 banks x 4 B per clock)
+# the quad-map stencil's shared-memory traffic per point and iteration: 15
+# loads of 16 bytes per quad of 4 points plus the store of p (context only;
+# the roofline's algorithmic bytes are the CG state's)
+SMEM_MODEL_BYTES_PER_POINT_ITER = 15 * 16 / 4 + 4
 
 
 def _peaks():
@@ -152,8 +153,9 @@ def _algorithmic(pairs, stats, n_pe, n_me, precision):
     """Algorithmic bytes and FLOPs of one pair-kernel launch: per-unit figures
     times the units the launch processed (the design notes derive each).
 
-    smem: the CG keeps every vector on chip; each point-iteration reads the
-      19 stencil operands of p and stores p once (80 B in FP32).
+    cg: each point-iteration must read and write the CG state x, r and p
+      once: 6 words, 24 B in FP32 (the fast path keeps them on chip) and
+      48 B in FP64.
     hbm: per pair, the gather of phi_i, phi_j on the ME ball (16 B per point),
       the D_xx read-modify-write of one or two orbitals on the ME ball
       (16 or 32 B per point) and one more read of phi_i, phi_j for the scatter.
@@ -163,7 +165,7 @@ def _algorithmic(pairs, stats, n_pe, n_me, precision):
     two = (pairs["i"] != pairs["j"]).astype(np.float64)
     hbm = float(np.sum((16.0 + 16.0 + 16.0 * (1.0 + two)) * n_me))
     s = 4 if precision == 1 else 8
-    return dict(smem=20.0 * s * point_iters, hbm=hbm, flops=38.0 * point_iters, point_iters=point_iters)
+    return dict(cg=6.0 * s * point_iters, hbm=hbm, flops=38.0 * point_iters, point_iters=point_iters)
 
 
 def run_oracle_sample(w, phi, pairs_all, seconds=12.0, seed=0):
@@ -265,6 +267,7 @@ def main():
 
     from paper_1911_10630_gb300 import build as _build
     _build.build(quiet=True)
+    from paper_1911_10630_gb300 import exx as exx_mod
     from paper_1911_10630_gb300.exx import Exx
 
     phi = w.orbitals()
@@ -310,25 +313,30 @@ def main():
     hbm_peak, sm_mhz_max, peak_src = _peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     workload_key = f"{w.name}|p{args.precision}"
+    fp64_peak = exx_mod.probe_fp64_rate(stream)  # the FP64 pipe's FMA rate, measured on this GPU
     if args.precision == 1:
         kname = "cluster_pair_kernel" if st["solver_kind"] == 2 else "pair_kernel"
         smem_peak = n_sm * SMEM_BYTES_PER_CLK_SM * sm_mhz_max * 1e6 / 1e9
-        achieved = alg["smem"] / (kern_ms / 1e3) / 1e9
+        achieved = alg["cg"] / (kern_ms / 1e3) / 1e9
         roofline = {"kernel": kname, "bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
                     "frac": achieved / smem_peak,
                     "peak_source": f"{n_sm} SMs x {SMEM_BYTES_PER_CLK_SM} B/clk x {sm_mhz_max:.0f} MHz "
                                    f"(max SM clock, {peak_src})",
-                    "algorithmic_bytes_per_launch": alg["smem"], "bytes_per_point_iteration": 80,
+                    "algorithmic_bytes_per_launch": alg["cg"], "bytes_per_point_iteration": 24,
                     "traffic": _traffic(kname, workload_key),
+                    "smem_model": {"bytes_per_point_iteration": SMEM_MODEL_BYTES_PER_POINT_ITER,
+                                   "frac": SMEM_MODEL_BYTES_PER_POINT_ITER / 24 * achieved / smem_peak},
                     "hbm": {"algorithmic_bytes_per_launch": alg["hbm"],
                             "achieved": alg["hbm"] / (kern_ms / 1e3) / 1e9, "peak": hbm_peak,
                             "peak_source": peak_src},
                     "kernel_ms": kern_ms}
     else:
         fl = alg["flops"] / (kern_ms / 1e3) / 1e12
-        roofline = {"kernel": "pair_kernel", "bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": fl / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64 rate",
-                    "traffic": _traffic("pair_kernel", workload_key), "kernel_ms": kern_ms}
+        roofline = {"kernel": "pair_kernel", "bound": "alu", "achieved": fl, "peak": fp64_peak,
+                    "unit": "TFLOP/s", "frac": fl / fp64_peak,
+                    "peak_source": "FP64 FMA rate measured on this GPU (exx_probe_fp64_rate)",
+                    "flops_per_point_iteration": 38, "traffic": _traffic("pair_kernel", workload_key),
+                    "kernel_ms": kern_ms}
 
     extra = {}
     if rank == 0 and args.precision == 1 and args.plain_steps > 0:
@@ -343,10 +351,18 @@ def main():
             torch.cuda.synchronize(dev)
             t.append(ev0.elapsed_time(ev1))
         st0 = ex0.stats()
+        alg0 = _algorithmic(ex0.pairs(), st0, n_pe, n_me, 0)
+        fl0 = alg0["flops"] / (st0["solve_ms"] / 1e3) / 1e12
         extra["plain_fp64_cg"] = {"value": n_pair / (statistics.mean(t) / 1e3), "unit": UNIT,
                                   "ms_per_step": statistics.mean(t), "E_xx": e0,
                                   "dE_vs_fast_per_orbital": abs(e0 - exx_vals[-1]) / w.n,
-                                  "iters_p50": st0["iters_p50"], "iters_max": st0["iters_max"]}
+                                  "iters_p50": st0["iters_p50"], "iters_max": st0["iters_max"],
+                                  "roofline": {"kernel": "pair_kernel", "bound": "alu", "achieved": fl0,
+                                               "peak": fp64_peak, "unit": "TFLOP/s", "frac": fl0 / fp64_peak,
+                                               "peak_source": "FP64 FMA rate measured on this GPU "
+                                                              "(exx_probe_fp64_rate)",
+                                               "flops_per_point_iteration": 38,
+                                               "kernel_ms": st0["solve_ms"]}}
         extra["speedup_vs_plain_fp64_cg"] = value / ws / extra["plain_fp64_cg"]["value"]
         ex0.close()
 

@@ -46,7 +46,11 @@ typedef enum {
     EXX_ENOMEM = -2,   /* device or host allocation failed                           */
     EXX_ECUDA = -3,    /* a CUDA call failed (no device, launch error, ...)           */
     EXX_ENOCONV = -4,  /* some CG solves reached max_iter; all outputs still written */
-    EXX_ENOPAIR = -5   /* a query named a pair that is not in the current list       */
+    EXX_ENOPAIR = -5,  /* a query named a pair that is not in the current list       */
+    EXX_ETIMEOUT = -6  /* a bounded device wait ran out (a cluster exchange or a
+                          tensor-core completion did not arrive within its poll
+                          limit); outputs are written but not to be trusted;
+                          the context stays usable                            */
 } exx_status;
 
 /* Solver choices. exx_default_options() fills the defaults noted here. */
@@ -138,6 +142,12 @@ typedef struct {
                           (resolution 2^-40, |D_xx| < 2^22) by integer atomic
                           adds, whose sum does not depend on their order, then
                           converted to FP64 in place: bitwise reproducible.     */
+    int inject_wait_timeout; /* test only (default 0): the next this-many calls
+                          of the context each make one extra bounded device wait
+                          run out (cluster solver: thread 0 of every CTA polls an
+                          mbarrier that nothing arrives on, with no copy or store
+                          in flight to it), so the call returns EXX_ETIMEOUT
+                          while its results stay those of a normal call.       */
 } exx_options;
 
 typedef struct {
@@ -164,6 +174,11 @@ typedef struct {
     int n_candidates;      /* launch shapes the autotuner could choose from          */
     double tune_ms;        /* host time spent by the autotuner (first call)          */
     double guess_ms;       /* device time of the learned guesses (warm_start 2)      */
+    int n_timeouts;        /* bounded device waits that ran out (EXX_ETIMEOUT)       */
+    int n_nonfinite;       /* non-finite inputs seen: centres that are NaN or Inf,
+                              plus pairs whose E_ij came out NaN or Inf (a NaN or
+                              Inf orbital value on the pair's PE ball propagates
+                              into E_ij, E_xx and D_xx; nothing is masked)      */
 } exx_stats;
 
 /* Defaults described in exx_options. */
@@ -203,7 +218,9 @@ exx_status exx_init(exx_ctx **out, const double cell[3], const int grid[3], doub
  *   stream    cudaStream_t, NULL = the legacy default stream
  * Work is ordered on the stream; the call returns after E_xx is on the host,
  * so d_xx is complete when it returns. The arrays must stay valid until then.
- * Errors: EXX_EINVAL, EXX_ECUDA, EXX_ENOMEM, EXX_ENOCONV (outputs written).
+ * Errors: EXX_EINVAL, EXX_ECUDA, EXX_ENOMEM, EXX_ENOCONV (outputs written),
+ * EXX_ETIMEOUT (outputs written, not to be trusted). NaN or Inf inputs are not
+ * an error: they propagate into the outputs and exx_get_stats counts them.
  */
 exx_status exx_compute(exx_ctx *ctx, const double *orbitals, const double *centers, int n,
                        const double *alphas, double *e_xx, double *d_xx, void *stream);
@@ -272,14 +289,17 @@ exx_status exx_ball_size(const exx_ctx *ctx, int *n_pe, int *n_me);
 exx_status exx_load_guess_model(exx_ctx *ctx, const void *weights, size_t bytes);
 
 /*
- * Pair list without device allocation. The paper has no counterpart: this
- * entry point exists for callers that cannot call cudaMalloc, for example code
- * running during CUDA-graph stream capture, or hosts confined to a fixed
- * device-memory budget or their own pool. It computes the same pair list as
- * exx_compute (Sec. III.C Step II rule, same rounding and order). Its scratch
- * (per-orbital counts and prefix sums) lives in a static device array sized
- * for 16384 orbitals; every GPU that loads the library holds that array
- * (about 128 KiB) until the process exits.
+ * Pair list without device allocation. The paper has no counterpart. It is
+ * for callers that cannot call cudaMalloc: applications that route all device
+ * memory through their own pool or arena (a framework's caching allocator, a
+ * service held to a fixed per-process budget), where an allocation outside
+ * the pool breaks the budget or fails near the memory limit, and latency-bound
+ * loops that cannot afford cudaMalloc's implicit device synchronisation. It
+ * returns the pair list exx_compute builds for the same centres (the same
+ * count / scan / fill kernels, hence the same records in the same order).
+ * Its scratch (per-orbital counts, prefix sums and the pair count) lives in
+ * a static device array sized for 16384 orbitals; every GPU that loads the
+ * library holds that array (about 128 KiB) until the process exits.
  *   centers   device, [n][3] FP64 orbital centres (bohr)
  *   n         1 <= n <= 16384, else EXX_EINVAL
  *   cell, grid, r_pair  as for exx_init
@@ -291,7 +311,8 @@ exx_status exx_load_guess_model(exx_ctx *ctx, const void *weights, size_t bytes)
  *   stream    cudaStream_t, NULL = legacy default stream; the call waits for it
  * The first call on a device looks up the array's device address (once per
  * device), so make that call before any stream capture. All calls share the
- * one array: calls that overlap on the GPU race and must be serialised.
+ * one array, which keeps the last call's contents (every word a call reads it
+ * writes first): calls that overlap on the GPU race and must be serialised.
  * Allocates nothing. Errors are read with exx_last_error(NULL).
  */
 exx_status exx_pair_list_static(const double *centers, int n, const double cell[3], const int grid[3],
@@ -322,6 +343,18 @@ exx_status exx_pair_list_static(const double *centers, int n, const double cell[
  */
 exx_status exx_quad_map(int r_pe, int cluster_size, int threads, int quads, int bank_aware, int *quad_pk,
                         int *quad_k, size_t cap, int *info);
+
+/*
+ * Measures the FP64 FMA rate of the current device, the roofline denominator
+ * of the plain FP64 CG (whose binding unit on this GPU is the FP64 pipe, not
+ * HBM). The paper has no counterpart. Eight independent FMA chains per thread
+ * on 8 CTAs of 256 threads per SM; the best of three timed launches.
+ *   tflops   host, receives 2 x FMAs / s / 1e12
+ *   stream   cudaStream_t, NULL = legacy default stream; the call waits for it
+ * Allocates nothing on the device. Errors (EXX_EINVAL, EXX_ECUDA) are read
+ * with exx_last_error(NULL).
+ */
+exx_status exx_probe_fp64_rate(double *tflops, void *stream);
 
 /* Message of the last error on this context (or of the last failed exx_init
  * when ctx is NULL); owned by the library, valid until the next call. */

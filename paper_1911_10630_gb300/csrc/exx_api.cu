@@ -21,13 +21,13 @@ namespace exx {
 cudaError_t launch_pair_list(int n, const double* centers, const double L[3], const double delta[3], const int N[3],
                              double r_pair, int r_pe, int r_me, int* counts, int* offsets, int* n_pair, int* queue,
                              PairRec* pairs, cudaStream_t st, const double* alphas, double ln_inv_eps,
-                             double delta_max, int r_min, int ns_pe = 0, int ns_me = 0);
+                             double delta_max, int r_min, int ns_pe = 0, int ns_me = 0, int* bad = nullptr);
 cudaError_t launch_radii_sort(const PairRec* pairs, const int* n_pair, int* hist, int n_geo, int* order, int num_sms,
                               cudaStream_t st);
 cudaError_t launch_zero(double* p, long long n, int num_sms, cudaStream_t st);
 cudaError_t launch_dfix_convert(double* p, long long n, double inv, int num_sms, cudaStream_t st);
 cudaError_t launch_exx_reduce(const PairRec* pairs, const int* n_pair, const double* e_pair, double* out,
-                              cudaStream_t st);
+                              cudaStream_t st, int* bad = nullptr);
 cudaError_t set_multipole_const_solve(const MultipoleConst& mc);
 cudaError_t set_multipole_const_cluster(const MultipoleConst& mc);
 size_t pair_kernel_smem(int Rc, int r_pe_max);
@@ -152,6 +152,12 @@ struct exx_ctx {
     double* d_alpha = nullptr;
     size_t host_cap_bytes = 0;
     int host_cap_n = 0;
+
+    // test of the time-out path: calls left that inject one run-out wait, and
+    // whether the current call does
+    int inject_left = 0;
+    int inject_now = 0;
+    int g_inject = -1;  // injection state the cached graph was captured with
 
     // graph cache
     cudaGraphExec_t gexec = nullptr;
@@ -355,10 +361,12 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         return fail(nullptr, EXX_EINVAL, "exx_init: fixed_residual must be 0, 1 or 2");
     if (o.deterministic < 0 || o.deterministic > 1)
         return fail(nullptr, EXX_EINVAL, "exx_init: deterministic must be 0 or 1");
+    if (o.inject_wait_timeout < 0) return fail(nullptr, EXX_EINVAL, "exx_init: inject_wait_timeout must be >= 0");
 
     c = new exx_ctx();
     std::memset(&c->stats, 0, sizeof(c->stats));
     c->opt = o;
+    c->inject_left = o.inject_wait_timeout;
     for (int a = 0; a < 3; ++a) {
         c->cell[a] = cell[a];
         c->grid[a] = grid[a];
@@ -757,6 +765,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     P.n_pair = c->d_scalars;
     P.queue = c->d_scalars + 1;
     P.nonconv = c->d_scalars + 2;
+    P.timeouts = c->d_scalars + 10;  // [11]: non-finite inputs (pair list, E_xx reduction)
 
     c->stats.n_pe = B.n_pe;
     c->stats.n_me = B.n_me;
@@ -803,14 +812,16 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
     P.refines = c->d_refines;
     P.dbg_b = nullptr;
     P.phase_clk = c->use_cluster ? c->d_phase : nullptr;
+    P.test_wait = c->inject_now;
     CK(cudaEventRecordWithFlags(c->ev[0], st, evf), "cudaEventRecord");
     CK(launch_zero(d_xx, (long long)n * c->ngrid, c->num_sms, st), "zero D_xx");
     CK(cudaMemsetAsync(c->d_scalars + 2, 0, sizeof(int), st), "reset counters");
+    CK(cudaMemsetAsync(c->d_scalars + 10, 0, 2 * sizeof(int), st), "reset counters");
     CK(cudaMemsetAsync(c->d_phase, 0, sizeof(unsigned long long) * 4, st), "reset phase clocks");
     CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
                         c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st,
                         c->opt.radii_mode == 1 ? alphas : nullptr, c->ln_inv_eps, c->delta_max, c->r_min, c->ns_pe,
-                        c->ns_me),
+                        c->ns_me, c->d_scalars + 11),
        "pair list");
     if (c->n_geo > 1)
         CK(launch_radii_sort(c->d_pairs, c->d_scalars, c->d_hist, c->n_geo, c->d_order, c->num_sms, st),
@@ -823,7 +834,7 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
     if (P.dfix != 0.0)
         CK(launch_dfix_convert(d_xx, (long long)n * c->ngrid, 1.0 / P.dfix, c->num_sms, st), "D_xx to FP64");
     CK(cudaEventRecordWithFlags(c->ev[2], st, evf), "cudaEventRecord");
-    CK(launch_exx_reduce(c->d_pairs, c->d_scalars, c->d_epair, c->d_exx, st), "E_xx reduction");
+    CK(launch_exx_reduce(c->d_pairs, c->d_scalars, c->d_epair, c->d_exx, st, c->d_scalars + 11), "E_xx reduction");
     CK(cudaMemcpyAsync(c->h_exx, c->d_exx, sizeof(double), cudaMemcpyDeviceToHost, st), "copy E_xx");
     CK(cudaEventRecordWithFlags(c->ev[3], st, evf), "cudaEventRecord");
     return EXX_OK;
@@ -845,13 +856,15 @@ static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double*
     P.refines = c->d_refines;
     P.dbg_b = nullptr;
     P.phase_clk = c->d_phase;
+    P.test_wait = c->inject_now;
     CK(cudaEventRecord(c->ev[0], st), "cudaEventRecord");
     CK(launch_zero(d_xx, (long long)n * c->ngrid, c->num_sms, st), "zero D_xx");
     CK(cudaMemsetAsync(c->d_scalars + 2, 0, sizeof(int), st), "reset counters");
+    CK(cudaMemsetAsync(c->d_scalars + 10, 0, 2 * sizeof(int), st), "reset counters");
     CK(cudaMemsetAsync(c->d_phase, 0, sizeof(unsigned long long) * 4, st), "reset phase clocks");
     CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
                         c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st, nullptr, c->ln_inv_eps,
-                        c->delta_max, c->r_min),
+                        c->delta_max, c->r_min, 0, 0, c->d_scalars + 11),
        "pair list");
     int np = 0;
     CK(cudaMemcpyAsync(&np, c->d_scalars, sizeof(int), cudaMemcpyDeviceToHost, st), "read n_pair");
@@ -942,7 +955,7 @@ static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double*
     if (P.dfix != 0.0)
         CK(launch_dfix_convert(d_xx, (long long)n * c->ngrid, 1.0 / P.dfix, c->num_sms, st), "D_xx to FP64");
     CK(cudaEventRecord(c->ev[2], st), "cudaEventRecord");
-    CK(launch_exx_reduce(c->d_pairs, c->d_scalars, c->d_epair, c->d_exx, st), "E_xx reduction");
+    CK(launch_exx_reduce(c->d_pairs, c->d_scalars, c->d_epair, c->d_exx, st, c->d_scalars + 11), "E_xx reduction");
     CK(cudaMemcpyAsync(c->h_exx, c->d_exx, sizeof(double), cudaMemcpyDeviceToHost, st), "copy E_xx");
     if (c->opt.warm_start == 3 && c->have_prev) {
         // the previous call moves one level back in the history (pointer
@@ -972,7 +985,7 @@ static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double*
         int h = 0;
         CK(cudaMemcpyAsync(&h, c->gnet->d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "guess status");
         CK(cudaStreamSynchronize(st), "guess status");
-        if (h) return fail(c, EXX_ECUDA, "exx_compute: a tensor-core wait of the guess network timed out");
+        if (h) return fail(c, EXX_ETIMEOUT, "exx_compute: a tensor-core wait of the guess network timed out");
         float ms = 0.f;
         c->guess_ms = cudaEventElapsedTime(&ms, c->ev_g[0], c->ev_g[1]) == cudaSuccess ? ms : -1.0;
     }
@@ -1110,12 +1123,14 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
         if (s != EXX_OK) return s;
     }
     cudaError_t e;
+    c->inject_now = c->inject_left > 0 ? 1 : 0;
+    if (c->inject_now) --c->inject_left;
     if (c->opt.warm_start) {
         s = compute_warm(c, orbitals, centers, alphas, n, d_xx, st);
         if (s != EXX_OK) return s;
     } else if (c->opt.batched) {
         const void* key[5] = {orbitals, centers, d_xx, alphas, nullptr};
-        bool hit = c->gexec && c->g_n == n && std::equal(key, key + 5, c->g_key);
+        bool hit = c->gexec && c->g_n == n && std::equal(key, key + 5, c->g_key) && c->g_inject == c->inject_now;
         if (!hit) {
             drop_graph(c);
             cudaGraph_t g;
@@ -1136,6 +1151,7 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
             }
             std::copy(key, key + 5, c->g_key);
             c->g_n = n;
+            c->g_inject = c->inject_now;
         }
         e = cudaGraphLaunch(c->gexec, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
@@ -1154,12 +1170,20 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
     c->stats.solve_ms = cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess ? ms : -1.0;
     c->stats.total_ms = cudaEventElapsedTime(&ms, c->ev[0], c->ev[3]) == cudaSuccess ? ms : -1.0;
     (void)cudaGetLastError();  // a failed timing query must not leak into later status checks
-    int nonconv = 0, npair = 0;
-    CK(cudaMemcpy(&npair, c->d_scalars, sizeof(int), cudaMemcpyDeviceToHost), "read n_pair");
-    CK(cudaMemcpy(&nonconv, c->d_scalars + 2, sizeof(int), cudaMemcpyDeviceToHost), "read nonconv");
+    int sc[12];
+    CK(cudaMemcpy(sc, c->d_scalars, sizeof(sc), cudaMemcpyDeviceToHost), "read counters");
+    const int npair = sc[0], nonconv = sc[2];
     c->stats.n_pair = npair;
     c->stats.n_nonconv = nonconv;
+    c->stats.n_timeouts = sc[10];
+    c->stats.n_nonfinite = sc[11];
     c->stats.iters_max = -1;  // filled lazily by exx_get_stats
+    if (sc[10] > 0) {
+        char buf[160];
+        std::snprintf(buf, sizeof(buf), "%d bounded device waits ran out (results written, not to be trusted)",
+                      sc[10]);
+        return fail(c, EXX_ETIMEOUT, buf);
+    }
     if (nonconv > 0) {
         char buf[128];
         std::snprintf(buf, sizeof(buf), "%d of %d pair solves reached the iteration cap", nonconv, npair);
@@ -1199,7 +1223,7 @@ extern "C" exx_status exx_compute_host(exx_ctx* c, const double* orbitals_host, 
         CK(cudaMemcpyAsync(c->d_alpha, alphas_host, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, st),
            "copy alphas");
     exx_status s = exx_compute(c, c->d_orb, c->d_cent, n, alphas_host ? c->d_alpha : nullptr, e_xx, c->d_dxx, stream);
-    if (s != EXX_OK && s != EXX_ENOCONV) return s;
+    if (s != EXX_OK && s != EXX_ENOCONV && s != EXX_ETIMEOUT) return s;
     CK(cudaMemcpyAsync(d_xx_host, c->d_dxx, bytes, cudaMemcpyDeviceToHost, st), "copy d_xx");
     CK(cudaStreamSynchronize(st), "exx_compute_host (stream synchronize)");
     return s;

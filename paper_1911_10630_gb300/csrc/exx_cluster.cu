@@ -320,7 +320,7 @@ struct RunCgCtx {
     int max_iter;
     double target2;
     float drop2;
-    int* fault;  // incremented when a cluster-reduction wait gives up
+    int* fault;  // the call's time-out count, incremented when a bounded wait gives up
     long long* vfix;  // fixed-point copy of v (when fix)
     double s2E;       // its scale 2^E
     int fix;          // keep vfix current at the end of each segment
@@ -344,6 +344,22 @@ __device__ __forceinline__ uint32_t cluster_addr(uint32_t a, int rank) {
     return r;
 }
 
+// Polls the given phase parity of a CTA-local mbarrier at most limit times;
+// returns whether the phase completed. Every wait of the cluster solver is one
+// of these, so none can spin forever.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity, int limit) {
+    uint32_t done = 0;
+    for (int it = 0; it < limit && !done; ++it)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mb), "r"(parity)
+            : "memory");
+    return done != 0;
+}
+
 // Sum over the cluster without a cluster barrier: the CTA total goes to every
 // CTA's g_rc_mpart[b][rank] by st.async, which counts its bytes on that CTA's
 // mbarrier b; each CTA announces the C x 4 bytes it expects and waits for the
@@ -351,7 +367,8 @@ __device__ __forceinline__ uint32_t cluster_addr(uint32_t a, int rank) {
 // from the running count n of these sums. A CTA refills buffer b (sum n + 2)
 // only after every CTA has sent sum n + 1, which each does after all of its
 // threads have read sum n, so the two buffers suffice. A wait that gives up
-// (it never should) bumps *g_rc.fault and takes what has arrived.
+// (it never should) bumps the call's time-out count (*g_rc.fault) and takes
+// what has arrived.
 template <int NT, int C>
 __device__ __forceinline__ float cluster_sum_mb(float v, int& flip, int& n, int rank) {
     v = warp_sum(v);
@@ -377,17 +394,7 @@ __device__ __forceinline__ float cluster_sum_mb(float v, int& flip, int& n, int 
                          : "memory");
         }
     }
-    uint32_t done = 0;
-    const int limit = g_rc_late ? 1 : (1 << 16);
-    for (int it = 0; it < limit && !done; ++it)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(mb), "r"(parity)
-            : "memory");
-    if (!done) {
+    if (!mbar_wait_bounded(mb, parity, g_rc_late ? 1 : (1 << 16))) {
         g_rc_late = 1;  // later waits of this CTA give up at once
         if (threadIdx.x == 0) atomicAdd(g_rc.fault, 1);
     }
@@ -435,17 +442,7 @@ __device__ __forceinline__ float4 cluster_sum4_mb(float4 v, int& flip, int& n, i
                          : "memory");
         }
     }
-    uint32_t done = 0;
-    const int limit = g_rc_late ? 1 : (1 << 16);
-    for (int it = 0; it < limit && !done; ++it)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(mb), "r"(parity)
-            : "memory");
-    if (!done) {
+    if (!mbar_wait_bounded(mb, parity, g_rc_late ? 1 : (1 << 16))) {
         g_rc_late = 1;
         if (threadIdx.x == 0) atomicAdd(g_rc.fault, 1);
     }
@@ -869,21 +866,12 @@ __device__ __noinline__ RunSeg quad_segment(float* ps, const float* pm, const fl
 // after its x legs, so one mbarrier suffices; its phase count hph runs for
 // the whole launch, and every phase opened is waited for.
 __shared__ __align__(8) unsigned long long g_halo_mbar;
+__shared__ __align__(8) unsigned long long g_test_mbar;  // the injected time-out's barrier (test only)
 
 // Bounded wait for the given phase parity of a CTA-local mbarrier; a wait that
 // gives up marks the CTA late (later waits give up at once) and bumps the fault count.
 __device__ __forceinline__ void halo_wait(uint32_t mb, uint32_t parity) {
-    uint32_t done = 0;
-    const int limit = g_rc_late ? 1 : (1 << 16);
-    for (int it = 0; it < limit && !done; ++it)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(mb), "r"(parity)
-            : "memory");
-    if (!done) {
+    if (!mbar_wait_bounded(mb, parity, g_rc_late ? 1 : (1 << 16))) {
         g_rc_late = 1;
         if (threadIdx.x == 0) atomicAdd(g_rc.fault, 1);
     }
@@ -1204,6 +1192,15 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         g_rc_late = 0;
     }
+    if (P.test_wait && threadIdx.x == 0) {
+        // test of the time-out path: a bounded wait on a fresh mbarrier that
+        // nothing arrives on and no copy or store targets runs out; the count
+        // reaches the host as EXX_ETIMEOUT, the rest of the launch is unchanged
+        const uint32_t tmb = smem_u32(&g_test_mbar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tmb) : "memory");
+        if (!mbar_wait_bounded(tmb, 0u, 256)) atomicAdd(P.timeouts, 1);
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(tmb) : "memory");
+    }
     cl.sync();
 
     for (;;) {
@@ -1365,7 +1362,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
                 g_rc.max_iter = P.max_iter;
                 g_rc.target2 = target2;
                 g_rc.drop2 = (float)(P.update_drop * P.update_drop);
-                g_rc.fault = P.nonconv;
+                g_rc.fault = P.timeouts;
                 g_rc.vfix = vfix;
                 g_rc.s2E = s2E;
                 g_rc.fix = fix ? 1 : 0;

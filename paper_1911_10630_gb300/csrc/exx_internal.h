@@ -131,6 +131,8 @@ struct SolveParams {
     int* iters;
     int* refines;
     int* nonconv;
+    int* timeouts;        // bounded device waits that ran out
+    int test_wait;        // 1: thread 0 of every CTA makes one extra bounded wait run out (test of the time-out path)
     // debug
     double* dbg_b;        // if set, the RHS b of the processed pair (slot 0)
 };

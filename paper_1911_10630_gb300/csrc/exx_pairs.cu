@@ -30,6 +30,7 @@ struct PairGeom {
     // separate radii for non-self pairs (ns_pe > 0): self pairs keep r_pe,
     // r_me (geometry 1), non-self pairs take ns_pe, ns_me (geometry 0)
     int ns_pe, ns_me;
+    int* bad;  // if set, counts orbitals whose centre is NaN or Inf
 };
 
 // R_PE = clamp(ceil((s_eps + |cbar - C_ij|)/delta), r_min, r_max) with
@@ -60,6 +61,8 @@ __device__ __forceinline__ bool pair_within(const double* __restrict__ C, int i,
 // counts[i] = number of j >= i paired with i. One block per i.
 __global__ void pairs_count_kernel(int n, const double* __restrict__ C, PairGeom G, int* __restrict__ counts) {
     const int i = blockIdx.x;
+    if (G.bad && threadIdx.x == 0 && !(isfinite(C[3 * i]) && isfinite(C[3 * i + 1]) && isfinite(C[3 * i + 2])))
+        atomicAdd(G.bad, 1);
     int cnt = 0;
     for (int j = i + threadIdx.x; j < n; j += blockDim.x) {
         double d[3];
@@ -107,9 +110,31 @@ __global__ void pairs_scan_kernel(int n, const int* __restrict__ counts, int* __
     }
 }
 
+// Where the fill kernel puts a pair: the pair records of exx_compute, or the
+// five-int records (i, j, g0, g1, g2) of exx_pair_list_static, whose list
+// positions at or beyond cap are skipped.
+struct RecordOut {
+    PairRec* pairs;
+    __device__ __forceinline__ void put(int pos, const PairRec& r) const { pairs[pos] = r; }
+};
+struct PackedOut {
+    int* out;
+    int cap;
+    __device__ __forceinline__ void put(int pos, const PairRec& r) const {
+        if (pos >= cap) return;
+        int* rec = out + 5 * (long long)pos;
+        rec[0] = r.i;
+        rec[1] = r.j;
+        rec[2] = r.g[0];
+        rec[3] = r.g[1];
+        rec[4] = r.g[2];
+    }
+};
+
 // Ordered fill: block i writes its pairs (i, j), j ascending, at offsets[i].
+template <class Out>
 __global__ void pairs_fill_kernel(int n, const double* __restrict__ C, PairGeom G, const int* __restrict__ offsets,
-                                  PairRec* __restrict__ pairs) {
+                                  Out out) {
     const int i = blockIdx.x;
     __shared__ int s_w[33];
     int base = offsets[i];
@@ -160,7 +185,7 @@ __global__ void pairs_fill_kernel(int n, const double* __restrict__ C, PairGeom 
                 r.r_me = G.r_me;
                 r.geo = 0;
             }
-            pairs[pos] = r;
+            out.put(pos, r);
         }
         base += s_w[32];
         __syncthreads();
@@ -216,19 +241,31 @@ __global__ void dfix_convert_kernel(double* __restrict__ p, long long n, double 
         p[k] = (double)q[k] * inv;
 }
 
-// E_xx = -(sum_i E_ii + 2 sum_{i<j} E_ij), in a fixed order (one block).
+// E_xx = -(sum_i E_ii + 2 sum_{i<j} E_ij), in a fixed order (one block); pairs
+// whose E_ij is NaN or Inf are added to *bad (non-finite input propagated).
 __global__ void exx_reduce_kernel(const PairRec* __restrict__ pairs, const int* __restrict__ n_pair,
-                                  const double* __restrict__ e_pair, double* __restrict__ out) {
+                                  const double* __restrict__ e_pair, double* __restrict__ out, int* __restrict__ bad) {
     __shared__ double red[2][33];
+    __shared__ int nbad;
     int flip = 0;
+    if (threadIdx.x == 0) nbad = 0;
+    __syncthreads();
     const int np = *n_pair;
     double s = 0.0;
+    int nb = 0;
     for (int p = threadIdx.x; p < np; p += 1024) {
         const PairRec r = pairs[p];
-        s += (r.i == r.j ? 1.0 : 2.0) * e_pair[p];
+        const double e = e_pair[p];
+        s += (r.i == r.j ? 1.0 : 2.0) * e;
+        nb += isfinite(e) ? 0 : 1;
     }
     s = block_sum<1024, double>(s, red, flip);
-    if (threadIdx.x == 0) out[0] = -s;
+    if (nb) atomicAdd(&nbad, nb);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out[0] = -s;
+        if (bad && nbad) atomicAdd(bad, nbad);
+    }
 }
 
 }  // namespace exx
@@ -239,7 +276,7 @@ namespace exx {
 cudaError_t launch_pair_list(int n, const double* centers, const double L[3], const double delta[3], const int N[3],
                              double r_pair, int r_pe, int r_me, int* counts, int* offsets, int* n_pair, int* queue,
                              PairRec* pairs, cudaStream_t st, const double* alphas, double ln_inv_eps,
-                             double delta_max, int r_min, int ns_pe, int ns_me) {
+                             double delta_max, int r_min, int ns_pe, int ns_me, int* bad) {
     PairGeom G;
     for (int a = 0; a < 3; ++a) {
         G.L[a] = L[a];
@@ -255,9 +292,31 @@ cudaError_t launch_pair_list(int n, const double* centers, const double L[3], co
     G.r_min = r_min;
     G.ns_pe = ns_pe;
     G.ns_me = ns_me;
+    G.bad = bad;
     pairs_count_kernel<<<n, 256, 0, st>>>(n, centers, G, counts);
     pairs_scan_kernel<<<1, 1024, 0, st>>>(n, counts, offsets, n_pair, queue);
-    pairs_fill_kernel<<<n, 256, 0, st>>>(n, centers, G, offsets, pairs);
+    pairs_fill_kernel<<<n, 256, 0, st>>>(n, centers, G, offsets, RecordOut{pairs});
+    return cudaGetLastError();
+}
+
+// The same count / scan / fill for exx_pair_list_static: fixed radii, records
+// of five ints, positions at or beyond cap skipped; scratch holds counts[n],
+// offsets[n + 1] and two ints (pair count, unused queue word), in that order.
+cudaError_t launch_pair_list_packed(int n, const double* centers, const double L[3], const double delta[3],
+                                    const int N[3], double r_pair, int* scratch, int* out, int cap, cudaStream_t st) {
+    PairGeom G = {};
+    for (int a = 0; a < 3; ++a) {
+        G.L[a] = L[a];
+        G.delta[a] = delta[a];
+        G.N[a] = N[a];
+    }
+    G.r2cut = r_pair * r_pair;
+    int* counts = scratch;
+    int* offsets = scratch + n;
+    int* tail = offsets + n + 1;
+    pairs_count_kernel<<<n, 256, 0, st>>>(n, centers, G, counts);
+    pairs_scan_kernel<<<1, 1024, 0, st>>>(n, counts, offsets, tail, tail + 1);
+    pairs_fill_kernel<<<n, 256, 0, st>>>(n, centers, G, offsets, PackedOut{out, cap});
     return cudaGetLastError();
 }
 
@@ -283,8 +342,8 @@ cudaError_t launch_dfix_convert(double* p, long long n, double inv, int num_sms,
 }
 
 cudaError_t launch_exx_reduce(const PairRec* pairs, const int* n_pair, const double* e_pair, double* out,
-                              cudaStream_t st) {
-    exx_reduce_kernel<<<1, 1024, 0, st>>>(pairs, n_pair, e_pair, out);
+                              cudaStream_t st, int* bad) {
+    exx_reduce_kernel<<<1, 1024, 0, st>>>(pairs, n_pair, e_pair, out, bad);
     return cudaGetLastError();
 }
 

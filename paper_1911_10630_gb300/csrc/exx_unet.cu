@@ -253,12 +253,14 @@ __global__ void head_kernel(const __nv_bfloat16* __restrict__ y0, const float* _
 }
 
 // Loss L = sum_v m_v (out_v - t_v)^2 / (B S^3), m_v = input mask channel; the
-// head's gradients, and the gradient at y0 masked by ReLU (y0 > 0).
+// head's gradients, and the gradient at y0 masked by ReLU (y0 > 0). Each block
+// writes its partial sums (16 weights, bias, loss) to part[block][18]; they are
+// added in block order by reduce_parts_kernel, so the result does not depend
+// on the order in which blocks run.
 __global__ void head_backward_kernel(const float* __restrict__ in, const float* __restrict__ target,
                                      const float* __restrict__ out, const __nv_bfloat16* __restrict__ y0,
-                                     const float* __restrict__ hw, float* __restrict__ ghw,
-                                     __nv_bfloat16* __restrict__ g_y0, float* __restrict__ loss, long long nv,
-                                     float inv_n) {
+                                     const float* __restrict__ hw, __nv_bfloat16* __restrict__ g_y0,
+                                     float* __restrict__ part, long long nv, float inv_n) {
     __shared__ float red[17][8];
     float lsum = 0.0f, gw[17];
 #pragma unroll
@@ -296,15 +298,27 @@ __global__ void head_backward_kernel(const float* __restrict__ in, const float* 
     __shared__ float lred[8];
     if (lane == 0) lred[wid] = lsum;
     __syncthreads();
+    float* mine = part + (size_t)blockIdx.x * 18;
     if (threadIdx.x < 17) {
         float s = 0.0f;
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[threadIdx.x][k];
-        atomicAdd(&ghw[threadIdx.x], s);
+        mine[threadIdx.x] = s;
     }
     if (threadIdx.x == 32) {
         float s = 0.0f;
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += lred[k];
-        atomicAdd(loss, s * inv_n);
+        mine[17] = s * inv_n;
+    }
+}
+
+// out[i] = sum over s = 0 .. n_parts - 1 of part[s * stride + i], in that order
+// (the fixed-order second stage of every gradient and loss reduction).
+__global__ void reduce_parts_kernel(const float* __restrict__ part, int n_parts, long long stride, int count,
+                                    float* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int k = 0; k < n_parts; ++k) s += part[(size_t)k * stride + i];
+        out[i] = s;
     }
 }
 
@@ -414,14 +428,15 @@ __global__ void skip_back_kernel(const __nv_bfloat16* __restrict__ dpool, const 
     }
 }
 
-// Weight gradient of a 3x3x3 layer: dW[tap][ci][co] += sum over samples and
+// Weight gradient of a 3x3x3 layer: dW[tap][ci][co] = sum over samples and
 // voxels of x[v + tap - 1][ci] g[v][co]; the centre-tap blocks of the first ci
-// block also accumulate the bias gradient. Block = 16 x 16 (ci, co); grid.x =
-// tap, grid.y = ci block, grid.z = co block x voxel split.
+// block also form the bias gradient. Block = 16 x 16 (ci, co); grid.x = tap,
+// grid.y = ci block, grid.z = co block x voxel split. Each split writes its
+// partial sums to its own slice of part ([split][27 cin cout + cout]), which
+// reduce_parts_kernel adds in split order.
 constexpr int kDwTile = 64;
 __global__ void __launch_bounds__(256) dw_kernel(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ g,
-                                                 float* __restrict__ dw, float* __restrict__ db, int B, int S, int cin,
-                                                 int cout, int nsplit) {
+                                                 float* __restrict__ part, int B, int S, int cin, int cout, int nsplit) {
     __shared__ float xs[kDwTile][17];
     __shared__ float gs[kDwTile][17];
     const int tap = blockIdx.x, cib = blockIdx.y;
@@ -468,14 +483,16 @@ __global__ void __launch_bounds__(256) dw_kernel(const __nv_bfloat16* __restrict
         }
         __syncthreads();
     }
-    atomicAdd(&dw[((size_t)tap * cin + cib * 16 + ty) * cout + cob * 16 + tx], acc);
-    if (do_bias && ty == 0) atomicAdd(&db[cob * 16 + tx], bacc);
+    float* dw = part + (size_t)split * ((size_t)27 * cin * cout + cout);
+    dw[((size_t)tap * cin + cib * 16 + ty) * cout + cob * 16 + tx] = acc;
+    if (do_bias && ty == 0) dw[(size_t)27 * cin * cout + cob * 16 + tx] = bacc;
 }
 
 // Weight gradient of the 2-channel FP32 input layer: 27 x 2 x 16 weights and
-// 16 biases; one thread per weight, voxels split over blocks.
+// 16 biases; one thread per weight, voxels split over blocks, each block's
+// partial sums in part[block][27 * 32 + 16] (added in block order afterwards).
 __global__ void dw_first_kernel(const float* __restrict__ in, const __nv_bfloat16* __restrict__ g,
-                                float* __restrict__ dw, float* __restrict__ db, int B, int S, int nsplit) {
+                                float* __restrict__ part, int B, int S, int nsplit) {
     const int t = threadIdx.x;  // 0 .. 27*32+16-1
     if (t >= 27 * 32 + 16) return;
     const long long nv = (long long)B * S * S * S;
@@ -493,12 +510,11 @@ __global__ void dw_first_kernel(const float* __restrict__ in, const __nv_bfloat1
             const long long u = ((bb * S + z2) * S + y2) * S + x2;
             acc = fmaf(in[2 * u + ci], bf2f(g[v * 16 + co]), acc);
         }
-        atomicAdd(&dw[t], acc);
     } else {
         const int co = t - 27 * 32;
         for (long long v = v0; v < v1; ++v) acc += bf2f(g[v * 16 + co]);
-        atomicAdd(&db[co], acc);
     }
+    part[(size_t)blockIdx.x * (27 * 32 + 16) + t] = acc;
 }
 
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -603,6 +619,15 @@ cudaError_t conv3_tc(const __nv_bfloat16* x, const __nv_bfloat16* wp, const floa
 
 // ---- network driver --------------------------------------------------------
 
+// Voxel splits of a weight-gradient launch: about 8192 voxels per split, at
+// most 64 blocks per SM in all.
+static int dw_splits(long long nv, int cin, int cout, int n_sm) {
+    int nsplit = (int)((nv + 8191) / 8192);
+    const int blocks = 27 * (cin / 16) * (cout / 16);
+    while (nsplit > 1 && (long long)blocks * nsplit > 64LL * n_sm) --nsplit;
+    return nsplit;
+}
+
 cudaError_t create(Net& n, int S, int Bmax) {
     n.S = S;
     n.Bmax = Bmax;
@@ -670,6 +695,19 @@ cudaError_t create(Net& n, int S, int Bmax) {
     UCK(act(&n.g_x0, v0, 16));
     UCK(act(&n.g_x0a, v0, 16));
     UCK(alloc((void**)&n.out, v0 * 4));
+    // partial sums of the gradient reductions: the largest of the head's
+    // per-block sums, the input layer's and every 3x3x3 layer's per-split sums
+    {
+        size_t need = (size_t)18 * 16 * n.n_sm;
+        need = std::max(need, (size_t)4 * n.n_sm * (27 * 32 + 16));
+        const int lvl[kLayers] = {0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0, 0};
+        for (int l = 1; l < kHead; ++l) {
+            const long long nv = (long long)v0 >> (3 * lvl[l]);
+            need = std::max(need, (size_t)dw_splits(nv, kCin[l], kCout[l], n.n_sm) *
+                                      ((size_t)27 * kCin[l] * kCout[l] + kCout[l]));
+        }
+        UCK(alloc((void**)&n.gpart, need * 4));
+    }
     UCK(alloc((void**)&n.d_loss, 4));
     UCK(alloc((void**)&n.d_err, 4));
     UCK(cudaMemset(n.d_err, 0, 4));
@@ -731,10 +769,14 @@ cudaError_t backward(Net& n, const float* in, const float* target, int B, cudaSt
     const int S = n.S, S1 = S / 2, S2 = S / 4, S3 = S / 8;
     const long long v0 = (long long)B * S * S * S, v1 = v0 / 8, v2 = v1 / 8, v3 = v2 / 8;
     zero_f32_kernel<<<grid_for((long long)n.nparam, n.n_sm), 256, 0, st>>>(n.grads, (long long)n.nparam);
-    UCK(cudaMemsetAsync(n.d_loss, 0, 4, st));
-    head_backward_kernel<<<grid_for(v0, n.n_sm), 256, 0, st>>>(in, target, n.out, n.y0, n.params + param_offset(kHead),
-                                                              n.grads + param_offset(kHead), n.g_y0, n.d_loss, v0,
-                                                              1.0f / (float)v0);
+    {
+        const int nblk = grid_for(v0, n.n_sm);
+        float* ghw = n.grads + param_offset(kHead);
+        head_backward_kernel<<<nblk, 256, 0, st>>>(in, target, n.out, n.y0, n.params + param_offset(kHead), n.g_y0,
+                                                   n.gpart, v0, 1.0f / (float)v0);
+        reduce_parts_kernel<<<1, 32, 0, st>>>(n.gpart, nblk, 18, 17, ghw);
+        reduce_parts_kernel<<<1, 32, 0, st>>>(n.gpart + 17, nblk, 18, 1, n.d_loss);
+    }
     UCK(cudaGetLastError());
     // data gradient through layer l: from g (cout channels) to cin channels,
     // masked by ReLU of the layer's input when that input is a ReLU output
@@ -744,12 +786,12 @@ cudaError_t backward(Net& n, const float* in, const float* target, int B, cudaSt
     };
     auto dweight = [&](const __nv_bfloat16* x, const __nv_bfloat16* g, int l, int s) {
         const long long nv = (long long)B * s * s * s;
-        int nsplit = (int)((nv + 8191) / 8192);
-        const int blocks = 27 * (kCin[l] / 16) * (kCout[l] / 16);
-        while (nsplit > 1 && (long long)blocks * nsplit > 64LL * n.n_sm) --nsplit;
+        const int nsplit = dw_splits(nv, kCin[l], kCout[l], n.n_sm);
         dim3 grid(27, kCin[l] / 16, (kCout[l] / 16) * nsplit);
-        float* gw = n.grads + param_offset(l);
-        dw_kernel<<<grid, 256, 0, st>>>(x, g, gw, gw + (size_t)27 * kCin[l] * kCout[l], B, s, kCin[l], kCout[l], nsplit);
+        const int count = 27 * kCin[l] * kCout[l] + kCout[l];
+        dw_kernel<<<grid, 256, 0, st>>>(x, g, n.gpart, B, s, kCin[l], kCout[l], nsplit);
+        reduce_parts_kernel<<<grid_for(count, n.n_sm), 256, 0, st>>>(n.gpart, nsplit, count, count,
+                                                                     n.grads + param_offset(l));
         return cudaGetLastError();
     };
     // level 0, up path
@@ -793,8 +835,10 @@ cudaError_t backward(Net& n, const float* in, const float* target, int B, cudaSt
     UCK(dconv(n.g_x0, n.x0a, n.g_x0a, 1, S));
     {
         const int nsplit = 4 * n.n_sm;
-        float* gw = n.grads + param_offset(0);
-        dw_first_kernel<<<nsplit, 27 * 32 + 16, 0, st>>>(in, n.g_x0a, gw, gw + 27 * 32, B, S, nsplit);
+        const int count = 27 * 32 + 16;
+        dw_first_kernel<<<nsplit, count, 0, st>>>(in, n.g_x0a, n.gpart, B, S, nsplit);
+        reduce_parts_kernel<<<grid_for(count, n.n_sm), 256, 0, st>>>(n.gpart, nsplit, count, count,
+                                                                     n.grads + param_offset(0));
     }
     return cudaGetLastError();
 }

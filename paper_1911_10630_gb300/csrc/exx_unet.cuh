@@ -45,6 +45,7 @@ struct Net {
     __nv_bfloat16 *g_y0, *g_y0a, *g_c0, *g_y1, *g_y1a, *g_c1, *g_y2, *g_y2a, *g_c2;
     __nv_bfloat16 *g_x3, *g_x3a, *g_p2, *g_x2, *g_x2a, *g_p1, *g_x1, *g_x1a, *g_p0, *g_x0, *g_x0a;
     float* out = nullptr;           // [Bmax][S^3] FP32 network output
+    float* gpart = nullptr;         // per-block / per-split partial sums of the gradient reductions
     float* d_loss = nullptr;        // [1]
     int* d_err = nullptr;           // tensor-core wait time-out flag
 };

@@ -18,9 +18,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libexx_gb300.so")
 
-EXX_OK, EXX_EINVAL, EXX_ENOMEM, EXX_ECUDA, EXX_ENOCONV, EXX_ENOPAIR = 0, -1, -2, -3, -4, -5
+EXX_OK, EXX_EINVAL, EXX_ENOMEM, EXX_ECUDA, EXX_ENOCONV, EXX_ENOPAIR, EXX_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 _STATUS = {0: "EXX_OK", -1: "EXX_EINVAL", -2: "EXX_ENOMEM", -3: "EXX_ECUDA", -4: "EXX_ENOCONV",
-           -5: "EXX_ENOPAIR"}
+           -5: "EXX_ENOPAIR", -6: "EXX_ETIMEOUT"}
 
 
 class ExxError(RuntimeError):
@@ -36,7 +36,7 @@ class exx_options(ctypes.Structure):
                 ("solver_kind", ctypes.c_int), ("cluster_size", ctypes.c_int), ("update_drop", ctypes.c_double),
                 ("lane_map", ctypes.c_int), ("autotune", ctypes.c_int), ("r_pe_nonself", ctypes.c_int),
                 ("r_me_nonself", ctypes.c_int), ("fixed_residual", ctypes.c_int),
-                ("deterministic", ctypes.c_int)]
+                ("deterministic", ctypes.c_int), ("inject_wait_timeout", ctypes.c_int)]
 
 
 class exx_stats(ctypes.Structure):
@@ -47,7 +47,7 @@ class exx_stats(ctypes.Structure):
                 ("solver_kind", ctypes.c_int), ("cluster_size", ctypes.c_int), ("grid_ctas", ctypes.c_int),
                 ("threads", ctypes.c_int), ("phase_ms", ctypes.c_double * 4), ("lane_map", ctypes.c_int),
                 ("n_candidates", ctypes.c_int), ("tune_ms", ctypes.c_double),
-                ("guess_ms", ctypes.c_double)]
+                ("guess_ms", ctypes.c_double), ("n_timeouts", ctypes.c_int), ("n_nonfinite", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -81,6 +81,7 @@ SIGNATURES = [
     ("exx_load_guess_model", ctypes.c_int, [_ctx_p, _vp, ctypes.c_size_t]),
     ("exx_pair_list_static", ctypes.c_int, [_vp, ctypes.c_int, _d, _i, ctypes.c_double, _vp, ctypes.c_int, _i,
                                             _vp]),
+    ("exx_probe_fp64_rate", ctypes.c_int, [_d, _vp]),
     ("exx_last_error", ctypes.c_char_p, [_ctx_p]),
     ("exx_destroy", None, [_ctx_p]),
     # include/exx_guess.h
@@ -122,6 +123,13 @@ def exx_default_options() -> exx_options:
 def exx_last_error(ctx=None) -> str:
     s = load().exx_last_error(ctx)
     return s.decode() if s else ""
+
+
+def probe_fp64_rate(stream=None) -> float:
+    """Measured FP64 FMA rate of the current device in TFLOP/s (exx_probe_fp64_rate)."""
+    out = ctypes.c_double(0.0)
+    _check(load().exx_probe_fp64_rate(ctypes.byref(out), _stream_handle(stream)))
+    return float(out.value)
 
 
 def _check(status: int, ctx=None):
@@ -187,13 +195,14 @@ class Exx:
         except Exception:
             pass
 
-    def compute(self, orbitals, centers, d_xx, alphas=None, stream=None, allow_noconv=False) -> float:
+    def compute(self, orbitals, centers, d_xx, alphas=None, stream=None, allow_noconv=False,
+                allow_timeout=False) -> float:
         """exx_compute on device tensors; returns E_xx, fills d_xx."""
         e = ctypes.c_double()
         st = load().exx_compute(self._ctx, _ptr(orbitals), _ptr(centers), int(centers.shape[0]), _ptr(alphas),
                                 ctypes.byref(e), _ptr(d_xx), _stream_handle(stream))
         self.last_status = st
-        if not (st == EXX_OK or (allow_noconv and st == EXX_ENOCONV)):
+        if not (st == EXX_OK or (allow_noconv and st == EXX_ENOCONV) or (allow_timeout and st == EXX_ETIMEOUT)):
             _check(st, self._ctx)
         return e.value
 

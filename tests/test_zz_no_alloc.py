@@ -1,11 +1,13 @@
 """The allocation-free pair list (exx_pair_list_static) against exx_compute's.
 
-exx_pair_list_static serves callers that cannot allocate device memory, such as
-code running under CUDA-graph stream capture or hosts held to a fixed
-memory pool. Its scratch is a static device array shared by all calls. The
-test therefore calls it twice in a row, on two different inputs. Each result
-must equal, bit for bit, the pair list that exx_compute built for the same
-input (the pair list is integer output, compared exactly).
+exx_pair_list_static serves callers that cannot allocate device memory:
+applications whose device memory all goes through their own pool or a fixed
+budget, and latency-bound loops that cannot take cudaMalloc's implicit
+synchronisation. Its scratch is a static device array shared by all calls and
+kept between them. The test therefore calls it twice in a row, on two
+different inputs. Each result must equal, bit for bit, the pair list that
+exx_compute built for the same input (the pair list is integer output,
+compared exactly).
 """
 import ctypes
 import math
