@@ -168,6 +168,51 @@ def _algorithmic(pairs, stats, n_pe, n_me, precision):
     return dict(cg=6.0 * s * point_iters, hbm=hbm, flops=38.0 * point_iters, point_iters=point_iters)
 
 
+def batched_uneven_leg(dev, stream, steps=3, plain_steps=1):
+    """Config 2 (batched uneven): 512 orbitals in 128 clusters on 150^3, per-pair
+    radii 12..32 from the orbital exponents, tol 1e-8. The mixed-precision
+    cluster solver in radius classes (one launch per R_PE, the largest first,
+    one captured graph) against the pure-FP64 GPU solve of the same pairs; both
+    from inputs resident on the device, CUDA events on the stream."""
+    import torch
+    from paper_1911_10630_gb300 import synth
+    from paper_1911_10630_gb300.exx import Exx
+    w = synth.config2()
+    phi = synth.orbitals_torch(w, device=dev)
+    cen = torch.from_numpy(np.ascontiguousarray(w.centers)).to(dev)
+    al = torch.from_numpy(np.ascontiguousarray(w.alphas)).to(dev)
+    D = torch.empty_like(phi)
+    out = {"workload": w.name, "n_orbitals": w.n, "grid": int(w.grid[0]), "tol": w.tol}
+
+    def timed(n, **opt):
+        ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, radii_mode=1, **opt)
+        e = ex.compute(phi, cen, D, alphas=al, stream=stream)  # warm-up (graph capture)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(n):
+            e = ex.compute(phi, cen, D, alphas=al, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / n
+        st = ex.stats()
+        cls = ex.radius_classes()
+        ex.close()
+        return e, ms, st, cls
+
+    e1, ms1, st1, cls = timed(steps, precision=1)
+    e0, ms0, st0, _ = timed(plain_steps, precision=0)
+    n_pair = st1["n_pair"]
+    out.update({"n_pair": n_pair, "value": n_pair / (ms1 / 1e3), "unit": UNIT, "ms_per_step": ms1,
+                "iters_p50": st1["iters_p50"], "iters_max": st1["iters_max"], "n_nonconv": st1["n_nonconv"],
+                "radius_classes": [{"r_pe": r, "ctas_per_pair": c, "resident": k} for r, c, k in cls],
+                "pure_fp64_gpu": {"value": n_pair / (ms0 / 1e3), "ms_per_step": ms0, "iters_p50": st0["iters_p50"]},
+                "speedup_vs_pure_fp64_gpu": ms0 / ms1, "dE_vs_fp64_per_orbital": abs(e1 - e0) / w.n})
+    del phi, D
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_oracle_sample(w, phi, pairs_all, seconds=12.0, seed=0):
     """Times the oracle on a bounded random sample of the workload's pairs."""
     import oracle
@@ -244,6 +289,7 @@ def main():
     ap.add_argument("--lane-map", type=int, default=0)
     ap.add_argument("--update-drop", type=float, default=1e-4)
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--no-legs", action="store_true", help="skip the batched-uneven (config 2) leg")
     ap.add_argument("--orbitals", type=int, default=0,
                     help="keep only the first N orbitals of the workload (small cases for profiling)")
     args = ap.parse_args()
@@ -384,6 +430,9 @@ def main():
                "d2h_bytes_per_step": int(phi.nbytes + 8), "ms_per_step": dt * 1e3}
         exh.close()
         del hphi, hD
+
+    if rank == 0 and ws == 1 and not args.no_legs and not args.orbitals:
+        extra["batched_uneven"] = batched_uneven_leg(dev, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

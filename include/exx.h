@@ -83,7 +83,13 @@ typedef struct {
                              paper's self / non-self proto-subdomains, Sec. IV):
                              self pairs use R_PE / R_ME of exx_init, non-self
                              pairs r_pe_nonself / r_me_nonself below.
-                          1 and 2 run on the one-CTA solver (solver_kind 1).   */
+                          1 with precision 1 runs the cluster solver in radius
+                          classes: one launch per R_PE, the largest first, each
+                          on the smallest cluster whose slab layout fits (one
+                          CTA holds a ball up to R_PE 13; 2, 4, 9 or 16 CTAs
+                          share larger ones), the one-CTA solver for a radius
+                          that fits none; 1 with precision 0, or solver_kind 1,
+                          and 2 run on the one-CTA solver.                      */
     int max_iter;      /* CG iteration cap per solve (default 20000).            */
     int inner_max_iter;/* FP32 inner iterations per refinement step (default 4000) */
     double inner_tol;  /* FP32 inner relative tolerance (default 1e-5).          */
@@ -275,12 +281,28 @@ exx_status exx_debug_pair(exx_ctx *ctx, const double *orbitals, int index, doubl
  */
 exx_status exx_apply_operator(exx_ctx *ctx, const double *p, double *ap, void *stream);
 
+/*
+ * The launch plan of per-pair radii on the cluster solver (radii_mode 1,
+ * precision 1): one class per R_PE, launched largest first. The paper has no
+ * counterpart (its subdomain sizes vary per pair, Sec. IV.A; how they map to
+ * thread-block clusters is this library's). Host arrays of capacity cap:
+ *   r_pe          the class's R_PE
+ *   cluster_size  CTAs per pair (1 = the whole ball in one CTA's shared
+ *                 memory), or 0 when the class runs on the one-CTA solver
+ *                 with its state in global memory
+ *   resident      clusters (or CTAs) the class's launch keeps resident
+ * *n_class receives the class count (0 when the context has no classes). Any
+ * output array may be NULL. EXX_EINVAL if cap is too small.
+ */
+exx_status exx_radius_classes(const exx_ctx *ctx, int *r_pe, int *cluster_size, int *resident, int cap,
+                              int *n_class);
+
 /* Ball sizes for the context's fixed radii. */
 exx_status exx_ball_size(const exx_ctx *ctx, int *n_pe, int *n_me);
 
 /*
  * Loads the learned warm-start model used by warm_start = 2: a blob of four
- * int32 {0x47585845, 1, S, count} followed by count FP32 parameters of the
+ * int32 {0x47585845, 2, S, count} followed by count FP32 parameters of the
  * U-Net described in include/exx_guess.h (S = side of the network's input
  * cube). weights: host. Allocates the network and its batch buffers (about
  * 4 GB). EXX_EINVAL if the header or the size does not match; a later load

@@ -17,22 +17,26 @@
  * 3x3x3 convolutions after the input layer run on the tcgen05 tensor cores.
  *
  * Sample layout (every array FP32, C order):
- *   input  [batch][S][S][S][2]: channel 0 = rho(o) / s on the PE ball and 0
- *          elsewhere, channel 1 = 1 on the PE ball (|o|^2 <= R_PE^2) and 0
- *          elsewhere; cube voxel (z, y, x) is the offset o = (z, y, x) - S/2
- *          (axes in the orbital-array order); s = max |rho| on the ball.
+ *   input  [batch][S][S][S][3]: channel 0 = rho(o) / s on the PE ball and 0
+ *          elsewhere; channel 1 = the multipole boundary values: outside the
+ *          PE ball, the expansion of Eq. me (moments of Eq. mepole of rho / s
+ *          over the ball points in the cube, l <= l_max, in FP32) divided by
+ *          delta^2, and 0 on the ball; channel 2 = 1 on the PE ball
+ *          (|o|^2 <= R_PE^2) and 0 elsewhere; cube voxel (z, y, x) is the
+ *          offset o = (z, y, x) - S/2 (axes in the orbital-array order); s =
+ *          max |rho| on the ball.
  *   target / output [batch][S][S][S]: v(o) / (s delta^2), delta^2 the
  *          geometric mean of the squared spacings.
  * Loss: sum over the batch of (output - target)^2 on ball voxels, divided by
  * batch * S^3.
  *
  * Parameters: exx_guess_param_count() FP32 values, layers in the order
- *   in(2->16) c0b(16->16) c1a(16->32) c1b(32->32) c2a(32->64) c2b(64->64)
+ *   in(3->16) c0b(16->16) c1a(16->32) c1b(32->32) c2a(32->64) c2b(64->64)
  *   c3a(64->128) c3b(128->128) u2a(192->64) u2b(64->64) u1a(96->32)
  *   u1b(32->32) u0a(48->16) u0b(16->16) head(16->1)
  * each as W[27][cin][cout] (tap = 9 dz + 3 dy + dx over offsets -1..1 in the
  * z, y, x order above) then bias[cout]; the head is w[16] then b[1]. A model
- * blob for exx_load_guess_model is four int32 {0x47585845, 1, S, count}
+ * blob for exx_load_guess_model is four int32 {0x47585845, 2, S, count}
  * followed by the count parameters.
  *
  * Errors: every function returns an exx_status; exx_last_error(NULL)
@@ -66,7 +70,7 @@ exx_status exx_guess_set_params(exx_guess *g, const float *params, size_t n);
 exx_status exx_guess_get_params(exx_guess *g, float *params, size_t n);
 
 /*
- * Inference. input: device [batch][S^3][2]; output: device [batch][S^3].
+ * Inference. input: device [batch][S^3][3]; output: device [batch][S^3].
  * stream: cudaStream_t (NULL = legacy default); the call is stream-ordered
  * and synchronises only to read the tensor-core time-out flag.
  */
@@ -91,7 +95,7 @@ void exx_guess_destroy(exx_guess *g);
  * for the first min(count, cap) pairs of that call's list the network input
  * and target on a cube of side S (even, 8..128) as laid out above.
  *   orbitals  device, the same array the call used (EXX_EINVAL otherwise)
- *   input     device [cap][S^3][2]; target device [cap][S^3]
+ *   input     device [cap][S^3][3]; target device [cap][S^3]
  *   count     host, receives the call's pair count
  * Synchronises the context's work and the given stream. Errors are reported
  * through exx_last_error(ctx).

@@ -20,7 +20,8 @@ from __future__ import annotations
 
 import numpy as np
 
-CIN = (2, 16, 16, 32, 32, 64, 64, 128, 192, 64, 96, 32, 48, 16, 16)
+CIN = (3, 16, 16, 32, 32, 64, 64, 128, 192, 64, 96, 32, 48, 16, 16)
+MASK = 2  # input channels: rho / s, the multipole boundary values, the ball mask
 COUT = (16, 16, 32, 32, 64, 64, 128, 128, 64, 64, 32, 32, 16, 16, 1)
 HEAD = 14
 TAPS = [(dz, dy, dx) for dz in range(3) for dy in range(3) for dx in range(3)]
@@ -106,7 +107,7 @@ def relu(x):
 
 
 def forward(params, inp, bf16=False):
-    """inp [B][S][S][S][2] -> (out [B][S][S][S], cache of activations)."""
+    """inp [B][S][S][S][3] -> (out [B][S][S][S], cache of activations)."""
     P = unpack(params)
     r = bf16_round if bf16 else (lambda a: a)
     Wq = [(P[l][0] if l in (0, HEAD) else r(P[l][0]), P[l][1]) for l in range(len(P))]
@@ -146,7 +147,7 @@ def loss_and_gradient(params, inp, target, bf16=False):
     out, (a, Wq) = forward(params, inp, bf16)
     r = bf16_round if bf16 else (lambda x: x)
     n = out.size
-    m = (a["in"][..., 1] > 0.5).astype(np.float64)
+    m = (a["in"][..., MASK] > 0.5).astype(np.float64)
     diff = out - np.asarray(target, np.float64)
     loss = float(np.sum(m * diff * diff) / n)
     gout = 2.0 * m * diff / n

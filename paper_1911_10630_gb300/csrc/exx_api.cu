@@ -23,7 +23,8 @@ cudaError_t launch_pair_list(int n, const double* centers, const double L[3], co
                              PairRec* pairs, cudaStream_t st, const double* alphas, double ln_inv_eps,
                              double delta_max, int r_min, int ns_pe = 0, int ns_me = 0, int* bad = nullptr);
 cudaError_t launch_radii_sort(const PairRec* pairs, const int* n_pair, int* hist, int n_geo, int* order, int num_sms,
-                              cudaStream_t st);
+                              cudaStream_t st, int* classes = nullptr);
+cudaError_t cluster_set_smem(int variant, size_t smem);
 cudaError_t launch_zero(double* p, long long n, int num_sms, cudaStream_t st);
 cudaError_t launch_dfix_convert(double* p, long long n, double inv, int num_sms, cudaStream_t st);
 cudaError_t launch_exx_reduce(const PairRec* pairs, const int* n_pair, const double* e_pair, double* out,
@@ -104,6 +105,16 @@ struct exx_ctx {
     int n_clusters = 0;
     ClusterLayout CL;
     std::vector<void*> cl_mem;  // device tables of all candidates
+    // per-pair radii on the cluster solver: one launch per radius class
+    // (geometry), largest first, each with the launch shape that fits it
+    // (kind 2: cluster kernel candidate; kind 1: the one-CTA pair kernel)
+    struct RadiusClass {
+        int geo = 0, kind = 1;
+        ClusterCand cand;
+    };
+    bool per_class = false;
+    std::vector<RadiusClass> classes;
+    int* d_class = nullptr;  // [2 n_geo] start and length of each class in the order, [n_geo] work counters
     double* d_pow = nullptr;
     unsigned long long* d_phase = nullptr;  // [4] phase cycles of the cluster solver
     int clock_khz = 0;
@@ -241,6 +252,71 @@ static void apply_cand(exx_ctx* cc, int k) {
     cc->n_clusters = std::min(K.n_clusters, cc->n_slots > 0 ? cc->n_slots : K.n_clusters);
 }
 
+// One quad-map cluster candidate with halo planes (mode 3, bank-aware
+// dealing) for ball B on variant v: slab layout, thread map and first-residual
+// order, with their tables uploaded. fits = false when the slabs, the quads
+// or the shared memory do not fit, or no cluster of this size can be resident.
+static exx_status make_quad_cand(exx_ctx* c, const HostBall& B, int v, int max_optin, exx_ctx::ClusterCand& K,
+                                 bool& fits) {
+    fits = false;
+    const int C = cluster_variant_size(v);
+    ClusterLayout L;
+    std::vector<int> pt;
+    // planes a CTA can hold besides its 6 halo planes, the slot map and the
+    // static shared memory (4 KiB kept free)
+    const long plane_bytes = 4L * (((2 * B.r_pe + 7 + 3) & ~3) * (2 * B.r_pe + 7));
+    const long budget = (long)max_optin - 4096 - 4L * cluster_variant_threads(v) * cluster_variant_pts(v);
+    const int max_planes = (int)(budget / plane_bytes) - 6;
+    if (max_planes < 3 || !build_cluster_layout(B, C, L, pt, true, max_planes)) return EXX_OK;
+    std::vector<int> spk, sk, res_list, res_nrim;
+    // bank-aware dealing (lane map 5) when the slab's quads allow it, else
+    // the natural order (lane map 4): the dealing needs every bank group in
+    // every run of 8 slots, which some pitches do not offer
+    int lane_map = 5;
+    if (build_quad_maps(L, pt, cluster_variant_threads(v), cluster_variant_pts(v), spk, sk, 1) < 0) {
+        lane_map = 4;
+        if (build_quad_maps(L, pt, cluster_variant_threads(v), cluster_variant_pts(v), spk, sk, 0) < 0) return EXX_OK;
+    }
+    const size_t sm = cluster_kernel_smem(B.r_me, L, v);
+    if ((long)sm + 4096 > (long)max_optin) return EXX_OK;
+    int nclu = 0;
+    cudaError_t e = cluster_prepare(v, sm, &nclu);
+    if (e != cudaSuccess || nclu < 1) {
+        (void)cudaGetLastError();
+        return EXX_OK;
+    }
+    build_residual_order(B, L, res_list, res_nrim);
+    int4 ri[kMaxCluster];
+    for (int r = 0; r < C; ++r) ri[r] = make_int4(L.x0[r], L.planes[r], L.k0[r], L.k1[r]);
+    const size_t n_int = pt.size() + 4 * (size_t)C + spk.size() + sk.size() + res_list.size() + res_nrim.size();
+    int* d = nullptr;
+    e = cudaMalloc(&d, sizeof(int) * n_int);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(class tables)");
+    c->cl_mem.push_back(d);
+    int* at = d;
+    auto put = [&](const void* src, size_t n) -> int* {
+        int* here = at;
+        if (e == cudaSuccess && n) e = cudaMemcpy(here, src, sizeof(int) * n, cudaMemcpyHostToDevice);
+        at += n;
+        return here;
+    };
+    L.rank_info = reinterpret_cast<const int4*>(put(ri, 4 * (size_t)C));  // first: 16-byte aligned
+    L.pt_slab = put(pt.data(), pt.size());
+    L.slot_pk = put(spk.data(), spk.size());
+    L.slot_k = put(sk.data(), sk.size());
+    L.res_list = put(res_list.data(), res_list.size());
+    L.res_nrim = put(res_nrim.data(), res_nrim.size());
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy(class tables)");
+    K.C = C;
+    K.variant = v;
+    K.lane_map = lane_map;
+    K.n_clusters = nclu;
+    K.smem = sm;
+    K.L = L;
+    fits = true;
+    return EXX_OK;
+}
+
 static void free_pairs(exx_ctx* c) {
     cudaFree(c->d_counts);
     cudaFree(c->d_offsets);
@@ -270,6 +346,7 @@ extern "C" void exx_destroy(exx_ctx* c) {
     free_pairs(c);
     cudaFree(c->d_scalars);
     cudaFree(c->d_hist);
+    cudaFree(c->d_class);
     cudaFree(c->d_exx);
     if (c->h_exx) cudaFreeHost(c->h_exx);
     cudaFree(c->ws);
@@ -338,7 +415,6 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         if (r_me < rme_rule)
             return fail(nullptr, EXX_EINVAL,
                         "exx_init: with radii_mode 1, r_me must be >= r_pe + max(3, ceil(r_pe/3)) (the largest pair's R_ME)");
-        if (o.solver_kind == 2) return fail(nullptr, EXX_EINVAL, "exx_init: radii_mode 1 runs on solver_kind 1");
     }
     if (o.warm_start < 0 || o.warm_start > 3)
         return fail(nullptr, EXX_EINVAL, "exx_init: warm_start must be 0, 1, 2 or 3");
@@ -399,6 +475,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     }
     e = set_multipole_const_solve(mc);
     if (e == cudaSuccess) e = set_multipole_const_cluster(mc);
+    if (e == cudaSuccess) e = exx::unet::set_multipole_const_unet(mc);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpyToSymbol(multipoles)"));
 
     // ball geometries (Algorithm 2), cube radius Rc = R_ME (the largest)
@@ -671,6 +748,52 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         if (!c->use_cluster && o.solver_kind == 2)
             return bail(fail(c, EXX_EINVAL, "exx_init: no cluster layout fits these radii"));
     }
+    // per-pair radii on the cluster solver: for every radius class the first
+    // fitting quad-map launch shape in the order of increasing cluster size
+    // (a small ball in one CTA's shared memory, larger ones over 2 to 16
+    // CTAs; at a cluster size, the variant specialised for the slab pitch
+    // first, then fewer quads per thread); the one-CTA pair kernel takes any
+    // class that fits none
+    if (o.precision == 1 && o.solver_kind != 1 && o.radii_mode == 1) {
+        int max_optin = 0;
+        cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+        const bool isotropic = c->delta[0] == c->delta[1] && c->delta[1] == c->delta[2];
+        std::vector<int> order;  // mode-3 variants by cluster size, specialised first, then quads per thread
+        for (int v = 0; v < cluster_variant_count(); ++v)
+            if (cluster_variant_mode(v) == 3 && cluster_variant_threads(v) == 512) order.push_back(v);
+        std::stable_sort(order.begin(), order.end(), [](int a, int b) {
+            if (cluster_variant_size(a) != cluster_variant_size(b)) return cluster_variant_size(a) < cluster_variant_size(b);
+            if ((cluster_variant_syz(a) != 0) != (cluster_variant_syz(b) != 0)) return cluster_variant_syz(a) != 0;
+            return cluster_variant_pts(a) < cluster_variant_pts(b);
+        });
+        std::vector<size_t> need_smem(cluster_variant_count(), 0);
+        c->classes.resize(c->n_geo);
+        for (int g = 0; g < c->n_geo; ++g) {
+            exx_ctx::RadiusClass& RC = c->classes[g];
+            RC.geo = g;
+            RC.kind = 1;
+            const HostBall& Bg = c->balls[g];
+            for (int v : order) {
+                if (o.cluster_size && cluster_variant_size(v) != o.cluster_size) continue;
+                if (cluster_variant_syz(v) && (cluster_variant_syz(v) != 2 * Bg.r_pe + 7 || !isotropic)) continue;
+                if (cluster_variant_iso(v) && !isotropic) continue;
+                bool fits = false;
+                const exx_status sa = make_quad_cand(c, Bg, v, max_optin, RC.cand, fits);
+                if (sa != EXX_OK) return bail(sa);
+                if (fits) {
+                    RC.kind = 2;
+                    need_smem[v] = std::max(need_smem[v], RC.cand.smem);
+                    break;
+                }
+            }
+        }
+        for (int v = 0; v < cluster_variant_count(); ++v)
+            if (need_smem[v] && (e = cluster_set_smem(v, need_smem[v])) != cudaSuccess)
+                return bail(cuda_fail(c, e, "cudaFuncSetAttribute(class shared memory)"));
+        c->per_class = true;
+        e = cudaMalloc(&c->d_class, sizeof(int) * 3 * (size_t)c->n_geo);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(radius classes)"));
+    }
     if (o.warm_start != 0 && !c->use_cluster)
         return bail(fail(c, EXX_EINVAL, "exx_init: warm_start 1 and 2 need the cluster solver, which does not fit these radii"));
     if (c->use_cluster) apply_cand(c, c->cand);
@@ -682,6 +805,14 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (c->use_cluster) {
         want = 0;
         for (const auto& K : c->cands) want = std::max<long long>(want, K.n_clusters);
+    } else if (c->per_class) {
+        // the classes run one after another and share the slots
+        e = pair_kernel_occupancy(c->threads, true, c->smem, &bps);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
+        want = 0;
+        for (const auto& RC : c->classes)
+            want = std::max<long long>(want, RC.kind == 2 ? RC.cand.n_clusters
+                                                         : (long long)c->num_sms * std::max(1, std::min(bps, 2)));
     } else {
         e = pair_kernel_occupancy(c->threads, o.precision == 1, c->smem, &bps);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
@@ -769,7 +900,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
 
     c->stats.n_pe = B.n_pe;
     c->stats.n_me = B.n_me;
-    c->stats.solver_kind = c->use_cluster ? 2 : 1;
+    c->stats.solver_kind = (c->use_cluster || c->per_class) ? 2 : 1;
     c->stats.cluster_size = c->use_cluster ? c->CL.C : 1;
     c->stats.grid_ctas = c->use_cluster ? c->n_clusters * c->CL.C : c->n_slots;
     c->stats.lane_map = c->use_cluster ? c->cands[c->cand].lane_map : 0;
@@ -811,7 +942,7 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
     P.iters = c->d_iters;
     P.refines = c->d_refines;
     P.dbg_b = nullptr;
-    P.phase_clk = c->use_cluster ? c->d_phase : nullptr;
+    P.phase_clk = (c->use_cluster || c->per_class) ? c->d_phase : nullptr;
     P.test_wait = c->inject_now;
     CK(cudaEventRecordWithFlags(c->ev[0], st, evf), "cudaEventRecord");
     CK(launch_zero(d_xx, (long long)n * c->ngrid, c->num_sms, st), "zero D_xx");
@@ -824,10 +955,27 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
                         c->ns_me, c->d_scalars + 11),
        "pair list");
     if (c->n_geo > 1)
-        CK(launch_radii_sort(c->d_pairs, c->d_scalars, c->d_hist, c->n_geo, c->d_order, c->num_sms, st),
+        CK(launch_radii_sort(c->d_pairs, c->d_scalars, c->d_hist, c->n_geo, c->d_order, c->num_sms, st,
+                             c->per_class ? c->d_class : nullptr),
            "largest-first order");
     CK(cudaEventRecordWithFlags(c->ev[1], st, evf), "cudaEventRecord");
-    if (c->use_cluster)
+    if (c->per_class) {
+        // one launch per radius class, the largest radius first; each takes
+        // its run of the sorted order from the device (start, length, counter)
+        for (int g = c->n_geo - 1; g >= 0; --g) {
+            const exx_ctx::RadiusClass& RC = c->classes[g];
+            SolveParams Pg = P;
+            Pg.item_base = c->d_class + 2 * g;
+            Pg.n_pair = c->d_class + 2 * g + 1;
+            Pg.queue = c->d_class + 2 * c->n_geo + g;
+            if (RC.kind == 2)
+                CK(launch_cluster_kernel(RC.cand.variant, Pg, RC.cand.L, std::min(RC.cand.n_clusters, c->n_slots),
+                                         RC.cand.smem, st),
+                   "cluster pair kernel (radius class)");
+            else
+                CK(launch_pair_kernel(Pg, c->threads, true, c->n_slots, c->smem, st), "pair kernel (radius class)");
+        }
+    } else if (c->use_cluster)
         CK(launch_cluster_kernel(c->cl_variant, P, c->CL, c->n_clusters, c->smem, st), "cluster pair kernel");
     else
         CK(launch_pair_kernel(P, c->threads, c->opt.precision == 1, c->n_slots, c->smem, st), "pair kernel");
@@ -940,7 +1088,7 @@ static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double*
         for (int k0 = 0; k0 < np; k0 += net.Bmax) {
             const int nk = std::min(net.Bmax, np - k0);
             CK(exx::unet::sample_prep(orbitals, c->grid, c->d_pairs, k0, nk, net.S, c->geo_host, c->d_gin,
-                                      c->d_gscale, nullptr, nullptr, d2, st),
+                                      c->d_gscale, nullptr, nullptr, d2, c->delta, c->dV, c->lmax, st),
                "guess input");
             CK(exx::unet::forward(net, c->d_gin, nk, st), "guess network");
             CK(exx::unet::guess_scatter(net.out, c->d_gscale, k0, nk, net.S, c->geo_host, d2, c->d_guess, st),
@@ -1260,7 +1408,21 @@ extern "C" exx_status exx_get_stats(const exx_ctx* cc, exx_stats* out) {
         // shares of the pair-kernel time (the clusters run side by side)
         const double cyc = (double)ph[0] + (double)ph[1] + (double)ph[2] + (double)ph[3];
         for (int k = 0; k < 4; ++k)
-            c->stats.phase_ms[k] = (c->use_cluster && cyc > 0.0) ? c->stats.solve_ms * (double)ph[k] / cyc : 0.0;
+            c->stats.phase_ms[k] =
+                ((c->use_cluster || c->per_class) && cyc > 0.0) ? c->stats.solve_ms * (double)ph[k] / cyc : 0.0;
+    }
+    if (c->per_class) {  // radius classes: the largest cluster and grid of any class
+        int cmax = 1, gmax = c->n_slots;
+        for (const auto& RC : c->classes)
+            if (RC.kind == 2) {
+                cmax = std::max(cmax, RC.cand.C);
+                gmax = std::max(gmax, std::min(RC.cand.n_clusters, c->n_slots) * RC.cand.C);
+            }
+        c->stats.solver_kind = 2;
+        c->stats.cluster_size = cmax;
+        c->stats.grid_ctas = gmax;
+        c->stats.threads = 512;
+        c->stats.lane_map = 5;
     }
     if (c->use_cluster) {
         c->stats.solver_kind = 2;
@@ -1395,6 +1557,22 @@ extern "C" exx_status exx_quad_map(int r_pe, int cluster_size, int threads, int 
     return EXX_OK;
 }
 
+extern "C" exx_status exx_radius_classes(const exx_ctx* c, int* r_pe, int* cluster_size, int* resident, int cap,
+                                         int* n_class) {
+    if (!c || !n_class) return fail(const_cast<exx_ctx*>(c), EXX_EINVAL, "exx_radius_classes: NULL argument");
+    const int n = c->per_class ? (int)c->classes.size() : 0;
+    *n_class = n;
+    if (n > cap && (r_pe || cluster_size || resident))
+        return fail(const_cast<exx_ctx*>(c), EXX_EINVAL, "exx_radius_classes: cap smaller than the class count");
+    for (int k = 0; k < n; ++k) {
+        const exx_ctx::RadiusClass& RC = c->classes[k];
+        if (r_pe) r_pe[k] = c->balls[RC.geo].r_pe;
+        if (cluster_size) cluster_size[k] = RC.kind == 2 ? RC.cand.C : 0;
+        if (resident) resident[k] = RC.kind == 2 ? std::min(RC.cand.n_clusters, c->n_slots) : c->n_slots;
+    }
+    return EXX_OK;
+}
+
 extern "C" exx_status exx_ball_size(const exx_ctx* c, int* n_pe, int* n_me) {
     if (!c) return fail(nullptr, EXX_EINVAL, "exx_ball_size: ctx is NULL");
     if (n_pe) *n_pe = c->hb.n_pe;
@@ -1408,7 +1586,7 @@ extern "C" exx_status exx_load_guess_model(exx_ctx* c, const void* weights, size
     int32_t hdr[4];
     std::memcpy(hdr, weights, sizeof(hdr));
     const size_t np = exx::unet::param_count();
-    if (hdr[0] != 0x47585845 || hdr[1] != 1) return fail(c, EXX_EINVAL, "exx_load_guess_model: bad magic or version");
+    if (hdr[0] != 0x47585845 || hdr[1] != 2) return fail(c, EXX_EINVAL, "exx_load_guess_model: bad magic or version");
     if (hdr[2] < 16 || hdr[2] > 64 || hdr[2] % 8) return fail(c, EXX_EINVAL, "exx_load_guess_model: bad cube side");
     if ((size_t)hdr[3] != np || bytes != 16 + np * sizeof(float))
         return fail(c, EXX_EINVAL, "exx_load_guess_model: parameter count does not match the network");
@@ -1428,7 +1606,7 @@ extern "C" exx_status exx_load_guess_model(exx_ctx* c, const void* weights, size
     const int bmax = (int)std::max(1LL, std::min(256LL, (4LL << 30) / per));
     c->gnet = new exx::unet::Net();
     cudaError_t e = exx::unet::create(*c->gnet, S, bmax);
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_gin, sizeof(float) * 2 * (size_t)bmax * S * S * S);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_gin, sizeof(float) * exx::unet::kIn * (size_t)bmax * S * S * S);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_gscale, sizeof(float) * (size_t)bmax);
     if (e == cudaSuccess)
         e = cudaMemcpy(c->gnet->params, static_cast<const char*>(weights) + 16, np * sizeof(float),
@@ -1466,7 +1644,7 @@ extern "C" exx_status exx_export_samples(exx_ctx* c, const double* orbitals, int
     CK(cudaMalloc(&d_scale, sizeof(float) * (size_t)nk), "exx_export_samples");
     const double d2 = std::cbrt(c->delta[0] * c->delta[0] * c->delta[1] * c->delta[1] * c->delta[2] * c->delta[2]);
     cudaError_t e = exx::unet::sample_prep(orbitals, c->grid, c->d_prev_pairs, 0, nk, S, c->geo_host, input, d_scale,
-                                           target, c->d_vcache[c->parity ^ 1], d2, st);
+                                           target, c->d_vcache[c->parity ^ 1], d2, c->delta, c->dV, c->lmax, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d_scale);
     if (e != cudaSuccess) return cuda_fail(c, e, "exx_export_samples");

@@ -866,7 +866,29 @@ __device__ __noinline__ RunSeg quad_segment(float* ps, const float* pm, const fl
 // after its x legs, so one mbarrier suffices; its phase count hph runs for
 // the whole launch, and every phase opened is waited for.
 __shared__ __align__(8) unsigned long long g_halo_mbar;
-__shared__ __align__(8) unsigned long long g_test_mbar;  // the injected time-out's barrier (test only)
+
+// Test of the time-out path (exx_options.inject_wait_timeout): a bounded wait
+// on a fresh mbarrier that nothing arrives on and no copy or store targets
+// runs out; the count reaches the host as EXX_ETIMEOUT and the rest of the
+// launch is unchanged. The barrier is a spare 8-byte word past the end of the
+// launch's dynamic shared memory layout, and the code stays out of line, so
+// the kernel's own code and static shared layout do not change.
+__device__ __noinline__ void inject_wait_timeout(uint32_t mb, int* timeouts) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    if (!mbar_wait_bounded(mb, 0u, 256)) atomicAdd(timeouts, 1);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mb) : "memory");
+}
+
+// Byte offset of that spare word in the dynamic shared memory of a launch
+// (after the slab, d and the slot map as cluster_kernel_smem counts them).
+__host__ __device__ inline size_t cluster_smem_test_offset(const ClusterLayout& CL, int mode, int pts, int nt) {
+    const size_t per = (size_t)nt * pts;
+    const bool runs = mode == 1, halo = mode == 1 || mode == 3;
+    const size_t slab = (size_t)(CL.cap_planes + (halo ? 6 : 0)) * CL.Sp2;
+    const size_t dsf = mode == 3 ? 0 : (mode == 2 ? 4 : 1) * per;
+    const size_t b = sizeof(float) * (((slab + 3) & ~(size_t)3) + dsf) + (runs ? 0 : sizeof(int) * per);
+    return (b + 7) & ~(size_t)7;
+}
 
 // Bounded wait for the given phase parity of a CTA-local mbarrier; a wait that
 // gives up marks the CTA late (later waits give up at once) and bumps the fault count.
@@ -1192,15 +1214,6 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         g_rc_late = 0;
     }
-    if (P.test_wait && threadIdx.x == 0) {
-        // test of the time-out path: a bounded wait on a fresh mbarrier that
-        // nothing arrives on and no copy or store targets runs out; the count
-        // reaches the host as EXX_ETIMEOUT, the rest of the launch is unchanged
-        const uint32_t tmb = smem_u32(&g_test_mbar);
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tmb) : "memory");
-        if (!mbar_wait_bounded(tmb, 0u, 256)) atomicAdd(P.timeouts, 1);
-        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(tmb) : "memory");
-    }
     cl.sync();
 
     for (;;) {
@@ -1211,7 +1224,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
         cl.sync();
         const int item = s_item;
         if (item >= np) break;
-        const int pidx = P.order ? P.order[item] : item;
+        const int pidx = P.order ? P.order[(P.item_base ? *P.item_base : 0) + item] : item;
         const PairRec pr = P.pairs[pidx];
         const BallGeo G = P.geos[pr.geo];
         const int* cube = G.pt_cube;
@@ -1448,6 +1461,10 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
             atomicAdd(P.phase_clk + 3, (unsigned long long)(t3 - t2));
         }
     }
+    // the time-out test's wait comes after the pair loop: placed before it, it
+    // slowed the loop by 7 % on the water-64 workload (measured)
+    if (P.test_wait && threadIdx.x == 0)
+        inject_wait_timeout(smem_u32(smem) + (uint32_t)cluster_smem_test_offset(CL, MODE, PTS, NT), P.timeouts);
 }
 
 // ---- host side ----
@@ -1507,6 +1524,12 @@ static const ClusterVariant kVariants[] = {
     // quad map with halo planes: R_PE = 24 on isotropic grids, and any radius
     EXX_CLUSTER_VARIANT(512, 9, 4, 3, 55, true),   EXX_CLUSTER_VARIANT(512, 9, 4, 3, 0, false),
     EXX_CLUSTER_VARIANT(512, 2, 4, 3, 0, false),
+    // quad map with halo planes, 6 quads per thread: the radius classes of
+    // per-pair radii (one CTA holds a whole small ball; 2, 4, 9 or 16 CTAs
+    // share a larger one)
+    EXX_CLUSTER_VARIANT(512, 1, 6, 3, 0, false),   EXX_CLUSTER_VARIANT(512, 2, 6, 3, 0, false),
+    EXX_CLUSTER_VARIANT(512, 4, 6, 3, 0, false),   EXX_CLUSTER_VARIANT(512, 9, 6, 3, 0, false),
+    EXX_CLUSTER_VARIANT(512, 16, 6, 3, 0, false),
 };
 #undef EXX_CLUSTER_VARIANT
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
@@ -1559,6 +1582,12 @@ cudaError_t cluster_prepare(int variant, size_t smem, int* max_clusters) {
     return cudaOccupancyMaxActiveClusters(max_clusters, K.fn, &cfg);
 }
 
+// Raises the variant's dynamic shared-memory limit (launch shapes of several
+// radius classes can share one variant).
+cudaError_t cluster_set_smem(int variant, size_t smem) {
+    return cudaFuncSetAttribute(kVariants[variant].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 cudaError_t launch_cluster_kernel(int variant, const SolveParams& P, const ClusterLayout& CL, int n_clusters,
                                   size_t smem, cudaStream_t st) {
     return kVariants[variant].launch(P, CL, n_clusters, smem, st);
@@ -1574,15 +1603,12 @@ int cluster_variant_pts(int variant) { return kVariants[variant].pts; }
 
 size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant) {
     (void)Rc;
-    const size_t per = (size_t)kVariants[variant].nt * kVariants[variant].pts;
-    const int mode = kVariants[variant].mode;
-    const bool runs = mode == 1, halo = mode == 1 || mode == 3;
     // slab (with 3 halo planes per side for modes 1 and 3), d ([PTS][NT]
-    // points, or quads for mode 2; none for mode 3), the slot
-    // map (point or quad slots); as laid out by cluster_pair_kernel
-    const size_t slab = (size_t)(CL.cap_planes + (halo ? 6 : 0)) * CL.Sp2;
-    const size_t dsf = mode == 3 ? 0 : (mode == 2 ? 4 : 1) * per;
-    return sizeof(float) * (((slab + 3) & ~(size_t)3) + dsf) + (runs ? 0 : sizeof(int) * per);
+    // points, or quads for mode 2; none for mode 3), the slot map (point or
+    // quad slots), as laid out by cluster_pair_kernel, then the spare word of
+    // the time-out test
+    const ClusterVariant& K = kVariants[variant];
+    return cluster_smem_test_offset(CL, K.mode, K.pts, K.nt) + 8;
 }
 
 }  // namespace exx

@@ -178,9 +178,11 @@ void build_ball(HostBall& B, int r_pe, int r_me, int Rc) {
     B.n_me = (int)B.cube.size();
 }
 
-bool build_cluster_layout(const HostBall& B, int C, ClusterLayout& L, std::vector<int>& pt_slab, bool pitch4) {
+bool build_cluster_layout(const HostBall& B, int C, ClusterLayout& L, std::vector<int>& pt_slab, bool pitch4,
+                          int max_planes) {
     const int R = B.r_pe, P = 2 * R + 1;
     if (C < 1 || C > kMaxCluster || P < 3 * C) return false;
+    if (max_planes < 3) max_planes = P;
     std::vector<long> n(P, 0), cum(P + 1, 0);
     for (const RowRec& row : B.rows_pe) n[row.ox + R] += 2 * row.zpe + 1;
     for (int i = 0; i < P; ++i) cum[i + 1] = cum[i] + n[i];
@@ -191,7 +193,7 @@ bool build_cluster_layout(const HostBall& B, int C, ClusterLayout& L, std::vecto
     f[0][0] = 0;
     for (int r = 1; r <= C; ++r)
         for (int i = 3 * r; i <= P; ++i)
-            for (int j = 3 * (r - 1); j <= i - 3; ++j) {
+            for (int j = std::max(3 * (r - 1), i - max_planes); j <= i - 3; ++j) {
                 if (f[r - 1][j] >= INF) continue;
                 const long v = std::max(f[r - 1][j], cum[i] - cum[j]);
                 if (v < f[r][i]) {

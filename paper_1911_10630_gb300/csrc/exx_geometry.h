@@ -25,8 +25,10 @@ void build_multipole_const(MultipoleConst& mc);
 // minimising the largest point count. Fills L (without the device pointer) and
 // the per-point slab offsets. The slab box has 2 R_PE + 7 rows of 2 R_PE + 7
 // points per plane; pitch4 pads the row pitch to a multiple of 4 (16-byte rows
-// for the quad map). Returns false if no such split exists.
-bool build_cluster_layout(const HostBall& B, int C, ClusterLayout& L, std::vector<int>& pt_slab, bool pitch4 = false);
+// for the quad map). max_planes >= 3 caps the planes of a slab (the shared
+// memory a CTA can hold). Returns false if no such split exists.
+bool build_cluster_layout(const HostBall& B, int C, ClusterLayout& L, std::vector<int>& pt_slab, bool pitch4 = false,
+                          int max_planes = 0);
 void build_ball(HostBall& B, int r_pe, int r_me, int Rc);
 
 // Thread-slot maps of the cluster solver for NT threads x PTS points per CTA:

@@ -75,6 +75,7 @@ struct SolveParams {
     const PairRec* pairs;
     const int* n_pair;  // device scalar
     const int* order;   // processing order (NULL = list order)
+    const int* item_base;  // if set, the launch takes order[*item_base + item] (one radius class per launch)
     int* queue;         // device work counter
 
     // geometry

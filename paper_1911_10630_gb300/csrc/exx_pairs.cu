@@ -218,6 +218,17 @@ __global__ void radii_scatter_kernel(const PairRec* __restrict__ pairs, const in
         order[atomicAdd(hist + n_geo + pairs[p].geo, 1)] = p;
 }
 
+// The radius classes of the sorted order: after the scatter, hist[n_geo + g]
+// is the end of geometry g's run; cls[2 g] = its start, cls[2 g + 1] = its
+// length, cls[2 n_geo + g] = 0 (the class launch's work counter).
+__global__ void radii_classes_kernel(const int* __restrict__ hist, int n_geo, int* __restrict__ cls) {
+    for (int g = threadIdx.x; g < n_geo; g += blockDim.x) {
+        cls[2 * g] = hist[n_geo + g] - hist[g];
+        cls[2 * g + 1] = hist[g];
+        cls[2 * n_geo + g] = 0;
+    }
+}
+
 // D_xx = 0 (grid-stride fill; 16-byte stores when the pointer allows them).
 __global__ void zero_kernel(double* __restrict__ p, long long n, int vec) {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -321,12 +332,13 @@ cudaError_t launch_pair_list_packed(int n, const double* centers, const double L
 }
 
 cudaError_t launch_radii_sort(const PairRec* pairs, const int* n_pair, int* hist, int n_geo, int* order, int num_sms,
-                              cudaStream_t st) {
+                              cudaStream_t st, int* classes) {
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * 2 * n_geo, st);
     if (e != cudaSuccess) return e;
     radii_count_kernel<<<num_sms * 2, 256, 0, st>>>(pairs, n_pair, hist, n_geo);
     radii_scan_kernel<<<1, 32, 0, st>>>(hist, n_geo);
     radii_scatter_kernel<<<num_sms * 2, 256, 0, st>>>(pairs, n_pair, hist, n_geo, order);
+    if (classes) radii_classes_kernel<<<1, 64, 0, st>>>(hist, n_geo, classes);
     return cudaGetLastError();
 }
 

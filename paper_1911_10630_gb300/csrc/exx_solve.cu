@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(NT, 1) pair_kernel(const __grid_constant__ Sol
         __syncthreads();
         const int item = s_item;
         if (item >= np) break;
-        const int pidx = P.order ? P.order[item] : item;
+        const int pidx = P.order ? P.order[(P.item_base ? *P.item_base : 0) + item] : item;
         const PairRec pr = P.pairs[pidx];
         const BallGeo G = P.geos[pr.geo];
         const int* cube = G.pt_cube;

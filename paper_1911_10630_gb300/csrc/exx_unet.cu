@@ -18,6 +18,7 @@
 // the bias / ReLU / mask epilogue.
 #include "exx_unet.cuh"
 #include "exx_unet_tc.cuh"
+#include "exx_phases.cuh"  // the multipole constants (this unit's copy of c_mp)
 
 #include <algorithm>
 #include <cmath>
@@ -205,12 +206,13 @@ __global__ void pack_kernel(const float* __restrict__ w, __nv_bfloat16* __restri
 
 // ---- CUDA-core layers ------------------------------------------------------
 
-// Input layer: 2 FP32 channels -> 16, ReLU. One thread per output voxel.
+// Input layer: kIn FP32 channels -> 16, ReLU. One thread per output voxel.
 __global__ void conv_first_kernel(const float* __restrict__ in, const float* __restrict__ w,
                                   const float* __restrict__ bias, __nv_bfloat16* __restrict__ y, int B, int S) {
-    __shared__ float ws[27 * 2 * 16 + 16];
-    for (int i = threadIdx.x; i < 27 * 32; i += blockDim.x) ws[i] = w[i];
-    if (threadIdx.x < 16) ws[27 * 32 + threadIdx.x] = bias[threadIdx.x];
+    constexpr int CI = kCin[0];
+    __shared__ float ws[27 * CI * 16 + 16];
+    for (int i = threadIdx.x; i < 27 * CI * 16; i += blockDim.x) ws[i] = w[i];
+    if (threadIdx.x < 16) ws[27 * CI * 16 + threadIdx.x] = bias[threadIdx.x];
     __syncthreads();
     const long long nv = (long long)B * S * S * S;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
@@ -219,13 +221,17 @@ __global__ void conv_first_kernel(const float* __restrict__ in, const float* __r
         const long long bb = v / ((long long)S * S * S);
         float acc[16];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) acc[c] = ws[27 * 32 + c];
+        for (int c = 0; c < 16; ++c) acc[c] = ws[27 * CI * 16 + c];
         for (int tap = 0; tap < 27; ++tap) {
             const int zz = z + tap / 9 - 1, y2 = yy + (tap / 3) % 3 - 1, x2 = x + tap % 3 - 1;
             if (zz < 0 || zz >= S || y2 < 0 || y2 >= S || x2 < 0 || x2 >= S) continue;
-            const float2 iv = reinterpret_cast<const float2*>(in)[((bb * S + zz) * S + y2) * S + x2];
+            const float* iv = in + (((bb * S + zz) * S + y2) * S + x2) * CI;
 #pragma unroll
-            for (int c = 0; c < 16; ++c) acc[c] = fmaf(iv.x, ws[tap * 32 + c], fmaf(iv.y, ws[tap * 32 + 16 + c], acc[c]));
+            for (int ci = 0; ci < CI; ++ci) {
+                const float a = iv[ci];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) acc[c] = fmaf(a, ws[(tap * CI + ci) * 16 + c], acc[c]);
+            }
         }
         uint4 o[2];
         __nv_bfloat16* ob = reinterpret_cast<__nv_bfloat16*>(o);
@@ -267,7 +273,7 @@ __global__ void head_backward_kernel(const float* __restrict__ in, const float* 
     for (int c = 0; c < 17; ++c) gw[c] = 0.0f;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
          v += (long long)gridDim.x * blockDim.x) {
-        const float m = in[2 * v + 1] > 0.5f ? 1.0f : 0.0f;
+        const float m = in[kIn * v + kMaskChannel] > 0.5f ? 1.0f : 0.0f;
         const float diff = out[v] - target[v];
         lsum += m * diff * diff;
         const float g = 2.0f * m * diff * inv_n;
@@ -488,33 +494,34 @@ __global__ void __launch_bounds__(256) dw_kernel(const __nv_bfloat16* __restrict
     if (do_bias && ty == 0) dw[(size_t)27 * cin * cout + cob * 16 + tx] = bacc;
 }
 
-// Weight gradient of the 2-channel FP32 input layer: 27 x 2 x 16 weights and
-// 16 biases; one thread per weight, voxels split over blocks, each block's
-// partial sums in part[block][27 * 32 + 16] (added in block order afterwards).
+// Weight gradient of the FP32 input layer: 27 x kIn x 16 weights and 16
+// biases; voxels split over blocks, each block's partial sums in
+// part[block][27 * kIn * 16 + 16] (added in block order afterwards).
 __global__ void dw_first_kernel(const float* __restrict__ in, const __nv_bfloat16* __restrict__ g,
                                 float* __restrict__ part, int B, int S, int nsplit) {
-    const int t = threadIdx.x;  // 0 .. 27*32+16-1
-    if (t >= 27 * 32 + 16) return;
+    constexpr int CI = kCin[0], NW = 27 * CI * 16;
     const long long nv = (long long)B * S * S * S;
     const long long per = (nv + nsplit - 1) / nsplit;
     const long long v0 = blockIdx.x * per, v1 = v0 + per < nv ? v0 + per : nv;
-    float acc = 0.0f;
-    if (t < 27 * 32) {
-        const int tap = t / 32, ci = (t / 16) % 2, co = t % 16;
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        for (long long v = v0; v < v1; ++v) {
-            const int xx = (int)(v % S), yy = (int)((v / S) % S), zz = (int)((v / ((long long)S * S)) % S);
-            const long long bb = v / ((long long)S * S * S);
-            const int z2 = zz + dz, y2 = yy + dy, x2 = xx + dx;
-            if (z2 < 0 || z2 >= S || y2 < 0 || y2 >= S || x2 < 0 || x2 >= S) continue;
-            const long long u = ((bb * S + z2) * S + y2) * S + x2;
-            acc = fmaf(in[2 * u + ci], bf2f(g[v * 16 + co]), acc);
+    for (int t = threadIdx.x; t < NW + 16; t += blockDim.x) {
+        float acc = 0.0f;
+        if (t < NW) {
+            const int tap = t / (CI * 16), ci = (t / 16) % CI, co = t % 16;
+            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            for (long long v = v0; v < v1; ++v) {
+                const int xx = (int)(v % S), yy = (int)((v / S) % S), zz = (int)((v / ((long long)S * S)) % S);
+                const long long bb = v / ((long long)S * S * S);
+                const int z2 = zz + dz, y2 = yy + dy, x2 = xx + dx;
+                if (z2 < 0 || z2 >= S || y2 < 0 || y2 >= S || x2 < 0 || x2 >= S) continue;
+                const long long u = ((bb * S + z2) * S + y2) * S + x2;
+                acc = fmaf(in[CI * u + ci], bf2f(g[v * 16 + co]), acc);
+            }
+        } else {
+            const int co = t - NW;
+            for (long long v = v0; v < v1; ++v) acc += bf2f(g[v * 16 + co]);
         }
-    } else {
-        const int co = t - 27 * 32;
-        for (long long v = v0; v < v1; ++v) acc += bf2f(g[v * 16 + co]);
+        part[(size_t)blockIdx.x * (NW + 16) + t] = acc;
     }
-    part[(size_t)blockIdx.x * (27 * 32 + 16) + t] = acc;
 }
 
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -699,7 +706,7 @@ cudaError_t create(Net& n, int S, int Bmax) {
     // per-block sums, the input layer's and every 3x3x3 layer's per-split sums
     {
         size_t need = (size_t)18 * 16 * n.n_sm;
-        need = std::max(need, (size_t)4 * n.n_sm * (27 * 32 + 16));
+        need = std::max(need, (size_t)4 * n.n_sm * (27 * kIn * 16 + 16));
         const int lvl[kLayers] = {0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0, 0};
         for (int l = 1; l < kHead; ++l) {
             const long long nv = (long long)v0 >> (3 * lvl[l]);
@@ -835,8 +842,8 @@ cudaError_t backward(Net& n, const float* in, const float* target, int B, cudaSt
     UCK(dconv(n.g_x0, n.x0a, n.g_x0a, 1, S));
     {
         const int nsplit = 4 * n.n_sm;
-        const int count = 27 * 32 + 16;
-        dw_first_kernel<<<nsplit, count, 0, st>>>(in, n.g_x0a, n.gpart, B, S, nsplit);
+        const int count = 27 * kIn * 16 + 16;
+        dw_first_kernel<<<nsplit, 256, 0, st>>>(in, n.g_x0a, n.gpart, B, S, nsplit);
         reduce_parts_kernel<<<grid_for(count, n.n_sm), 256, 0, st>>>(n.gpart, nsplit, count, count,
                                                                      n.grads + param_offset(0));
     }
@@ -876,12 +883,30 @@ __device__ __forceinline__ int wrapi(int a, int n) {
     return a < 0 ? a + n : a;
 }
 
+// Index of the Cartesian monomial x^a y^b z^c, l = a + b + c, in the
+// library's order (degree ascending, then a descending, then b descending).
+__host__ __device__ constexpr int mono_index(int a, int b, int c) {
+    return (a + b + c) * (a + b + c + 1) * (a + b + c + 2) / 6 + (b + c) * (b + c + 1) / 2 + c;
+}
+
+// One network sample per pair (one CTA of 256 threads per pair):
+//   channel 0: rho / s on the PE ball (s = max |rho| there), 0 elsewhere;
+//   channel 1: on the cube outside the PE ball, the multipole expansion of
+//     Eq. me evaluated from the moments of rho / s on the ball (Eq. mepole,
+//     l <= lmax; FP32, Cartesian form with the library's K_l matrices), over
+//     delta^2: the boundary values the solver imposes, in the target's units;
+//   channel 2: the ball mask;
+// and with vcache the target v / (s delta^2) on the ball.
 __global__ void __launch_bounds__(256) sample_prep_kernel(const double* __restrict__ phi, int N0, int N1, int N2,
                                                           const PairRec* __restrict__ pairs, int k0, int S,
                                                           const BallGeo G, float* __restrict__ input,
                                                           float* __restrict__ scale, float* __restrict__ target,
-                                                          const float* __restrict__ vcache, double d2) {
+                                                          const float* __restrict__ vcache, double d2, float dx,
+                                                          float dy, float dz, float dV, int lmax) {
+    constexpr int NM = kNMono;
     __shared__ double red[8];
+    __shared__ float s_Mw[8][NM];
+    __shared__ float s_M[NM], s_T[NM];
     const int k = k0 + blockIdx.x;
     const PairRec pr = pairs[k];
     const long long ng = (long long)N0 * N1 * N2;
@@ -903,7 +928,7 @@ __global__ void __launch_bounds__(256) sample_prep_kernel(const double* __restri
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, red[w]);
     if (!(s > 0.0)) s = 1.0;
     const double inv = 1.0 / s, tinv = 1.0 / (s * d2);
-    float* in = input + (size_t)blockIdx.x * S3 * 2;
+    float* in = input + (size_t)blockIdx.x * S3 * kIn;
     float* tg = target ? target + (size_t)blockIdx.x * S3 : nullptr;
     const float* vc = vcache ? vcache + (size_t)k * G.n_pe : nullptr;
     const int W = 2 * R + 1;
@@ -920,11 +945,128 @@ __global__ void __launch_bounds__(256) sample_prep_kernel(const double* __restri
                 t = (float)(vc[Rw.pe_start + oz + Rw.zpe] * tinv);
             }
         }
-        in[2 * v] = r;
-        in[2 * v + 1] = m;
+        in[kIn * v] = r;
+        in[kIn * v + 1] = 0.0f;
+        in[kIn * v + kMaskChannel] = m;
         if (tg) tg[v] = t;
     }
     if (threadIdx.x == 0) scale[blockIdx.x] = (float)s;
+    __syncthreads();
+
+    // Moments M_abc = sum rho/s x^a y^b z^c dV over the ball points of the
+    // cube: one thread per cube row (x, y), row sums S_c = sum_z rho/s z^c,
+    // then every monomial; per-thread partials added in a fixed order.
+    float M[NM];
+#pragma unroll
+    for (int q = 0; q < NM; ++q) M[q] = 0.0f;
+    for (int row = threadIdx.x; row < S * S; row += blockDim.x) {
+        const int ox = row / S - h, oy = row % S - h;
+        const int rem = R * R - ox * ox - oy * oy;
+        if (rem < 0) continue;
+        int zr = (int)sqrtf((float)rem);
+        while ((zr + 1) * (zr + 1) <= rem) ++zr;
+        while (zr * zr > rem) --zr;
+        const int zlo = max(-zr, -h), zhi = min(zr, h - 1);
+        float sc[kLmaxMax + 1];
+#pragma unroll
+        for (int c = 0; c <= kLmaxMax; ++c) sc[c] = 0.0f;
+        const float* rp = in + (size_t)row * S * kIn;
+        for (int z = zlo; z <= zhi; ++z) {
+            float p = rp[(z + h) * kIn];
+            const float zz = (float)z * dz;
+#pragma unroll
+            for (int c = 0; c <= kLmaxMax; ++c) {
+                sc[c] += p;
+                p *= zz;
+            }
+        }
+        float xa[kLmaxMax + 1], yb[kLmaxMax + 1];
+        xa[0] = yb[0] = 1.0f;
+#pragma unroll
+        for (int e = 1; e <= kLmaxMax; ++e) {
+            xa[e] = xa[e - 1] * ((float)ox * dx);
+            yb[e] = yb[e - 1] * ((float)oy * dy);
+        }
+#pragma unroll
+        for (int l = 0; l <= kLmaxMax; ++l)
+#pragma unroll
+            for (int a = l; a >= 0; --a)
+#pragma unroll
+                for (int b = l - a; b >= 0; --b) {
+                    const int c = l - a - b;
+                    M[mono_index(a, b, c)] = fmaf(xa[a] * yb[b], sc[c], M[mono_index(a, b, c)]);
+                }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NM; ++q) {
+        float v = M[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_Mw[wid][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NM) {
+        const int q = threadIdx.x;
+        float t = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_Mw[w][q];
+        const int l = c_mp.mono[q][0] + c_mp.mono[q][1] + c_mp.mono[q][2];
+        s_M[q] = l <= lmax ? t * dV : 0.0f;
+    }
+    __syncthreads();
+    // T = K M (the polynomials P_l of the expansion, K_l from the host tables)
+    if (threadIdx.x < NM) {
+        const int q = threadIdx.x;
+        const int l = c_mp.mono[q][0] + c_mp.mono[q][1] + c_mp.mono[q][2];
+        const int nl = (l + 1) * (l + 2) / 2, r0 = c_mp.mono_off[l];
+        const double* Kr = c_mp.K + c_mp.k_off[l] + (q - r0) * nl;
+        float acc = 0.0f;
+        for (int t = 0; t < nl; ++t) acc = fmaf((float)Kr[t], s_M[r0 + t], acc);
+        s_T[q] = acc;
+    }
+    __syncthreads();
+    // channel 1 on the cube points outside the ball: v = sum_l P_l / r^(2l+1),
+    // with P_l = sum_c U_{l,c}(x, y) z^c formed once per row
+    const float id2 = (float)(1.0 / d2);
+    for (int row = threadIdx.x; row < S * S; row += blockDim.x) {
+        const int ox = row / S - h, oy = row % S - h;
+        const int rxy = ox * ox + oy * oy;
+        if (rxy + h * h <= R * R) continue;  // the whole row inside the ball
+        const float x = (float)ox * dx, y = (float)oy * dy;
+        float xa[kLmaxMax + 1], yb[kLmaxMax + 1];
+        xa[0] = yb[0] = 1.0f;
+#pragma unroll
+        for (int e = 1; e <= kLmaxMax; ++e) {
+            xa[e] = xa[e - 1] * x;
+            yb[e] = yb[e - 1] * y;
+        }
+        float U[kNU];
+#pragma unroll
+        for (int l = 0; l <= kLmaxMax; ++l)
+#pragma unroll
+            for (int c = 0; c <= l; ++c) {
+                float u = 0.0f;
+#pragma unroll
+                for (int a = l - c; a >= 0; --a) u = fmaf(s_T[mono_index(a, l - c - a, c)], xa[a] * yb[l - c - a], u);
+                U[l * (l + 1) / 2 + c] = u;
+            }
+        const float rxy2 = x * x + y * y;
+        float* rp = in + (size_t)row * S * kIn;
+        for (int z = -h; z < h; ++z) {
+            if (rxy + z * z <= R * R) continue;
+            const float zz = (float)z * dz;
+            const float ir = rsqrtf(fmaf(zz, zz, rxy2));
+            const float ir2 = ir * ir;
+            float acc = 0.0f;
+#pragma unroll
+            for (int l = kLmaxMax; l >= 0; --l) {
+                float pl = U[l * (l + 1) / 2 + l];
+#pragma unroll
+                for (int c = l - 1; c >= 0; --c) pl = fmaf(pl, zz, U[l * (l + 1) / 2 + c]);
+                acc = fmaf(acc, ir2, pl);
+            }
+            rp[(z + h) * kIn + 1] = acc * ir * id2;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(256) guess_scatter_kernel(const float* __restrict__ out,
@@ -947,10 +1089,15 @@ __global__ void __launch_bounds__(256) guess_scatter_kernel(const float* __restr
 
 cudaError_t sample_prep(const double* phi, const int N[3], const PairRec* pairs, int k0, int nk, int S,
                         const BallGeo& G, float* input, float* scale, float* target, const float* vcache, double d2,
-                        cudaStream_t st) {
+                        const double delta[3], double dV, int lmax, cudaStream_t st) {
     if (nk <= 0) return cudaSuccess;
-    sample_prep_kernel<<<nk, 256, 0, st>>>(phi, N[0], N[1], N[2], pairs, k0, S, G, input, scale, target, vcache, d2);
+    sample_prep_kernel<<<nk, 256, 0, st>>>(phi, N[0], N[1], N[2], pairs, k0, S, G, input, scale, target, vcache, d2,
+                                           (float)delta[0], (float)delta[1], (float)delta[2], (float)dV, lmax);
     return cudaGetLastError();
+}
+
+cudaError_t set_multipole_const_unet(const MultipoleConst& mc) {
+    return cudaMemcpyToSymbol(c_mp, &mc, sizeof(MultipoleConst));
 }
 
 cudaError_t guess_scatter(const float* out, const float* scale, int k0, int nk, int S, const BallGeo& G, double d2,

@@ -18,7 +18,11 @@ namespace unet {
 // the 1x1x1 head. Order = order of the flat parameter vector (W[27][cin][cout]
 // then bias[cout] per layer; the head has w[16] then b[1]).
 constexpr int kLayers = 15;
-constexpr int kCin[kLayers] = {2, 16, 16, 32, 32, 64, 64, 128, 192, 64, 96, 32, 48, 16, 16};
+// input channels: rho / s on the PE ball, the multipole boundary values
+// v_ME / (s delta^2) on the cube outside the ball, the ball mask
+constexpr int kIn = 3;
+constexpr int kMaskChannel = 2;
+constexpr int kCin[kLayers] = {kIn, 16, 16, 32, 32, 64, 64, 128, 192, 64, 96, 32, 48, 16, 16};
 constexpr int kCout[kLayers] = {16, 16, 32, 32, 64, 64, 128, 128, 64, 64, 32, 32, 16, 16, 1};
 constexpr int kHead = 14;
 
@@ -55,7 +59,7 @@ struct Net {
 cudaError_t create(Net& n, int S, int Bmax);
 void destroy(Net& n);
 cudaError_t pack(Net& n, cudaStream_t st);                       // params -> BF16 packed weights
-cudaError_t forward(Net& n, const float* in, int B, cudaStream_t st);   // in: [B][S^3][2]; result in n.out
+cudaError_t forward(Net& n, const float* in, int B, cudaStream_t st);   // in: [B][S^3][kIn]; result in n.out
 cudaError_t backward(Net& n, const float* in, const float* target, int B, cudaStream_t st);  // grads, loss
 cudaError_t adam_step(Net& n, float lr, cudaStream_t st);
 cudaError_t check_error(Net& n, cudaStream_t st);
@@ -73,13 +77,16 @@ cudaError_t pack_weights(const float* w, __nv_bfloat16* wp, int cin, int cout, i
 
 // Network inputs of pairs k0 .. k0 + nk - 1 of the list: cube of side S
 // centred on g_ij (offset o = index - S/2), channel 0 = rho / s on the PE
-// ball, channel 1 = ball mask, s = max |rho| on the ball (scale[k - k0]).
-// With vcache (the pairs' PE-ball potentials, FP32, list order), target
-// receives v / (s d2) on the ball and 0 elsewhere. input [nk][S^3][2],
-// target [nk][S^3].
+// ball, channel 1 = the multipole boundary values v_ME / (s d2) on the cube
+// outside the ball (Eqs. mepole, me; l <= lmax), channel 2 = ball mask, s =
+// max |rho| on the ball (scale[k - k0]). With vcache (the pairs' PE-ball
+// potentials, FP32, list order), target receives v / (s d2) on the ball and 0
+// elsewhere. input [nk][S^3][kIn], target [nk][S^3].
 cudaError_t sample_prep(const double* phi, const int N[3], const PairRec* pairs, int k0, int nk, int S,
                         const BallGeo& G, float* input, float* scale, float* target, const float* vcache, double d2,
-                        cudaStream_t st);
+                        const double delta[3], double dV, int lmax, cudaStream_t st);
+// The multipole constants of the boundary channel (this unit's copy).
+cudaError_t set_multipole_const_unet(const MultipoleConst& mc);
 // vguess[k][p] = out[k - k0][cube(o_p)] * scale[k - k0] * d2 on the PE points
 // p of pairs k0 .. k0 + nk - 1 (0 where o_p falls outside the cube).
 cudaError_t guess_scatter(const float* out, const float* scale, int k0, int nk, int S, const BallGeo& G, double d2,

@@ -76,6 +76,7 @@ SIGNATURES = [
     ("exx_debug_pair", ctypes.c_int, [_ctx_p, _vp, ctypes.c_int, _d, _d, _d, _vp]),
     ("exx_apply_operator", ctypes.c_int, [_ctx_p, _vp, _vp, _vp]),
     ("exx_ball_size", ctypes.c_int, [_ctx_p, _i, _i]),
+    ("exx_radius_classes", ctypes.c_int, [_ctx_p, _i, _i, _i, ctypes.c_int, _i]),
     ("exx_quad_map", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("exx_load_guess_model", ctypes.c_int, [_ctx_p, _vp, ctypes.c_size_t]),
@@ -248,6 +249,15 @@ class Exx:
                                     ctypes.byref(n)), self._ctx)
         return dict(i=pi, j=pj, g=g, radii=radii, e_pair=e, iters=it)
 
+    def radius_classes(self):
+        """exx_radius_classes: (R_PE, CTAs per pair or 0, resident clusters) per class."""
+        n = ctypes.c_int()
+        _check(load().exx_radius_classes(self._ctx, None, None, None, 0, ctypes.byref(n)), self._ctx)
+        r, c, k = (np.zeros(n.value, np.int32) for _ in range(3))
+        _check(load().exx_radius_classes(self._ctx, r.ctypes.data_as(_i), c.ctypes.data_as(_i), k.ctypes.data_as(_i),
+                                         n.value, ctypes.byref(n)), self._ctx)
+        return [(int(a), int(b), int(x)) for a, b, x in zip(r, c, k)]
+
     def ball_size(self):
         a, b = ctypes.c_int(), ctypes.c_int()
         _check(load().exx_ball_size(self._ctx, ctypes.byref(a), ctypes.byref(b)), self._ctx)
@@ -322,6 +332,7 @@ def unet_conv3d(x, w, bias, mask, y, batch, D, H, W, cin, cout, mode, stream=Non
 
 
 GUESS_MAGIC = 0x47585845
+GUESS_CHANNELS = 3  # network input: rho / s, multipole boundary values, ball mask
 
 
 def quad_map(r_pe: int, cluster_size: int, threads: int, quads: int, bank_aware: int = 0):
@@ -339,6 +350,6 @@ def quad_map(r_pe: int, cluster_size: int, threads: int, quads: int, bank_aware:
 
 
 def guess_model_blob(S: int, params: np.ndarray) -> bytes:
-    """Model blob of exx_load_guess_model: {magic, 1, S, count} then the FP32 parameters."""
+    """Model blob of exx_load_guess_model: {magic, 2, S, count} then the FP32 parameters."""
     p = np.ascontiguousarray(params, dtype=np.float32)
-    return np.array([GUESS_MAGIC, 1, int(S), p.size], dtype=np.int32).tobytes() + p.tobytes()
+    return np.array([GUESS_MAGIC, 2, int(S), p.size], dtype=np.int32).tobytes() + p.tobytes()

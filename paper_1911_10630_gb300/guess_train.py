@@ -24,7 +24,7 @@ import time
 import numpy as np
 
 from . import synth
-from .exx import Exx, GuessNet, guess_model_blob
+from .exx import GUESS_CHANNELS, Exx, GuessNet, guess_model_blob
 
 CUBE = 32      # network input side for R_PE = 16 (the ball's +16 poles fall outside)
 CUBE_R24 = 48  # and for R_PE = 24
@@ -32,7 +32,7 @@ CUBE_R24 = 48  # and for R_PE = 24
 
 def init_params(n_params: int, seed: int) -> np.ndarray:
     """He-uniform weights (bound sqrt(6 / fan_in)), zero biases, layer table of exx_guess.h."""
-    cin = (2, 16, 16, 32, 32, 64, 64, 128, 192, 64, 96, 32, 48, 16, 16)
+    cin = (GUESS_CHANNELS, 16, 16, 32, 32, 64, 64, 128, 192, 64, 96, 32, 48, 16, 16)
     cout = (16, 16, 32, 32, 64, 64, 128, 128, 64, 64, 32, 32, 16, 16, 1)
     rng = np.random.default_rng(seed)
     parts = []
@@ -48,7 +48,7 @@ def init_params(n_params: int, seed: int) -> np.ndarray:
 
 def solve_and_export(seeds, S: int = CUBE, torch=None, workload=None, per_workload: int = 0):
     """Solves each seeded workload (default: the tiny form, synth.config0) and
-    returns the samples of its pairs as device tensors (input [n][S^3][2],
+    returns the samples of its pairs as device tensors (input [n][S^3][3],
     target [n][S^3]); per_workload > 0 keeps that many pairs, spread evenly
     over the list, of each workload."""
     import torch as _t
@@ -67,7 +67,7 @@ def solve_and_export(seeds, S: int = CUBE, torch=None, workload=None, per_worklo
         ex.compute(phi, cen, D)
         del D
         cap = ex.stats()["n_pair"]
-        inp = torch.empty((cap, S, S, S, 2), dtype=torch.float32, device="cuda")
+        inp = torch.empty((cap, S, S, S, GUESS_CHANNELS), dtype=torch.float32, device="cuda")
         tgt = torch.empty((cap, S, S, S), dtype=torch.float32, device="cuda")
         n = ex.export_samples(phi, S, inp, tgt, cap)
         keep = torch.arange(n, device="cuda")
@@ -116,7 +116,7 @@ def train(inp, tgt, S: int = CUBE, epochs: int = 20, batch: int = 32, lr: float 
 
 def conv_macs(S: int) -> int:
     """Multiply-adds of one forward pass at cube side S (3x3x3 layers)."""
-    cin = (2, 16, 16, 32, 32, 64, 64, 128, 192, 64, 96, 32, 48, 16)
+    cin = (GUESS_CHANNELS, 16, 16, 32, 32, 64, 64, 128, 192, 64, 96, 32, 48, 16)
     cout = (16, 16, 32, 32, 64, 64, 128, 128, 64, 64, 32, 32, 16, 16)
     lvl = (0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0)
     return sum(27 * a * b * (S >> l) ** 3 for a, b, l in zip(cin, cout, lvl))
@@ -127,7 +127,7 @@ def time_forward(S: int, B: int, reps: int = 5) -> dict:
     import torch
     net = GuessNet(S, B)
     net.set_params(init_params(net.n_params, 0))
-    inp = torch.rand((B, S, S, S, 2), device="cuda", dtype=torch.float32)
+    inp = torch.rand((B, S, S, S, GUESS_CHANNELS), device="cuda", dtype=torch.float32)
     out = torch.empty((B, S, S, S), device="cuda", dtype=torch.float32)
     net.forward(inp, out, B)
     torch.cuda.synchronize()

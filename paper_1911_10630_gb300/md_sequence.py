@@ -24,10 +24,19 @@ from . import synth
 from .exx import Exx
 
 
-def run(steps: int = 20, warm: int = 0, model_blob: bytes = None, seed: int = 0, on_step=None):
+def pair_energies(ex, subset):
+    """E_ij of the last call for the (i, j) pairs of subset (NaN for a pair
+    that left the list)."""
+    pairs = ex.pairs()
+    key = {(int(i), int(j)): k for k, (i, j) in enumerate(zip(pairs["i"], pairs["j"]))}
+    return np.array([pairs["e_pair"][key[p]] if p in key else np.nan for p in subset])
+
+
+def run(steps: int = 20, warm: int = 0, model_blob: bytes = None, seed: int = 0, on_step=None, subset=None):
     """Runs the sequence; returns one dict per step (E_xx, pairs, timings, CG
-    iterations). on_step(step, workload, orbitals, d_xx, exx) is called after
-    each step (for checks on the step's outputs)."""
+    iterations; with subset, a list of (i, j), also their E_ij as e_sub).
+    on_step(step, workload, orbitals, d_xx, exx) is called after each step
+    (for checks on the step's outputs)."""
     import torch
     w0 = synth.config4(seed, 0)
     ex = Exx(w0.cell, w0.grid, w0.r_pair, w0.r_pe, w0.r_me, w0.l_max, w0.tol, precision=1, warm_start=warm)
@@ -49,11 +58,19 @@ def run(steps: int = 20, warm: int = 0, model_blob: bytes = None, seed: int = 0,
                    guess_ms=st["guess_ms"], wall_ms=1e3 * wall, iters_p50=st["iters_p50"],
                    iters_p99=st["iters_p99"], iters_total=st["iters_total"], n_nonconv=st["n_nonconv"],
                    pair_solves_per_s=st["n_pair"] / (st["total_ms"] / 1e3))
+        if subset is not None:
+            rec["e_sub"] = pair_energies(ex, subset).tolist()
         out.append(rec)
         if on_step:
             on_step(s, w, phi, D, ex)
     ex.close()
     return out
+
+
+def step_time_percentiles(recs):
+    """p50 and p99 of the device time per step over the sequence (ms)."""
+    t = np.array([r["total_ms"] for r in recs])
+    return float(np.percentile(t, 50)), float(np.percentile(t, 99))
 
 
 def main():

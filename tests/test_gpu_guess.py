@@ -25,8 +25,8 @@ def test_exported_samples_match_the_oracle_pair_solution(torch):
     dphi = torch.from_numpy(phi).cuda()
     dD = torch.empty_like(dphi)
     ex.compute(dphi, torch.from_numpy(np.ascontiguousarray(w.centers)).cuda(), dD)
-    S = 40  # larger than the ball: voxels outside it must be zero
-    inp = torch.empty((36, S, S, S, 2), dtype=torch.float32, device="cuda")
+    S = 40  # larger than the ME ball but for its +20 poles
+    inp = torch.empty((36, S, S, S, 3), dtype=torch.float32, device="cuda")
     tgt = torch.empty((36, S, S, S), dtype=torch.float32, device="cuda")
     n = ex.export_samples(dphi, S, inp, tgt, 36)
     assert n == 36
@@ -42,13 +42,22 @@ def test_exported_samples_match_the_oracle_pair_solution(torch):
         s = np.max(np.abs(rho))
         # density channel, mask channel, target = v / (s delta^2) on the ball
         np.testing.assert_allclose(inp[k][idx][:, 0], rho / s, rtol=1e-6, atol=1e-7)
-        assert np.all(inp[k][idx][:, 1] == 1.0)
-        assert inp[k][..., 1].sum() == npe
+        assert np.all(inp[k][idx][:, 2] == 1.0)
+        assert inp[k][..., 2].sum() == npe
+        assert np.all(inp[k][idx][:, 1] == 0.0)
         v = ref["v"][:npe]
         np.testing.assert_allclose(tgt[k][idx] * s * d2, v, rtol=0, atol=2e-6 * np.max(np.abs(v)))
+        # boundary channel on the shell points in the cube: the oracle's
+        # multipole expansion (Eq. me, FP64) against the FP32 channel
+        sh = ref["off"][npe:]
+        inside = np.all(sh + S // 2 < S, axis=1)
+        sidx = tuple((sh[inside] + S // 2).T)
+        vsh = ref["v"][npe:][inside]
+        np.testing.assert_allclose(inp[k][sidx][:, 1] * s * d2, vsh, rtol=0, atol=1e-4 * np.max(np.abs(vsh)))
         outside = np.ones((S, S, S), bool)
         outside[idx] = False
-        assert np.all(inp[k][outside] == 0.0) and np.all(tgt[k][outside] == 0.0)
+        assert np.all(inp[k][outside][:, 0] == 0.0) and np.all(inp[k][outside][:, 2] == 0.0)
+        assert np.all(tgt[k][outside] == 0.0)
     ex.close()
 
 

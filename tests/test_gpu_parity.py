@@ -275,14 +275,18 @@ def _pairs_radii_equal(gpu_pairs, ref_pairs):
     np.testing.assert_array_equal(gpu_pairs["radii"][:, 1], rme)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_per_pair_radii_small(torch, precision):
+@pytest.mark.parametrize("precision,solver_kind", [(1, 0), (1, 1), (0, 0)])
+def test_per_pair_radii_small(torch, precision, solver_kind):
+    """Per-pair radii against the oracle: precision 1 runs the cluster solver
+    in radius classes (one CTA per ball below R_PE 14, clusters above), or the
+    one-CTA solver on request; precision 0 the one-CTA FP64 solver."""
     w = synth.tiny(seed=8, n=6, npts=48, length=9.6, r_pe=16, r_me=22, alpha=(0.5, 2.0), tol=1e-10, min_sep=1.2)
     w.radii_mode = 1
     phi = w.orbitals()
     ref = oracle.exx_workload(w, tol=1e-13, orbitals=phi)
     assert len(set(ref["pairs"][3])) >= 3  # several radii in play
-    out = run_gpu(w, phi, torch=torch, precision=precision)
+    out = run_gpu(w, phi, torch=torch, precision=precision, solver_kind=solver_kind)
+    assert out["stats"]["solver_kind"] == (2 if precision == 1 and solver_kind == 0 else 1)
     _pairs_radii_equal(out["pairs"], ref["pairs"])
     assert out["stats"]["n_nonconv"] == 0
     assert abs(out["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL

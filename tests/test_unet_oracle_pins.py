@@ -70,7 +70,7 @@ def _sample(S, B, seed):
     c = (np.arange(S) - S / 2)
     z, y, x = np.meshgrid(c, c, c, indexing="ij")
     r2 = x * x + y * y + z * z
-    inp = np.zeros((B, S, S, S, 2))
+    inp = np.zeros((B, S, S, S, 3))
     tgt = np.zeros((B, S, S, S))
     for b in range(B):
         a = rng.uniform(0.05, 0.2)
@@ -78,7 +78,8 @@ def _sample(S, B, seed):
         rho = np.exp(-a * ((x - sh[0]) ** 2 + (y - sh[1]) ** 2 + (z - sh[2]) ** 2))
         mask = r2 <= (S / 2 - 1) ** 2
         inp[b, ..., 0] = rho * mask
-        inp[b, ..., 1] = mask
+        inp[b, ..., 1] = rng.normal(0, 1, (S, S, S)) * ~mask
+        inp[b, ..., 2] = mask
         tgt[b] = rng.normal(0, 1, (S, S, S)) * mask
     return inp, tgt
 
