@@ -185,6 +185,8 @@ typedef struct {
                               plus pairs whose E_ij came out NaN or Inf (a NaN or
                               Inf orbital value on the pair's PE ball propagates
                               into E_ij, E_xx and D_xx; nothing is masked)      */
+    int n_clipped;         /* exx_compute_boxes: pairs whose ME ball is not inside
+                              both orbitals' boxes (0 for full grids)           */
 } exx_stats;
 
 /* Defaults described in exx_options. */
@@ -230,6 +232,31 @@ exx_status exx_init(exx_ctx **out, const double cell[3], const int grid[3], doub
  */
 exx_status exx_compute(exx_ctx *ctx, const double *orbitals, const double *centers, int n,
                        const double *alphas, double *e_xx, double *d_xx, void *stream);
+
+/*
+ * exx_compute on orbitals stored as compact boxes instead of full grids: the
+ * paper's outlook redistributes the orbitals by their compact supports
+ * (Sec. IV.B); here each orbital is kept only on a periodic box of grid points
+ * around its support, which cuts the memory of orbitals and D_xx by the ratio
+ * of box to grid volume (about 4x for 1024 orbitals on 190^3 points).
+ *   boxes     device, [n][B0][B1][B2] FP64: orbital i on the grid points
+ *             (origin_i + b) mod N, 0 <= b < box_dim, C order, read only
+ *   origin    device, [n][3] int: the boxes' corners, each in [0, N)
+ *   box_dim   host int[3]: B_a, 2 R_ME + 1 <= B_a <= N_a, the same for all
+ *             orbitals
+ *   centers, n, alphas, e_xx, stream: as for exx_compute
+ *   d_boxes   device, same layout as boxes: D_xx^i on orbital i's box
+ *             (zeroed by the library first)
+ * An orbital counts as zero outside its box, and D_xx^i is kept only on it.
+ * When every pair's ME ball lies inside both of its orbitals' boxes the
+ * results equal exx_compute's on the full grids; boxes of side
+ * 2 (ceil(R_pair / (2 delta)) + R_ME + 1) + 1 around the orbitals' nearest grid
+ * points guarantee it. exx_get_stats reports the pairs for which it fails
+ * (n_clipped). Errors: as exx_compute; EXX_EINVAL for bad box_dim.
+ */
+exx_status exx_compute_boxes(exx_ctx *ctx, const double *boxes, const int *origin, const int box_dim[3],
+                             const double *centers, int n, const double *alphas, double *e_xx, double *d_boxes,
+                             void *stream);
 
 /*
  * Same as exx_compute with HOST buffers: copies orbitals, centers (and alphas)

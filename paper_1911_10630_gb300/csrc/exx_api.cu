@@ -26,6 +26,8 @@ cudaError_t launch_radii_sort(const PairRec* pairs, const int* n_pair, int* hist
                               cudaStream_t st, int* classes = nullptr);
 cudaError_t cluster_set_smem(int variant, size_t smem);
 cudaError_t launch_zero(double* p, long long n, int num_sms, cudaStream_t st);
+cudaError_t launch_box_clip(const PairRec* pairs, const int* n_pair, const int* box_org, const int bdim[3],
+                            const int N[3], int* clipped, int num_sms, cudaStream_t st);
 cudaError_t launch_dfix_convert(double* p, long long n, double inv, int num_sms, cudaStream_t st);
 cudaError_t launch_exx_reduce(const PairRec* pairs, const int* n_pair, const double* e_pair, double* out,
                               cudaStream_t st, int* bad = nullptr);
@@ -114,6 +116,12 @@ struct exx_ctx {
     };
     bool per_class = false;
     std::vector<RadiusClass> classes;
+    // the classes alternate between the context stream (lane 0) and aux
+    // (lane 1), forked and joined inside the graph, so that one class's tail
+    // overlaps the next class's work; each lane has its own workspace slots
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int lane_slots[2] = {0, 0};
     int* d_class = nullptr;  // [2 n_geo] start and length of each class in the order, [n_geo] work counters
     double* d_pow = nullptr;
     unsigned long long* d_phase = nullptr;  // [4] phase cycles of the cluster solver
@@ -169,6 +177,13 @@ struct exx_ctx {
     int inject_left = 0;
     int inject_now = 0;
     int g_inject = -1;  // injection state the cached graph was captured with
+
+    // the current call's orbital storage: full grids (cur_box NULL) or
+    // compact boxes (exx_compute_boxes)
+    const int* cur_box = nullptr;
+    int cur_bdim[3] = {0, 0, 0};
+    long long cur_ostride = 0;
+    int g_bdim[3] = {0, 0, 0};  // box dimensions the cached graph was captured with
 
     // graph cache
     cudaGraphExec_t gexec = nullptr;
@@ -376,6 +391,9 @@ extern "C" void exx_destroy(exx_ctx* c) {
         if (e) cudaEventDestroy(e);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->aux) cudaStreamDestroy(c->aux);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->work) cudaStreamDestroy(c->work);
@@ -806,13 +824,16 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         want = 0;
         for (const auto& K : c->cands) want = std::max<long long>(want, K.n_clusters);
     } else if (c->per_class) {
-        // the classes run one after another and share the slots
+        // the classes of a lane run one after another and share its slots
         e = pair_kernel_occupancy(c->threads, true, c->smem, &bps);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
-        want = 0;
-        for (const auto& RC : c->classes)
-            want = std::max<long long>(want, RC.kind == 2 ? RC.cand.n_clusters
-                                                         : (long long)c->num_sms * std::max(1, std::min(bps, 2)));
+        for (int g = 0; g < c->n_geo; ++g) {
+            const exx_ctx::RadiusClass& RC = c->classes[g];
+            const int lane = (c->n_geo - 1 - g) & 1;
+            const int need = RC.kind == 2 ? RC.cand.n_clusters : c->num_sms * std::max(1, std::min(bps, 2));
+            c->lane_slots[lane] = std::max(c->lane_slots[lane], need);
+        }
+        want = (long long)c->lane_slots[0] + c->lane_slots[1];
     } else {
         e = pair_kernel_occupancy(c->threads, o.precision == 1, c->smem, &bps);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
@@ -824,6 +845,10 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     cudaMemGetInfo(&free_b, &total_b);
     long long fit = (long long)(0.25 * (double)free_b / (double)c->slot_bytes);
     c->n_slots = (int)std::max(1LL, std::min(want, fit));
+    if (c->per_class && c->n_slots < want) {  // not enough memory for two lanes: one lane, shared slots
+        c->lane_slots[0] = c->n_slots;
+        c->lane_slots[1] = 0;
+    }
     if (c->use_cluster) apply_cand(c, c->cand);
     e = cudaMalloc(&c->ws, c->slot_bytes * (size_t)c->n_slots);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(workspace)"));
@@ -849,6 +874,11 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         (e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(cuda_fail(c, e, "stream/event creation"));
+    if (c->per_class && c->lane_slots[1] > 0 &&
+        ((e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+         (e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess ||
+         (e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking)) != cudaSuccess))
+        return bail(cuda_fail(c, e, "stream/event creation (radius classes)"));
 
     // fixed kernel parameters
     for (int a = 0; a < 3; ++a) {
@@ -856,6 +886,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         P.delta[a] = c->delta[a];
     }
     P.ngrid = c->ngrid;
+    P.ostride = c->ngrid;
     P.dV = c->dV;
     const double W[4] = {-49.0 / 18.0, 3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0};  // Eq. d2_1
     double inv2[3];
@@ -944,10 +975,13 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
     P.dbg_b = nullptr;
     P.phase_clk = (c->use_cluster || c->per_class) ? c->d_phase : nullptr;
     P.test_wait = c->inject_now;
+    P.box_org = c->cur_box;
+    for (int a = 0; a < 3; ++a) P.bdim[a] = c->cur_bdim[a];
+    P.ostride = c->cur_ostride;
     CK(cudaEventRecordWithFlags(c->ev[0], st, evf), "cudaEventRecord");
-    CK(launch_zero(d_xx, (long long)n * c->ngrid, c->num_sms, st), "zero D_xx");
+    CK(launch_zero(d_xx, (long long)n * c->cur_ostride, c->num_sms, st), "zero D_xx");
     CK(cudaMemsetAsync(c->d_scalars + 2, 0, sizeof(int), st), "reset counters");
-    CK(cudaMemsetAsync(c->d_scalars + 10, 0, 2 * sizeof(int), st), "reset counters");
+    CK(cudaMemsetAsync(c->d_scalars + 10, 0, 3 * sizeof(int), st), "reset counters");
     CK(cudaMemsetAsync(c->d_phase, 0, sizeof(unsigned long long) * 4, st), "reset phase clocks");
     CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
                         c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st,
@@ -958,29 +992,47 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
         CK(launch_radii_sort(c->d_pairs, c->d_scalars, c->d_hist, c->n_geo, c->d_order, c->num_sms, st,
                              c->per_class ? c->d_class : nullptr),
            "largest-first order");
+    if (c->cur_box)
+        CK(launch_box_clip(c->d_pairs, c->d_scalars, c->cur_box, c->cur_bdim, c->grid, c->d_scalars + 12, c->num_sms,
+                           st),
+           "box check");
     CK(cudaEventRecordWithFlags(c->ev[1], st, evf), "cudaEventRecord");
     if (c->per_class) {
-        // one launch per radius class, the largest radius first; each takes
-        // its run of the sorted order from the device (start, length, counter)
+        // one launch per radius class, the largest radius first, alternating
+        // between the two lanes; each takes its run of the sorted order from
+        // the device (start, length, work counter)
+        const bool two = c->aux != nullptr;
+        if (two) {
+            CK(cudaEventRecord(c->ev_fork, st), "cudaEventRecord(fork)");
+            CK(cudaStreamWaitEvent(c->aux, c->ev_fork, 0), "cudaStreamWaitEvent(fork)");
+        }
         for (int g = c->n_geo - 1; g >= 0; --g) {
             const exx_ctx::RadiusClass& RC = c->classes[g];
+            const int lane = two ? (c->n_geo - 1 - g) & 1 : 0;
+            cudaStream_t ls = lane ? c->aux : st;
+            const int slots = two ? c->lane_slots[lane] : c->n_slots;
             SolveParams Pg = P;
+            Pg.ws = c->ws + (size_t)(lane ? c->lane_slots[0] : 0) * c->slot_bytes;
             Pg.item_base = c->d_class + 2 * g;
             Pg.n_pair = c->d_class + 2 * g + 1;
             Pg.queue = c->d_class + 2 * c->n_geo + g;
             if (RC.kind == 2)
-                CK(launch_cluster_kernel(RC.cand.variant, Pg, RC.cand.L, std::min(RC.cand.n_clusters, c->n_slots),
-                                         RC.cand.smem, st),
+                CK(launch_cluster_kernel(RC.cand.variant, Pg, RC.cand.L, std::min(RC.cand.n_clusters, slots),
+                                         RC.cand.smem, ls),
                    "cluster pair kernel (radius class)");
             else
-                CK(launch_pair_kernel(Pg, c->threads, true, c->n_slots, c->smem, st), "pair kernel (radius class)");
+                CK(launch_pair_kernel(Pg, c->threads, true, slots, c->smem, ls), "pair kernel (radius class)");
+        }
+        if (two) {
+            CK(cudaEventRecord(c->ev_join, c->aux), "cudaEventRecord(join)");
+            CK(cudaStreamWaitEvent(st, c->ev_join, 0), "cudaStreamWaitEvent(join)");
         }
     } else if (c->use_cluster)
         CK(launch_cluster_kernel(c->cl_variant, P, c->CL, c->n_clusters, c->smem, st), "cluster pair kernel");
     else
         CK(launch_pair_kernel(P, c->threads, c->opt.precision == 1, c->n_slots, c->smem, st), "pair kernel");
     if (P.dfix != 0.0)
-        CK(launch_dfix_convert(d_xx, (long long)n * c->ngrid, 1.0 / P.dfix, c->num_sms, st), "D_xx to FP64");
+        CK(launch_dfix_convert(d_xx, (long long)n * c->cur_ostride, 1.0 / P.dfix, c->num_sms, st), "D_xx to FP64");
     CK(cudaEventRecordWithFlags(c->ev[2], st, evf), "cudaEventRecord");
     CK(launch_exx_reduce(c->d_pairs, c->d_scalars, c->d_epair, c->d_exx, st, c->d_scalars + 11), "E_xx reduction");
     CK(cudaMemcpyAsync(c->h_exx, c->d_exx, sizeof(double), cudaMemcpyDeviceToHost, st), "copy E_xx");
@@ -1005,15 +1057,22 @@ static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double*
     P.dbg_b = nullptr;
     P.phase_clk = c->d_phase;
     P.test_wait = c->inject_now;
+    P.box_org = c->cur_box;
+    for (int a = 0; a < 3; ++a) P.bdim[a] = c->cur_bdim[a];
+    P.ostride = c->cur_ostride;
     CK(cudaEventRecord(c->ev[0], st), "cudaEventRecord");
-    CK(launch_zero(d_xx, (long long)n * c->ngrid, c->num_sms, st), "zero D_xx");
+    CK(launch_zero(d_xx, (long long)n * c->cur_ostride, c->num_sms, st), "zero D_xx");
     CK(cudaMemsetAsync(c->d_scalars + 2, 0, sizeof(int), st), "reset counters");
-    CK(cudaMemsetAsync(c->d_scalars + 10, 0, 2 * sizeof(int), st), "reset counters");
+    CK(cudaMemsetAsync(c->d_scalars + 10, 0, 3 * sizeof(int), st), "reset counters");
     CK(cudaMemsetAsync(c->d_phase, 0, sizeof(unsigned long long) * 4, st), "reset phase clocks");
     CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
                         c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st, nullptr, c->ln_inv_eps,
                         c->delta_max, c->r_min, 0, 0, c->d_scalars + 11),
        "pair list");
+    if (c->cur_box)
+        CK(launch_box_clip(c->d_pairs, c->d_scalars, c->cur_box, c->cur_bdim, c->grid, c->d_scalars + 12, c->num_sms,
+                           st),
+           "box check");
     int np = 0;
     CK(cudaMemcpyAsync(&np, c->d_scalars, sizeof(int), cudaMemcpyDeviceToHost, st), "read n_pair");
     CK(cudaStreamSynchronize(st), "warm start synchronize");
@@ -1088,7 +1147,8 @@ static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double*
         for (int k0 = 0; k0 < np; k0 += net.Bmax) {
             const int nk = std::min(net.Bmax, np - k0);
             CK(exx::unet::sample_prep(orbitals, c->grid, c->d_pairs, k0, nk, net.S, c->geo_host, c->d_gin,
-                                      c->d_gscale, nullptr, nullptr, d2, c->delta, c->dV, c->lmax, st),
+                                      c->d_gscale, nullptr, nullptr, d2, c->delta, c->dV, c->lmax, c->cur_box,
+                                      c->cur_bdim, c->cur_ostride, st),
                "guess input");
             CK(exx::unet::forward(net, c->d_gin, nk, st), "guess network");
             CK(exx::unet::guess_scatter(net.out, c->d_gscale, k0, nk, net.S, c->geo_host, d2, c->d_guess, st),
@@ -1101,7 +1161,7 @@ static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double*
     CK(cudaEventRecord(c->ev[1], st), "cudaEventRecord");
     CK(launch_cluster_kernel(c->cl_variant, P, c->CL, c->n_clusters, c->smem, st), "cluster pair kernel");
     if (P.dfix != 0.0)
-        CK(launch_dfix_convert(d_xx, (long long)n * c->ngrid, 1.0 / P.dfix, c->num_sms, st), "D_xx to FP64");
+        CK(launch_dfix_convert(d_xx, (long long)n * c->cur_ostride, 1.0 / P.dfix, c->num_sms, st), "D_xx to FP64");
     CK(cudaEventRecord(c->ev[2], st), "cudaEventRecord");
     CK(launch_exx_reduce(c->d_pairs, c->d_scalars, c->d_epair, c->d_exx, st, c->d_scalars + 11), "E_xx reduction");
     CK(cudaMemcpyAsync(c->h_exx, c->d_exx, sizeof(double), cudaMemcpyDeviceToHost, st), "copy E_xx");
@@ -1205,6 +1265,9 @@ static exx_status autotune(exx_ctx* c, const double* orbitals, const double* cen
     SolveParams P = c->P;
     P.phi = orbitals;
     P.dxx = nullptr;
+    P.box_org = c->cur_box;
+    for (int a = 0; a < 3; ++a) P.bdim[a] = c->cur_bdim[a];
+    P.ostride = c->cur_ostride;
     P.pairs = c->d_pairs;
     P.order = nullptr;
     P.e_pair = c->d_epair;
@@ -1246,8 +1309,10 @@ static exx_status autotune(exx_ctx* c, const double* orbitals, const double* cen
     return EXX_OK;
 }
 
-extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const double* centers, int n,
-                                  const double* alphas, double* e_xx, double* d_xx, void* stream) {
+// exx_compute and exx_compute_boxes: box = NULL for full grids, else the
+// boxes' corners (device, [n][3]) and their dimensions (host, 3 ints).
+static exx_status compute_impl(exx_ctx* c, const double* orbitals, const double* centers, int n, const double* alphas,
+                               double* e_xx, double* d_xx, void* stream, const int* box, const int* bdim) {
     if (!c) return fail(nullptr, EXX_EINVAL, "exx_compute: ctx is NULL");
     if (!orbitals || !centers || !e_xx || !d_xx) return fail(c, EXX_EINVAL, "exx_compute: NULL array argument");
     if (n < 1 || n > 65535) return fail(c, EXX_EINVAL, "exx_compute: n must be in [1, 65535]");
@@ -1258,6 +1323,9 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
           reinterpret_cast<uintptr_t>(d_xx) | reinterpret_cast<uintptr_t>(alphas)) & 7u) != 0)
         return fail(c, EXX_EINVAL, "exx_compute: arrays must be 8-byte aligned");
     cudaStream_t user = (cudaStream_t)stream;
+    c->cur_box = box;
+    for (int a = 0; a < 3; ++a) c->cur_bdim[a] = box ? bdim[a] : 0;
+    c->cur_ostride = box ? (long long)bdim[0] * bdim[1] * bdim[2] : c->ngrid;
     exx_status s = ensure_pairs(c, n);
     if (s != EXX_OK) return s;
     // all work runs on the context's stream, ordered after the caller's stream
@@ -1277,8 +1345,9 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
         s = compute_warm(c, orbitals, centers, alphas, n, d_xx, st);
         if (s != EXX_OK) return s;
     } else if (c->opt.batched) {
-        const void* key[5] = {orbitals, centers, d_xx, alphas, nullptr};
-        bool hit = c->gexec && c->g_n == n && std::equal(key, key + 5, c->g_key) && c->g_inject == c->inject_now;
+        const void* key[5] = {orbitals, centers, d_xx, alphas, box};
+        bool hit = c->gexec && c->g_n == n && std::equal(key, key + 5, c->g_key) && c->g_inject == c->inject_now &&
+                   std::equal(c->cur_bdim, c->cur_bdim + 3, c->g_bdim);
         if (!hit) {
             drop_graph(c);
             cudaGraph_t g;
@@ -1300,6 +1369,7 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
             std::copy(key, key + 5, c->g_key);
             c->g_n = n;
             c->g_inject = c->inject_now;
+            std::copy(c->cur_bdim, c->cur_bdim + 3, c->g_bdim);
         }
         e = cudaGraphLaunch(c->gexec, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
@@ -1318,13 +1388,14 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
     c->stats.solve_ms = cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess ? ms : -1.0;
     c->stats.total_ms = cudaEventElapsedTime(&ms, c->ev[0], c->ev[3]) == cudaSuccess ? ms : -1.0;
     (void)cudaGetLastError();  // a failed timing query must not leak into later status checks
-    int sc[12];
+    int sc[13];
     CK(cudaMemcpy(sc, c->d_scalars, sizeof(sc), cudaMemcpyDeviceToHost), "read counters");
     const int npair = sc[0], nonconv = sc[2];
     c->stats.n_pair = npair;
     c->stats.n_nonconv = nonconv;
     c->stats.n_timeouts = sc[10];
     c->stats.n_nonfinite = sc[11];
+    c->stats.n_clipped = box ? sc[12] : 0;
     c->stats.iters_max = -1;  // filled lazily by exx_get_stats
     if (sc[10] > 0) {
         char buf[160];
@@ -1338,6 +1409,24 @@ extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const doub
         return fail(c, EXX_ENOCONV, buf);
     }
     return EXX_OK;
+}
+
+extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const double* centers, int n,
+                                  const double* alphas, double* e_xx, double* d_xx, void* stream) {
+    return compute_impl(c, orbitals, centers, n, alphas, e_xx, d_xx, stream, nullptr, nullptr);
+}
+
+extern "C" exx_status exx_compute_boxes(exx_ctx* c, const double* boxes, const int* origin, const int box_dim[3],
+                                        const double* centers, int n, const double* alphas, double* e_xx,
+                                        double* d_boxes, void* stream) {
+    if (!c) return fail(nullptr, EXX_EINVAL, "exx_compute_boxes: ctx is NULL");
+    if (!origin || !box_dim) return fail(c, EXX_EINVAL, "exx_compute_boxes: NULL origin or box_dim");
+    if ((reinterpret_cast<uintptr_t>(origin) & 3u) != 0)
+        return fail(c, EXX_EINVAL, "exx_compute_boxes: origin must be 4-byte aligned");
+    for (int a = 0; a < 3; ++a)
+        if (box_dim[a] < 2 * c->r_me + 1 || box_dim[a] > c->grid[a])
+            return fail(c, EXX_EINVAL, "exx_compute_boxes: box_dim must be in [2 r_me + 1, N] on every axis");
+    return compute_impl(c, boxes, centers, n, alphas, e_xx, d_boxes, stream, origin, box_dim);
 }
 
 extern "C" exx_status exx_compute_host(exx_ctx* c, const double* orbitals_host, const double* centers_host, int n,
@@ -1488,8 +1577,11 @@ extern "C" exx_status exx_debug_pair(exx_ctx* c, const double* orbitals, int ind
     CK(cudaMemcpy(d_one, &pr, sizeof(PairRec), cudaMemcpyHostToDevice), "copy pair");
     CK(cudaMemcpy(d_sc, sc, sizeof(sc), cudaMemcpyHostToDevice), "copy scalars");
     SolveParams P = c->P;
-    P.phi = orbitals;
+    P.phi = orbitals;  // stored as in the last call (full grids or compact boxes)
     P.dxx = nullptr;
+    P.box_org = c->cur_box;
+    for (int a = 0; a < 3; ++a) P.bdim[a] = c->cur_bdim[a];
+    P.ostride = c->cur_ostride ? c->cur_ostride : c->ngrid;
     P.pairs = d_one;
     P.n_pair = d_sc;
     P.queue = d_sc + 1;
@@ -1568,7 +1660,9 @@ extern "C" exx_status exx_radius_classes(const exx_ctx* c, int* r_pe, int* clust
         const exx_ctx::RadiusClass& RC = c->classes[k];
         if (r_pe) r_pe[k] = c->balls[RC.geo].r_pe;
         if (cluster_size) cluster_size[k] = RC.kind == 2 ? RC.cand.C : 0;
-        if (resident) resident[k] = RC.kind == 2 ? std::min(RC.cand.n_clusters, c->n_slots) : c->n_slots;
+        const int lane = c->aux ? (c->n_geo - 1 - RC.geo) & 1 : 0;
+        const int slots = c->aux ? c->lane_slots[lane] : c->n_slots;
+        if (resident) resident[k] = RC.kind == 2 ? std::min(RC.cand.n_clusters, slots) : slots;
     }
     return EXX_OK;
 }
@@ -1644,7 +1738,8 @@ extern "C" exx_status exx_export_samples(exx_ctx* c, const double* orbitals, int
     CK(cudaMalloc(&d_scale, sizeof(float) * (size_t)nk), "exx_export_samples");
     const double d2 = std::cbrt(c->delta[0] * c->delta[0] * c->delta[1] * c->delta[1] * c->delta[2] * c->delta[2]);
     cudaError_t e = exx::unet::sample_prep(orbitals, c->grid, c->d_prev_pairs, 0, nk, S, c->geo_host, input, d_scale,
-                                           target, c->d_vcache[c->parity ^ 1], d2, c->delta, c->dV, c->lmax, st);
+                                           target, c->d_vcache[c->parity ^ 1], d2, c->delta, c->dV, c->lmax,
+                                           c->cur_box, c->cur_bdim, c->cur_ostride, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d_scale);
     if (e != cudaSuccess) return cuda_fail(c, e, "exx_export_samples");

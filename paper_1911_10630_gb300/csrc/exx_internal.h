@@ -65,6 +65,12 @@ struct SolveParams {
     const double* phi;
     double* dxx;
     long long ngrid;    // N0 N1 N2
+    // compact orbital boxes (exx_compute_boxes): orbital i holds the grid
+    // points (box_org[i] + b) mod N, b in [0, bdim), in C order; the points
+    // outside count as zero for it. NULL = full grids.
+    const int* box_org;
+    int bdim[3];
+    long long ostride;  // values per orbital in phi and dxx: ngrid, or the box volume
     int N[3];
     double delta[3];
     double dV;

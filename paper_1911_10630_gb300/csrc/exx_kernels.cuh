@@ -73,4 +73,19 @@ __device__ __forceinline__ long long grid_index(const int* N, const int* g, int 
     return ((long long)x * N[1] + y) * N[2] + z;
 }
 
+// Where orbital orb keeps grid point g + o (o packed as in pt_off): the
+// full-grid index, or with compact boxes its index in the orbital's box, or
+// -1 when the point lies outside the box (the orbital is zero there).
+__device__ __forceinline__ long long orb_index(const int* N, const int* g, int packed, const int* box_org,
+                                              const int* bdim, int orb) {
+    const int x = wrap(g[0] + off_x(packed), N[0]);
+    const int y = wrap(g[1] + off_y(packed), N[1]);
+    const int z = wrap(g[2] + off_z(packed), N[2]);
+    if (!box_org) return ((long long)x * N[1] + y) * N[2] + z;
+    const int bx = wrap(x - box_org[3 * orb], N[0]), by = wrap(y - box_org[3 * orb + 1], N[1]),
+              bz = wrap(z - box_org[3 * orb + 2], N[2]);
+    if (bx >= bdim[0] || by >= bdim[1] || bz >= bdim[2]) return -1;
+    return ((long long)bx * bdim[1] + by) * bdim[2] + bz;
+}
+
 }  // namespace exx

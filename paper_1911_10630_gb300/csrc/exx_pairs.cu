@@ -229,6 +229,31 @@ __global__ void radii_classes_kernel(const int* __restrict__ hist, int n_geo, in
     }
 }
 
+// Compact boxes: counts the pairs whose ME ball (the bounding cube of side
+// 2 R_ME + 1 around g_ij) is not inside both orbitals' boxes; for those the
+// result differs from the full-grid one (the orbitals count as zero outside).
+__global__ void box_clip_kernel(const PairRec* __restrict__ pairs, const int* __restrict__ n_pair,
+                                const int* __restrict__ box_org, int3 bdim, int3 N, int* __restrict__ clipped) {
+    const int np = *n_pair;
+    int c = 0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+        const PairRec r = pairs[p];
+        const int g[3] = {r.g[0], r.g[1], r.g[2]}, n[3] = {N.x, N.y, N.z}, b[3] = {bdim.x, bdim.y, bdim.z};
+        bool in = true;
+        for (int t = 0; t < 2; ++t) {
+            const int o = t ? r.j : r.i;
+            for (int a = 0; a < 3; ++a) {
+                int s = (g[a] - r.r_me - box_org[3 * o + a]) % n[a];
+                s += s < 0 ? n[a] : 0;
+                in = in && s + 2 * r.r_me < b[a];
+            }
+        }
+        c += in ? 0 : 1;
+    }
+    c = warp_sum_int(c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(clipped, c);
+}
+
 // D_xx = 0 (grid-stride fill; 16-byte stores when the pointer allows them).
 __global__ void zero_kernel(double* __restrict__ p, long long n, int vec) {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -339,6 +364,13 @@ cudaError_t launch_radii_sort(const PairRec* pairs, const int* n_pair, int* hist
     radii_scan_kernel<<<1, 32, 0, st>>>(hist, n_geo);
     radii_scatter_kernel<<<num_sms * 2, 256, 0, st>>>(pairs, n_pair, hist, n_geo, order);
     if (classes) radii_classes_kernel<<<1, 64, 0, st>>>(hist, n_geo, classes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_box_clip(const PairRec* pairs, const int* n_pair, const int* box_org, const int bdim[3],
+                            const int N[3], int* clipped, int num_sms, cudaStream_t st) {
+    box_clip_kernel<<<num_sms, 256, 0, st>>>(pairs, n_pair, box_org, make_int3(bdim[0], bdim[1], bdim[2]),
+                                             make_int3(N[0], N[1], N[2]), clipped);
     return cudaGetLastError();
 }
 

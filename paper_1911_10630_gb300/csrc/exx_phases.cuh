@@ -37,16 +37,26 @@ __device__ __forceinline__ void fill_power_tables(const SolveParams& P, double* 
 // and stores through generic pointers would otherwise force their reload.
 static __device__ __noinline__ void gather_rho(const SolveParams& P, const BallGeo& G, const PairRec& pr,
                                                double* __restrict__ rho, double* __restrict__ vc, int tid, int nthr) {
-    const double* __restrict__ phi_i = P.phi + (long long)pr.i * P.ngrid;
-    const double* __restrict__ phi_j = P.phi + (long long)pr.j * P.ngrid;
+    const double* __restrict__ phi_i = P.phi + (long long)pr.i * P.ostride;
+    const double* __restrict__ phi_j = P.phi + (long long)pr.j * P.ostride;
     const int N[3] = {P.N[0], P.N[1], P.N[2]};
     const int g[3] = {pr.g[0], pr.g[1], pr.g[2]};
     const int n_pe = G.n_pe;
     const int* __restrict__ off = G.pt_off;
     const int* __restrict__ cube = G.pt_cube;
+    if (!P.box_org) {
+        for (int k = tid; k < n_pe; k += nthr) {
+            const long long gi = grid_index(N, g, off[k]);
+            rho[k] = phi_i[gi] * phi_j[gi];
+            vc[cube[k]] = 0.0;
+        }
+        return;
+    }
+    const int bd[3] = {P.bdim[0], P.bdim[1], P.bdim[2]};
     for (int k = tid; k < n_pe; k += nthr) {
-        const long long gi = grid_index(N, g, off[k]);
-        rho[k] = phi_i[gi] * phi_j[gi];
+        const long long ii = orb_index(N, g, off[k], P.box_org, bd, pr.i);
+        const long long ij = orb_index(N, g, off[k], P.box_org, bd, pr.j);
+        rho[k] = (ii >= 0 && ij >= 0) ? phi_i[ii] * phi_j[ij] : 0.0;
         vc[cube[k]] = 0.0;
     }
 }
@@ -279,7 +289,7 @@ static __device__ __noinline__ double shell_points(const SolveParams& P, const B
 static __device__ __noinline__ void scatter_dxx(const SolveParams& P, const BallGeo& G, const PairRec& pr,
                                                 const double* __restrict__ vc, int tid, int nthr) {
     if (!P.dxx) return;
-    const long long ng = P.ngrid;
+    const long long ng = P.ostride;
     const double* __restrict__ phi_i = P.phi + (long long)pr.i * ng;
     const double* __restrict__ phi_j = P.phi + (long long)pr.j * ng;
     double* Di = P.dxx + (long long)pr.i * ng;
@@ -291,18 +301,27 @@ static __device__ __noinline__ void scatter_dxx(const SolveParams& P, const Ball
     const int* __restrict__ off = G.pt_off;
     const int* __restrict__ cube = G.pt_cube;
     const double dfix = P.dfix;
+    const int bd[3] = {P.bdim[0], P.bdim[1], P.bdim[2]};
     for (int q = tid; q < n_me; q += nthr) {
-        const long long gi = grid_index(N, g, off[q]);
+        long long ii, ij;
+        if (!P.box_org) {
+            ii = ij = grid_index(N, g, off[q]);
+        } else {  // a point outside a box: that orbital is zero there, and its D is not kept there
+            ii = orb_index(N, g, off[q], P.box_org, bd, pr.i);
+            ij = orb_index(N, g, off[q], P.box_org, bd, pr.j);
+        }
         const double v = vc[cube[q]];
+        const double pj = ij >= 0 ? phi_j[ij] : 0.0, pi = ii >= 0 ? phi_i[ii] : 0.0;
         if (dfix != 0.0) {  // integer adds: the sum is the same in any order
-            atomicAdd(reinterpret_cast<unsigned long long*>(Di + gi),
-                      (unsigned long long)__double2ll_rn(v * phi_j[gi] * dfix));
-            if (two)
-                atomicAdd(reinterpret_cast<unsigned long long*>(Dj + gi),
-                          (unsigned long long)__double2ll_rn(v * phi_i[gi] * dfix));
+            if (ii >= 0)
+                atomicAdd(reinterpret_cast<unsigned long long*>(Di + ii),
+                          (unsigned long long)__double2ll_rn(v * pj * dfix));
+            if (two && ij >= 0)
+                atomicAdd(reinterpret_cast<unsigned long long*>(Dj + ij),
+                          (unsigned long long)__double2ll_rn(v * pi * dfix));
         } else {
-            atomicAdd(Di + gi, v * phi_j[gi]);
-            if (two) atomicAdd(Dj + gi, v * phi_i[gi]);
+            if (ii >= 0) atomicAdd(Di + ii, v * pj);
+            if (two && ij >= 0) atomicAdd(Dj + ij, v * pi);
         }
     }
 }

@@ -79,7 +79,7 @@ __device__ int cg_ball(T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d,
 // The persistent pair kernel.
 // --------------------------------------------------------------------------
 template <int NT, bool MIXED>
-__global__ void __launch_bounds__(NT, 1) pair_kernel(const __grid_constant__ SolveParams P) {
+__global__ void __launch_bounds__(NT, MIXED ? 1 : 2) pair_kernel(const __grid_constant__ SolveParams P) {
     extern __shared__ double smem[];
     __shared__ double red[2][33];
     __shared__ float red32[2][33];
@@ -235,11 +235,12 @@ __global__ void __launch_bounds__(NT, 1) pair_kernel(const __grid_constant__ Sol
 __global__ void debug_pair_readback(const SolveParams P, PairRec pr, double* rho_me, double* v_me) {
     const BallGeo G = P.geos[pr.geo];
     const double* vc = reinterpret_cast<const double*>(P.ws + P.off_vcube);
-    const double* phi_i = P.phi + (long long)pr.i * P.ngrid;
-    const double* phi_j = P.phi + (long long)pr.j * P.ngrid;
+    const double* phi_i = P.phi + (long long)pr.i * P.ostride;
+    const double* phi_j = P.phi + (long long)pr.j * P.ostride;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < G.n_me; q += gridDim.x * blockDim.x) {
-        const long long g = grid_index(P.N, pr.g, G.pt_off[q]);
-        rho_me[q] = phi_i[g] * phi_j[g];
+        const long long ii = orb_index(P.N, pr.g, G.pt_off[q], P.box_org, P.bdim, pr.i);
+        const long long ij = orb_index(P.N, pr.g, G.pt_off[q], P.box_org, P.bdim, pr.j);
+        rho_me[q] = (ii >= 0 && ij >= 0) ? phi_i[ii] * phi_j[ij] : 0.0;
         v_me[q] = vc[G.pt_cube[q]];
     }
 }

@@ -878,10 +878,6 @@ namespace unet {
 
 namespace {
 
-__device__ __forceinline__ int wrapi(int a, int n) {
-    a %= n;
-    return a < 0 ? a + n : a;
-}
 
 // Index of the Cartesian monomial x^a y^b z^c, l = a + b + c, in the
 // library's order (degree ascending, then a descending, then b descending).
@@ -902,24 +898,31 @@ __global__ void __launch_bounds__(256) sample_prep_kernel(const double* __restri
                                                           const BallGeo G, float* __restrict__ input,
                                                           float* __restrict__ scale, float* __restrict__ target,
                                                           const float* __restrict__ vcache, double d2, float dx,
-                                                          float dy, float dz, float dV, int lmax) {
+                                                          float dy, float dz, float dV, int lmax,
+                                                          const int* __restrict__ box_org, int3 bdim,
+                                                          long long ostride) {
     constexpr int NM = kNMono;
     __shared__ double red[8];
     __shared__ float s_Mw[8][NM];
     __shared__ float s_M[NM], s_T[NM];
     const int k = k0 + blockIdx.x;
     const PairRec pr = pairs[k];
-    const long long ng = (long long)N0 * N1 * N2;
-    const double* pi = phi + (long long)pr.i * ng;
-    const double* pj = phi + (long long)pr.j * ng;
+    const double* pi = phi + (long long)pr.i * ostride;
+    const double* pj = phi + (long long)pr.j * ostride;
+    const int N[3] = {N0, N1, N2}, bd[3] = {bdim.x, bdim.y, bdim.z};
+    // rho at offset o of the pair's grid point (zero where o leaves a box)
+    auto rho_at = [&](int ox, int oy, int oz) -> double {
+        const int packed = (ox + 128) | ((oy + 128) << 8) | ((oz + 128) << 16);
+        const long long ii = orb_index(N, pr.g, packed, box_org, bd, pr.i);
+        const long long ij = orb_index(N, pr.g, packed, box_org, bd, pr.j);
+        return (ii >= 0 && ij >= 0) ? pi[ii] * pj[ij] : 0.0;
+    };
     const int R = G.r_pe, h = S / 2, S3 = S * S * S;
     double mx = 0.0;
     for (int v = threadIdx.x; v < S3; v += blockDim.x) {
         const int ox = v / (S * S) - h, oy = (v / S) % S - h, oz = v % S - h;
         if (ox * ox + oy * oy + oz * oz > R * R) continue;
-        const long long g = ((long long)wrapi(pr.g[0] + ox, N0) * N1 + wrapi(pr.g[1] + oy, N1)) * N2 +
-                            wrapi(pr.g[2] + oz, N2);
-        mx = fmax(mx, fabs(pi[g] * pj[g]));
+        mx = fmax(mx, fabs(rho_at(ox, oy, oz)));
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
@@ -936,9 +939,7 @@ __global__ void __launch_bounds__(256) sample_prep_kernel(const double* __restri
         const int ox = v / (S * S) - h, oy = (v / S) % S - h, oz = v % S - h;
         float r = 0.0f, m = 0.0f, t = 0.0f;
         if (ox * ox + oy * oy + oz * oz <= R * R) {
-            const long long g = ((long long)wrapi(pr.g[0] + ox, N0) * N1 + wrapi(pr.g[1] + oy, N1)) * N2 +
-                                wrapi(pr.g[2] + oz, N2);
-            r = (float)(pi[g] * pj[g] * inv);
+            r = (float)(rho_at(ox, oy, oz) * inv);
             m = 1.0f;
             if (tg && vc) {
                 const RowRec Rw = G.rows_pe[G.row_of[(ox + R) * W + (oy + R)]];
@@ -1089,10 +1090,12 @@ __global__ void __launch_bounds__(256) guess_scatter_kernel(const float* __restr
 
 cudaError_t sample_prep(const double* phi, const int N[3], const PairRec* pairs, int k0, int nk, int S,
                         const BallGeo& G, float* input, float* scale, float* target, const float* vcache, double d2,
-                        const double delta[3], double dV, int lmax, cudaStream_t st) {
+                        const double delta[3], double dV, int lmax, const int* box_org, const int bdim[3],
+                        long long ostride, cudaStream_t st) {
     if (nk <= 0) return cudaSuccess;
     sample_prep_kernel<<<nk, 256, 0, st>>>(phi, N[0], N[1], N[2], pairs, k0, S, G, input, scale, target, vcache, d2,
-                                           (float)delta[0], (float)delta[1], (float)delta[2], (float)dV, lmax);
+                                           (float)delta[0], (float)delta[1], (float)delta[2], (float)dV, lmax,
+                                           box_org, make_int3(bdim[0], bdim[1], bdim[2]), ostride);
     return cudaGetLastError();
 }
 

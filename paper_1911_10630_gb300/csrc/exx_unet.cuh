@@ -81,10 +81,12 @@ cudaError_t pack_weights(const float* w, __nv_bfloat16* wp, int cin, int cout, i
 // outside the ball (Eqs. mepole, me; l <= lmax), channel 2 = ball mask, s =
 // max |rho| on the ball (scale[k - k0]). With vcache (the pairs' PE-ball
 // potentials, FP32, list order), target receives v / (s d2) on the ball and 0
-// elsewhere. input [nk][S^3][kIn], target [nk][S^3].
+// elsewhere. input [nk][S^3][kIn], target [nk][S^3]. phi holds ostride values
+// per orbital: full grids (box_org NULL) or compact boxes (as SolveParams).
 cudaError_t sample_prep(const double* phi, const int N[3], const PairRec* pairs, int k0, int nk, int S,
                         const BallGeo& G, float* input, float* scale, float* target, const float* vcache, double d2,
-                        const double delta[3], double dV, int lmax, cudaStream_t st);
+                        const double delta[3], double dV, int lmax, const int* box_org, const int bdim[3],
+                        long long ostride, cudaStream_t st);
 // The multipole constants of the boundary channel (this unit's copy).
 cudaError_t set_multipole_const_unet(const MultipoleConst& mc);
 // vguess[k][p] = out[k - k0][cube(o_p)] * scale[k - k0] * d2 on the PE points

@@ -47,7 +47,8 @@ class exx_stats(ctypes.Structure):
                 ("solver_kind", ctypes.c_int), ("cluster_size", ctypes.c_int), ("grid_ctas", ctypes.c_int),
                 ("threads", ctypes.c_int), ("phase_ms", ctypes.c_double * 4), ("lane_map", ctypes.c_int),
                 ("n_candidates", ctypes.c_int), ("tune_ms", ctypes.c_double),
-                ("guess_ms", ctypes.c_double), ("n_timeouts", ctypes.c_int), ("n_nonfinite", ctypes.c_int)]
+                ("guess_ms", ctypes.c_double), ("n_timeouts", ctypes.c_int), ("n_nonfinite", ctypes.c_int),
+                ("n_clipped", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,6 +72,7 @@ SIGNATURES = [
                                 ctypes.c_int, ctypes.c_double, ctypes.POINTER(exx_options)]),
     ("exx_compute", ctypes.c_int, [_ctx_p, _vp, _vp, ctypes.c_int, _vp, _d, _vp, _vp]),
     ("exx_compute_host", ctypes.c_int, [_ctx_p, _vp, _vp, ctypes.c_int, _vp, _d, _vp, _vp]),
+    ("exx_compute_boxes", ctypes.c_int, [_ctx_p, _vp, _vp, _i, _vp, ctypes.c_int, _vp, _d, _vp, _vp]),
     ("exx_get_stats", ctypes.c_int, [_ctx_p, ctypes.POINTER(exx_stats)]),
     ("exx_get_pairs", ctypes.c_int, [_ctx_p, _i, _i, _i, _i, _d, _i, ctypes.c_int, _i]),
     ("exx_debug_pair", ctypes.c_int, [_ctx_p, _vp, ctypes.c_int, _d, _d, _d, _vp]),
@@ -204,6 +206,18 @@ class Exx:
                                 ctypes.byref(e), _ptr(d_xx), _stream_handle(stream))
         self.last_status = st
         if not (st == EXX_OK or (allow_noconv and st == EXX_ENOCONV) or (allow_timeout and st == EXX_ETIMEOUT)):
+            _check(st, self._ctx)
+        return e.value
+
+    def compute_boxes(self, boxes, origin, centers, d_boxes, alphas=None, stream=None, allow_noconv=False) -> float:
+        """exx_compute_boxes on device tensors: boxes [n][B0][B1][B2], origin [n][3] int32; returns E_xx."""
+        e = ctypes.c_double()
+        bd = np.ascontiguousarray(boxes.shape[1:], np.int32)
+        st = load().exx_compute_boxes(self._ctx, _ptr(boxes), _ptr(origin), bd.ctypes.data_as(_i), _ptr(centers),
+                                      int(centers.shape[0]), _ptr(alphas), ctypes.byref(e), _ptr(d_boxes),
+                                      _stream_handle(stream))
+        self.last_status = st
+        if not (st == EXX_OK or (allow_noconv and st == EXX_ENOCONV)):
             _check(st, self._ctx)
         return e.value
 
