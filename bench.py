@@ -213,6 +213,52 @@ def batched_uneven_leg(dev, stream, steps=3, plain_steps=1):
     return out
 
 
+def learned_leg(w, dphi, dcen, dD, stream, zero_ms, plain_ms, steps=2, train_workloads=4, per_workload=400,
+                epochs=4):
+    """The workload solved from the learned warm start (warm_start = 2): the
+    R_PE 24 network (cube 48) trained on the GPU by the library's own kernels
+    on solver samples of other seeds of the same form (train_workloads x
+    per_workload pairs), then the batched mixed-precision solve from its guess.
+    Reports pair solves/s with the network's time included, CG iterations per
+    pair against the zero start, and the ratios to the zero start and to the
+    plain FP64 CG of the main line."""
+    import time as _t
+    import torch
+    from paper_1911_10630_gb300 import guess_train, synth
+    from paper_1911_10630_gb300.exx import Exx, guess_model_blob
+    t0 = _t.time()
+    inp, tgt = guess_train.solve_and_export(range(3000, 3000 + train_workloads), S=guess_train.CUBE_R24,
+                                            torch=torch, workload=synth.config1, per_workload=per_workload)
+    net, hist = guess_train.train(inp, tgt, S=guess_train.CUBE_R24, epochs=epochs, batch=32, lr=1e-3)
+    blob = guess_model_blob(guess_train.CUBE_R24, net.get_params())
+    net.close()
+    del inp, tgt
+    torch.cuda.empty_cache()
+    train_s = _t.time() - t0
+    ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=1, warm_start=2)
+    ex.load_guess_model(blob)
+    e = ex.compute(dphi, dcen, dD, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    its, gms = [], []
+    for _ in range(steps):
+        e = ex.compute(dphi, dcen, dD, stream=stream)
+        st = ex.stats()
+        its.append(st["iters_total"] / st["n_pair"])
+        gms.append(st["guess_ms"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    n_pair = st["n_pair"]
+    ex.close()
+    return {"value": n_pair / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "guess_ms_per_step": float(np.mean(gms)),
+            "iters_per_pair": float(np.mean(its)), "E_xx": e, "n_nonconv": st["n_nonconv"],
+            "training": {"samples": train_workloads * per_workload, "epochs": epochs, "seconds": train_s,
+                         "loss_first_last": [hist[0], hist[-1]]},
+            "vs_zero_start": zero_ms / ms, "speedup_vs_plain_fp64_cg": plain_ms / ms if plain_ms else None}
+
+
 def run_oracle_sample(w, phi, pairs_all, seconds=12.0, seed=0):
     """Times the oracle on a bounded random sample of the workload's pairs."""
     import oracle
@@ -289,7 +335,8 @@ def main():
     ap.add_argument("--lane-map", type=int, default=0)
     ap.add_argument("--update-drop", type=float, default=1e-4)
     ap.add_argument("--autotune", type=int, default=1)
-    ap.add_argument("--no-legs", action="store_true", help="skip the batched-uneven (config 2) leg")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the batched-uneven (config 2) and learned-guess legs")
     ap.add_argument("--orbitals", type=int, default=0,
                     help="keep only the first N orbitals of the workload (small cases for profiling)")
     args = ap.parse_args()
@@ -433,6 +480,9 @@ def main():
 
     if rank == 0 and ws == 1 and not args.no_legs and not args.orbitals:
         extra["batched_uneven"] = batched_uneven_leg(dev, stream)
+        plain_ms = extra.get("plain_fp64_cg", {}).get("ms_per_step")
+        extra["learned_guess"] = learned_leg(w, dphi, dcen, dD, stream, total_ms / args.steps, plain_ms)
+        extra["learned_guess"]["iters_per_pair_zero_start"] = st["iters_total"] / st["n_pair"]
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -43,6 +43,7 @@ struct ConvArgs {
     __nv_bfloat16* y;
     int B, D, H, W, cin, cout;
     int epi, DT, ncols, nbuf;
+    int fold;  // the three depth taps of a (dh, dw) in one MMA of N = 3 cout (depth-shifted TMEM slices)
     int tiles_d, tiles_h, tiles_w;
     uint32_t itile, wtile, stage;
     int* err;
@@ -75,9 +76,16 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const ConvArgs a) {
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = s_tmem;
+    if (a.fold) {  // every slice accumulates from several MMAs: start from zero
+        for (int c0 = 0; c0 < a.ncols; c0 += 16) tc::tmem_st16_zero(tbase + ((uint32_t)(warp * 32) << 16) + c0);
+        tc::tmem_wait_st();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
 
     const int nch = a.cin / 16;
-    const uint32_t idesc = tc::idesc_bf16_f32(128, a.cout);
+    const uint32_t idesc = tc::idesc_bf16_f32(128, a.fold ? 3 * a.cout : a.cout);
     const int nvox = (DT + 2) * kHH * kWW;
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
@@ -112,14 +120,30 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const ConvArgs a) {
         if (tid == 0) {
             tc::fence_after_sync();
             const uint32_t sa = tc::smem_addr(st), sw = tc::smem_addr(wdst);
-            for (int tt = 0; tt < DT; ++tt) {
+            if (a.fold) {
+                // input slice u (depth d0 - 1 + u) feeds the outputs tt = u - dz,
+                // dz = 2, 1, 0: TMEM slices u .. u + 2 (slice = tt + 2), with the
+                // weights of (dh, dw) packed as three N-blocks in that order
+                for (int u = 0; u < DT + 2; ++u) {
 #pragma unroll 1
-                for (int tap = 0; tap < 27; ++tap) {
-                    const int dd = tap / 9, dh = (tap / 3) % 3, dw = tap % 3;
-                    const uint32_t aoff = (uint32_t)((((tt + dd) * kHH + dh) * kWW + dw) * 16);
-                    const uint64_t ad = tc::sdesc(sa + aoff, a.itile, kWW * 16);
-                    const uint64_t bd = tc::sdesc(sw + (uint32_t)(tap * a.cout * 32), 128, 256);
-                    tc::mma_bf16(tbase + (uint32_t)(tt * a.cout), ad, bd, idesc, (c > 0 || tap > 0) ? 1u : 0u);
+                    for (int hw = 0; hw < 9; ++hw) {
+                        const int dh = hw / 3, dw = hw % 3;
+                        const uint32_t aoff = (uint32_t)(((u * kHH + dh) * kWW + dw) * 16);
+                        const uint64_t ad = tc::sdesc(sa + aoff, a.itile, kWW * 16);
+                        const uint64_t bd = tc::sdesc(sw + (uint32_t)(hw * 3 * a.cout * 32), 128, 256);
+                        tc::mma_bf16(tbase + (uint32_t)(u * a.cout), ad, bd, idesc, 1u);
+                    }
+                }
+            } else {
+                for (int tt = 0; tt < DT; ++tt) {
+#pragma unroll 1
+                    for (int tap = 0; tap < 27; ++tap) {
+                        const int dd = tap / 9, dh = (tap / 3) % 3, dw = tap % 3;
+                        const uint32_t aoff = (uint32_t)((((tt + dd) * kHH + dh) * kWW + dw) * 16);
+                        const uint64_t ad = tc::sdesc(sa + aoff, a.itile, kWW * 16);
+                        const uint64_t bd = tc::sdesc(sw + (uint32_t)(tap * a.cout * 32), 128, 256);
+                        tc::mma_bf16(tbase + (uint32_t)(tt * a.cout), ad, bd, idesc, (c > 0 || tap > 0) ? 1u : 0u);
+                    }
                 }
             }
             tc::commit(&mbar[s]);
@@ -140,7 +164,8 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const ConvArgs a) {
             const size_t vox = (((size_t)b * a.D + d) * a.H + h) * a.W + w;
             for (int c0 = 0; c0 < a.cout; c0 += 16) {
                 float v[16];
-                tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(tt * a.cout + c0), v);
+                tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)((tt + (a.fold ? 2 : 0)) * a.cout + c0),
+                              v);
                 if (!live) continue;
                 if (a.bias) {
 #pragma unroll
@@ -180,9 +205,10 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const ConvArgs a) {
 // Packed operand: [K/16][27][N/8][2][8 n][8 k], k = 16 chunk + 8 half + e.
 // Forward: K = cin, N = cout, value W[tap][k][n]. Data gradient (flip): the
 // convolution maps cout -> cin channels, K = cout, N = cin, value
-// W[26 - tap][n][k].
+// W[26 - tap][n][k]. Depth-folded (fold): the 27 slots of a chunk are taken
+// as [9 (dh, dw)][3], slot 3 hw + b holding the tap of depth offset dz = 2 - b.
 __global__ void pack_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wp, int cin, int cout,
-                            int flip) {
+                            int flip, int fold) {
     const int K = flip ? cout : cin, N = flip ? cin : cout;
     const long long total = 27LL * K * N;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -196,7 +222,8 @@ __global__ void pack_kernel(const float* __restrict__ w, __nv_bfloat16* __restri
         r /= 2;
         const int ng = (int)(r % (N / 8));
         r /= (N / 8);
-        const int tap = (int)(r % 27);
+        const int slot = (int)(r % 27);
+        const int tap = fold ? (2 - slot % 3) * 9 + slot / 3 : slot;
         const int chunk = (int)(r / 27);
         const int k = chunk * 16 + half * 8 + e, n = ng * 8 + nl;
         const float v = flip ? w[((size_t)(26 - tap) * cin + n) * cout + k] : w[((size_t)tap * cin + k) * cout + n];
@@ -564,9 +591,15 @@ size_t param_offset(int layer) {
 }
 size_t param_count() { return param_offset(kLayers); }
 
+// Whether a convolution with n_out output channels folds its depth taps (one
+// MMA of N = 3 n_out per (dh, dw)): N <= 256 and the depth-shifted TMEM slices
+// of a tile within 256 columns (two CTAs per SM).
+static bool conv_folds(int n_out) { return n_out <= 32; }
+
 cudaError_t pack_weights(const float* w, __nv_bfloat16* wp, int cin, int cout, int flip, cudaStream_t st) {
     const long long total = 27LL * cin * cout;
-    pack_kernel<<<(int)((total + 255) / 256), 256, 0, st>>>(w, wp, cin, cout, flip);
+    pack_kernel<<<(int)((total + 255) / 256), 256, 0, st>>>(w, wp, cin, cout, flip,
+                                                            conv_folds(flip ? cin : cout) ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -593,15 +626,19 @@ cudaError_t conv3_tc(const __nv_bfloat16* x, const __nv_bfloat16* wp, const floa
     // leave one CTA per SM whose 128 threads stage too slowly to keep the
     // tensor cores fed (measured slower on GB300); double-buffered chunks when
     // the input has more than one chunk and two stages fit.
-    int DT = 4;
-    while (DT > 1 && DT * cout > 512) --DT;
+    // Folded layers: 8 (16 outputs) or 4 (32 outputs) slices per tile, the
+    // tile's DT + 4 accumulator slices (two of them on each side only collect
+    // halo contributions) in at most 256 TMEM columns.
+    a.fold = conv_folds(cout) ? 1 : 0;
+    int DT = a.fold ? (cout <= 16 ? 8 : 4) : 4;
+    while (!a.fold && DT > 1 && DT * cout > 512) --DT;
     if (DT > D) DT = D;
     const size_t stage_b = (size_t)2 * (DT + 2) * kHH * kWW * 16 + (size_t)27 * cout * 32;
     const int nbuf = (2 * stage_b + 128 <= 200 * 1024 && cin > 16) ? 2 : 1;
     if (DT < 1) return cudaErrorInvalidValue;
     a.DT = DT;
     int nc = 32;
-    while (nc < DT * cout) nc *= 2;
+    while (nc < (DT + (a.fold ? 4 : 0)) * cout) nc *= 2;
     a.ncols = nc;
     a.itile = (uint32_t)(DT + 2) * kHH * kWW * 16;
     a.wtile = 27u * (uint32_t)cout * 32u;

@@ -26,6 +26,13 @@ def _bf16_tensor(torch, a):
     (1, 6, 17, 9, 192, 64, 1),     # widest input (up-path concat)
     (2, 5, 18, 10, 64, 32, 2),     # data gradient, cout -> cin
     (1, 4, 16, 16, 192, 64, 2),    # data gradient with 192 outputs (two TMEM slices of 192)
+    # depth-folded tiles (one MMA of N = 3 x outputs per (dh, dw)): 16 outputs
+    # (8 slices per tile) and 32 outputs (4 slices), ragged depth, 1-3 chunks
+    (2, 10, 20, 12, 16, 32, 1),
+    (1, 9, 16, 8, 48, 16, 0),
+    (1, 3, 5, 4, 32, 16, 1),       # depth shorter than a tile
+    (2, 6, 18, 9, 16, 32, 2),      # data gradient onto 16 channels
+    (1, 5, 17, 9, 32, 48, 2),      # data gradient onto 32 channels
 ])
 def test_conv3_tensor_core_matches_oracle(torch, B, D, H, W, cin, cout, mode):
     from paper_1911_10630_gb300 import exx
