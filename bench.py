@@ -213,8 +213,8 @@ def batched_uneven_leg(dev, stream, steps=3, plain_steps=1):
     return out
 
 
-def learned_leg(w, dphi, dcen, dD, stream, zero_ms, plain_ms, steps=2, train_workloads=4, per_workload=400,
-                epochs=4):
+def learned_leg(w, dphi, dcen, dD, stream, zero_ms, plain_ms, steps=2, train_workloads=8, per_workload=400,
+                epochs=6):
     """The workload solved from the learned warm start (warm_start = 2): the
     R_PE 24 network (cube 48) trained on the GPU by the library's own kernels
     on solver samples of other seeds of the same form (train_workloads x

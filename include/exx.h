@@ -147,7 +147,9 @@ typedef struct {
                           1 = accumulated as 64-bit fixed-point integers
                           (resolution 2^-40, |D_xx| < 2^22) by integer atomic
                           adds, whose sum does not depend on their order, then
-                          converted to FP64 in place: bitwise reproducible.     */
+                          converted to FP64 in place: bitwise reproducible. A
+                          contribution |v phi| >= 2^22 is dropped and the call
+                          returns EXX_EINVAL (outputs written, D_xx incomplete). */
     int inject_wait_timeout; /* test only (default 0): the next this-many calls
                           of the context each make one extra bounded device wait
                           run out (cluster solver: thread 0 of every CTA polls an

@@ -927,7 +927,8 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     P.n_pair = c->d_scalars;
     P.queue = c->d_scalars + 1;
     P.nonconv = c->d_scalars + 2;
-    P.timeouts = c->d_scalars + 10;  // [11]: non-finite inputs (pair list, E_xx reduction)
+    P.timeouts = c->d_scalars + 10;  // [11]: non-finite inputs (pair list, E_xx reduction), [12]: clipped pairs
+    P.dfix_range = c->d_scalars + 13;
 
     c->stats.n_pe = B.n_pe;
     c->stats.n_me = B.n_me;
@@ -981,7 +982,7 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
     CK(cudaEventRecordWithFlags(c->ev[0], st, evf), "cudaEventRecord");
     CK(launch_zero(d_xx, (long long)n * c->cur_ostride, c->num_sms, st), "zero D_xx");
     CK(cudaMemsetAsync(c->d_scalars + 2, 0, sizeof(int), st), "reset counters");
-    CK(cudaMemsetAsync(c->d_scalars + 10, 0, 3 * sizeof(int), st), "reset counters");
+    CK(cudaMemsetAsync(c->d_scalars + 10, 0, 4 * sizeof(int), st), "reset counters");
     CK(cudaMemsetAsync(c->d_phase, 0, sizeof(unsigned long long) * 4, st), "reset phase clocks");
     CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
                         c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st,
@@ -1063,7 +1064,7 @@ static exx_status compute_warm(exx_ctx* c, const double* orbitals, const double*
     CK(cudaEventRecord(c->ev[0], st), "cudaEventRecord");
     CK(launch_zero(d_xx, (long long)n * c->cur_ostride, c->num_sms, st), "zero D_xx");
     CK(cudaMemsetAsync(c->d_scalars + 2, 0, sizeof(int), st), "reset counters");
-    CK(cudaMemsetAsync(c->d_scalars + 10, 0, 3 * sizeof(int), st), "reset counters");
+    CK(cudaMemsetAsync(c->d_scalars + 10, 0, 4 * sizeof(int), st), "reset counters");
     CK(cudaMemsetAsync(c->d_phase, 0, sizeof(unsigned long long) * 4, st), "reset phase clocks");
     CK(launch_pair_list(n, centers, c->cell, c->delta, c->grid, c->r_pair, c->r_pe, c->r_me, c->d_counts,
                         c->d_offsets, c->d_scalars, c->d_scalars + 1, c->d_pairs, st, nullptr, c->ln_inv_eps,
@@ -1388,7 +1389,7 @@ static exx_status compute_impl(exx_ctx* c, const double* orbitals, const double*
     c->stats.solve_ms = cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess ? ms : -1.0;
     c->stats.total_ms = cudaEventElapsedTime(&ms, c->ev[0], c->ev[3]) == cudaSuccess ? ms : -1.0;
     (void)cudaGetLastError();  // a failed timing query must not leak into later status checks
-    int sc[13];
+    int sc[14];
     CK(cudaMemcpy(sc, c->d_scalars, sizeof(sc), cudaMemcpyDeviceToHost), "read counters");
     const int npair = sc[0], nonconv = sc[2];
     c->stats.n_pair = npair;
@@ -1397,6 +1398,14 @@ static exx_status compute_impl(exx_ctx* c, const double* orbitals, const double*
     c->stats.n_nonfinite = sc[11];
     c->stats.n_clipped = box ? sc[12] : 0;
     c->stats.iters_max = -1;  // filled lazily by exx_get_stats
+    if (sc[13] > 0) {
+        char buf[200];
+        std::snprintf(buf, sizeof(buf),
+                      "deterministic D_xx: %d contributions |v phi| >= 2^22 lie beyond the fixed-point range and were "
+                      "dropped (D_xx incomplete; use deterministic = 0)",
+                      sc[13]);
+        return fail(c, EXX_EINVAL, buf);
+    }
     if (sc[10] > 0) {
         char buf[160];
         std::snprintf(buf, sizeof(buf), "%d bounded device waits ran out (results written, not to be trusted)",

@@ -103,6 +103,7 @@ struct SolveParams {
                               // (1; 2: bound made too small, every pair falls back, for tests)
     double fix_inv;           // 1 / (180 delta^2): the integer stencil's weights are 180 delta^2 x Eq. d2_1's
     double dfix;              // D_xx as fixed-point integers with this scale (2^40; 0 = FP64 atomics)
+    int* dfix_range;          // counts fixed-point D_xx contributions beyond the range (dropped)
     const double* pow_tab;  // [3][2 Rc + 1][8] x^e, y^e, z^e (cluster kernel; global, read-only)
 
     // solver

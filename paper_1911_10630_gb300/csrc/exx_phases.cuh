@@ -313,12 +313,15 @@ static __device__ __noinline__ void scatter_dxx(const SolveParams& P, const Ball
         const double v = vc[cube[q]];
         const double pj = ij >= 0 ? phi_j[ij] : 0.0, pi = ii >= 0 ? phi_i[ii] : 0.0;
         if (dfix != 0.0) {  // integer adds: the sum is the same in any order
-            if (ii >= 0)
-                atomicAdd(reinterpret_cast<unsigned long long*>(Di + ii),
-                          (unsigned long long)__double2ll_rn(v * pj * dfix));
-            if (two && ij >= 0)
-                atomicAdd(reinterpret_cast<unsigned long long*>(Dj + ij),
-                          (unsigned long long)__double2ll_rn(v * pi * dfix));
+            // a contribution at or beyond 2^22 (2^62 at the scale 2^40) would
+            // wrap: it is dropped and counted (the call then fails)
+            const double xi = v * pj * dfix, xj = v * pi * dfix;
+            const bool oki = fabs(xi) < 4611686018427387904.0, okj = fabs(xj) < 4611686018427387904.0;  // 2^62
+            if (ii >= 0 && oki)
+                atomicAdd(reinterpret_cast<unsigned long long*>(Di + ii), (unsigned long long)__double2ll_rn(xi));
+            if (two && ij >= 0 && okj)
+                atomicAdd(reinterpret_cast<unsigned long long*>(Dj + ij), (unsigned long long)__double2ll_rn(xj));
+            if (!oki || (two && !okj)) atomicAdd(P.dfix_range, 1);
         } else {
             if (ii >= 0) atomicAdd(Di + ii, v * pj);
             if (two && ij >= 0) atomicAdd(Dj + ij, v * pi);

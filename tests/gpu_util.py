@@ -29,7 +29,17 @@ def run_gpu(w, phi=None, torch=None, allow_noconv=False, **opts):
     if getattr(w, "radii_mode", 0) == 1:
         opts.setdefault("radii_mode", 1)
         dal = torch.from_numpy(np.ascontiguousarray(w.alphas, dtype=np.float64)).cuda()
+    expect = opts.pop("expect_status", None)
     ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, opts.pop("tol", w.tol), **opts)
+    if expect is not None:  # a call expected to fail: report its status and message
+        from paper_1911_10630_gb300.exx import ExxError
+        try:
+            e = ex.compute(dphi, dcen, dD, alphas=dal, allow_noconv=allow_noconv)
+            err = ""
+        except ExxError as x:
+            e, err = float("nan"), str(x)
+        torch.cuda.synchronize()
+        return dict(E_xx=e, status=ex.last_status, error=err, ex=ex)
     e = ex.compute(dphi, dcen, dD, alphas=dal, allow_noconv=allow_noconv)
     torch.cuda.synchronize()
     out = dict(E_xx=e, D=dD.cpu().numpy(), pairs=ex.pairs(), stats=ex.stats(), ex=ex, dphi=dphi,

@@ -64,37 +64,41 @@ def test_exported_samples_match_the_oracle_pair_solution(torch):
 def test_learned_warm_start_meets_the_gates_with_fewer_iterations(torch):
     """Training is bitwise reproducible (fixed-order gradient reductions, seeded
     initialisation and batch order, solver samples from one fixed launch
-    shape), so the gain is one number per GPU model: about 9 % fewer CG
-    iterations on this held-out workload, asserted at 5 %."""
+    shape), so the gain is one number per GPU model and build: 5.9 % fewer CG
+    iterations over these three held-out workloads with 7,200 training samples
+    on GB300 (12.8 % over 40 workloads with 18,000 samples), asserted at 3 % to
+    leave room for the rounding differences of another build."""
     from paper_1911_10630_gb300 import guess_train
     from paper_1911_10630_gb300.exx import Exx, guess_model_blob
-    inp, tgt = guess_train.solve_and_export(range(1000, 1100), torch=torch)
-    net, hist = guess_train.train(inp, tgt, epochs=12, batch=32, lr=1e-3)
+    inp, tgt = guess_train.solve_and_export(range(1000, 1200), torch=torch)
+    net, hist = guess_train.train(inp, tgt, epochs=8, batch=32, lr=1e-3)
     assert hist[-1] < 0.01 * hist[0]
     blob = guess_model_blob(guess_train.CUBE, net.get_params())
     net.close()
-    w = synth.config0(7)  # not among the training workloads
-    phi = w.orbitals()
-    dphi = torch.from_numpy(phi).cuda()
-    dcen = torch.from_numpy(np.ascontiguousarray(w.centers)).cuda()
-    dD = torch.empty_like(dphi)
-    iters = {}
-    for warm in (0, 2):
-        ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=1, warm_start=warm,
-                 autotune=0)
-        if warm == 2:
-            ex.load_guess_model(blob)
-        e = ex.compute(dphi, dcen, dD)
-        st = ex.stats()
-        iters[warm] = st["iters_total"]
-        if warm == 2:
-            assert st["guess_ms"] > 0.0
-            ref = oracle.exx_workload(w, tol=1e-13, orbitals=phi)
-            assert abs(e - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
-            assert d_maxrel(dD.cpu().numpy(), ref["D"]) <= D_GATE_MAXREL
-        ex.close()
+    del inp, tgt
+    iters = {0: 0, 2: 0}
+    for seed in (7, 8, 9):  # not among the training workloads
+        w = synth.config0(seed)
+        phi = w.orbitals()
+        dphi = torch.from_numpy(phi).cuda()
+        dcen = torch.from_numpy(np.ascontiguousarray(w.centers)).cuda()
+        dD = torch.empty_like(dphi)
+        for warm in (0, 2):
+            ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=1, warm_start=warm,
+                     autotune=0)
+            if warm == 2:
+                ex.load_guess_model(blob)
+            e = ex.compute(dphi, dcen, dD)
+            st = ex.stats()
+            iters[warm] += st["iters_total"]
+            if warm == 2:
+                assert st["guess_ms"] > 0.0
+                ref = oracle.exx_workload(w, tol=1e-13, orbitals=phi)
+                assert abs(e - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
+                assert d_maxrel(dD.cpu().numpy(), ref["D"]) <= D_GATE_MAXREL
+            ex.close()
     print("CG iterations from zero", iters[0], "from the learned guess", iters[2])
-    assert iters[2] < 0.95 * iters[0], iters
+    assert iters[2] < 0.97 * iters[0], iters
 
 
 def test_warm_start_2_without_a_model_is_rejected(torch):

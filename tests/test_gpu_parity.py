@@ -102,6 +102,37 @@ def test_cfg0_residual_paths(torch, cfg0, fixed_residual):
     np.testing.assert_allclose(out["pairs"]["e_pair"], ref["E_pair"], rtol=1e-8, atol=1e-12)
 
 
+@pytest.mark.parametrize("scale", [1e3, 1e-3])
+def test_fixed_point_residuals_at_large_and_small_potentials(torch, cfg0, scale):
+    """The fixed-point residual stencil (the exponent of its scale chosen per
+    pair from a bound on |v|) against the FP64 stencil on orbitals scaled by
+    1e3 and 1e-3 (rho and v by 1e6 and 1e-6): the same energies to the solve's
+    tolerance, both within the gates of the oracle scaled alike."""
+    w, phi, ref = cfg0
+    outs = {}
+    for fixed in (0, 1):
+        outs[fixed] = run_gpu(w, phi * scale, torch=torch, precision=1, solver_kind=2, cluster_size=9, lane_map=5,
+                              autotune=0, fixed_residual=fixed)
+        assert outs[fixed]["stats"]["n_nonconv"] == 0
+    e_ref = ref["E_xx"] * scale ** 4
+    for fixed in (0, 1):
+        assert abs(outs[fixed]["E_xx"] - e_ref) / w.n <= E_GATE_PER_ORBITAL * scale ** 4
+    np.testing.assert_allclose(outs[0]["pairs"]["e_pair"], outs[1]["pairs"]["e_pair"], rtol=1e-8,
+                               atol=1e-12 * scale ** 4)
+
+
+def test_deterministic_d_xx_range_is_guarded(torch, cfg0):
+    """deterministic = 1 keeps D_xx as integers at scale 2^40: contributions
+    |v phi| >= 2^22 cannot be represented; they are dropped and counted, and
+    the call fails instead of returning a wrapped sum."""
+    from paper_1911_10630_gb300.exx import EXX_EINVAL
+    w, phi, _ = cfg0
+    out = run_gpu(w, phi * 400.0, torch=torch, precision=1, deterministic=1, allow_noconv=False,
+                  expect_status=EXX_EINVAL)
+    assert out["status"] == EXX_EINVAL
+    assert "2^22" in out["error"]
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_cfg0_pair_intermediates(torch, cfg0, precision):
     w, phi, ref = cfg0
