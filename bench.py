@@ -431,6 +431,29 @@ def main():
                     "flops_per_point_iteration": 38, "traffic": _traffic("pair_kernel", workload_key),
                     "kernel_ms": kern_ms}
 
+    # the host-buffer leg runs first, before the comparison contexts below
+    # allocate and free their workspaces (measured: copies into freshly
+    # allocated device buffers run at about 200 GB/s, after much allocation
+    # churn far slower)
+    e2e = None
+    if not args.no_e2e:
+        hphi = torch.from_numpy(phi).pin_memory()
+        hD = torch.empty(phi.shape, dtype=torch.float64).pin_memory()
+        hc = torch.from_numpy(centers).pin_memory()
+        exh = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=args.precision)
+        exh.compute_host(hphi, hc, hD, stream=stream)  # warm-up (allocates the device copies)
+        barrier()
+        t0 = time.perf_counter()
+        nrep = max(1, min(args.steps, 3))
+        for _ in range(nrep):
+            exh.compute_host(hphi, hc, hD, stream=stream)
+        barrier()
+        dt = (time.perf_counter() - t0) / nrep
+        e2e = {"value": ws * n_pair / dt, "unit": UNIT, "h2d_bytes_per_step": int(phi.nbytes + centers.nbytes),
+               "d2h_bytes_per_step": int(phi.nbytes + 8), "ms_per_step": dt * 1e3}
+        exh.close()
+        del hphi, hD
+
     extra = {}
     if rank == 0 and args.precision == 1 and args.plain_steps > 0:
         ex0 = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=0)
@@ -458,25 +481,21 @@ def main():
                                                "kernel_ms": st0["solve_ms"]}}
         extra["speedup_vs_plain_fp64_cg"] = value / ws / extra["plain_fp64_cg"]["value"]
         ex0.close()
-
-    e2e = None
-    if not args.no_e2e:
-        hphi = torch.from_numpy(phi).pin_memory()
-        hD = torch.empty(phi.shape, dtype=torch.float64).pin_memory()
-        hc = torch.from_numpy(centers).pin_memory()
-        exh = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=args.precision)
-        exh.compute_host(hphi, hc, hD, stream=stream)  # warm-up (allocates the device copies)
-        barrier()
-        t0 = time.perf_counter()
-        nrep = max(1, min(args.steps, 3))
-        for _ in range(nrep):
-            exh.compute_host(hphi, hc, hD, stream=stream)
-        barrier()
-        dt = (time.perf_counter() - t0) / nrep
-        e2e = {"value": ws * n_pair / dt, "unit": UNIT, "h2d_bytes_per_step": int(phi.nbytes + centers.nbytes),
-               "d2h_bytes_per_step": int(phi.nbytes + 8), "ms_per_step": dt * 1e3}
-        exh.close()
-        del hphi, hD
+        # the same FP64 solve with the multigrid-preconditioned CG (one V-cycle per iteration)
+        exm = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=0, preconditioner=1)
+        exm.compute(dphi, dcen, dD, stream=stream)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        em = exm.compute(dphi, dcen, dD, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        tm = ev0.elapsed_time(ev1)
+        stm = exm.stats()
+        extra["fp64_multigrid_pcg"] = {"value": n_pair / (tm / 1e3), "unit": UNIT, "ms_per_step": tm, "E_xx": em,
+                                       "dE_vs_plain_per_orbital": abs(em - e0) / w.n,
+                                       "iters_p50": stm["iters_p50"], "iters_max": stm["iters_max"],
+                                       "speedup_vs_plain_fp64_cg": statistics.mean(t) / tm}
+        exm.close()
 
     if rank == 0 and ws == 1 and not args.no_legs and not args.orbitals:
         extra["batched_uneven"] = batched_uneven_leg(dev, stream)

@@ -150,6 +150,17 @@ typedef struct {
                           converted to FP64 in place: bitwise reproducible. A
                           contribution |v phi| >= 2^22 is dropped and the call
                           returns EXX_EINVAL (outputs written, D_xx incomplete). */
+    int preconditioner;/* 0: plain CG (default). 1: CG preconditioned by one
+                          symmetric geometric-multigrid V-cycle per iteration
+                          (the paper names preconditioners as the main future
+                          speed-up, Sec. IV.B and the conclusions): the balls
+                          of radius R_l = ceil(R_{l-1} / 2) at spacing
+                          2^l delta down to R <= 3, the 19-point stencil on
+                          every level, one weighted-Jacobi sweep (weight 0.8)
+                          down and up, full-weighting restriction, trilinear
+                          prolongation, the coarsest ball solved exactly. Needs
+                          precision 0 (FP64, one CTA per pair). The stop rule
+                          is unchanged: ||r|| <= tol ||b||.                    */
     int inject_wait_timeout; /* test only (default 0): the next this-many calls
                           of the context each make one extra bounded device wait
                           run out (cluster solver: thread 0 of every CTA polls an

@@ -79,6 +79,8 @@ struct exx_ctx {
     double ln_inv_eps = 0.0, delta_max = 0.0;
     void* geo_mem = nullptr;  // device tables
     BallGeo* d_geos = nullptr;
+    void* mg_mem = nullptr;   // multigrid hierarchies (preconditioner 1)
+    MGGeo* d_mg = nullptr;
     BallGeo geo_host;
 
     // workspace
@@ -366,6 +368,7 @@ extern "C" void exx_destroy(exx_ctx* c) {
     if (c->h_exx) cudaFreeHost(c->h_exx);
     cudaFree(c->ws);
     cudaFree(c->geo_mem);
+    cudaFree(c->mg_mem);
     cudaFree(c->d_orb);
     cudaFree(c->d_dxx);
     cudaFree(c->d_cent);
@@ -456,6 +459,11 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (o.deterministic < 0 || o.deterministic > 1)
         return fail(nullptr, EXX_EINVAL, "exx_init: deterministic must be 0 or 1");
     if (o.inject_wait_timeout < 0) return fail(nullptr, EXX_EINVAL, "exx_init: inject_wait_timeout must be >= 0");
+    if (o.preconditioner < 0 || o.preconditioner > 1)
+        return fail(nullptr, EXX_EINVAL, "exx_init: preconditioner must be 0 or 1");
+    if (o.preconditioner == 1 && (o.precision != 0 || o.solver_kind == 2))
+        return fail(nullptr, EXX_EINVAL,
+                    "exx_init: the multigrid preconditioner runs on the FP64 one-CTA solver (precision 0)");
 
     c = new exx_ctx();
     std::memset(&c->stats, 0, sizeof(c->stats));
@@ -580,6 +588,19 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpy(geometry records)"));
     }
 
+    // multigrid hierarchies of every ball geometry (preconditioner 1)
+    std::vector<std::vector<HostMGLevel>> mgl(c->n_geo);
+    std::vector<std::vector<double>> mgi(c->n_geo);
+    int mg_levels = 0;
+    if (o.preconditioner == 1) {
+        for (int g = 0; g < c->n_geo; ++g) {
+            if (c->balls[g].r_pe <= 3) continue;  // nothing coarser: plain CG for this ball
+            if (!build_mg_levels(c->balls[g].r_pe, c->delta, mgl[g], mgi[g]))
+                return bail(fail(c, EXX_EINVAL, "exx_init: multigrid hierarchy could not be built"));
+            mg_levels = std::max(mg_levels, (int)mgl[g].size());
+        }
+    }
+
     // workspace slots
     const long long S3 = (long long)S * S * S;
     SolveParams& P = c->P;
@@ -599,6 +620,22 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     P.off_sy = off; off = align256(off + sizeof(double) * (size_t)kMaxCluster * (((2 * r_pe + 1) * 28 + 1) & ~1));
     P.off_ush = off; off = align256(off + (sizeof(double) + sizeof(float)) * kNU * B.rows_me.size());
     P.off_vfix = off; off = align256(off + sizeof(long long) * S3);
+    if (mg_levels > 0) {
+        P.off_zc = off; off = align256(off + sizeof(double) * S3);
+        P.off_tc = off; off = align256(off + sizeof(double) * S3);
+        for (int l = 1; l <= mg_levels; ++l) {
+            size_t cube = 0, npts = 0;
+            for (int g = 0; g < c->n_geo; ++g)
+                if ((int)mgl[g].size() >= l) {
+                    const HostMGLevel& H = mgl[g][l - 1];
+                    cube = std::max(cube, (size_t)H.side * H.side * H.side);
+                    npts = std::max(npts, H.off.size());
+                }
+            P.off_mgz[l] = off; off = align256(off + sizeof(double) * cube);
+            P.off_mgt[l] = off; off = align256(off + sizeof(double) * cube);
+            P.off_mgr[l] = off; off = align256(off + sizeof(double) * npts);
+        }
+    }
     c->slot_bytes = off;
     // x^e, y^e, z^e (e < 8) for offsets -Rc..Rc, by repeated multiplication
     {
@@ -616,6 +653,45 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         if (e == cudaSuccess) e = cudaMemcpy(c->d_pow, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "power table"));
         P.pow_tab = c->d_pow;
+    }
+
+    if (mg_levels > 0) {
+        size_t bytes = align256(sizeof(MGGeo) * c->n_geo);
+        for (int g = 0; g < c->n_geo; ++g) {
+            for (const HostMGLevel& H : mgl[g]) bytes += align256(sizeof(int) * H.off.size()) * 2;
+            bytes += align256(sizeof(double) * mgi[g].size());
+        }
+        e = cudaMalloc(&c->mg_mem, bytes);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(multigrid tables)"));
+        char* at = (char*)c->mg_mem + align256(sizeof(MGGeo) * c->n_geo);
+        std::vector<MGGeo> mv(c->n_geo);
+        for (int g = 0; g < c->n_geo && e == cudaSuccess; ++g) {
+            MGGeo& M = mv[g];
+            std::memset(&M, 0, sizeof(M));
+            M.L = (int)mgl[g].size();
+            for (int l = 1; l <= M.L && e == cudaSuccess; ++l) {
+                const HostMGLevel& H = mgl[g][l - 1];
+                MGLevel& lv = M.lv[l];
+                lv.R = H.R;
+                lv.n = (int)H.off.size();
+                lv.side = H.side;
+                lv.cube = (const int*)at;
+                e = cudaMemcpy(at, H.cube.data(), sizeof(int) * H.cube.size(), cudaMemcpyHostToDevice);
+                at += align256(sizeof(int) * H.cube.size());
+                lv.off = (const int*)at;
+                if (e == cudaSuccess) e = cudaMemcpy(at, H.off.data(), sizeof(int) * H.off.size(), cudaMemcpyHostToDevice);
+                at += align256(sizeof(int) * H.off.size());
+            }
+            M.minv = (const double*)at;
+            if (e == cudaSuccess && !mgi[g].empty())
+                e = cudaMemcpy(at, mgi[g].data(), sizeof(double) * mgi[g].size(), cudaMemcpyHostToDevice);
+            at += align256(sizeof(double) * mgi[g].size());
+        }
+        c->d_mg = (MGGeo*)c->mg_mem;
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_mg, mv.data(), sizeof(MGGeo) * c->n_geo, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpy(multigrid tables)"));
+        P.mg = c->d_mg;
+        P.mg_omega = 0.8;
     }
 
     // cluster solver candidates: every cluster size, thread count and lane map

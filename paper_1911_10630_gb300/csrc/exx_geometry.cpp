@@ -480,4 +480,81 @@ void build_residual_order(const HostBall& B, const ClusterLayout& L, std::vector
     }
 }
 
+bool build_mg_levels(int r_pe, const double delta[3], std::vector<HostMGLevel>& levels, std::vector<double>& minv) {
+    levels.clear();
+    minv.clear();
+    int R = r_pe;
+    int l = 0;
+    while (R > 3) {
+        R = (R + 1) / 2;
+        ++l;
+        if (l > kMGMax) return false;
+        HostMGLevel H;
+        H.R = R;
+        H.side = 2 * R + 7;
+        const int c = R + 3;
+        for (int x = -R; x <= R; ++x)
+            for (int y = -R; y <= R; ++y)
+                for (int z = -R; z <= R; ++z) {
+                    if (x * x + y * y + z * z > R * R) continue;
+                    H.cube.push_back(((x + c) * H.side + (y + c)) * H.side + (z + c));
+                    H.off.push_back((x + 128) | ((y + 128) << 8) | ((z + 128) << 16));
+                }
+        levels.push_back(H);
+    }
+    if (levels.empty()) return false;
+    // the coarsest operator, dense: A = -lap at spacing 2^L delta (Eq. d2_1, n = 3)
+    const HostMGLevel& C = levels.back();
+    const int n = (int)C.off.size();
+    const double Wt[4] = {-49.0 / 18.0, 3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0};
+    double ih2[3];
+    for (int a = 0; a < 3; ++a) {
+        const double h = std::ldexp(delta[a], l);
+        ih2[a] = 1.0 / (h * h);
+    }
+    std::vector<int> pos((size_t)C.side * C.side * C.side, -1);
+    for (int k = 0; k < n; ++k) pos[C.cube[k]] = k;
+    std::vector<double> A((size_t)n * n, 0.0);
+    const int st[3] = {C.side * C.side, C.side, 1};
+    for (int k = 0; k < n; ++k) {
+        A[(size_t)k * n + k] = -Wt[0] * (ih2[0] + ih2[1] + ih2[2]);
+        for (int a = 0; a < 3; ++a)
+            for (int q = 1; q <= 3; ++q)
+                for (int sgn = -1; sgn <= 1; sgn += 2) {
+                    const int j = pos[C.cube[k] + sgn * q * st[a]];
+                    if (j >= 0) A[(size_t)k * n + j] -= Wt[q] * ih2[a];
+                }
+    }
+    // Cholesky A = U^T U (A is symmetric positive definite on the ball), then
+    // the inverse column by column from the two triangular solves
+    std::vector<double> U((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double d = A[(size_t)i * n + i];
+        for (int k = 0; k < i; ++k) d -= U[(size_t)k * n + i] * U[(size_t)k * n + i];
+        if (!(d > 0.0)) return false;
+        d = std::sqrt(d);
+        U[(size_t)i * n + i] = d;
+        for (int j = i + 1; j < n; ++j) {
+            double t = A[(size_t)i * n + j];
+            for (int k = 0; k < i; ++k) t -= U[(size_t)k * n + i] * U[(size_t)k * n + j];
+            U[(size_t)i * n + j] = t / d;
+        }
+    }
+    minv.assign((size_t)n * n, 0.0);
+    std::vector<double> y(n);
+    for (int col = 0; col < n; ++col) {
+        for (int i = 0; i < n; ++i) {  // U^T y = e_col
+            double t = i == col ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) t -= U[(size_t)k * n + i] * y[k];
+            y[i] = t / U[(size_t)i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {  // U x = y
+            double t = y[i];
+            for (int k = i + 1; k < n; ++k) t -= U[(size_t)i * n + k] * minv[(size_t)k * n + col];
+            minv[(size_t)i * n + col] = t / U[(size_t)i * n + i];
+        }
+    }
+    return true;
+}
+
 }  // namespace exx

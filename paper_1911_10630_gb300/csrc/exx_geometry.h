@@ -71,4 +71,15 @@ int build_quad_maps(const ClusterLayout& L, const std::vector<int>& pt_slab, int
 // list[k0 .. k1) holds rank r's compact indices, nrim[r] its rim count.
 void build_residual_order(const HostBall& B, const ClusterLayout& L, std::vector<int>& list, std::vector<int>& nrim);
 
+// The coarse levels of the multigrid preconditioner for a PE ball of radius
+// r_pe: R_l = ceil(R_{l-1} / 2) while R_{l-1} > 3; for each level its radius,
+// points (lexicographic), cube side 2 R + 7 and cube indices, packed offsets;
+// minv the inverse of the coarsest level's operator -lap (Eq. d2_1 at spacing
+// 2^L delta_a, zero outside the ball), row-major. Returns false on failure.
+struct HostMGLevel {
+    int R = 0, side = 0;
+    std::vector<int> cube, off;
+};
+bool build_mg_levels(int r_pe, const double delta[3], std::vector<HostMGLevel>& levels, std::vector<double>& minv);
+
 }  // namespace exx

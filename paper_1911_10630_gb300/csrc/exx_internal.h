@@ -59,6 +59,23 @@ struct Stencil {
 
 constexpr int kMaxGeo = 64;
 
+// Geometric multigrid of the preconditioned CG (one CTA per pair): level 0 is
+// the PE ball of R_PE at spacing delta in the workspace cube; level l >= 1 is
+// the ball of R_l = ceil(R_{l-1} / 2) at spacing 2^l delta, stored in its own
+// zero-padded cube of side 2 R_l + 7 (centre R_l + 3), down to R_L <= 3, where
+// the coarse problem is solved with its dense inverse.
+constexpr int kMGMax = 6;  // coarse levels at most (R_PE <= 64)
+struct MGLevel {
+    int R, n, side;         // radius, points, cube side
+    const int* cube;        // [n] index of each point in the level cube (Algorithm 2 order)
+    const int* off;         // [n] packed offsets, as BallGeo::pt_off
+};
+struct MGGeo {
+    int L;                  // coarse levels (1..L)
+    MGLevel lv[kMGMax + 1]; // lv[1..L]
+    const double* minv;     // [n_L][n_L] inverse of the coarsest operator
+};
+
 // Everything the pair kernel needs, passed by value.
 struct SolveParams {
     // inputs / outputs
@@ -104,6 +121,11 @@ struct SolveParams {
     double fix_inv;           // 1 / (180 delta^2): the integer stencil's weights are 180 delta^2 x Eq. d2_1's
     double dfix;              // D_xx as fixed-point integers with this scale (2^40; 0 = FP64 atomics)
     int* dfix_range;          // counts fixed-point D_xx contributions beyond the range (dropped)
+    // multigrid-preconditioned CG (one-CTA FP64 solver): per geometry, NULL = plain CG
+    const MGGeo* mg;
+    double mg_omega;          // weight of the Jacobi smoothing sweeps
+    size_t off_zc, off_tc;    // level-0 cubes (the workspace cube's size): smoothed correction, residual
+    size_t off_mgz[kMGMax + 1], off_mgt[kMGMax + 1], off_mgr[kMGMax + 1];  // levels 1..: cubes and right-hand side
     const double* pow_tab;  // [3][2 Rc + 1][8] x^e, y^e, z^e (cluster kernel; global, read-only)
 
     // solver

@@ -36,7 +36,8 @@ class exx_options(ctypes.Structure):
                 ("solver_kind", ctypes.c_int), ("cluster_size", ctypes.c_int), ("update_drop", ctypes.c_double),
                 ("lane_map", ctypes.c_int), ("autotune", ctypes.c_int), ("r_pe_nonself", ctypes.c_int),
                 ("r_me_nonself", ctypes.c_int), ("fixed_residual", ctypes.c_int),
-                ("deterministic", ctypes.c_int), ("inject_wait_timeout", ctypes.c_int)]
+                ("deterministic", ctypes.c_int), ("preconditioner", ctypes.c_int),
+                ("inject_wait_timeout", ctypes.c_int)]
 
 
 class exx_stats(ctypes.Structure):

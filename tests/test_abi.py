@@ -114,6 +114,20 @@ def test_init_rejects_bad_options(lib):
     o.deterministic = 2
     st, ctx = _init(lib, opt=o)
     assert st == -1 and "deterministic" in lib.exx_last_error(None).decode()
+    o = lib.exx_default_options()
+    assert o.preconditioner == 0 and o.inject_wait_timeout == 0
+    o.preconditioner = 2
+    st, ctx = _init(lib, opt=o)
+    assert st == -1 and "preconditioner" in lib.exx_last_error(None).decode()
+    o = lib.exx_default_options()
+    o.preconditioner = 1
+    o.precision = 1  # the multigrid-preconditioned CG is the FP64 one-CTA solver's
+    st, ctx = _init(lib, opt=o)
+    assert st == -1 and "multigrid" in lib.exx_last_error(None).decode()
+    o = lib.exx_default_options()
+    o.inject_wait_timeout = -1
+    st, ctx = _init(lib, opt=o)
+    assert st == -1 and "inject_wait_timeout" in lib.exx_last_error(None).decode()
 
 
 def test_null_and_destroy_are_safe(lib):

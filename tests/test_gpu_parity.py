@@ -412,3 +412,63 @@ def test_warm_start_from_previous_step(torch):
     before = {(a, b): g for a, b, g in zip(i0.tolist(), j0.tolist(), g0.tolist())}
     moved = [k for k, g in zip(zip(i1.tolist(), j1.tolist()), g1.tolist()) if k in before and before[k] != g]
     assert moved  # some kept pairs' grid centres moved: the shifted start was exercised
+
+
+# --------------------------------------------------------------------------
+# Multigrid-preconditioned CG (preconditioner 1, FP64, one CTA per pair)
+# --------------------------------------------------------------------------
+
+def test_multigrid_pcg_meets_the_gates_in_far_fewer_iterations(torch, cfg0):
+    """Config 0 (R_PE 16 / R_ME 20, tol 1e-10; levels 16, 8, 4, 2): the same
+    energies and forces as the oracle under the gates, every pair's E_ij to
+    the solve's tolerance, in a small fraction of the plain CG's iterations."""
+    w, phi, ref = cfg0
+    plain = run_gpu(w, phi, torch=torch, precision=0)
+    mg = run_gpu(w, phi, torch=torch, precision=0, preconditioner=1)
+    assert mg["stats"]["n_nonconv"] == 0 and mg["stats"]["solver_kind"] == 1
+    _pairs_equal(mg["pairs"], ref["pairs"])
+    assert abs(mg["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
+    assert d_maxrel(mg["D"], ref["D"]) <= D_GATE_MAXREL
+    np.testing.assert_allclose(mg["pairs"]["e_pair"], ref["E_pair"], rtol=1e-8, atol=1e-12)
+    it_plain, it_mg = plain["stats"]["iters_total"], mg["stats"]["iters_total"]
+    assert it_mg < 0.25 * it_plain, (it_mg, it_plain)
+
+
+def test_multigrid_pcg_per_pair_radii(torch):
+    """Per-pair radii (R_PE 12..16): one hierarchy per ball (levels 12, 6, 3 up to
+    16, 8, 4, 2) in the same workspace slots, cleared between pairs."""
+    w = synth.tiny(seed=8, n=6, npts=48, length=9.6, r_pe=16, r_me=22, alpha=(0.5, 2.0), tol=1e-10, min_sep=1.2)
+    w.radii_mode = 1
+    phi = w.orbitals()
+    ref = oracle.exx_workload(w, tol=1e-13, orbitals=phi)
+    assert len(set(ref["pairs"][3])) >= 3
+    out = run_gpu(w, phi, torch=torch, precision=0, preconditioner=1)
+    _pairs_radii_equal(out["pairs"], ref["pairs"])
+    assert out["stats"]["n_nonconv"] == 0
+    assert abs(out["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
+    assert d_maxrel(out["D"], ref["D"]) <= D_GATE_MAXREL
+    np.testing.assert_allclose(out["pairs"]["e_pair"], ref["E_pair"], rtol=1e-7, atol=1e-12)
+
+
+def test_multigrid_pcg_anisotropic_ragged(torch):
+    """Non-cubic grid and cell (each level's stencil with its own spacings),
+    small balls (levels 5, 3), pairs across faces."""
+    w = synth.tiny(seed=3, n=6, npts=28, length=6.5, r_pe=5, r_me=9, r_pair=3.0, tol=1e-10)
+    w.grid = np.array([28, 30, 26])
+    w.cell = np.array([6.5, 7.1, 6.2])
+    w.centers = np.mod(w.centers, w.cell)
+    w.centers[0] = [0.05, 3.0, 6.1]
+    w.centers[1] = [6.3, 3.2, 0.2]
+    phi = w.orbitals()
+    ref = oracle.exx_workload(w, tol=1e-13, orbitals=phi)
+    out = run_gpu(w, phi, torch=torch, precision=0, preconditioner=1)
+    _pairs_equal(out["pairs"], ref["pairs"])
+    assert abs(out["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
+    assert d_maxrel(out["D"], ref["D"]) <= D_GATE_MAXREL
+
+
+def test_multigrid_requires_fp64(torch):
+    from paper_1911_10630_gb300.exx import Exx, ExxError
+    w = synth.config0()
+    with pytest.raises(ExxError, match="multigrid"):
+        Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=1, preconditioner=1)
