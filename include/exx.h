@@ -158,9 +158,12 @@ typedef struct {
                           2^l delta down to R <= 3, the 19-point stencil on
                           every level, one weighted-Jacobi sweep (weight 0.8)
                           down and up, full-weighting restriction, trilinear
-                          prolongation, the coarsest ball solved exactly. Needs
-                          precision 0 (FP64, one CTA per pair). The stop rule
-                          is unchanged: ||r|| <= tol ||b||.                    */
+                          prolongation, the coarsest ball solved exactly. Runs
+                          on the one-CTA solver; the CG recurrence and its stop
+                          test are FP64 (||r|| <= tol ||b|| as without it); with
+                          precision 0 every level is FP64, with precision 1 the
+                          V-cycle runs in FP32 on r / ||r|| (scaled back: the
+                          preconditioner is linear). Not with warm_start.      */
     int inject_wait_timeout; /* test only (default 0): the next this-many calls
                           of the context each make one extra bounded device wait
                           run out (cluster solver: thread 0 of every CTA polls an

@@ -461,9 +461,10 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (o.inject_wait_timeout < 0) return fail(nullptr, EXX_EINVAL, "exx_init: inject_wait_timeout must be >= 0");
     if (o.preconditioner < 0 || o.preconditioner > 1)
         return fail(nullptr, EXX_EINVAL, "exx_init: preconditioner must be 0 or 1");
-    if (o.preconditioner == 1 && (o.precision != 0 || o.solver_kind == 2))
+    if (o.preconditioner == 1 && (o.solver_kind == 2 || o.warm_start != 0))
         return fail(nullptr, EXX_EINVAL,
-                    "exx_init: the multigrid preconditioner runs on the FP64 one-CTA solver (precision 0)");
+                    "exx_init: the multigrid-preconditioned CG runs on the one-CTA solver (solver_kind 0 or 1, "
+                    "warm_start 0)");
 
     c = new exx_ctx();
     std::memset(&c->stats, 0, sizeof(c->stats));
@@ -659,7 +660,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         size_t bytes = align256(sizeof(MGGeo) * c->n_geo);
         for (int g = 0; g < c->n_geo; ++g) {
             for (const HostMGLevel& H : mgl[g]) bytes += align256(sizeof(int) * H.off.size()) * 2;
-            bytes += align256(sizeof(double) * mgi[g].size());
+            bytes += align256(sizeof(double) * mgi[g].size()) + align256(sizeof(float) * mgi[g].size());
         }
         e = cudaMalloc(&c->mg_mem, bytes);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(multigrid tables)"));
@@ -686,17 +687,23 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             if (e == cudaSuccess && !mgi[g].empty())
                 e = cudaMemcpy(at, mgi[g].data(), sizeof(double) * mgi[g].size(), cudaMemcpyHostToDevice);
             at += align256(sizeof(double) * mgi[g].size());
+            std::vector<float> m32(mgi[g].begin(), mgi[g].end());
+            M.minv32 = (const float*)at;
+            if (e == cudaSuccess && !m32.empty())
+                e = cudaMemcpy(at, m32.data(), sizeof(float) * m32.size(), cudaMemcpyHostToDevice);
+            at += align256(sizeof(float) * m32.size());
         }
         c->d_mg = (MGGeo*)c->mg_mem;
         if (e == cudaSuccess) e = cudaMemcpy(c->d_mg, mv.data(), sizeof(MGGeo) * c->n_geo, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpy(multigrid tables)"));
         P.mg = c->d_mg;
         P.mg_omega = 0.8;
+        P.mg32 = o.precision == 1 ? 1 : 0;
     }
 
     // cluster solver candidates: every cluster size, thread count and lane map
     // whose slab layout, registers and shared memory fit
-    if (o.precision == 1 && o.solver_kind != 1 && c->n_geo == 1) {
+    if (o.precision == 1 && o.solver_kind != 1 && o.preconditioner == 0 && c->n_geo == 1) {
         int max_optin = 0;
         cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
         const int csizes[4] = {9, 8, 4, 2};
@@ -848,7 +855,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     // CTAs; at a cluster size, the variant specialised for the slab pitch
     // first, then fewer quads per thread); the one-CTA pair kernel takes any
     // class that fits none
-    if (o.precision == 1 && o.solver_kind != 1 && o.radii_mode == 1) {
+    if (o.precision == 1 && o.solver_kind != 1 && o.preconditioner == 0 && o.radii_mode == 1) {
         int max_optin = 0;
         cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
         const bool isotropic = c->delta[0] == c->delta[1] && c->delta[1] == c->delta[2];
@@ -911,7 +918,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         }
         want = (long long)c->lane_slots[0] + c->lane_slots[1];
     } else {
-        e = pair_kernel_occupancy(c->threads, o.precision == 1, c->smem, &bps);
+        e = pair_kernel_occupancy(c->threads, o.precision == 1 && o.preconditioner == 0, c->smem, &bps);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
         if (bps < 1) return bail(fail(c, EXX_ECUDA, "pair kernel does not fit on an SM"));
         int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, bps) : std::min(bps, 2);

@@ -86,29 +86,35 @@ __device__ int cg_ball(T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d,
 // symmetric positive definite operator and the CG stays a CG. Vectors that a
 // stencil or a transfer reads live in zero-padded cubes of the workspace slot.
 // --------------------------------------------------------------------------
+template <typename T>
 struct MGView {
     const int* cube;
     const int* off;
     int n, S, c;       // points, cube side, cube centre
     long long S2;
-    double* Z;         // smoothed correction (cube)
-    double* T;         // residual, then the post-smoothed correction (cube)
-    const double* rhs; // right-hand side (compact)
-    double* rnext;     // the next level's right-hand side (compact), NULL on the coarsest
-    Stencil<double> A; // -lap at the level's spacing
+    T* Z;              // smoothed correction (cube)
+    T* Tc;             // residual, then the post-smoothed correction (cube)
+    const T* rhs;      // right-hand side (compact)
+    T* rnext;          // the next level's right-hand side (compact), NULL on the coarsest
+    Stencil<T> A;      // -lap at the level's spacing
 };
 
-__device__ __forceinline__ long long mg_idx(const MGView& v, int x, int y, int z) {
+template <typename T>
+__device__ __forceinline__ long long mg_idx(const MGView<T>& v, int x, int y, int z) {
     return ((long long)(x + v.c) * v.S + (y + v.c)) * v.S + (z + v.c);
 }
 
-// z of level l (in T) from its right-hand side: the down and up halves of the V-cycle.
-template <int NT>
+// z of level 0 (in its Tc cube) from the right-hand side r0 (compact): the
+// down and up halves of the V-cycle, in T (FP64, or FP32 on a normalised r0).
+template <int NT, typename T>
 __device__ __noinline__ void mg_vcycle(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot,
-                          const double* __restrict__ r0) {
-    const double w = P.mg_omega;
+                                       const T* __restrict__ r0) {
+    const T w = (T)P.mg_omega;
     auto view = [&](int l) {
-        MGView v;
+        MGView<T> v;
+        Stencil<T> base;
+        if constexpr (sizeof(T) == 8) base = negated(P.st64);
+        else base = negated(P.st32);
         if (l == 0) {
             v.cube = G.pt_cube;
             v.off = G.pt_off;
@@ -116,10 +122,10 @@ __device__ __noinline__ void mg_vcycle(const SolveParams& P, const BallGeo& G, c
             v.S = P.S;
             v.c = P.Rc;
             v.S2 = P.S2;
-            v.Z = reinterpret_cast<double*>(slot + P.off_zc);
-            v.T = reinterpret_cast<double*>(slot + P.off_tc);
+            v.Z = reinterpret_cast<T*>(slot + P.off_zc);
+            v.Tc = reinterpret_cast<T*>(slot + P.off_tc);
             v.rhs = r0;
-            v.A = negated(P.st64);
+            v.A = base;
         } else {
             const MGLevel& lv = M.lv[l];
             v.cube = lv.cube;
@@ -128,11 +134,11 @@ __device__ __noinline__ void mg_vcycle(const SolveParams& P, const BallGeo& G, c
             v.S = lv.side;
             v.c = lv.R + 3;
             v.S2 = (long long)lv.side * lv.side;
-            v.Z = reinterpret_cast<double*>(slot + P.off_mgz[l]);
-            v.T = reinterpret_cast<double*>(slot + P.off_mgt[l]);
-            v.rhs = reinterpret_cast<const double*>(slot + P.off_mgr[l]);
-            const double sc = ldexp(1.0, -2 * l);  // spacing 2^l delta
-            v.A = negated(P.st64);
+            v.Z = reinterpret_cast<T*>(slot + P.off_mgz[l]);
+            v.Tc = reinterpret_cast<T*>(slot + P.off_mgt[l]);
+            v.rhs = reinterpret_cast<const T*>(slot + P.off_mgr[l]);
+            const T sc = (T)ldexp(1.0, -2 * l);  // spacing 2^l delta
+            v.A = base;
             v.A.c0 *= sc;
             for (int q = 0; q < 3; ++q) {
                 v.A.cx[q] *= sc;
@@ -140,53 +146,56 @@ __device__ __noinline__ void mg_vcycle(const SolveParams& P, const BallGeo& G, c
                 v.A.cz[q] *= sc;
             }
         }
-        v.rnext = l < M.L ? reinterpret_cast<double*>(slot + P.off_mgr[l + 1]) : nullptr;
+        v.rnext = l < M.L ? reinterpret_cast<T*>(slot + P.off_mgr[l + 1]) : nullptr;
         return v;
     };
     // down: Jacobi from zero, residual, restriction
     for (int l = 0; l < M.L; ++l) {
-        const MGView v = view(l);
-        const double wd = w / v.A.c0;
+        const MGView<T> v = view(l);
+        const T wd = w / v.A.c0;
         for (int k = threadIdx.x; k < v.n; k += NT) v.Z[v.cube[k]] = wd * v.rhs[k];
         __syncthreads();
         for (int k = threadIdx.x; k < v.n; k += NT) {
             const int c = v.cube[k];
-            v.T[c] = v.rhs[k] - lap19<double>(v.Z, c, v.S, v.S2, v.A);
+            v.Tc[c] = v.rhs[k] - lap19<T>(v.Z, c, v.S, v.S2, v.A);
         }
         __syncthreads();
         const MGLevel& cl = M.lv[l + 1];
         for (int k = threadIdx.x; k < cl.n; k += NT) {
             const int pk = cl.off[k];
             const int X = 2 * off_x(pk), Y = 2 * off_y(pk), Z = 2 * off_z(pk);
-            double acc = 0.0;
+            T acc = T(0);
 #pragma unroll
             for (int ex = -1; ex <= 1; ++ex)
 #pragma unroll
                 for (int ey = -1; ey <= 1; ++ey)
 #pragma unroll
                     for (int ez = -1; ez <= 1; ++ez) {
-                        const double wt = (ex ? 0.5 : 1.0) * (ey ? 0.5 : 1.0) * (ez ? 0.5 : 1.0);
-                        acc = fma(wt, v.T[mg_idx(v, X + ex, Y + ey, Z + ez)], acc);
+                        const T wt = (ex ? T(0.5) : T(1)) * (ey ? T(0.5) : T(1)) * (ez ? T(0.5) : T(1));
+                        acc = fma(wt, v.Tc[mg_idx(v, X + ex, Y + ey, Z + ez)], acc);
                     }
-            v.rnext[k] = 0.125 * acc;
+            v.rnext[k] = T(0.125) * acc;
         }
         __syncthreads();
     }
     // the coarsest level: its dense inverse
     {
-        const MGView v = view(M.L);
+        const MGView<T> v = view(M.L);
+        const T* minv;
+        if constexpr (sizeof(T) == 8) minv = M.minv;
+        else minv = M.minv32;
         for (int k = threadIdx.x; k < v.n; k += NT) {
-            const double* row = M.minv + (size_t)k * v.n;
-            double acc = 0.0;
+            const T* row = minv + (size_t)k * v.n;
+            T acc = T(0);
             for (int j = 0; j < v.n; ++j) acc = fma(row[j], v.rhs[j], acc);
             v.Z[v.cube[k]] = acc;
         }
         __syncthreads();
     }
-    // up: prolongation of the coarser correction, then a Jacobi sweep into T
+    // up: prolongation of the coarser correction, then a Jacobi sweep into Tc
     for (int l = M.L - 1; l >= 0; --l) {
-        const MGView v = view(l), vc = view(l + 1);
-        const double* zc = (l + 1 == M.L) ? vc.Z : vc.T;
+        const MGView<T> v = view(l), vc = view(l + 1);
+        const T* zc = (l + 1 == M.L) ? vc.Z : vc.Tc;
         for (int k = threadIdx.x; k < v.n; k += NT) {
             const int pk = v.off[k];
             const int o[3] = {off_x(pk), off_y(pk), off_z(pk)};
@@ -196,7 +205,7 @@ __device__ __noinline__ void mg_vcycle(const SolveParams& P, const BallGeo& G, c
                 lo[a] = (o[a] - (o[a] & 1)) / 2;  // floor(o / 2)
                 hi[a] = lo[a] + (o[a] & 1);
             }
-            double acc = 0.0;
+            T acc = T(0);
 #pragma unroll
             for (int cx = 0; cx < 2; ++cx)
 #pragma unroll
@@ -204,18 +213,18 @@ __device__ __noinline__ void mg_vcycle(const SolveParams& P, const BallGeo& G, c
 #pragma unroll
                     for (int cz = 0; cz < 2; ++cz) {
                         if ((cx && hi[0] == lo[0]) || (cy && hi[1] == lo[1]) || (cz && hi[2] == lo[2])) continue;
-                        const double wt = (hi[0] != lo[0] ? 0.5 : 1.0) * (hi[1] != lo[1] ? 0.5 : 1.0) *
-                                          (hi[2] != lo[2] ? 0.5 : 1.0);
+                        const T wt = (hi[0] != lo[0] ? T(0.5) : T(1)) * (hi[1] != lo[1] ? T(0.5) : T(1)) *
+                                     (hi[2] != lo[2] ? T(0.5) : T(1));
                         acc = fma(wt, zc[mg_idx(vc, cx ? hi[0] : lo[0], cy ? hi[1] : lo[1], cz ? hi[2] : lo[2])],
                                   acc);
                     }
             v.Z[v.cube[k]] += acc;
         }
         __syncthreads();
-        const double wd = w / v.A.c0;
+        const T wd = w / v.A.c0;
         for (int k = threadIdx.x; k < v.n; k += NT) {
             const int c = v.cube[k];
-            v.T[c] = fma(wd, v.rhs[k] - lap19<double>(v.Z, c, v.S, v.S2, v.A), v.Z[c]);
+            v.Tc[c] = fma(wd, v.rhs[k] - lap19<T>(v.Z, c, v.S, v.S2, v.A), v.Z[c]);
         }
         __syncthreads();
     }
@@ -223,36 +232,57 @@ __device__ __noinline__ void mg_vcycle(const SolveParams& P, const BallGeo& G, c
 
 // Clears what a pair wrote into the multigrid cubes (per-pair radii: the next
 // pair's balls may have other sizes, and every cube must be zero off its ball).
-template <int NT>
+template <int NT, typename T>
 __device__ void mg_clear(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot) {
-    double* Z0 = reinterpret_cast<double*>(slot + P.off_zc);
-    double* T0 = reinterpret_cast<double*>(slot + P.off_tc);
-    for (int k = threadIdx.x; k < G.n_pe; k += NT) Z0[G.pt_cube[k]] = T0[G.pt_cube[k]] = 0.0;
+    T* Z0 = reinterpret_cast<T*>(slot + P.off_zc);
+    T* T0 = reinterpret_cast<T*>(slot + P.off_tc);
+    for (int k = threadIdx.x; k < G.n_pe; k += NT) Z0[G.pt_cube[k]] = T0[G.pt_cube[k]] = T(0);
     for (int l = 1; l <= M.L; ++l) {
-        double* Z = reinterpret_cast<double*>(slot + P.off_mgz[l]);
-        double* T = reinterpret_cast<double*>(slot + P.off_mgt[l]);
-        for (int k = threadIdx.x; k < M.lv[l].n; k += NT) Z[M.lv[l].cube[k]] = T[M.lv[l].cube[k]] = 0.0;
+        T* Z = reinterpret_cast<T*>(slot + P.off_mgz[l]);
+        T* Tc = reinterpret_cast<T*>(slot + P.off_mgt[l]);
+        for (int k = threadIdx.x; k < M.lv[l].n; k += NT) Z[M.lv[l].cube[k]] = Tc[M.lv[l].cube[k]] = T(0);
     }
 }
 
 // PCG on the PE ball with the V-cycle as the preconditioner. On entry: r = rhs,
-// d = 0, rr = ||rhs||^2; p goes to the cube pc (zero off the ball). Returns the
-// iteration count; rr_out receives the final ||r||^2.
+// d = 0, rr = ||rhs||^2; p goes to the cube pc (zero off the ball). The CG
+// recurrence and its stop test are FP64; with P.mg32 the V-cycle runs in FP32
+// on r / ||r|| (r32 its compact FP32 copy) and its result is scaled back by
+// ||r||, the preconditioner being linear. Returns the iteration count;
+// rr_out receives the final ||r||^2.
 template <int NT>
-__device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot, double* __restrict__ pc,
-                      double* __restrict__ r, double* __restrict__ d, double* __restrict__ ap, double rr,
-                      double target2, int max_iter, double (*red)[33], int& flip, double& rr_out) {
+__device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot,
+                                   double* __restrict__ pc, double* __restrict__ r, double* __restrict__ d,
+                                   double* __restrict__ ap, float* __restrict__ r32, double rr, double target2,
+                                   int max_iter, double (*red)[33], int& flip, double& rr_out) {
     const int* cube = G.pt_cube;
     const int n_pe = G.n_pe, S = P.S;
     const long long S2 = P.S2;
     const Stencil<double> A = negated(P.st64);
+    const bool f32 = P.mg32 != 0;
     const double* T0 = reinterpret_cast<const double*>(slot + P.off_tc);
-    mg_vcycle<NT>(P, G, M, slot, r);
+    const float* T32 = reinterpret_cast<const float*>(slot + P.off_tc);
+    double zs = 1.0;  // scale of the FP32 V-cycle's result
+    // z = M r into the level-0 Tc cube (FP64, or FP32 times zs)
+    auto precondition = [&](double rr_now) {
+        if (f32) {
+            zs = sqrt(rr_now);
+            const double inv = zs > 0.0 ? 1.0 / zs : 0.0;
+            for (int k = threadIdx.x; k < n_pe; k += NT) r32[k] = (float)(r[k] * inv);
+            __syncthreads();
+            mg_vcycle<NT, float>(P, G, M, slot, r32);
+        } else {
+            mg_vcycle<NT, double>(P, G, M, slot, r);
+        }
+    };
+    auto zval = [&](int c) -> double { return f32 ? zs * (double)T32[c] : T0[c]; };
+    precondition(rr);
     double rz = 0.0;
     for (int k = threadIdx.x; k < n_pe; k += NT) {
         const int c = cube[k];
-        pc[c] = T0[c];
-        rz = fma(r[k], T0[c], rz);
+        const double z = zval(c);
+        pc[c] = z;
+        rz = fma(r[k], z, rz);
     }
     rz = block_sum<NT, double>(rz, red, flip);
     int it = 0;
@@ -278,15 +308,15 @@ __device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const
         ++it;
         rr = rrn;
         if (rrn <= target2 || !(rrn == rrn)) break;
-        mg_vcycle<NT>(P, G, M, slot, r);
+        precondition(rrn);
         double rzn = 0.0;
-        for (int k = threadIdx.x; k < n_pe; k += NT) rzn = fma(r[k], T0[cube[k]], rzn);
+        for (int k = threadIdx.x; k < n_pe; k += NT) rzn = fma(r[k], zval(cube[k]), rzn);
         rzn = block_sum<NT, double>(rzn, red, flip);
         const double be = rzn / rz;
         rz = rzn;
         for (int k = threadIdx.x; k < n_pe; k += NT) {
             const int c = cube[k];
-            pc[c] = fma(be, pc[c], T0[c]);
+            pc[c] = fma(be, pc[c], zval(c));
         }
         __syncthreads();
     }
@@ -378,7 +408,8 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) pair_kernel(const __grid_co
             double rr_fin;
             const double target2 = P.tol * P.tol * bb;
             if (MG && P.mg[pr.geo].L > 0)
-                iters = mg_pcg<NT>(P, G, P.mg[pr.geo], slot, pc, r, d, ap, bb, target2, P.max_iter, red, flip, rr_fin);
+                iters = mg_pcg<NT>(P, G, P.mg[pr.geo], slot, pc, r, d, ap, r32, bb, target2, P.max_iter, red, flip,
+                                   rr_fin);
             else
                 iters = cg_ball<double, NT>(pc, r, d, ap, cube, n_pe, S, S2, neg64, bb, target2, P.max_iter, red,
                                             flip, rr_fin);
@@ -448,7 +479,10 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) pair_kernel(const __grid_co
                 if (MIXED) p32[cube[k]] = 0.0f;
                 else pc[cube[k]] = 0.0;
             }
-            if (MG && P.mg[pr.geo].L > 0) mg_clear<NT>(P, G, P.mg[pr.geo], slot);
+            if (MG && P.mg[pr.geo].L > 0) {
+                if (P.mg32) mg_clear<NT, float>(P, G, P.mg[pr.geo], slot);
+                else mg_clear<NT, double>(P, G, P.mg[pr.geo], slot);
+            }
         }
         __syncthreads();
     }
@@ -507,7 +541,7 @@ static cudaError_t launch_t(const SolveParams& P, int grid, size_t smem, cudaStr
 }
 
 cudaError_t launch_pair_kernel(const SolveParams& P, int threads, bool mixed, int grid, size_t smem, cudaStream_t st) {
-    if (P.mg && !mixed) {  // the multigrid-preconditioned FP64 CG (512 threads)
+    if (P.mg) {  // the multigrid-preconditioned CG: FP64 recurrence, FP64 or FP32 V-cycle (512 threads)
         pair_kernel<512, false, true><<<grid, 512, smem, st>>>(P);
         return cudaGetLastError();
     }

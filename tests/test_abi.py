@@ -121,7 +121,8 @@ def test_init_rejects_bad_options(lib):
     assert st == -1 and "preconditioner" in lib.exx_last_error(None).decode()
     o = lib.exx_default_options()
     o.preconditioner = 1
-    o.precision = 1  # the multigrid-preconditioned CG is the FP64 one-CTA solver's
+    o.precision = 1
+    o.solver_kind = 2  # the multigrid-preconditioned CG is the one-CTA solver's
     st, ctx = _init(lib, opt=o)
     assert st == -1 and "multigrid" in lib.exx_last_error(None).decode()
     o = lib.exx_default_options()

@@ -418,13 +418,15 @@ def test_warm_start_from_previous_step(torch):
 # Multigrid-preconditioned CG (preconditioner 1, FP64, one CTA per pair)
 # --------------------------------------------------------------------------
 
-def test_multigrid_pcg_meets_the_gates_in_far_fewer_iterations(torch, cfg0):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multigrid_pcg_meets_the_gates_in_far_fewer_iterations(torch, cfg0, precision):
     """Config 0 (R_PE 16 / R_ME 20, tol 1e-10; levels 16, 8, 4, 2): the same
     energies and forces as the oracle under the gates, every pair's E_ij to
-    the solve's tolerance, in a small fraction of the plain CG's iterations."""
+    the solve's tolerance, in a small fraction of the plain CG's iterations;
+    precision 1 runs the V-cycle in FP32 inside the FP64 CG."""
     w, phi, ref = cfg0
     plain = run_gpu(w, phi, torch=torch, precision=0)
-    mg = run_gpu(w, phi, torch=torch, precision=0, preconditioner=1)
+    mg = run_gpu(w, phi, torch=torch, precision=precision, preconditioner=1)
     assert mg["stats"]["n_nonconv"] == 0 and mg["stats"]["solver_kind"] == 1
     _pairs_equal(mg["pairs"], ref["pairs"])
     assert abs(mg["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
@@ -434,7 +436,8 @@ def test_multigrid_pcg_meets_the_gates_in_far_fewer_iterations(torch, cfg0):
     assert it_mg < 0.25 * it_plain, (it_mg, it_plain)
 
 
-def test_multigrid_pcg_per_pair_radii(torch):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multigrid_pcg_per_pair_radii(torch, precision):
     """Per-pair radii (R_PE 12..16): one hierarchy per ball (levels 12, 6, 3 up to
     16, 8, 4, 2) in the same workspace slots, cleared between pairs."""
     w = synth.tiny(seed=8, n=6, npts=48, length=9.6, r_pe=16, r_me=22, alpha=(0.5, 2.0), tol=1e-10, min_sep=1.2)
@@ -442,7 +445,7 @@ def test_multigrid_pcg_per_pair_radii(torch):
     phi = w.orbitals()
     ref = oracle.exx_workload(w, tol=1e-13, orbitals=phi)
     assert len(set(ref["pairs"][3])) >= 3
-    out = run_gpu(w, phi, torch=torch, precision=0, preconditioner=1)
+    out = run_gpu(w, phi, torch=torch, precision=precision, preconditioner=1)
     _pairs_radii_equal(out["pairs"], ref["pairs"])
     assert out["stats"]["n_nonconv"] == 0
     assert abs(out["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
@@ -450,7 +453,8 @@ def test_multigrid_pcg_per_pair_radii(torch):
     np.testing.assert_allclose(out["pairs"]["e_pair"], ref["E_pair"], rtol=1e-7, atol=1e-12)
 
 
-def test_multigrid_pcg_anisotropic_ragged(torch):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multigrid_pcg_anisotropic_ragged(torch, precision):
     """Non-cubic grid and cell (each level's stencil with its own spacings),
     small balls (levels 5, 3), pairs across faces."""
     w = synth.tiny(seed=3, n=6, npts=28, length=6.5, r_pe=5, r_me=9, r_pair=3.0, tol=1e-10)
@@ -461,14 +465,14 @@ def test_multigrid_pcg_anisotropic_ragged(torch):
     w.centers[1] = [6.3, 3.2, 0.2]
     phi = w.orbitals()
     ref = oracle.exx_workload(w, tol=1e-13, orbitals=phi)
-    out = run_gpu(w, phi, torch=torch, precision=0, preconditioner=1)
+    out = run_gpu(w, phi, torch=torch, precision=precision, preconditioner=1)
     _pairs_equal(out["pairs"], ref["pairs"])
     assert abs(out["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
     assert d_maxrel(out["D"], ref["D"]) <= D_GATE_MAXREL
 
 
-def test_multigrid_requires_fp64(torch):
+def test_multigrid_runs_on_the_one_cta_solver(torch):
     from paper_1911_10630_gb300.exx import Exx, ExxError
     w = synth.config0()
     with pytest.raises(ExxError, match="multigrid"):
-        Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=1, preconditioner=1)
+        Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=1, preconditioner=1, solver_kind=2)
