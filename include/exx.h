@@ -159,11 +159,11 @@ typedef struct {
                           every level, one weighted-Jacobi sweep (weight 0.8)
                           down and up, full-weighting restriction, trilinear
                           prolongation, the coarsest ball solved exactly. Runs
-                          on the one-CTA solver; the CG recurrence and its stop
-                          test are FP64 (||r|| <= tol ||b|| as without it); with
-                          precision 0 every level is FP64, with precision 1 the
-                          V-cycle runs in FP32 on r / ||r|| (scaled back: the
-                          preconditioner is linear). Not with warm_start.      */
+                          on the one-CTA solver, not with warm_start. With
+                          precision 0 the PCG and every level are FP64; with
+                          precision 1 each inner solve of the FP64 refinement
+                          loop is this PCG in FP32 (recurrence and V-cycle).
+                          The stop rule is unchanged: ||r|| <= tol ||b||.      */
     int inject_wait_timeout; /* test only (default 0): the next this-many calls
                           of the context each make one extra bounded device wait
                           run out (cluster solver: thread 0 of every CTA polls an

@@ -35,7 +35,7 @@ cudaError_t set_multipole_const_solve(const MultipoleConst& mc);
 cudaError_t set_multipole_const_cluster(const MultipoleConst& mc);
 size_t pair_kernel_smem(int Rc, int r_pe_max);
 cudaError_t launch_pair_kernel(const SolveParams& P, int threads, bool mixed, int grid, size_t smem, cudaStream_t st);
-cudaError_t pair_kernel_occupancy(int threads, bool mixed, size_t smem, int* blocks_per_sm);
+cudaError_t pair_kernel_occupancy(int threads, bool mixed, bool mg, size_t smem, int* blocks_per_sm);
 cudaError_t launch_debug_readback(const SolveParams& P, const PairRec& pr, double* rho_me, double* v_me,
                                   cudaStream_t st);
 cudaError_t launch_apply(const SolveParams& P, const double* p, double* ap, cudaStream_t st);
@@ -698,7 +698,6 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMemcpy(multigrid tables)"));
         P.mg = c->d_mg;
         P.mg_omega = 0.8;
-        P.mg32 = o.precision == 1 ? 1 : 0;
     }
 
     // cluster solver candidates: every cluster size, thread count and lane map
@@ -908,7 +907,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         for (const auto& K : c->cands) want = std::max<long long>(want, K.n_clusters);
     } else if (c->per_class) {
         // the classes of a lane run one after another and share its slots
-        e = pair_kernel_occupancy(c->threads, true, c->smem, &bps);
+        e = pair_kernel_occupancy(c->threads, true, false, c->smem, &bps);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
         for (int g = 0; g < c->n_geo; ++g) {
             const exx_ctx::RadiusClass& RC = c->classes[g];
@@ -918,7 +917,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         }
         want = (long long)c->lane_slots[0] + c->lane_slots[1];
     } else {
-        e = pair_kernel_occupancy(c->threads, o.precision == 1 && o.preconditioner == 0, c->smem, &bps);
+        e = pair_kernel_occupancy(c->threads, o.precision == 1, o.preconditioner == 1, c->smem, &bps);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
         if (bps < 1) return bail(fail(c, EXX_ECUDA, "pair kernel does not fit on an SM"));
         int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, bps) : std::min(bps, 2);

@@ -125,7 +125,6 @@ struct SolveParams {
     // multigrid-preconditioned CG (one-CTA FP64 solver): per geometry, NULL = plain CG
     const MGGeo* mg;
     double mg_omega;          // weight of the Jacobi smoothing sweeps
-    int mg32;                 // 1: the V-cycle in FP32 on the normalised residual (the CG stays FP64)
     size_t off_zc, off_tc;    // level-0 cubes (the workspace cube's size): smoothed correction, residual
     size_t off_mgz[kMGMax + 1], off_mgt[kMGMax + 1], off_mgr[kMGMax + 1];  // levels 1..: cubes and right-hand side
     const double* pow_tab;  // [3][2 Rc + 1][8] x^e, y^e, z^e (cluster kernel; global, read-only)

@@ -245,78 +245,64 @@ __device__ void mg_clear(const SolveParams& P, const BallGeo& G, const MGGeo& M,
 }
 
 // PCG on the PE ball with the V-cycle as the preconditioner. On entry: r = rhs,
-// d = 0, rr = ||rhs||^2; p goes to the cube pc (zero off the ball). The CG
-// recurrence and its stop test are FP64; with P.mg32 the V-cycle runs in FP32
-// on r / ||r|| (r32 its compact FP32 copy) and its result is scaled back by
-// ||r||, the preconditioner being linear. Returns the iteration count;
-// rr_out receives the final ||r||^2.
-template <int NT>
+// d = 0, rr = ||rhs||^2; p goes to the cube pc (zero off the ball). Returns
+// the iteration count; rr_out receives the final recursive ||r||^2.
+//   T = double: the FP64 solve (precision 0), every level in FP64.
+//   T = float: the inner solve of the FP64 refinement loop (precision 1): the
+//   recurrence and the V-cycle in FP32 on the normalised residual, the stop
+//   test of the refinement loop on the FP64 residual.
+template <int NT, typename T>
 __device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot,
-                                   double* __restrict__ pc, double* __restrict__ r, double* __restrict__ d,
-                                   double* __restrict__ ap, float* __restrict__ r32, double rr, double target2,
-                                   int max_iter, double (*red)[33], int& flip, double& rr_out) {
+                                   T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d, T* __restrict__ ap, T rr,
+                                   T target2, int max_iter, T (*red)[33], int& flip, T& rr_out) {
     const int* cube = G.pt_cube;
     const int n_pe = G.n_pe, S = P.S;
     const long long S2 = P.S2;
-    const Stencil<double> A = negated(P.st64);
-    const bool f32 = P.mg32 != 0;
-    const double* T0 = reinterpret_cast<const double*>(slot + P.off_tc);
-    const float* T32 = reinterpret_cast<const float*>(slot + P.off_tc);
-    double zs = 1.0;  // scale of the FP32 V-cycle's result
-    // z = M r into the level-0 Tc cube (FP64, or FP32 times zs)
-    auto precondition = [&](double rr_now) {
-        if (f32) {
-            zs = sqrt(rr_now);
-            const double inv = zs > 0.0 ? 1.0 / zs : 0.0;
-            for (int k = threadIdx.x; k < n_pe; k += NT) r32[k] = (float)(r[k] * inv);
-            __syncthreads();
-            mg_vcycle<NT, float>(P, G, M, slot, r32);
-        } else {
-            mg_vcycle<NT, double>(P, G, M, slot, r);
-        }
-    };
-    auto zval = [&](int c) -> double { return f32 ? zs * (double)T32[c] : T0[c]; };
-    precondition(rr);
-    double rz = 0.0;
+    Stencil<T> A;
+    if constexpr (sizeof(T) == 8) A = negated(P.st64);
+    else A = negated(P.st32);
+    const T* Z = reinterpret_cast<const T*>(slot + P.off_tc);  // z = M r (level-0 cube)
+    mg_vcycle<NT, T>(P, G, M, slot, r);
+    T rz = T(0);
     for (int k = threadIdx.x; k < n_pe; k += NT) {
         const int c = cube[k];
-        const double z = zval(c);
+        const T z = Z[c];
         pc[c] = z;
         rz = fma(r[k], z, rz);
     }
-    rz = block_sum<NT, double>(rz, red, flip);
+    rz = block_sum<NT, T>(rz, red, flip);
     int it = 0;
     while (rr > target2 && it < max_iter) {
-        double pap = 0.0;
+        T pap = T(0);
         for (int k = threadIdx.x; k < n_pe; k += NT) {
             const int c = cube[k];
-            const double a = lap19<double>(pc, c, S, S2, A);
+            const T a = lap19<T>(pc, c, S, S2, A);
             ap[k] = a;
             pap = fma(pc[c], a, pap);
         }
-        pap = block_sum<NT, double>(pap, red, flip);
-        const double al = rz / pap;
-        double rrn = 0.0;
+        pap = block_sum<NT, T>(pap, red, flip);
+        const T al = rz / pap;
+        T rrn = T(0);
         for (int k = threadIdx.x; k < n_pe; k += NT) {
             const int c = cube[k];
             d[k] = fma(al, pc[c], d[k]);
-            const double rk = fma(-al, ap[k], r[k]);
+            const T rk = fma(-al, ap[k], r[k]);
             r[k] = rk;
             rrn = fma(rk, rk, rrn);
         }
-        rrn = block_sum<NT, double>(rrn, red, flip);
+        rrn = block_sum<NT, T>(rrn, red, flip);
         ++it;
         rr = rrn;
         if (rrn <= target2 || !(rrn == rrn)) break;
-        precondition(rrn);
-        double rzn = 0.0;
-        for (int k = threadIdx.x; k < n_pe; k += NT) rzn = fma(r[k], zval(cube[k]), rzn);
-        rzn = block_sum<NT, double>(rzn, red, flip);
-        const double be = rzn / rz;
+        mg_vcycle<NT, T>(P, G, M, slot, r);
+        T rzn = T(0);
+        for (int k = threadIdx.x; k < n_pe; k += NT) rzn = fma(r[k], Z[cube[k]], rzn);
+        rzn = block_sum<NT, T>(rzn, red, flip);
+        const T be = rzn / rz;
         rz = rzn;
         for (int k = threadIdx.x; k < n_pe; k += NT) {
             const int c = cube[k];
-            pc[c] = fma(be, pc[c], zval(c));
+            pc[c] = fma(be, pc[c], Z[c]);
         }
         __syncthreads();
     }
@@ -328,7 +314,7 @@ __device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const
 // The persistent pair kernel.
 // --------------------------------------------------------------------------
 template <int NT, bool MIXED, bool MG = false>
-__global__ void __launch_bounds__(NT, MIXED ? 1 : 2) pair_kernel(const __grid_constant__ SolveParams P) {
+__global__ void __launch_bounds__(NT, (MIXED && !MG) ? 1 : 2) pair_kernel(const __grid_constant__ SolveParams P) {
     extern __shared__ double smem[];
     __shared__ double red[2][33];
     __shared__ float red32[2][33];
@@ -408,8 +394,8 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) pair_kernel(const __grid_co
             double rr_fin;
             const double target2 = P.tol * P.tol * bb;
             if (MG && P.mg[pr.geo].L > 0)
-                iters = mg_pcg<NT>(P, G, P.mg[pr.geo], slot, pc, r, d, ap, r32, bb, target2, P.max_iter, red, flip,
-                                   rr_fin);
+                iters = mg_pcg<NT, double>(P, G, P.mg[pr.geo], slot, pc, r, d, ap, bb, target2, P.max_iter, red,
+                                           flip, rr_fin);
             else
                 iters = cg_ball<double, NT>(pc, r, d, ap, cube, n_pe, S, S2, neg64, bb, target2, P.max_iter, red,
                                             flip, rr_fin);
@@ -452,8 +438,12 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) pair_kernel(const __grid_co
                 eta = eta > P.inner_tol ? eta : P.inner_tol;
                 float rr_fin;
                 const int budget = min(P.inner_max_iter, P.max_iter - iters);
-                iters += cg_ball<float, NT>(p32, r32, d32, ap32, cube, n_pe, S, S2, neg32, rr32,
-                                            (float)(eta * eta) * rr32, budget, red32, flip32, rr_fin);
+                if (MG && P.mg[pr.geo].L > 0)
+                    iters += mg_pcg<NT, float>(P, G, P.mg[pr.geo], slot, p32, r32, d32, ap32, rr32,
+                                               (float)(eta * eta) * rr32, budget, red32, flip32, rr_fin);
+                else
+                    iters += cg_ball<float, NT>(p32, r32, d32, ap32, cube, n_pe, S, S2, neg32, rr32,
+                                                (float)(eta * eta) * rr32, budget, red32, flip32, rr_fin);
                 for (int k = threadIdx.x; k < n_pe; k += NT) vc[cube[k]] = fma(rn, (double)d32[k], vc[cube[k]]);
                 ++refines;
                 __syncthreads();
@@ -480,7 +470,7 @@ __global__ void __launch_bounds__(NT, MIXED ? 1 : 2) pair_kernel(const __grid_co
                 else pc[cube[k]] = 0.0;
             }
             if (MG && P.mg[pr.geo].L > 0) {
-                if (P.mg32) mg_clear<NT, float>(P, G, P.mg[pr.geo], slot);
+                if (MIXED) mg_clear<NT, float>(P, G, P.mg[pr.geo], slot);
                 else mg_clear<NT, double>(P, G, P.mg[pr.geo], slot);
             }
         }
@@ -541,8 +531,9 @@ static cudaError_t launch_t(const SolveParams& P, int grid, size_t smem, cudaStr
 }
 
 cudaError_t launch_pair_kernel(const SolveParams& P, int threads, bool mixed, int grid, size_t smem, cudaStream_t st) {
-    if (P.mg) {  // the multigrid-preconditioned CG: FP64 recurrence, FP64 or FP32 V-cycle (512 threads)
-        pair_kernel<512, false, true><<<grid, 512, smem, st>>>(P);
+    if (P.mg) {  // the multigrid-preconditioned CG (512 threads): FP64, or FP32 inside FP64 refinement
+        if (mixed) pair_kernel<512, true, true><<<grid, 512, smem, st>>>(P);
+        else pair_kernel<512, false, true><<<grid, 512, smem, st>>>(P);
         return cudaGetLastError();
     }
     if (threads == 256) return mixed ? launch_t<256, true>(P, grid, smem, st) : launch_t<256, false>(P, grid, smem, st);
@@ -551,9 +542,10 @@ cudaError_t launch_pair_kernel(const SolveParams& P, int threads, bool mixed, in
     return mixed ? launch_t<512, true>(P, grid, smem, st) : launch_t<512, false>(P, grid, smem, st);
 }
 
-cudaError_t pair_kernel_occupancy(int threads, bool mixed, size_t smem, int* blocks_per_sm) {
+cudaError_t pair_kernel_occupancy(int threads, bool mixed, bool mg, size_t smem, int* blocks_per_sm) {
     const void* f;
-    if (threads == 256) f = mixed ? (const void*)pair_kernel<256, true> : (const void*)pair_kernel<256, false>;
+    if (mg) f = mixed ? (const void*)pair_kernel<512, true, true> : (const void*)pair_kernel<512, false, true>;
+    else if (threads == 256) f = mixed ? (const void*)pair_kernel<256, true> : (const void*)pair_kernel<256, false>;
     else if (threads == 1024) f = mixed ? (const void*)pair_kernel<1024, true> : (const void*)pair_kernel<1024, false>;
     else f = mixed ? (const void*)pair_kernel<512, true> : (const void*)pair_kernel<512, false>;
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
