@@ -325,6 +325,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="exx", choices=["exx", "reference"])
     ap.add_argument("--precision", type=int, default=1, help="1: FP32 inner + FP64 refinement, 0: FP64 CG")
+    ap.add_argument("--preconditioner", type=int, default=0,
+                    help="1: multigrid-preconditioned CG on the one-CTA solver, 0: plain CG")
     ap.add_argument("--plain-steps", type=int, default=1, help="timed steps of the plain FP64 CG comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -372,7 +374,7 @@ def main():
     ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=args.precision,
              threads=args.threads, ctas_per_sm=args.ctas_per_sm, solver_kind=args.solver_kind,
              cluster_size=args.cluster_size, lane_map=args.lane_map, update_drop=args.update_drop,
-             autotune=args.autotune)
+             autotune=args.autotune, preconditioner=args.preconditioner)
 
     def barrier():
         if ws > 1:
