@@ -97,14 +97,18 @@ typedef struct {
                           32 in [256, 1024]; the one-CTA solver runs 256, 512
                           or 1024 (other values give 512), the cluster solver
                           only the launch shapes it is built for.               */
-    int ctas_per_sm;   /* resident CTAs per SM, 0 = library choice.              */
+    int ctas_per_sm;   /* resident CTAs per SM, 0 = library choice (the
+                          multigrid CG on clusters: 1 or 2, default 2).         */
     int solver_kind;   /* 0 = library choice; 1 = one CTA per pair with state in
                           global memory; 2 = one thread-block cluster per pair
-                          with the FP32 inner state in shared memory.            */
+                          (plain CG: the FP32 inner state in shared memory;
+                          multigrid CG: all state in the pair's workspace,
+                          shared by the cluster's CTAs).                        */
     int cluster_size;  /* CTAs per cluster for solver_kind 2: 0 = library choice,
                           else 2, 4, 8 or 9 (9 with the non-portable cluster
                           size opt-in; on GB300, 15 clusters of 9 CTAs fit
-                          against 15 of 8).                                      */
+                          against 15 of 8); for the multigrid CG 2, 4, 8
+                          (default) or 16.                                      */
     double update_drop;/* cluster solver: the FP64 residual replaces the FP32 one
                           each time the FP32 residual has dropped by this factor
                           (reliable updates; default 1e-4: tol 1e-8 in two
@@ -158,11 +162,14 @@ typedef struct {
                           2^l delta down to R <= 3, the 19-point stencil on
                           every level, one weighted-Jacobi sweep (weight 0.8)
                           down and up, full-weighting restriction, trilinear
-                          prolongation, the coarsest ball solved exactly. Runs
-                          on the one-CTA solver, not with warm_start. With
-                          precision 0 the PCG and every level are FP64; with
-                          precision 1 each inner solve of the FP64 refinement
-                          loop is this PCG in FP32 (recurrence and V-cycle).
+                          prolongation, the coarsest ball solved exactly. Not
+                          with warm_start. With precision 0 the PCG and every
+                          level are FP64, one CTA per pair; with precision 1
+                          each inner solve of the FP64 refinement loop is this
+                          PCG in FP32 (recurrence and V-cycle), by default on a
+                          cluster of CTAs per pair whose vectors stay in L2
+                          (solver_kind 1: one CTA per pair). A ball of radius
+                          <= 3 has no coarse level: its CG is unpreconditioned.
                           The stop rule is unchanged: ||r|| <= tol ||b||.      */
     int inject_wait_timeout; /* test only (default 0): the next this-many calls
                           of the context each make one extra bounded device wait

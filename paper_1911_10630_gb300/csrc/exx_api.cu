@@ -51,6 +51,9 @@ int cluster_variant_iso(int variant);
 int cluster_variant_syz(int variant);
 int cluster_variant_count();
 int cluster_variant_size(int variant);
+bool mg_cluster_size_ok(int C);
+cudaError_t mg_cluster_prepare(int C, int minb, int* max_clusters);
+cudaError_t launch_cluster_mg(int C, int minb, const SolveParams& P, int n_clusters, cudaStream_t st);
 }  // namespace exx
 
 using namespace exx;
@@ -118,6 +121,9 @@ struct exx_ctx {
     };
     bool per_class = false;
     std::vector<RadiusClass> classes;
+    // the multigrid-preconditioned CG on clusters (preconditioner 1, precision 1):
+    // mg_C CTAs per pair, mg_minb CTAs per SM, up to mg_clusters resident clusters
+    int mg_C = 0, mg_minb = 2, mg_clusters = 0;
     // the classes alternate between the context stream (lane 0) and aux
     // (lane 1), forked and joined inside the graph, so that one class's tail
     // overlaps the next class's work; each lane has its own workspace slots
@@ -429,7 +435,9 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
             o.r_me_nonself < o.r_pe_nonself + 3)
             return fail(nullptr, EXX_EINVAL,
                         "exx_init: radii_mode 2 needs 1 <= r_pe_nonself <= r_pe, r_pe_nonself + 3 <= r_me_nonself <= r_me");
-        if (o.solver_kind == 2) return fail(nullptr, EXX_EINVAL, "exx_init: radii_mode 2 runs on solver_kind 1");
+        if (o.solver_kind == 2 && o.preconditioner != 1)
+            return fail(nullptr, EXX_EINVAL,
+                        "exx_init: radii_mode 2 runs on solver_kind 1 (or on clusters with preconditioner 1)");
     }
     if (o.radii_mode == 1) {
         const int rme_rule = r_pe + std::max(3, (r_pe + 2) / 3);
@@ -452,8 +460,9 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (o.solver_kind == 2 && o.precision != 1)
         return fail(nullptr, EXX_EINVAL, "exx_init: solver_kind 2 (cluster) runs the FP32 inner solver: precision must be 1");
     if (o.cluster_size != 0 && o.cluster_size != 2 && o.cluster_size != 4 && o.cluster_size != 8 &&
-        o.cluster_size != 9)
-        return fail(nullptr, EXX_EINVAL, "exx_init: cluster_size must be 0, 2, 4, 8 or 9");
+        o.cluster_size != 9 && !(o.cluster_size == 16 && o.preconditioner == 1))
+        return fail(nullptr, EXX_EINVAL,
+                    "exx_init: cluster_size must be 0, 2, 4, 8 or 9 (16 with the multigrid CG)");
     if (o.fixed_residual < 0 || o.fixed_residual > 2)
         return fail(nullptr, EXX_EINVAL, "exx_init: fixed_residual must be 0, 1 or 2");
     if (o.deterministic < 0 || o.deterministic > 1)
@@ -461,10 +470,14 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (o.inject_wait_timeout < 0) return fail(nullptr, EXX_EINVAL, "exx_init: inject_wait_timeout must be >= 0");
     if (o.preconditioner < 0 || o.preconditioner > 1)
         return fail(nullptr, EXX_EINVAL, "exx_init: preconditioner must be 0 or 1");
-    if (o.preconditioner == 1 && (o.solver_kind == 2 || o.warm_start != 0))
+    if (o.preconditioner == 1 && o.warm_start != 0)
+        return fail(nullptr, EXX_EINVAL, "exx_init: the multigrid-preconditioned CG takes no warm start");
+    if (o.preconditioner == 1 && o.solver_kind == 2 && o.precision != 1)
         return fail(nullptr, EXX_EINVAL,
-                    "exx_init: the multigrid-preconditioned CG runs on the one-CTA solver (solver_kind 0 or 1, "
-                    "warm_start 0)");
+                    "exx_init: the multigrid-preconditioned CG on clusters (solver_kind 2) needs precision 1");
+    if (o.preconditioner == 1 && o.solver_kind != 1 && o.precision == 1 && o.cluster_size != 0 &&
+        !mg_cluster_size_ok(o.cluster_size))
+        return fail(nullptr, EXX_EINVAL, "exx_init: the multigrid CG on clusters takes cluster_size 2, 4, 8 or 16");
 
     c = new exx_ctx();
     std::memset(&c->stats, 0, sizeof(c->stats));
@@ -894,6 +907,23 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         e = cudaMalloc(&c->d_class, sizeof(int) * 3 * (size_t)c->n_geo);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(radius classes)"));
     }
+    // the multigrid-preconditioned CG on clusters (solver_kind 0 or 2 at precision 1)
+    if (o.preconditioner == 1 && o.precision == 1 && o.solver_kind != 1 && mg_levels > 0) {
+        const int C = o.cluster_size ? o.cluster_size : 8;
+        const int minb = o.ctas_per_sm == 1 ? 1 : 2;
+        int nclu = 0;
+        e = mg_cluster_prepare(C, minb, &nclu);
+        if (e != cudaSuccess || nclu < 1) {
+            (void)cudaGetLastError();
+            if (o.solver_kind == 2)
+                return bail(fail(c, EXX_EINVAL, "exx_init: no cluster of this size can be resident for the multigrid CG"));
+        } else {
+            c->mg_C = C;
+            c->mg_minb = minb;
+            c->mg_clusters = nclu;
+            c->threads = 512;
+        }
+    }
     if (o.warm_start != 0 && !c->use_cluster)
         return bail(fail(c, EXX_EINVAL, "exx_init: warm_start 1 and 2 need the cluster solver, which does not fit these radii"));
     if (c->use_cluster) apply_cand(c, c->cand);
@@ -905,6 +935,8 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
     if (c->use_cluster) {
         want = 0;
         for (const auto& K : c->cands) want = std::max<long long>(want, K.n_clusters);
+    } else if (c->mg_C) {
+        want = c->mg_clusters;
     } else if (c->per_class) {
         // the classes of a lane run one after another and share its slots
         e = pair_kernel_occupancy(c->threads, true, false, c->smem, &bps);
@@ -1014,9 +1046,10 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
 
     c->stats.n_pe = B.n_pe;
     c->stats.n_me = B.n_me;
-    c->stats.solver_kind = (c->use_cluster || c->per_class) ? 2 : 1;
-    c->stats.cluster_size = c->use_cluster ? c->CL.C : 1;
-    c->stats.grid_ctas = c->use_cluster ? c->n_clusters * c->CL.C : c->n_slots;
+    c->stats.solver_kind = (c->use_cluster || c->per_class || c->mg_C) ? 2 : 1;
+    c->stats.cluster_size = c->use_cluster ? c->CL.C : (c->mg_C ? c->mg_C : 1);
+    c->stats.grid_ctas = c->use_cluster ? c->n_clusters * c->CL.C
+                                        : (c->mg_C ? std::min(c->mg_clusters, c->n_slots) * c->mg_C : c->n_slots);
     c->stats.lane_map = c->use_cluster ? c->cands[c->cand].lane_map : 0;
     c->stats.n_candidates = (int)c->cands.size();
     c->stats.threads = c->threads;
@@ -1056,7 +1089,7 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
     P.iters = c->d_iters;
     P.refines = c->d_refines;
     P.dbg_b = nullptr;
-    P.phase_clk = (c->use_cluster || c->per_class) ? c->d_phase : nullptr;
+    P.phase_clk = (c->use_cluster || c->per_class || c->mg_C) ? c->d_phase : nullptr;
     P.test_wait = c->inject_now;
     P.box_org = c->cur_box;
     for (int a = 0; a < 3; ++a) P.bdim[a] = c->cur_bdim[a];
@@ -1112,6 +1145,9 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
         }
     } else if (c->use_cluster)
         CK(launch_cluster_kernel(c->cl_variant, P, c->CL, c->n_clusters, c->smem, st), "cluster pair kernel");
+    else if (c->mg_C)
+        CK(launch_cluster_mg(c->mg_C, c->mg_minb, P, std::min(c->mg_clusters, c->n_slots), st),
+           "cluster multigrid kernel");
     else
         CK(launch_pair_kernel(P, c->threads, c->opt.precision == 1, c->n_slots, c->smem, st), "pair kernel");
     if (P.dfix != 0.0)
@@ -1588,8 +1624,9 @@ extern "C" exx_status exx_get_stats(const exx_ctx* cc, exx_stats* out) {
         // shares of the pair-kernel time (the clusters run side by side)
         const double cyc = (double)ph[0] + (double)ph[1] + (double)ph[2] + (double)ph[3];
         for (int k = 0; k < 4; ++k)
-            c->stats.phase_ms[k] =
-                ((c->use_cluster || c->per_class) && cyc > 0.0) ? c->stats.solve_ms * (double)ph[k] / cyc : 0.0;
+            c->stats.phase_ms[k] = ((c->use_cluster || c->per_class || c->mg_C) && cyc > 0.0)
+                                       ? c->stats.solve_ms * (double)ph[k] / cyc
+                                       : 0.0;
     }
     if (c->per_class) {  // radius classes: the largest cluster and grid of any class
         int cmax = 1, gmax = c->n_slots;

@@ -25,6 +25,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include "exx_mg.cuh"
 #include "exx_phases.cuh"
 
 namespace cg = cooperative_groups;
@@ -1470,6 +1471,282 @@ __global__ void __launch_bounds__(NT, 1) cluster_pair_kernel(const __grid_consta
         inject_wait_timeout(smem_u32(smem) + (uint32_t)cluster_smem_test_offset(CL, MODE, PTS, NT), P.timeouts);
 }
 
+// ---------------------------------------------------------------------------
+// The multigrid-preconditioned CG on a thread-block cluster (precision 1 with
+// preconditioner 1). The C CTAs of a cluster share one pair and keep all its
+// vectors in the cluster's workspace slot. One CTA per pair keeps about 300
+// pairs in flight, whose FP32 vectors (about 2 MB each) are far beyond the
+// 129 MB L2, and waits on DRAM; a cluster per pair keeps the vectors of the
+// pairs in flight in L2. Each CTA sweeps a contiguous range of the PE ball's
+// compact points (the points are ordered plane by plane, so a range is a slab
+// and the stencil's reach into the neighbours' ranges is short); a cluster
+// barrier separates two sweeps whenever the second reads what other CTAs
+// wrote in the first. The V-cycle's level 0 and the restriction to level 1
+// run on the whole cluster, the coarser levels (an eighth of the points and
+// less) on CTA 0 while the others wait. Setup, FP64 residuals, E_ij and the
+// scatter are the cluster solver's phases.
+// ---------------------------------------------------------------------------
+
+// Two FP32 sums over the cluster at once (as cluster_sum).
+template <int NT, int C>
+__device__ __forceinline__ float2 cluster_sum2(float2 v, float2 (*red)[33], int& flip, float2 (*part)[16], int& cflip,
+                                               cg::cluster_group& cl, int rank) {
+    v.x = warp_sum(v.x);
+    v.y = warp_sum(v.y);
+    float2* buf = red[flip];
+    flip ^= 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) buf[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        float2 t = lane < NT / 32 ? buf[lane] : make_float2(0.0f, 0.0f);
+        t.x = warp_sum(t.x);
+        t.y = warp_sum(t.y);
+        if (lane < C) {
+            float2* dst = cl.map_shared_rank(&part[cflip][0], lane);
+            dst[rank] = t;
+        }
+    }
+    cl.sync();
+    float2 s = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+        s.x += part[cflip][r].x;
+        s.y += part[cflip][r].y;
+    }
+    cflip ^= 1;
+    return s;
+}
+
+struct MGSums {
+    float (*red)[33];
+    float (*part)[16];
+    float2 (*red2)[33];
+    float2 (*part2)[16];
+    int flip, cflip, flip2, cflip2;
+};
+
+// The preconditioner z = M r after the sweep that wrote r and the V-cycle's
+// first Jacobi sweep (Z = w D^-1 r on level 0): the rest of the V-cycle, z into
+// the level-0 Tc cube; returns this thread's r.z.
+template <int NT, int C>
+__device__ __noinline__ float cluster_mg_precondition(const SolveParams& P, const BallGeo& G, const MGGeo& M,
+                                                      char* slot, int k0, int k1) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int kb = k0 + (int)threadIdx.x;
+    const float* r = reinterpret_cast<const float*>(slot + P.off_r32);
+    const MGView<float> v0 = mg_view<float>(P, G, M, slot, 0, r);
+    const int n1 = M.lv[1].n;
+    cl.sync();  // Z
+    mg_residual(v0, kb, k1, NT);
+    cl.sync();  // Tc
+    mg_restrict(v0, M.lv[1], n1 * rank / C + (int)threadIdx.x, n1 * (rank + 1) / C, NT);
+    cl.sync();  // level-1 right-hand side
+    if (rank == 0) mg_vcycle<NT, float>(P, G, M, slot, r, 1);
+    cl.sync();  // level-1 correction
+    const MGView<float> v1 = mg_view<float>(P, G, M, slot, 1, r);
+    mg_prolong(v0, v1, M.L == 1 ? v1.Z : v1.Tc, kb, k1, NT);
+    cl.sync();  // Z
+    return mg_smooth(v0, (float)P.mg_omega, kb, k1, NT);
+}
+
+// One inner solve of the refinement loop: the FP32 PCG for A d = r64 / rn on
+// the CTA's points [k0, k1), from d = 0, until r.r <= eta2 (r0.r0) or after
+// max_iter iterations; d goes to the slot's FP32 d. Returns the iterations.
+// The stop test comes after the preconditioner (its r.r is summed with r.z),
+// so an iteration has one sum fewer and a solve one V-cycle more. Without
+// coarse levels (a ball of radius <= 3) the preconditioner is the identity.
+template <int NT, int C>
+__device__ __noinline__ int cluster_mg_pcg(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot, int k0,
+                                           int k1, double inv_rn, float eta2, int max_iter, MGSums& sm) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int kb = k0 + (int)threadIdx.x;
+    const int* cube = G.pt_cube;
+    const double* r64 = reinterpret_cast<const double*>(slot + P.off_r);
+    float* pc = reinterpret_cast<float*>(slot + P.off_p32);
+    float* r = reinterpret_cast<float*>(slot + P.off_r32);
+    float* d = reinterpret_cast<float*>(slot + P.off_d32);
+    float* ap = reinterpret_cast<float*>(slot + P.off_ap32);
+    float* Z0 = reinterpret_cast<float*>(slot + P.off_zc);
+    float* T0 = reinterpret_cast<float*>(slot + P.off_tc);  // z
+    const int S = P.S;
+    const long long S2 = P.S2;
+    const Stencil<float> A = negated(P.st32);
+    const bool mg = M.L > 0;
+    const float wd = (float)P.mg_omega / A.c0;
+    float* zw = mg ? Z0 : T0;  // the sweep that writes r writes Z = wd r, or z = r
+    const float zs = mg ? wd : 1.0f;
+    float rr_part = 0.0f;
+    for (int k = kb; k < k1; k += NT) {
+        const float rk = (float)(r64[k] * inv_rn);
+        r[k] = rk;
+        d[k] = 0.0f;
+        zw[cube[k]] = zs * rk;
+        rr_part = fmaf(rk, rk, rr_part);
+    }
+    float rz_part = mg ? cluster_mg_precondition<NT, C>(P, G, M, slot, k0, k1) : rr_part;
+    float2 s = cluster_sum2<NT, C>(make_float2(rz_part, rr_part), sm.red2, sm.flip2, sm.part2, sm.cflip2, cl, rank);
+    float rz = s.x;
+    const float target = eta2 * s.y;
+    for (int k = kb; k < k1; k += NT) pc[cube[k]] = T0[cube[k]];
+    int it = 0;
+    while (it < max_iter) {
+        cl.sync();  // p
+        float pap = 0.0f;
+        for (int k = kb; k < k1; k += NT) {
+            const int c = cube[k];
+            const float a = lap19<float>(pc, c, S, S2, A);
+            ap[k] = a;
+            pap = fmaf(pc[c], a, pap);
+        }
+        pap = cluster_sum<NT, C, float>(pap, sm.red, sm.flip, sm.part, sm.cflip, cl, rank);
+        const float al = rz / pap;
+        rr_part = 0.0f;
+        for (int k = kb; k < k1; k += NT) {
+            const int c = cube[k];
+            d[k] = fmaf(al, pc[c], d[k]);
+            const float rk = fmaf(-al, ap[k], r[k]);
+            r[k] = rk;
+            rr_part = fmaf(rk, rk, rr_part);
+            zw[c] = zs * rk;
+        }
+        ++it;
+        rz_part = mg ? cluster_mg_precondition<NT, C>(P, G, M, slot, k0, k1) : rr_part;
+        s = cluster_sum2<NT, C>(make_float2(rz_part, rr_part), sm.red2, sm.flip2, sm.part2, sm.cflip2, cl, rank);
+        if (s.y <= target || !(s.y == s.y)) break;
+        const float be = s.x / rz;
+        rz = s.x;
+        for (int k = kb; k < k1; k += NT) {
+            const int c = cube[k];
+            pc[c] = fmaf(be, pc[c], T0[c]);
+        }
+    }
+    return it;
+}
+
+template <int NT, int C, int MINB>
+__global__ void __launch_bounds__(NT, MINB) cluster_mg_kernel(const __grid_constant__ SolveParams P) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    __shared__ double red[2][33];
+    __shared__ double part[2][16];
+    __shared__ float red32[2][33];
+    __shared__ float part32[2][16];
+    __shared__ float2 red2[2][33];
+    __shared__ float2 part2[2][16];
+    __shared__ double s_M[kNMono], s_T[kNMono];
+    __shared__ int s_item;
+    int flip = 0, cflip = 0;
+    MGSums sm{red32, part32, red2, part2, 0, 0, 0, 0};
+
+    const int Rc = P.Rc;
+    const double* xp = P.pow_tab;
+    const double* yp = xp + (2 * Rc + 1) * 8;
+    const double* zp = yp + (2 * Rc + 1) * 8;
+    const int cid = blockIdx.x / C;
+    char* slot = P.ws + (size_t)cid * P.slot_bytes;
+    double* vc = reinterpret_cast<double*>(slot + P.off_vcube);
+    double* rho = reinterpret_cast<double*>(slot + P.off_rho);
+    double* r64 = reinterpret_cast<double*>(slot + P.off_r);
+    double* rowS = reinterpret_cast<double*>(slot + P.off_rows);
+    double* sYc = reinterpret_cast<double*>(slot + P.off_sy);
+    float* d32 = reinterpret_cast<float*>(slot + P.off_d32);
+    float* p32 = reinterpret_cast<float*>(slot + P.off_p32);
+    double* U64 = reinterpret_cast<double*>(slot + P.off_ush);
+    float* U32 = reinterpret_cast<float*>(U64 + (size_t)kNU * P.geos[P.n_geo - 1].n_rows_me);
+    const int t = threadIdx.x;
+    const int gt = rank * NT + t, gn = C * NT;
+    const int np = *P.n_pair;
+
+    for (;;) {
+        if (rank == 0 && t == 0) {
+            const int it = atomicAdd(P.queue, 1);
+            for (int r = 0; r < C; ++r) *cl.map_shared_rank(&s_item, r) = it;
+        }
+        cl.sync();
+        const int item = s_item;
+        if (item >= np) break;
+        const int pidx = P.order ? P.order[(P.item_base ? *P.item_base : 0) + item] : item;
+        const PairRec pr = P.pairs[pidx];
+        const BallGeo G = P.geos[pr.geo];
+        const MGGeo& M = P.mg[pr.geo];
+        const int* cube = G.pt_cube;
+        const int n_pe = G.n_pe;
+        const int k0 = n_pe * rank / C, k1 = n_pe * (rank + 1) / C;
+        const int npl = 2 * G.r_pe + 1;
+        const int pl0 = npl * rank / C, pl1 = npl * (rank + 1) / C;
+        const bool clk = P.phase_clk && rank == 0 && t == 0;
+        const long long t0 = clk ? clock64() : 0;
+        long long tr = 0;
+
+        // gather, multipoles, shell potential (FP64, spread over the cluster)
+        gather_rho(P, G, pr, rho, vc, gt, gn);
+        cl.sync();
+        moment_rows(P, G, rho, rowS, zp, gt, gn);
+        cl.sync();
+        moment_finish_cluster<NT>(P, G, rowS, xp, yp, sYc, pl0, pl1 - pl0, s_M, s_T, cl);
+        shell_rows(P, G, xp, yp, s_T, U64, U32, gt, gn);
+        cl.sync();
+        shell_points<true>(P, G, vc, U64, U32, G.sh_near, G.n_near, gt, gn);
+        shell_points<false>(P, G, vc, U64, U32, G.sh_far, G.n_far, gt, gn);
+        cl.sync();
+        const long long t1 = clk ? clock64() : 0;
+
+        // FP64 refinement: r = 4 pi rho + lap v, then the FP32 PCG on r / ||r||
+        int iters = 0, refines = 0;
+        bool conv = true;
+        double bb = -1.0, rn_prev = 1e300;
+        for (;;) {
+            const long long tu = clk ? clock64() : 0;
+            double acc = cta_residual(P, cube, rho, vc, r64, k0, k1, NT, bb < 0.0 && P.dbg_b != nullptr);
+            const double rn2 = cluster_sum<NT, C, double>(acc, red, flip, part, cflip, cl, rank);
+            if (clk) tr += clock64() - tu;
+            if (bb < 0.0) bb = rn2;
+            if (rn2 <= P.tol * P.tol * bb) break;
+            const double rn = sqrt(rn2);
+            if (refines >= P.max_refine || iters >= P.max_iter || !(rn < rn_prev)) {
+                conv = false;
+                break;
+            }
+            rn_prev = rn;
+            double eta = 0.3 * P.tol * sqrt(bb) / rn;
+            eta = eta > P.inner_tol ? eta : P.inner_tol;
+            const int budget = min(P.inner_max_iter, P.max_iter - iters);
+            iters += cluster_mg_pcg<NT, C>(P, G, M, slot, k0, k1, 1.0 / rn, (float)(eta * eta), budget, sm);
+            for (int k = k0 + t; k < k1; k += NT) vc[cube[k]] = fma(rn, (double)d32[k], vc[cube[k]]);
+            ++refines;
+            cl.sync();  // v
+        }
+        const long long t2 = clk ? clock64() : 0;
+
+        // E_ij and the D_xx scatter
+        double e = cta_energy(cube, rho, vc, k0, k1, NT);
+        e = cluster_sum<NT, C, double>(e, red, flip, part, cflip, cl, rank);
+        if (rank == 0 && t == 0) {
+            P.e_pair[pidx] = e * P.dV;
+            P.iters[pidx] = iters;
+            if (P.refines) P.refines[pidx] = refines;
+            if (!conv) atomicAdd(P.nonconv, 1);
+        }
+        scatter_dxx(P, G, pr, vc, gt, gn);
+        if (P.n_geo > 1) {
+            // the next pair may have other balls: every cube must be zero off them
+            for (int k = k0 + t; k < k1; k += NT) p32[cube[k]] = 0.0f;
+            mg_clear<float>(P, G, M, slot, k0 + t, k1, rank == 0 ? t : -1, NT);
+        }
+        cl.sync();
+        if (clk) {
+            const long long t3 = clock64();
+            atomicAdd(P.phase_clk + 0, (unsigned long long)(t1 - t0));
+            atomicAdd(P.phase_clk + 1, (unsigned long long)tr);
+            atomicAdd(P.phase_clk + 2, (unsigned long long)(t2 - t1 - tr));
+            atomicAdd(P.phase_clk + 3, (unsigned long long)(t3 - t2));
+        }
+    }
+}
+
 // ---- host side ----
 cudaError_t set_multipole_const_cluster(const MultipoleConst& mc) {
     return cudaMemcpyToSymbol(c_mp, &mc, sizeof(MultipoleConst));
@@ -1613,5 +1890,74 @@ size_t cluster_kernel_smem(int Rc, const ClusterLayout& CL, int variant) {
     const ClusterVariant& K = kVariants[variant];
     return cluster_smem_test_offset(CL, K.mode, K.pts, K.nt) + 8;
 }
+
+// The cluster multigrid kernel: 512 threads per CTA, C = 2, 4, 8 or 16 CTAs per
+// pair, built for one (128 registers) or two (64 registers) CTAs per SM.
+template <int C, int MINB>
+static cudaError_t mg_cluster_cfg(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int n_clusters,
+                                  cudaStream_t st) {
+    cfg = {};
+    cfg.gridDim = dim3(n_clusters * C, 1, 1);
+    cfg.blockDim = dim3(512, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (C > 8)
+        return cudaFuncSetAttribute(cluster_mg_kernel<512, C, MINB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return cudaSuccess;
+}
+
+template <int C, int MINB>
+static cudaError_t mg_cluster_prepare_t(int* max_clusters) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    cudaError_t e = mg_cluster_cfg<C, MINB>(cfg, attr, 1, nullptr);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveClusters(max_clusters, cluster_mg_kernel<512, C, MINB>, &cfg);
+}
+
+template <int C, int MINB>
+static cudaError_t mg_cluster_launch_t(const SolveParams& P, int n_clusters, cudaStream_t st) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    cudaError_t e = mg_cluster_cfg<C, MINB>(cfg, attr, n_clusters, st);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, cluster_mg_kernel<512, C, MINB>, P);
+}
+
+bool mg_cluster_size_ok(int C) { return C == 2 || C == 4 || C == 8 || C == 16; }
+
+#define EXX_MG_SWITCH(CALL2, CALL1)                          \
+    switch (C * 4 + (minb == 1 ? 1 : 2)) {                   \
+        case 2 * 4 + 2: return CALL2(2);                     \
+        case 4 * 4 + 2: return CALL2(4);                     \
+        case 8 * 4 + 2: return CALL2(8);                     \
+        case 16 * 4 + 2: return CALL2(16);                   \
+        case 8 * 4 + 1: return CALL1(8);                     \
+        case 16 * 4 + 1: return CALL1(16);                   \
+        default: return cudaErrorInvalidValue;               \
+    }
+
+cudaError_t mg_cluster_prepare(int C, int minb, int* max_clusters) {
+#define P2(c) mg_cluster_prepare_t<c, 2>(max_clusters)
+#define P1(c) mg_cluster_prepare_t<c, 1>(max_clusters)
+    EXX_MG_SWITCH(P2, P1)
+#undef P2
+#undef P1
+}
+
+cudaError_t launch_cluster_mg(int C, int minb, const SolveParams& P, int n_clusters, cudaStream_t st) {
+#define L2(c) mg_cluster_launch_t<c, 2>(P, n_clusters, st)
+#define L1(c) mg_cluster_launch_t<c, 1>(P, n_clusters, st)
+    EXX_MG_SWITCH(L2, L1)
+#undef L2
+#undef L1
+}
+#undef EXX_MG_SWITCH
 
 }  // namespace exx

@@ -23,7 +23,7 @@
 // needs no bounds checks; the other CG vectors are compact over the PE ball.
 #include <cuda_runtime.h>
 
-#include "exx_phases.cuh"
+#include "exx_mg.cuh"
 
 namespace exx {
 
@@ -73,175 +73,6 @@ __device__ int cg_ball(T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d,
     }
     rr_out = rr;
     return it;
-}
-
-// --------------------------------------------------------------------------
-// Multigrid-preconditioned CG (FP64, one CTA per pair). The preconditioner is
-// one symmetric V-cycle of the geometric hierarchy of MGGeo: on each level a
-// weighted-Jacobi sweep from zero, the residual, full-weighting restriction
-// (R = P^T / 8) down to the coarsest ball, which is solved with its dense
-// inverse, then trilinear prolongation (P) and one more Jacobi sweep on the
-// way up. Every level's operator is the 19-point stencil of Eq. d2_1 at the
-// level's spacing with zero outside its ball, so the V-cycle is a fixed
-// symmetric positive definite operator and the CG stays a CG. Vectors that a
-// stencil or a transfer reads live in zero-padded cubes of the workspace slot.
-// --------------------------------------------------------------------------
-template <typename T>
-struct MGView {
-    const int* cube;
-    const int* off;
-    int n, S, c;       // points, cube side, cube centre
-    long long S2;
-    T* Z;              // smoothed correction (cube)
-    T* Tc;             // residual, then the post-smoothed correction (cube)
-    const T* rhs;      // right-hand side (compact)
-    T* rnext;          // the next level's right-hand side (compact), NULL on the coarsest
-    Stencil<T> A;      // -lap at the level's spacing
-};
-
-template <typename T>
-__device__ __forceinline__ long long mg_idx(const MGView<T>& v, int x, int y, int z) {
-    return ((long long)(x + v.c) * v.S + (y + v.c)) * v.S + (z + v.c);
-}
-
-// z of level 0 (in its Tc cube) from the right-hand side r0 (compact): the
-// down and up halves of the V-cycle, in T (FP64, or FP32 on a normalised r0).
-template <int NT, typename T>
-__device__ __noinline__ void mg_vcycle(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot,
-                                       const T* __restrict__ r0) {
-    const T w = (T)P.mg_omega;
-    auto view = [&](int l) {
-        MGView<T> v;
-        Stencil<T> base;
-        if constexpr (sizeof(T) == 8) base = negated(P.st64);
-        else base = negated(P.st32);
-        if (l == 0) {
-            v.cube = G.pt_cube;
-            v.off = G.pt_off;
-            v.n = G.n_pe;
-            v.S = P.S;
-            v.c = P.Rc;
-            v.S2 = P.S2;
-            v.Z = reinterpret_cast<T*>(slot + P.off_zc);
-            v.Tc = reinterpret_cast<T*>(slot + P.off_tc);
-            v.rhs = r0;
-            v.A = base;
-        } else {
-            const MGLevel& lv = M.lv[l];
-            v.cube = lv.cube;
-            v.off = lv.off;
-            v.n = lv.n;
-            v.S = lv.side;
-            v.c = lv.R + 3;
-            v.S2 = (long long)lv.side * lv.side;
-            v.Z = reinterpret_cast<T*>(slot + P.off_mgz[l]);
-            v.Tc = reinterpret_cast<T*>(slot + P.off_mgt[l]);
-            v.rhs = reinterpret_cast<const T*>(slot + P.off_mgr[l]);
-            const T sc = (T)ldexp(1.0, -2 * l);  // spacing 2^l delta
-            v.A = base;
-            v.A.c0 *= sc;
-            for (int q = 0; q < 3; ++q) {
-                v.A.cx[q] *= sc;
-                v.A.cy[q] *= sc;
-                v.A.cz[q] *= sc;
-            }
-        }
-        v.rnext = l < M.L ? reinterpret_cast<T*>(slot + P.off_mgr[l + 1]) : nullptr;
-        return v;
-    };
-    // down: Jacobi from zero, residual, restriction
-    for (int l = 0; l < M.L; ++l) {
-        const MGView<T> v = view(l);
-        const T wd = w / v.A.c0;
-        for (int k = threadIdx.x; k < v.n; k += NT) v.Z[v.cube[k]] = wd * v.rhs[k];
-        __syncthreads();
-        for (int k = threadIdx.x; k < v.n; k += NT) {
-            const int c = v.cube[k];
-            v.Tc[c] = v.rhs[k] - lap19<T>(v.Z, c, v.S, v.S2, v.A);
-        }
-        __syncthreads();
-        const MGLevel& cl = M.lv[l + 1];
-        for (int k = threadIdx.x; k < cl.n; k += NT) {
-            const int pk = cl.off[k];
-            const int X = 2 * off_x(pk), Y = 2 * off_y(pk), Z = 2 * off_z(pk);
-            T acc = T(0);
-#pragma unroll
-            for (int ex = -1; ex <= 1; ++ex)
-#pragma unroll
-                for (int ey = -1; ey <= 1; ++ey)
-#pragma unroll
-                    for (int ez = -1; ez <= 1; ++ez) {
-                        const T wt = (ex ? T(0.5) : T(1)) * (ey ? T(0.5) : T(1)) * (ez ? T(0.5) : T(1));
-                        acc = fma(wt, v.Tc[mg_idx(v, X + ex, Y + ey, Z + ez)], acc);
-                    }
-            v.rnext[k] = T(0.125) * acc;
-        }
-        __syncthreads();
-    }
-    // the coarsest level: its dense inverse
-    {
-        const MGView<T> v = view(M.L);
-        const T* minv;
-        if constexpr (sizeof(T) == 8) minv = M.minv;
-        else minv = M.minv32;
-        for (int k = threadIdx.x; k < v.n; k += NT) {
-            const T* row = minv + (size_t)k * v.n;
-            T acc = T(0);
-            for (int j = 0; j < v.n; ++j) acc = fma(row[j], v.rhs[j], acc);
-            v.Z[v.cube[k]] = acc;
-        }
-        __syncthreads();
-    }
-    // up: prolongation of the coarser correction, then a Jacobi sweep into Tc
-    for (int l = M.L - 1; l >= 0; --l) {
-        const MGView<T> v = view(l), vc = view(l + 1);
-        const T* zc = (l + 1 == M.L) ? vc.Z : vc.Tc;
-        for (int k = threadIdx.x; k < v.n; k += NT) {
-            const int pk = v.off[k];
-            const int o[3] = {off_x(pk), off_y(pk), off_z(pk)};
-            int lo[3], hi[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                lo[a] = (o[a] - (o[a] & 1)) / 2;  // floor(o / 2)
-                hi[a] = lo[a] + (o[a] & 1);
-            }
-            T acc = T(0);
-#pragma unroll
-            for (int cx = 0; cx < 2; ++cx)
-#pragma unroll
-                for (int cy = 0; cy < 2; ++cy)
-#pragma unroll
-                    for (int cz = 0; cz < 2; ++cz) {
-                        if ((cx && hi[0] == lo[0]) || (cy && hi[1] == lo[1]) || (cz && hi[2] == lo[2])) continue;
-                        const T wt = (hi[0] != lo[0] ? T(0.5) : T(1)) * (hi[1] != lo[1] ? T(0.5) : T(1)) *
-                                     (hi[2] != lo[2] ? T(0.5) : T(1));
-                        acc = fma(wt, zc[mg_idx(vc, cx ? hi[0] : lo[0], cy ? hi[1] : lo[1], cz ? hi[2] : lo[2])],
-                                  acc);
-                    }
-            v.Z[v.cube[k]] += acc;
-        }
-        __syncthreads();
-        const T wd = w / v.A.c0;
-        for (int k = threadIdx.x; k < v.n; k += NT) {
-            const int c = v.cube[k];
-            v.Tc[c] = fma(wd, v.rhs[k] - lap19<T>(v.Z, c, v.S, v.S2, v.A), v.Z[c]);
-        }
-        __syncthreads();
-    }
-}
-
-// Clears what a pair wrote into the multigrid cubes (per-pair radii: the next
-// pair's balls may have other sizes, and every cube must be zero off its ball).
-template <int NT, typename T>
-__device__ void mg_clear(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot) {
-    T* Z0 = reinterpret_cast<T*>(slot + P.off_zc);
-    T* T0 = reinterpret_cast<T*>(slot + P.off_tc);
-    for (int k = threadIdx.x; k < G.n_pe; k += NT) Z0[G.pt_cube[k]] = T0[G.pt_cube[k]] = T(0);
-    for (int l = 1; l <= M.L; ++l) {
-        T* Z = reinterpret_cast<T*>(slot + P.off_mgz[l]);
-        T* Tc = reinterpret_cast<T*>(slot + P.off_mgt[l]);
-        for (int k = threadIdx.x; k < M.lv[l].n; k += NT) Z[M.lv[l].cube[k]] = Tc[M.lv[l].cube[k]] = T(0);
-    }
 }
 
 // PCG on the PE ball with the V-cycle as the preconditioner. On entry: r = rhs,
@@ -470,8 +301,9 @@ __global__ void __launch_bounds__(NT, (MIXED && !MG) ? 1 : 2) pair_kernel(const 
                 else pc[cube[k]] = 0.0;
             }
             if (MG && P.mg[pr.geo].L > 0) {
-                if (MIXED) mg_clear<NT, float>(P, G, P.mg[pr.geo], slot);
-                else mg_clear<NT, double>(P, G, P.mg[pr.geo], slot);
+                const int t = threadIdx.x;
+                if (MIXED) mg_clear<float>(P, G, P.mg[pr.geo], slot, t, n_pe, t, NT);
+                else mg_clear<double>(P, G, P.mg[pr.geo], slot, t, n_pe, t, NT);
             }
         }
         __syncthreads();

@@ -121,8 +121,20 @@ def test_init_rejects_bad_options(lib):
     assert st == -1 and "preconditioner" in lib.exx_last_error(None).decode()
     o = lib.exx_default_options()
     o.preconditioner = 1
+    o.precision = 0
+    o.solver_kind = 2  # the multigrid CG on clusters is FP32 inside FP64 refinement
+    st, ctx = _init(lib, opt=o)
+    assert st == -1 and "precision" in lib.exx_last_error(None).decode()
+    o = lib.exx_default_options()
+    o.preconditioner = 1
     o.precision = 1
-    o.solver_kind = 2  # the multigrid-preconditioned CG is the one-CTA solver's
+    o.cluster_size = 9  # cluster sizes of the multigrid CG: 2, 4, 8, 16
+    st, ctx = _init(lib, opt=o)
+    assert st == -1 and "multigrid" in lib.exx_last_error(None).decode()
+    o = lib.exx_default_options()
+    o.preconditioner = 1
+    o.precision = 1
+    o.warm_start = 1
     st, ctx = _init(lib, opt=o)
     assert st == -1 and "multigrid" in lib.exx_last_error(None).decode()
     o = lib.exx_default_options()

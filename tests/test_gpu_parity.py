@@ -415,19 +415,35 @@ def test_warm_start_from_previous_step(torch):
 
 
 # --------------------------------------------------------------------------
-# Multigrid-preconditioned CG (preconditioner 1, FP64, one CTA per pair)
+# Multigrid-preconditioned CG (preconditioner 1): FP64 on one CTA per pair;
+# FP32 inside the FP64 refinement on one CTA per pair (solver_kind 1) or on a
+# cluster of C CTAs per pair (solver_kind 0 or 2), one or two CTAs per SM
 # --------------------------------------------------------------------------
+MG_FORMS = [dict(precision=0), dict(precision=1, solver_kind=1), dict(precision=1),
+            dict(precision=1, solver_kind=2, cluster_size=2), dict(precision=1, solver_kind=2, cluster_size=4),
+            dict(precision=1, solver_kind=2, cluster_size=16),
+            dict(precision=1, solver_kind=2, cluster_size=8, ctas_per_sm=1)]
+MG_IDS = ["fp64", "fp32-cta", "fp32-c8", "fp32-c2", "fp32-c4", "fp32-c16", "fp32-c8-1sm"]
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_multigrid_pcg_meets_the_gates_in_far_fewer_iterations(torch, cfg0, precision):
+
+def _mg_form_check(out, form):
+    if form.get("solver_kind") == 1 or form["precision"] == 0:
+        assert out["stats"]["solver_kind"] == 1
+    else:
+        assert out["stats"]["solver_kind"] == 2
+        assert out["stats"]["cluster_size"] == form.get("cluster_size", 8)
+
+
+@pytest.mark.parametrize("form", MG_FORMS, ids=MG_IDS)
+def test_multigrid_pcg_meets_the_gates_in_far_fewer_iterations(torch, cfg0, form):
     """Config 0 (R_PE 16 / R_ME 20, tol 1e-10; levels 16, 8, 4, 2): the same
     energies and forces as the oracle under the gates, every pair's E_ij to
-    the solve's tolerance, in a small fraction of the plain CG's iterations;
-    precision 1 runs the V-cycle in FP32 inside the FP64 CG."""
+    the solve's tolerance, in a small fraction of the plain CG's iterations."""
     w, phi, ref = cfg0
     plain = run_gpu(w, phi, torch=torch, precision=0)
-    mg = run_gpu(w, phi, torch=torch, precision=precision, preconditioner=1)
-    assert mg["stats"]["n_nonconv"] == 0 and mg["stats"]["solver_kind"] == 1
+    mg = run_gpu(w, phi, torch=torch, preconditioner=1, **form)
+    _mg_form_check(mg, form)
+    assert mg["stats"]["n_nonconv"] == 0
     _pairs_equal(mg["pairs"], ref["pairs"])
     assert abs(mg["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
     assert d_maxrel(mg["D"], ref["D"]) <= D_GATE_MAXREL
@@ -436,8 +452,8 @@ def test_multigrid_pcg_meets_the_gates_in_far_fewer_iterations(torch, cfg0, prec
     assert it_mg < 0.25 * it_plain, (it_mg, it_plain)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_multigrid_pcg_per_pair_radii(torch, precision):
+@pytest.mark.parametrize("form", MG_FORMS[:4], ids=MG_IDS[:4])
+def test_multigrid_pcg_per_pair_radii(torch, form):
     """Per-pair radii (R_PE 12..16): one hierarchy per ball (levels 12, 6, 3 up to
     16, 8, 4, 2) in the same workspace slots, cleared between pairs."""
     w = synth.tiny(seed=8, n=6, npts=48, length=9.6, r_pe=16, r_me=22, alpha=(0.5, 2.0), tol=1e-10, min_sep=1.2)
@@ -445,7 +461,8 @@ def test_multigrid_pcg_per_pair_radii(torch, precision):
     phi = w.orbitals()
     ref = oracle.exx_workload(w, tol=1e-13, orbitals=phi)
     assert len(set(ref["pairs"][3])) >= 3
-    out = run_gpu(w, phi, torch=torch, precision=precision, preconditioner=1)
+    out = run_gpu(w, phi, torch=torch, preconditioner=1, **form)
+    _mg_form_check(out, form)
     _pairs_radii_equal(out["pairs"], ref["pairs"])
     assert out["stats"]["n_nonconv"] == 0
     assert abs(out["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
@@ -453,8 +470,8 @@ def test_multigrid_pcg_per_pair_radii(torch, precision):
     np.testing.assert_allclose(out["pairs"]["e_pair"], ref["E_pair"], rtol=1e-7, atol=1e-12)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_multigrid_pcg_anisotropic_ragged(torch, precision):
+@pytest.mark.parametrize("form", MG_FORMS[:4], ids=MG_IDS[:4])
+def test_multigrid_pcg_anisotropic_ragged(torch, form):
     """Non-cubic grid and cell (each level's stencil with its own spacings),
     small balls (levels 5, 3), pairs across faces."""
     w = synth.tiny(seed=3, n=6, npts=28, length=6.5, r_pe=5, r_me=9, r_pair=3.0, tol=1e-10)
@@ -465,14 +482,45 @@ def test_multigrid_pcg_anisotropic_ragged(torch, precision):
     w.centers[1] = [6.3, 3.2, 0.2]
     phi = w.orbitals()
     ref = oracle.exx_workload(w, tol=1e-13, orbitals=phi)
-    out = run_gpu(w, phi, torch=torch, precision=precision, preconditioner=1)
+    out = run_gpu(w, phi, torch=torch, preconditioner=1, **form)
+    _mg_form_check(out, form)
     _pairs_equal(out["pairs"], ref["pairs"])
     assert abs(out["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
     assert d_maxrel(out["D"], ref["D"]) <= D_GATE_MAXREL
 
 
-def test_multigrid_runs_on_the_one_cta_solver(torch):
+def test_multigrid_smallest_balls_on_clusters(torch):
+    """Self pairs on R_PE/R_ME = 8/12 (levels 8, 4, 2), non-self pairs on 3/7: a
+    ball of radius 3 has no coarse level, so the cluster PCG runs those pairs
+    with the identity preconditioner, and its 7 planes are fewer than the 8
+    CTAs. With every ball of radius 3 there is no hierarchy at all and the
+    one-CTA solver takes the call."""
+    w = synth.tiny(seed=9, n=5, npts=32, length=8.0, r_pe=8, r_me=12, tol=1e-10)
+    phi = w.orbitals()
+    pi, pj, g = oracle.pair_list(w.centers, w.cell, w.grid, w.r_pair)
+    self_ = pi == pj
+    rpe = np.where(self_, 8, 3).astype(np.int32)
+    rme = np.where(self_, 12, 7).astype(np.int32)
+    ref = oracle.exx(w.cell, w.grid, phi, (pi, pj, g, rpe, rme), 8, 12, w.l_max, tol=1e-13, want_d=True)
+    out = run_gpu(w, phi, torch=torch, precision=1, preconditioner=1, solver_kind=2, cluster_size=8,
+                  radii_mode=2, r_pe_nonself=3, r_me_nonself=7)
+    assert out["stats"]["solver_kind"] == 2 and out["stats"]["n_nonconv"] == 0
+    _pairs_radii_equal(out["pairs"], (pi, pj, g, rpe, rme))
+    assert abs(out["E_xx"] - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
+    assert d_maxrel(out["D"], ref["D"]) <= D_GATE_MAXREL
+    np.testing.assert_allclose(out["pairs"]["e_pair"], ref["E_pair"], rtol=1e-7, atol=1e-12)
+    w3 = synth.tiny(seed=9, n=4, npts=20, length=5.0, r_pe=3, r_me=7, tol=1e-10)
+    phi3 = w3.orbitals()
+    ref3 = oracle.exx_workload(w3, tol=1e-13, orbitals=phi3)
+    out3 = run_gpu(w3, phi3, torch=torch, precision=1, preconditioner=1)
+    assert out3["stats"]["solver_kind"] == 1 and out3["stats"]["n_nonconv"] == 0
+    assert abs(out3["E_xx"] - ref3["E_xx"]) / w3.n <= E_GATE_PER_ORBITAL
+
+
+def test_multigrid_option_errors(torch):
     from paper_1911_10630_gb300.exx import Exx, ExxError
     w = synth.config0()
+    with pytest.raises(ExxError, match="precision"):
+        Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=0, preconditioner=1, solver_kind=2)
     with pytest.raises(ExxError, match="multigrid"):
-        Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=1, preconditioner=1, solver_kind=2)
+        Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=1, preconditioner=1, cluster_size=9)
