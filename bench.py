@@ -37,6 +37,12 @@ SMEM_BYTES_PER_CLK_SM = 128  # shared-memory bandwidth of one SM (32 banks x 4 B
 # loads of 16 bytes per quad of 4 points plus the store of p (context only;
 # the roofline's algorithmic bytes are the CG state's)
 SMEM_MODEL_BYTES_PER_POINT_ITER = 15 * 16 / 4 + 4
+# The multigrid PCG's algorithmic bytes per fine-level point and iteration
+# (FP32, every vector read or written once per sweep): A p (8), the d and r
+# updates (24), the V-cycle's level-0 sweeps: Jacobi (8), residual (12),
+# restriction (4), prolongation (8), smoothing (12); r.z (8) and the p update
+# (12): 96 B; the coarse levels add their share of the V-cycle (44 B x 1/7)
+MG_BYTES_PER_POINT_ITER = 96 + 44 / 7
 
 
 def _peaks():
@@ -52,7 +58,7 @@ def _peaks():
 # the sources that decide the pair kernels' code and launch layout (DRAM
 # traffic): a change to any of them invalidates the committed ncu figures
 KERNEL_SOURCES = ("exx_cluster.cu", "exx_phases.cuh", "exx_kernels.cuh", "exx_internal.h", "exx_geometry.cpp",
-                  "exx_geometry.h", "exx_solve.cu")
+                  "exx_geometry.h", "exx_solve.cu", "exx_mg.cuh")
 
 
 def _kernel_hash():
@@ -325,8 +331,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="exx", choices=["exx", "reference"])
     ap.add_argument("--precision", type=int, default=1, help="1: FP32 inner + FP64 refinement, 0: FP64 CG")
-    ap.add_argument("--preconditioner", type=int, default=0,
-                    help="1: multigrid-preconditioned CG on the one-CTA solver, 0: plain CG")
+    ap.add_argument("--preconditioner", type=int, default=1,
+                    help="1: multigrid-preconditioned CG (the fastest form; FP32 inside FP64 refinement at "
+                         "precision 1), 0: plain CG (the cluster solver at precision 1)")
     ap.add_argument("--plain-steps", type=int, default=1, help="timed steps of the plain FP64 CG comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -342,6 +349,8 @@ def main():
     ap.add_argument("--orbitals", type=int, default=0,
                     help="keep only the first N orbitals of the workload (small cases for profiling)")
     args = ap.parse_args()
+    if args.precision == 0:
+        args.preconditioner = 0  # the FP64 bench line is the plain FP64 CG (the speed-ups' denominator)
 
     from paper_1911_10630_gb300 import synth
     w = synth.config1()
@@ -407,24 +416,37 @@ def main():
     kern_ms = statistics.mean(solve_ms)
     hbm_peak, sm_mhz_max, peak_src = _peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    workload_key = f"{w.name}|p{args.precision}"
+    workload_key = f"{w.name}|p{args.precision}" + ("m" if args.preconditioner == 1 else "")
     fp64_peak = exx_mod.probe_fp64_rate(stream)  # the FP64 pipe's FMA rate, measured on this GPU
-    if args.precision == 1:
-        kname = "cluster_pair_kernel" if st["solver_kind"] == 2 else "pair_kernel"
+    def cg_roofline(st_, alg_, kms):
+        """The plain FP32 CG's roofline: the cluster solver keeps the CG state in
+        shared memory, so the bound is shared-memory bandwidth."""
+        kname = "cluster_pair_kernel" if st_["solver_kind"] == 2 else "pair_kernel"
         smem_peak = n_sm * SMEM_BYTES_PER_CLK_SM * sm_mhz_max * 1e6 / 1e9
-        achieved = alg["cg"] / (kern_ms / 1e3) / 1e9
-        roofline = {"kernel": kname, "bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
-                    "frac": achieved / smem_peak,
-                    "peak_source": f"{n_sm} SMs x {SMEM_BYTES_PER_CLK_SM} B/clk x {sm_mhz_max:.0f} MHz "
-                                   f"(max SM clock, {peak_src})",
-                    "algorithmic_bytes_per_launch": alg["cg"], "bytes_per_point_iteration": 24,
-                    "traffic": _traffic(kname, workload_key),
-                    "smem_model": {"bytes_per_point_iteration": SMEM_MODEL_BYTES_PER_POINT_ITER,
-                                   "frac": SMEM_MODEL_BYTES_PER_POINT_ITER / 24 * achieved / smem_peak},
-                    "hbm": {"algorithmic_bytes_per_launch": alg["hbm"],
-                            "achieved": alg["hbm"] / (kern_ms / 1e3) / 1e9, "peak": hbm_peak,
-                            "peak_source": peak_src},
-                    "kernel_ms": kern_ms}
+        achieved = alg_["cg"] / (kms / 1e3) / 1e9
+        return {"kernel": kname, "bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
+                "frac": achieved / smem_peak,
+                "peak_source": f"{n_sm} SMs x {SMEM_BYTES_PER_CLK_SM} B/clk x {sm_mhz_max:.0f} MHz "
+                               f"(max SM clock, {peak_src})",
+                "algorithmic_bytes_per_launch": alg_["cg"], "bytes_per_point_iteration": 24,
+                "traffic": _traffic(kname, f"{w.name}|p1"),
+                "smem_model": {"bytes_per_point_iteration": SMEM_MODEL_BYTES_PER_POINT_ITER,
+                               "frac": SMEM_MODEL_BYTES_PER_POINT_ITER / 24 * achieved / smem_peak},
+                "hbm": {"algorithmic_bytes_per_launch": alg_["hbm"],
+                        "achieved": alg_["hbm"] / (kms / 1e3) / 1e9, "peak": hbm_peak, "peak_source": peak_src},
+                "kernel_ms": kms}
+
+    if args.precision == 1 and args.preconditioner == 1:
+        # one CTA per pair, every vector in the pair's workspace: the sweeps
+        # stream from HBM (the pairs in flight hold far more than L2)
+        mg_bytes = MG_BYTES_PER_POINT_ITER * alg["point_iters"]
+        achieved = mg_bytes / (kern_ms / 1e3) / 1e9
+        roofline = {"kernel": "pair_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "peak_source": peak_src,
+                    "algorithmic_bytes_per_launch": mg_bytes, "bytes_per_point_iteration": MG_BYTES_PER_POINT_ITER,
+                    "traffic": _traffic("pair_kernel", workload_key), "kernel_ms": kern_ms}
+    elif args.precision == 1:
+        roofline = cg_roofline(st, alg, kern_ms)
     else:
         fl = alg["flops"] / (kern_ms / 1e3) / 1e12
         roofline = {"kernel": "pair_kernel", "bound": "alu", "achieved": fl, "peak": fp64_peak,
@@ -442,7 +464,8 @@ def main():
         hphi = torch.from_numpy(phi).pin_memory()
         hD = torch.empty(phi.shape, dtype=torch.float64).pin_memory()
         hc = torch.from_numpy(centers).pin_memory()
-        exh = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=args.precision)
+        exh = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=args.precision,
+                  preconditioner=args.preconditioner)
         exh.compute_host(hphi, hc, hD, stream=stream)  # warm-up (allocates the device copies)
         barrier()
         t0 = time.perf_counter()
@@ -483,6 +506,34 @@ def main():
                                                "kernel_ms": st0["solve_ms"]}}
         extra["speedup_vs_plain_fp64_cg"] = value / ws / extra["plain_fp64_cg"]["value"]
         ex0.close()
+        if args.preconditioner == 1:
+            # the unpreconditioned FP32 CG on the cluster solver (autotuned launch shape)
+            exc = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=1)
+            exc.compute(dphi, dcen, dD, stream=stream)
+            torch.cuda.synchronize(dev)
+            tc, sc = [], []
+            for _ in range(max(1, min(args.steps, 3))):
+                ev0.record(stream)
+                ec = exc.compute(dphi, dcen, dD, stream=stream)
+                ev1.record(stream)
+                torch.cuda.synchronize(dev)
+                tc.append(ev0.elapsed_time(ev1))
+                sc.append(exc.stats()["solve_ms"])
+            stc = exc.stats()
+            algc = _algorithmic(exc.pairs(), stc, n_pe, n_me, 1)
+            extra["cluster_cg"] = {
+                "value": n_pair / (statistics.mean(tc) / 1e3), "unit": UNIT, "ms_per_step": statistics.mean(tc),
+                "E_xx": ec, "dE_vs_headline_per_orbital": abs(ec - exx_vals[-1]) / w.n,
+                "iters_p50": stc["iters_p50"], "iters_max": stc["iters_max"],
+                "iters_per_pair": stc["iters_total"] / stc["n_pair"],
+                "solver": f"{stc['solver_kind']}x{stc['cluster_size']} ctas={stc['grid_ctas']} "
+                          f"threads={stc['threads']} lane_map={stc['lane_map']} "
+                          f"autotuned_from={stc['n_candidates']}",
+                "roofline": cg_roofline(stc, algc, statistics.mean(sc)),
+                "phase_ms_per_cluster": {"setup": stc["phase_ms"][0], "fp64_residuals": stc["phase_ms"][1],
+                                         "fp32_cg": stc["phase_ms"][2], "finish": stc["phase_ms"][3]},
+                "speedup_vs_plain_fp64_cg": statistics.mean(t) / statistics.mean(tc)}
+            exc.close()
         # the same FP64 solve with the multigrid-preconditioned CG (one V-cycle per iteration)
         exm = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=0, preconditioner=1)
         exm.compute(dphi, dcen, dD, stream=stream)
@@ -502,8 +553,12 @@ def main():
     if rank == 0 and ws == 1 and not args.no_legs and not args.orbitals:
         extra["batched_uneven"] = batched_uneven_leg(dev, stream)
         plain_ms = extra.get("plain_fp64_cg", {}).get("ms_per_step")
-        extra["learned_guess"] = learned_leg(w, dphi, dcen, dD, stream, total_ms / args.steps, plain_ms)
-        extra["learned_guess"]["iters_per_pair_zero_start"] = st["iters_total"] / st["n_pair"]
+        # the learned start runs on the unpreconditioned cluster solver: compare it with that solver's zero start
+        zc = extra.get("cluster_cg")
+        zero_ms = zc["ms_per_step"] if zc else total_ms / args.steps
+        extra["learned_guess"] = learned_leg(w, dphi, dcen, dD, stream, zero_ms, plain_ms)
+        extra["learned_guess"]["iters_per_pair_zero_start"] = (zc["iters_per_pair"] if zc
+                                                               else st["iters_total"] / st["n_pair"])
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -522,8 +577,10 @@ def main():
             "dtype": "f32+f64" if args.precision == 1 else "f64", "data": "synthetic",
             "config": {"workload": w.name, "n_orbitals": w.n, "grid": int(w.grid[0]), "cell_bohr": float(w.cell[0]),
                        "r_pair_bohr": w.r_pair, "r_pe": w.r_pe, "r_me": w.r_me, "l_max": w.l_max, "tol": w.tol,
-                       "n_pair": n_pair, "precision": "fp32 inner CG + fp64 refinement" if args.precision == 1
-                       else "fp64 CG", "l2": "inputs larger than L2 (orbitals 3.5 GB, D_xx 3.5 GB)",
+                       "n_pair": n_pair,
+                       "precision": ("fp32 multigrid-preconditioned CG + fp64 refinement" if args.preconditioner == 1
+                                     else "fp32 inner CG + fp64 refinement") if args.precision == 1 else "fp64 CG",
+                       "l2": "inputs larger than L2 (orbitals 3.5 GB, D_xx 3.5 GB)",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "solver": f"{st['solver_kind']}x{st['cluster_size']} ctas={st['grid_ctas']} "
                                  f"threads={st['threads']} lane_map={st['lane_map']} "

@@ -103,7 +103,7 @@ typedef struct {
                           global memory; 2 = one thread-block cluster per pair
                           (plain CG: the FP32 inner state in shared memory;
                           multigrid CG: all state in the pair's workspace,
-                          shared by the cluster's CTAs).                        */
+                          shared by the cluster's CTAs; only when requested). */
     int cluster_size;  /* CTAs per cluster for solver_kind 2: 0 = library choice,
                           else 2, 4, 8 or 9 (9 with the non-portable cluster
                           size opt-in; on GB300, 15 clusters of 9 CTAs fit
@@ -166,10 +166,10 @@ typedef struct {
                           with warm_start. With precision 0 the PCG and every
                           level are FP64, one CTA per pair; with precision 1
                           each inner solve of the FP64 refinement loop is this
-                          PCG in FP32 (recurrence and V-cycle), by default on a
-                          cluster of CTAs per pair whose vectors stay in L2
-                          (solver_kind 1: one CTA per pair). A ball of radius
-                          <= 3 has no coarse level: its CG is unpreconditioned.
+                          PCG in FP32 (recurrence and V-cycle), on one CTA per
+                          pair, or with solver_kind 2 on a cluster of CTAs per
+                          pair whose vectors stay in L2. A ball of radius <= 3
+                          has no coarse level: its CG is unpreconditioned.
                           The stop rule is unchanged: ||r|| <= tol ||b||.      */
     int inject_wait_timeout; /* test only (default 0): the next this-many calls
                           of the context each make one extra bounded device wait

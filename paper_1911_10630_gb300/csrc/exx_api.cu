@@ -907,8 +907,8 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         e = cudaMalloc(&c->d_class, sizeof(int) * 3 * (size_t)c->n_geo);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaMalloc(radius classes)"));
     }
-    // the multigrid-preconditioned CG on clusters (solver_kind 0 or 2 at precision 1)
-    if (o.preconditioner == 1 && o.precision == 1 && o.solver_kind != 1 && mg_levels > 0) {
+    // the multigrid-preconditioned CG on clusters (solver_kind 2 at precision 1)
+    if (o.preconditioner == 1 && o.precision == 1 && o.solver_kind == 2 && mg_levels > 0) {
         const int C = o.cluster_size ? o.cluster_size : 8;
         const int minb = o.ctas_per_sm == 1 ? 1 : 2;
         int nclu = 0;

@@ -21,6 +21,10 @@
 
 namespace exx {
 
+// Points per thread in flight in a stage's loop (loop unrolling over
+// restrict-qualified arrays lets the loads of several points overlap).
+constexpr int kMGUnroll = 2;
+
 template <typename T>
 struct MGView {
     const int* cube;
@@ -87,23 +91,36 @@ __device__ __forceinline__ MGView<T> mg_view(const SolveParams& P, const BallGeo
 template <typename T>
 __device__ __forceinline__ void mg_jacobi0(const MGView<T>& v, T w, int kb, int ke, int step) {
     const T wd = w / v.A.c0;
-    for (int k = kb; k < ke; k += step) v.Z[v.cube[k]] = wd * v.rhs[k];
+    const int* __restrict__ cube = v.cube;
+    const T* __restrict__ rhs = v.rhs;
+    T* __restrict__ Zs = v.Z;
+#pragma unroll (kMGUnroll)
+    for (int k = kb; k < ke; k += step) Zs[cube[k]] = wd * rhs[k];
 }
 
 // Residual into Tc: rhs - A Z.
 template <typename T>
 __device__ __forceinline__ void mg_residual(const MGView<T>& v, int kb, int ke, int step) {
+    const int* __restrict__ cube = v.cube;
+    const T* __restrict__ rhs = v.rhs;
+    const T* __restrict__ Zs = v.Z;
+    T* __restrict__ Tcs = v.Tc;
+#pragma unroll (kMGUnroll)
     for (int k = kb; k < ke; k += step) {
-        const int c = v.cube[k];
-        v.Tc[c] = v.rhs[k] - lap19<T>(v.Z, c, v.S, v.S2, v.A);
+        const int c = cube[k];
+        Tcs[c] = rhs[k] - lap19<T>(Zs, c, v.S, v.S2, v.A);
     }
 }
 
 // Full weighting of Tc onto the points kb.. of the next level cl (its rhs).
 template <typename T>
 __device__ __forceinline__ void mg_restrict(const MGView<T>& v, const MGLevel& cl, int kb, int ke, int step) {
+    const int* __restrict__ off = cl.off;
+    const T* __restrict__ Tcs = v.Tc;
+    T* __restrict__ rn = v.rnext;
+#pragma unroll (kMGUnroll)
     for (int k = kb; k < ke; k += step) {
-        const int pk = cl.off[k];
+        const int pk = off[k];
         const int X = 2 * off_x(pk), Y = 2 * off_y(pk), Z = 2 * off_z(pk);
         T acc = T(0);
 #pragma unroll
@@ -113,9 +130,9 @@ __device__ __forceinline__ void mg_restrict(const MGView<T>& v, const MGLevel& c
 #pragma unroll
                 for (int ez = -1; ez <= 1; ++ez) {
                     const T wt = (ex ? T(0.5) : T(1)) * (ey ? T(0.5) : T(1)) * (ez ? T(0.5) : T(1));
-                    acc = fma(wt, v.Tc[mg_idx(v, X + ex, Y + ey, Z + ez)], acc);
+                    acc = fma(wt, Tcs[mg_idx(v, X + ex, Y + ey, Z + ez)], acc);
                 }
-        v.rnext[k] = T(0.125) * acc;
+        rn[k] = T(0.125) * acc;
     }
 }
 
@@ -134,8 +151,13 @@ __device__ __forceinline__ void mg_bottom(const MGView<T>& v, const T* minv, int
 template <typename T>
 __device__ __forceinline__ void mg_prolong(const MGView<T>& v, const MGView<T>& vc, const T* zc, int kb, int ke,
                                            int step) {
+    const int* __restrict__ off = v.off;
+    const int* __restrict__ cube = v.cube;
+    T* __restrict__ Zs = v.Z;
+    const T* __restrict__ zcs = zc;
+#pragma unroll (kMGUnroll)
     for (int k = kb; k < ke; k += step) {
-        const int pk = v.off[k];
+        const int pk = off[k];
         const int o[3] = {off_x(pk), off_y(pk), off_z(pk)};
         int lo[3], hi[3];
 #pragma unroll
@@ -153,9 +175,9 @@ __device__ __forceinline__ void mg_prolong(const MGView<T>& v, const MGView<T>& 
                     if ((cx && hi[0] == lo[0]) || (cy && hi[1] == lo[1]) || (cz && hi[2] == lo[2])) continue;
                     const T wt = (hi[0] != lo[0] ? T(0.5) : T(1)) * (hi[1] != lo[1] ? T(0.5) : T(1)) *
                                  (hi[2] != lo[2] ? T(0.5) : T(1));
-                    acc = fma(wt, zc[mg_idx(vc, cx ? hi[0] : lo[0], cy ? hi[1] : lo[1], cz ? hi[2] : lo[2])], acc);
+                    acc = fma(wt, zcs[mg_idx(vc, cx ? hi[0] : lo[0], cy ? hi[1] : lo[1], cz ? hi[2] : lo[2])], acc);
                 }
-        v.Z[v.cube[k]] += acc;
+        Zs[cube[k]] += acc;
     }
 }
 
@@ -164,12 +186,17 @@ __device__ __forceinline__ void mg_prolong(const MGView<T>& v, const MGView<T>& 
 template <typename T>
 __device__ __forceinline__ T mg_smooth(const MGView<T>& v, T w, int kb, int ke, int step) {
     const T wd = w / v.A.c0;
+    const int* __restrict__ cube = v.cube;
+    const T* __restrict__ rhs = v.rhs;
+    const T* __restrict__ Zs = v.Z;
+    T* __restrict__ Tcs = v.Tc;
     T rz = T(0);
+#pragma unroll (kMGUnroll)
     for (int k = kb; k < ke; k += step) {
-        const int c = v.cube[k];
-        const T t = fma(wd, v.rhs[k] - lap19<T>(v.Z, c, v.S, v.S2, v.A), v.Z[c]);
-        v.Tc[c] = t;
-        rz = fma(v.rhs[k], t, rz);
+        const int c = cube[k];
+        const T t = fma(wd, rhs[k] - lap19<T>(Zs, c, v.S, v.S2, v.A), Zs[c]);
+        Tcs[c] = t;
+        rz = fma(rhs[k], t, rz);
     }
     return rz;
 }

@@ -92,7 +92,7 @@ __device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const
     Stencil<T> A;
     if constexpr (sizeof(T) == 8) A = negated(P.st64);
     else A = negated(P.st32);
-    const T* Z = reinterpret_cast<const T*>(slot + P.off_tc);  // z = M r (level-0 cube)
+    const T* __restrict__ Z = reinterpret_cast<const T*>(slot + P.off_tc);  // z = M r (level-0 cube)
     mg_vcycle<NT, T>(P, G, M, slot, r);
     T rz = T(0);
     for (int k = threadIdx.x; k < n_pe; k += NT) {
@@ -105,6 +105,7 @@ __device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const
     int it = 0;
     while (rr > target2 && it < max_iter) {
         T pap = T(0);
+#pragma unroll (kMGUnroll)
         for (int k = threadIdx.x; k < n_pe; k += NT) {
             const int c = cube[k];
             const T a = lap19<T>(pc, c, S, S2, A);
@@ -114,6 +115,7 @@ __device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const
         pap = block_sum<NT, T>(pap, red, flip);
         const T al = rz / pap;
         T rrn = T(0);
+#pragma unroll (kMGUnroll)
         for (int k = threadIdx.x; k < n_pe; k += NT) {
             const int c = cube[k];
             d[k] = fma(al, pc[c], d[k]);
@@ -127,10 +129,12 @@ __device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const
         if (rrn <= target2 || !(rrn == rrn)) break;
         mg_vcycle<NT, T>(P, G, M, slot, r);
         T rzn = T(0);
+#pragma unroll (kMGUnroll)
         for (int k = threadIdx.x; k < n_pe; k += NT) rzn = fma(r[k], Z[cube[k]], rzn);
         rzn = block_sum<NT, T>(rzn, red, flip);
         const T be = rzn / rz;
         rz = rzn;
+#pragma unroll (kMGUnroll)
         for (int k = threadIdx.x; k < n_pe; k += NT) {
             const int c = cube[k];
             pc[c] = fma(be, pc[c], Z[c]);

@@ -255,15 +255,18 @@ def test_iteration_cap_reports_nonconvergence(torch, cfg0):
     assert np.isfinite(out["E_xx"])
 
 
-@pytest.mark.parametrize("precision,lane_map", [(1, None), (1, 2), (1, 3), (1, 4), (1, 5), (0, None)])
-def test_water64_full_size_sampled(torch, precision, lane_map):
+@pytest.mark.parametrize("precision,lane_map,preconditioner", [(1, None, 1), (1, None, 0), (1, 2, 0), (1, 3, 0),
+                                                                (1, 4, 0), (1, 5, 0), (0, None, 0)])
+def test_water64_full_size_sampled(torch, precision, lane_map, preconditioner):
     """The bench workload (water-64 scale, 120^3, 256 orbitals, R_pair = 10 bohr,
-    R_PE/R_ME = 24/32, tol 1e-8) in the launch configuration bench.py times
-    (autotuned), and with the z-run and quad thread maps forced; checked on sampled pairs
-    and sampled orbitals the oracle computes one by one."""
+    R_PE/R_ME = 24/32, tol 1e-8) in the configuration bench.py times (the FP32
+    multigrid PCG in FP64 refinement, one CTA per pair), on the autotuned cluster
+    solver and with its z-run and quad thread maps forced; checked on sampled
+    pairs and sampled orbitals the oracle computes one by one."""
     w = synth.config1()
     phi = w.orbitals()
     extra = {} if lane_map is None else dict(lane_map=lane_map, autotune=0)
+    extra["preconditioner"] = preconditioner
     out = run_gpu(w, phi, torch=torch, precision=precision, **extra)
     if lane_map is not None:
         assert out["stats"]["lane_map"] == lane_map
@@ -419,7 +422,7 @@ def test_warm_start_from_previous_step(torch):
 # FP32 inside the FP64 refinement on one CTA per pair (solver_kind 1) or on a
 # cluster of C CTAs per pair (solver_kind 0 or 2), one or two CTAs per SM
 # --------------------------------------------------------------------------
-MG_FORMS = [dict(precision=0), dict(precision=1, solver_kind=1), dict(precision=1),
+MG_FORMS = [dict(precision=0), dict(precision=1), dict(precision=1, solver_kind=2),
             dict(precision=1, solver_kind=2, cluster_size=2), dict(precision=1, solver_kind=2, cluster_size=4),
             dict(precision=1, solver_kind=2, cluster_size=16),
             dict(precision=1, solver_kind=2, cluster_size=8, ctas_per_sm=1)]
@@ -427,7 +430,7 @@ MG_IDS = ["fp64", "fp32-cta", "fp32-c8", "fp32-c2", "fp32-c4", "fp32-c16", "fp32
 
 
 def _mg_form_check(out, form):
-    if form.get("solver_kind") == 1 or form["precision"] == 0:
+    if form.get("solver_kind", 0) != 2:
         assert out["stats"]["solver_kind"] == 1
     else:
         assert out["stats"]["solver_kind"] == 2
