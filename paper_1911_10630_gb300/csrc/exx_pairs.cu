@@ -380,6 +380,28 @@ cudaError_t launch_zero(double* p, long long n, int num_sms, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Copy of n2 16-byte words between device-visible buffers (one of them pinned
+// host memory, read or written by the SMs over the chip-to-chip link): four
+// independent words in flight per thread and step.
+__global__ void copy16_kernel(const double2* __restrict__ src, double2* __restrict__ dst, long long n2) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; k + 3 * stride < n2; k += 4 * stride) {
+        const double2 a = src[k], b = src[k + stride], c = src[k + 2 * stride], d = src[k + 3 * stride];
+        dst[k] = a;
+        dst[k + stride] = b;
+        dst[k + 2 * stride] = c;
+        dst[k + 3 * stride] = d;
+    }
+    for (; k < n2; k += stride) dst[k] = src[k];
+}
+
+cudaError_t launch_copy16(const void* src, void* dst, long long n2, int num_sms, cudaStream_t st) {
+    copy16_kernel<<<num_sms * 8, 256, 0, st>>>(reinterpret_cast<const double2*>(src), reinterpret_cast<double2*>(dst),
+                                                n2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dfix_convert(double* p, long long n, double inv, int num_sms, cudaStream_t st) {
     dfix_convert_kernel<<<num_sms * 8, 256, 0, st>>>(p, n, inv);
     return cudaGetLastError();

@@ -246,6 +246,33 @@ def test_host_buffers_match_device(torch, cfg0):
     assert abs(e - ref["E_xx"]) / w.n <= E_GATE_PER_ORBITAL
 
 
+def test_host_buffers_pinned_and_pageable(torch, cfg0):
+    """exx_compute_host copies pinned, device-mapped host buffers with the SMs
+    (copy16_kernel) and any other memory with the copy engine: both give the
+    same results bit for bit, also from a pinned buffer 8 bytes off the 16-byte
+    boundary (which takes the copy engine). D_xx is summed deterministically
+    so that the calls can be compared bit for bit."""
+    w, phi, _ = cfg0
+    from paper_1911_10630_gb300.exx import Exx
+    ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, 6, w.tol, deterministic=1)
+    cen = np.ascontiguousarray(w.centers)
+    D0 = np.empty_like(phi)
+    e0 = ex.compute_host(phi, cen, D0)
+    hphi = torch.from_numpy(phi).pin_memory()
+    hD = torch.empty(phi.shape, dtype=torch.float64).pin_memory()
+    e1 = ex.compute_host(hphi, torch.from_numpy(cen).pin_memory(), hD)
+    assert e1 == e0
+    np.testing.assert_array_equal(hD.numpy(), D0)
+    flat = torch.empty(phi.size + 1, dtype=torch.float64).pin_memory()
+    off = flat[1:].view(phi.shape)
+    off.copy_(torch.from_numpy(phi))
+    hD2 = torch.empty(phi.size + 1, dtype=torch.float64).pin_memory()[1:].view(phi.shape)
+    e2 = ex.compute_host(off, cen, hD2)
+    assert e2 == e0
+    np.testing.assert_array_equal(hD2.numpy(), D0)
+    ex.close()
+
+
 def test_iteration_cap_reports_nonconvergence(torch, cfg0):
     w, phi, _ = cfg0
     out = run_gpu(w, phi, torch=torch, allow_noconv=True, max_iter=5)
