@@ -205,16 +205,20 @@ __device__ __forceinline__ T mg_smooth(const MGView<T>& v, T w, int kb, int ke, 
 // between the stages). With l0 = 0 this is the whole preconditioner z = M r0
 // (z in the level-0 Tc cube); with l0 = 1 it continues a cycle whose level-1
 // right-hand side is already in the slot, leaving level 1's correction in its
-// Tc cube (its Z cube when level 1 is the coarsest).
+// Tc cube (its Z cube when level 1 is the coarsest). With z0_ready the caller
+// has already written level l0's first Jacobi sweep (Z = w D^-1 rhs) and
+// synchronised. Returns this thread's share of rhs . z on level l0.
 template <int NT, typename T>
-__device__ __noinline__ void mg_vcycle(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot,
-                                       const T* __restrict__ r0, int l0 = 0) {
+__device__ __noinline__ T mg_vcycle(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot,
+                                    const T* __restrict__ r0, int l0 = 0, bool z0_ready = false) {
     const T w = (T)P.mg_omega;
     const int t = threadIdx.x;
     for (int l = l0; l < M.L; ++l) {
         const MGView<T> v = mg_view<T>(P, G, M, slot, l, r0);
-        mg_jacobi0(v, w, t, v.n, NT);
-        __syncthreads();
+        if (!(l == l0 && z0_ready)) {
+            mg_jacobi0(v, w, t, v.n, NT);
+            __syncthreads();
+        }
         mg_residual(v, t, v.n, NT);
         __syncthreads();
         mg_restrict(v, M.lv[l + 1], t, M.lv[l + 1].n, NT);
@@ -228,13 +232,15 @@ __device__ __noinline__ void mg_vcycle(const SolveParams& P, const BallGeo& G, c
         mg_bottom(v, minv, t, v.n, NT);
         __syncthreads();
     }
+    T rz = T(0);
     for (int l = M.L - 1; l >= l0; --l) {
         const MGView<T> v = mg_view<T>(P, G, M, slot, l, r0), vc = mg_view<T>(P, G, M, slot, l + 1, r0);
         mg_prolong(v, vc, (l + 1 == M.L) ? vc.Z : vc.Tc, t, v.n, NT);
         __syncthreads();
-        (void)mg_smooth(v, w, t, v.n, NT);
+        rz = mg_smooth(v, w, t, v.n, NT);
         __syncthreads();
     }
+    return rz;
 }
 
 // Zeroes the level cubes' points kb.. (per-pair radii: the next pair's balls

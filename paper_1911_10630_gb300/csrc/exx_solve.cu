@@ -93,17 +93,16 @@ __device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const
     if constexpr (sizeof(T) == 8) A = negated(P.st64);
     else A = negated(P.st32);
     const T* __restrict__ Z = reinterpret_cast<const T*>(slot + P.off_tc);  // z = M r (level-0 cube)
-    mg_vcycle<NT, T>(P, G, M, slot, r);
-    T rz = T(0);
+    T* __restrict__ Zj = reinterpret_cast<T*>(slot + P.off_zc);             // the V-cycle's first Jacobi sweep
+    const T wd = (T)P.mg_omega / A.c0;
+    T rz = block_sum<NT, T>(mg_vcycle<NT, T>(P, G, M, slot, r), red, flip);
     for (int k = threadIdx.x; k < n_pe; k += NT) {
         const int c = cube[k];
-        const T z = Z[c];
-        pc[c] = z;
-        rz = fma(r[k], z, rz);
+        pc[c] = Z[c];
     }
-    rz = block_sum<NT, T>(rz, red, flip);
     int it = 0;
     while (rr > target2 && it < max_iter) {
+        __syncthreads();  // p
         T pap = T(0);
 #pragma unroll (kMGUnroll)
         for (int k = threadIdx.x; k < n_pe; k += NT) {
@@ -115,23 +114,21 @@ __device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const
         pap = block_sum<NT, T>(pap, red, flip);
         const T al = rz / pap;
         T rrn = T(0);
+        // d, r and the V-cycle's first sweep Z = w D^-1 r in one pass
 #pragma unroll (kMGUnroll)
         for (int k = threadIdx.x; k < n_pe; k += NT) {
             const int c = cube[k];
             d[k] = fma(al, pc[c], d[k]);
             const T rk = fma(-al, ap[k], r[k]);
             r[k] = rk;
+            Zj[c] = wd * rk;
             rrn = fma(rk, rk, rrn);
         }
         rrn = block_sum<NT, T>(rrn, red, flip);
         ++it;
         rr = rrn;
         if (rrn <= target2 || !(rrn == rrn)) break;
-        mg_vcycle<NT, T>(P, G, M, slot, r);
-        T rzn = T(0);
-#pragma unroll (kMGUnroll)
-        for (int k = threadIdx.x; k < n_pe; k += NT) rzn = fma(r[k], Z[cube[k]], rzn);
-        rzn = block_sum<NT, T>(rzn, red, flip);
+        const T rzn = block_sum<NT, T>(mg_vcycle<NT, T>(P, G, M, slot, r, 0, true), red, flip);
         const T be = rzn / rz;
         rz = rzn;
 #pragma unroll (kMGUnroll)
@@ -139,7 +136,6 @@ __device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const
             const int c = cube[k];
             pc[c] = fma(be, pc[c], Z[c]);
         }
-        __syncthreads();
     }
     rr_out = rr;
     return it;
