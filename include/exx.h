@@ -195,10 +195,12 @@ typedef struct {
     int cluster_size;      /* CTAs per pair                                        */
     int grid_ctas;         /* CTAs launched for the pair kernel                    */
     int threads;           /* threads per CTA                                      */
-    double phase_ms[4];    /* cluster solver: the pair-kernel time split by the
-                              clusters' cycle counts into setup (gather,
-                              multipoles, shell), FP64 residuals, FP32 CG
-                              iterations and finish (E_ij, scatter)               */
+    double phase_ms[4];    /* the pair-kernel time split by the cycle counts of
+                              its CTAs (clusters) into setup (gather,
+                              multipoles, shell), the FP64 residuals of the
+                              refinement loop, the CG iterations (with the
+                              V-cycles under preconditioner 1) and finish
+                              (E_ij, scatter)                                    */
     int lane_map;          /* lane map in use (cluster solver)                      */
     int n_candidates;      /* launch shapes the autotuner could choose from          */
     double tune_ms;        /* host time spent by the autotuner (first call)          */

@@ -1090,7 +1090,7 @@ static exx_status enqueue(exx_ctx* c, const double* orbitals, const double* cent
     P.iters = c->d_iters;
     P.refines = c->d_refines;
     P.dbg_b = nullptr;
-    P.phase_clk = (c->use_cluster || c->per_class || c->mg_C) ? c->d_phase : nullptr;
+    P.phase_clk = c->d_phase;
     P.test_wait = c->inject_now;
     P.box_org = c->cur_box;
     for (int a = 0; a < 3; ++a) P.bdim[a] = c->cur_bdim[a];
@@ -1659,9 +1659,7 @@ extern "C" exx_status exx_get_stats(const exx_ctx* cc, exx_stats* out) {
         // shares of the pair-kernel time (the clusters run side by side)
         const double cyc = (double)ph[0] + (double)ph[1] + (double)ph[2] + (double)ph[3];
         for (int k = 0; k < 4; ++k)
-            c->stats.phase_ms[k] = ((c->use_cluster || c->per_class || c->mg_C) && cyc > 0.0)
-                                       ? c->stats.solve_ms * (double)ph[k] / cyc
-                                       : 0.0;
+            c->stats.phase_ms[k] = cyc > 0.0 ? c->stats.solve_ms * (double)ph[k] / cyc : 0.0;
     }
     if (c->per_class) {  // radius classes: the largest cluster and grid of any class
         int cmax = 1, gmax = c->n_slots;

@@ -193,6 +193,9 @@ __global__ void __launch_bounds__(NT, (MIXED && !MG) ? 1 : 2) pair_kernel(const 
         const BallGeo G = P.geos[pr.geo];
         const int* cube = G.pt_cube;
         const int n_pe = G.n_pe;
+        const bool clk = P.phase_clk && threadIdx.x == 0;
+        const long long t0 = clk ? clock64() : 0;
+        long long tr = 0;
 
         // 1. gather rho on the PE ball; v = 0 there
         gather_rho(P, G, pr, rho, vc, threadIdx.x, NT);
@@ -208,6 +211,7 @@ __global__ void __launch_bounds__(NT, (MIXED && !MG) ? 1 : 2) pair_kernel(const 
         __syncthreads();
 
         // 4./5. right-hand side and solve
+        const long long t1 = clk ? clock64() : 0;
         int iters = 0, refines = 0;
         bool conv = true;
         if (!MIXED) {
@@ -237,6 +241,7 @@ __global__ void __launch_bounds__(NT, (MIXED && !MG) ? 1 : 2) pair_kernel(const 
             double bb = -1.0, rn_prev = 1e300;
             for (;;) {
                 // FP64 residual r = 4 pi rho + lap v (v: current iterate on PE, shell values outside)
+                const long long tu = clk ? clock64() : 0;
                 double acc = 0.0;
                 for (int k = threadIdx.x; k < n_pe; k += NT) {
                     const int c = cube[k];
@@ -246,6 +251,7 @@ __global__ void __launch_bounds__(NT, (MIXED && !MG) ? 1 : 2) pair_kernel(const 
                     if (bb < 0.0 && P.dbg_b) P.dbg_b[k] = rk;
                 }
                 const double rn2 = block_sum<NT, double>(acc, red, flip);
+                if (clk) tr += clock64() - tu;
                 if (bb < 0.0) bb = rn2;
                 if (rn2 <= P.tol * P.tol * bb) break;
                 const double rn = sqrt(rn2);
@@ -281,6 +287,7 @@ __global__ void __launch_bounds__(NT, (MIXED && !MG) ? 1 : 2) pair_kernel(const 
             }
         }
         __syncthreads();
+        const long long t2 = clk ? clock64() : 0;
 
         // 6. E_ij over the PE ball and the D_xx scatter over the ME ball
         double e = 0.0;
@@ -307,6 +314,13 @@ __global__ void __launch_bounds__(NT, (MIXED && !MG) ? 1 : 2) pair_kernel(const 
             }
         }
         __syncthreads();
+        if (clk) {
+            const long long t3 = clock64();
+            atomicAdd(P.phase_clk + 0, (unsigned long long)(t1 - t0));
+            atomicAdd(P.phase_clk + 1, (unsigned long long)tr);
+            atomicAdd(P.phase_clk + 2, (unsigned long long)(t2 - t1 - tr));
+            atomicAdd(P.phase_clk + 3, (unsigned long long)(t3 - t2));
+        }
     }
 }
 
