@@ -288,7 +288,11 @@ exx_status exx_compute_boxes(exx_ctx *ctx, const double *boxes, const int *origi
  * to the device, runs exx_compute and copies D_xx back into d_xx_host.
  *   orbitals_host [n][N0][N1][N2], centers_host [n][3], alphas_host [n] or NULL,
  *   d_xx_host [n][N0][N1][N2] (written). Device buffers are held by the
- *   context between calls and grown when n grows.
+ *   context between calls and grown when n grows. An orbitals or d_xx buffer
+ *   in pinned, device-mapped host memory (cudaHostAlloc, cudaMallocHost,
+ *   cudaHostRegister with mapping), 16-byte aligned, is moved by the GPU's
+ *   SMs reading or writing it directly; any other buffer by cudaMemcpyAsync.
+ *   The call returns after D_xx has reached d_xx_host.
  */
 exx_status exx_compute_host(exx_ctx *ctx, const double *orbitals_host, const double *centers_host,
                             int n, const double *alphas_host, double *e_xx, double *d_xx_host,
