@@ -95,8 +95,10 @@ typedef struct {
     double inner_tol;  /* FP32 inner relative tolerance (default 1e-5).          */
     int threads;       /* threads per CTA, 0 = library choice, else a multiple of
                           32 in [256, 1024]; the one-CTA solver runs 256, 512
-                          or 1024 (other values give 512), the cluster solver
-                          only the launch shapes it is built for.               */
+                          or 1024 (other values: the library choice, 512, or
+                          256 for the FP32 multigrid CG, which then keeps four
+                          CTAs per SM), the cluster solver only the launch
+                          shapes it is built for.                               */
     int ctas_per_sm;   /* resident CTAs per SM, 0 = library choice (the
                           multigrid CG on clusters: 1 or 2, default 2).         */
     int solver_kind;   /* 0 = library choice; 1 = one CTA per pair with state in

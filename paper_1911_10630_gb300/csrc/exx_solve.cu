@@ -145,7 +145,7 @@ __device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const
 // The persistent pair kernel.
 // --------------------------------------------------------------------------
 template <int NT, bool MIXED, bool MG = false>
-__global__ void __launch_bounds__(NT, (MIXED && !MG) ? 1 : 2) pair_kernel(const __grid_constant__ SolveParams P) {
+__global__ void __launch_bounds__(NT, MG ? 1024 / NT : (MIXED ? 1 : 2)) pair_kernel(const __grid_constant__ SolveParams P) {
     extern __shared__ double smem[];
     __shared__ double red[2][33];
     __shared__ float red32[2][33];
@@ -377,9 +377,11 @@ static cudaError_t launch_t(const SolveParams& P, int grid, size_t smem, cudaStr
 }
 
 cudaError_t launch_pair_kernel(const SolveParams& P, int threads, bool mixed, int grid, size_t smem, cudaStream_t st) {
-    if (P.mg) {  // the multigrid-preconditioned CG (512 threads): FP64, or FP32 inside FP64 refinement
-        if (mixed) pair_kernel<512, true, true><<<grid, 512, smem, st>>>(P);
-        else pair_kernel<512, false, true><<<grid, 512, smem, st>>>(P);
+    if (P.mg) {  // the multigrid-preconditioned CG (64 registers): FP64, or FP32 inside FP64 refinement
+        if (!mixed) pair_kernel<512, false, true><<<grid, 512, smem, st>>>(P);
+        else if (threads == 256) pair_kernel<256, true, true><<<grid, 256, smem, st>>>(P);
+        else if (threads == 1024) pair_kernel<1024, true, true><<<grid, 1024, smem, st>>>(P);
+        else pair_kernel<512, true, true><<<grid, 512, smem, st>>>(P);
         return cudaGetLastError();
     }
     if (threads == 256) return mixed ? launch_t<256, true>(P, grid, smem, st) : launch_t<256, false>(P, grid, smem, st);
@@ -390,7 +392,10 @@ cudaError_t launch_pair_kernel(const SolveParams& P, int threads, bool mixed, in
 
 cudaError_t pair_kernel_occupancy(int threads, bool mixed, bool mg, size_t smem, int* blocks_per_sm) {
     const void* f;
-    if (mg) f = mixed ? (const void*)pair_kernel<512, true, true> : (const void*)pair_kernel<512, false, true>;
+    if (mg && !mixed) f = (const void*)pair_kernel<512, false, true>;
+    else if (mg && threads == 256) f = (const void*)pair_kernel<256, true, true>;
+    else if (mg && threads == 1024) f = (const void*)pair_kernel<1024, true, true>;
+    else if (mg) f = (const void*)pair_kernel<512, true, true>;
     else if (threads == 256) f = mixed ? (const void*)pair_kernel<256, true> : (const void*)pair_kernel<256, false>;
     else if (threads == 1024) f = mixed ? (const void*)pair_kernel<1024, true> : (const void*)pair_kernel<1024, false>;
     else f = mixed ? (const void*)pair_kernel<512, true> : (const void*)pair_kernel<512, false>;
