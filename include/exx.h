@@ -214,6 +214,9 @@ typedef struct {
                               into E_ij, E_xx and D_xx; nothing is masked)      */
     int n_clipped;         /* exx_compute_boxes: pairs whose ME ball is not inside
                               both orbitals' boxes (0 for full grids)           */
+    int n_dropped;         /* deterministic D_xx: contributions beyond the
+                              fixed-point range, dropped (the synchronous calls
+                              return EXX_EINVAL for them)                        */
 } exx_stats;
 
 /* Defaults described in exx_options. */
@@ -284,6 +287,25 @@ exx_status exx_compute(exx_ctx *ctx, const double *orbitals, const double *cente
 exx_status exx_compute_boxes(exx_ctx *ctx, const double *boxes, const int *origin, const int box_dim[3],
                              const double *centers, int n, const double *alphas, double *e_xx, double *d_boxes,
                              void *stream);
+
+/*
+ * exx_compute without any host synchronisation (no counterpart in the paper,
+ * whose module returns to a CPU caller): the same work, enqueued after the
+ * caller's stream, with E_xx written to e_xx_dev (one double in DEVICE memory)
+ * and D_xx to d_xx; the caller's stream is ordered after the work, so a kernel
+ * or copy the caller enqueues next sees both. The call returns EXX_OK once the
+ * work is enqueued (errors in its arguments or launches as for exx_compute);
+ * its outcome (non-converged solves, timed-out waits, non-finite inputs,
+ * dropped deterministic D_xx contributions) is read with exx_get_stats, which
+ * waits for the last call first, as exx_get_pairs and exx_debug_pair do. Only
+ * the last call's counters are kept: an asynchronous call issued before the
+ * previous one's counters were read replaces them. The first call of a context
+ * on the cluster solver times its launch shapes (autotune) and so blocks.
+ * Errors: EXX_EINVAL for a NULL, misaligned or non-device e_xx_dev and with
+ * warm_start != 0 (those keep host-side state; use exx_compute).
+ */
+exx_status exx_compute_async(exx_ctx *ctx, const double *orbitals, const double *centers, int n,
+                             const double *alphas, double *e_xx_dev, double *d_xx, void *stream);
 
 /*
  * Same as exx_compute with HOST buffers: copies orbitals, centers (and alphas)

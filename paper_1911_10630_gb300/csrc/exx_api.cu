@@ -125,6 +125,10 @@ struct exx_ctx {
     // the multigrid-preconditioned CG on clusters (preconditioner 1, precision 1):
     // mg_C CTAs per pair, mg_minb CTAs per SM, up to mg_clusters resident clusters
     int mg_C = 0, mg_minb = 2, mg_clusters = 0;
+    // exx_compute_async: the last call's counters are read (after waiting for
+    // the call) by the next exx_get_stats; box of that call
+    bool stats_pending = false;
+    bool pending_box = false;
     // the classes alternate between the context stream (lane 0) and aux
     // (lane 1), forked and joined inside the graph, so that one class's tail
     // overlaps the next class's work; each lane has its own workspace slots
@@ -1436,10 +1440,27 @@ static exx_status autotune(exx_ctx* c, const double* orbitals, const double* cen
 
 // exx_compute and exx_compute_boxes: box = NULL for full grids, else the
 // boxes' corners (device, [n][3]) and their dimensions (host, 3 ints).
+static exx_status finish_stats(exx_ctx* c, bool box);
+
+// After an exx_compute_async call: waits for its work and reads its counters
+// (its outcome stays in them; a call's status is not returned here).
+static cudaError_t wait_pending(exx_ctx* c) {
+    if (!c->stats_pending) return cudaSuccess;
+    const cudaError_t e = cudaStreamSynchronize(c->work);
+    if (e != cudaSuccess) return e;
+    (void)finish_stats(c, c->pending_box);
+    return cudaSuccess;
+}
+
+// One call. With e_xx_dev set (exx_compute_async) E_xx goes to that device
+// double and the call returns without waiting for its work; else E_xx goes to
+// *e_xx on the host after the work has finished.
 static exx_status compute_impl(exx_ctx* c, const double* orbitals, const double* centers, int n, const double* alphas,
-                               double* e_xx, double* d_xx, void* stream, const int* box, const int* bdim) {
+                               double* e_xx, double* d_xx, void* stream, const int* box, const int* bdim,
+                               double* e_xx_dev = nullptr) {
     if (!c) return fail(nullptr, EXX_EINVAL, "exx_compute: ctx is NULL");
-    if (!orbitals || !centers || !e_xx || !d_xx) return fail(c, EXX_EINVAL, "exx_compute: NULL array argument");
+    if (!orbitals || !centers || !(e_xx || e_xx_dev) || !d_xx)
+        return fail(c, EXX_EINVAL, "exx_compute: NULL array argument");
     if (n < 1 || n > 65535) return fail(c, EXX_EINVAL, "exx_compute: n must be in [1, 65535]");
     if ((const void*)orbitals == (const void*)d_xx) return fail(c, EXX_EINVAL, "exx_compute: d_xx aliases orbitals");
     if (c->opt.radii_mode == 1 && !alphas)
@@ -1502,13 +1523,28 @@ static exx_status compute_impl(exx_ctx* c, const double* orbitals, const double*
         s = enqueue(c, orbitals, centers, alphas, n, d_xx, st, false);
         if (s != EXX_OK) return s;
     }
+    if (e_xx_dev)
+        CK(cudaMemcpyAsync(e_xx_dev, c->d_exx, sizeof(double), cudaMemcpyDeviceToDevice, st), "copy E_xx (device)");
     CK(cudaEventRecord(c->ev_out, st), "cudaEventRecord(done)");
     CK(cudaStreamWaitEvent(user, c->ev_out, 0), "cudaStreamWaitEvent(caller stream)");
+    c->last_n = n;
+    c->last_orb = orbitals;
+    if (e_xx_dev) {  // no host synchronisation: the counters wait for exx_get_stats
+        c->stats_pending = true;
+        c->pending_box = box != nullptr;
+        return EXX_OK;
+    }
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(c, e, "exx_compute (stream synchronize)");
     *e_xx = c->h_exx[0];
-    c->last_n = n;
-    c->last_orb = orbitals;
+    return finish_stats(c, box != nullptr);
+}
+
+// Timings and counters of the last call, once its work has finished; the
+// call's status from them (EXX_EINVAL for dropped deterministic D_xx
+// contributions, EXX_ETIMEOUT, EXX_ENOCONV).
+static exx_status finish_stats(exx_ctx* c, bool box) {
+    c->stats_pending = false;
     float ms = 0.f;
     c->stats.solve_ms = cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess ? ms : -1.0;
     c->stats.total_ms = cudaEventElapsedTime(&ms, c->ev[0], c->ev[3]) == cudaSuccess ? ms : -1.0;
@@ -1521,6 +1557,7 @@ static exx_status compute_impl(exx_ctx* c, const double* orbitals, const double*
     c->stats.n_timeouts = sc[10];
     c->stats.n_nonfinite = sc[11];
     c->stats.n_clipped = box ? sc[12] : 0;
+    c->stats.n_dropped = sc[13];
     c->stats.iters_max = -1;  // filled lazily by exx_get_stats
     if (sc[13] > 0) {
         char buf[200];
@@ -1547,6 +1584,21 @@ static exx_status compute_impl(exx_ctx* c, const double* orbitals, const double*
 extern "C" exx_status exx_compute(exx_ctx* c, const double* orbitals, const double* centers, int n,
                                   const double* alphas, double* e_xx, double* d_xx, void* stream) {
     return compute_impl(c, orbitals, centers, n, alphas, e_xx, d_xx, stream, nullptr, nullptr);
+}
+
+extern "C" exx_status exx_compute_async(exx_ctx* c, const double* orbitals, const double* centers, int n,
+                                        const double* alphas, double* e_xx_dev, double* d_xx, void* stream) {
+    if (!c) return fail(nullptr, EXX_EINVAL, "exx_compute_async: ctx is NULL");
+    if (!e_xx_dev || (reinterpret_cast<uintptr_t>(e_xx_dev) & 7u) != 0)
+        return fail(c, EXX_EINVAL, "exx_compute_async: e_xx_dev must be an 8-byte aligned device pointer");
+    if (c->opt.warm_start != 0)
+        return fail(c, EXX_EINVAL, "exx_compute_async: warm starts need exx_compute (host-side bookkeeping)");
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, e_xx_dev) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        (void)cudaGetLastError();
+        return fail(c, EXX_EINVAL, "exx_compute_async: e_xx_dev must be device memory");
+    }
+    return compute_impl(c, orbitals, centers, n, alphas, nullptr, d_xx, stream, nullptr, nullptr, e_xx_dev);
 }
 
 extern "C" exx_status exx_compute_boxes(exx_ctx* c, const double* boxes, const int* origin, const int box_dim[3],
@@ -1636,6 +1688,7 @@ extern "C" exx_status exx_compute_host(exx_ctx* c, const double* orbitals_host, 
 extern "C" exx_status exx_get_stats(const exx_ctx* cc, exx_stats* out) {
     exx_ctx* c = const_cast<exx_ctx*>(cc);
     if (!c || !out) return fail(c, EXX_EINVAL, "exx_get_stats: NULL argument");
+    CK(wait_pending(c), "exx_get_stats (waiting for the last call)");
     if (c->stats.iters_max < 0 && c->stats.n_pair > 0) {
         const int np = c->stats.n_pair;
         std::vector<int> it(np), rf(np);
@@ -1697,6 +1750,7 @@ extern "C" exx_status exx_get_pairs(const exx_ctx* cc, int* pi, int* pj, int* g,
                                     int* iters, int cap, int* n_pair) {
     exx_ctx* c = const_cast<exx_ctx*>(cc);
     if (!c) return fail(nullptr, EXX_EINVAL, "exx_get_pairs: ctx is NULL");
+    CK(wait_pending(c), "exx_get_pairs (waiting for the last call)");
     const int np = c->stats.n_pair;
     if (n_pair) *n_pair = np;
     if (np > cap && (pi || pj || g || radii || e_pair || iters))
@@ -1723,6 +1777,7 @@ extern "C" exx_status exx_debug_pair(exx_ctx* c, const double* orbitals, int ind
                                      void* stream) {
     if (!c) return fail(nullptr, EXX_EINVAL, "exx_debug_pair: ctx is NULL");
     if (!orbitals) return fail(c, EXX_EINVAL, "exx_debug_pair: orbitals is NULL");
+    CK(wait_pending(c), "exx_debug_pair (waiting for the last call)");
     if (index < 0 || index >= c->stats.n_pair) return fail(c, EXX_ENOPAIR, "exx_debug_pair: index out of range");
     (void)cudaGetLastError();
     cudaStream_t st = (cudaStream_t)stream;

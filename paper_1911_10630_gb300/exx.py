@@ -49,7 +49,7 @@ class exx_stats(ctypes.Structure):
                 ("threads", ctypes.c_int), ("phase_ms", ctypes.c_double * 4), ("lane_map", ctypes.c_int),
                 ("n_candidates", ctypes.c_int), ("tune_ms", ctypes.c_double),
                 ("guess_ms", ctypes.c_double), ("n_timeouts", ctypes.c_int), ("n_nonfinite", ctypes.c_int),
-                ("n_clipped", ctypes.c_int)]
+                ("n_clipped", ctypes.c_int), ("n_dropped", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -72,6 +72,7 @@ SIGNATURES = [
     ("exx_init", ctypes.c_int, [ctypes.POINTER(_ctx_p), _d, _i, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_double, ctypes.POINTER(exx_options)]),
     ("exx_compute", ctypes.c_int, [_ctx_p, _vp, _vp, ctypes.c_int, _vp, _d, _vp, _vp]),
+    ("exx_compute_async", ctypes.c_int, [_ctx_p, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]),
     ("exx_compute_host", ctypes.c_int, [_ctx_p, _vp, _vp, ctypes.c_int, _vp, _d, _vp, _vp]),
     ("exx_compute_boxes", ctypes.c_int, [_ctx_p, _vp, _vp, _i, _vp, ctypes.c_int, _vp, _d, _vp, _vp]),
     ("exx_get_stats", ctypes.c_int, [_ctx_p, ctypes.POINTER(exx_stats)]),
@@ -209,6 +210,14 @@ class Exx:
         if not (st == EXX_OK or (allow_noconv and st == EXX_ENOCONV) or (allow_timeout and st == EXX_ETIMEOUT)):
             _check(st, self._ctx)
         return e.value
+
+    def compute_async(self, orbitals, centers, d_xx, e_xx_dev, alphas=None, stream=None) -> None:
+        """exx_compute_async: E_xx into e_xx_dev (a float64 device tensor of one element), no host wait;
+        the outcome is in stats()."""
+        st = load().exx_compute_async(self._ctx, _ptr(orbitals), _ptr(centers), int(centers.shape[0]), _ptr(alphas),
+                                      _ptr(e_xx_dev), _ptr(d_xx), _stream_handle(stream))
+        self.last_status = st
+        _check(st, self._ctx)
 
     def compute_boxes(self, boxes, origin, centers, d_boxes, alphas=None, stream=None, allow_noconv=False) -> float:
         """exx_compute_boxes on device tensors: boxes [n][B0][B1][B2], origin [n][3] int32; returns E_xx."""

@@ -29,7 +29,7 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for required in ("exx_init", "exx_compute", "exx_compute_host", "exx_get_stats", "exx_last_error",
+    for required in ("exx_init", "exx_compute", "exx_compute_async", "exx_compute_host", "exx_get_stats", "exx_last_error",
                      "exx_destroy", "exx_default_options"):
         assert required in names
 

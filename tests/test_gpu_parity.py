@@ -273,6 +273,40 @@ def test_host_buffers_pinned_and_pageable(torch, cfg0):
     ex.close()
 
 
+def test_async_call_matches_and_reports_in_stats(torch, cfg0):
+    """exx_compute_async writes E_xx to device memory with no host wait: two calls
+    queued back to back on one stream give the synchronous call's E_xx bit for bit
+    (fixed-order reduction) and the same D_xx, a kernel the caller queues after
+    the call reads the finished E_xx, and the outcome of a call that hits the
+    iteration cap is in the statistics rather than in its return value."""
+    w, phi, _ = cfg0
+    from paper_1911_10630_gb300.exx import Exx, ExxError
+    dphi = torch.from_numpy(phi).cuda()
+    dcen = torch.from_numpy(np.ascontiguousarray(w.centers)).cuda()
+    ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, deterministic=1)
+    D0 = torch.empty_like(dphi)
+    e0 = ex.compute(dphi, dcen, D0)
+    s = torch.cuda.Stream()
+    E = torch.zeros(2, dtype=torch.float64, device="cuda")
+    D1 = torch.empty_like(dphi)
+    with torch.cuda.stream(s):
+        ex.compute_async(dphi, dcen, D1, E[0:1], stream=s)
+        ex.compute_async(dphi, dcen, D1, E[1:2], stream=s)
+        twice = E * 2.0  # queued after the calls on the same stream
+    s.synchronize()
+    assert E[0].item() == e0 and E[1].item() == e0 and twice[1].item() == 2.0 * e0
+    assert torch.equal(D1, D0)
+    st = ex.stats()
+    assert st["n_pair"] == 36 and st["n_nonconv"] == 0 and st["n_dropped"] == 0
+    ex.close()
+    capped = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, max_iter=5)
+    capped.compute_async(dphi, dcen, D1, E[0:1])
+    assert capped.stats()["n_nonconv"] == 36
+    with pytest.raises(ExxError, match="device"):
+        capped.compute_async(dphi, dcen, D1, torch.zeros(1, dtype=torch.float64))  # host memory
+    capped.close()
+
+
 def test_iteration_cap_reports_nonconvergence(torch, cfg0):
     w, phi, _ = cfg0
     out = run_gpu(w, phi, torch=torch, allow_noconv=True, max_iter=5)
