@@ -37,8 +37,8 @@ def _boxes(phi, w, side):
     return box, org.astype(np.int32), idx
 
 
-@pytest.mark.parametrize("precision", [1, 0])
-def test_boxes_equal_full_grids(torch, precision):
+@pytest.mark.parametrize("precision,preconditioner", [(1, 0), (0, 0), (1, 1), (0, 1)])
+def test_boxes_equal_full_grids(torch, precision, preconditioner):
     from paper_1911_10630_gb300.exx import Exx
     w = synth.tiny(seed=5, n=6, npts=40, length=8.0, r_pe=6, r_me=9, r_pair=3.0, tol=1e-10)
     phi = w.orbitals()
@@ -46,7 +46,8 @@ def test_boxes_equal_full_grids(torch, precision):
     assert side < w.grid[0]
     box, org, idx = _boxes(phi, w, side)
     dcen = torch.from_numpy(np.ascontiguousarray(w.centers)).cuda()
-    ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=precision, deterministic=1)
+    ex = Exx(w.cell, w.grid, w.r_pair, w.r_pe, w.r_me, w.l_max, w.tol, precision=precision, deterministic=1,
+             preconditioner=preconditioner)
     dphi = torch.from_numpy(phi).cuda()
     dD = torch.empty_like(dphi)
     e_full = ex.compute(dphi, dcen, dD)

@@ -553,6 +553,24 @@ def test_multigrid_pcg_anisotropic_ragged(torch, form):
     assert d_maxrel(out["D"], ref["D"]) <= D_GATE_MAXREL
 
 
+@pytest.mark.parametrize("form", [MG_FORMS[1], MG_FORMS[2]], ids=[MG_IDS[1], MG_IDS[2]])
+def test_multigrid_deterministic_dxx_is_bitwise_reproducible(torch, cfg0, form):
+    """With deterministic = 1 the multigrid forms give the same D_xx bit for bit
+    from call to call (order-independent integer accumulation, fixed-order sums
+    within a pair), and the same D_xx as the FP64-atomic mode within roundoff."""
+    w, phi, ref = cfg0
+    a = run_gpu(w, phi, torch=torch, preconditioner=1, deterministic=1, **form)
+    b = run_gpu(w, phi, torch=torch, preconditioner=1, deterministic=1, **form)
+    c = run_gpu(w, phi, torch=torch, preconditioner=1, **form)
+    assert a["E_xx"] == b["E_xx"]
+    np.testing.assert_array_equal(a["D"], b["D"])
+    # each contribution rounds to a multiple of 2^-40 (9.1e-13), and a grid
+    # point sums a few dozen of them: far below 1e-9 of max |D| on this case
+    assert np.max(np.abs(a["D"] - c["D"])) <= 64 * 2.0 ** -40
+    assert d_maxrel(a["D"], c["D"]) <= 1e-9
+    assert d_maxrel(a["D"], ref["D"]) <= D_GATE_MAXREL
+
+
 def test_multigrid_smallest_balls_on_clusters(torch):
     """Self pairs on R_PE/R_ME = 8/12 (levels 8, 4, 2), non-self pairs on 3/7: a
     ball of radius 3 has no coarse level, so the cluster PCG runs those pairs
