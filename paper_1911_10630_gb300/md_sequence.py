@@ -8,9 +8,12 @@ of the exponents; the orbitals are rebuilt on the device between steps
 (untimed). The solver runs the batched mixed-precision path with one of the
 warm starts of exx_options.warm_start: 0 (zero), 1 (the previous step's
 potential of each pair kept from the previous step), 2 (a learned guess) or 3
-(polynomial extrapolation from the last two or three steps).
+(polynomial extrapolation from the last two or three steps). With
+--preconditioner 1 each step is solved from zero by the multigrid-
+preconditioned CG instead (exx_options.preconditioner; it takes no warm start).
 
     python -m paper_1911_10630_gb300.md_sequence --steps 20 --warm 1
+    python -m paper_1911_10630_gb300.md_sequence --steps 20 --warm 0 --preconditioner 1
 """
 from __future__ import annotations
 
@@ -32,14 +35,16 @@ def pair_energies(ex, subset):
     return np.array([pairs["e_pair"][key[p]] if p in key else np.nan for p in subset])
 
 
-def run(steps: int = 20, warm: int = 0, model_blob: bytes = None, seed: int = 0, on_step=None, subset=None):
+def run(steps: int = 20, warm: int = 0, model_blob: bytes = None, seed: int = 0, on_step=None, subset=None,
+        preconditioner: int = 0):
     """Runs the sequence; returns one dict per step (E_xx, pairs, timings, CG
     iterations; with subset, a list of (i, j), also their E_ij as e_sub).
     on_step(step, workload, orbitals, d_xx, exx) is called after each step
     (for checks on the step's outputs)."""
     import torch
     w0 = synth.config4(seed, 0)
-    ex = Exx(w0.cell, w0.grid, w0.r_pair, w0.r_pe, w0.r_me, w0.l_max, w0.tol, precision=1, warm_start=warm)
+    ex = Exx(w0.cell, w0.grid, w0.r_pair, w0.r_pe, w0.r_me, w0.l_max, w0.tol, precision=1, warm_start=warm,
+             preconditioner=preconditioner)
     if warm == 2:
         ex.load_guess_model(model_blob)
     phi = torch.empty((w0.n, int(w0.grid[0]), int(w0.grid[1]), int(w0.grid[2])), dtype=torch.float64, device="cuda")
@@ -78,13 +83,15 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warm", type=int, default=1, choices=[0, 1, 2, 3])
     ap.add_argument("--model", default=None, help="model blob for --warm 2")
+    ap.add_argument("--preconditioner", type=int, default=0, choices=[0, 1],
+                    help="1: the multigrid-preconditioned CG (with --warm 0)")
     args = ap.parse_args()
     blob = open(args.model, "rb").read() if args.model else None
-    recs = run(args.steps, args.warm, blob)
+    recs = run(args.steps, args.warm, blob, preconditioner=args.preconditioner)
     for r in recs:
         print(json.dumps(r), flush=True)
     t = np.array([r["total_ms"] for r in recs[1:]] or [recs[0]["total_ms"]])
-    print(json.dumps({"warm": args.warm, "p50_ms": float(np.percentile(t, 50)), "p99_ms": float(np.percentile(t, 99)),
+    print(json.dumps({"warm": args.warm, "preconditioner": args.preconditioner, "p50_ms": float(np.percentile(t, 50)), "p99_ms": float(np.percentile(t, 99)),
                       "pair_solves_per_s": float(np.mean([r["pair_solves_per_s"] for r in recs[1:]] or [0]))}))
 
 
