@@ -257,7 +257,7 @@ extern "C" exx_options exx_default_options(void) {
     o.deterministic = 0;
     o.max_iter = 20000;
     o.inner_max_iter = 4000;
-    o.inner_tol = 1e-5;
+    o.inner_tol = 0.0;  // library choice
     o.threads = 0;
     o.ctas_per_sm = 0;
     o.solver_kind = 0;
@@ -457,7 +457,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
                     "exx_init: warm_start 1 and 2 run on the cluster solver (precision 1, fixed radii, solver_kind 0 or 2)");
     if (o.max_iter <= 0) o.max_iter = 20000;
     if (o.inner_max_iter <= 0) o.inner_max_iter = 4000;
-    if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) o.inner_tol = 1e-5;
+    if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) o.inner_tol = o.preconditioner == 1 ? 1e-4 : 1e-5;
     if (!(o.update_drop > 0.0 && o.update_drop < 1.0)) o.update_drop = 1e-4;
     if (o.threads != 0 && (o.threads < 256 || o.threads > 1024 || o.threads % 32))
         return fail(nullptr, EXX_EINVAL, "exx_init: threads must be 0 or a multiple of 32 in [256, 1024]");
