@@ -461,64 +461,111 @@ __global__ void skip_back_kernel(const __nv_bfloat16* __restrict__ dpool, const 
     }
 }
 
-// Weight gradient of a 3x3x3 layer: dW[tap][ci][co] = sum over samples and
-// voxels of x[v + tap - 1][ci] g[v][co]; the centre-tap blocks of the first ci
-// block also form the bias gradient. Block = 16 x 16 (ci, co); grid.x = tap,
-// grid.y = ci block, grid.z = co block x voxel split. Each split writes its
-// partial sums to its own slice of part ([split][27 cin cout + cout]), which
-// reduce_parts_kernel adds in split order.
-constexpr int kDwTile = 64;
-__global__ void __launch_bounds__(256) dw_kernel(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ g,
-                                                 float* __restrict__ part, int B, int S, int cin, int cout, int nsplit) {
-    __shared__ float xs[kDwTile][17];
-    __shared__ float gs[kDwTile][17];
-    const int tap = blockIdx.x, cib = blockIdx.y;
-    const int cob = blockIdx.z % (cout / 16), split = blockIdx.z / (cout / 16);
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const long long nv = (long long)B * S * S * S;
-    const long long per = ((nv + nsplit - 1) / nsplit + kDwTile - 1) / kDwTile * kDwTile;
-    const long long v0 = split * per, v1 = v0 + per < nv ? v0 + per : nv;
-    float acc = 0.0f, bacc = 0.0f;
-    const bool do_bias = (tap == 13 && cib == 0);
-    for (long long vt = v0; vt < v1; vt += kDwTile) {
-        {   // 64 voxels x 16 channels of x (shifted) and g: each thread loads 4 channels of one voxel
-            const int vl = threadIdx.x >> 2, cq = (threadIdx.x & 3) * 4;
-            const long long v = vt + vl;
-            float xv[4] = {0, 0, 0, 0}, gv[4] = {0, 0, 0, 0};
-            if (v < v1) {
-                const int xx = (int)(v % S), yy = (int)((v / S) % S), zz = (int)((v / ((long long)S * S)) % S);
-                const long long bb = v / ((long long)S * S * S);
-                const int z2 = zz + dz, y2 = yy + dy, x2 = xx + dx;
-                if (z2 >= 0 && z2 < S && y2 >= 0 && y2 < S && x2 >= 0 && x2 < S) {
-                    const long long u = ((bb * S + z2) * S + y2) * S + x2;
-                    const uint2 q = *reinterpret_cast<const uint2*>(x + u * cin + cib * 16 + cq);
-                    const __nv_bfloat16* qb = reinterpret_cast<const __nv_bfloat16*>(&q);
+// Weight gradient of a 3x3x3 layer, dW[tap][ci][co] = sum over samples and
+// voxels of x[v + tap - 1][ci] g[v][co], all 27 taps in one block: the block
+// stages a voxel tile of one sample (4 x 4 x 8 voxels: a 6 x 6 x 10 halo of x
+// and the tile of g, one 16-channel block of each, in FP32) once, and thread
+// (tap, ci) adds x[v + tap - 1][ci] g[v][0..15] for every voxel of the tile:
+// one x value and a broadcast row of g (every thread of the block reads the
+// same g row) per 16 FMAs. Thread (centre tap, ci 0) of the first ci block also
+// sums g for the bias gradient. Grid: x = voxel-tile split (split s takes the
+// tiles [s T / nsplit, (s + 1) T / nsplit)), y = ci block, z = co block; each
+// split writes its partial sums to its own slice of part ([split][27 cin cout +
+// cout]), which reduce_parts_kernel adds in split order.
+constexpr int kDwD = 4, kDwH = 4, kDwW = 8, kDwVox = kDwD * kDwH * kDwW;
+constexpr int kDwHD = kDwD + 2, kDwHH = kDwH + 2, kDwHW = kDwW + 2, kDwHalo = kDwHD * kDwHH * kDwHW;
+constexpr int kDwThreads = 448;  // 27 taps x 16 ci = 432 accumulate; all stage
+
+__global__ void __launch_bounds__(kDwThreads) dw_kernel(const __nv_bfloat16* __restrict__ x,
+                                                        const __nv_bfloat16* __restrict__ g,
+                                                        float* __restrict__ part, int B, int S, int cin, int cout,
+                                                        int nsplit) {
+    __shared__ float xs[kDwHalo][17];
+    __shared__ __align__(16) float gs[kDwVox][16];
+    const int cib = blockIdx.y, cob = blockIdx.z, split = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int tap = tid >> 4, ci = tid & 15;
+    const bool acc_thread = tid < 27 * 16;
+    const bool bias_thread = cib == 0 && tap == 13 && ci == 0;
+    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // halo offsets of the tap
+    const int td = (S + kDwD - 1) / kDwD, th = (S + kDwH - 1) / kDwH, tw = (S + kDwW - 1) / kDwW;
+    const long long T = (long long)B * td * th * tw;
+    const long long t0 = T * split / nsplit, t1 = T * (split + 1) / nsplit;
+    float acc[16], bacc[16];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) xv[e] = bf2f(qb[e]);
+    for (int k = 0; k < 16; ++k) acc[k] = bacc[k] = 0.0f;
+    for (long long t = t0; t < t1; ++t) {
+        long long r = t;
+        const int iw = (int)(r % tw);
+        r /= tw;
+        const int ih = (int)(r % th);
+        r /= th;
+        const int id = (int)(r % td);
+        const int b = (int)(r / td);
+        const int d0 = id * kDwD, h0 = ih * kDwH, w0 = iw * kDwW;
+        __syncthreads();  // the previous tile's values are no longer read
+        // stage: x halo (each item: 8 channels of one voxel) and the g tile
+        for (int u = tid; u < 2 * kDwHalo + 2 * kDwVox; u += kDwThreads) {
+            const bool isx = u < 2 * kDwHalo;
+            const int uu = isx ? u : u - 2 * kDwHalo;
+            const int half = uu & 1, vx = uu >> 1;
+            int d, h, w;
+            if (isx) {
+                d = d0 - 1 + vx / (kDwHH * kDwHW);
+                h = h0 - 1 + (vx / kDwHW) % kDwHH;
+                w = w0 - 1 + vx % kDwHW;
+            } else {
+                d = d0 + vx / (kDwH * kDwW);
+                h = h0 + (vx / kDwW) % kDwH;
+                w = w0 + vx % kDwW;
+            }
+            float v8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (d >= 0 && d < S && h >= 0 && h < S && w >= 0 && w < S) {
+                const long long vox = (((long long)b * S + d) * S + h) * S + w;
+                const uint4 q = isx ? *reinterpret_cast<const uint4*>(x + vox * cin + cib * 16 + half * 8)
+                                    : *reinterpret_cast<const uint4*>(g + vox * cout + cob * 16 + half * 8);
+                const __nv_bfloat16* qb = reinterpret_cast<const __nv_bfloat16*>(&q);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v8[e] = bf2f(qb[e]);
+            }
+            float* dst = isx ? &xs[vx][half * 8] : &gs[vx][half * 8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) dst[e] = v8[e];
+        }
+        __syncthreads();
+        if (acc_thread) {
+#pragma unroll 4
+            for (int v = 0; v < kDwVox; ++v) {
+                const int vd = v / (kDwH * kDwW), vh = (v / kDwW) % kDwH, vw = v % kDwW;
+                const float xv = xs[((vd + dz) * kDwHH + (vh + dy)) * kDwHW + (vw + dx)][ci];
+                const float4* gr = reinterpret_cast<const float4*>(gs[v]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 gq = gr[q];
+                    acc[4 * q + 0] = fmaf(xv, gq.x, acc[4 * q + 0]);
+                    acc[4 * q + 1] = fmaf(xv, gq.y, acc[4 * q + 1]);
+                    acc[4 * q + 2] = fmaf(xv, gq.z, acc[4 * q + 2]);
+                    acc[4 * q + 3] = fmaf(xv, gq.w, acc[4 * q + 3]);
+                    if (bias_thread) {
+                        bacc[4 * q + 0] += gq.x;
+                        bacc[4 * q + 1] += gq.y;
+                        bacc[4 * q + 2] += gq.z;
+                        bacc[4 * q + 3] += gq.w;
+                    }
                 }
-                const uint2 r = *reinterpret_cast<const uint2*>(g + v * cout + cob * 16 + cq);
-                const __nv_bfloat16* rb = reinterpret_cast<const __nv_bfloat16*>(&r);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) gv[e] = bf2f(rb[e]);
-            }
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                xs[vl][cq + e] = xv[e];
-                gs[vl][cq + e] = gv[e];
             }
         }
-        __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < kDwTile; ++k) {
-            acc = fmaf(xs[k][ty], gs[k][tx], acc);
-            if (do_bias && ty == 0) bacc += gs[k][tx];
-        }
-        __syncthreads();
     }
-    float* dw = part + (size_t)split * ((size_t)27 * cin * cout + cout);
-    dw[((size_t)tap * cin + cib * 16 + ty) * cout + cob * 16 + tx] = acc;
-    if (do_bias && ty == 0) dw[(size_t)27 * cin * cout + cob * 16 + tx] = bacc;
+    if (acc_thread) {
+        float* dw = part + (size_t)split * ((size_t)27 * cin * cout + cout);
+        float* row = dw + ((size_t)tap * cin + cib * 16 + ci) * cout + cob * 16;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) row[k] = acc[k];
+        if (bias_thread) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) dw[(size_t)27 * cin * cout + cob * 16 + k] = bacc[k];
+        }
+    }
 }
 
 // Weight gradient of the FP32 input layer: 27 x kIn x 16 weights and 16
@@ -663,13 +710,13 @@ cudaError_t conv3_tc(const __nv_bfloat16* x, const __nv_bfloat16* wp, const floa
 
 // ---- network driver --------------------------------------------------------
 
-// Voxel splits of a weight-gradient launch: about 8192 voxels per split, at
-// most 64 blocks per SM in all.
-static int dw_splits(long long nv, int cin, int cout, int n_sm) {
-    int nsplit = (int)((nv + 8191) / 8192);
-    const int blocks = 27 * (cin / 16) * (cout / 16);
-    while (nsplit > 1 && (long long)blocks * nsplit > 64LL * n_sm) --nsplit;
-    return nsplit;
+// Voxel-tile splits of a weight-gradient launch: about eight blocks per SM
+// over the (ci, co) blocks, and no split without a tile.
+static int dw_splits(int B, int S, int cin, int cout, int n_sm) {
+    const long long tiles = (long long)B * ((S + kDwD - 1) / kDwD) * ((S + kDwH - 1) / kDwH) * ((S + kDwW - 1) / kDwW);
+    const long long cb = (long long)(cin / 16) * (cout / 16);
+    const long long want = std::max(1LL, 8LL * n_sm / cb);
+    return (int)std::max(1LL, std::min(tiles, want));
 }
 
 cudaError_t create(Net& n, int S, int Bmax) {
@@ -745,11 +792,9 @@ cudaError_t create(Net& n, int S, int Bmax) {
         size_t need = (size_t)18 * 16 * n.n_sm;
         need = std::max(need, (size_t)4 * n.n_sm * (27 * kIn * 16 + 16));
         const int lvl[kLayers] = {0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0, 0};
-        for (int l = 1; l < kHead; ++l) {
-            const long long nv = (long long)v0 >> (3 * lvl[l]);
-            need = std::max(need, (size_t)dw_splits(nv, kCin[l], kCout[l], n.n_sm) *
+        for (int l = 1; l < kHead; ++l)
+            need = std::max(need, (size_t)dw_splits(Bmax, S >> lvl[l], kCin[l], kCout[l], n.n_sm) *
                                       ((size_t)27 * kCin[l] * kCout[l] + kCout[l]));
-        }
         UCK(alloc((void**)&n.gpart, need * 4));
     }
     UCK(alloc((void**)&n.d_loss, 4));
@@ -829,11 +874,10 @@ cudaError_t backward(Net& n, const float* in, const float* target, int B, cudaSt
                         n.n_sm, st);
     };
     auto dweight = [&](const __nv_bfloat16* x, const __nv_bfloat16* g, int l, int s) {
-        const long long nv = (long long)B * s * s * s;
-        const int nsplit = dw_splits(nv, kCin[l], kCout[l], n.n_sm);
-        dim3 grid(27, kCin[l] / 16, (kCout[l] / 16) * nsplit);
+        const int nsplit = dw_splits(B, s, kCin[l], kCout[l], n.n_sm);
+        dim3 grid(nsplit, kCin[l] / 16, kCout[l] / 16);
         const int count = 27 * kCin[l] * kCout[l] + kCout[l];
-        dw_kernel<<<grid, 256, 0, st>>>(x, g, n.gpart, B, s, kCin[l], kCout[l], nsplit);
+        dw_kernel<<<grid, kDwThreads, 0, st>>>(x, g, n.gpart, B, s, kCin[l], kCout[l], nsplit);
         reduce_parts_kernel<<<grid_for(count, n.n_sm), 256, 0, st>>>(n.gpart, nsplit, count, count,
                                                                      n.grads + param_offset(l));
         return cudaGetLastError();
