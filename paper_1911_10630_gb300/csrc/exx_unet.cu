@@ -534,26 +534,30 @@ __global__ void __launch_bounds__(kDwThreads) dw_kernel(const __nv_bfloat16* __r
         }
         __syncthreads();
         if (acc_thread) {
-#pragma unroll 4
-            for (int v = 0; v < kDwVox; ++v) {
-                const int vd = v / (kDwH * kDwW), vh = (v / kDwW) % kDwH, vw = v % kDwW;
-                const float xv = xs[((vd + dz) * kDwHH + (vh + dy)) * kDwHW + (vw + dx)][ci];
-                const float4* gr = reinterpret_cast<const float4*>(gs[v]);
+            // row by row of the tile: the tap's halo row, then 8 voxels along w
+            for (int vd = 0; vd < kDwD; ++vd)
+                for (int vh = 0; vh < kDwH; ++vh) {
+                    const float* xrow = &xs[((vd + dz) * kDwHH + (vh + dy)) * kDwHW + dx][ci];
+                    const float4* grow = reinterpret_cast<const float4*>(gs[(vd * kDwH + vh) * kDwW]);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 gq = gr[q];
-                    acc[4 * q + 0] = fmaf(xv, gq.x, acc[4 * q + 0]);
-                    acc[4 * q + 1] = fmaf(xv, gq.y, acc[4 * q + 1]);
-                    acc[4 * q + 2] = fmaf(xv, gq.z, acc[4 * q + 2]);
-                    acc[4 * q + 3] = fmaf(xv, gq.w, acc[4 * q + 3]);
-                    if (bias_thread) {
-                        bacc[4 * q + 0] += gq.x;
-                        bacc[4 * q + 1] += gq.y;
-                        bacc[4 * q + 2] += gq.z;
-                        bacc[4 * q + 3] += gq.w;
+                    for (int vw = 0; vw < kDwW; ++vw) {
+                        const float xv = xrow[vw * 17];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float4 gq = grow[vw * 4 + q];
+                            acc[4 * q + 0] = fmaf(xv, gq.x, acc[4 * q + 0]);
+                            acc[4 * q + 1] = fmaf(xv, gq.y, acc[4 * q + 1]);
+                            acc[4 * q + 2] = fmaf(xv, gq.z, acc[4 * q + 2]);
+                            acc[4 * q + 3] = fmaf(xv, gq.w, acc[4 * q + 3]);
+                            if (bias_thread) {
+                                bacc[4 * q + 0] += gq.x;
+                                bacc[4 * q + 1] += gq.y;
+                                bacc[4 * q + 2] += gq.z;
+                                bacc[4 * q + 3] += gq.w;
+                            }
+                        }
                     }
                 }
-            }
         }
     }
     if (acc_thread) {
