@@ -316,18 +316,22 @@ def test_iteration_cap_reports_nonconvergence(torch, cfg0):
     assert np.isfinite(out["E_xx"])
 
 
-@pytest.mark.parametrize("precision,lane_map,preconditioner", [(1, None, 1), (1, None, 0), (1, 2, 0), (1, 3, 0),
-                                                                (1, 4, 0), (1, 5, 0), (0, None, 0)])
-def test_water64_full_size_sampled(torch, precision, lane_map, preconditioner):
+@pytest.mark.parametrize("precision,lane_map,preconditioner,cluster", [
+    (1, None, 1, 0), (1, None, 1, 2), (1, None, 0, 0), (1, 2, 0, 0), (1, 3, 0, 0), (1, 4, 0, 0), (1, 5, 0, 0),
+    (0, None, 0, 0)])
+def test_water64_full_size_sampled(torch, precision, lane_map, preconditioner, cluster):
     """The bench workload (water-64 scale, 120^3, 256 orbitals, R_pair = 10 bohr,
     R_PE/R_ME = 24/32, tol 1e-8) in the configuration bench.py times (the FP32
     multigrid PCG in FP64 refinement, one CTA per pair), on the autotuned cluster
-    solver and with its z-run and quad thread maps forced; checked on sampled
-    pairs and sampled orbitals the oracle computes one by one."""
+    solver and with its z-run and quad thread maps forced, and the multigrid CG
+    on 2-CTA clusters; checked on sampled pairs and sampled orbitals the oracle
+    computes one by one."""
     w = synth.config1()
     phi = w.orbitals()
     extra = {} if lane_map is None else dict(lane_map=lane_map, autotune=0)
     extra["preconditioner"] = preconditioner
+    if cluster:  # the multigrid CG on clusters of this size
+        extra.update(solver_kind=2, cluster_size=cluster)
     out = run_gpu(w, phi, torch=torch, precision=precision, **extra)
     if lane_map is not None:
         assert out["stats"]["lane_map"] == lane_map
