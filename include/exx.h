@@ -99,7 +99,7 @@ typedef struct {
     int threads;       /* threads per CTA, 0 = library choice, else a multiple of
                           32 in [256, 1024]; the one-CTA solver runs 256, 512
                           or 1024 (other values: the library choice, 512, or
-                          256 for the FP32 multigrid CG, which then keeps four
+                          256 for the FP32 multigrid CG, which then keeps five
                           CTAs per SM), the cluster solver only the launch
                           shapes it is built for.                               */
     int ctas_per_sm;   /* resident CTAs per SM, 0 = library choice (the

@@ -933,7 +933,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         return bail(fail(c, EXX_EINVAL, "exx_init: warm_start 1 and 2 need the cluster solver, which does not fit these radii"));
     if (c->use_cluster) apply_cand(c, c->cand);
 
-    // one CTA per pair: 512 threads, or 256 (four CTAs per SM, measured fastest) for the FP32 multigrid CG
+    // one CTA per pair: 512 threads, or 256 (five CTAs per SM, measured fastest) for the FP32 multigrid CG
     const int def_threads = (o.preconditioner == 1 && o.precision == 1) ? 256 : 512;
     c->threads = c->use_cluster ? c->threads
                                 : ((o.threads == 256 || o.threads == 512 || o.threads == 1024) ? o.threads : def_threads);
@@ -960,9 +960,10 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         e = pair_kernel_occupancy(c->threads, o.precision == 1, o.preconditioner == 1, c->smem, &bps);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
         if (bps < 1) return bail(fail(c, EXX_ECUDA, "pair kernel does not fit on an SM"));
-        // all resident (the launch bounds allow two CTAs per SM, four for the
-        // 256-thread multigrid kernel)
-        int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, bps) : std::min(bps, 4);
+        // all resident (the launch bounds allow two CTAs per SM, five for the
+        // 256-thread FP32 multigrid kernel)
+        const int cap = (o.preconditioner == 1 && o.precision == 1) ? 5 : 4;
+        int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, bps) : std::min(bps, cap);
         want = (long long)c->num_sms * per_sm;
     }
     size_t free_b = 0, total_b = 0;

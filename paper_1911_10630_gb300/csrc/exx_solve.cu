@@ -144,8 +144,17 @@ __device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const
 // --------------------------------------------------------------------------
 // The persistent pair kernel.
 // --------------------------------------------------------------------------
+// Resident CTAs per SM the launch bounds ask for: two of the FP64 and the
+// 512-thread kernels; for the multigrid kernels 1024 threads per SM, except
+// the 256-thread FP32 one, which takes five CTAs (1280 threads, 48 registers):
+// the sweeps wait on DRAM, and the fifth CTA's loads in flight outweigh the
+// spills of its setup and finish phases (measured: 4 CTAs 0.580 s, 5 0.566,
+// 6 0.616 on the water-64 workload).
+template <int NT>
+constexpr int mg_min_blocks() { return NT == 256 ? 5 : 1024 / NT; }
+
 template <int NT, bool MIXED, bool MG = false>
-__global__ void __launch_bounds__(NT, MG ? 1024 / NT : (MIXED ? 1 : 2)) pair_kernel(const __grid_constant__ SolveParams P) {
+__global__ void __launch_bounds__(NT, MG ? mg_min_blocks<NT>() : (MIXED ? 1 : 2)) pair_kernel(const __grid_constant__ SolveParams P) {
     extern __shared__ double smem[];
     __shared__ double red[2][33];
     __shared__ float red32[2][33];
@@ -377,7 +386,7 @@ static cudaError_t launch_t(const SolveParams& P, int grid, size_t smem, cudaStr
 }
 
 cudaError_t launch_pair_kernel(const SolveParams& P, int threads, bool mixed, int grid, size_t smem, cudaStream_t st) {
-    if (P.mg) {  // the multigrid-preconditioned CG (64 registers): FP64, or FP32 inside FP64 refinement
+    if (P.mg) {  // the multigrid-preconditioned CG: FP64, or FP32 inside FP64 refinement
         if (!mixed) pair_kernel<512, false, true><<<grid, 512, smem, st>>>(P);
         else if (threads == 256) pair_kernel<256, true, true><<<grid, 256, smem, st>>>(P);
         else if (threads == 1024) pair_kernel<1024, true, true><<<grid, 1024, smem, st>>>(P);
