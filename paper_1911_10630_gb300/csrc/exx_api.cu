@@ -1034,6 +1034,24 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         P.st32.cy[q] = (float)P.st64.cy[q];
         P.st32.cz[q] = (float)P.st64.cz[q];
     }
+    for (int l = 0; l <= kMGMax; ++l) {
+        const double s64 = std::ldexp(1.0, -2 * l);
+        const float s32 = (float)s64;
+        Stencil<double>& a = P.mg_a64[l];
+        Stencil<float>& b = P.mg_a32[l];
+        a.c0 = -P.st64.c0 * s64;
+        b.c0 = -P.st32.c0 * s32;
+        for (int q = 0; q < 3; ++q) {
+            a.cx[q] = -P.st64.cx[q] * s64;
+            a.cy[q] = -P.st64.cy[q] * s64;
+            a.cz[q] = -P.st64.cz[q] * s64;
+            b.cx[q] = -P.st32.cx[q] * s32;
+            b.cy[q] = -P.st32.cy[q] * s32;
+            b.cz[q] = -P.st32.cz[q] * s32;
+        }
+        P.mg_wd64[l] = P.mg_omega / a.c0;
+        P.mg_wd32[l] = (float)P.mg_omega / b.c0;
+    }
     P.geos = c->d_geos;
     P.n_geo = c->n_geo;
     P.S = S;

@@ -1539,7 +1539,7 @@ __device__ __noinline__ float cluster_mg_precondition(const SolveParams& P, cons
     const MGView<float> v0 = mg_view<float>(P, G, M, slot, 0, r);
     const int n1 = M.lv[1].n;
     cl.sync();  // Z
-    mg_residual(v0, kb, k1, NT);
+    mg_residual(P, v0, kb, k1, NT);
     cl.sync();  // Tc
     mg_restrict(v0, M.lv[1], n1 * rank / C + (int)threadIdx.x, n1 * (rank + 1) / C, NT);
     cl.sync();  // level-1 right-hand side
@@ -1548,7 +1548,7 @@ __device__ __noinline__ float cluster_mg_precondition(const SolveParams& P, cons
     const MGView<float> v1 = mg_view<float>(P, G, M, slot, 1, r);
     mg_prolong(v0, v1, M.L == 1 ? v1.Z : v1.Tc, kb, k1, NT);
     cl.sync();  // Z
-    return mg_smooth(v0, (float)P.mg_omega, kb, k1, NT);
+    return mg_smooth(P, v0, kb, k1, NT);
 }
 
 // One inner solve of the refinement loop: the FP32 PCG for A d = r64 / rn on

@@ -125,6 +125,13 @@ struct SolveParams {
     // multigrid-preconditioned CG (one-CTA FP64 solver): per geometry, NULL = plain CG
     const MGGeo* mg;
     double mg_omega;          // weight of the Jacobi smoothing sweeps
+    // per level l: -lap at spacing 2^l delta (the negated weights of Eq. d2_1
+    // times 4^-l, exact in either precision) and the Jacobi factor omega over
+    // its diagonal; in the parameters, the sweeps read them as constants
+    Stencil<double> mg_a64[kMGMax + 1];
+    Stencil<float> mg_a32[kMGMax + 1];
+    double mg_wd64[kMGMax + 1];
+    float mg_wd32[kMGMax + 1];
     size_t off_zc, off_tc;    // level-0 cubes (the workspace cube's size): smoothed correction, residual
     size_t off_mgz[kMGMax + 1], off_mgt[kMGMax + 1], off_mgr[kMGMax + 1];  // levels 1..: cubes and right-hand side
     const double* pow_tab;  // [3][2 Rc + 1][8] x^e, y^e, z^e (cluster kernel; global, read-only)

@@ -35,8 +35,21 @@ struct MGView {
     T* Tc;             // residual, then the post-smoothed correction (cube)
     const T* rhs;      // right-hand side (compact)
     T* rnext;          // the next level's right-hand side (compact), NULL on the coarsest
-    Stencil<T> A;      // -lap at the level's spacing
+    int l;             // level (its operator: mg_stencil)
 };
+
+// -lap at level l's spacing and the Jacobi factor omega / diagonal, read from
+// the kernel parameters (the caller passes the kernel's own parameter block).
+template <typename T>
+__device__ __forceinline__ const Stencil<T>& mg_stencil(const SolveParams& P, int l) {
+    if constexpr (sizeof(T) == 8) return P.mg_a64[l];
+    else return P.mg_a32[l];
+}
+template <typename T>
+__device__ __forceinline__ T mg_wd(const SolveParams& P, int l) {
+    if constexpr (sizeof(T) == 8) return P.mg_wd64[l];
+    else return P.mg_wd32[l];
+}
 
 template <typename T>
 __device__ __forceinline__ long long mg_idx(const MGView<T>& v, int x, int y, int z) {
@@ -49,9 +62,7 @@ template <typename T>
 __device__ __forceinline__ MGView<T> mg_view(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot,
                                              int l, const T* r0) {
     MGView<T> v;
-    Stencil<T> base;
-    if constexpr (sizeof(T) == 8) base = negated(P.st64);
-    else base = negated(P.st32);
+    v.l = l;
     if (l == 0) {
         v.cube = G.pt_cube;
         v.off = G.pt_off;
@@ -62,7 +73,6 @@ __device__ __forceinline__ MGView<T> mg_view(const SolveParams& P, const BallGeo
         v.Z = reinterpret_cast<T*>(slot + P.off_zc);
         v.Tc = reinterpret_cast<T*>(slot + P.off_tc);
         v.rhs = r0;
-        v.A = base;
     } else {
         const MGLevel& lv = M.lv[l];
         v.cube = lv.cube;
@@ -74,14 +84,6 @@ __device__ __forceinline__ MGView<T> mg_view(const SolveParams& P, const BallGeo
         v.Z = reinterpret_cast<T*>(slot + P.off_mgz[l]);
         v.Tc = reinterpret_cast<T*>(slot + P.off_mgt[l]);
         v.rhs = reinterpret_cast<const T*>(slot + P.off_mgr[l]);
-        const T sc = (T)ldexp(1.0, -2 * l);  // spacing 2^l delta
-        v.A = base;
-        v.A.c0 *= sc;
-        for (int q = 0; q < 3; ++q) {
-            v.A.cx[q] *= sc;
-            v.A.cy[q] *= sc;
-            v.A.cz[q] *= sc;
-        }
     }
     v.rnext = l < M.L ? reinterpret_cast<T*>(slot + P.off_mgr[l + 1]) : nullptr;
     return v;
@@ -89,8 +91,8 @@ __device__ __forceinline__ MGView<T> mg_view(const SolveParams& P, const BallGeo
 
 // Jacobi from zero: Z = w D^-1 rhs.
 template <typename T>
-__device__ __forceinline__ void mg_jacobi0(const MGView<T>& v, T w, int kb, int ke, int step) {
-    const T wd = w / v.A.c0;
+__device__ __forceinline__ void mg_jacobi0(const SolveParams& P, const MGView<T>& v, int kb, int ke, int step) {
+    const T wd = mg_wd<T>(P, v.l);
     const int* __restrict__ cube = v.cube;
     const T* __restrict__ rhs = v.rhs;
     T* __restrict__ Zs = v.Z;
@@ -100,7 +102,8 @@ __device__ __forceinline__ void mg_jacobi0(const MGView<T>& v, T w, int kb, int 
 
 // Residual into Tc: rhs - A Z.
 template <typename T>
-__device__ __forceinline__ void mg_residual(const MGView<T>& v, int kb, int ke, int step) {
+__device__ __forceinline__ void mg_residual(const SolveParams& P, const MGView<T>& v, int kb, int ke, int step) {
+    const Stencil<T>& A = mg_stencil<T>(P, v.l);
     const int* __restrict__ cube = v.cube;
     const T* __restrict__ rhs = v.rhs;
     const T* __restrict__ Zs = v.Z;
@@ -108,7 +111,7 @@ __device__ __forceinline__ void mg_residual(const MGView<T>& v, int kb, int ke, 
 #pragma unroll (kMGUnroll)
     for (int k = kb; k < ke; k += step) {
         const int c = cube[k];
-        Tcs[c] = rhs[k] - lap19<T>(Zs, c, v.S, v.S2, v.A);
+        Tcs[c] = rhs[k] - lap19<T>(Zs, c, v.S, v.S2, A);
     }
 }
 
@@ -184,8 +187,9 @@ __device__ __forceinline__ void mg_prolong(const MGView<T>& v, const MGView<T>& 
 // Post-smoothing: Tc = Z + w D^-1 (rhs - A Z); returns this thread's sum of
 // rhs . Tc (on level 0: r . z for the PCG).
 template <typename T>
-__device__ __forceinline__ T mg_smooth(const MGView<T>& v, T w, int kb, int ke, int step) {
-    const T wd = w / v.A.c0;
+__device__ __forceinline__ T mg_smooth(const SolveParams& P, const MGView<T>& v, int kb, int ke, int step) {
+    const T wd = mg_wd<T>(P, v.l);
+    const Stencil<T>& A = mg_stencil<T>(P, v.l);
     const int* __restrict__ cube = v.cube;
     const T* __restrict__ rhs = v.rhs;
     const T* __restrict__ Zs = v.Z;
@@ -194,7 +198,7 @@ __device__ __forceinline__ T mg_smooth(const MGView<T>& v, T w, int kb, int ke, 
 #pragma unroll (kMGUnroll)
     for (int k = kb; k < ke; k += step) {
         const int c = cube[k];
-        const T t = fma(wd, rhs[k] - lap19<T>(Zs, c, v.S, v.S2, v.A), Zs[c]);
+        const T t = fma(wd, rhs[k] - lap19<T>(Zs, c, v.S, v.S2, A), Zs[c]);
         Tcs[c] = t;
         rz = fma(rhs[k], t, rz);
     }
@@ -209,17 +213,16 @@ __device__ __forceinline__ T mg_smooth(const MGView<T>& v, T w, int kb, int ke, 
 // has already written level l0's first Jacobi sweep (Z = w D^-1 rhs) and
 // synchronised. Returns this thread's share of rhs . z on level l0.
 template <int NT, typename T>
-__device__ __noinline__ T mg_vcycle(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot,
-                                    const T* __restrict__ r0, int l0 = 0, bool z0_ready = false) {
-    const T w = (T)P.mg_omega;
+__device__ __forceinline__ T mg_vcycle(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot,
+                                       const T* __restrict__ r0, int l0 = 0, bool z0_ready = false) {
     const int t = threadIdx.x;
     for (int l = l0; l < M.L; ++l) {
         const MGView<T> v = mg_view<T>(P, G, M, slot, l, r0);
         if (!(l == l0 && z0_ready)) {
-            mg_jacobi0(v, w, t, v.n, NT);
+            mg_jacobi0(P, v, t, v.n, NT);
             __syncthreads();
         }
-        mg_residual(v, t, v.n, NT);
+        mg_residual(P, v, t, v.n, NT);
         __syncthreads();
         mg_restrict(v, M.lv[l + 1], t, M.lv[l + 1].n, NT);
         __syncthreads();
@@ -237,7 +240,7 @@ __device__ __noinline__ T mg_vcycle(const SolveParams& P, const BallGeo& G, cons
         const MGView<T> v = mg_view<T>(P, G, M, slot, l, r0), vc = mg_view<T>(P, G, M, slot, l + 1, r0);
         mg_prolong(v, vc, (l + 1 == M.L) ? vc.Z : vc.Tc, t, v.n, NT);
         __syncthreads();
-        rz = mg_smooth(v, w, t, v.n, NT);
+        rz = mg_smooth(P, v, t, v.n, NT);
         __syncthreads();
     }
     return rz;

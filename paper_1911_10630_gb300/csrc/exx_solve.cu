@@ -83,18 +83,16 @@ __device__ int cg_ball(T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d,
 //   recurrence and the V-cycle in FP32 on the normalised residual, the stop
 //   test of the refinement loop on the FP64 residual.
 template <int NT, typename T>
-__device__ __noinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot,
-                                   T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d, T* __restrict__ ap, T rr,
-                                   T target2, int max_iter, T (*red)[33], int& flip, T& rr_out) {
+__device__ __forceinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot,
+                                      T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d, T* __restrict__ ap, T rr,
+                                      T target2, int max_iter, T (*red)[33], int& flip, T& rr_out) {
     const int* cube = G.pt_cube;
     const int n_pe = G.n_pe, S = P.S;
     const long long S2 = P.S2;
-    Stencil<T> A;
-    if constexpr (sizeof(T) == 8) A = negated(P.st64);
-    else A = negated(P.st32);
+    const Stencil<T>& A = mg_stencil<T>(P, 0);
     const T* __restrict__ Z = reinterpret_cast<const T*>(slot + P.off_tc);  // z = M r (level-0 cube)
     T* __restrict__ Zj = reinterpret_cast<T*>(slot + P.off_zc);             // the V-cycle's first Jacobi sweep
-    const T wd = (T)P.mg_omega / A.c0;
+    const T wd = mg_wd<T>(P, 0);
     T rz = block_sum<NT, T>(mg_vcycle<NT, T>(P, G, M, slot, r), red, flip);
     for (int k = threadIdx.x; k < n_pe; k += NT) {
         const int c = cube[k];
