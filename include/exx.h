@@ -99,9 +99,9 @@ typedef struct {
     int threads;       /* threads per CTA, 0 = library choice, else a multiple of
                           32 in [256, 1024]; the one-CTA solver runs 256, 512
                           or 1024 (other values: the library choice, 512, or
-                          256 for the FP32 multigrid CG, which then keeps five
-                          CTAs per SM), the cluster solver only the launch
-                          shapes it is built for.                               */
+                          256 for the FP32 multigrid CG, which then keeps six
+                          CTAs per SM, five with per-pair radii), the cluster
+                          solver only the launch shapes it is built for.      */
     int ctas_per_sm;   /* resident CTAs per SM, 0 = library choice (the
                           multigrid CG on clusters: 1 or 2, default 2).         */
     int solver_kind;   /* 0 = library choice; 1 = one CTA per pair with state in

@@ -36,7 +36,7 @@ cudaError_t set_multipole_const_solve(const MultipoleConst& mc);
 cudaError_t set_multipole_const_cluster(const MultipoleConst& mc);
 size_t pair_kernel_smem(int Rc, int r_pe_max);
 cudaError_t launch_pair_kernel(const SolveParams& P, int threads, bool mixed, int grid, size_t smem, cudaStream_t st);
-cudaError_t pair_kernel_occupancy(int threads, bool mixed, bool mg, size_t smem, int* blocks_per_sm);
+cudaError_t pair_kernel_occupancy(int threads, bool mixed, bool mg, bool one_ball, size_t smem, int* blocks_per_sm);
 cudaError_t launch_debug_readback(const SolveParams& P, const PairRec& pr, double* rho_me, double* v_me,
                                   cudaStream_t st);
 cudaError_t launch_apply(const SolveParams& P, const double* p, double* ap, cudaStream_t st);
@@ -933,7 +933,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         return bail(fail(c, EXX_EINVAL, "exx_init: warm_start 1 and 2 need the cluster solver, which does not fit these radii"));
     if (c->use_cluster) apply_cand(c, c->cand);
 
-    // one CTA per pair: 512 threads, or 256 (five CTAs per SM, measured fastest) for the FP32 multigrid CG
+    // one CTA per pair: 512 threads, or 256 (five or six CTAs per SM, measured fastest) for the FP32 multigrid CG
     const int def_threads = (o.preconditioner == 1 && o.precision == 1) ? 256 : 512;
     c->threads = c->use_cluster ? c->threads
                                 : ((o.threads == 256 || o.threads == 512 || o.threads == 1024) ? o.threads : def_threads);
@@ -947,7 +947,7 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         want = c->mg_clusters;
     } else if (c->per_class) {
         // the classes of a lane run one after another and share its slots
-        e = pair_kernel_occupancy(c->threads, true, false, c->smem, &bps);
+        e = pair_kernel_occupancy(c->threads, true, false, c->n_geo == 1, c->smem, &bps);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
         for (int g = 0; g < c->n_geo; ++g) {
             const exx_ctx::RadiusClass& RC = c->classes[g];
@@ -957,12 +957,12 @@ extern "C" exx_status exx_init(exx_ctx** out, const double cell[3], const int gr
         }
         want = (long long)c->lane_slots[0] + c->lane_slots[1];
     } else {
-        e = pair_kernel_occupancy(c->threads, o.precision == 1, o.preconditioner == 1, c->smem, &bps);
+        e = pair_kernel_occupancy(c->threads, o.precision == 1, o.preconditioner == 1, c->n_geo == 1, c->smem, &bps);
         if (e != cudaSuccess) return bail(cuda_fail(c, e, "occupancy query"));
         if (bps < 1) return bail(fail(c, EXX_ECUDA, "pair kernel does not fit on an SM"));
-        // all resident (the launch bounds allow two CTAs per SM, five for the
-        // 256-thread FP32 multigrid kernel)
-        const int cap = (o.preconditioner == 1 && o.precision == 1) ? 5 : 4;
+        // all resident (the launch bounds allow two CTAs per SM; the 256-thread
+        // FP32 multigrid kernel six on one ball, five with per-pair radii)
+        const int cap = (o.preconditioner == 1 && o.precision == 1) ? (c->n_geo == 1 ? 6 : 5) : 4;
         int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, bps) : std::min(bps, cap);
         want = (long long)c->num_sms * per_sm;
     }

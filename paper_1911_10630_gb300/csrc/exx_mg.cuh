@@ -17,13 +17,14 @@
 // (kb = threadIdx.x, step = NT), a cluster gives each CTA a range of them.
 #pragma once
 
-#include "exx_phases.cuh"  // negated()
+#include "exx_kernels.cuh"  // lap19, off_x / off_y / off_z
 
 namespace exx {
 
-// Points per thread in flight in a stage's loop (loop unrolling over
-// restrict-qualified arrays lets the loads of several points overlap).
-constexpr int kMGUnroll = 2;
+// U: unrolling of a stage's loop over its points (over restrict-qualified
+// arrays the loads of the unrolled points overlap, at the price of registers).
+// The default, 2, is the cluster kernels'; the one-CTA kernel picks its own
+// by its residency.
 
 template <typename T>
 struct MGView {
@@ -90,25 +91,25 @@ __device__ __forceinline__ MGView<T> mg_view(const SolveParams& P, const BallGeo
 }
 
 // Jacobi from zero: Z = w D^-1 rhs.
-template <typename T>
+template <typename T, int U = 2>
 __device__ __forceinline__ void mg_jacobi0(const SolveParams& P, const MGView<T>& v, int kb, int ke, int step) {
     const T wd = mg_wd<T>(P, v.l);
     const int* __restrict__ cube = v.cube;
     const T* __restrict__ rhs = v.rhs;
     T* __restrict__ Zs = v.Z;
-#pragma unroll (kMGUnroll)
+#pragma unroll (U)
     for (int k = kb; k < ke; k += step) Zs[cube[k]] = wd * rhs[k];
 }
 
 // Residual into Tc: rhs - A Z.
-template <typename T>
+template <typename T, int U = 2>
 __device__ __forceinline__ void mg_residual(const SolveParams& P, const MGView<T>& v, int kb, int ke, int step) {
     const Stencil<T>& A = mg_stencil<T>(P, v.l);
     const int* __restrict__ cube = v.cube;
     const T* __restrict__ rhs = v.rhs;
     const T* __restrict__ Zs = v.Z;
     T* __restrict__ Tcs = v.Tc;
-#pragma unroll (kMGUnroll)
+#pragma unroll (U)
     for (int k = kb; k < ke; k += step) {
         const int c = cube[k];
         Tcs[c] = rhs[k] - lap19<T>(Zs, c, v.S, v.S2, A);
@@ -116,12 +117,12 @@ __device__ __forceinline__ void mg_residual(const SolveParams& P, const MGView<T
 }
 
 // Full weighting of Tc onto the points kb.. of the next level cl (its rhs).
-template <typename T>
+template <typename T, int U = 2>
 __device__ __forceinline__ void mg_restrict(const MGView<T>& v, const MGLevel& cl, int kb, int ke, int step) {
     const int* __restrict__ off = cl.off;
     const T* __restrict__ Tcs = v.Tc;
     T* __restrict__ rn = v.rnext;
-#pragma unroll (kMGUnroll)
+#pragma unroll (U)
     for (int k = kb; k < ke; k += step) {
         const int pk = off[k];
         const int X = 2 * off_x(pk), Y = 2 * off_y(pk), Z = 2 * off_z(pk);
@@ -151,14 +152,14 @@ __device__ __forceinline__ void mg_bottom(const MGView<T>& v, const T* minv, int
 }
 
 // Z += P zc: trilinear prolongation of the coarser correction zc (level vc's cube).
-template <typename T>
+template <typename T, int U = 2>
 __device__ __forceinline__ void mg_prolong(const MGView<T>& v, const MGView<T>& vc, const T* zc, int kb, int ke,
                                            int step) {
     const int* __restrict__ off = v.off;
     const int* __restrict__ cube = v.cube;
     T* __restrict__ Zs = v.Z;
     const T* __restrict__ zcs = zc;
-#pragma unroll (kMGUnroll)
+#pragma unroll (U)
     for (int k = kb; k < ke; k += step) {
         const int pk = off[k];
         const int o[3] = {off_x(pk), off_y(pk), off_z(pk)};
@@ -186,7 +187,7 @@ __device__ __forceinline__ void mg_prolong(const MGView<T>& v, const MGView<T>& 
 
 // Post-smoothing: Tc = Z + w D^-1 (rhs - A Z); returns this thread's sum of
 // rhs . Tc (on level 0: r . z for the PCG).
-template <typename T>
+template <typename T, int U = 2>
 __device__ __forceinline__ T mg_smooth(const SolveParams& P, const MGView<T>& v, int kb, int ke, int step) {
     const T wd = mg_wd<T>(P, v.l);
     const Stencil<T>& A = mg_stencil<T>(P, v.l);
@@ -195,7 +196,7 @@ __device__ __forceinline__ T mg_smooth(const SolveParams& P, const MGView<T>& v,
     const T* __restrict__ Zs = v.Z;
     T* __restrict__ Tcs = v.Tc;
     T rz = T(0);
-#pragma unroll (kMGUnroll)
+#pragma unroll (U)
     for (int k = kb; k < ke; k += step) {
         const int c = cube[k];
         const T t = fma(wd, rhs[k] - lap19<T>(Zs, c, v.S, v.S2, A), Zs[c]);
@@ -212,19 +213,19 @@ __device__ __forceinline__ T mg_smooth(const SolveParams& P, const MGView<T>& v,
 // Tc cube (its Z cube when level 1 is the coarsest). With z0_ready the caller
 // has already written level l0's first Jacobi sweep (Z = w D^-1 rhs) and
 // synchronised. Returns this thread's share of rhs . z on level l0.
-template <int NT, typename T>
+template <int NT, typename T, int U = 2>
 __device__ __forceinline__ T mg_vcycle(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot,
                                        const T* __restrict__ r0, int l0 = 0, bool z0_ready = false) {
     const int t = threadIdx.x;
     for (int l = l0; l < M.L; ++l) {
         const MGView<T> v = mg_view<T>(P, G, M, slot, l, r0);
         if (!(l == l0 && z0_ready)) {
-            mg_jacobi0(P, v, t, v.n, NT);
+            mg_jacobi0<T, U>(P, v, t, v.n, NT);
             __syncthreads();
         }
-        mg_residual(P, v, t, v.n, NT);
+        mg_residual<T, U>(P, v, t, v.n, NT);
         __syncthreads();
-        mg_restrict(v, M.lv[l + 1], t, M.lv[l + 1].n, NT);
+        mg_restrict<T, U>(v, M.lv[l + 1], t, M.lv[l + 1].n, NT);
         __syncthreads();
     }
     {
@@ -238,9 +239,9 @@ __device__ __forceinline__ T mg_vcycle(const SolveParams& P, const BallGeo& G, c
     T rz = T(0);
     for (int l = M.L - 1; l >= l0; --l) {
         const MGView<T> v = mg_view<T>(P, G, M, slot, l, r0), vc = mg_view<T>(P, G, M, slot, l + 1, r0);
-        mg_prolong(v, vc, (l + 1 == M.L) ? vc.Z : vc.Tc, t, v.n, NT);
+        mg_prolong<T, U>(v, vc, (l + 1 == M.L) ? vc.Z : vc.Tc, t, v.n, NT);
         __syncthreads();
-        rz = mg_smooth(P, v, t, v.n, NT);
+        rz = mg_smooth<T, U>(P, v, t, v.n, NT);
         __syncthreads();
     }
     return rz;

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "exx_mg.cuh"
+#include "exx_phases.cuh"
 
 namespace exx {
 
@@ -82,7 +83,7 @@ __device__ int cg_ball(T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d,
 //   T = float: the inner solve of the FP64 refinement loop (precision 1): the
 //   recurrence and the V-cycle in FP32 on the normalised residual, the stop
 //   test of the refinement loop on the FP64 residual.
-template <int NT, typename T>
+template <int NT, typename T, int U>
 __device__ __forceinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot,
                                       T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d, T* __restrict__ ap, T rr,
                                       T target2, int max_iter, T (*red)[33], int& flip, T& rr_out) {
@@ -93,7 +94,7 @@ __device__ __forceinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, co
     const T* __restrict__ Z = reinterpret_cast<const T*>(slot + P.off_tc);  // z = M r (level-0 cube)
     T* __restrict__ Zj = reinterpret_cast<T*>(slot + P.off_zc);             // the V-cycle's first Jacobi sweep
     const T wd = mg_wd<T>(P, 0);
-    T rz = block_sum<NT, T>(mg_vcycle<NT, T>(P, G, M, slot, r), red, flip);
+    T rz = block_sum<NT, T>(mg_vcycle<NT, T, U>(P, G, M, slot, r), red, flip);
     for (int k = threadIdx.x; k < n_pe; k += NT) {
         const int c = cube[k];
         pc[c] = Z[c];
@@ -102,7 +103,7 @@ __device__ __forceinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, co
     while (rr > target2 && it < max_iter) {
         __syncthreads();  // p
         T pap = T(0);
-#pragma unroll (kMGUnroll)
+#pragma unroll (U)
         for (int k = threadIdx.x; k < n_pe; k += NT) {
             const int c = cube[k];
             const T a = lap19<T>(pc, c, S, S2, A);
@@ -113,7 +114,7 @@ __device__ __forceinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, co
         const T al = rz / pap;
         T rrn = T(0);
         // d, r and the V-cycle's first sweep Z = w D^-1 r in one pass
-#pragma unroll (kMGUnroll)
+#pragma unroll (U)
         for (int k = threadIdx.x; k < n_pe; k += NT) {
             const int c = cube[k];
             d[k] = fma(al, pc[c], d[k]);
@@ -126,10 +127,10 @@ __device__ __forceinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, co
         ++it;
         rr = rrn;
         if (rrn <= target2 || !(rrn == rrn)) break;
-        const T rzn = block_sum<NT, T>(mg_vcycle<NT, T>(P, G, M, slot, r, 0, true), red, flip);
+        const T rzn = block_sum<NT, T>(mg_vcycle<NT, T, U>(P, G, M, slot, r, 0, true), red, flip);
         const T be = rzn / rz;
         rz = rzn;
-#pragma unroll (kMGUnroll)
+#pragma unroll (U)
         for (int k = threadIdx.x; k < n_pe; k += NT) {
             const int c = cube[k];
             pc[c] = fma(be, pc[c], Z[c]);
@@ -144,15 +145,19 @@ __device__ __forceinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, co
 // --------------------------------------------------------------------------
 // Resident CTAs per SM the launch bounds ask for: two of the FP64 and the
 // 512-thread kernels; for the multigrid kernels 1024 threads per SM, except
-// the 256-thread FP32 one, which takes five CTAs (1280 threads, 48 registers):
-// the sweeps wait on DRAM, and the fifth CTA's loads in flight outweigh the
-// spills of its setup and finish phases (measured: 4 CTAs 0.580 s, 5 0.566,
-// 6 0.616 on the water-64 workload).
-template <int NT>
-constexpr int mg_min_blocks() { return NT == 256 ? 5 : 1024 / NT; }
+// the 256-thread FP32 one: the sweeps wait on DRAM, and more CTAs keep more
+// loads in flight at the price of registers (spills) and of cache space per
+// pair. ONE_BALL (every pair on one PE ball, fixed radii): six CTAs, 40
+// registers, the sweeps unrolled by 2; per-pair radii, whose largest balls
+// then thrash the caches at six: five CTAs, 48 registers, no unrolling.
+// Measured on one box, water-64 workload: five 0.512 s (unrolled) / 0.507
+// (not), six 0.488 (unrolled); batched-uneven workload: five 0.331 / 0.328,
+// six 0.467 (unrolled).
+template <int NT, bool ONE_BALL>
+constexpr int mg_min_blocks() { return NT == 256 ? (ONE_BALL ? 6 : 5) : 1024 / NT; }
 
-template <int NT, bool MIXED, bool MG = false>
-__global__ void __launch_bounds__(NT, MG ? mg_min_blocks<NT>() : (MIXED ? 1 : 2)) pair_kernel(const __grid_constant__ SolveParams P) {
+template <int NT, bool MIXED, bool MG = false, bool ONE_BALL = false>
+__global__ void __launch_bounds__(NT, MG ? mg_min_blocks<NT, ONE_BALL>() : (MIXED ? 1 : 2)) pair_kernel(const __grid_constant__ SolveParams P) {
     extern __shared__ double smem[];
     __shared__ double red[2][33];
     __shared__ float red32[2][33];
@@ -236,7 +241,7 @@ __global__ void __launch_bounds__(NT, MG ? mg_min_blocks<NT>() : (MIXED ? 1 : 2)
             double rr_fin;
             const double target2 = P.tol * P.tol * bb;
             if (MG && P.mg[pr.geo].L > 0)
-                iters = mg_pcg<NT, double>(P, G, P.mg[pr.geo], slot, pc, r, d, ap, bb, target2, P.max_iter, red,
+                iters = mg_pcg<NT, double, 2>(P, G, P.mg[pr.geo], slot, pc, r, d, ap, bb, target2, P.max_iter, red,
                                            flip, rr_fin);
             else
                 iters = cg_ball<double, NT>(pc, r, d, ap, cube, n_pe, S, S2, neg64, bb, target2, P.max_iter, red,
@@ -283,7 +288,7 @@ __global__ void __launch_bounds__(NT, MG ? mg_min_blocks<NT>() : (MIXED ? 1 : 2)
                 float rr_fin;
                 const int budget = min(P.inner_max_iter, P.max_iter - iters);
                 if (MG && P.mg[pr.geo].L > 0)
-                    iters += mg_pcg<NT, float>(P, G, P.mg[pr.geo], slot, p32, r32, d32, ap32, rr32,
+                    iters += mg_pcg<NT, float, ONE_BALL ? 2 : 1>(P, G, P.mg[pr.geo], slot, p32, r32, d32, ap32, rr32,
                                                (float)(eta * eta) * rr32, budget, red32, flip32, rr_fin);
                 else
                     iters += cg_ball<float, NT>(p32, r32, d32, ap32, cube, n_pe, S, S2, neg32, rr32,
@@ -386,6 +391,7 @@ static cudaError_t launch_t(const SolveParams& P, int grid, size_t smem, cudaStr
 cudaError_t launch_pair_kernel(const SolveParams& P, int threads, bool mixed, int grid, size_t smem, cudaStream_t st) {
     if (P.mg) {  // the multigrid-preconditioned CG: FP64, or FP32 inside FP64 refinement
         if (!mixed) pair_kernel<512, false, true><<<grid, 512, smem, st>>>(P);
+        else if (threads == 256 && P.n_geo == 1) pair_kernel<256, true, true, true><<<grid, 256, smem, st>>>(P);
         else if (threads == 256) pair_kernel<256, true, true><<<grid, 256, smem, st>>>(P);
         else if (threads == 1024) pair_kernel<1024, true, true><<<grid, 1024, smem, st>>>(P);
         else pair_kernel<512, true, true><<<grid, 512, smem, st>>>(P);
@@ -397,9 +403,10 @@ cudaError_t launch_pair_kernel(const SolveParams& P, int threads, bool mixed, in
     return mixed ? launch_t<512, true>(P, grid, smem, st) : launch_t<512, false>(P, grid, smem, st);
 }
 
-cudaError_t pair_kernel_occupancy(int threads, bool mixed, bool mg, size_t smem, int* blocks_per_sm) {
+cudaError_t pair_kernel_occupancy(int threads, bool mixed, bool mg, bool one_ball, size_t smem, int* blocks_per_sm) {
     const void* f;
     if (mg && !mixed) f = (const void*)pair_kernel<512, false, true>;
+    else if (mg && threads == 256 && one_ball) f = (const void*)pair_kernel<256, true, true, true>;
     else if (mg && threads == 256) f = (const void*)pair_kernel<256, true, true>;
     else if (mg && threads == 1024) f = (const void*)pair_kernel<1024, true, true>;
     else if (mg) f = (const void*)pair_kernel<512, true, true>;
