@@ -83,6 +83,8 @@ __device__ int cg_ball(T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d,
 //   T = float: the inner solve of the FP64 refinement loop (precision 1): the
 //   recurrence and the V-cycle in FP32 on the normalised residual, the stop
 //   test of the refinement loop on the FP64 residual.
+// Inlined into the kernel with P its own parameter block, so that the sweeps
+// read the level operators as parameter constants; U unrolls the sweeps.
 template <int NT, typename T, int U>
 __device__ __forceinline__ int mg_pcg(const SolveParams& P, const BallGeo& G, const MGGeo& M, char* slot,
                                       T* __restrict__ pc, T* __restrict__ r, T* __restrict__ d, T* __restrict__ ap, T rr,
