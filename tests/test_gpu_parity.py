@@ -484,19 +484,23 @@ def test_warm_start_from_previous_step(torch):
 
 # --------------------------------------------------------------------------
 # Multigrid-preconditioned CG (preconditioner 1): FP64 on one CTA per pair;
-# FP32 inside the FP64 refinement on one CTA per pair (solver_kind 1) or on a
-# cluster of C CTAs per pair (solver_kind 0 or 2), one or two CTAs per SM
+# FP32 inside the FP64 refinement on one CTA per pair (solver_kind 1; 256
+# threads by default, 512 or 1024 on request) or on a cluster of C CTAs per
+# pair (solver_kind 0 or 2), one or two CTAs per SM
 # --------------------------------------------------------------------------
 MG_FORMS = [dict(precision=0), dict(precision=1), dict(precision=1, solver_kind=2),
             dict(precision=1, solver_kind=2, cluster_size=2), dict(precision=1, solver_kind=2, cluster_size=4),
             dict(precision=1, solver_kind=2, cluster_size=16),
-            dict(precision=1, solver_kind=2, cluster_size=8, ctas_per_sm=1)]
-MG_IDS = ["fp64", "fp32-cta", "fp32-c8", "fp32-c2", "fp32-c4", "fp32-c16", "fp32-c8-1sm"]
+            dict(precision=1, solver_kind=2, cluster_size=8, ctas_per_sm=1),
+            dict(precision=1, threads=512), dict(precision=1, threads=1024)]
+MG_IDS = ["fp64", "fp32-cta", "fp32-c8", "fp32-c2", "fp32-c4", "fp32-c16", "fp32-c8-1sm", "fp32-cta512",
+          "fp32-cta1024"]
 
 
 def _mg_form_check(out, form):
     if form.get("solver_kind", 0) != 2:
         assert out["stats"]["solver_kind"] == 1
+        assert out["stats"]["threads"] == form.get("threads", 256 if form.get("precision") == 1 else 512)
     else:
         assert out["stats"]["solver_kind"] == 2
         assert out["stats"]["cluster_size"] == form.get("cluster_size", 8)
