@@ -450,6 +450,31 @@ exx_status exx_quad_map(int r_pe, int cluster_size, int threads, int quads, int 
                         int *quad_k, size_t cap, int *info);
 
 /*
+ * The multigrid hierarchy that preconditions the CG (preconditioner = 1; the
+ * paper names preconditioning as the way to fewer iterations, Sec. IV.B and
+ * Sec. V), built on the host as exx_init builds it, with no CUDA call. For a
+ * PE ball of radius r_pe at spacings delta, level l >= 1 is the ball of radius
+ * R_l = ceil(R_{l-1} / 2) (R_0 = r_pe) at spacing 2^l delta, down to the first
+ * R_l <= 3; its points are those of the ball in lexicographic (x, y, z)
+ * order, held in a zero-padded cube of side 2 R_l + 7.
+ *   r_pe      PE radius in grid points (4..127; a ball of radius 3 or less
+ *             has no coarser level)
+ *   delta     host double[3]: grid spacings in bohr (> 0)
+ *   radius, points, side   host int[cap]: R_l, the ball's point count and the
+ *             cube side of levels l = 1..L, level l at entry l - 1
+ *   cap       entries each of radius, points and side can hold
+ *   levels    host, receives L
+ *   minv      host double[points[L-1]^2], or NULL: the inverse of the coarsest
+ *             level's operator (-lap of Eq. d2_1 at spacing 2^L delta, zero
+ *             outside the ball), row-major in the level's point order
+ *   minv_cap  entries minv can hold
+ * Returns EXX_EINVAL on bad arguments, a cap or minv_cap too small, or a
+ * hierarchy that cannot be built; the message is read with exx_last_error(NULL).
+ */
+exx_status exx_mg_levels(int r_pe, const double delta[3], int *radius, int *points, int *side, int cap, int *levels,
+                         double *minv, size_t minv_cap);
+
+/*
  * Measures the FP64 FMA rate of the current device, the roofline denominator
  * of the plain FP64 CG (whose binding unit on this GPU is the FP64 pipe, not
  * HBM). The paper has no counterpart. Eight independent FMA chains per thread

@@ -1889,6 +1889,31 @@ extern "C" exx_status exx_quad_map(int r_pe, int cluster_size, int threads, int 
     return EXX_OK;
 }
 
+extern "C" exx_status exx_mg_levels(int r_pe, const double delta[3], int* radius, int* points, int* side, int cap,
+                                    int* levels, double* minv, size_t minv_cap) {
+    if (r_pe < 4 || r_pe > 127 || !delta || !radius || !points || !side || !levels || cap < 0)
+        return fail(nullptr, EXX_EINVAL, "exx_mg_levels: bad arguments");
+    for (int a = 0; a < 3; ++a)
+        if (!(delta[a] > 0.0) || !std::isfinite(delta[a]))
+            return fail(nullptr, EXX_EINVAL, "exx_mg_levels: spacings must be finite and > 0");
+    std::vector<HostMGLevel> lv;
+    std::vector<double> mi;
+    if (!build_mg_levels(r_pe, delta, lv, mi))
+        return fail(nullptr, EXX_EINVAL, "exx_mg_levels: the hierarchy could not be built");
+    *levels = (int)lv.size();
+    if (cap < (int)lv.size()) return fail(nullptr, EXX_EINVAL, "exx_mg_levels: cap smaller than the level count");
+    for (size_t l = 0; l < lv.size(); ++l) {
+        radius[l] = lv[l].R;
+        points[l] = (int)lv[l].off.size();
+        side[l] = lv[l].side;
+    }
+    if (minv) {
+        if (minv_cap < mi.size()) return fail(nullptr, EXX_EINVAL, "exx_mg_levels: minv_cap too small");
+        std::memcpy(minv, mi.data(), sizeof(double) * mi.size());
+    }
+    return EXX_OK;
+}
+
 extern "C" exx_status exx_radius_classes(const exx_ctx* c, int* r_pe, int* cluster_size, int* resident, int cap,
                                          int* n_class) {
     if (!c || !n_class) return fail(const_cast<exx_ctx*>(c), EXX_EINVAL, "exx_radius_classes: NULL argument");

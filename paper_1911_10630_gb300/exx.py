@@ -83,6 +83,7 @@ SIGNATURES = [
     ("exx_radius_classes", ctypes.c_int, [_ctx_p, _i, _i, _i, ctypes.c_int, _i]),
     ("exx_quad_map", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("exx_mg_levels", ctypes.c_int, [ctypes.c_int, _d, _i, _i, _i, ctypes.c_int, _i, _d, ctypes.c_size_t]),
     ("exx_load_guess_model", ctypes.c_int, [_ctx_p, _vp, ctypes.c_size_t]),
     ("exx_pair_list_static", ctypes.c_int, [_vp, ctypes.c_int, _d, _i, ctypes.c_double, _vp, ctypes.c_int, _i,
                                             _vp]),
@@ -371,6 +372,29 @@ def quad_map(r_pe: int, cluster_size: int, threads: int, quads: int, bank_aware:
                                pk.ctypes.data, kk.ctypes.data, n, info.ctypes.data))
     shape = (cluster_size, quads, threads)
     return pk.reshape(shape), kk.reshape(shape), info
+
+
+def mg_levels(r_pe: int, delta, want_minv: bool = False):
+    """exx_mg_levels: the multigrid hierarchy of a PE ball, built on the host.
+    Returns a dict with int32 arrays radius, points, side (levels 1..L) and,
+    with want_minv, the coarsest level's inverse operator [n][n]."""
+    d = np.ascontiguousarray(delta, dtype=np.float64)
+    cap = 8
+    radius, points, side = (np.zeros(cap, np.int32) for _ in range(3))
+    levels = ctypes.c_int(0)
+    lib = load()
+    _check(lib.exx_mg_levels(int(r_pe), d.ctypes.data_as(_d), radius.ctypes.data_as(_i), points.ctypes.data_as(_i),
+                             side.ctypes.data_as(_i), cap, ctypes.byref(levels), None, 0))
+    L = levels.value
+    out = dict(radius=radius[:L].copy(), points=points[:L].copy(), side=side[:L].copy())
+    if want_minv:
+        n = int(points[L - 1])
+        m = np.zeros(n * n, np.float64)
+        _check(lib.exx_mg_levels(int(r_pe), d.ctypes.data_as(_d), radius.ctypes.data_as(_i),
+                                 points.ctypes.data_as(_i), side.ctypes.data_as(_i), cap, ctypes.byref(levels),
+                                 m.ctypes.data_as(_d), m.size))
+        out["minv"] = m.reshape(n, n)
+    return out
 
 
 def guess_model_blob(S: int, params: np.ndarray) -> bytes:
