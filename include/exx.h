@@ -450,6 +450,28 @@ exx_status exx_quad_map(int r_pe, int cluster_size, int threads, int quads, int 
                         int *quad_k, size_t cap, int *info);
 
 /*
+ * The ball tables the kernels index, built on the host as exx_init builds
+ * them, with no CUDA call: the proto-subdomain of Algorithm 2 (Sec. III.C,
+ * Step III), the PE ball |o| <= r_pe followed by the shell r_pe < |o| <= r_me,
+ * each in lexicographic (x, y, z) order.
+ *   r_pe, r_me  radii in grid points, 1 <= r_pe < r_me <= 64
+ *   off         host int[cap]: packed offsets (x + 128) | (y + 128) << 8 |
+ *               (z + 128) << 16
+ *   cube        host int[cap], or NULL: each point's index in the cube of side
+ *               S = 2 r_me + 1 around the origin, ((x + r_me) S + y + r_me) S +
+ *               z + r_me
+ *   near        host int[cap], or NULL: 1 for a shell point whose far-field
+ *               potential is evaluated in FP64 (the layer next to the PE ball
+ *               that the stencil of Eq. d2_1 reads), 0 for the other shell
+ *               points (FP32) and for the PE ball
+ *   cap         entries each array can hold (at least the ME ball's points)
+ *   n_pe, n_me  host: points of the PE ball and of the whole ME ball
+ * Returns EXX_EINVAL on bad arguments or a cap too small (n_pe and n_me are
+ * still written); the message is read with exx_last_error(NULL).
+ */
+exx_status exx_ball_tables(int r_pe, int r_me, int *off, int *cube, int *near, size_t cap, int *n_pe, int *n_me);
+
+/*
  * The multigrid hierarchy that preconditions the CG (preconditioner = 1; the
  * paper names preconditioning as the way to fewer iterations, Sec. IV.B and
  * Sec. V), built on the host as exx_init builds it, with no CUDA call. For a

@@ -1889,6 +1889,32 @@ extern "C" exx_status exx_quad_map(int r_pe, int cluster_size, int threads, int 
     return EXX_OK;
 }
 
+extern "C" exx_status exx_ball_tables(int r_pe, int r_me, int* off, int* cube, int* near, size_t cap, int* n_pe,
+                                      int* n_me) {
+    if (r_pe < 1 || r_me <= r_pe || r_me > 64 || !off || !n_pe || !n_me)
+        return fail(nullptr, EXX_EINVAL, "exx_ball_tables: bad arguments");
+    HostBall B;
+    build_ball(B, r_pe, r_me, r_me);
+    *n_pe = B.n_pe;
+    *n_me = B.n_me;
+    if (cap < (size_t)B.n_me) return fail(nullptr, EXX_EINVAL, "exx_ball_tables: cap smaller than the ME ball");
+    std::memcpy(off, B.off.data(), sizeof(int) * B.off.size());
+    if (cube) std::memcpy(cube, B.cube.data(), sizeof(int) * B.cube.size());
+    if (near) {
+        // the near list holds (ME row << 8) | (z + 128); mark those points by
+        // their cube index
+        std::vector<char> is_near((size_t)(2 * r_me + 1) * (2 * r_me + 1) * (2 * r_me + 1), 0);
+        const int S = 2 * r_me + 1;
+        for (int e : B.sh_near) {
+            const RowRec& R = B.rows_me[e >> 8];
+            const int z = (e & 0xff) - 128;
+            is_near[((size_t)(R.ox + r_me) * S + (R.oy + r_me)) * S + (z + r_me)] = 1;
+        }
+        for (int k = 0; k < B.n_me; ++k) near[k] = k < B.n_pe ? 0 : (int)is_near[B.cube[k]];
+    }
+    return EXX_OK;
+}
+
 extern "C" exx_status exx_mg_levels(int r_pe, const double delta[3], int* radius, int* points, int* side, int cap,
                                     int* levels, double* minv, size_t minv_cap) {
     if (r_pe < 4 || r_pe > 127 || !delta || !radius || !points || !side || !levels || cap < 0)

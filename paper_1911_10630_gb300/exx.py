@@ -83,6 +83,7 @@ SIGNATURES = [
     ("exx_radius_classes", ctypes.c_int, [_ctx_p, _i, _i, _i, ctypes.c_int, _i]),
     ("exx_quad_map", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("exx_ball_tables", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i, _i, _i, ctypes.c_size_t, _i, _i]),
     ("exx_mg_levels", ctypes.c_int, [ctypes.c_int, _d, _i, _i, _i, ctypes.c_int, _i, _d, ctypes.c_size_t]),
     ("exx_load_guess_model", ctypes.c_int, [_ctx_p, _vp, ctypes.c_size_t]),
     ("exx_pair_list_static", ctypes.c_int, [_vp, ctypes.c_int, _d, _i, ctypes.c_double, _vp, ctypes.c_int, _i,
@@ -372,6 +373,23 @@ def quad_map(r_pe: int, cluster_size: int, threads: int, quads: int, bank_aware:
                                pk.ctypes.data, kk.ctypes.data, n, info.ctypes.data))
     shape = (cluster_size, quads, threads)
     return pk.reshape(shape), kk.reshape(shape), info
+
+
+def ball_tables(r_pe: int, r_me: int):
+    """exx_ball_tables: the proto-subdomain tables built on the host. Returns a
+    dict with int32 arrays off (packed), cube and near (one entry per ME ball
+    point, PE ball first) and the counts n_pe, n_me."""
+    n_pe, n_me = ctypes.c_int(0), ctypes.c_int(0)
+    lib = load()
+    status = lib.exx_ball_tables(int(r_pe), int(r_me), (ctypes.c_int * 1)(), None, None, 0, ctypes.byref(n_pe),
+                                 ctypes.byref(n_me))
+    if n_me.value == 0:
+        _check(status)
+    n = n_me.value
+    off, cube, near = (np.zeros(n, np.int32) for _ in range(3))
+    _check(lib.exx_ball_tables(int(r_pe), int(r_me), off.ctypes.data_as(_i), cube.ctypes.data_as(_i),
+                               near.ctypes.data_as(_i), n, ctypes.byref(n_pe), ctypes.byref(n_me)))
+    return dict(off=off, cube=cube, near=near, n_pe=n_pe.value, n_me=n_me.value)
 
 
 def mg_levels(r_pe: int, delta, want_minv: bool = False):
