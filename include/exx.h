@@ -365,6 +365,18 @@ exx_status exx_debug_pair(exx_ctx *ctx, const double *orbitals, int index, doubl
 exx_status exx_apply_operator(exx_ctx *ctx, const double *p, double *ap, void *stream);
 
 /*
+ * Applies the multigrid preconditioner of the PCG (preconditioner = 1; the
+ * paper names preconditioning as the way to fewer iterations, Sec. IV.B and
+ * Sec. V) once: z = M r, one symmetric V-cycle in FP64 over the levels of
+ * exx_mg_levels, on the PE ball of the context's largest R_PE.
+ *   r, z      device, [N_PE] FP64 in Algorithm 2 order
+ * Uses workspace slot 0 and leaves it as the solvers expect; waits for the
+ * stream. Must not overlap an exx_compute call on the same context.
+ * EXX_EINVAL without a hierarchy (preconditioner 0, or R_PE <= 3).
+ */
+exx_status exx_apply_preconditioner(exx_ctx *ctx, const double *r, double *z, void *stream);
+
+/*
  * The launch plan of per-pair radii on the cluster solver (radii_mode 1,
  * precision 1): one class per R_PE, launched largest first. The paper has no
  * counterpart (its subdomain sizes vary per pair, Sec. IV.A; how they map to

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libexx_gb300.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["exx_api.cu", "exx_pairs.cu", "exx_solve.cu", "exx_cluster.cu", "exx_static.cu", "exx_unet.cu", "exx_probe.cu",
+SOURCES = ["exx_api.cu", "exx_pairs.cu", "exx_solve.cu", "exx_cluster.cu", "exx_static.cu", "exx_unet.cu", "exx_probe.cu", "exx_debug.cu",
            "exx_geometry.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

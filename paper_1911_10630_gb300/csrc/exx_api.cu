@@ -37,6 +37,7 @@ cudaError_t set_multipole_const_cluster(const MultipoleConst& mc);
 size_t pair_kernel_smem(int Rc, int r_pe_max);
 cudaError_t launch_pair_kernel(const SolveParams& P, int threads, bool mixed, int grid, size_t smem, cudaStream_t st);
 cudaError_t pair_kernel_occupancy(int threads, bool mixed, bool mg, bool one_ball, size_t smem, int* blocks_per_sm);
+cudaError_t launch_mg_apply(const SolveParams& P, int geo, const double* r, double* z, cudaStream_t st);  // exx_debug.cu
 cudaError_t launch_debug_readback(const SolveParams& P, const PairRec& pr, double* rho_me, double* v_me,
                                   cudaStream_t st);
 cudaError_t launch_apply(const SolveParams& P, const double* p, double* ap, cudaStream_t st);
@@ -1856,6 +1857,26 @@ extern "C" exx_status exx_apply_operator(exx_ctx* c, const double* p, double* ap
     cudaStream_t st = (cudaStream_t)stream;
     CK(launch_apply(c->P, p, ap, st), "apply operator");
     CK(cudaStreamSynchronize(st), "apply operator (synchronize)");
+    return EXX_OK;
+}
+
+extern "C" exx_status exx_apply_preconditioner(exx_ctx* c, const double* r, double* z, void* stream) {
+    if (!c) return fail(nullptr, EXX_EINVAL, "exx_apply_preconditioner: ctx is NULL");
+    if (!r || !z) return fail(c, EXX_EINVAL, "exx_apply_preconditioner: NULL argument");
+    const int geo = c->n_geo - 1;
+    if (!c->P.mg || c->balls[geo].r_pe <= 3)
+        return fail(c, EXX_EINVAL, "exx_apply_preconditioner: no multigrid hierarchy (needs preconditioner = 1 and R_PE > 3)");
+    (void)cudaGetLastError();
+    cudaStream_t st = (cudaStream_t)stream;
+    // slot 0's multigrid cubes: the FP32 solver keeps floats there, which an
+    // FP64 view does not see as zero off the ball; cleared before the cycle,
+    // and after it for the solvers, which expect zero off every ball
+    char* mg0 = c->ws + c->P.off_zc;
+    const size_t mgb = c->slot_bytes - c->P.off_zc;
+    CK(cudaMemsetAsync(mg0, 0, mgb, st), "apply preconditioner (clear)");
+    CK(launch_mg_apply(c->P, geo, r, z, st), "apply preconditioner");
+    CK(cudaMemsetAsync(mg0, 0, mgb, st), "apply preconditioner (clear)");
+    CK(cudaStreamSynchronize(st), "apply preconditioner (synchronize)");
     return EXX_OK;
 }
 

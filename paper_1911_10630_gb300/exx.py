@@ -79,6 +79,7 @@ SIGNATURES = [
     ("exx_get_pairs", ctypes.c_int, [_ctx_p, _i, _i, _i, _i, _d, _i, ctypes.c_int, _i]),
     ("exx_debug_pair", ctypes.c_int, [_ctx_p, _vp, ctypes.c_int, _d, _d, _d, _vp]),
     ("exx_apply_operator", ctypes.c_int, [_ctx_p, _vp, _vp, _vp]),
+    ("exx_apply_preconditioner", ctypes.c_int, [_ctx_p, _vp, _vp, _vp]),
     ("exx_ball_size", ctypes.c_int, [_ctx_p, _i, _i]),
     ("exx_radius_classes", ctypes.c_int, [_ctx_p, _i, _i, _i, ctypes.c_int, _i]),
     ("exx_quad_map", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -300,6 +301,9 @@ class Exx:
 
     def apply_operator(self, p, ap, stream=None):
         _check(load().exx_apply_operator(self._ctx, _ptr(p), _ptr(ap), _stream_handle(stream)), self._ctx)
+
+    def apply_preconditioner(self, r, z, stream=None):
+        _check(load().exx_apply_preconditioner(self._ctx, _ptr(r), _ptr(z), _stream_handle(stream)), self._ctx)
 
 
 class GuessNet:
