@@ -181,3 +181,47 @@ def test_guess_create_rejects_bad_sizes(lib):
     assert "multiple of 8" in lib.exx_last_error(None).decode()
     assert lib.exx_guess_create(ctypes.byref(h), 16, 0) == -1
     assert not h.value
+
+
+C_CALLER = r"""
+#include <stdio.h>
+#include <stdlib.h>
+#include "exx.h"
+#include "exx_guess.h"
+
+int main(void) {
+    int n_pe = 0, n_me = 0, levels = 0, radius[8], points[8], side[8];
+    const double delta[3] = {0.2, 0.2, 0.2};
+    int *off = (int *)malloc(sizeof(int) * 40000);
+    if (!off) return 2;
+    if (exx_ball_tables(16, 20, off, NULL, NULL, 40000, &n_pe, &n_me) != EXX_OK) return 3;
+    if (exx_mg_levels(24, delta, radius, points, side, 8, &levels, NULL, 0) != EXX_OK) return 4;
+    printf("%d %d %d", n_pe, n_me, levels);
+    for (int l = 0; l < levels; ++l) printf(" %d", radius[l]);
+    printf("\n");
+    free(off);
+    return exx_mg_levels(3, delta, radius, points, side, 8, &levels, NULL, 0) == EXX_EINVAL ? 0 : 5;
+}
+"""
+
+
+def test_a_c_program_compiles_links_and_calls_the_boundary(tmp_path, lib):
+    """The headers are plain C (C99, warnings as errors); a C program links the
+    library and calls host-only entry points without any GPU: the ball counts
+    of R 16 / 20 (17,077 and 33,401 points) and the levels of an R_PE 24
+    hierarchy (12, 6, 3)."""
+    import shutil
+    import subprocess
+    from paper_1911_10630_gb300 import exx
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(exx.LIB_PATH)
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-L", libdir, "-lexx_gb300", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, (out.returncode, out.stdout, out.stderr)
+    assert out.stdout.split() == ["17077", "33401", "3", "12", "6", "3"]
